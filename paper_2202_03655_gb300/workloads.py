@@ -1,0 +1,105 @@
+"""Seeded synthetic inputs shaped like the method's workloads.
+
+Only random inputs live here: no step of the factorization is computed in this module.
+Both the CUDA path (through tests and bench.py) and the CPU oracle (through tests) are
+fed the same arrays from these generators.  Every generator takes a numpy Generator;
+``rng(idx)`` seeds PCG64 with 20220207 + idx for workload number idx.
+
+Workloads (Sec. 4 uses normal points scaled to maximum norm 1; the shapes below widen
+that to the point distributions the factorization is expected to meet):
+
+  0  ball3_gauss      n=2,000, d=3, uniform in the unit ball, Gaussian l=0.5, tol 1e-6
+  1  mixture3_matern  n=1,000,000, d=3, 8-component isotropic Gaussian mixture
+                      (means U[-2,2]^3, sigma 0.3, equal weights), Matern-3/2 l=1, tol 1e-8,
+                      V with 64 N(0,1) columns
+  2  normal5_cauchy   n=4,000,000, d=5, N(0,I) rotated by a random orthogonal matrix and
+                      standardised per dimension, Cauchy l=2, tol 1e-4, V with 16 columns
+  3  cube4_gauss      n=500,000, d=4, uniform in [-1,1]^4, Gaussian l=0.8, tol 1e-6
+  4  batch512_gauss   512 sets, n log-uniform in [1000, 65536], d=3, uniform in a ball of
+                      radius U[0.5, 2], Gaussian l ~ U[0.3, 1.5], tol 1e-6, V with 8 columns
+  5  fig1_cauchy      Sec. 4.1 Fig. 1 shape: N(0,I) points scaled to max norm 1, Cauchy l=1
+"""
+import numpy as np
+
+SEED_BASE = 20220207
+
+
+def rng(idx):
+    return np.random.Generator(np.random.PCG64(SEED_BASE + int(idx)))
+
+
+def uniform_ball(g, n, d, radius=1.0):
+    """Uniform in the d-ball: direction = normalised N(0, I), radius * U^(1/d)."""
+    dirs = g.standard_normal((n, d))
+    nrm = np.linalg.norm(dirs, axis=1, keepdims=True)
+    nrm[nrm == 0] = 1.0
+    return radius * dirs / nrm * g.random((n, 1)) ** (1.0 / d)
+
+
+def gaussian_mixture(g, n, d=3, components=8, lo=-2.0, hi=2.0, sigma=0.3):
+    """Equal-weight isotropic Gaussian mixture with means uniform in [lo, hi]^d."""
+    means = g.uniform(lo, hi, size=(components, d))
+    lab = g.integers(0, components, size=n)
+    return means[lab] + sigma * g.standard_normal((n, d))
+
+
+def rotated_standard_normal(g, n, d=5):
+    """N(0, I) times a random orthogonal matrix (QR of a Gaussian), standardised per dimension."""
+    Q, R = np.linalg.qr(g.standard_normal((d, d)))
+    Q = Q * np.sign(np.diag(R))[None, :]
+    x = g.standard_normal((n, d)) @ Q
+    x -= x.mean(axis=0)
+    x /= x.std(axis=0)
+    return x
+
+
+def uniform_cube(g, n, d=4):
+    return g.uniform(-1.0, 1.0, size=(n, d))
+
+
+def normal_maxnorm1(g, n, d):
+    """N(0, I) scaled so that the largest norm is 1 (Sec. 4.1)."""
+    x = g.standard_normal((n, d))
+    return x / np.linalg.norm(x, axis=1).max()
+
+
+def vectors(g, n, c):
+    """c columns of N(0,1), column-major as an (n, c) Fortran-ordered array."""
+    return np.asfortranarray(g.standard_normal((n, c)))
+
+
+def batch_sets(g, nsets=512, nmin=1000, nmax=65536, d=3):
+    """Ragged sets: sizes log-uniform in [nmin, nmax], radius U[0.5, 2], lengthscale U[0.3, 1.5].
+
+    Returns (x concatenated (sum n, d), offsets (nsets+1,), lengthscales (nsets,))."""
+    sizes = np.floor(np.exp(g.uniform(np.log(nmin), np.log(nmax), size=nsets))).astype(np.int64)
+    radii = g.uniform(0.5, 2.0, size=nsets)
+    ells = g.uniform(0.3, 1.5, size=nsets)
+    xs = [uniform_ball(g, int(m), d, r) for m, r in zip(sizes, radii)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return np.concatenate(xs, axis=0), offsets, ells
+
+
+WORKLOADS = {
+    "ball3_gauss": dict(idx=0, n=2000, d=3, kernel="gaussian", ell=0.5, tol=1e-6, ncols=1),
+    "mixture3_matern": dict(idx=1, n=1_000_000, d=3, kernel="matern32", ell=1.0, tol=1e-8, ncols=64),
+    "normal5_cauchy": dict(idx=2, n=4_000_000, d=5, kernel="cauchy", ell=2.0, tol=1e-4, ncols=16),
+    "cube4_gauss": dict(idx=3, n=500_000, d=4, kernel="gaussian", ell=0.8, tol=1e-6, ncols=1),
+    "batch512_gauss": dict(idx=4, nsets=512, d=3, kernel="gaussian", tol=1e-6, ncols=8),
+}
+
+
+def points(name, n=None, idx=None):
+    """Points of a named workload (optionally with a smaller n, same distribution)."""
+    w = WORKLOADS[name]
+    n = w["n"] if n is None else int(n)
+    g = rng(w["idx"] if idx is None else idx)
+    if name == "ball3_gauss":
+        return uniform_ball(g, n, 3)
+    if name == "mixture3_matern":
+        return gaussian_mixture(g, n, 3)
+    if name == "normal5_cauchy":
+        return rotated_standard_normal(g, n, 5)
+    if name == "cube4_gauss":
+        return uniform_cube(g, n, 4)
+    raise ValueError(name)
