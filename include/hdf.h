@@ -1,0 +1,169 @@
+/*
+ * hdf.h -- C ABI of the GB300 Harmonic Decomposition Factorization library (libhdf.so).
+ *
+ * Method: Ryan & Damle, "Linear Time Kernel Matrix Approximation via Hyperspherical
+ * Harmonics", ICML 2022.  For points x_1..x_n in R^d and an isotropic kernel k(|x - y|)
+ * the library builds K ~= U diag(S) U^T (Algorithm 1 in the symmetric form of Remark 1)
+ * with a relative error target tol (the abstract: the method takes the tolerance, not
+ * the rank, as input), then applies K~ V = U (S (U^T V)) (Sec. 3.6) and solves
+ * (lambda I + K~) X = B (the system of Eq. opt, via Sherman-Morrison-Woodbury, Sec. 1).
+ *
+ * Conventions for every entry point below:
+ *  - Every call returns an hdf_status; nothing throws across the ABI.  On error the
+ *    output buffers are left untouched and hdf_last_error() (thread-local) describes it.
+ *  - "_dev" pointers are CUDA device pointers, "_host" pointers host memory.  The caller
+ *    owns every buffer it passes; the library owns the opaque hdf_factor and the device
+ *    memory inside it (U, S and work space), released by hdf_free.
+ *  - Points are row-major n x d FP64 (x[i*d + j]).  Vector blocks V, Y, B, X are
+ *    column-major n x ncols with a leading dimension >= n, in the factor's bulk type
+ *    (double for HDF_FP64, float for HDF_FP32).
+ *  - Work is ordered on the given stream (NULL = legacy default stream).  hdf_build
+ *    synchronises the stream (host planning needs device reductions); hdf_matvec is
+ *    asynchronous; hdf_solve synchronises (its small core is solved on the host).
+ *  - Supported: 3 <= d <= 8, n >= 1, tol in (0, 1), lengthscale > 0, p_max <= 128.
+ */
+#ifndef HDF_H
+#define HDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdf_factor hdf_factor;       /* opaque, owned by the library */
+typedef void* hdf_stream;                    /* a cudaStream_t; NULL = default stream */
+
+typedef enum {
+    HDF_OK = 0,
+    HDF_EINVAL = 1,           /* bad argument (message in hdf_last_error) */
+    HDF_ENOMEM = 2,           /* device or host allocation failed */
+    HDF_ECUDA = 3,            /* a CUDA call failed */
+    HDF_ETOL_UNREACHABLE = 4, /* degree cap p_max hit: the factor is built at p = p_max and
+                                 hdf_factor_info reports the Chebyshev tail achieved */
+    HDF_ENOTFINITE = 5,       /* NaN or Inf in the input points */
+    HDF_ESINGULAR = 6,        /* the solve core is singular */
+    HDF_ETIMEOUT = 7,         /* a bounded device wait expired */
+    HDF_ETOOBIG = 8           /* a size exceeds a documented limit */
+} hdf_status;
+
+/* Isotropic kernels of Sec. 4.1 with lengthscale l (the Gaussian in the exp(-r^2/(2 l^2))
+ * convention; the paper's exp(-(r/sigma)^2) is the same family with sigma = sqrt(2) l). */
+typedef enum {
+    HDF_GAUSSIAN = 0,   /* exp(-r^2 / (2 l^2)) */
+    HDF_CAUCHY = 1,     /* 1 / (1 + r^2 / l^2) */
+    HDF_MATERN32 = 2,   /* (1 + sqrt3 r/l) exp(-sqrt3 r/l) */
+    HDF_MATERN52 = 3    /* (1 + sqrt5 r/l + 5 r^2/(3 l^2)) exp(-sqrt5 r/l) */
+} hdf_kernel;
+
+/* Bulk precision: the type of U, of the harmonics and of the matvec GEMMs.  The radial
+ * basis, its Gram matrix, the cores and every small factorisation stay FP64. */
+typedef enum {
+    HDF_FP64 = 0,
+    HDF_FP32 = 1
+} hdf_precision;
+
+typedef struct {
+    int p_max;      /* cap on the Chebyshev degree p (even; default 64, max 128) */
+    double eta;     /* share of tol given to eigenpair truncation (default 1) */
+    int flags;      /* reserved, 0 */
+} hdf_options;
+
+#define HDF_MAX_D 8
+#define HDF_MAX_L 64
+
+typedef struct {
+    int64_t n;
+    int d;
+    int precision;          /* hdf_precision */
+    int p;                  /* Chebyshev degree chosen (Remark 3) */
+    int L;                  /* p / 2, the highest harmonic degree */
+    int reached;            /* 1 if the tail budget was met at p <= p_max */
+    int64_t rank;           /* r = sum_k |H_k| s_k (Sec. 3.6) */
+    int64_t ldu;            /* leading dimension of the row-major n x r U */
+    int64_t nharm;          /* number of harmonics evaluated per point */
+    double center[HDF_MAX_D];
+    double radius;          /* R = max |x_i - c|; x' = (x - c) / (2R) */
+    double mu2;             /* mean of K_ij^2 used for |K|_F = n sqrt(mu2) */
+    double cheb_tail;       /* estimated Chebyshev tail epsilon_c(p) (Sec. 3.5) */
+    double tail_budget;     /* tol sqrt(mu2) / 2 */
+    double drop_budget;     /* eta tol n sqrt(mu2) / 2 */
+    double dropped_cost;    /* sum over dropped eigenpairs of |lambda| |H_k| / |S^{d-1}| */
+    double err_bound;       /* (n cheb_tail + dropped_cost) / (n sqrt(mu2)): a-priori bound
+                               on |K - K~|_F / |K|_F */
+    int s_k[HDF_MAX_L + 1]; /* kept radial rank per harmonic degree k (Sec. 3.4) */
+} hdf_info;
+
+/* ---------------------------------------------------------------- factorization ---- */
+
+/* Build K ~= U S U^T for the points x_dev (row-major n x d FP64, device) -- Algorithm 1,
+ * symmetric form (Remark 1).  Steps: centre and scale to |x'| <= 1/2 (Sec. 3.3 footnote),
+ * Chebyshev coefficients and degree (Sec. 3.3, Remark 3), radial cores (Eq. rdef,
+ * App. A), radial-basis QR (Eq. svd), eigendecomposition and truncation (Sec. 3.4,
+ * Remark 2), harmonics times radial factors into U (Algorithm 1's inner loops).
+ * opt may be NULL.  *out receives a new factor on HDF_OK or HDF_ETOL_UNREACHABLE (the
+ * latter still returns a usable factor at p = p_max); otherwise *out is set to NULL.
+ * Synchronises the stream. */
+hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel,
+                     double lengthscale, double tol, hdf_precision prec,
+                     const hdf_options* opt, hdf_stream stream, hdf_factor** out);
+
+/* Y = K~ V = U (S (U^T V)) (Sec. 3.6: O(n r) per column).  V_dev and Y_dev are column-major
+ * n x ncols blocks (leading dimensions ldv, ldy >= n) of the factor's bulk type; they must
+ * not overlap.  1 <= ncols <= 1024.  Asynchronous on the stream. */
+hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
+                      void* Y_dev, int64_t ldy, hdf_stream stream);
+
+/* X = (lambda I + K~)^{-1} B (Eq. opt with the Woodbury identity of Sec. 1), followed by
+ * refine_steps steps of iterative refinement X += (lambda I + K~)^{-1} (B - lambda X - K~ X).
+ * lambda > 0.  The r x r core lambda S^{-1} + U^T U is factored on the host in FP64 (LU
+ * with partial pivoting) and cached per lambda; rank r must be <= 4096.  Synchronises. */
+hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev, int64_t ldb, int ncols,
+                     void* X_dev, int64_t ldx, int refine_steps, hdf_stream stream);
+
+/* Metadata of a factor (sizes, scaling, degree, ranks, error budget and bound). */
+hdf_status hdf_factor_info(const hdf_factor* f, hdf_info* info);
+
+/* Device pointers to U (row-major n x ldu, bulk type) and S (rank entries, bulk type). */
+hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void** S_dev);
+
+/* Copy U (n x rank, row-major, bulk type, packed: leading dimension rank) and S (FP64) to
+ * host buffers the caller allocated.  Either pointer may be NULL.  Synchronises. */
+hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host);
+
+/* Release a factor (NULL is ignored). */
+void hdf_free(hdf_factor* f);
+
+/* --------------------------------------------------------- host planner (no GPU) ---- */
+/* These run on the host only and need no device; they expose the planning steps so
+ * that they can be checked on their own. */
+
+/* Number of DCT nodes used for the Chebyshev coefficients: 4 (p_max + 2). */
+int hdf_cheb_nodes(int p_max);
+
+/* a[0..M-1]: Chebyshev coefficients of kappa(|r|) = k(two_r |r|; l) on [-1, 1] by the DCT
+ * at M first-kind nodes (Sec. 3.3, Eq. chebtrunc); odd entries are exactly 0. */
+hdf_status hdf_cheb_coeffs(hdf_kernel kernel, double lengthscale, double two_r, int M,
+                           double* a_host);
+
+/* Smallest even p <= p_max whose estimated tail sum_{p<i<M}|a_i| + sum_{i>=M/2}|a_i| is
+ * <= budget (Remark 3).  *p gets the degree, *tail its tail, *reached 0 if capped. */
+hdf_status hdf_choose_degree(const double* a_host, int M, double budget, int p_max,
+                             int* p, double* tail, int* reached);
+
+/* Radial cores Gamma_k, k = 0..p/2, of r^(k)(a, b) (Eq. rdef) in the basis
+ * rho^(k mod 2) T_l(8 rho^2 - 1), l < nb_k, with nb_k = p/2 + 1 (even k) or p/2 (odd k).
+ * cores_host receives the row-major nb_k x nb_k blocks one after another (total
+ * sum_k nb_k^2 doubles; pass NULL to query the size in *count). */
+hdf_status hdf_radial_cores(const double* a_host, int p, int d, double* cores_host,
+                            int64_t* count);
+
+/* ----------------------------------------------------------------------- errors ---- */
+const char* hdf_status_string(hdf_status s);
+const char* hdf_last_error(void);           /* thread-local message of the last failure */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDF_H */

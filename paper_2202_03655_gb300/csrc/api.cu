@@ -1,0 +1,729 @@
+// C ABI of the HDF library: orchestration of the device kernels and the host planner.
+// Declarations and argument contracts are in include/hdf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hdf.h"
+#include "hdf_kernels.cuh"
+#include "planner.h"
+
+using namespace hdf;
+
+static thread_local std::string g_err;
+
+static hdf_status fail(hdf_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define HDF_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            return fail(HDF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+        }                                                                                \
+    } while (0)
+
+// Owns one device allocation.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t b) {
+        if (p) { cudaFree(p); p = nullptr; }
+        bytes = b;
+        return b ? cudaMalloc(&p, b) : cudaSuccess;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct hdf_factor {
+    hdf_info info{};
+    int kernel = 0;
+    double ell = 0, tol = 0;
+    int prec = 0;
+    size_t esz = 8;                 // bytes per bulk element
+    DevBuf U, S;                    // U n x ldu, S rank (bulk type)
+    std::vector<double> S_host;
+    // solve core (lambda S^-1 + U^T U), LU factors on the host
+    std::vector<double> G;
+    double core_lambda = -1.0;
+    std::vector<double> LU;
+    std::vector<int> piv;
+};
+
+// --------------------------------------------------------------------- helpers
+static int grid_for(int64_t work, int per_block, int cap) {
+    int64_t g = (work + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+template <typename T>
+static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d, const dev::Center& cen,
+                               double inv2R, int L, const std::vector<std::vector<double>>& Qmat,
+                               const std::vector<int>& nbv, const std::vector<int>& mv,
+                               const std::vector<std::vector<double>>& Wk, const std::vector<int>& sk,
+                               cudaStream_t st);
+
+extern "C" {
+
+const char* hdf_status_string(hdf_status s) {
+    switch (s) {
+        case HDF_OK: return "ok";
+        case HDF_EINVAL: return "invalid argument";
+        case HDF_ENOMEM: return "out of memory";
+        case HDF_ECUDA: return "CUDA error";
+        case HDF_ETOL_UNREACHABLE: return "tolerance unreachable at the degree cap";
+        case HDF_ENOTFINITE: return "non-finite input";
+        case HDF_ESINGULAR: return "singular core";
+        case HDF_ETIMEOUT: return "device wait timed out";
+        case HDF_ETOOBIG: return "size exceeds a documented limit";
+    }
+    return "unknown status";
+}
+
+const char* hdf_last_error(void) { return g_err.c_str(); }
+
+int hdf_cheb_nodes(int p_max) { return cheb_nodes(p_max); }
+
+hdf_status hdf_cheb_coeffs(hdf_kernel kernel, double lengthscale, double two_r, int M, double* a_host) {
+    if (kernel < 0 || kernel > 3 || !(lengthscale > 0) || !(two_r >= 0) || M < 2 || !a_host)
+        return fail(HDF_EINVAL, "hdf_cheb_coeffs: bad argument");
+    cheb_coeffs(kernel, lengthscale, two_r, M, false, a_host);
+    return HDF_OK;
+}
+
+hdf_status hdf_choose_degree(const double* a_host, int M, double budget, int p_max, int* p, double* tail,
+                             int* reached) {
+    if (!a_host || M < 2 || p_max < 0 || !p || !tail || !reached)
+        return fail(HDF_EINVAL, "hdf_choose_degree: bad argument");
+    bool ok = false;
+    *p = choose_degree(a_host, M, budget, p_max, tail, &ok);
+    *reached = ok ? 1 : 0;
+    return HDF_OK;
+}
+
+hdf_status hdf_radial_cores(const double* a_host, int p, int d, double* cores_host, int64_t* count) {
+    if (!a_host || p < 0 || (p & 1) || d < 3 || d > HDF_MAX_D || p > 2 * HDF_MAX_L || !count)
+        return fail(HDF_EINVAL, "hdf_radial_cores: bad argument");
+    const int L = p / 2;
+    int64_t tot = 0;
+    for (int k = 0; k <= L; ++k) { const int nb = (k % 2 == 0) ? L + 1 : L; tot += (int64_t)nb * nb; }
+    *count = tot;
+    if (!cores_host) return HDF_OK;
+    std::vector<std::vector<double>> cores;
+    radial_cores(a_host, p, d, cores);
+    int64_t off = 0;
+    for (int k = 0; k <= L; ++k) {
+        std::memcpy(cores_host + off, cores[k].data(), cores[k].size() * sizeof(double));
+        off += (int64_t)cores[k].size();
+    }
+    return HDF_OK;
+}
+
+hdf_status hdf_factor_info(const hdf_factor* f, hdf_info* info) {
+    if (!f || !info) return fail(HDF_EINVAL, "hdf_factor_info: null argument");
+    *info = f->info;
+    return HDF_OK;
+}
+
+hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void** S_dev) {
+    if (!f) return fail(HDF_EINVAL, "hdf_factor_device: null factor");
+    if (U_dev) *U_dev = f->U.p;
+    if (S_dev) *S_dev = f->S.p;
+    return HDF_OK;
+}
+
+hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) {
+    if (!f) return fail(HDF_EINVAL, "hdf_factor_export: null factor");
+    const int64_t n = f->info.n, r = f->info.rank;
+    if (U_host && r > 0) {
+        HDF_CUDA(cudaMemcpy2D(U_host, r * f->esz, f->U.p, f->info.ldu * f->esz, r * f->esz, n,
+                              cudaMemcpyDeviceToHost));
+    }
+    if (S_host && r > 0) std::memcpy(S_host, f->S_host.data(), r * sizeof(double));
+    return HDF_OK;
+}
+
+void hdf_free(hdf_factor* f) { delete f; }
+
+// --------------------------------------------------------------------------- build
+hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, double lengthscale,
+                     double tol, hdf_precision prec, const hdf_options* opt, hdf_stream stream,
+                     hdf_factor** out) {
+    if (out) *out = nullptr;
+    if (!x_dev || !out || n < 1 || d < 3 || d > HDF_MAX_D || kernel < 0 || kernel > 3 ||
+        !(lengthscale > 0) || !(tol > 0 && tol < 1) || (prec != HDF_FP64 && prec != HDF_FP32))
+        return fail(HDF_EINVAL, "hdf_build: bad argument (need n>=1, 3<=d<=8, l>0, 0<tol<1)");
+    int p_max = 64;
+    double eta = 1.0;
+    if (opt) {
+        if (opt->p_max > 0) p_max = opt->p_max;
+        if (opt->eta > 0) eta = opt->eta;
+    }
+    if (p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, "hdf_build: p_max > 128");
+    p_max -= p_max % 2;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    // ---- A0: centre (mean) and radius (max norm), two-stage reductions
+    const int gsum = grid_for(n, 2048, 1024);
+    const int64_t chunk = (n + gsum - 1) / gsum;
+    DevBuf part;
+    HDF_CUDA(part.alloc(sizeof(double) * std::max<int64_t>(gsum * d, 2048)));
+    dev::k_sum_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)gsum * d);
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    dev::Center cen{};
+    for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int b = 0; b < gsum; ++b) s += hp[(size_t)b * d + j];
+        cen.c[j] = s / (double)n;
+        if (!std::isfinite(cen.c[j])) return fail(HDF_ENOTFINITE, "hdf_build: non-finite point coordinates");
+    }
+    dev::k_maxnorm_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, cen, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, gsum * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    double R2 = 0.0;
+    for (int b = 0; b < gsum; ++b) R2 = std::max(R2, hp[b]);
+    double R = std::sqrt(R2);
+    if (!std::isfinite(R)) return fail(HDF_ENOTFINITE, "hdf_build: non-finite point coordinates");
+    if (R == 0.0) R = 1.0;
+    const double inv2R = 1.0 / (2.0 * R);
+
+    // ---- mean-square kernel value on the strided subsample
+    const int m = (int)std::min<int64_t>(n, 2048);
+    dev::k_mu2_rows<<<m, 256, 0, st>>>(x_dev, n, d, m, kernel, lengthscale, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> mu_part(m);
+    HDF_CUDA(cudaMemcpyAsync(mu_part.data(), part.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    double mu2 = 0.0;
+    for (int t = 0; t < m; ++t) mu2 += mu_part[t];
+    mu2 /= (double)m * (double)m;
+
+    // ---- A1: Chebyshev coefficients and degree
+    const int M = cheb_nodes(p_max);
+    std::vector<double> a(M);
+    cheb_coeffs(kernel, lengthscale, 2.0 * R, M, false, a.data());
+    const double tail_budget = 0.5 * tol * std::sqrt(mu2);
+    const double drop_budget = 0.5 * eta * tol * (double)n * std::sqrt(mu2);
+    double tail = 0.0;
+    bool reached = false;
+    const int p = choose_degree(a.data(), M, tail_budget, p_max, &tail, &reached);
+    const int L = p / 2;
+
+    // ---- A2: radial cores
+    std::vector<std::vector<double>> cores;
+    radial_cores(a.data(), p, d, cores);
+
+    // ---- A3: Gram matrices of the radial basis (FP64 on the device)
+    const int nb0 = L + 1, nb1 = L;
+    const int npairs = nb0 * (nb0 + 1) / 2;
+    std::vector<uint16_t> pairs;
+    for (int l = 0; l < nb0; ++l)
+        for (int lp = l; lp < nb0; ++lp) { pairs.push_back((uint16_t)l); pairs.push_back((uint16_t)lp); }
+    const int ggram = grid_for(n, 4096, 2 * 152);
+    const int64_t gchunk = (n + ggram - 1) / ggram;
+    DevBuf dpairs, gpart, gsumd;
+    HDF_CUDA(dpairs.alloc(pairs.size() * sizeof(uint16_t)));
+    HDF_CUDA(gpart.alloc(sizeof(double) * (size_t)ggram * 2 * npairs));
+    HDF_CUDA(gsumd.alloc(sizeof(double) * 2 * npairs));
+    HDF_CUDA(cudaMemcpyAsync(dpairs.p, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+    const size_t gsm = sizeof(double) * (dev::kGramTile * (L + 1) + dev::kGramTile);
+    dev::k_radial_gram<<<ggram, 256, gsm, st>>>(x_dev, n, d, gchunk, cen, inv2R, L, dpairs.as<uint16_t>(),
+                                                 npairs, gpart.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    dev::k_reduce_cols<<<grid_for(2 * npairs, 256, 1 << 20), 256, 0, st>>>(gpart.as<double>(), ggram,
+                                                                          2 * npairs, gsumd.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> gram(2 * npairs);
+    HDF_CUDA(cudaMemcpyAsync(gram.data(), gsumd.p, gram.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+
+    // ---- A3 (host): factor of each parity's basis from its Gram: B = Q Rf, Rf = D^{1/2} V^T,
+    // keeping eigen-directions above a relative floor; Qmat = V D^{-1/2} maps B to Q.
+    std::vector<std::vector<double>> Rf(2), Qmat(2);
+    std::vector<int> nbv = {nb0, nb1}, mv = {0, 0};
+    for (int par = 0; par < 2; ++par) {
+        const int nb = nbv[par];
+        if (nb == 0) continue;
+        std::vector<double> Gm(nb * nb), w(nb), V(nb * nb);
+        int q = 0;
+        for (int l = 0; l < nb0; ++l)
+            for (int lp = l; lp < nb0; ++lp, ++q) {
+                if (l < nb && lp < nb) Gm[l * nb + lp] = Gm[lp * nb + l] = gram[(size_t)par * npairs + q];
+            }
+        sym_eig(nb, Gm.data(), w.data(), V.data());
+        double wmax = 0.0;
+        for (int l = 0; l < nb; ++l) wmax = std::max(wmax, w[l]);
+        const double floor_ = wmax * 1e-13 * nb;
+        std::vector<int> keep;
+        for (int l = 0; l < nb; ++l) if (w[l] > floor_) keep.push_back(l);
+        const int mk = (int)keep.size();
+        mv[par] = mk;
+        Rf[par].assign((size_t)mk * nb, 0.0);
+        Qmat[par].assign((size_t)nb * mk, 0.0);
+        for (int o = 0; o < mk; ++o) {
+            const double sq = std::sqrt(w[keep[o]]);
+            for (int l = 0; l < nb; ++l) {
+                Rf[par][(size_t)o * nb + l] = sq * V[l * nb + keep[o]];
+                Qmat[par][(size_t)l * mk + o] = V[l * nb + keep[o]] / sq;
+            }
+        }
+    }
+
+    // ---- A4: per-degree eigendecompositions G_k = Rf Gamma_k Rf^T and global truncation
+    const double area = sphere_area(d);
+    struct Item { double cost; int k, j; };
+    std::vector<Item> items;
+    std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
+    for (int k = 0; k <= L; ++k) {
+        const int par = k % 2, nb = nbv[par], mk = mv[par];
+        if (mk == 0 || nb == 0) continue;
+        const std::vector<double>& Gk = cores[k];
+        std::vector<double> T1((size_t)mk * nb, 0.0), Gm((size_t)mk * mk, 0.0);
+        for (int o = 0; o < mk; ++o)
+            for (int l = 0; l < nb; ++l) {
+                double s = 0.0;
+                for (int t = 0; t < nb; ++t) s += Rf[par][(size_t)o * nb + t] * Gk[(size_t)t * nb + l];
+                T1[(size_t)o * nb + l] = s;
+            }
+        for (int o = 0; o < mk; ++o)
+            for (int o2 = 0; o2 <= o; ++o2) {
+                double s = 0.0;
+                for (int l = 0; l < nb; ++l) s += T1[(size_t)o * nb + l] * Rf[par][(size_t)o2 * nb + l];
+                Gm[(size_t)o * mk + o2] = Gm[(size_t)o2 * mk + o] = s;
+            }
+        lam[k].resize(mk);
+        vec[k].resize((size_t)mk * mk);
+        sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
+        const double hk = (double)harmonic_count(k, d);
+        for (int j = 0; j < mk; ++j) items.push_back({std::fabs(lam[k][j]) * hk / area, k, j});
+    }
+    std::sort(items.begin(), items.end(), [](const Item& A, const Item& B) {
+        if (A.cost != B.cost) return A.cost < B.cost;
+        if (A.k != B.k) return A.k < B.k;
+        return A.j < B.j;
+    });
+    std::vector<std::vector<char>> dropped(L + 1);
+    for (int k = 0; k <= L; ++k) dropped[k].assign(lam[k].size(), 0);
+    double acc = 0.0;
+    for (const Item& it : items) {
+        if (acc + it.cost > drop_budget) break;
+        acc += it.cost;
+        dropped[it.k][it.j] = 1;
+    }
+    std::vector<int> sk(L + 1, 0);
+    std::vector<std::vector<double>> Wk(L + 1);     // mk x s_k, row-major, columns by decreasing |lambda|
+    std::vector<double> S_host;
+    std::vector<int64_t> hcount(L + 1);
+    int L_used = -1;
+    int64_t rank = 0, nH = 0;
+    for (int k = 0; k <= L; ++k) {
+        hcount[k] = harmonic_count(k, d);
+        std::vector<int> idx;
+        for (int j = 0; j < (int)lam[k].size(); ++j) if (!dropped[k][j]) idx.push_back(j);
+        std::sort(idx.begin(), idx.end(), [&](int A, int B) {
+            const double fa = std::fabs(lam[k][A]), fb = std::fabs(lam[k][B]);
+            if (fa != fb) return fa > fb;
+            return A < B;
+        });
+        sk[k] = (int)idx.size();
+        if (sk[k] == 0) continue;
+        L_used = k;
+        const int mk = mv[k % 2];
+        Wk[k].assign((size_t)mk * sk[k], 0.0);
+        for (int s = 0; s < sk[k]; ++s)
+            for (int o = 0; o < mk; ++o) Wk[k][(size_t)o * sk[k] + s] = vec[k][(size_t)o * mk + idx[s]];
+        rank += hcount[k] * sk[k];
+        nH += hcount[k];
+        for (int s = 0; s < sk[k]; ++s)
+            for (int64_t h = 0; h < hcount[k]; ++h) S_host.push_back(lam[k][idx[s]]);
+    }
+
+    hdf_factor* f = new hdf_factor();
+    f->kernel = kernel;
+    f->ell = lengthscale;
+    f->tol = tol;
+    f->prec = prec;
+    f->esz = (prec == HDF_FP64) ? 8 : 4;
+    hdf_info& I = f->info;
+    I.n = n;
+    I.d = d;
+    I.precision = prec;
+    I.p = p;
+    I.L = L;
+    I.reached = reached ? 1 : 0;
+    I.rank = rank;
+    I.nharm = nH;
+    for (int j = 0; j < d; ++j) I.center[j] = cen.c[j];
+    I.radius = R;
+    I.mu2 = mu2;
+    I.cheb_tail = tail;
+    I.tail_budget = tail_budget;
+    I.drop_budget = drop_budget;
+    I.dropped_cost = acc;
+    I.err_bound = ((double)n * tail + acc) / ((double)n * std::sqrt(mu2));
+    for (int k = 0; k <= std::min(L, HDF_MAX_L); ++k) I.s_k[k] = sk[k];
+    f->S_host = S_host;
+
+    hdf_status st_dev = (prec == HDF_FP64)
+        ? build_device<double>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st)
+        : build_device<float>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st);
+    if (st_dev != HDF_OK) { delete f; return st_dev; }
+    *out = f;
+    if (!reached) {
+        g_err = "hdf_build: tolerance not reached at p_max; factor built at the cap";
+        return HDF_ETOL_UNREACHABLE;
+    }
+    return HDF_OK;
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------------------------- matvec
+template <typename T>
+static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy,
+                           const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
+    const int64_t n = f->info.n, r = f->info.rank;
+    const T* U = f->U.as<T>();
+    if (r == 0) {
+        for (int j = 0; j < ncols; ++j) {
+            if (B) {
+                dev::k_axpby<T><<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(n, 1, beta, B + j * ldb, ldb, (T)0,
+                                                                          Y + j * ldy, ldy);
+            } else {
+                HDF_CUDA(cudaMemsetAsync(Y + j * ldy, 0, n * sizeof(T), st));
+            }
+        }
+        HDF_CUDA(cudaGetLastError());
+        return HDF_OK;
+    }
+    const int nchunk = grid_for(n, 8192, 256);
+    const int64_t chunk = (n + nchunk - 1) / nchunk;
+    DevBuf part, W;
+    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * dev::kCB * r));
+    HDF_CUDA(W.alloc(sizeof(T) * (size_t)r * dev::kCB));
+    for (int j0 = 0; j0 < ncols; j0 += dev::kCB) {
+        const int cg = std::min(dev::kCB, ncols - j0);
+        dim3 g1(nchunk, (unsigned)((r + 255) / 256));
+        dev::k_utv<T><<<g1, 256, 0, st>>>(U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, chunk, part.as<double>());
+        HDF_CUDA(cudaGetLastError());
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
+                                                                               S_scale, W.as<T>(), nullptr);
+        HDF_CUDA(cudaGetLastError());
+        dev::k_uw<T><<<grid_for(n * 32, 256, 152 * 16), 256, 0, st>>>(U, f->info.ldu, n, r, W.as<T>(), cg, alpha,
+                                                                      B ? B + j0 * ldb : nullptr, ldb, beta,
+                                                                      Y + j0 * ldy, ldy);
+        HDF_CUDA(cudaGetLastError());
+    }
+    return HDF_OK;
+}
+
+extern "C" hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols, void* Y_dev, int64_t ldy,
+                      hdf_stream stream) {
+    if (!f || !V_dev || !Y_dev || ncols < 1 || ncols > 1024 || ldv < f->info.n || ldy < f->info.n)
+        return fail(HDF_EINVAL, "hdf_matvec: bad argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (f->prec == HDF_FP64)
+        return matvec_t<double>(f, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy, f->S.as<double>(), 1.0,
+                                nullptr, 0, 0.0, st);
+    return matvec_t<float>(f, (const float*)V_dev, ldv, ncols, (float*)Y_dev, ldy, f->S.as<float>(), 1.0f,
+                           nullptr, 0, 0.0f, st);
+}
+
+// --------------------------------------------------------------------------- solve
+
+// Host LU with partial pivoting of the r x r core (row-major, in place).
+static bool lu_factor(int64_t r, std::vector<double>& A, std::vector<int>& piv) {
+    piv.resize(r);
+    for (int64_t k = 0; k < r; ++k) {
+        int64_t p = k;
+        double best = std::fabs(A[k * r + k]);
+        for (int64_t i = k + 1; i < r; ++i)
+            if (std::fabs(A[i * r + k]) > best) { best = std::fabs(A[i * r + k]); p = i; }
+        piv[k] = (int)p;
+        if (best == 0.0 || !std::isfinite(best)) return false;
+        if (p != k)
+            for (int64_t j = 0; j < r; ++j) std::swap(A[k * r + j], A[p * r + j]);
+        const double inv = 1.0 / A[k * r + k];
+        for (int64_t i = k + 1; i < r; ++i) {
+            double* Ai = &A[i * r];
+            const double l = Ai[k] * inv;
+            Ai[k] = l;
+            if (l == 0.0) continue;
+            const double* Ak = &A[k * r];
+            for (int64_t j = k + 1; j < r; ++j) Ai[j] -= l * Ak[j];
+        }
+    }
+    return true;
+}
+
+// Solve LU z = b in place for one column b (length r).
+static void lu_solve(int64_t r, const std::vector<double>& A, const std::vector<int>& piv, double* b) {
+    for (int64_t k = 0; k < r; ++k) if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+    for (int64_t i = 0; i < r; ++i) {
+        double s = b[i];
+        for (int64_t j = 0; j < i; ++j) s -= A[i * r + j] * b[j];
+        b[i] = s;
+    }
+    for (int64_t i = r - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int64_t j = i + 1; j < r; ++j) s -= A[i * r + j] * b[j];
+        b[i] = s / A[i * r + i];
+    }
+}
+
+// Xout = (lambda I + U S U^T)^{-1} Bin = (Bin - U C^{-1} U^T Bin) / lambda, C = lambda S^{-1} + U^T U.
+template <typename T>
+static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int64_t ldb, int ncols, T* Xout,
+                                 int64_t ldx, cudaStream_t st) {
+    const int64_t n = f->info.n, r = f->info.rank;
+    const T* U = f->U.as<T>();
+    if (r == 0) {
+        dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(1.0 / lambda), Bin, ldb,
+                                                                           (T)0, Xout, ldx);
+        HDF_CUDA(cudaGetLastError());
+        return HDF_OK;
+    }
+    const int nchunk = grid_for(n, 8192, 256);
+    const int64_t chunk = (n + nchunk - 1) / nchunk;
+    DevBuf part, Wd, Wt;
+    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * dev::kCB * r));
+    HDF_CUDA(Wd.alloc(sizeof(double) * (size_t)r * dev::kCB));
+    HDF_CUDA(Wt.alloc(sizeof(T) * (size_t)r * dev::kCB));
+    std::vector<double> z((size_t)r * dev::kCB), col(r);
+    std::vector<T> y((size_t)r * dev::kCB);
+    for (int j0 = 0; j0 < ncols; j0 += dev::kCB) {
+        const int cg = std::min(dev::kCB, ncols - j0);
+        dim3 g1(nchunk, (unsigned)((r + 255) / 256));
+        dev::k_utv<T><<<g1, 256, 0, st>>>(U, f->info.ldu, n, r, Bin + j0 * ldb, ldb, cg, chunk, part.as<double>());
+        HDF_CUDA(cudaGetLastError());
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
+                                                                               nullptr, nullptr, Wd.as<double>());
+        HDF_CUDA(cudaGetLastError());
+        HDF_CUDA(cudaMemcpyAsync(z.data(), Wd.p, sizeof(double) * r * cg, cudaMemcpyDeviceToHost, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < cg; ++j) {
+            for (int64_t a = 0; a < r; ++a) col[a] = z[a * cg + j];
+            lu_solve(r, f->LU, f->piv, col.data());
+            for (int64_t a = 0; a < r; ++a) y[a * cg + j] = (T)col[a];
+        }
+        HDF_CUDA(cudaMemcpyAsync(Wt.p, y.data(), sizeof(T) * r * cg, cudaMemcpyHostToDevice, st));
+        dev::k_uw<T><<<grid_for(n * 32, 256, 152 * 16), 256, 0, st>>>(U, f->info.ldu, n, r, Wt.as<T>(), cg,
+                                                                      (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
+                                                                      (T)(1.0 / lambda), Xout + j0 * ldx, ldx);
+        HDF_CUDA(cudaGetLastError());
+        HDF_CUDA(cudaStreamSynchronize(st));
+    }
+    return HDF_OK;
+}
+
+template <typename T>
+static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb, int ncols, T* X, int64_t ldx,
+                          int refine, cudaStream_t st) {
+    const int64_t n = f->info.n, r = f->info.rank;
+    if (r > 4096) return fail(HDF_ETOOBIG, "hdf_solve: rank > 4096");
+    if (r > 0 && f->G.empty()) {
+        DevBuf Gd;
+        HDF_CUDA(Gd.alloc(sizeof(double) * (size_t)r * r));
+        const unsigned nt = (unsigned)((r + 63) / 64);
+        dev::k_gram<T><<<dim3(nt, nt), 256, 0, st>>>(f->U.as<T>(), f->info.ldu, n, r, Gd.as<double>());
+        HDF_CUDA(cudaGetLastError());
+        f->G.resize((size_t)r * r);
+        HDF_CUDA(cudaMemcpyAsync(f->G.data(), Gd.p, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+    }
+    if (r > 0 && f->core_lambda != lambda) {
+        f->LU = f->G;
+        for (int64_t a = 0; a < r; ++a) f->LU[a * r + a] += lambda / f->S_host[a];
+        if (!lu_factor(r, f->LU, f->piv)) {
+            f->core_lambda = -1.0;
+            return fail(HDF_ESINGULAR, "hdf_solve: singular core lambda S^-1 + U^T U");
+        }
+        f->core_lambda = lambda;
+    }
+    hdf_status s = woodbury_apply<T>(f, lambda, B, ldb, ncols, X, ldx, st);
+    if (s != HDF_OK || refine <= 0) return s;
+    DevBuf Rb, KX, dX;
+    HDF_CUDA(Rb.alloc(sizeof(T) * (size_t)n * ncols));
+    HDF_CUDA(KX.alloc(sizeof(T) * (size_t)n * ncols));
+    HDF_CUDA(dX.alloc(sizeof(T) * (size_t)n * ncols));
+    for (int it = 0; it < refine; ++it) {
+        // Rb = B - lambda X - K~ X
+        s = matvec_t<T>(f, X, ldx, ncols, KX.as<T>(), n, f->S.as<T>(), (T)1, nullptr, 0, (T)0, st);
+        if (s != HDF_OK) return s;
+        for (int j = 0; j < ncols; ++j)
+            HDF_CUDA(cudaMemcpyAsync(Rb.as<T>() + j * n, B + j * ldb, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(-lambda), X, ldx, (T)1,
+                                                                           Rb.as<T>(), n);
+        dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(-1), KX.as<T>(), n, (T)1,
+                                                                           Rb.as<T>(), n);
+        HDF_CUDA(cudaGetLastError());
+        s = woodbury_apply<T>(f, lambda, Rb.as<T>(), n, ncols, dX.as<T>(), n, st);
+        if (s != HDF_OK) return s;
+        dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)1, dX.as<T>(), n, (T)1, X,
+                                                                           ldx);
+        HDF_CUDA(cudaGetLastError());
+    }
+    HDF_CUDA(cudaStreamSynchronize(st));
+    return HDF_OK;
+}
+
+extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev, int64_t ldb, int ncols,
+                                void* X_dev, int64_t ldx, int refine_steps, hdf_stream stream) {
+    if (!f || !B_dev || !X_dev || ncols < 1 || ncols > 1024 || !(lambda > 0) || ldb < f->info.n ||
+        ldx < f->info.n || refine_steps < 0)
+        return fail(HDF_EINVAL, "hdf_solve: bad argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (f->prec == HDF_FP64)
+        return solve_t<double>(f, lambda, (const double*)B_dev, ldb, ncols, (double*)X_dev, ldx, refine_steps, st);
+    return solve_t<float>(f, lambda, (const float*)B_dev, ldb, ncols, (float*)X_dev, ldx, refine_steps, st);
+}
+
+// ---------------------------------------------------------- device part of build
+template <typename T>
+static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d, const dev::Center& cen,
+                               double inv2R, int L, const std::vector<std::vector<double>>& Qmat,
+                               const std::vector<int>& nbv, const std::vector<int>& mv,
+                               const std::vector<std::vector<double>>& Wk, const std::vector<int>& sk,
+                               cudaStream_t st) {
+    hdf_info& I = f->info;
+    const int64_t r = I.rank;
+    const int vw = (sizeof(T) == 4) ? 4 : 2;
+    I.ldu = std::max<int64_t>(vw, ((r + vw - 1) / vw) * vw);
+    // S on the device
+    {
+        std::vector<T> Sd(I.ldu, (T)0);
+        for (int64_t a = 0; a < r; ++a) Sd[a] = (T)f->S_host[a];
+        HDF_CUDA(f->S.alloc(sizeof(T) * I.ldu));
+        HDF_CUDA(cudaMemcpyAsync(f->S.p, Sd.data(), sizeof(T) * I.ldu, cudaMemcpyHostToDevice, st));
+    }
+    const size_t ubytes = sizeof(T) * (size_t)n * (size_t)I.ldu;
+    if (f->U.alloc(ubytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HDF_ENOMEM, "hdf_build: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
+    }
+    if (r == 0) { HDF_CUDA(cudaStreamSynchronize(st)); return HDF_OK; }
+
+    int L_used = 0;
+    for (int k = 0; k <= L; ++k) if (sk[k] > 0) L_used = k;
+    // F columns: (k, s) for kept pairs, k ascending
+    std::vector<int> fbase(L + 2, 0);
+    for (int k = 0; k <= L; ++k) fbase[k + 1] = fbase[k] + sk[k];
+    const int nF = fbase[L + 1];
+    const int mmax = std::max(mv[0], mv[1]);
+    std::vector<T> Wt((size_t)std::max(1, mmax) * nF, (T)0);
+    std::vector<uint8_t> colpar(nF);
+    for (int k = 0; k <= L; ++k)
+        for (int s = 0; s < sk[k]; ++s) {
+            const int col = fbase[k] + s, mk = mv[k % 2];
+            colpar[col] = (uint8_t)(k % 2);
+            for (int o = 0; o < mk; ++o) Wt[(size_t)o * nF + col] = (T)Wk[k][(size_t)o * sk[k] + s];
+        }
+    // harmonic tables and chains for degrees <= L_used
+    HarmonicTables ht;
+    harmonic_tables(d, L_used, ht);
+    std::vector<int16_t> chains;
+    std::vector<int64_t> hbase(L + 2, 0);
+    for (int k = 0; k <= L; ++k) {
+        hbase[k + 1] = hbase[k];
+        if (sk[k] == 0) continue;
+        append_chains(k, d, L_used, chains);
+        hbase[k + 1] += ht.count[k];
+    }
+    const int64_t nH = hbase[L + 1];
+    if (nH >= (1 << 20) || nF >= 4095) return fail(HDF_ETOOBIG, "hdf_build: too many harmonics or radial columns");
+    // column descriptors
+    std::vector<uint32_t> desc(I.ldu);
+    {
+        int64_t col = 0;
+        for (int k = 0; k <= L; ++k)
+            for (int s = 0; s < sk[k]; ++s)
+                for (int64_t h = 0; h < ht.count[k] * (sk[k] > 0); ++h)
+                    desc[col++] = ((uint32_t)(fbase[k] + s) << 20) | (uint32_t)(hbase[k] + h);
+        for (; col < I.ldu; ++col) desc[col] = ((uint32_t)nF << 20);
+    }
+    std::vector<T> cA(ht.coefA.size()), cB(ht.coefB.size());
+    for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)ht.coefA[q]; cB[q] = (T)ht.coefB[q]; }
+
+    // upload
+    DevBuf dQ0, dQ1, dW, dpar, dF, dchains, ddesc, dA, dB;
+    const int nb0 = nbv[0], nb1 = nbv[1], m0 = mv[0], m1 = mv[1];
+    HDF_CUDA(dQ0.alloc(sizeof(double) * std::max<size_t>(1, Qmat[0].size())));
+    HDF_CUDA(dQ1.alloc(sizeof(double) * std::max<size_t>(1, Qmat[1].size())));
+    HDF_CUDA(dW.alloc(sizeof(T) * Wt.size()));
+    HDF_CUDA(dpar.alloc(colpar.size()));
+    HDF_CUDA(dchains.alloc(sizeof(int16_t) * chains.size()));
+    HDF_CUDA(ddesc.alloc(sizeof(uint32_t) * desc.size()));
+    HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
+    HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
+    const int64_t ldF = nF;
+    if (dF.alloc(sizeof(T) * (size_t)n * ldF) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HDF_ENOMEM, "hdf_build: cannot allocate the radial factor buffer");
+    }
+    if (!Qmat[0].empty()) HDF_CUDA(cudaMemcpyAsync(dQ0.p, Qmat[0].data(), sizeof(double) * Qmat[0].size(), cudaMemcpyHostToDevice, st));
+    if (!Qmat[1].empty()) HDF_CUDA(cudaMemcpyAsync(dQ1.p, Qmat[1].data(), sizeof(double) * Qmat[1].size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dW.p, Wt.data(), sizeof(T) * Wt.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dpar.p, colpar.data(), colpar.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dchains.p, chains.data(), sizeof(int16_t) * chains.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(ddesc.p, desc.data(), sizeof(uint32_t) * desc.size(), cudaMemcpyHostToDevice, st));
+    if (!cA.empty()) {
+        HDF_CUDA(cudaMemcpyAsync(dA.p, cA.data(), sizeof(T) * cA.size(), cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaMemcpyAsync(dB.p, cB.data(), sizeof(T) * cB.size(), cudaMemcpyHostToDevice, st));
+    }
+
+    // A5a: radial factors F
+    {
+        const size_t sm = sizeof(double) * (dev::kFTile * (L + 1) + dev::kFTile) + sizeof(T) * (m0 + m1) * dev::kFTile;
+        if (sm > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
+        HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int grid = grid_for((n + dev::kFTile - 1) / dev::kFTile, 1, 152 * 8);
+        dev::k_radial_F<T><<<grid, 256, sm, st>>>(x, n, d, cen, inv2R, L, dQ0.as<double>(), nb0, m0,
+                                                  dQ1.as<double>(), nb1, m1, dW.as<T>(), dpar.as<uint8_t>(), nF,
+                                                  dF.as<T>(), ldF);
+        HDF_CUDA(cudaGetLastError());
+    }
+    // A5b: harmonics and U
+    {
+        dev::UWParams P{};
+        P.x = x; P.n = n; P.d = d; P.c = cen; P.inv2R = inv2R;
+        P.L = L_used; P.tri = ht.tri;
+        P.chains = dchains.as<int16_t>(); P.nH = (int)nH;
+        P.desc = ddesc.as<uint32_t>(); P.nF = nF;
+        P.F = dF.p; P.ldF = ldF;
+        P.U = f->U.p; P.ldU = I.ldu;
+        P.coefA = dA.p; P.coefB = dB.p;
+        const int levels = d - 2;
+        int per_warp = levels * ht.tri + 2 * L_used + 1 + (int)nH + nF + 1;
+        per_warp = (per_warp + 3) & ~3;     // keep 16-byte alignment of each warp's area
+        P.per_warp = per_warp;
+        const size_t fixed = sizeof(T) * 2 * levels * ht.tri;
+        const size_t budget = 200 * 1024;
+        int warps = 8;
+        while (warps > 1 && fixed + sizeof(T) * (size_t)warps * per_warp > budget) warps >>= 1;
+        const size_t sm = fixed + sizeof(T) * (size_t)warps * per_warp;
+        if (sm > budget) return fail(HDF_ETOOBIG, "hdf_build: harmonic tables exceed shared memory");
+        HDF_CUDA(cudaFuncSetAttribute(dev::k_uwriter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int occ = 0;
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_uwriter<T>, warps * 32, sm));
+        int nsm = 0, dv = 0;
+        HDF_CUDA(cudaGetDevice(&dv));
+        HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+        const int grid = std::max(1, std::min<int>(nsm * std::max(occ, 1), (int)((n + warps - 1) / warps)));
+        dev::k_uwriter<T><<<grid, warps * 32, sm, st>>>(P);
+        HDF_CUDA(cudaGetLastError());
+    }
+    HDF_CUDA(cudaStreamSynchronize(st));
+    return HDF_OK;
+}

@@ -1,0 +1,298 @@
+// Host-side planning of the HDF factorization (FP64).  See planner.h.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+
+namespace hdf {
+
+// ------------------------------------------------------------------------- kernels
+double kernel_value(int kernel, double r, double ell) {
+    const double z = std::fabs(r) / ell;
+    switch (kernel) {
+        case 0: return std::exp(-0.5 * z * z);
+        case 1: return 1.0 / (1.0 + z * z);
+        case 2: { const double s = std::sqrt(3.0) * z; return (1.0 + s) * std::exp(-s); }
+        case 3: { const double s = std::sqrt(5.0) * z; return (1.0 + s + s * s / 3.0) * std::exp(-s); }
+    }
+    return NAN;
+}
+
+double kernel_dz(int kernel, double z) {
+    switch (kernel) {
+        case 0: return -z * std::exp(-0.5 * z * z);
+        case 1: { const double q = 1.0 + z * z; return -2.0 * z / (q * q); }
+        case 2: return -3.0 * z * std::exp(-std::sqrt(3.0) * z);
+        case 3: { const double s = std::sqrt(5.0) * z; return -(5.0 / 3.0) * z * (1.0 + s) * std::exp(-s); }
+    }
+    return NAN;
+}
+
+double kernel_dell(int kernel, double r, double ell) {
+    const double z = std::fabs(r) / ell;
+    return kernel_dz(kernel, z) * (-z / ell);
+}
+
+// ----------------------------------------------------------------------- Chebyshev
+int cheb_nodes(int p_max) { return 4 * (p_max + 2); }
+
+void cheb_coeffs(int kernel, double ell, double two_r, int M, bool dell, double* a) {
+    std::vector<double> th(M), v(M);
+    for (int j = 0; j < M; ++j) {
+        th[j] = kPi * (j + 0.5) / M;
+        const double r = std::fabs(std::cos(th[j]));
+        v[j] = dell ? kernel_dell(kernel, two_r * r, ell) : kernel_value(kernel, two_r * r, ell);
+    }
+    for (int i = 0; i < M; ++i) {
+        if (i & 1) { a[i] = 0.0; continue; }
+        double s = 0.0;
+        for (int j = 0; j < M; ++j) s += std::cos(i * th[j]) * v[j];
+        a[i] = (2.0 / M) * s;
+    }
+    a[0] *= 0.5;
+}
+
+void tail_sums(const double* a, int M, std::vector<double>& tails) {
+    tails.assign(M, 0.0);
+    double guard = 0.0;
+    for (int i = M / 2; i < M; ++i) guard += std::fabs(a[i]);
+    double acc = 0.0;                       // sum_{i > p}
+    for (int p = M - 1; p >= 0; --p) {
+        tails[p] = acc + guard;
+        acc += std::fabs(a[p]);
+    }
+}
+
+int choose_degree(const double* a, int M, double budget, int p_max, double* tail, bool* reached) {
+    std::vector<double> tails;
+    tail_sums(a, M, tails);
+    p_max -= p_max % 2;
+    for (int p = 0; p <= p_max && p < M; p += 2) {
+        if (tails[p] <= budget) { *tail = tails[p]; *reached = true; return p; }
+    }
+    *tail = tails[std::min(p_max, M - 1)];
+    *reached = false;
+    return p_max;
+}
+
+// ------------------------------------------------------------------ sphere, counts
+double sphere_area(int d) { return 2.0 * std::pow(kPi, 0.5 * d) / std::tgamma(0.5 * d); }
+
+static int64_t binom(int64_t n, int64_t k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int64_t i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+int64_t harmonic_count(int k, int d) { return binom(k + d - 1, k) - binom(k + d - 3, k - 2); }
+
+// -------------------------------------------------------------- symmetric eigen
+void sym_eig(int n, double* A, double* w, double* V) {
+    for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int p = 0; p < n; ++p) {
+            tot += A[p * n + p] * A[p * n + p];
+            for (int q = p + 1; q < n; ++q) off += 2.0 * A[p * n + q] * A[p * n + q];
+        }
+        if (off <= 1e-32 * (tot + off) || off == 0.0) break;
+        for (int p = 0; p < n; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[p * n + p], aqq = A[q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {          // A <- A J
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {          // A <- J^T A
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                A[p * n + q] = A[q * n + p] = 0.0;
+                for (int k = 0; k < n; ++k) {          // V <- V J
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+void gauss_gegenbauer(int N, double lam, double* t, double* w) {
+    // Jacobi matrix of the monic Gegenbauer recurrence p_{j+1} = t p_j - b_j p_{j-1},
+    // b_j = j (j + 2 lam - 1) / (4 (j + lam)(j + lam - 1)); nodes = eigenvalues,
+    // weights = mu0 * (first eigenvector component)^2 (Golub-Welsch).
+    std::vector<double> J(N * N, 0.0), V(N * N), ev(N);
+    for (int j = 1; j < N; ++j) {
+        const double b = j * (j + 2.0 * lam - 1.0) / (4.0 * (j + lam) * (j + lam - 1.0));
+        J[(j - 1) * N + j] = J[j * N + j - 1] = std::sqrt(b);
+    }
+    sym_eig(N, J.data(), ev.data(), V.data());
+    const double mu0 = std::exp(0.5 * std::log(kPi) + std::lgamma(lam + 0.5) - std::lgamma(lam + 1.0));
+    std::vector<int> idx(N);
+    for (int i = 0; i < N; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+    for (int i = 0; i < N; ++i) {
+        t[i] = ev[idx[i]];
+        w[i] = mu0 * V[idx[i]] * V[idx[i]];     // row 0, column idx[i]
+    }
+}
+
+// ------------------------------------------------------------------- radial cores
+// F(s) = sum_q f_q T_q(2s - 1), f_q = a_{2q} (T_{2q}(r) = T_q(2 r^2 - 1)).  By Rodrigues'
+// formula and k integrations by parts, the Gegenbauer coefficient of F(a^2+b^2-2abt) times
+// the addition-theorem normaliser Z_k is
+//   r^(k)(a,b) = (-1)^k |S^{d-1}| Gamma(alpha+1) / (sqrt(pi) Gamma(k+alpha+1/2))
+//                (ab)^k int_{-1}^{1} F^(k)(a^2+b^2-2abt) (1-t^2)^(k+alpha-1/2) dt,
+// the integrand being a polynomial of degree L-k in t: Gauss-Gegenbauer with parameter
+// k+alpha and (L-k)/2+2 nodes is exact.  r^(k) is then interpolated at first-kind
+// Chebyshev nodes in u = 8 rho^2 - 1 and converted to Chebyshev coefficients (DCT).
+static void cheb_derivative(const std::vector<double>& c, std::vector<double>& dc, double scale) {
+    const int N = (int)c.size() - 1;        // degree
+    if (N <= 0) { dc.assign(1, 0.0); return; }
+    std::vector<double> e(N + 2, 0.0);
+    for (int q = N; q >= 1; --q) e[q - 1] = e[q + 1] + 2.0 * q * c[q];
+    e[0] *= 0.5;
+    dc.assign(N, 0.0);
+    for (int q = 0; q < N; ++q) dc[q] = scale * e[q];
+}
+
+static double clenshaw(const std::vector<double>& c, double u) {
+    double b1 = 0.0, b2 = 0.0;
+    for (int q = (int)c.size() - 1; q >= 1; --q) {
+        const double b0 = 2.0 * u * b1 - b2 + c[q];
+        b2 = b1;
+        b1 = b0;
+    }
+    return u * b1 - b2 + c[0];
+}
+
+void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out) {
+    const int L = p / 2;
+    const double alpha = 0.5 * d - 1.0;
+    const double area = sphere_area(d);
+    std::vector<double> Fk(L + 1);
+    for (int q = 0; q <= L; ++q) Fk[q] = a[2 * q];
+    out.assign(L + 1, std::vector<double>());
+    for (int k = 0; k <= L; ++k) {
+        if (k > 0) {
+            std::vector<double> tmp;
+            cheb_derivative(Fk, tmp, 2.0);   // d/ds = 2 d/du
+            Fk.swap(tmp);
+        }
+        const int nb = (k % 2 == 0) ? L + 1 : L;
+        if (nb == 0) continue;
+        const int Nq = (L - k) / 2 + 2;
+        std::vector<double> tq(Nq), wq(Nq);
+        gauss_gegenbauer(Nq, k + alpha, tq.data(), wq.data());
+        const double lpref = std::log(area) + std::lgamma(alpha + 1.0) - 0.5 * std::log(kPi)
+                             - std::lgamma(k + alpha + 0.5);
+        const double pref = ((k & 1) ? -1.0 : 1.0) * std::exp(lpref);
+        std::vector<double> u(nb), rho(nb);
+        for (int j = 0; j < nb; ++j) {
+            u[j] = std::cos(kPi * (j + 0.5) / nb);
+            rho[j] = std::sqrt((u[j] + 1.0) / 8.0);
+        }
+        std::vector<double> Vv(nb * nb);
+        for (int i = 0; i < nb; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                const double ab = rho[i] * rho[j];
+                const double s0 = rho[i] * rho[i] + rho[j] * rho[j];
+                double integ = 0.0;
+                for (int q = 0; q < Nq; ++q) integ += wq[q] * clenshaw(Fk, 2.0 * (s0 - 2.0 * ab * tq[q]) - 1.0);
+                const double v = pref * std::pow(ab, (double)(k - (k & 1))) * integ;
+                Vv[i * nb + j] = Vv[j * nb + i] = v;
+            }
+        }
+        // Gamma = D V D^T with D[l][j] = (2 - delta_l0)/nb cos(l pi (j+1/2)/nb)
+        std::vector<double> D(nb * nb), T(nb * nb, 0.0), G(nb * nb, 0.0);
+        for (int l = 0; l < nb; ++l)
+            for (int j = 0; j < nb; ++j)
+                D[l * nb + j] = (l == 0 ? 1.0 : 2.0) / nb * std::cos(l * kPi * (j + 0.5) / nb);
+        for (int l = 0; l < nb; ++l)
+            for (int j = 0; j < nb; ++j) {
+                double s = 0.0;
+                for (int m = 0; m < nb; ++m) s += D[l * nb + m] * Vv[m * nb + j];
+                T[l * nb + j] = s;
+            }
+        for (int l = 0; l < nb; ++l)
+            for (int m = 0; m < nb; ++m) {
+                double s = 0.0;
+                for (int j = 0; j < nb; ++j) s += T[l * nb + j] * D[m * nb + j];
+                G[l * nb + m] = s;
+            }
+        for (int l = 0; l < nb; ++l)
+            for (int m = 0; m < l; ++m) G[l * nb + m] = G[m * nb + l] = 0.5 * (G[l * nb + m] + G[m * nb + l]);
+        out[k].swap(G);
+    }
+}
+
+// --------------------------------------------------------------- harmonic tables
+void harmonic_tables(int d, int L, HarmonicTables& t) {
+    t.d = d;
+    t.L = L;
+    t.tri = (L + 1) * (L + 2) / 2;
+    const int levels = d - 2;
+    t.coefA.assign((size_t)levels * t.tri, 0.0);
+    t.coefB.assign((size_t)levels * t.tri, 0.0);
+    for (int j = 0; j < levels; ++j) {
+        const double alpha_j = 0.5 * (d - j - 2);
+        for (int mu = 0; mu <= L; ++mu) {
+            const double lam = mu + alpha_j;
+            auto log_h = [&](int n) {       // log of the Gegenbauer norm h_n^lam
+                return std::log(kPi) + (1.0 - 2.0 * lam) * std::log(2.0) + std::lgamma(n + 2.0 * lam)
+                       - std::lgamma(n + 1.0) - std::log(n + lam) - 2.0 * std::lgamma(lam);
+            };
+            double* A = &t.coefA[(size_t)j * t.tri + tri_index(L, mu, 0)];
+            double* B = &t.coefB[(size_t)j * t.tri + tri_index(L, mu, 0)];
+            const int nmax = L - mu;
+            A[0] = std::exp(-0.5 * log_h(0));
+            if (nmax >= 1) A[1] = 2.0 * lam * std::exp(-0.5 * log_h(1));
+            for (int n = 2; n <= nmax; ++n) {
+                const double r1 = std::exp(0.5 * (log_h(n - 1) - log_h(n)));   // s_n / s_{n-1}
+                const double r2 = std::exp(0.5 * (log_h(n - 2) - log_h(n)));   // s_n / s_{n-2}
+                A[n] = 2.0 * (n + lam - 1.0) / n * r1;
+                B[n] = (n + 2.0 * lam - 2.0) / n * r2;
+            }
+        }
+    }
+    t.count.resize(L + 1);
+    for (int k = 0; k <= L; ++k) t.count[k] = harmonic_count(k, d);
+}
+
+void append_chains(int k, int d, int L, std::vector<int16_t>& out) {
+    const int levels = d - 2;
+    std::vector<int> mu(d - 1);              // mu[0] = k, mu[1..d-2]
+    mu[0] = k;
+    std::function<void(int)> rec = [&](int pos) {
+        if (pos == d - 2) {                   // last entry may be negative
+            for (int m = -mu[pos - 1]; m <= mu[pos - 1]; ++m) {
+                mu[pos] = m;
+                for (int j = 0; j < levels; ++j) {
+                    const int mnext = std::abs(mu[j + 1]);
+                    out.push_back((int16_t)tri_index(L, mnext, mu[j] - mnext));
+                }
+                out.push_back((int16_t)m);
+            }
+            return;
+        }
+        for (int m = 0; m <= mu[pos - 1]; ++m) {
+            mu[pos] = m;
+            rec(pos + 1);
+        }
+    };
+    rec(1);
+}
+
+}  // namespace hdf

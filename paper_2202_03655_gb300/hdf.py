@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libhdf.so (argument marshalling only).
+
+Every step of the factorization runs inside the library; this module only converts
+torch tensors and numpy arrays to pointers, sizes and streams, and library status codes
+to exceptions.  If the library has not been built the first call raises: there is no
+fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhdf.so")
+
+KERNELS = {"gaussian": 0, "cauchy": 1, "matern32": 2, "matern52": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+STATUS = {0: "HDF_OK", 1: "HDF_EINVAL", 2: "HDF_ENOMEM", 3: "HDF_ECUDA", 4: "HDF_ETOL_UNREACHABLE",
+          5: "HDF_ENOTFINITE", 6: "HDF_ESINGULAR", 7: "HDF_ETIMEOUT", 8: "HDF_ETOOBIG"}
+HDF_OK, HDF_ETOL_UNREACHABLE = 0, 4
+MAX_D, MAX_L = 8, 64
+
+# Every exported entry point with its ctypes signature (include/hdf.h).
+_c_int, _c_i64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_pdbl = ctypes.POINTER(ctypes.c_double)
+
+
+class HdfOptions(ctypes.Structure):
+    _fields_ = [("p_max", _c_int), ("eta", _c_dbl), ("flags", _c_int)]
+
+
+class HdfInfo(ctypes.Structure):
+    _fields_ = [("n", _c_i64), ("d", _c_int), ("precision", _c_int), ("p", _c_int), ("L", _c_int),
+                ("reached", _c_int), ("rank", _c_i64), ("ldu", _c_i64), ("nharm", _c_i64),
+                ("center", _c_dbl * MAX_D), ("radius", _c_dbl), ("mu2", _c_dbl), ("cheb_tail", _c_dbl),
+                ("tail_budget", _c_dbl), ("drop_budget", _c_dbl), ("dropped_cost", _c_dbl),
+                ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1))]
+
+
+SIGNATURES = {
+    "hdf_build": (_c_int, [_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(HdfOptions),
+                           _vp, ctypes.POINTER(_vp)]),
+    "hdf_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
+    "hdf_solve": (_c_int, [_vp, _c_dbl, _vp, _c_i64, _c_int, _vp, _c_i64, _c_int, _vp]),
+    "hdf_factor_info": (_c_int, [_vp, ctypes.POINTER(HdfInfo)]),
+    "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "hdf_factor_export": (_c_int, [_vp, _vp, _pdbl]),
+    "hdf_free": (None, [_vp]),
+    "hdf_cheb_nodes": (_c_int, [_c_int]),
+    "hdf_cheb_coeffs": (_c_int, [_c_int, _c_dbl, _c_dbl, _c_int, _pdbl]),
+    "hdf_choose_degree": (_c_int, [_pdbl, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int), _pdbl,
+                                   ctypes.POINTER(_c_int)]),
+    "hdf_radial_cores": (_c_int, [_pdbl, _c_int, _c_int, _pdbl, ctypes.POINTER(_c_i64)]),
+    "hdf_status_string": (ctypes.c_char_p, [_c_int]),
+    "hdf_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class HdfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libhdf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, allow=(HDF_OK,)):
+    if status not in allow:
+        raise HdfError(status, lib().hdf_last_error().decode())
+    return status
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_pdbl)
+
+
+# ------------------------------------------------------------------ host planner calls
+
+def cheb_nodes(p_max):
+    return lib().hdf_cheb_nodes(int(p_max))
+
+
+def cheb_coeffs(kernel, lengthscale, two_r, M):
+    a = np.zeros(int(M))
+    _check(lib().hdf_cheb_coeffs(KERNELS[kernel], float(lengthscale), float(two_r), int(M), _dptr(a)))
+    return a
+
+
+def choose_degree(a, budget, p_max):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    p, tail, ok = _c_int(), _c_dbl(), _c_int()
+    _check(lib().hdf_choose_degree(_dptr(a), a.size, float(budget), int(p_max), ctypes.byref(p),
+                                   ctypes.byref(tail), ctypes.byref(ok)))
+    return p.value, tail.value, bool(ok.value)
+
+
+def radial_cores(a, p, d):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    cnt = _c_i64()
+    _check(lib().hdf_radial_cores(_dptr(a), int(p), int(d), None, ctypes.byref(cnt)))
+    buf = np.zeros(cnt.value)
+    _check(lib().hdf_radial_cores(_dptr(a), int(p), int(d), _dptr(buf), ctypes.byref(cnt)))
+    L = p // 2
+    out, off = [], 0
+    for k in range(L + 1):
+        nb = L + 1 if k % 2 == 0 else L
+        out.append(buf[off:off + nb * nb].reshape(nb, nb))
+        off += nb * nb
+    return out
+
+
+# --------------------------------------------------------------------- device calls
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+class Factor:
+    """K ~= U diag(S) U^T held by the library (U and S in device memory)."""
+
+    def __init__(self, handle, status):
+        self._h = handle
+        self.status = status
+        self.info = HdfInfo()
+        _check(lib().hdf_factor_info(self._h, ctypes.byref(self.info)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hdf_free(h)
+            self._h = None
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.info.precision == 0 else torch.float32
+
+    @property
+    def n(self):
+        return self.info.n
+
+    @property
+    def rank(self):
+        return self.info.rank
+
+    @property
+    def s_k(self):
+        return [self.info.s_k[k] for k in range(self.info.L + 1)]
+
+    def _block(self, V):
+        import torch
+        if not (V.is_cuda and V.dtype == self.dtype):
+            raise ValueError(f"expected a CUDA tensor of dtype {self.dtype}")
+        if V.dim() == 1:
+            V = V.reshape(-1, 1)
+        if V.shape[0] != self.n:
+            raise ValueError("first dimension must be n")
+        # column-major n x c: a (c, n) row-major tensor transposed
+        Vc = V.t().contiguous()
+        return Vc
+
+    def matvec(self, V, stream=None):
+        """Y = K~ V for V of shape (n,) or (n, c) on the device (Sec. 3.6)."""
+        import torch
+        vec = V.dim() == 1
+        Vc = self._block(V)
+        c = Vc.shape[0]
+        Yc = torch.empty_like(Vc)
+        _check(lib().hdf_matvec(self._h, _vp(Vc.data_ptr()), self.n, c, _vp(Yc.data_ptr()), self.n,
+                                _stream_handle(stream)))
+        Y = Yc.t()
+        return Y.reshape(-1) if vec else Y
+
+    def matvec_ptr(self, V_ptr, ldv, ncols, Y_ptr, ldy, stream=None):
+        """Raw-pointer form of matvec (column-major blocks already on the device)."""
+        _check(lib().hdf_matvec(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),
+                                _stream_handle(stream)))
+
+    def solve(self, lam, B, refine_steps=1, stream=None):
+        """X = (lam I + K~)^{-1} B (Eq. opt via Woodbury), with iterative refinement."""
+        import torch
+        vec = B.dim() == 1
+        Bc = self._block(B)
+        c = Bc.shape[0]
+        Xc = torch.empty_like(Bc)
+        _check(lib().hdf_solve(self._h, float(lam), _vp(Bc.data_ptr()), self.n, c, _vp(Xc.data_ptr()), self.n,
+                               int(refine_steps), _stream_handle(stream)))
+        X = Xc.t()
+        return X.reshape(-1) if vec else X
+
+    def device_U(self):
+        """(U pointer, ldu, S pointer) in device memory."""
+        u, s = _vp(), _vp()
+        _check(lib().hdf_factor_device(self._h, ctypes.byref(u), ctypes.byref(s)))
+        return u.value, self.info.ldu, s.value
+
+    def export(self):
+        """(U as numpy (n, rank), S as numpy (rank,) float64)."""
+        dt = np.float64 if self.info.precision == 0 else np.float32
+        U = np.zeros((self.n, self.rank), dtype=dt)
+        S = np.zeros(self.rank)
+        _check(lib().hdf_factor_export(self._h, _vp(U.ctypes.data), _dptr(S)))
+        return U, S
+
+
+def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, stream=None):
+    """Factor K(x, x) for points x (torch CUDA float64, shape (n, d)).
+
+    Returns a Factor; a factor capped at p_max (HDF_ETOL_UNREACHABLE) is returned with
+    ``status`` set and ``info.reached == 0``.
+    """
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.dim() == 2):
+        raise ValueError("x must be a CUDA float64 tensor of shape (n, d)")
+    x = x.contiguous()
+    opt = HdfOptions(int(p_max or 0), float(eta or 0.0), 0)
+    h = _vp()
+    st = lib().hdf_build(_vp(x.data_ptr()), x.shape[0], x.shape[1], KERNELS[kernel], float(lengthscale),
+                         float(tol), PRECISIONS[precision], ctypes.byref(opt), _stream_handle(stream),
+                         ctypes.byref(h))
+    _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
+    return Factor(h, st)
