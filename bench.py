@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the HDF hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the hot path over the benchmark workload with the points already in
+HBM: hdf_build (centre/scale, Chebyshev degree, radial cores, radial-basis Gram, eigen
+truncation, radial factors, harmonics + U) followed by K~ V for the workload's V block.
+
+Default workload (name in config.workload): mixture3_matern -- n = 1,000,000 points in R^3
+from an 8-component isotropic Gaussian mixture (means U[-2,2]^3, sigma 0.3), Matern-3/2
+with l = 1, tol = 1e-8, V with 64 N(0,1) columns, FP32 bulk (FP64 radial basis and cores).
+The tolerance is beyond the degree cap (Matern-3/2 coefficients decay like i^-4), so the
+factor is built at p = p_max and the achieved error is measured and reported.
+
+Printed: one JSON line (rank 0).  value = points per second of whole steps, summed over
+ranks; e2e = the same through the C ABI from pinned host buffers (H2D of x and V, build,
+K~ V, D2H of Y).  The roofline object describes the dominant kernel of the step.  The
+FP64-bulk form of the same step is timed beside it (detail.fp64).
+
+--impl reference times the CPU oracle (the only other implementation of this method here)
+on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP32_LANES_PER_SM, NSM, SM_MAX_MHZ = 128, 152, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixture3_matern")
+    ap.add_argument("--n", type=int, default=None, help="override n (same distribution)")
+    ap.add_argument("--p-max", type=int, default=64)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-n", type=int, default=12000, help="oracle sample size")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_params(args):
+    from paper_2202_03655_gb300 import workloads as W
+    w = dict(W.WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
+    return w
+
+
+def exact_rows_matvec(x, kname, ell, v, rows):
+    """(K v)[rows] for the exact kernel with plain torch FP64 ops (an accuracy check only)."""
+    import numpy as np
+    import torch
+    out = []
+    for s in range(0, len(rows), 128):
+        r = torch.from_numpy(np.asarray(rows[s:s + 128])).to(x.device)
+        z = torch.cdist(x[r], x) / ell
+        if kname == "gaussian":
+            K = torch.exp(-0.5 * z * z)
+        elif kname == "cauchy":
+            K = 1.0 / (1.0 + z * z)
+        elif kname == "matern32":
+            K = (1 + 3 ** 0.5 * z) * torch.exp(-(3 ** 0.5) * z)
+        else:
+            K = (1 + 5 ** 0.5 * z + 5.0 / 3.0 * z * z) * torch.exp(-(5 ** 0.5) * z)
+        out.append((K @ v).cpu().numpy())
+        del K, z
+    return np.concatenate(out)
+
+
+def cpu_oracle_step(x, w, V, p_max):
+    """One oracle step (build + K~ V) on the host; returns seconds."""
+    from oracle import hdf as ohdf
+    t = time.perf_counter()
+    fo = ohdf.build(x, w["kernel"], w["ell"], w["tol"], p_max=p_max)
+    ohdf.matvec(fo, V)
+    return time.perf_counter() - t
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: bounded samples of the workload, steps timed."""
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from paper_2202_03655_gb300 import workloads as W
+    w = workload_params(args)
+    ns = min(args.cpu_n, w["n"])
+    x = W.points(args.workload, n=ns)
+    V = np.random.default_rng(1).standard_normal((ns, w["ncols"]))
+    for _ in range(args.warmup):
+        cpu_oracle_step(x, w, V, args.p_max)
+    ts = [cpu_oracle_step(x, w, V, args.p_max) for _ in range(args.steps)]
+    tot = sum(ts)
+    val = ns * args.steps / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": "factor-build points/s (build + K~V step)", "value": val,
+            "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_sample": ns, "d": w["d"], "kernel": w["kernel"],
+                       "lengthscale": w["ell"], "tol": w["tol"], "ncols": w["ncols"], "p_max": args.p_max},
+            "cpu_baseline": {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {ns} points of the workload, full step (build + K~V)"},
+            "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    w = workload_params(args)
+    n, c, d = w["n"], w["ncols"], w["d"]
+    x_np = W.points(args.workload, n=n)
+    V_np = np.asfortranarray(W.rng(w["idx"] + 100).standard_normal((n, c)).astype(np.float32))
+    x = torch.from_numpy(x_np).to(dev)
+    Vc = torch.from_numpy(np.ascontiguousarray(V_np.T)).to(dev)      # (c, n) = column-major n x c
+    Yc = torch.empty_like(Vc)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec, Vblk, Yblk, keep=False):
+        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision=prec, p_max=args.p_max, stream=stream)
+        f.matvec_ptr(Vblk.data_ptr(), n, c, Yblk.data_ptr(), n, stream=stream)
+        info = (f.info.t_ms[5], f.matvec_timings() if keep else None)
+        return f, info
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- warm-up
+    for _ in range(max(args.warmup, 0)):
+        f, _ = step("fp32", Vc, Yc)
+        f.free()
+    torch.cuda.synchronize()
+
+    # ---- timed region (FP32 bulk)
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    l0 = hdf.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    uw_ms, mv_ms, infos = [], [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        f, _ = step("fp32", Vc, Yc)
+        uw_ms.append(f.info.t_ms[5])
+        infos.append(f.info)
+        mv_ms.append(f.matvec_timings())
+        f.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = hdf.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = ws * n * args.steps / (ms_total / 1e3)
+
+    # ---- accuracy of the benchmarked factor (outside the timed region)
+    info = infos[-1]
+    f, _ = step("fp32", Vc, Yc)
+    rows = np.sort(W.rng(7).choice(n, 512, replace=False))
+    exact = exact_rows_matvec(x, w["kernel"], w["ell"], Vc[0].double(), rows)
+    approx = Yc[0][torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+    rel_err = float(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    f.free()
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    r, ldu = info.rank, info.ldu
+    nF = sum(info.s_k[k] for k in range(info.L + 1))
+    uw_bytes = n * ldu * 4 + n * d * 8 + n * nF * 4
+    mv = np.array(mv_ms).mean(axis=0)            # utv, reduce, uw (first 64-column group)
+    utv_bytes = n * ldu * 4 + n * c * 4
+    uwm_bytes = n * ldu * 4 + n * c * 4
+    kernels = {
+        "k_uwriter": (float(np.mean(uw_ms)), uw_bytes),
+        "k_utv_tile": (float(mv[0]), utv_bytes),
+        "k_uw_tile": (float(mv[2]), uwm_bytes),
+    }
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_dom, b_dom = kernels[dom]
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    if dom == "k_uwriter":
+        roof = {"kernel": dom, "bound": "hbm", "achieved": b_dom / (t_dom / 1e3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "peak_source": peak_src}
+    else:
+        flops = 2.0 * n * r * c
+        peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": flops / (t_dom / 1e3) / 1e12, "peak": peak_alu,
+                "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                "hbm_achieved_gbs": b_dom / (t_dom / 1e3) / 1e9}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["algorithmic_bytes"] = b_dom
+    roof["ms_per_launch"] = t_dom
+    kv_bytes = 2 * n * ldu * 4 + n * c * 8
+    kv_ms = float(mv.sum())
+
+    # ---- FP64 form of the same step
+    fp64 = None
+    if not args.no_fp64:
+        V64 = Vc.double()
+        Y64 = torch.empty_like(V64)
+        f, _ = step("fp64", V64, Y64)
+        f.free()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        f, _ = step("fp64", V64, Y64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t64 = a0.elapsed_time(a1)
+        mv64 = f.matvec_timings()
+        approx64 = Y64[0][torch.from_numpy(rows).to(dev)].cpu().numpy()
+        fp64 = {"ms_per_step": t64, "points_per_s": n / (t64 / 1e3), "build_ms": f.info.t_ms[7],
+                "kv_ms": float(mv64.sum()), "kv_gbs": (2 * n * f.info.ldu * 8 + n * c * 16) / (float(mv64.sum()) / 1e3) / 1e9,
+                "rank": f.info.rank, "rel_err_sampled": float(np.linalg.norm(approx64 - exact) / np.linalg.norm(exact))}
+        f.free()
+        del V64, Y64
+
+    # ---- end to end through the C ABI from pinned host buffers
+    xh = torch.from_numpy(x_np).pin_memory()
+    Vh = torch.from_numpy(np.ascontiguousarray(V_np.T)).pin_memory()
+    Yh = torch.empty_like(Vh).pin_memory()
+    xd = torch.empty_like(x)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    b0.record(stream)
+    for _ in range(e2e_steps):
+        xd.copy_(xh, non_blocking=True)
+        Vc.copy_(Vh, non_blocking=True)
+        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
+        Yh.copy_(Yc, non_blocking=True)
+        f.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / e2e_steps
+    e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8 + n * c * 4,
+           "d2h_bytes_per_step": n * c * 4, "ms_per_step": e2e_ms}
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        ns = min(args.cpu_n, n)
+        xs = x_np[:ns]
+        Vs = V_np[:ns].astype(np.float64)
+        ts = cpu_oracle_step(xs, w, Vs, args.p_max)
+        cpu = {"value": ns / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {ns} of the {n} points, one full step (build + K~V, {c} columns), FP64 numpy"}
+
+    if rank == 0:
+        line = {
+            "metric": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
+            "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "kernel": w["kernel"], "lengthscale": w["ell"],
+                       "tol": w["tol"], "ncols": c, "p_max": args.p_max, "p": info.p, "reached": bool(info.reached),
+                       "rank": r, "U_bytes": n * ldu * 4, "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (U alone is ~40 GB)"},
+            "e2e": e2e,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "detail": {
+                "rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound, "cheb_tail": info.cheb_tail,
+                "build_ms": float(np.mean([i.t_ms[7] for i in infos])),
+                "build_phase_ms": [float(np.mean([i.t_ms[q] for i in infos])) for q in range(8)],
+                "build_points_per_s": n / (np.mean([i.t_ms[7] for i in infos]) / 1e3),
+                "kv_ms": kv_ms, "kv_gbs": kv_bytes / (kv_ms / 1e3) / 1e9,
+                "kernel_ms": {k: v[0] for k, v in kernels.items()},
+                "fp64": fp64,
+            },
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

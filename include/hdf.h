@@ -72,6 +72,7 @@ typedef struct {
 
 #define HDF_MAX_D 8
 #define HDF_MAX_L 64
+#define HDF_NPHASE 8
 
 typedef struct {
     int64_t n;
@@ -93,6 +94,11 @@ typedef struct {
     double err_bound;       /* (n cheb_tail + dropped_cost) / (n sqrt(mu2)): a-priori bound
                                on |K - K~|_F / |K|_F */
     int s_k[HDF_MAX_L + 1]; /* kept radial rank per harmonic degree k (Sec. 3.4) */
+    double t_ms[HDF_NPHASE];/* build phase times in ms: 0 centre/radius/mu2 reductions,
+                               1 Chebyshev + degree + radial cores (host), 2 radial-basis Gram
+                               (device), 3 basis factor + eigendecompositions + truncation
+                               (host), 4 radial factors (device), 5 harmonics + U (device),
+                               6 unused, 7 whole build */
 } hdf_info;
 
 /* ---------------------------------------------------------------- factorization ---- */
@@ -132,6 +138,11 @@ hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void
  * host buffers the caller allocated.  Either pointer may be NULL.  Synchronises. */
 hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host);
 
+/* Device times (ms, CUDA events on the launching stream) of the most recent hdf_matvec on
+ * this factor, first column group: ms3[0] U^T V, ms3[1] partial reduction and scaling by S,
+ * ms3[2] U W.  Waits for those events.  HDF_EINVAL if no matvec has run yet. */
+hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3);
+
 /* Release a factor (NULL is ignored). */
 void hdf_free(hdf_factor* f);
 
@@ -161,6 +172,8 @@ hdf_status hdf_radial_cores(const double* a_host, int p, int d, double* cores_ho
 
 /* ----------------------------------------------------------------------- errors ---- */
 const char* hdf_status_string(hdf_status s);
+/* Number of CUDA kernels this library has launched in the process so far (all threads). */
+long long hdf_launch_count(void);
 const char* hdf_last_error(void);           /* thread-local message of the last failure */
 
 #ifdef __cplusplus

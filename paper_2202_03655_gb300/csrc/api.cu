@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +18,8 @@
 using namespace hdf;
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches(0);     // kernels launched by this library
+#define HDF_COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
 
 static hdf_status fail(hdf_status s, const std::string& msg) {
     g_err = msg;
@@ -56,9 +60,17 @@ struct hdf_factor {
     double core_lambda = -1.0;
     std::vector<double> LU;
     std::vector<int> piv;
+    // events around the kernels of the most recent matvec (first column group)
+    cudaEvent_t mv_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool mv_recorded = false;
+    ~hdf_factor() { for (auto& e : mv_ev) if (e) cudaEventDestroy(e); }
 };
 
 // --------------------------------------------------------------------- helpers
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 static int grid_for(int64_t work, int per_block, int cap) {
     int64_t g = (work + per_block - 1) / per_block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
@@ -89,6 +101,8 @@ const char* hdf_status_string(hdf_status s) {
 }
 
 const char* hdf_last_error(void) { return g_err.c_str(); }
+
+long long hdf_launch_count(void) { return g_launches.load(); }
 
 int hdf_cheb_nodes(int p_max) { return cheb_nodes(p_max); }
 
@@ -153,6 +167,18 @@ hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) 
 
 void hdf_free(hdf_factor* f) { delete f; }
 
+hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3) {
+    if (!f || !ms3) return fail(HDF_EINVAL, "hdf_matvec_timings: null argument");
+    if (!f->mv_recorded) return fail(HDF_EINVAL, "hdf_matvec_timings: no matvec recorded yet");
+    for (int q = 0; q < 3; ++q) {
+        float ms = 0.f;
+        HDF_CUDA(cudaEventSynchronize(f->mv_ev[q + 1]));
+        HDF_CUDA(cudaEventElapsedTime(&ms, f->mv_ev[q], f->mv_ev[q + 1]));
+        ms3[q] = ms;
+    }
+    return HDF_OK;
+}
+
 // --------------------------------------------------------------------------- build
 hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, double lengthscale,
                      double tol, hdf_precision prec, const hdf_options* opt, hdf_stream stream,
@@ -170,12 +196,15 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     if (p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, "hdf_build: p_max > 128");
     p_max -= p_max % 2;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double tph[HDF_NPHASE] = {};
+    const double t_start = now_ms();
 
     // ---- A0: centre (mean) and radius (max norm), two-stage reductions
     const int gsum = grid_for(n, 2048, 1024);
     const int64_t chunk = (n + gsum - 1) / gsum;
     DevBuf part;
     HDF_CUDA(part.alloc(sizeof(double) * std::max<int64_t>(gsum * d, 2048)));
+    HDF_COUNT_LAUNCH();
     dev::k_sum_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, part.as<double>());
     HDF_CUDA(cudaGetLastError());
     std::vector<double> hp((size_t)gsum * d);
@@ -188,6 +217,7 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
         cen.c[j] = s / (double)n;
         if (!std::isfinite(cen.c[j])) return fail(HDF_ENOTFINITE, "hdf_build: non-finite point coordinates");
     }
+    HDF_COUNT_LAUNCH();
     dev::k_maxnorm_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, cen, part.as<double>());
     HDF_CUDA(cudaGetLastError());
     HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, gsum * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -201,6 +231,7 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
 
     // ---- mean-square kernel value on the strided subsample
     const int m = (int)std::min<int64_t>(n, 2048);
+    HDF_COUNT_LAUNCH();
     dev::k_mu2_rows<<<m, 256, 0, st>>>(x_dev, n, d, m, kernel, lengthscale, part.as<double>());
     HDF_CUDA(cudaGetLastError());
     std::vector<double> mu_part(m);
@@ -210,6 +241,8 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     for (int t = 0; t < m; ++t) mu2 += mu_part[t];
     mu2 /= (double)m * (double)m;
 
+    tph[0] = now_ms() - t_start;
+    double t0 = now_ms();
     // ---- A1: Chebyshev coefficients and degree
     const int M = cheb_nodes(p_max);
     std::vector<double> a(M);
@@ -225,6 +258,8 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     std::vector<std::vector<double>> cores;
     radial_cores(a.data(), p, d, cores);
 
+    tph[1] = now_ms() - t0;
+    t0 = now_ms();
     // ---- A3: Gram matrices of the radial basis (FP64 on the device)
     const int nb0 = L + 1, nb1 = L;
     const int npairs = nb0 * (nb0 + 1) / 2;
@@ -239,15 +274,19 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     HDF_CUDA(gsumd.alloc(sizeof(double) * 2 * npairs));
     HDF_CUDA(cudaMemcpyAsync(dpairs.p, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
     const size_t gsm = sizeof(double) * (dev::kGramTile * (L + 1) + dev::kGramTile);
+    HDF_COUNT_LAUNCH();
     dev::k_radial_gram<<<ggram, 256, gsm, st>>>(x_dev, n, d, gchunk, cen, inv2R, L, dpairs.as<uint16_t>(),
                                                  npairs, gpart.as<double>());
     HDF_CUDA(cudaGetLastError());
+    HDF_COUNT_LAUNCH();
     dev::k_reduce_cols<<<grid_for(2 * npairs, 256, 1 << 20), 256, 0, st>>>(gpart.as<double>(), ggram,
                                                                           2 * npairs, gsumd.as<double>());
     HDF_CUDA(cudaGetLastError());
     std::vector<double> gram(2 * npairs);
     HDF_CUDA(cudaMemcpyAsync(gram.data(), gsumd.p, gram.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     HDF_CUDA(cudaStreamSynchronize(st));
+    tph[2] = now_ms() - t0;
+    t0 = now_ms();
 
     // ---- A3 (host): factor of each parity's basis from its Gram: B = Q Rf, Rf = D^{1/2} V^T,
     // keeping eigen-directions above a relative floor; Qmat = V D^{-1/2} maps B to Q.
@@ -286,9 +325,9 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     struct Item { double cost; int k, j; };
     std::vector<Item> items;
     std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
-    for (int k = 0; k <= L; ++k) {
+    parallel_for(L + 1, [&](int k) {
         const int par = k % 2, nb = nbv[par], mk = mv[par];
-        if (mk == 0 || nb == 0) continue;
+        if (mk == 0 || nb == 0) return;
         const std::vector<double>& Gk = cores[k];
         std::vector<double> T1((size_t)mk * nb, 0.0), Gm((size_t)mk * mk, 0.0);
         for (int o = 0; o < mk; ++o)
@@ -306,8 +345,10 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
         lam[k].resize(mk);
         vec[k].resize((size_t)mk * mk);
         sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
+    });
+    for (int k = 0; k <= L; ++k) {
         const double hk = (double)harmonic_count(k, d);
-        for (int j = 0; j < mk; ++j) items.push_back({std::fabs(lam[k][j]) * hk / area, k, j});
+        for (int j = 0; j < (int)lam[k].size(); ++j) items.push_back({std::fabs(lam[k][j]) * hk / area, k, j});
     }
     std::sort(items.begin(), items.end(), [](const Item& A, const Item& B) {
         if (A.cost != B.cost) return A.cost < B.cost;
@@ -376,10 +417,13 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     for (int k = 0; k <= std::min(L, HDF_MAX_L); ++k) I.s_k[k] = sk[k];
     f->S_host = S_host;
 
+    tph[3] = now_ms() - t0;
+    for (int q = 0; q < 4; ++q) I.t_ms[q] = tph[q];
     hdf_status st_dev = (prec == HDF_FP64)
         ? build_device<double>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st)
         : build_device<float>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st);
     if (st_dev != HDF_OK) { delete f; return st_dev; }
+    I.t_ms[HDF_NPHASE - 1] = now_ms() - t_start;
     *out = f;
     if (!reached) {
         g_err = "hdf_build: tolerance not reached at p_max; factor built at the cap";
@@ -391,6 +435,45 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
 }  // extern "C"
 
 // -------------------------------------------------------------------------- matvec
+static int ct_for(int c) { return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : c <= 8 ? 8 : c <= 16 ? 16 : c <= 32 ? 32 : 64; }
+
+template <typename T>
+static void launch_utv(int ct, const T* U, int64_t ldU, int64_t n, int64_t r, const T* V, int64_t ldv, int c,
+                       int nchunk, int64_t chunk, double* part, cudaStream_t st) {
+#define HDF_UTV(CT)                                                                                    \
+    case CT: {                                                                                         \
+        dim3 g(nchunk, (unsigned)((r + dev::UtvShape<CT>::AB - 1) / dev::UtvShape<CT>::AB));           \
+        HDF_COUNT_LAUNCH();                                                                            \
+        dev::k_utv_tile<T, CT><<<g, 256, 0, st>>>(U, ldU, n, r, V, ldv, c, chunk, part);               \
+        break;                                                                                         \
+    }
+    switch (ct) { HDF_UTV(1) HDF_UTV(2) HDF_UTV(4) HDF_UTV(8) HDF_UTV(16) HDF_UTV(32) HDF_UTV(64) }
+#undef HDF_UTV
+}
+
+template <typename T>
+static void launch_uw(int ct, const T* U, int64_t ldU, int64_t n, int64_t r, const T* W, int c, T alpha,
+                      const T* B, int64_t ldb, T beta, T* Y, int64_t ldy, cudaStream_t st) {
+#define HDF_UW(CT)                                                                                     \
+    case CT: {                                                                                         \
+        const unsigned g = (unsigned)((n + dev::UwShape<CT>::RB - 1) / dev::UwShape<CT>::RB);          \
+        HDF_COUNT_LAUNCH();                                                                            \
+        dev::k_uw_tile<T, CT><<<g, 256, 0, st>>>(U, ldU, n, r, W, c, alpha, B, ldb, beta, Y, ldy);     \
+        break;                                                                                         \
+    }
+    switch (ct) { HDF_UW(1) HDF_UW(2) HDF_UW(4) HDF_UW(8) HDF_UW(16) HDF_UW(32) HDF_UW(64) }
+#undef HDF_UW
+}
+
+// Row chunks for the split over n: enough blocks to fill the GPU, partials capped at 256 MB.
+static int utv_chunks(int64_t n, int64_t r, int cg) {
+    const int64_t by_rows = (n + 2047) / 2048;
+    const int64_t by_mem = std::max<int64_t>(1, (int64_t)(256ll << 20) / (8 * std::max<int64_t>(1, r * cg)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min(by_rows, by_mem), 1024));
+}
+
+constexpr int kMaxGroup = 64;
+
 template <typename T>
 static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy,
                            const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
@@ -399,6 +482,7 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
     if (r == 0) {
         for (int j = 0; j < ncols; ++j) {
             if (B) {
+                HDF_COUNT_LAUNCH();
                 dev::k_axpby<T><<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(n, 1, beta, B + j * ldb, ldb, (T)0,
                                                                           Y + j * ldy, ldy);
             } else {
@@ -408,23 +492,30 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
         HDF_CUDA(cudaGetLastError());
         return HDF_OK;
     }
-    const int nchunk = grid_for(n, 8192, 256);
+    const int cmax = std::min(ncols, kMaxGroup);
+    const int nchunk = utv_chunks(n, r, cmax);
     const int64_t chunk = (n + nchunk - 1) / nchunk;
     DevBuf part, W;
-    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * dev::kCB * r));
-    HDF_CUDA(W.alloc(sizeof(T) * (size_t)r * dev::kCB));
-    for (int j0 = 0; j0 < ncols; j0 += dev::kCB) {
-        const int cg = std::min(dev::kCB, ncols - j0);
-        dim3 g1(nchunk, (unsigned)((r + 255) / 256));
-        dev::k_utv<T><<<g1, 256, 0, st>>>(U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, chunk, part.as<double>());
+    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * cmax * r));
+    HDF_CUDA(W.alloc(sizeof(T) * (size_t)r * cmax));
+    hdf_factor* fm = const_cast<hdf_factor*>(f);
+    const bool rec = fm->mv_ev[0] != nullptr;
+    for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
+        const int cg = std::min(kMaxGroup, ncols - j0);
+        const int ct = ct_for(cg);
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
+        launch_utv<T>(ct, U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, nchunk, chunk, part.as<double>(), st);
         HDF_CUDA(cudaGetLastError());
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
+        HDF_COUNT_LAUNCH();
         dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
                                                                                S_scale, W.as<T>(), nullptr);
         HDF_CUDA(cudaGetLastError());
-        dev::k_uw<T><<<grid_for(n * 32, 256, 152 * 16), 256, 0, st>>>(U, f->info.ldu, n, r, W.as<T>(), cg, alpha,
-                                                                      B ? B + j0 * ldb : nullptr, ldb, beta,
-                                                                      Y + j0 * ldy, ldy);
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
+        launch_uw<T>(ct, U, f->info.ldu, n, r, W.as<T>(), cg, alpha, B ? B + j0 * ldb : nullptr, ldb, beta,
+                     Y + j0 * ldy, ldy, st);
         HDF_CUDA(cudaGetLastError());
+        if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
     }
     return HDF_OK;
 }
@@ -490,24 +581,27 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
     const int64_t n = f->info.n, r = f->info.rank;
     const T* U = f->U.as<T>();
     if (r == 0) {
+        HDF_COUNT_LAUNCH();
         dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(1.0 / lambda), Bin, ldb,
                                                                            (T)0, Xout, ldx);
         HDF_CUDA(cudaGetLastError());
         return HDF_OK;
     }
-    const int nchunk = grid_for(n, 8192, 256);
+    const int cmax = std::min(ncols, kMaxGroup);
+    const int nchunk = utv_chunks(n, r, cmax);
     const int64_t chunk = (n + nchunk - 1) / nchunk;
     DevBuf part, Wd, Wt;
-    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * dev::kCB * r));
-    HDF_CUDA(Wd.alloc(sizeof(double) * (size_t)r * dev::kCB));
-    HDF_CUDA(Wt.alloc(sizeof(T) * (size_t)r * dev::kCB));
-    std::vector<double> z((size_t)r * dev::kCB), col(r);
-    std::vector<T> y((size_t)r * dev::kCB);
-    for (int j0 = 0; j0 < ncols; j0 += dev::kCB) {
-        const int cg = std::min(dev::kCB, ncols - j0);
-        dim3 g1(nchunk, (unsigned)((r + 255) / 256));
-        dev::k_utv<T><<<g1, 256, 0, st>>>(U, f->info.ldu, n, r, Bin + j0 * ldb, ldb, cg, chunk, part.as<double>());
+    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * cmax * r));
+    HDF_CUDA(Wd.alloc(sizeof(double) * (size_t)r * cmax));
+    HDF_CUDA(Wt.alloc(sizeof(T) * (size_t)r * cmax));
+    std::vector<double> z((size_t)r * cmax), col(r);
+    std::vector<T> y((size_t)r * cmax);
+    for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
+        const int cg = std::min(kMaxGroup, ncols - j0);
+        const int ct = ct_for(cg);
+        launch_utv<T>(ct, U, f->info.ldu, n, r, Bin + j0 * ldb, ldb, cg, nchunk, chunk, part.as<double>(), st);
         HDF_CUDA(cudaGetLastError());
+        HDF_COUNT_LAUNCH();
         dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
                                                                                nullptr, nullptr, Wd.as<double>());
         HDF_CUDA(cudaGetLastError());
@@ -519,9 +613,8 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
             for (int64_t a = 0; a < r; ++a) y[a * cg + j] = (T)col[a];
         }
         HDF_CUDA(cudaMemcpyAsync(Wt.p, y.data(), sizeof(T) * r * cg, cudaMemcpyHostToDevice, st));
-        dev::k_uw<T><<<grid_for(n * 32, 256, 152 * 16), 256, 0, st>>>(U, f->info.ldu, n, r, Wt.as<T>(), cg,
-                                                                      (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
-                                                                      (T)(1.0 / lambda), Xout + j0 * ldx, ldx);
+        launch_uw<T>(ct, U, f->info.ldu, n, r, Wt.as<T>(), cg, (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
+                     (T)(1.0 / lambda), Xout + j0 * ldx, ldx, st);
         HDF_CUDA(cudaGetLastError());
         HDF_CUDA(cudaStreamSynchronize(st));
     }
@@ -537,6 +630,7 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
         DevBuf Gd;
         HDF_CUDA(Gd.alloc(sizeof(double) * (size_t)r * r));
         const unsigned nt = (unsigned)((r + 63) / 64);
+        HDF_COUNT_LAUNCH();
         dev::k_gram<T><<<dim3(nt, nt), 256, 0, st>>>(f->U.as<T>(), f->info.ldu, n, r, Gd.as<double>());
         HDF_CUDA(cudaGetLastError());
         f->G.resize((size_t)r * r);
@@ -564,13 +658,16 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
         if (s != HDF_OK) return s;
         for (int j = 0; j < ncols; ++j)
             HDF_CUDA(cudaMemcpyAsync(Rb.as<T>() + j * n, B + j * ldb, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        HDF_COUNT_LAUNCH();
         dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(-lambda), X, ldx, (T)1,
                                                                            Rb.as<T>(), n);
+        HDF_COUNT_LAUNCH();
         dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(-1), KX.as<T>(), n, (T)1,
                                                                            Rb.as<T>(), n);
         HDF_CUDA(cudaGetLastError());
         s = woodbury_apply<T>(f, lambda, Rb.as<T>(), n, ncols, dX.as<T>(), n, st);
         if (s != HDF_OK) return s;
+        HDF_COUNT_LAUNCH();
         dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)1, dX.as<T>(), n, (T)1, X,
                                                                            ldx);
         HDF_CUDA(cudaGetLastError());
@@ -683,17 +780,23 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaMemcpyAsync(dB.p, cB.data(), sizeof(T) * cB.size(), cudaMemcpyHostToDevice, st));
     }
 
+    cudaEvent_t ev[3];
+    for (int q = 0; q < 3; ++q) HDF_CUDA(cudaEventCreate(&ev[q]));
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int q = 0; q < 3; ++q) cudaEventDestroy(e[q]); } } evg{ev};
+    HDF_CUDA(cudaEventRecord(ev[0], st));
     // A5a: radial factors F
     {
         const size_t sm = sizeof(double) * (dev::kFTile * (L + 1) + dev::kFTile) + sizeof(T) * (m0 + m1) * dev::kFTile;
         if (sm > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
         HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int grid = grid_for((n + dev::kFTile - 1) / dev::kFTile, 1, 152 * 8);
+        HDF_COUNT_LAUNCH();
         dev::k_radial_F<T><<<grid, 256, sm, st>>>(x, n, d, cen, inv2R, L, dQ0.as<double>(), nb0, m0,
                                                   dQ1.as<double>(), nb1, m1, dW.as<T>(), dpar.as<uint8_t>(), nF,
                                                   dF.as<T>(), ldF);
         HDF_CUDA(cudaGetLastError());
     }
+    HDF_CUDA(cudaEventRecord(ev[1], st));
     // A5b: harmonics and U
     {
         dev::UWParams P{};
@@ -705,25 +808,36 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         P.U = f->U.p; P.ldU = I.ldu;
         P.coefA = dA.p; P.coefB = dB.p;
         const int levels = d - 2;
-        int per_warp = levels * ht.tri + 2 * L_used + 1 + (int)nH + nF + 1;
-        per_warp = (per_warp + 3) & ~3;     // keep 16-byte alignment of each warp's area
-        P.per_warp = per_warp;
         const size_t fixed = sizeof(T) * 2 * levels * ht.tri;
         const size_t budget = 200 * 1024;
+        const int pw_fly = ((levels * ht.tri + 2 * L_used + 1 + nF + 1) + 3) & ~3;
+        const int pw_pre = ((levels * ht.tri + 2 * L_used + 1 + (int)nH + nF + 1) + 3) & ~3;
+        const bool pre = fixed + sizeof(T) * 4 * (size_t)pw_pre <= budget;
+        const int per_warp = pre ? pw_pre : pw_fly;
+        P.per_warp = per_warp;
         int warps = 8;
         while (warps > 1 && fixed + sizeof(T) * (size_t)warps * per_warp > budget) warps >>= 1;
         const size_t sm = fixed + sizeof(T) * (size_t)warps * per_warp;
         if (sm > budget) return fail(HDF_ETOOBIG, "hdf_build: harmonic tables exceed shared memory");
-        HDF_CUDA(cudaFuncSetAttribute(dev::k_uwriter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        auto kern = pre ? dev::k_uwriter<T, true> : dev::k_uwriter<T, false>;
+        HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         int occ = 0;
-        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_uwriter<T>, warps * 32, sm));
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm));
         int nsm = 0, dv = 0;
         HDF_CUDA(cudaGetDevice(&dv));
         HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
         const int grid = std::max(1, std::min<int>(nsm * std::max(occ, 1), (int)((n + warps - 1) / warps)));
-        dev::k_uwriter<T><<<grid, warps * 32, sm, st>>>(P);
+        HDF_COUNT_LAUNCH();
+        kern<<<grid, warps * 32, sm, st>>>(P);
         HDF_CUDA(cudaGetLastError());
     }
+    HDF_CUDA(cudaEventRecord(ev[2], st));
     HDF_CUDA(cudaStreamSynchronize(st));
+    float ms1 = 0.f, ms2 = 0.f;
+    HDF_CUDA(cudaEventElapsedTime(&ms1, ev[0], ev[1]));
+    HDF_CUDA(cudaEventElapsedTime(&ms2, ev[1], ev[2]));
+    I.t_ms[4] = ms1;
+    I.t_ms[5] = ms2;
+    for (auto& e : f->mv_ev) HDF_CUDA(cudaEventCreate(&e));
     return HDF_OK;
 }

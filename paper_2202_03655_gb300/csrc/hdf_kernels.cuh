@@ -270,7 +270,9 @@ struct UWParams {
     int per_warp;              // shared elements (type T) per warp
 };
 
-template <typename T>
+// PRE: harmonics precomputed per point into shared memory (nH values per warp); otherwise each
+// column's harmonic is multiplied out from the level tables as it is written.
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int levels = P.d - 2;
@@ -285,8 +287,8 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
     T* base = cB + levels * P.tri + (size_t)warp * P.per_warp;
     T* tbl = base;                               // levels * tri
     T* trig = tbl + levels * P.tri;              // 2L+1, index L + mu
-    T* Ys = trig + 2 * P.L + 1;                  // nH
-    T* Fs = Ys + P.nH;                           // nF + 1
+    T* Ys = trig + 2 * P.L + 1;                  // nH (PRE only)
+    T* Fs = Ys + (PRE ? P.nH : 0);               // nF + 1
     const T* Fg = reinterpret_cast<const T*>(P.F);
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
@@ -350,11 +352,13 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
         if (lane == 0) Fs[P.nF] = (T)0;
         __syncwarp();
         // harmonics
-        for (int g = lane; g < P.nH; g += 32) {
-            const int16_t* ch = P.chains + (int64_t)g * (levels + 1);
-            T v = trig[P.L + ch[levels]];
-            for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + ch[j]];
-            Ys[g] = v;
+        if (PRE) {
+            for (int g = lane; g < P.nH; g += 32) {
+                const int16_t* ch = P.chains + (int64_t)g * (levels + 1);
+                T v = trig[P.L + ch[levels]];
+                for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + ch[j]];
+                Ys[g] = v;
+            }
         }
         __syncwarp();
         // row write, VW consecutive columns per lane per step
@@ -364,7 +368,14 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
                 const uint32_t dsc = __ldg(P.desc + c0 + e);
-                v[e] = Fs[dsc >> 20] * Ys[dsc & 0xFFFFFu];
+                if (PRE) {
+                    v[e] = Fs[dsc >> 20] * Ys[dsc & 0xFFFFFu];
+                } else {
+                    const int16_t* ch = P.chains + (int64_t)(dsc & 0xFFFFFu) * (levels + 1);
+                    T h = trig[P.L + __ldg(ch + levels)];
+                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(ch + j)];
+                    v[e] = Fs[dsc >> 20] * h;
+                }
             }
             VT out;
             if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
@@ -376,38 +387,91 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
 }
 
 // --------------------------------------------------------------------- A7: matvec
-// Partial W = U^T V over row chunks: part[(chunk * c + j) * r + a] (FP64), c <= kCB.
-constexpr int kCB = 16;
-constexpr int kUtvRows = 32;
+// Register-tiled GEMMs on the CUDA cores.  CT = padded column count of the V block (c <= CT).
+// U^T V: a block owns 128 (256 when CT = 1) columns of U and a chunk of rows; each thread
+// keeps a TA x TJ tile of the product.  Partials per chunk are summed in FP64 afterwards.
+template <int CT> struct UtvShape {
+    static constexpr int AB = (CT == 1) ? 256 : 128;                       // columns per block
+    static constexpr int TA = (CT >= 8) ? 4 : (CT == 4 ? 2 : 1);            // columns per thread
+    static constexpr int TJ = (CT * (AB / TA)) / 256;                       // V columns per thread
+};
+constexpr int kKT = 32;     // rows (k) per shared tile
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_utv(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
-                                             const T* __restrict__ V, int64_t ldv, int c, int64_t chunk,
-                                             double* __restrict__ part) {
-    __shared__ T Vs[kUtvRows][kCB];
-    const int64_t a = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+template <typename T, int N> struct VecLd;
+template <typename T> struct VecLd<T, 1> { static __device__ __forceinline__ void ld(const T* p, T* o) { o[0] = p[0]; } };
+template <typename T> struct VecLd<T, 2> {
+    static __device__ __forceinline__ void ld(const T* p, T* o) { o[0] = p[0]; o[1] = p[1]; }
+};
+template <> struct VecLd<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) {
+        const float4 v = *reinterpret_cast<const float4*>(p); o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <> struct VecLd<double, 4> {
+    static __device__ __forceinline__ void ld(const double* p, double* o) {
+        const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+};
+template <> struct VecLd<float, 8> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) { VecLd<float, 4>::ld(p, o); VecLd<float, 4>::ld(p + 4, o + 4); }
+};
+template <> struct VecLd<double, 8> {
+    static __device__ __forceinline__ void ld(const double* p, double* o) { VecLd<double, 4>::ld(p, o); VecLd<double, 4>::ld(p + 4, o + 4); }
+};
+
+// part[(chunk * c + j) * r + a] = sum_{i in chunk} U[i, a] V[i + j ldv]
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_utv_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
+                                                  const T* __restrict__ V, int64_t ldv, int c, int64_t chunk,
+                                                  double* __restrict__ part) {
+    using S = UtvShape<CT>;
+    __shared__ __align__(16) T Us[kKT][S::AB];
+    __shared__ __align__(16) T Vs[kKT][CT];
+    const int t = threadIdx.x;
+    const int tx = t % (S::AB / S::TA), ty = t / (S::AB / S::TA);
+    const int64_t a0 = blockIdx.y * (int64_t)S::AB;
     const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-    T acc[kCB];
+    T acc[S::TA][S::TJ];
 #pragma unroll
-    for (int j = 0; j < kCB; ++j) acc[j] = (T)0;
-    for (int64_t t0 = i0; t0 < i1; t0 += kUtvRows) {
-        const int cnt = (int)min((int64_t)kUtvRows, i1 - t0);
-        for (int idx = threadIdx.x; idx < kUtvRows * kCB; idx += blockDim.x) {
-            const int rr = idx % kUtvRows, j = idx / kUtvRows;
-            Vs[rr][j] = (rr < cnt && j < c) ? V[(t0 + rr) + j * ldv] : (T)0;
+    for (int p = 0; p < S::TA; ++p)
+#pragma unroll
+        for (int q = 0; q < S::TJ; ++q) acc[p][q] = (T)0;
+    for (int64_t k0 = i0; k0 < i1; k0 += kKT) {
+        // U tile: kKT rows x AB columns, row segments are contiguous
+        for (int e = t; e < kKT * S::AB; e += 256) {
+            const int kk = e / S::AB, aa = e % S::AB;
+            const int64_t i = k0 + kk, a = a0 + aa;
+            Us[kk][aa] = (i < i1 && a < ldU) ? U[i * ldU + a] : (T)0;
+        }
+        // V tile: kKT rows x CT columns (column-major source: coalesced along rows)
+        for (int e = t; e < kKT * CT; e += 256) {
+            const int kk = e % kKT, j = e / kKT;
+            const int64_t i = k0 + kk;
+            Vs[kk][j] = (i < i1 && j < c) ? V[i + (int64_t)j * ldv] : (T)0;
         }
         __syncthreads();
-        if (a < r) {
-            for (int rr = 0; rr < cnt; ++rr) {
-                const T u = U[(t0 + rr) * ldU + a];
+#pragma unroll 8
+        for (int kk = 0; kk < kKT; ++kk) {
+            T ua[S::TA], vj[S::TJ];
+            VecLd<T, S::TA>::ld(&Us[kk][tx * S::TA], ua);
+            VecLd<T, S::TJ>::ld(&Vs[kk][ty * S::TJ], vj);
 #pragma unroll
-                for (int j = 0; j < kCB; ++j) acc[j] += u * Vs[rr][j];
-            }
+            for (int p = 0; p < S::TA; ++p)
+#pragma unroll
+                for (int q = 0; q < S::TJ; ++q) acc[p][q] += ua[p] * vj[q];
         }
         __syncthreads();
     }
-    if (a < r)
-        for (int j = 0; j < c; ++j) part[((int64_t)blockIdx.x * c + j) * r + a] = (double)acc[j];
+#pragma unroll
+    for (int p = 0; p < S::TA; ++p) {
+        const int64_t a = a0 + tx * S::TA + p;
+#pragma unroll
+        for (int q = 0; q < S::TJ; ++q) {
+            const int j = ty * S::TJ + q;
+            if (a < r && j < c) part[((int64_t)blockIdx.x * c + j) * r + a] = (double)acc[p][q];
+        }
+    }
 }
 
 // W[a * c + j] = scale_a * sum_chunk part[(chunk * c + j) * r + a]; scale = S[a] or 1.
@@ -425,41 +489,67 @@ __global__ void k_reduce_scale(const double* __restrict__ part, int nchunk, int6
     if (Wd) Wd[idx] = s;
 }
 
-// Y[i + j ldy] = alpha * sum_a U[i, a] W[a * c + j] + beta * B[i + j ldb]; warp per row.
-template <typename T>
-__global__ void __launch_bounds__(256) k_uw(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
-                                            const T* __restrict__ W, int c, T alpha,
-                                            const T* __restrict__ B, int64_t ldb, T beta,
-                                            T* __restrict__ Y, int64_t ldy) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = gw; i < n; i += nw) {
-        T acc[kCB];
+// Y[i + j ldy] = alpha * sum_a U[i, a] W[a * c + j] + beta * B[i + j ldb].
+// A block owns RB rows and all CT columns; each thread keeps a TM x TN tile.
+template <int CT> struct UwShape {
+    static constexpr int RB = (CT == 1) ? 256 : 128;
+    static constexpr int TM = (CT == 64) ? 8 : (CT >= 8 ? 4 : (CT == 4 ? 2 : 1));
+    static constexpr int TN = (CT * (RB / TM)) / 256;
+};
+
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_uw_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
+                                                 const T* __restrict__ W, int c, T alpha,
+                                                 const T* __restrict__ B, int64_t ldb, T beta,
+                                                 T* __restrict__ Y, int64_t ldy) {
+    using S = UwShape<CT>;
+    constexpr int PAD = 4;
+    __shared__ __align__(16) T Us[kKT][S::RB + PAD];
+    __shared__ __align__(16) T Ws[kKT][CT];
+    const int t = threadIdx.x;
+    const int tx = t % (S::RB / S::TM), ty = t / (S::RB / S::TM);
+    const int64_t m0 = blockIdx.x * (int64_t)S::RB;
+    T acc[S::TM][S::TN];
 #pragma unroll
-        for (int j = 0; j < kCB; ++j) acc[j] = (T)0;
-        const T* row = U + i * ldU;
-        for (int64_t a = lane; a < r; a += 32) {
-            const T u = row[a];
-            const T* w = W + a * c;
+    for (int p = 0; p < S::TM; ++p)
 #pragma unroll
-            for (int j = 0; j < kCB; ++j)
-                if (j < c) acc[j] += u * w[j];
+        for (int q = 0; q < S::TN; ++q) acc[p][q] = (T)0;
+    for (int64_t k0 = 0; k0 < r; k0 += kKT) {
+        for (int e = t; e < kKT * S::RB; e += 256) {
+            const int mm = e / kKT, kk = e % kKT;            // consecutive threads walk one row
+            const int64_t i = m0 + mm, a = k0 + kk;
+            Us[kk][mm] = (i < n && a < r) ? U[i * ldU + a] : (T)0;
         }
-#pragma unroll
-        for (int j = 0; j < kCB; ++j) {
-            T v = acc[j];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[j] = v;
+        for (int e = t; e < kKT * CT; e += 256) {
+            const int kk = e / CT, j = e % CT;
+            const int64_t a = k0 + kk;
+            Ws[kk][j] = (a < r && j < c) ? W[a * c + j] : (T)0;
         }
-        if (lane < c) {
-            T v = (T)0;
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kKT; ++kk) {
+            T um[S::TM], wn[S::TN];
+            VecLd<T, S::TM>::ld(&Us[kk][tx * S::TM], um);
+            VecLd<T, S::TN>::ld(&Ws[kk][ty * S::TN], wn);
 #pragma unroll
-            for (int j = 0; j < kCB; ++j)
-                if (j == lane) v = acc[j];
-            T out = alpha * v;
-            if (B) out += beta * B[i + (int64_t)lane * ldb];
-            Y[i + (int64_t)lane * ldy] = out;
+            for (int p = 0; p < S::TM; ++p)
+#pragma unroll
+                for (int q = 0; q < S::TN; ++q) acc[p][q] += um[p] * wn[q];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < S::TN; ++q) {
+        const int j = ty * S::TN + q;
+        if (j >= c) continue;
+#pragma unroll
+        for (int p = 0; p < S::TM; ++p) {
+            const int64_t i = m0 + tx * S::TM + p;
+            if (i < n) {
+                T out = alpha * acc[p][q];
+                if (B) out += beta * B[i + (int64_t)j * ldb];
+                Y[i + (int64_t)j * ldy] = out;
+            }
         }
     }
 }

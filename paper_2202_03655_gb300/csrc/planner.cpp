@@ -2,8 +2,10 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <functional>
+#include <thread>
 
 namespace hdf {
 
@@ -32,6 +34,22 @@ double kernel_dz(int kernel, double z) {
 double kernel_dell(int kernel, double r, double ell) {
     const double z = std::fabs(r) / ell;
     return kernel_dz(kernel, z) * (-z / ell);
+}
+
+void parallel_for(int n, const std::function<void(int)>& fn) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(std::min(n, hw), 32);
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&]() {
+            for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+        });
+    for (auto& th : pool) th.join();
 }
 
 // ----------------------------------------------------------------------- Chebyshev
@@ -182,17 +200,15 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
     const int L = p / 2;
     const double alpha = 0.5 * d - 1.0;
     const double area = sphere_area(d);
-    std::vector<double> Fk(L + 1);
-    for (int q = 0; q <= L; ++q) Fk[q] = a[2 * q];
+    std::vector<std::vector<double>> deriv(L + 1);   // Chebyshev coefficients of F^(k)
+    deriv[0].resize(L + 1);
+    for (int q = 0; q <= L; ++q) deriv[0][q] = a[2 * q];
+    for (int k = 1; k <= L; ++k) cheb_derivative(deriv[k - 1], deriv[k], 2.0);   // d/ds = 2 d/du
     out.assign(L + 1, std::vector<double>());
-    for (int k = 0; k <= L; ++k) {
-        if (k > 0) {
-            std::vector<double> tmp;
-            cheb_derivative(Fk, tmp, 2.0);   // d/ds = 2 d/du
-            Fk.swap(tmp);
-        }
+    parallel_for(L + 1, [&](int k) {
+        const std::vector<double>& Fk = deriv[k];
         const int nb = (k % 2 == 0) ? L + 1 : L;
-        if (nb == 0) continue;
+        if (nb == 0) return;
         const int Nq = (L - k) / 2 + 2;
         std::vector<double> tq(Nq), wq(Nq);
         gauss_gegenbauer(Nq, k + alpha, tq.data(), wq.data());
@@ -235,7 +251,7 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
         for (int l = 0; l < nb; ++l)
             for (int m = 0; m < l; ++m) G[l * nb + m] = G[m * nb + l] = 0.5 * (G[l * nb + m] + G[m * nb + l]);
         out[k].swap(G);
-    }
+    });
 }
 
 // --------------------------------------------------------------- harmonic tables

@@ -7,6 +7,7 @@
 // Remark 1), the truncation rule (Sec. 3.4-3.5), and the harmonic index tables (App. B).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -18,6 +19,9 @@ constexpr double kPi = 3.14159265358979323846;
 double kernel_value(int kernel, double r, double ell);
 double kernel_dz(int kernel, double z);                  // dk/dz, z = r/l
 double kernel_dell(int kernel, double r, double ell);    // dk/dl
+
+// Run fn(0..n-1) on up to hardware_concurrency host threads (each index independent).
+void parallel_for(int n, const std::function<void(int)>& fn);
 
 int cheb_nodes(int p_max);                               // 4 (p_max + 2)
 // a[0..M-1] of f(|r|) on [-1,1], f(r) = k(two_r r; ell) (or dk/dl if dell), DCT-II.

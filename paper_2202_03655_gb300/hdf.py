@@ -18,7 +18,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "HDF_OK", 1: "HDF_EINVAL", 2: "HDF_ENOMEM", 3: "HDF_ECUDA", 4: "HDF_ETOL_UNREACHABLE",
           5: "HDF_ENOTFINITE", 6: "HDF_ESINGULAR", 7: "HDF_ETIMEOUT", 8: "HDF_ETOOBIG"}
 HDF_OK, HDF_ETOL_UNREACHABLE = 0, 4
-MAX_D, MAX_L = 8, 64
+MAX_D, MAX_L, NPHASE = 8, 64, 8
 
 # Every exported entry point with its ctypes signature (include/hdf.h).
 _c_int, _c_i64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -34,7 +34,7 @@ class HdfInfo(ctypes.Structure):
                 ("reached", _c_int), ("rank", _c_i64), ("ldu", _c_i64), ("nharm", _c_i64),
                 ("center", _c_dbl * MAX_D), ("radius", _c_dbl), ("mu2", _c_dbl), ("cheb_tail", _c_dbl),
                 ("tail_budget", _c_dbl), ("drop_budget", _c_dbl), ("dropped_cost", _c_dbl),
-                ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1))]
+                ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1)), ("t_ms", _c_dbl * NPHASE)]
 
 
 SIGNATURES = {
@@ -46,6 +46,7 @@ SIGNATURES = {
     "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "hdf_factor_export": (_c_int, [_vp, _vp, _pdbl]),
     "hdf_free": (None, [_vp]),
+    "hdf_matvec_timings": (_c_int, [_vp, _pdbl]),
     "hdf_cheb_nodes": (_c_int, [_c_int]),
     "hdf_cheb_coeffs": (_c_int, [_c_int, _c_dbl, _c_dbl, _c_int, _pdbl]),
     "hdf_choose_degree": (_c_int, [_pdbl, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int), _pdbl,
@@ -53,6 +54,7 @@ SIGNATURES = {
     "hdf_radial_cores": (_c_int, [_pdbl, _c_int, _c_int, _pdbl, ctypes.POINTER(_c_i64)]),
     "hdf_status_string": (ctypes.c_char_p, [_c_int]),
     "hdf_last_error": (ctypes.c_char_p, []),
+    "hdf_launch_count": (ctypes.c_longlong, []),
 }
 
 _lib = None
@@ -123,6 +125,11 @@ def radial_cores(a, p, d):
         out.append(buf[off:off + nb * nb].reshape(nb, nb))
         off += nb * nb
     return out
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().hdf_launch_count())
 
 
 # --------------------------------------------------------------------- device calls
@@ -205,6 +212,19 @@ class Factor:
                                int(refine_steps), _stream_handle(stream)))
         X = Xc.t()
         return X.reshape(-1) if vec else X
+
+    def matvec_timings(self):
+        """(U^T V ms, reduce ms, U W ms) of the most recent matvec (device events)."""
+        out = np.zeros(3)
+        _check(lib().hdf_matvec_timings(self._h, _dptr(out)))
+        return out
+
+    def free(self):
+        """Release the factor's device memory now."""
+        h = getattr(self, "_h", None)
+        if h is not None:
+            lib().hdf_free(h)
+            self._h = None
 
     def device_U(self):
         """(U pointer, ldu, S pointer) in device memory."""
