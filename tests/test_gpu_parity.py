@@ -75,13 +75,14 @@ def test_many_columns_and_layout():
 def test_identical_points_and_single_point():
     import torch
     hdf = _lib()
+    # K = k(0) 1 1^T exactly; the factor approximates it to tol like any other input
     x = np.ones((50, 3)) * 0.3
     f = hdf.build(to_dev(x), "gaussian", 1.0, 1e-6)
     v = np.arange(50, dtype=np.float64)
     y = f.matvec(to_dev(v)).cpu().numpy()
-    assert np.allclose(y, np.full(50, v.sum()), rtol=1e-10)
+    assert rel(y, np.full(50, v.sum())) <= 1e-6
     f1 = hdf.build(to_dev(np.array([[1.0, 2.0, 3.0]])), "cauchy", 1.0, 1e-6)
-    assert np.allclose(f1.matvec(to_dev(np.array([2.5]))).cpu().numpy(), [2.5], rtol=1e-10)
+    assert rel(f1.matvec(to_dev(np.array([2.5]))).cpu().numpy(), [2.5]) <= 1e-6
 
 
 def test_entries_of_K_tilde_match_oracle():
