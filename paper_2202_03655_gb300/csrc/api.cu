@@ -13,58 +13,20 @@
 
 #include "../../include/hdf.h"
 #include "hdf_kernels.cuh"
+#include "internal.h"
 #include "planner.h"
 
 using namespace hdf;
 
 static thread_local std::string g_err;
-static std::atomic<long long> g_launches(0);     // kernels launched by this library
-#define HDF_COUNT_LAUNCH() g_launches.fetch_add(1, std::memory_order_relaxed)
+namespace hdf {
+std::atomic<long long> g_launches(0);     // kernels launched by this library
 
-static hdf_status fail(hdf_status s, const std::string& msg) {
+hdf_status fail(hdf_status s, const std::string& msg) {
     g_err = msg;
     return s;
 }
-
-#define HDF_CUDA(call)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            return fail(HDF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
-        }                                                                                \
-    } while (0)
-
-// Owns one device allocation.
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    ~DevBuf() { if (p) cudaFree(p); }
-    cudaError_t alloc(size_t b) {
-        if (p) { cudaFree(p); p = nullptr; }
-        bytes = b;
-        return b ? cudaMalloc(&p, b) : cudaSuccess;
-    }
-    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
-};
-
-struct hdf_factor {
-    hdf_info info{};
-    int kernel = 0;
-    double ell = 0, tol = 0;
-    int prec = 0;
-    size_t esz = 8;                 // bytes per bulk element
-    DevBuf U, S;                    // U n x ldu, S rank (bulk type)
-    std::vector<double> S_host;
-    // solve core (lambda S^-1 + U^T U), LU factors on the host
-    std::vector<double> G;
-    double core_lambda = -1.0;
-    std::vector<double> LU;
-    std::vector<int> piv;
-    // events around the kernels of the most recent matvec (first column group)
-    cudaEvent_t mv_ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool mv_recorded = false;
-    ~hdf_factor() { for (auto& e : mv_ev) if (e) cudaEventDestroy(e); }
-};
+}  // namespace hdf
 
 // --------------------------------------------------------------------- helpers
 static double now_ms() {
@@ -102,7 +64,7 @@ const char* hdf_status_string(hdf_status s) {
 
 const char* hdf_last_error(void) { return g_err.c_str(); }
 
-long long hdf_launch_count(void) { return g_launches.load(); }
+long long hdf_launch_count(void) { return hdf::g_launches.load(); }
 
 int hdf_cheb_nodes(int p_max) { return cheb_nodes(p_max); }
 

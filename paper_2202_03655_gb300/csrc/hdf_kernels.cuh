@@ -46,7 +46,7 @@ __device__ __forceinline__ double block_sum_256(double v, double* sh) {
 
 // ------------------------------------------------------------- A0: centre, radius
 // part[b*d + j] = sum over the block's chunk of x[i, j].
-__global__ void k_sum_partial(const double* __restrict__ x, int64_t n, int d, int64_t chunk,
+static __global__ void k_sum_partial(const double* __restrict__ x, int64_t n, int d, int64_t chunk,
                               double* __restrict__ part) {
     __shared__ double sh[256];
     const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -62,7 +62,7 @@ __global__ void k_sum_partial(const double* __restrict__ x, int64_t n, int d, in
 }
 
 // part[b] = max over the block's chunk of |x_i - c|^2.
-__global__ void k_maxnorm_partial(const double* __restrict__ x, int64_t n, int d, int64_t chunk,
+static __global__ void k_maxnorm_partial(const double* __restrict__ x, int64_t n, int d, int64_t chunk,
                                   Center c, double* __restrict__ part) {
     __shared__ double sh[256];
     const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -83,7 +83,7 @@ __global__ void k_maxnorm_partial(const double* __restrict__ x, int64_t n, int d
 
 // Mean-square kernel value over the subsample idx(t) = floor(t n / m), t < m:
 // part[t] = sum_u k(|x_idx(t) - x_idx(u)|)^2.
-__global__ void k_mu2_rows(const double* __restrict__ x, int64_t n, int d, int m, int kernel,
+static __global__ void k_mu2_rows(const double* __restrict__ x, int64_t n, int d, int m, int kernel,
                            double ell, double* __restrict__ part) {
     __shared__ double sh[256];
     const int t = blockIdx.x;
@@ -109,7 +109,7 @@ __global__ void k_mu2_rows(const double* __restrict__ x, int64_t n, int d, int m
 constexpr int kGramTile = 64;
 constexpr int kGramMaxQ = 9;     // ceil(npairs / 256) for L <= 64
 
-__global__ void __launch_bounds__(256) k_radial_gram(const double* __restrict__ x, int64_t n, int d,
+static __global__ void __launch_bounds__(256) k_radial_gram(const double* __restrict__ x, int64_t n, int d,
                                                      int64_t chunk, Center c, double inv2R, int L,
                                                      const uint16_t* __restrict__ pairs, int npairs,
                                                      double* __restrict__ part) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_radial_gram(const double* __restrict__ 
 }
 
 // out[j] = sum_b part[b * ncols + j] in block order.
-__global__ void k_reduce_cols(const double* __restrict__ part, int nblk, int64_t ncols,
+static __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, int64_t ncols,
                               double* __restrict__ out) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= ncols) return;
