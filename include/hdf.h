@@ -121,6 +121,21 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel,
 hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
                       void* Y_dev, int64_t ldy, hdf_stream stream);
 
+/* Same product as hdf_matvec, for callers that must not allocate device memory during the
+ * call: code running while a stream is being captured, code whose device memory belongs to
+ * another allocator's pool, or loops that reserve all memory up front.  The paper has no
+ * counterpart; this is a library convenience.  The partial sums live in a fixed 32 MiB
+ * array inside the library (held on every device that loads it until the process exits)
+ * instead of memory obtained per call; no cudaMalloc, cudaFree or allocating library routine
+ * is called.  Limit: rank * min(ncols, 64) * (8 + element size) bytes <= 32 MiB, otherwise
+ * HDF_ETOOBIG.  The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  All calls share
+ * the one array (each call overwrites every entry it reads), so calls whose executions
+ * overlap on the GPU -- on different streams or from different threads -- race and must
+ * be serialised by the caller.  Arguments and layout as hdf_matvec. */
+hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
+                              void* Y_dev, int64_t ldy, hdf_stream stream);
+
 /* X = (lambda I + K~)^{-1} B (Eq. opt with the Woodbury identity of Sec. 1), followed by
  * refine_steps steps of iterative refinement X += (lambda I + K~)^{-1} (B - lambda X - K~ X).
  * lambda > 0.  The r x r core lambda S^{-1} + U^T U is factored on the host in FP64 (LU

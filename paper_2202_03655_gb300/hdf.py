@@ -41,6 +41,7 @@ SIGNATURES = {
     "hdf_build": (_c_int, [_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(HdfOptions),
                            _vp, ctypes.POINTER(_vp)]),
     "hdf_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
+    "hdf_matvec_noalloc": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_solve": (_c_int, [_vp, _c_dbl, _vp, _c_i64, _c_int, _vp, _c_i64, _c_int, _vp]),
     "hdf_factor_info": (_c_int, [_vp, ctypes.POINTER(HdfInfo)]),
     "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -200,6 +201,11 @@ class Factor:
         """Raw-pointer form of matvec (column-major blocks already on the device)."""
         _check(lib().hdf_matvec(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),
                                 _stream_handle(stream)))
+
+    def matvec_noalloc_ptr(self, V_ptr, ldv, ncols, Y_ptr, ldy, stream=None):
+        """K~ V through hdf_matvec_noalloc (work space in the library's fixed array)."""
+        _check(lib().hdf_matvec_noalloc(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),
+                                        _stream_handle(stream)))
 
     def solve(self, lam, B, refine_steps=1, stream=None):
         """X = (lam I + K~)^{-1} B (Eq. opt via Woodbury), with iterative refinement."""
