@@ -143,6 +143,20 @@ hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev, int64_t ld
 hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev, int64_t ldb, int ncols,
                      void* X_dev, int64_t ldx, int refine_steps, hdf_stream stream);
 
+/* Adjoint of f = sum_j w_j^T K~ v_j (j < ncols <= 64) with respect to the points and the
+ * lengthscale.  The paper does not differentiate the factorization; the semantics are
+ * "frozen structure": the build's scaling (c, R), degree p, radial-basis factor and kept
+ * eigenvectors stay fixed, so row i of U is a smooth function of x_i and S depends on l
+ * only through the radial cores (Eq. rdef).  x_dev must be the points the factor was
+ * built from (row-major n x d FP64).  V_dev, W_dev: column-major n x ncols blocks of the
+ * bulk type.  Output: grad_x_dev (row-major n x d, bulk type, overwritten), and on the
+ * host grad_l_host (d f / d l) and value_host (f) when non-NULL.  Harmonics, radial factors
+ * and their derivatives are recomputed per point; U's Jacobian is never stored.
+ * Synchronises the stream. */
+hdf_status hdf_matvec_adjoint(hdf_factor* f, const double* x_dev, const void* V_dev, int64_t ldv,
+                              const void* W_dev, int64_t ldw, int ncols, void* grad_x_dev,
+                              double* grad_l_host, double* value_host, hdf_stream stream);
+
 /* Metadata of a factor (sizes, scaling, degree, ranks, error budget and bound). */
 hdf_status hdf_factor_info(const hdf_factor* f, hdf_info* info);
 

@@ -1,0 +1,415 @@
+// Adjoint of f = sum_j w_j^T K~ v_j with respect to the points and the lengthscale.
+//
+// The paper does not differentiate the factorization.  We use frozen-structure semantics:
+// the scaling (c, R), the degree p, the radial-basis factor and the kept eigenvectors are
+// those of the build, so that row i of U is an explicit smooth function of x_i,
+//     U_i[(k,s,h)] = F_ks(|x'_i|) Y_k^h(x'_i / |x'_i|),  x' = (x - c)/(2R),
+// and S depends on l only through the radial cores: S_k(l) = W_k^T R_f Gamma_k(l) R_f^T W_k.
+// Then, with a = S U^T v and b = S U^T w,
+//     grad_{x_i} f = (w_i a + v_i b) . dU_i/dx_i,     df/dl = (U^T w)^T (dS/dl) (U^T v).
+// The kernel recomputes F, dF/drho, the harmonics and their gradients per point (nothing of
+// U's Jacobian is stored): for a solid harmonic H of degree k (H(x_hat) = Y(x_hat)),
+//     d/dx' [F(rho) Y(x'/rho)] = [F' - k F/rho] Y x_hat + (F/rho) grad H(x_hat).
+// grad H comes from carrying d/dz and d/dq through the level recurrences
+// P(n) = A z P(n-1) - B q P(n-2) (z = x_{D_j}, q = |x_{0..D_j}|^2) and from
+// d(x0 + i x1)^mu = mu (x0 + i x1)^(mu-1) (dx0 + i dx1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hdf_kernels.cuh"
+#include "internal.h"
+#include "planner.h"
+
+namespace {
+
+using hdf::dev::kMaxD;
+
+template <typename T>
+struct AdjParams {
+    const double* x; int64_t n; int d; double c[kMaxD]; double inv2R;
+    int L;                         // degrees of the harmonic tables (L_used)
+    int Lr;                        // radial degree: basis sizes Lr+1 (even), Lr (odd)
+    int tri;
+    const double* Qm0; int nb0, m0;
+    const double* Qm1; int nb1, m1;
+    const T* Wt; const uint8_t* colk; int nF;
+    const int16_t* chains; int nH; const uint8_t* hk; const int* ktab;
+    const T* coefA; const T* coefB;
+    const T* a; const T* b; int ab_stride;        // a[col * ab_stride], b[col * ab_stride]
+    const T* v; const T* w;                        // this column of V and W (length n)
+    T* grad; int accumulate;
+    int per_warp_d;                                // doubles per warp
+    int per_warp_t;                                // T elements per warp
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int levels = P.d - 2;
+    double* dbase = reinterpret_cast<double*>(smem_raw) + (size_t)warp * P.per_warp_d;
+    double* Tl = dbase;                        // Lr+1: T_l(u)
+    double* dTl = Tl + (P.Lr + 1);             // Lr+1: T_l'(u)
+    double* Q = dTl + (P.Lr + 1);              // m0+m1
+    double* dQ = Q + (P.m0 + P.m1);            // m0+m1
+    T* tbase = reinterpret_cast<T*>(reinterpret_cast<double*>(smem_raw) + (size_t)nwarps * P.per_warp_d) +
+               (size_t)warp * P.per_warp_t;
+    T* R1 = tbase;                             // nF
+    T* R2 = R1 + P.nF;                         // nF
+    T* tv = R2 + P.nF;                         // levels * tri: P
+    T* tz = tv + levels * P.tri;               // dP/dz
+    T* tq = tz + levels * P.tri;               // dP/dq
+    T* trig = tq + levels * P.tri;             // 2L+1
+    T* trx = trig + 2 * P.L + 1;               // d/dx0
+    T* try_ = trx + 2 * P.L + 1;               // d/dx1
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
+    for (int64_t i = gw; i < P.n; i += nw) {
+        double xh[kMaxD];
+        double s2 = 0.0;
+        for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
+        const double rho = sqrt(s2);
+        if (s2 > 0.0) { for (int j = 0; j < P.d; ++j) xh[j] /= rho; }
+        else { for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+        const double u = 8.0 * s2 - 1.0;
+        if (lane == 0) {
+            Tl[0] = 1.0; dTl[0] = 0.0;
+            if (P.Lr >= 1) { Tl[1] = u; dTl[1] = 1.0; }
+            for (int l = 2; l <= P.Lr; ++l) {
+                Tl[l] = 2.0 * u * Tl[l - 1] - Tl[l - 2];
+                dTl[l] = 2.0 * Tl[l - 1] + 2.0 * u * dTl[l - 1] - dTl[l - 2];
+            }
+        }
+        __syncwarp();
+        // Q = B Qmat and dQ/drho; B0 = T_l, B0' = 16 rho T_l'; B1 = rho T_l, B1' = T_l + 16 rho^2 T_l'
+        for (int o = lane; o < P.m0 + P.m1; o += 32) {
+            double q = 0.0, dq = 0.0;
+            if (o < P.m0) {
+                for (int l = 0; l < P.nb0; ++l) {
+                    const double qm = P.Qm0[l * P.m0 + o];
+                    q += Tl[l] * qm;
+                    dq += 16.0 * rho * dTl[l] * qm;
+                }
+            } else {
+                const int oo = o - P.m0;
+                for (int l = 0; l < P.nb1; ++l) {
+                    const double qm = P.Qm1[l * P.m1 + oo];
+                    q += rho * Tl[l] * qm;
+                    dq += (Tl[l] + 16.0 * s2 * dTl[l]) * qm;
+                }
+            }
+            Q[o] = q;
+            dQ[o] = dq;
+        }
+        __syncwarp();
+        // radial factors: R1 = F' - k F / rho, R2 = F / rho (tangential term dropped at rho = 0)
+        for (int col = lane; col < P.nF; col += 32) {
+            const int k = P.colk[col];
+            const int par = k & 1, ob = par ? P.m0 : 0, mp = par ? P.m1 : P.m0;
+            double F = 0.0, dF = 0.0;
+            for (int l = 0; l < mp; ++l) {
+                const double wv = (double)P.Wt[(int64_t)l * P.nF + col];
+                F += Q[ob + l] * wv;
+                dF += dQ[ob + l] * wv;
+            }
+            if (rho > 1e-30) {
+                R1[col] = (T)(dF - k * F / rho);
+                R2[col] = (T)(F / rho);
+            } else {
+                R1[col] = (T)dF;
+                R2[col] = (T)0;
+            }
+        }
+        // level tables with d/dz and d/dq
+        for (int j = 0; j < levels; ++j) {
+            const int D = P.d - 1 - j;
+            double q = 0.0;
+            for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
+            const T z = (T)xh[D], qq = (T)q;
+            const T* A = P.coefA + j * P.tri;
+            const T* B = P.coefB + j * P.tri;
+            T* pv = tv + j * P.tri;
+            T* pz = tz + j * P.tri;
+            T* pq = tq + j * P.tri;
+            for (int mu = lane; mu <= P.L; mu += 32) {
+                const int o = mu * (P.L + 1) - mu * (mu - 1) / 2;
+                const int nmax = P.L - mu;
+                T v2 = A[o], z2 = (T)0, q2 = (T)0;
+                pv[o] = v2; pz[o] = z2; pq[o] = q2;
+                if (nmax >= 1) {
+                    T v1 = A[o + 1] * z, z1 = A[o + 1], q1 = (T)0;
+                    pv[o + 1] = v1; pz[o + 1] = z1; pq[o + 1] = q1;
+                    for (int nn = 2; nn <= nmax; ++nn) {
+                        const T an = A[o + nn], bn = B[o + nn];
+                        const T v0 = an * z * v1 - bn * qq * v2;
+                        const T z0 = an * (v1 + z * z1) - bn * qq * z2;
+                        const T q0 = an * z * q1 - bn * (v2 + qq * q2);
+                        pv[o + nn] = v0; pz[o + nn] = z0; pq[o + nn] = q0;
+                        v2 = v1; z2 = z1; q2 = q1;
+                        v1 = v0; z1 = z0; q1 = q0;
+                    }
+                }
+            }
+        }
+        // (x0 + i x1)^mu and its derivatives, normalised as the harmonics
+        for (int mu = lane; mu <= P.L; mu += 32) {
+            double br = xh[0], bi = xh[1], rr = 1.0, ri = 0.0;     // z^mu
+            double pr = 1.0, pi = 0.0;                              // z^(mu-1)
+            int e = mu;
+            while (e) {
+                if (e & 1) { const double t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
+                const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+                e >>= 1;
+            }
+            if (mu >= 1) {
+                br = xh[0]; bi = xh[1]; e = mu - 1;
+                while (e) {
+                    if (e & 1) { const double t = pr * br - pi * bi; pi = pr * bi + pi * br; pr = t; }
+                    const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+                    e >>= 1;
+                }
+            }
+            if (mu == 0) {
+                trig[P.L] = (T)0.3989422804014327;
+                trx[P.L] = (T)0;
+                try_[P.L] = (T)0;
+            } else {
+                const double nm = 0.5641895835477563;
+                trig[P.L + mu] = (T)(rr * nm);            // Re z^mu
+                trig[P.L - mu] = (T)(ri * nm);            // Im z^mu
+                trx[P.L + mu] = (T)(mu * pr * nm);        // d Re / dx0
+                trx[P.L - mu] = (T)(mu * pi * nm);        // d Im / dx0
+                try_[P.L + mu] = (T)(-mu * pi * nm);      // d Re / dx1
+                try_[P.L - mu] = (T)(mu * pr * nm);       // d Im / dx1
+            }
+        }
+        __syncwarp();
+        const T wi = P.w[i], vi = P.v[i];
+        T g[kMaxD];
+#pragma unroll
+        for (int m = 0; m < kMaxD; ++m) g[m] = (T)0;
+        T xt[kMaxD];
+        for (int m = 0; m < P.d; ++m) xt[m] = (T)xh[m];
+        for (int gi = lane; gi < P.nH; gi += 32) {
+            const int k = P.hk[gi];
+            const int* kt = P.ktab + 5 * k;
+            const int fb = kt[0], sk = kt[1], cb = kt[2], dim = kt[3], hb = kt[4];
+            const int h = gi - hb;
+            T al = (T)0, be = (T)0;
+            for (int s = 0; s < sk; ++s) {
+                const int64_t col = cb + (int64_t)s * dim + h;
+                const T cc = wi * P.a[col * P.ab_stride] + vi * P.b[col * P.ab_stride];
+                al += cc * R1[fb + s];
+                be += cc * R2[fb + s];
+            }
+            const int16_t* ch = P.chains + (int64_t)gi * (levels + 1);
+            const int tmu = ch[levels];
+            T pvv[kMaxD], pzz[kMaxD], pqq[kMaxD];
+            T prod = trig[P.L + tmu];
+            for (int j = 0; j < levels; ++j) {
+                pvv[j] = tv[j * P.tri + ch[j]];
+                pzz[j] = tz[j * P.tri + ch[j]];
+                pqq[j] = tq[j * P.tri + ch[j]];
+                prod *= pvv[j];
+            }
+            // Y x_hat term
+            for (int m = 0; m < P.d; ++m) g[m] += al * prod * xt[m];
+            // grad H: level terms
+            for (int j = 0; j < levels; ++j) {
+                T other = trig[P.L + tmu];
+                for (int j2 = 0; j2 < levels; ++j2)
+                    if (j2 != j) other *= pvv[j2];
+                const int D = P.d - 1 - j;
+                const T cz = be * other * pzz[j], cq = be * other * pqq[j] * (T)2;
+                g[D] += cz;
+                for (int m = 0; m <= D; ++m) g[m] += cq * xt[m];
+            }
+            // grad H: trigonometric factor
+            T pl = (T)1;
+            for (int j = 0; j < levels; ++j) pl *= pvv[j];
+            g[0] += be * pl * trx[P.L + tmu];
+            g[1] += be * pl * try_[P.L + tmu];
+        }
+        for (int m = 0; m < P.d; ++m) {
+            T vsum = g[m];
+            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+            g[m] = vsum;
+        }
+        if (lane < P.d) {
+            T vsum = (T)0;
+            for (int m = 0; m < P.d; ++m) if (m == lane) vsum = g[m];
+            const T out = vsum * (T)P.inv2R;
+            T* dst = P.grad + i * P.d + lane;
+            *dst = P.accumulate ? *dst + out : out;
+        }
+        __syncwarp();
+    }
+}
+
+// dS_k/dl = W_k^T R_f (dGamma_k/dl) R_f^T W_k with dGamma from the Chebyshev coefficients of
+// d kappa/d l truncated at the build's degree (frozen p, c, R).
+void compute_dS(hdf_factor* f) {
+    FactorPlan& P = f->plan;
+    const int M = hdf::cheb_nodes(P.p_max);          // the build's node count
+    std::vector<double> a(std::max(M, 2 * P.L + 2));
+    hdf::cheb_coeffs(f->kernel, f->ell, 1.0 / P.inv2R, M, true, a.data());
+    for (size_t i = 2 * P.L + 1; i < a.size(); ++i) a[i] = 0.0;
+    std::vector<std::vector<double>> dG;
+    hdf::radial_cores(a.data(), 2 * P.L, P.d, dG);
+    P.dSk.assign(P.L + 1, std::vector<double>());
+    for (int k = 0; k <= P.L; ++k) {
+        const int sk = P.sk[k];
+        if (sk == 0) continue;
+        const int par = k & 1, nb = P.nb[par], mk = P.m[par];
+        const std::vector<double>& Rf = P.Rf[par];
+        const std::vector<double>& W = P.Wk[k];
+        // T1 = R_f dG R_f^T (mk x mk)
+        std::vector<double> A((size_t)mk * nb, 0.0), T1((size_t)mk * mk, 0.0), T2((size_t)sk * mk, 0.0);
+        for (int o = 0; o < mk; ++o)
+            for (int l = 0; l < nb; ++l) {
+                double s = 0.0;
+                for (int t = 0; t < nb; ++t) s += Rf[(size_t)o * nb + t] * dG[k][(size_t)t * nb + l];
+                A[(size_t)o * nb + l] = s;
+            }
+        for (int o = 0; o < mk; ++o)
+            for (int o2 = 0; o2 < mk; ++o2) {
+                double s = 0.0;
+                for (int l = 0; l < nb; ++l) s += A[(size_t)o * nb + l] * Rf[(size_t)o2 * nb + l];
+                T1[(size_t)o * mk + o2] = s;
+            }
+        for (int s_ = 0; s_ < sk; ++s_)
+            for (int o2 = 0; o2 < mk; ++o2) {
+                double s = 0.0;
+                for (int o = 0; o < mk; ++o) s += W[(size_t)o * sk + s_] * T1[(size_t)o * mk + o2];
+                T2[(size_t)s_ * mk + o2] = s;
+            }
+        std::vector<double> dS((size_t)sk * sk, 0.0);
+        for (int s_ = 0; s_ < sk; ++s_)
+            for (int t_ = 0; t_ < sk; ++t_) {
+                double s = 0.0;
+                for (int o2 = 0; o2 < mk; ++o2) s += T2[(size_t)s_ * mk + o2] * W[(size_t)o2 * sk + t_];
+                dS[(size_t)s_ * sk + t_] = s;
+            }
+        P.dSk[k].swap(dS);
+    }
+    P.have_dS = true;
+}
+
+template <typename T>
+hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T* Wv, int64_t ldw, int ncols,
+               T* grad, double* grad_l, double* value, cudaStream_t st) {
+    FactorPlan& P = f->plan;
+    const int64_t n = f->info.n, r = f->info.rank;
+    const int d = P.d;
+    if (r == 0) {
+        HDF_CUDA(cudaMemsetAsync(grad, 0, sizeof(T) * n * d, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+        if (grad_l) *grad_l = 0.0;
+        if (value) *value = 0.0;
+        return HDF_OK;
+    }
+    DevBuf ab, zd;
+    HDF_CUDA(ab.alloc(sizeof(T) * (size_t)r * ncols * 2));
+    HDF_CUDA(zd.alloc(sizeof(double) * (size_t)r * ncols * 2));
+    T* a = ab.as<T>();                         // S U^T V  (r x ncols)
+    T* b = a + (size_t)r * ncols;              // S U^T W
+    double* zv = zd.as<double>();              // U^T V (FP64)
+    double* zw = zv + (size_t)r * ncols;
+    hdf_status s = hdf::utv_reduce<T>(f, V, ldv, ncols, nullptr, nullptr, zv, st);
+    if (s != HDF_OK) return s;
+    s = hdf::utv_reduce<T>(f, Wv, ldw, ncols, nullptr, nullptr, zw, st);
+    if (s != HDF_OK) return s;
+    std::vector<double> hv((size_t)r * ncols), hw((size_t)r * ncols);
+    HDF_CUDA(cudaMemcpyAsync(hv.data(), zv, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaMemcpyAsync(hw.data(), zw, sizeof(double) * hw.size(), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<T> ha((size_t)r * ncols), hb((size_t)r * ncols);
+    double fval = 0.0;
+    for (int64_t col = 0; col < r; ++col)
+        for (int j = 0; j < ncols; ++j) {
+            const size_t q = (size_t)col * ncols + j;
+            ha[q] = (T)(f->S_host[col] * hv[q]);
+            hb[q] = (T)(f->S_host[col] * hw[q]);
+            fval += hw[q] * f->S_host[col] * hv[q];
+        }
+    HDF_CUDA(cudaMemcpyAsync(a, ha.data(), sizeof(T) * ha.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(b, hb.data(), sizeof(T) * hb.size(), cudaMemcpyHostToDevice, st));
+
+    AdjParams<T> A{};
+    A.x = x;
+    A.n = n; A.d = d;
+    for (int j = 0; j < d; ++j) A.c[j] = P.c[j];
+    A.inv2R = P.inv2R;
+    A.L = P.L_used; A.Lr = P.L; A.tri = P.tri;
+    A.Qm0 = P.dQ0.as<double>(); A.nb0 = P.nb[0]; A.m0 = P.m[0];
+    A.Qm1 = P.dQ1.as<double>(); A.nb1 = P.nb[1]; A.m1 = P.m[1];
+    A.Wt = P.dW.as<T>(); A.colk = P.dcolk.as<uint8_t>(); A.nF = P.nF;
+    A.chains = P.dchains.as<int16_t>(); A.nH = P.nH; A.hk = P.dhk.as<uint8_t>(); A.ktab = P.dktab.as<int>();
+    A.coefA = P.dA.as<T>(); A.coefB = P.dB.as<T>();
+    A.grad = grad;
+    const int levels = d - 2;
+    A.per_warp_d = 2 * (P.L + 1) + 2 * (P.m[0] + P.m[1]);
+    A.per_warp_t = ((2 * P.nF + 3 * levels * P.tri + 3 * (2 * P.L_used + 1)) + 3) & ~3;
+    const int warps = 4;
+    const size_t sm = sizeof(double) * warps * A.per_warp_d + sizeof(T) * warps * A.per_warp_t;
+    if (sm > 200 * 1024) return hdf::fail(HDF_ETOOBIG, "hdf_matvec_adjoint: per-point tables exceed shared memory");
+    HDF_CUDA(cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int nsm = 0, dv = 0, occ = 0;
+    HDF_CUDA(cudaGetDevice(&dv));
+    HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<T>, warps * 32, sm));
+    const int grid = std::max(1, std::min<int>(nsm * std::max(occ, 1), (int)((n + warps - 1) / warps)));
+    for (int j = 0; j < ncols; ++j) {
+        A.a = a + j; A.b = b + j; A.ab_stride = ncols;
+        A.v = V + j * ldv; A.w = Wv + j * ldw;
+        A.accumulate = (j > 0);
+        HDF_COUNT_LAUNCH();
+        k_adjoint<T><<<grid, warps * 32, sm, st>>>(A);
+        HDF_CUDA(cudaGetLastError());
+    }
+    // d f / d l on the host from U^T V, U^T W and the frozen dS_k/dl
+    if (grad_l) {
+        if (!P.have_dS) compute_dS(f);
+        double gl = 0.0;
+        std::vector<double> tmp;
+        for (int k = 0; k <= P.L; ++k) {
+            const int sk = P.sk[k];
+            if (sk == 0) continue;
+            const int dim = (int)hdf::harmonic_count(k, d);
+            const std::vector<double>& dS = P.dSk[k];
+            for (int j = 0; j < ncols; ++j)
+                for (int h = 0; h < dim; ++h)
+                    for (int s_ = 0; s_ < sk; ++s_) {
+                        const int64_t cs = P.cbase[k] + (int64_t)s_ * dim + h;
+                        double acc = 0.0;
+                        for (int t_ = 0; t_ < sk; ++t_) {
+                            const int64_t ct = P.cbase[k] + (int64_t)t_ * dim + h;
+                            acc += dS[(size_t)s_ * sk + t_] * hv[(size_t)ct * ncols + j];
+                        }
+                        gl += hw[(size_t)cs * ncols + j] * acc;
+                    }
+        }
+        *grad_l = gl;
+    }
+    if (value) *value = fval;
+    HDF_CUDA(cudaStreamSynchronize(st));
+    return HDF_OK;
+}
+
+}  // namespace
+
+extern "C" hdf_status hdf_matvec_adjoint(hdf_factor* f, const double* x_dev, const void* V_dev, int64_t ldv,
+                                         const void* W_dev, int64_t ldw, int ncols, void* grad_x_dev,
+                                         double* grad_l_host, double* value_host, hdf_stream stream) {
+    if (!f || !x_dev || !V_dev || !W_dev || !grad_x_dev || ncols < 1 || ncols > 64 || ldv < f->info.n ||
+        ldw < f->info.n)
+        return hdf::fail(HDF_EINVAL, "hdf_matvec_adjoint: bad argument (1 <= ncols <= 64)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (f->prec == HDF_FP64)
+        return run<double>(f, x_dev, (const double*)V_dev, ldv, (const double*)W_dev, ldw, ncols, (double*)grad_x_dev,
+                           grad_l_host, value_host, st);
+    return run<float>(f, x_dev, (const float*)V_dev, ldv, (const float*)W_dev, ldw, ncols, (float*)grad_x_dev,
+                      grad_l_host, value_host, st);
+}

@@ -381,6 +381,17 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
 
     tph[3] = now_ms() - t0;
     for (int q = 0; q < 4; ++q) I.t_ms[q] = tph[q];
+    {
+        FactorPlan& P = f->plan;
+        P.d = d;
+        P.L = L;
+        P.p_max = p_max;
+        for (int j = 0; j < d; ++j) P.c[j] = cen.c[j];
+        P.inv2R = inv2R;
+        for (int q = 0; q < 2; ++q) { P.nb[q] = nbv[q]; P.m[q] = mv[q]; P.Rf[q] = Rf[q]; P.Qmat[q] = Qmat[q]; }
+        P.Wk = Wk;
+        P.sk = sk;
+    }
     hdf_status st_dev = (prec == HDF_FP64)
         ? build_device<double>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st)
         : build_device<float>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st);
@@ -481,6 +492,31 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
     }
     return HDF_OK;
 }
+
+namespace hdf {
+template <typename T>
+hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const T* S_scale, T* W, double* Wd,
+                      cudaStream_t st) {
+    const int64_t n = f->info.n, r = f->info.rank;
+    if (c < 1 || c > kMaxGroup) return fail(HDF_EINVAL, "utv_reduce: 1 <= c <= 64");
+    const int nchunk = utv_chunks(n, r, c);
+    const int64_t chunk = (n + nchunk - 1) / nchunk;
+    DevBuf part;
+    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * c * r));
+    launch_utv<T>(ct_for(c), f->U.as<T>(), f->info.ldu, n, r, V, ldv, c, nchunk, chunk, part.as<double>(), st);
+    HDF_CUDA(cudaGetLastError());
+    HDF_COUNT_LAUNCH();
+    dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, c, S_scale,
+                                                                          W, Wd);
+    HDF_CUDA(cudaGetLastError());
+    HDF_CUDA(cudaStreamSynchronize(st));     // part is freed on return
+    return HDF_OK;
+}
+template hdf_status utv_reduce<float>(const hdf_factor*, const float*, int64_t, int, const float*, float*, double*,
+                                      cudaStream_t);
+template hdf_status utv_reduce<double>(const hdf_factor*, const double*, int64_t, int, const double*, double*,
+                                       double*, cudaStream_t);
+}  // namespace hdf
 
 extern "C" hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols, void* Y_dev, int64_t ldy,
                       hdf_stream stream) {
@@ -689,6 +725,9 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
             colpar[col] = (uint8_t)(k % 2);
             for (int o = 0; o < mk; ++o) Wt[(size_t)o * nF + col] = (T)Wk[k][(size_t)o * sk[k] + s];
         }
+    std::vector<uint8_t> colk(nF);
+    for (int k = 0; k <= L; ++k)
+        for (int s = 0; s < sk[k]; ++s) colk[fbase[k] + s] = (uint8_t)k;
     // harmonic tables and chains for degrees <= L_used
     HarmonicTables ht;
     harmonic_tables(d, L_used, ht);
@@ -702,6 +741,19 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     }
     const int64_t nH = hbase[L + 1];
     if (nH >= (1 << 20) || nF >= 4095) return fail(HDF_ETOOBIG, "hdf_build: too many harmonics or radial columns");
+    std::vector<uint8_t> hk(nH);
+    std::vector<int> ktab(5 * (L + 1), 0);
+    std::vector<int> cbase(L + 2, 0);
+    for (int k = 0; k <= L; ++k) {
+        for (int64_t g = hbase[k]; g < hbase[k + 1]; ++g) hk[g] = (uint8_t)k;
+        const int64_t hkc = (sk[k] > 0) ? ht.count[k] : 0;
+        cbase[k + 1] = cbase[k] + (int)(hkc * sk[k]);
+        ktab[5 * k + 0] = fbase[k];
+        ktab[5 * k + 1] = sk[k];
+        ktab[5 * k + 2] = cbase[k];
+        ktab[5 * k + 3] = (int)hkc;
+        ktab[5 * k + 4] = (int)hbase[k];
+    }
     // column descriptors
     std::vector<uint32_t> desc(I.ldu);
     {
@@ -715,8 +767,25 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     std::vector<T> cA(ht.coefA.size()), cB(ht.coefB.size());
     for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)ht.coefA[q]; cB[q] = (T)ht.coefB[q]; }
 
-    // upload
-    DevBuf dQ0, dQ1, dW, dpar, dF, dchains, ddesc, dA, dB;
+    // upload (kept in the factor for the adjoint)
+    FactorPlan& PL = f->plan;
+    PL.L_used = L_used;
+    PL.tri = ht.tri;
+    PL.nF = nF;
+    PL.nH = (int)nH;
+    PL.mmax = mmax;
+    PL.fbase.assign(fbase.begin(), fbase.end());
+    PL.cbase = cbase;
+    PL.hbase.assign(hbase.begin(), hbase.end());
+    DevBuf dpar, dF;
+    DevBuf &dQ0 = PL.dQ0, &dQ1 = PL.dQ1, &dW = PL.dW, &dchains = PL.dchains, &ddesc = PL.ddesc, &dA = PL.dA,
+           &dB = PL.dB;
+    HDF_CUDA(PL.dcolk.alloc(colk.size()));
+    HDF_CUDA(PL.dhk.alloc(hk.size() + 1));
+    HDF_CUDA(PL.dktab.alloc(sizeof(int) * ktab.size()));
+    HDF_CUDA(cudaMemcpyAsync(PL.dcolk.p, colk.data(), colk.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dhk.p, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dktab.p, ktab.data(), sizeof(int) * ktab.size(), cudaMemcpyHostToDevice, st));
     const int nb0 = nbv[0], nb1 = nbv[1], m0 = mv[0], m1 = mv[1];
     HDF_CUDA(dQ0.alloc(sizeof(double) * std::max<size_t>(1, Qmat[0].size())));
     HDF_CUDA(dQ1.alloc(sizeof(double) * std::max<size_t>(1, Qmat[1].size())));

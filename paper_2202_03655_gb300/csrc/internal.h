@@ -16,6 +16,12 @@ hdf_status fail(hdf_status s, const std::string& msg);
 // Counter of kernel launches reported by hdf_launch_count.
 extern std::atomic<long long> g_launches;
 
+// W = S_scale .* (U^T V) for one group of c <= 64 columns: W (r x c row-major, bulk) and/or
+// Wd (r x c, FP64).  S_scale may be null (no scaling).  Allocates its partial sums.
+template <typename T>
+hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const T* S_scale, T* W, double* Wd,
+                      cudaStream_t st);
+
 }  // namespace hdf
 
 #define HDF_COUNT_LAUNCH() hdf::g_launches.fetch_add(1, std::memory_order_relaxed)
@@ -41,7 +47,26 @@ struct DevBuf {
     template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// What the build decided, kept for the adjoint (frozen structure) and for diagnostics.
+struct FactorPlan {
+    int d = 0, L = 0, L_used = 0, tri = 0, nF = 0, nH = 0, mmax = 0, p_max = 0;
+    int nb[2] = {0, 0}, m[2] = {0, 0};
+    double c[HDF_MAX_D] = {};
+    double inv2R = 0.0;
+    std::vector<double> Rf[2], Qmat[2];        // basis factor and its inverse map, per parity
+    std::vector<std::vector<double>> Wk;       // kept eigenvectors per k (m x s_k, row-major)
+    std::vector<int> sk, fbase, cbase, hbase;  // per k: kept count, F column, U column, harmonic bases
+    // device copies: Qmat0, Qmat1 (FP64), Wt (m_max x nF, bulk), colk (F column -> k),
+    // chains (nH x (d-1) int16), hk (harmonic -> k), ktab (per k: fbase, s_k, cbase, |H_k|, hbase),
+    // desc (ldU column descriptors), coefA/coefB (level recurrences, bulk)
+    DevBuf dQ0, dQ1, dW, dcolk, dchains, dhk, dktab, ddesc, dA, dB;
+    // d S_k / d l (s_k x s_k), computed on first use by the adjoint
+    std::vector<std::vector<double>> dSk;
+    bool have_dS = false;
+};
+
 struct hdf_factor {
+    FactorPlan plan;
     hdf_info info{};
     int kernel = 0;
     double ell = 0, tol = 0;

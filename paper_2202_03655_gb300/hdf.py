@@ -43,6 +43,7 @@ SIGNATURES = {
     "hdf_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_matvec_noalloc": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_solve": (_c_int, [_vp, _c_dbl, _vp, _c_i64, _c_int, _vp, _c_i64, _c_int, _vp]),
+    "hdf_matvec_adjoint": (_c_int, [_vp, _vp, _vp, _c_i64, _vp, _c_i64, _c_int, _vp, _pdbl, _pdbl, _vp]),
     "hdf_factor_info": (_c_int, [_vp, ctypes.POINTER(HdfInfo)]),
     "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "hdf_factor_export": (_c_int, [_vp, _vp, _pdbl]),
@@ -206,6 +207,24 @@ class Factor:
         """K~ V through hdf_matvec_noalloc (work space in the library's fixed array)."""
         _check(lib().hdf_matvec_noalloc(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),
                                         _stream_handle(stream)))
+
+    def adjoint(self, x, V, W, stream=None):
+        """Gradient of f = sum_j W[:, j]^T K~ V[:, j] under frozen structure.
+
+        x: the build points (CUDA float64, (n, d)); V, W: (n,) or (n, c) of the bulk dtype.
+        Returns (grad_x (n, d) bulk dtype, d f / d l, f)."""
+        import torch
+        Vc, Wc = self._block(V), self._block(W)
+        c = Vc.shape[0]
+        if Wc.shape[0] != c:
+            raise ValueError("V and W must have the same number of columns")
+        x = x.contiguous()
+        G = torch.empty((self.n, self.info.d), dtype=self.dtype, device=x.device)
+        gl, val = _c_dbl(), _c_dbl()
+        _check(lib().hdf_matvec_adjoint(self._h, _vp(x.data_ptr()), _vp(Vc.data_ptr()), self.n,
+                                        _vp(Wc.data_ptr()), self.n, c, _vp(G.data_ptr()),
+                                        ctypes.byref(gl), ctypes.byref(val), _stream_handle(stream)))
+        return G, gl.value, val.value
 
     def solve(self, lam, B, refine_steps=1, stream=None):
         """X = (lam I + K~)^{-1} B (Eq. opt via Woodbury), with iterative refinement."""
