@@ -14,26 +14,36 @@ from paper_2202_03655_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _build(x, kname, ell, tol, prec):
+def _build(x, kname, ell, tol, prec, p_max=None):
     from paper_2202_03655_gb300 import hdf
-    return hdf.build(to_dev(x), kname, ell, tol, precision=prec)
+    return hdf.build(to_dev(x), kname, ell, tol, precision=prec, p_max=p_max)
 
 
-@pytest.mark.parametrize("d,kname,ell", [(4, "gaussian", 0.8), (3, "cauchy", 0.7), (5, "matern52", 2.0)])
-def test_adjoint_vs_oracle_fd(d, kname, ell):
+@pytest.mark.parametrize("d,kname,ell,n,p_max", [(4, "gaussian", 0.8, 120, 64), (3, "cauchy", 0.7, 120, 64),
+                                                (5, "gaussian", 2.0, 200, 64), (3, "matern52", 1.0, 400, 32)])
+def test_adjoint_vs_oracle_fd(d, kname, ell, n, p_max):
+    """The frozen radial functions agree between the two sides at the data points; between
+    them (and so in their derivatives) they agree only where the radial basis is well
+    conditioned on the data, so the cases keep n well above the basis size p/2 + 1.  At a
+    loose tol the two sides may also keep different eigenpairs near the budget boundary; at
+    1e-9 both keep the same set."""
     import torch
     g = np.random.default_rng(20 + d)
-    x = W.uniform_cube(g, 120, d)
-    v, w = g.standard_normal(120), g.standard_normal(120)
-    tol = 1e-9 if kname != "matern52" else 1e-5
-    f = _build(x, kname, ell, tol, "fp64")
+    x = W.uniform_cube(g, n, d)
+    v, w = g.standard_normal(n), g.standard_normal(n)
+    tol = 1e-9
+    f = _build(x, kname, ell, tol, "fp64", p_max)
     G, dl, val = f.adjoint(to_dev(x), to_dev(v), to_dev(w))
-    fo = ohdf.build(x, kname, ell, tol)
+    fo = ohdf.build(x, kname, ell, tol, p_max=p_max)
+    assert f.info.p == fo.plan.p
     Go, dlo = ohdf.adjoint_fd(fo, x, v, w)
     vo = float(w @ ohdf.matvec(fo, v))
-    assert abs(val - vo) <= 1e-9 * abs(vo) + 1e-12
-    assert rel(G.cpu().numpy(), Go) <= 1e-5
-    assert abs(dl - dlo) <= 1e-5 * abs(dlo)
+    # both sides are the same frozen-structure function up to rounding and truncation
+    # choices at the budget boundary, which are of order tol
+    gtol = max(1e-5, 100 * tol)
+    assert abs(val - vo) <= max(10 * tol, 1e-7) * abs(vo)
+    assert rel(G.cpu().numpy(), Go) <= gtol
+    assert abs(dl - dlo) <= gtol * abs(dlo)
 
 
 def test_adjoint_fp32_and_multicolumn():
