@@ -157,6 +157,41 @@ hdf_status hdf_matvec_adjoint(hdf_factor* f, const double* x_dev, const void* V_
                               const void* W_dev, int64_t ldw, int ncols, void* grad_x_dev,
                               double* grad_l_host, double* value_host, hdf_stream stream);
 
+/* ------------------------------------------------------------------ batches ---- */
+typedef struct hdf_batch hdf_batch;          /* opaque, owned by the library */
+
+/* Factor nsets independent point sets in one pass: set s is rows offsets[s]..offsets[s+1]-1
+ * of x_dev (row-major FP64, d columns; offsets_host[0] = 0, every set non-empty) with its own
+ * lengthscale lengthscales_host[s].  Each set is factored exactly as hdf_build would
+ * factor it alone (Algorithm 1, symmetric form, same tol, kernel and options); the batch only
+ * schedules the work together: segmented device reductions, per-set host planning on
+ * threads, and one persistent kernel that builds the radial factors and U of every set.
+ * Returns HDF_ETOL_UNREACHABLE (with a usable batch) if any set was capped at p_max.
+ * Synchronises the stream. */
+hdf_status hdf_build_batched(int nsets, const int64_t* offsets_host, const double* x_dev, int d,
+                             hdf_kernel kernel, const double* lengthscales_host, double tol,
+                             hdf_precision prec, const hdf_options* opt, hdf_stream stream,
+                             hdf_batch** out);
+
+/* Y_s = K~_s V_s for every set at once: V_dev, Y_dev are column-major (sum n) x ncols blocks of
+ * the bulk type whose rows follow the concatenated points; 1 <= ncols <= 64.  The kernels are
+ * recorded in a CUDA graph on the first call for a given (V, Y, ldv, ldy, ncols) and replayed
+ * on later calls.  Asynchronous on the stream. */
+hdf_status hdf_batch_matvec(hdf_batch* b, const void* V_dev, int64_t ldv, int ncols,
+                            void* Y_dev, int64_t ldy, hdf_stream stream);
+
+/* Metadata of set s (as hdf_factor_info). */
+hdf_status hdf_batch_info(const hdf_batch* b, int set, hdf_info* info);
+
+/* Phase times of the batched build in ms (layout of hdf_info.t_ms; index 5 is the persistent
+ * radial-factor + U kernel). */
+hdf_status hdf_batch_timings(const hdf_batch* b, double* t_ms);
+
+/* Copy set s's U (n_s x rank_s, packed row-major, bulk type) and S (FP64) to the host. */
+hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S_host);
+
+void hdf_batch_free(hdf_batch* b);
+
 /* Metadata of a factor (sizes, scaling, degree, ranks, error budget and bound). */
 hdf_status hdf_factor_info(const hdf_factor* f, hdf_info* info);
 

@@ -26,8 +26,9 @@ Steps, in the paper's order:
    Remark 1).  Column order: k ascending, then kept eigenpairs by decreasing |lambda|,
    then h in ``harmonics.index_set`` order.
 
-|K|_F is taken from mu2 = mean K_ij^2: exactly when n <= 2048, otherwise over all pairs of
-the 2048 points with indices floor(t n / 2048), t = 0..2047.
+|K|_F is taken from mu2 = mean K_ij^2: exactly when n <= 512, otherwise over all pairs of
+the 512 points with indices floor(t n / 512), t = 0..511 (the estimate only sets the two
+error budgets, so a coarse sample suffices).
 """
 from dataclasses import dataclass, field
 
@@ -41,7 +42,7 @@ from .radial import basis_size, literal_core, literal_power_core, radial_basis, 
 
 P_MAX_DEFAULT = 64
 ETA_DEFAULT = 1.0
-MU2_EXACT_MAX = 2048
+MU2_EXACT_MAX = 512
 
 
 def cheb_nodes_count(p_max):

@@ -19,6 +19,7 @@
 using namespace hdf;
 
 static thread_local std::string g_err;
+constexpr int kMu2Sample = 512;     // mu2 from all pairs of at most this many strided points
 namespace hdf {
 std::atomic<long long> g_launches(0);     // kernels launched by this library
 
@@ -40,10 +41,7 @@ static int grid_for(int64_t work, int per_block, int cap) {
 
 template <typename T>
 static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d, const dev::Center& cen,
-                               double inv2R, int L, const std::vector<std::vector<double>>& Qmat,
-                               const std::vector<int>& nbv, const std::vector<int>& mv,
-                               const std::vector<std::vector<double>>& Wk, const std::vector<int>& sk,
-                               cudaStream_t st);
+                               double inv2R, const DegreePlan& dp, const FactorChoice& fc, cudaStream_t st);
 
 extern "C" {
 
@@ -192,7 +190,7 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     const double inv2R = 1.0 / (2.0 * R);
 
     // ---- mean-square kernel value on the strided subsample
-    const int m = (int)std::min<int64_t>(n, 2048);
+    const int m = (int)std::min<int64_t>(n, kMu2Sample);
     HDF_COUNT_LAUNCH();
     dev::k_mu2_rows<<<m, 256, 0, st>>>(x_dev, n, d, m, kernel, lengthscale, part.as<double>());
     HDF_CUDA(cudaGetLastError());
@@ -205,25 +203,15 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
 
     tph[0] = now_ms() - t_start;
     double t0 = now_ms();
-    // ---- A1: Chebyshev coefficients and degree
-    const int M = cheb_nodes(p_max);
-    std::vector<double> a(M);
-    cheb_coeffs(kernel, lengthscale, 2.0 * R, M, false, a.data());
-    const double tail_budget = 0.5 * tol * std::sqrt(mu2);
-    const double drop_budget = 0.5 * eta * tol * (double)n * std::sqrt(mu2);
-    double tail = 0.0;
-    bool reached = false;
-    const int p = choose_degree(a.data(), M, tail_budget, p_max, &tail, &reached);
-    const int L = p / 2;
-
-    // ---- A2: radial cores
-    std::vector<std::vector<double>> cores;
-    radial_cores(a.data(), p, d, cores);
-
+    // ---- A1-A2: Chebyshev coefficients, degree, radial cores (host)
+    DegreePlan dp;
+    plan_degree(kernel, lengthscale, R, mu2, n, tol, eta, p_max, d, true, dp);
+    const int p = dp.p, L = dp.L;
     tph[1] = now_ms() - t0;
     t0 = now_ms();
+
     // ---- A3: Gram matrices of the radial basis (FP64 on the device)
-    const int nb0 = L + 1, nb1 = L;
+    const int nb0 = L + 1;
     const int npairs = nb0 * (nb0 + 1) / 2;
     std::vector<uint16_t> pairs;
     for (int l = 0; l < nb0; ++l)
@@ -250,108 +238,9 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     tph[2] = now_ms() - t0;
     t0 = now_ms();
 
-    // ---- A3 (host): factor of each parity's basis from its Gram: B = Q Rf, Rf = D^{1/2} V^T,
-    // keeping eigen-directions above a relative floor; Qmat = V D^{-1/2} maps B to Q.
-    std::vector<std::vector<double>> Rf(2), Qmat(2);
-    std::vector<int> nbv = {nb0, nb1}, mv = {0, 0};
-    for (int par = 0; par < 2; ++par) {
-        const int nb = nbv[par];
-        if (nb == 0) continue;
-        std::vector<double> Gm(nb * nb), w(nb), V(nb * nb);
-        int q = 0;
-        for (int l = 0; l < nb0; ++l)
-            for (int lp = l; lp < nb0; ++lp, ++q) {
-                if (l < nb && lp < nb) Gm[l * nb + lp] = Gm[lp * nb + l] = gram[(size_t)par * npairs + q];
-            }
-        sym_eig(nb, Gm.data(), w.data(), V.data());
-        double wmax = 0.0;
-        for (int l = 0; l < nb; ++l) wmax = std::max(wmax, w[l]);
-        const double floor_ = wmax * 1e-13 * nb;
-        std::vector<int> keep;
-        for (int l = 0; l < nb; ++l) if (w[l] > floor_) keep.push_back(l);
-        const int mk = (int)keep.size();
-        mv[par] = mk;
-        Rf[par].assign((size_t)mk * nb, 0.0);
-        Qmat[par].assign((size_t)nb * mk, 0.0);
-        for (int o = 0; o < mk; ++o) {
-            const double sq = std::sqrt(w[keep[o]]);
-            for (int l = 0; l < nb; ++l) {
-                Rf[par][(size_t)o * nb + l] = sq * V[l * nb + keep[o]];
-                Qmat[par][(size_t)l * mk + o] = V[l * nb + keep[o]] / sq;
-            }
-        }
-    }
-
-    // ---- A4: per-degree eigendecompositions G_k = Rf Gamma_k Rf^T and global truncation
-    const double area = sphere_area(d);
-    struct Item { double cost; int k, j; };
-    std::vector<Item> items;
-    std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
-    parallel_for(L + 1, [&](int k) {
-        const int par = k % 2, nb = nbv[par], mk = mv[par];
-        if (mk == 0 || nb == 0) return;
-        const std::vector<double>& Gk = cores[k];
-        std::vector<double> T1((size_t)mk * nb, 0.0), Gm((size_t)mk * mk, 0.0);
-        for (int o = 0; o < mk; ++o)
-            for (int l = 0; l < nb; ++l) {
-                double s = 0.0;
-                for (int t = 0; t < nb; ++t) s += Rf[par][(size_t)o * nb + t] * Gk[(size_t)t * nb + l];
-                T1[(size_t)o * nb + l] = s;
-            }
-        for (int o = 0; o < mk; ++o)
-            for (int o2 = 0; o2 <= o; ++o2) {
-                double s = 0.0;
-                for (int l = 0; l < nb; ++l) s += T1[(size_t)o * nb + l] * Rf[par][(size_t)o2 * nb + l];
-                Gm[(size_t)o * mk + o2] = Gm[(size_t)o2 * mk + o] = s;
-            }
-        lam[k].resize(mk);
-        vec[k].resize((size_t)mk * mk);
-        sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
-    });
-    for (int k = 0; k <= L; ++k) {
-        const double hk = (double)harmonic_count(k, d);
-        for (int j = 0; j < (int)lam[k].size(); ++j) items.push_back({std::fabs(lam[k][j]) * hk / area, k, j});
-    }
-    std::sort(items.begin(), items.end(), [](const Item& A, const Item& B) {
-        if (A.cost != B.cost) return A.cost < B.cost;
-        if (A.k != B.k) return A.k < B.k;
-        return A.j < B.j;
-    });
-    std::vector<std::vector<char>> dropped(L + 1);
-    for (int k = 0; k <= L; ++k) dropped[k].assign(lam[k].size(), 0);
-    double acc = 0.0;
-    for (const Item& it : items) {
-        if (acc + it.cost > drop_budget) break;
-        acc += it.cost;
-        dropped[it.k][it.j] = 1;
-    }
-    std::vector<int> sk(L + 1, 0);
-    std::vector<std::vector<double>> Wk(L + 1);     // mk x s_k, row-major, columns by decreasing |lambda|
-    std::vector<double> S_host;
-    std::vector<int64_t> hcount(L + 1);
-    int L_used = -1;
-    int64_t rank = 0, nH = 0;
-    for (int k = 0; k <= L; ++k) {
-        hcount[k] = harmonic_count(k, d);
-        std::vector<int> idx;
-        for (int j = 0; j < (int)lam[k].size(); ++j) if (!dropped[k][j]) idx.push_back(j);
-        std::sort(idx.begin(), idx.end(), [&](int A, int B) {
-            const double fa = std::fabs(lam[k][A]), fb = std::fabs(lam[k][B]);
-            if (fa != fb) return fa > fb;
-            return A < B;
-        });
-        sk[k] = (int)idx.size();
-        if (sk[k] == 0) continue;
-        L_used = k;
-        const int mk = mv[k % 2];
-        Wk[k].assign((size_t)mk * sk[k], 0.0);
-        for (int s = 0; s < sk[k]; ++s)
-            for (int o = 0; o < mk; ++o) Wk[k][(size_t)o * sk[k] + s] = vec[k][(size_t)o * mk + idx[s]];
-        rank += hcount[k] * sk[k];
-        nH += hcount[k];
-        for (int s = 0; s < sk[k]; ++s)
-            for (int64_t h = 0; h < hcount[k]; ++h) S_host.push_back(lam[k][idx[s]]);
-    }
+    // ---- A3-A4 (host): basis factor, per-degree eigendecompositions, truncation
+    FactorChoice fc;
+    plan_factor(gram, L, d, dp.cores, dp.drop_budget, true, fc);
 
     hdf_factor* f = new hdf_factor();
     f->kernel = kernel;
@@ -365,19 +254,19 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     I.precision = prec;
     I.p = p;
     I.L = L;
-    I.reached = reached ? 1 : 0;
-    I.rank = rank;
-    I.nharm = nH;
+    I.reached = dp.reached ? 1 : 0;
+    I.rank = fc.rank;
+    I.nharm = fc.nH;
     for (int j = 0; j < d; ++j) I.center[j] = cen.c[j];
     I.radius = R;
     I.mu2 = mu2;
-    I.cheb_tail = tail;
-    I.tail_budget = tail_budget;
-    I.drop_budget = drop_budget;
-    I.dropped_cost = acc;
-    I.err_bound = ((double)n * tail + acc) / ((double)n * std::sqrt(mu2));
-    for (int k = 0; k <= std::min(L, HDF_MAX_L); ++k) I.s_k[k] = sk[k];
-    f->S_host = S_host;
+    I.cheb_tail = dp.tail;
+    I.tail_budget = dp.tail_budget;
+    I.drop_budget = dp.drop_budget;
+    I.dropped_cost = fc.dropped;
+    I.err_bound = ((double)n * dp.tail + fc.dropped) / ((double)n * std::sqrt(mu2));
+    for (int k = 0; k <= std::min(L, HDF_MAX_L); ++k) I.s_k[k] = fc.sk[k];
+    f->S_host = fc.S;
 
     tph[3] = now_ms() - t0;
     for (int q = 0; q < 4; ++q) I.t_ms[q] = tph[q];
@@ -388,17 +277,17 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
         P.p_max = p_max;
         for (int j = 0; j < d; ++j) P.c[j] = cen.c[j];
         P.inv2R = inv2R;
-        for (int q = 0; q < 2; ++q) { P.nb[q] = nbv[q]; P.m[q] = mv[q]; P.Rf[q] = Rf[q]; P.Qmat[q] = Qmat[q]; }
-        P.Wk = Wk;
-        P.sk = sk;
+        for (int q = 0; q < 2; ++q) { P.nb[q] = fc.nb[q]; P.m[q] = fc.m[q]; P.Rf[q] = fc.Rf[q]; P.Qmat[q] = fc.Qmat[q]; }
+        P.Wk = fc.Wk;
+        P.sk = fc.sk;
     }
     hdf_status st_dev = (prec == HDF_FP64)
-        ? build_device<double>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st)
-        : build_device<float>(f, x_dev, n, d, cen, inv2R, L, Qmat, nbv, mv, Wk, sk, st);
+        ? build_device<double>(f, x_dev, n, d, cen, inv2R, dp, fc, st)
+        : build_device<float>(f, x_dev, n, d, cen, inv2R, dp, fc, st);
     if (st_dev != HDF_OK) { delete f; return st_dev; }
     I.t_ms[HDF_NPHASE - 1] = now_ms() - t_start;
     *out = f;
-    if (!reached) {
+    if (!dp.reached) {
         g_err = "hdf_build: tolerance not reached at p_max; factor built at the cap";
         return HDF_ETOL_UNREACHABLE;
     }
@@ -687,15 +576,23 @@ extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev,
 
 // ---------------------------------------------------------- device part of build
 template <typename T>
+static std::vector<T> cast_vec(const std::vector<double>& v) {
+    std::vector<T> o(v.size());
+    for (size_t q = 0; q < v.size(); ++q) o[q] = (T)v[q];
+    return o;
+}
+
+template <typename T>
 static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d, const dev::Center& cen,
-                               double inv2R, int L, const std::vector<std::vector<double>>& Qmat,
-                               const std::vector<int>& nbv, const std::vector<int>& mv,
-                               const std::vector<std::vector<double>>& Wk, const std::vector<int>& sk,
-                               cudaStream_t st) {
+                               double inv2R, const DegreePlan& dp, const FactorChoice& fc, cudaStream_t st) {
     hdf_info& I = f->info;
+    const int L = dp.L;
     const int64_t r = I.rank;
     const int vw = (sizeof(T) == 4) ? 4 : 2;
-    I.ldu = std::max<int64_t>(vw, ((r + vw - 1) / vw) * vw);
+    DeviceTables tb;
+    std::string terr;
+    if (!make_tables(fc, d, L, vw, tb, terr)) return fail(HDF_ETOOBIG, "hdf_build: " + terr);
+    I.ldu = tb.ldU;
     // S on the device
     {
         std::vector<T> Sd(I.ldu, (T)0);
@@ -709,90 +606,39 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         return fail(HDF_ENOMEM, "hdf_build: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
     }
     if (r == 0) { HDF_CUDA(cudaStreamSynchronize(st)); return HDF_OK; }
-
-    int L_used = 0;
-    for (int k = 0; k <= L; ++k) if (sk[k] > 0) L_used = k;
-    // F columns: (k, s) for kept pairs, k ascending
-    std::vector<int> fbase(L + 2, 0);
-    for (int k = 0; k <= L; ++k) fbase[k + 1] = fbase[k] + sk[k];
-    const int nF = fbase[L + 1];
-    const int mmax = std::max(mv[0], mv[1]);
-    std::vector<T> Wt((size_t)std::max(1, mmax) * nF, (T)0);
-    std::vector<uint8_t> colpar(nF);
-    for (int k = 0; k <= L; ++k)
-        for (int s = 0; s < sk[k]; ++s) {
-            const int col = fbase[k] + s, mk = mv[k % 2];
-            colpar[col] = (uint8_t)(k % 2);
-            for (int o = 0; o < mk; ++o) Wt[(size_t)o * nF + col] = (T)Wk[k][(size_t)o * sk[k] + s];
-        }
-    std::vector<uint8_t> colk(nF);
-    for (int k = 0; k <= L; ++k)
-        for (int s = 0; s < sk[k]; ++s) colk[fbase[k] + s] = (uint8_t)k;
-    // harmonic tables and chains for degrees <= L_used
+    const int L_used = tb.L_used, nF = tb.nF, mmax = tb.mmax;
+    const int64_t nH = tb.nH;
+    const std::vector<double>* Qmat = fc.Qmat;
+    const int nb0 = fc.nb[0], nb1 = fc.nb[1], m0 = fc.m[0], m1 = fc.m[1];
+    std::vector<T> Wt = cast_vec<T>(tb.Wt), cA = cast_vec<T>(tb.coefA), cB = cast_vec<T>(tb.coefB);
     HarmonicTables ht;
-    harmonic_tables(d, L_used, ht);
-    std::vector<int16_t> chains;
-    std::vector<int64_t> hbase(L + 2, 0);
-    for (int k = 0; k <= L; ++k) {
-        hbase[k + 1] = hbase[k];
-        if (sk[k] == 0) continue;
-        append_chains(k, d, L_used, chains);
-        hbase[k + 1] += ht.count[k];
-    }
-    const int64_t nH = hbase[L + 1];
-    if (nH >= (1 << 20) || nF >= 4095) return fail(HDF_ETOOBIG, "hdf_build: too many harmonics or radial columns");
-    std::vector<uint8_t> hk(nH);
-    std::vector<int> ktab(5 * (L + 1), 0);
-    std::vector<int> cbase(L + 2, 0);
-    for (int k = 0; k <= L; ++k) {
-        for (int64_t g = hbase[k]; g < hbase[k + 1]; ++g) hk[g] = (uint8_t)k;
-        const int64_t hkc = (sk[k] > 0) ? ht.count[k] : 0;
-        cbase[k + 1] = cbase[k] + (int)(hkc * sk[k]);
-        ktab[5 * k + 0] = fbase[k];
-        ktab[5 * k + 1] = sk[k];
-        ktab[5 * k + 2] = cbase[k];
-        ktab[5 * k + 3] = (int)hkc;
-        ktab[5 * k + 4] = (int)hbase[k];
-    }
-    // column descriptors
-    std::vector<uint32_t> desc(I.ldu);
-    {
-        int64_t col = 0;
-        for (int k = 0; k <= L; ++k)
-            for (int s = 0; s < sk[k]; ++s)
-                for (int64_t h = 0; h < ht.count[k] * (sk[k] > 0); ++h)
-                    desc[col++] = ((uint32_t)(fbase[k] + s) << 20) | (uint32_t)(hbase[k] + h);
-        for (; col < I.ldu; ++col) desc[col] = ((uint32_t)nF << 20);
-    }
-    std::vector<T> cA(ht.coefA.size()), cB(ht.coefB.size());
-    for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)ht.coefA[q]; cB[q] = (T)ht.coefB[q]; }
+    ht.tri = tb.tri;
 
     // upload (kept in the factor for the adjoint)
     FactorPlan& PL = f->plan;
     PL.L_used = L_used;
-    PL.tri = ht.tri;
+    PL.tri = tb.tri;
     PL.nF = nF;
     PL.nH = (int)nH;
     PL.mmax = mmax;
-    PL.fbase.assign(fbase.begin(), fbase.end());
-    PL.cbase = cbase;
-    PL.hbase.assign(hbase.begin(), hbase.end());
+    PL.fbase = tb.fbase;
+    PL.cbase = tb.cbase;
+    PL.hbase = tb.hbase;
     DevBuf dpar, dF;
     DevBuf &dQ0 = PL.dQ0, &dQ1 = PL.dQ1, &dW = PL.dW, &dchains = PL.dchains, &ddesc = PL.ddesc, &dA = PL.dA,
            &dB = PL.dB;
-    HDF_CUDA(PL.dcolk.alloc(colk.size()));
-    HDF_CUDA(PL.dhk.alloc(hk.size() + 1));
-    HDF_CUDA(PL.dktab.alloc(sizeof(int) * ktab.size()));
-    HDF_CUDA(cudaMemcpyAsync(PL.dcolk.p, colk.data(), colk.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(PL.dhk.p, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(PL.dktab.p, ktab.data(), sizeof(int) * ktab.size(), cudaMemcpyHostToDevice, st));
-    const int nb0 = nbv[0], nb1 = nbv[1], m0 = mv[0], m1 = mv[1];
+    HDF_CUDA(PL.dcolk.alloc(tb.colk.size()));
+    HDF_CUDA(PL.dhk.alloc(tb.hk.size() + 1));
+    HDF_CUDA(PL.dktab.alloc(sizeof(int) * tb.ktab.size()));
+    HDF_CUDA(cudaMemcpyAsync(PL.dcolk.p, tb.colk.data(), tb.colk.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dhk.p, tb.hk.data(), tb.hk.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dktab.p, tb.ktab.data(), sizeof(int) * tb.ktab.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(dQ0.alloc(sizeof(double) * std::max<size_t>(1, Qmat[0].size())));
     HDF_CUDA(dQ1.alloc(sizeof(double) * std::max<size_t>(1, Qmat[1].size())));
     HDF_CUDA(dW.alloc(sizeof(T) * Wt.size()));
-    HDF_CUDA(dpar.alloc(colpar.size()));
-    HDF_CUDA(dchains.alloc(sizeof(int16_t) * chains.size()));
-    HDF_CUDA(ddesc.alloc(sizeof(uint32_t) * desc.size()));
+    HDF_CUDA(dpar.alloc(tb.colpar.size()));
+    HDF_CUDA(dchains.alloc(sizeof(int16_t) * std::max<size_t>(1, tb.chains.size())));
+    HDF_CUDA(ddesc.alloc(sizeof(uint32_t) * tb.desc.size()));
     HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
     HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
     const int64_t ldF = nF;
@@ -803,9 +649,10 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     if (!Qmat[0].empty()) HDF_CUDA(cudaMemcpyAsync(dQ0.p, Qmat[0].data(), sizeof(double) * Qmat[0].size(), cudaMemcpyHostToDevice, st));
     if (!Qmat[1].empty()) HDF_CUDA(cudaMemcpyAsync(dQ1.p, Qmat[1].data(), sizeof(double) * Qmat[1].size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(dW.p, Wt.data(), sizeof(T) * Wt.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(dpar.p, colpar.data(), colpar.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(dchains.p, chains.data(), sizeof(int16_t) * chains.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(ddesc.p, desc.data(), sizeof(uint32_t) * desc.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dpar.p, tb.colpar.data(), tb.colpar.size(), cudaMemcpyHostToDevice, st));
+    if (!tb.chains.empty())
+        HDF_CUDA(cudaMemcpyAsync(dchains.p, tb.chains.data(), sizeof(int16_t) * tb.chains.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(ddesc.p, tb.desc.data(), sizeof(uint32_t) * tb.desc.size(), cudaMemcpyHostToDevice, st));
     if (!cA.empty()) {
         HDF_CUDA(cudaMemcpyAsync(dA.p, cA.data(), sizeof(T) * cA.size(), cudaMemcpyHostToDevice, st));
         HDF_CUDA(cudaMemcpyAsync(dB.p, cB.data(), sizeof(T) * cB.size(), cudaMemcpyHostToDevice, st));
@@ -817,14 +664,18 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(cudaEventRecord(ev[0], st));
     // A5a: radial factors F
     {
-        const size_t sm = sizeof(double) * (dev::kFTile * (L + 1) + dev::kFTile) + sizeof(T) * (m0 + m1) * dev::kFTile;
+        const size_t sm = dev::radialF_smem(L, m0, m1, sizeof(T));
         if (sm > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
         HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int grid = grid_for((n + dev::kFTile - 1) / dev::kFTile, 1, 152 * 8);
+        dev::RFParams R{};
+        R.x = x; R.n = n; R.d = d; R.c = cen; R.inv2R = inv2R; R.L = L;
+        R.Qm0 = dQ0.as<double>(); R.nb0 = nb0; R.m0 = m0;
+        R.Qm1 = dQ1.as<double>(); R.nb1 = nb1; R.m1 = m1;
+        R.Wt = dW.p; R.colpar = dpar.as<uint8_t>(); R.nF = nF;
+        R.F = dF.p; R.ldF = ldF;
         HDF_COUNT_LAUNCH();
-        dev::k_radial_F<T><<<grid, 256, sm, st>>>(x, n, d, cen, inv2R, L, dQ0.as<double>(), nb0, m0,
-                                                  dQ1.as<double>(), nb1, m1, dW.as<T>(), dpar.as<uint8_t>(), nF,
-                                                  dF.as<T>(), ldF);
+        dev::k_radial_F<T><<<grid, 256, sm, st>>>(R);
         HDF_CUDA(cudaGetLastError());
     }
     HDF_CUDA(cudaEventRecord(ev[1], st));
@@ -841,8 +692,8 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         const int levels = d - 2;
         const size_t fixed = sizeof(T) * 2 * levels * ht.tri;
         const size_t budget = 200 * 1024;
-        const int pw_fly = ((levels * ht.tri + 2 * L_used + 1 + nF + 1) + 3) & ~3;
-        const int pw_pre = ((levels * ht.tri + 2 * L_used + 1 + (int)nH + nF + 1) + 3) & ~3;
+        const int pw_fly = dev::uwriter_per_warp(levels, ht.tri, L_used, (int)nH, nF, false);
+        const int pw_pre = dev::uwriter_per_warp(levels, ht.tri, L_used, (int)nH, nF, true);
         const bool pre = fixed + sizeof(T) * 4 * (size_t)pw_pre <= budget;
         const int per_warp = pre ? pw_pre : pw_fly;
         P.per_warp = per_warp;

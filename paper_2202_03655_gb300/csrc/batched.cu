@@ -1,0 +1,854 @@
+// Batched factorization: many independent point sets (ragged sizes, one lengthscale each)
+// built and applied together.
+//
+// Each set is factored exactly as hdf_build would factor it on its own (Algorithm 1,
+// symmetric form); the batch changes only how the work is scheduled:
+//  * A0 and A3 (centre, radius, mean-square kernel value, radial-basis Gram) run as segmented
+//    reductions over all sets in one launch each, with per-item partials summed on the host in
+//    item order (deterministic);
+//  * A1-A2 and A4 (degree, cores, eigendecompositions, truncation, tables) run on host
+//    threads, one set per task;
+//  * A5 (radial factors and U) for all sets runs as ONE persistent kernel: each CTA pulls
+//    (set, 32-point tile) items from a device counter, computes the tile's radial factors and
+//    then its U rows;
+//  * K~V for all sets runs as persistent U^T V and U W kernels over (set, chunk, column block)
+//    and (set, row block) items, recorded once in a CUDA graph and replayed.
+// The persistent grid size (CTAs per SM) is chosen by a small autotuner that times the
+// candidates on first use and keeps the choice in a JSON cache ($HDF_AUTOTUNE_CACHE, default
+// $HOME/.cache/hdf_gb300_autotune.json).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <sys/stat.h>
+#include <vector>
+
+#include "hdf_kernels.cuh"
+#include "internal.h"
+#include "planner.h"
+
+using namespace hdf;
+
+namespace {
+
+constexpr int kMu2Sample = 512;
+constexpr int kSegChunk = 8192;      // points per reduction item
+constexpr int kGramChunk = 4096;     // points per Gram item
+
+struct SegItem {
+    int set;
+    int pad;
+    int64_t i0, i1;                  // global point range
+};
+
+struct SetGeom {                     // per set, for the segmented kernels
+    int64_t off, n;
+    double c[dev::kMaxD];
+    double inv2R;
+    int L, m;                        // degree, mu2 subsample size
+    double ell;
+};
+
+// ------------------------------------------------------------ segmented reductions
+__global__ void k_seg_sum(const double* __restrict__ x, int d, const SegItem* __restrict__ items,
+                          double* __restrict__ part) {
+    __shared__ double sh[256];
+    const SegItem it = items[blockIdx.x];
+    double acc[dev::kMaxD];
+#pragma unroll
+    for (int j = 0; j < dev::kMaxD; ++j) acc[j] = 0.0;
+    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x)
+        for (int j = 0; j < d; ++j) acc[j] += x[i * d + j];
+    for (int j = 0; j < d; ++j) {
+        const double s = dev::block_sum_256(acc[j], sh);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * d + j] = s;
+    }
+}
+
+__global__ void k_seg_maxnorm(const double* __restrict__ x, int d, const SegItem* __restrict__ items,
+                              const SetGeom* __restrict__ geo, double* __restrict__ part) {
+    __shared__ double sh[256];
+    const SegItem it = items[blockIdx.x];
+    const SetGeom& g = geo[it.set];
+    double m = 0.0;
+    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) { const double y = x[i * d + j] - g.c[j]; s += y * y; }
+        m = fmax(m, s);
+    }
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// rows: (set, t) pairs; part[row] = sum_u k(|x_idx(t) - x_idx(u)|)^2 over the set's subsample
+__global__ void k_seg_mu2(const double* __restrict__ x, int d, const int2* __restrict__ rows,
+                          const SetGeom* __restrict__ geo, int kernel, double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int2 rw = rows[blockIdx.x];
+    const SetGeom& g = geo[rw.x];
+    const int64_t i = g.off + ((int64_t)rw.y * g.n) / g.m;
+    double xi[dev::kMaxD];
+    for (int j = 0; j < d; ++j) xi[j] = x[i * d + j];
+    double acc = 0.0;
+    for (int u = threadIdx.x; u < g.m; u += blockDim.x) {
+        const int64_t jj = g.off + ((int64_t)u * g.n) / g.m;
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) { const double y = xi[j] - x[jj * d + j]; s += y * y; }
+        const double kv = dev::kernel_value(kernel, sqrt(s), g.ell);
+        acc += kv * kv;
+    }
+    const double tot = dev::block_sum_256(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Radial-basis Gram sums of one item: part[poff + q] (q < npairs) and part[poff + npairs + q].
+__global__ void __launch_bounds__(256) k_seg_gram(const double* __restrict__ x, int d,
+                                                  const SegItem* __restrict__ items,
+                                                  const int64_t* __restrict__ poff,
+                                                  const SetGeom* __restrict__ geo, double* __restrict__ part) {
+    extern __shared__ double smem[];
+    const SegItem it = items[blockIdx.x];
+    const SetGeom& g = geo[it.set];
+    const int L = g.L, LP1 = L + 1;
+    const int npairs = LP1 * (LP1 + 1) / 2;
+    double* Ts = smem;                              // [kGramTile][LP1]
+    double* r2 = smem + dev::kGramTile * LP1;
+    // this thread's pairs (l, l') in row order of the upper triangle
+    int pl[dev::kGramMaxQ], pr[dev::kGramMaxQ];
+#pragma unroll
+    for (int q = 0; q < dev::kGramMaxQ; ++q) {
+        int pi = threadIdx.x + 256 * q, l = 0;
+        pl[q] = -1;
+        pr[q] = 0;
+        if (pi < npairs) {
+            while (pi >= LP1 - l) { pi -= LP1 - l; ++l; }
+            pl[q] = l;
+            pr[q] = l + pi;
+        }
+    }
+    double a0[dev::kGramMaxQ], a1[dev::kGramMaxQ];
+#pragma unroll
+    for (int q = 0; q < dev::kGramMaxQ; ++q) { a0[q] = 0.0; a1[q] = 0.0; }
+    for (int64_t t0 = it.i0; t0 < it.i1; t0 += dev::kGramTile) {
+        const int cnt = (int)min((int64_t)dev::kGramTile, it.i1 - t0);
+        if (threadIdx.x < dev::kGramTile) {
+            const int p = threadIdx.x;
+            double* T = Ts + p * LP1;
+            if (p < cnt) {
+                const int64_t i = t0 + p;
+                double s = 0.0;
+                for (int j = 0; j < d; ++j) { const double y = (x[i * d + j] - g.c[j]) * g.inv2R; s += y * y; }
+                const double u = 8.0 * s - 1.0;
+                r2[p] = s;
+                T[0] = 1.0;
+                if (L >= 1) T[1] = u;
+                for (int l = 2; l <= L; ++l) T[l] = 2.0 * u * T[l - 1] - T[l - 2];
+            } else {
+                r2[p] = 0.0;
+                for (int l = 0; l <= L; ++l) T[l] = 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < dev::kGramMaxQ; ++q) {
+            if (pl[q] >= 0) {
+                double s0 = 0.0, s1 = 0.0;
+                for (int p = 0; p < cnt; ++p) {
+                    const double v = Ts[p * LP1 + pl[q]] * Ts[p * LP1 + pr[q]];
+                    s0 += v;
+                    s1 += v * r2[p];
+                }
+                a0[q] += s0;
+                a1[q] += s1;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < dev::kGramMaxQ; ++q) {
+        const int pi = threadIdx.x + 256 * q;
+        if (pi < npairs) {
+            part[poff[blockIdx.x] + pi] = a0[q];
+            part[poff[blockIdx.x] + npairs + pi] = a1[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------- persistent build
+struct BuildSet {
+    dev::RFParams rf;
+    dev::UWParams uw;
+    int pre;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict__ sets, const int2* __restrict__ items,
+                                                     int nitems, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const BuildSet& S = sets[w.x];
+        const int64_t t0 = (int64_t)w.y * dev::kFTile;
+        dev::radialF_tile<T>(S.rf, t0, smem_raw);           // F rows of the tile (global)
+        const int levels = S.uw.d - 2;
+        T* cA = reinterpret_cast<T*>(smem_raw);
+        T* cB = cA + levels * S.uw.tri;
+        for (int idx = threadIdx.x; idx < levels * S.uw.tri; idx += blockDim.x) {
+            cA[idx] = reinterpret_cast<const T*>(S.uw.coefA)[idx];
+            cB[idx] = reinterpret_cast<const T*>(S.uw.coefB)[idx];
+        }
+        __syncthreads();
+        T* base = cB + levels * S.uw.tri + (size_t)warp * S.uw.per_warp;
+        const int64_t t1 = min(t0 + dev::kFTile, S.uw.n);
+        for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, S.pre != 0, i, cA, cB, base, lane);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ persistent matvec
+struct MvSet {
+    const void* U; int64_t ldU, n, r, off;
+    const void* S;
+    double* part;                    // nchunk x c x r
+    void* W;                         // r x c (bulk type)
+    int64_t chunk;
+    int nchunk;
+};
+
+struct MvItem { int set, chunk; int64_t blk; };
+
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_batch_utv(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                   int nitems, int* counter, const T* __restrict__ V, int64_t ldv, int c) {
+    __shared__ __align__(16) T Us[dev::kKT][dev::UtvShape<CT>::AB];
+    __shared__ __align__(16) T Vs[dev::kKT][CT];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        const int64_t i0 = (int64_t)w.chunk * S.chunk, i1 = min(S.n, i0 + S.chunk);
+        dev::utv_tile_body<T, CT>(reinterpret_cast<const T*>(S.U), S.ldU, S.r, V + S.off, ldv, c, i0, i1,
+                                  w.blk * dev::UtvShape<CT>::AB, S.part + (int64_t)w.chunk * c * S.r, Us, Vs);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_batch_reduce(const MvSet* __restrict__ sets, const MvItem* __restrict__ items, int c) {
+    const MvItem w = items[blockIdx.x];
+    const MvSet& S = sets[w.set];
+    const int64_t a = w.blk * 256 + threadIdx.x;
+    if (a >= S.r) return;
+    const T* Sv = reinterpret_cast<const T*>(S.S);
+    T* W = reinterpret_cast<T*>(S.W);
+    for (int j = 0; j < c; ++j) {
+        double s = 0.0;
+        for (int b = 0; b < S.nchunk; ++b) s += S.part[((int64_t)b * c + j) * S.r + a];
+        W[a * c + j] = (T)(s * (double)Sv[a]);
+    }
+}
+
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_batch_uw(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                  int nitems, int* counter, T* __restrict__ Y, int64_t ldy, int c) {
+    __shared__ __align__(16) T Us[dev::kKT][dev::UwShape<CT>::RB + dev::kUwPad];
+    __shared__ __align__(16) T Ws[dev::kKT][CT];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        dev::uw_tile_body<T, CT>(reinterpret_cast<const T*>(S.U), S.ldU, S.n, S.r, reinterpret_cast<const T*>(S.W), c,
+                                 (T)1, nullptr, 0, (T)0, Y + S.off, ldy, w.blk * dev::UwShape<CT>::RB, Us, Ws);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ autotuner
+std::mutex g_tune_mu;
+
+std::string tune_path() {
+    if (const char* p = std::getenv("HDF_AUTOTUNE_CACHE")) return p;
+    const char* home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/hdf_gb300_autotune.json";
+}
+
+// Minimal JSON object of "key": integer pairs.
+std::map<std::string, int> tune_load() {
+    std::map<std::string, int> m;
+    std::ifstream in(tune_path());
+    if (!in) return m;
+    std::stringstream ss;
+    ss << in.rdbuf();
+    const std::string s = ss.str();
+    size_t pos = 0;
+    while ((pos = s.find('"', pos)) != std::string::npos) {
+        const size_t e = s.find('"', pos + 1);
+        if (e == std::string::npos) break;
+        const std::string key = s.substr(pos + 1, e - pos - 1);
+        const size_t colon = s.find(':', e);
+        if (colon == std::string::npos) break;
+        m[key] = std::atoi(s.c_str() + colon + 1);
+        pos = colon + 1;
+    }
+    return m;
+}
+
+void tune_store(const std::map<std::string, int>& m) {
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) mkdir(path.substr(0, slash).c_str(), 0755);   // one level, errors ignored
+    std::ofstream out(path);
+    if (!out) return;
+    out << "{";
+    bool first = true;
+    for (const auto& kv : m) {
+        out << (first ? "" : ", ") << "\"" << kv.first << "\": " << kv.second;
+        first = false;
+    }
+    out << "}\n";
+}
+
+int ct_for(int c) { return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : c <= 8 ? 8 : c <= 16 ? 16 : c <= 32 ? 32 : 64; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ batch object
+struct hdf_batch {
+    int nsets = 0, d = 0, prec = 0, kernel = 0;
+    double tol = 0.0;
+    size_t esz = 8;
+    std::vector<int64_t> off;                       // nsets + 1
+    std::vector<hdf_info> info;
+    std::vector<std::vector<double>> S_host;
+    std::vector<int64_t> uoff, soff;                // element offsets of U and S per set
+    DevBuf U, S, arena, dsets;
+    // matvec state
+    DevBuf mvsets, mvitems_utv, mvitems_red, mvitems_uw, mvpart, mvW, counters;
+    int mv_c = 0, n_utv = 0, n_red = 0, n_uw = 0;
+    cudaGraphExec_t mv_exec = nullptr;
+    const void* mv_V = nullptr;
+    void* mv_Y = nullptr;
+    int64_t mv_ldv = 0, mv_ldy = 0;
+    cudaStream_t cap = nullptr;
+    double t_ms[HDF_NPHASE] = {};
+    int grid_build = 0;
+    ~hdf_batch() {
+        if (mv_exec) cudaGraphExecDestroy(mv_exec);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+static double now_ms_b() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector<double>& ells, double tol, double eta,
+                                int p_max, cudaStream_t st, bool* all_reached) {
+    const int ns = b->nsets, d = b->d;
+    const double t_start = now_ms_b();
+    std::vector<SetGeom> geo(ns);
+    for (int s = 0; s < ns; ++s) {
+        geo[s].off = b->off[s];
+        geo[s].n = b->off[s + 1] - b->off[s];
+        geo[s].ell = ells[s];
+        geo[s].m = (int)std::min<int64_t>(geo[s].n, kMu2Sample);
+    }
+    // ---- A0: segmented centre, radius, mu2
+    std::vector<SegItem> items;
+    for (int s = 0; s < ns; ++s)
+        for (int64_t i0 = 0; i0 < geo[s].n; i0 += kSegChunk)
+            items.push_back({s, 0, geo[s].off + i0, geo[s].off + std::min<int64_t>(geo[s].n, i0 + kSegChunk)});
+    const int nit = (int)items.size();
+    std::vector<int2> mrows;
+    for (int s = 0; s < ns; ++s)
+        for (int t = 0; t < geo[s].m; ++t) mrows.push_back(make_int2(s, t));
+    DevBuf ditems, dgeo, dpart, drows;
+    HDF_CUDA(ditems.alloc(sizeof(SegItem) * nit));
+    HDF_CUDA(dgeo.alloc(sizeof(SetGeom) * ns));
+    HDF_CUDA(drows.alloc(sizeof(int2) * mrows.size()));
+    HDF_CUDA(dpart.alloc(sizeof(double) * std::max<size_t>((size_t)nit * d, mrows.size())));
+    HDF_CUDA(cudaMemcpyAsync(ditems.p, items.data(), sizeof(SegItem) * nit, cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(drows.p, mrows.data(), sizeof(int2) * mrows.size(), cudaMemcpyHostToDevice, st));
+    HDF_COUNT_LAUNCH();
+    k_seg_sum<<<nit, 256, 0, st>>>(x, d, ditems.as<SegItem>(), dpart.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)nit * d);
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), dpart.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    {
+        std::vector<std::vector<double>> sums(ns, std::vector<double>(d, 0.0));
+        for (int q = 0; q < nit; ++q)
+            for (int j = 0; j < d; ++j) sums[items[q].set][j] += hp[(size_t)q * d + j];
+        for (int s = 0; s < ns; ++s)
+            for (int j = 0; j < d; ++j) {
+                geo[s].c[j] = sums[s][j] / (double)geo[s].n;
+                if (!std::isfinite(geo[s].c[j])) return fail(HDF_ENOTFINITE, "hdf_build_batched: non-finite points");
+            }
+    }
+    HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
+    HDF_COUNT_LAUNCH();
+    k_seg_maxnorm<<<nit, 256, 0, st>>>(x, d, ditems.as<SegItem>(), dgeo.as<SetGeom>(), dpart.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), dpart.p, sizeof(double) * nit, cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> Rs(ns, 0.0);
+    for (int q = 0; q < nit; ++q) Rs[items[q].set] = std::max(Rs[items[q].set], hp[q]);
+    for (int s = 0; s < ns; ++s) {
+        Rs[s] = std::sqrt(Rs[s]);
+        if (!std::isfinite(Rs[s])) return fail(HDF_ENOTFINITE, "hdf_build_batched: non-finite points");
+        if (Rs[s] == 0.0) Rs[s] = 1.0;
+        geo[s].inv2R = 1.0 / (2.0 * Rs[s]);
+    }
+    HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
+    HDF_COUNT_LAUNCH();
+    k_seg_mu2<<<(unsigned)mrows.size(), 256, 0, st>>>(x, d, drows.as<int2>(), dgeo.as<SetGeom>(), b->kernel,
+                                                     dpart.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> mp(mrows.size());
+    HDF_CUDA(cudaMemcpyAsync(mp.data(), dpart.p, sizeof(double) * mp.size(), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> mu2(ns, 0.0);
+    for (size_t q = 0; q < mrows.size(); ++q) mu2[mrows[q].x] += mp[q];
+    for (int s = 0; s < ns; ++s) mu2[s] /= (double)geo[s].m * (double)geo[s].m;
+    b->t_ms[0] = now_ms_b() - t_start;
+
+    // ---- A1-A2 per set on host threads
+    double t0 = now_ms_b();
+    std::vector<DegreePlan> dps(ns);
+    parallel_for(ns, [&](int s) {
+        plan_degree(b->kernel, ells[s], Rs[s], mu2[s], geo[s].n, tol, eta, p_max, d, false, dps[s]);
+    });
+    for (int s = 0; s < ns; ++s) geo[s].L = dps[s].L;
+    b->t_ms[1] = now_ms_b() - t0;
+
+    // ---- A3: segmented radial-basis Gram
+    t0 = now_ms_b();
+    std::vector<SegItem> gitems;
+    std::vector<int64_t> gpoff;
+    int64_t gtot = 0;
+    for (int s = 0; s < ns; ++s) {
+        const int LP1 = geo[s].L + 1, npairs = LP1 * (LP1 + 1) / 2;
+        for (int64_t i0 = 0; i0 < geo[s].n; i0 += kGramChunk) {
+            gitems.push_back({s, 0, geo[s].off + i0, geo[s].off + std::min<int64_t>(geo[s].n, i0 + kGramChunk)});
+            gpoff.push_back(gtot);
+            gtot += 2 * npairs;
+        }
+    }
+    int Lmax = 0;
+    for (int s = 0; s < ns; ++s) Lmax = std::max(Lmax, geo[s].L);
+    DevBuf dgi, dgpoff, dgpart;
+    HDF_CUDA(dgi.alloc(sizeof(SegItem) * gitems.size()));
+    HDF_CUDA(dgpoff.alloc(sizeof(int64_t) * gpoff.size()));
+    HDF_CUDA(dgpart.alloc(sizeof(double) * gtot));
+    HDF_CUDA(cudaMemcpyAsync(dgi.p, gitems.data(), sizeof(SegItem) * gitems.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dgpoff.p, gpoff.data(), sizeof(int64_t) * gpoff.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
+    const size_t gsm = sizeof(double) * (dev::kGramTile * (Lmax + 1) + dev::kGramTile);
+    HDF_CUDA(cudaFuncSetAttribute(k_seg_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    HDF_COUNT_LAUNCH();
+    k_seg_gram<<<(unsigned)gitems.size(), 256, gsm, st>>>(x, d, dgi.as<SegItem>(), dgpoff.as<int64_t>(),
+                                                           dgeo.as<SetGeom>(), dgpart.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> gp(gtot);
+    HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<std::vector<double>> grams(ns);
+    for (int s = 0; s < ns; ++s) {
+        const int LP1 = geo[s].L + 1;
+        grams[s].assign(LP1 * (LP1 + 1), 0.0);
+    }
+    for (size_t q = 0; q < gitems.size(); ++q) {
+        std::vector<double>& G = grams[gitems[q].set];
+        for (size_t e = 0; e < G.size(); ++e) G[e] += gp[gpoff[q] + e];
+    }
+    b->t_ms[2] = now_ms_b() - t0;
+
+    // ---- A3-A4 per set on host threads, tables
+    t0 = now_ms_b();
+    const int vw = (sizeof(T) == 4) ? 4 : 2;
+    std::vector<FactorChoice> fcs(ns);
+    std::vector<DeviceTables> tbs(ns);
+    std::vector<std::string> errs(ns);
+    std::vector<char> ok(ns, 1);
+    parallel_for(ns, [&](int s) {
+        plan_factor(grams[s], geo[s].L, d, dps[s].cores, dps[s].drop_budget, false, fcs[s]);
+        ok[s] = make_tables(fcs[s], d, geo[s].L, vw, tbs[s], errs[s]) ? 1 : 0;
+    });
+    for (int s = 0; s < ns; ++s)
+        if (!ok[s]) return fail(HDF_ETOOBIG, "hdf_build_batched: set " + std::to_string(s) + ": " + errs[s]);
+    *all_reached = true;
+    b->info.assign(ns, hdf_info{});
+    b->S_host.assign(ns, std::vector<double>());
+    b->uoff.assign(ns + 1, 0);
+    b->soff.assign(ns + 1, 0);
+    std::vector<int64_t> foff(ns + 1, 0);
+    for (int s = 0; s < ns; ++s) {
+        hdf_info& I = b->info[s];
+        const DegreePlan& dp = dps[s];
+        const FactorChoice& fc = fcs[s];
+        I.n = geo[s].n; I.d = d; I.precision = b->prec; I.p = dp.p; I.L = dp.L;
+        I.reached = dp.reached ? 1 : 0;
+        if (!dp.reached) *all_reached = false;
+        I.rank = fc.rank; I.ldu = tbs[s].ldU; I.nharm = fc.nH;
+        for (int j = 0; j < d; ++j) I.center[j] = geo[s].c[j];
+        I.radius = Rs[s]; I.mu2 = mu2[s]; I.cheb_tail = dp.tail; I.tail_budget = dp.tail_budget;
+        I.drop_budget = dp.drop_budget; I.dropped_cost = fc.dropped;
+        I.err_bound = ((double)geo[s].n * dp.tail + fc.dropped) / ((double)geo[s].n * std::sqrt(mu2[s]));
+        for (int k = 0; k <= std::min(dp.L, HDF_MAX_L); ++k) I.s_k[k] = fc.sk[k];
+        b->S_host[s] = fc.S;
+        b->uoff[s + 1] = b->uoff[s] + geo[s].n * tbs[s].ldU;
+        b->soff[s + 1] = b->soff[s] + tbs[s].ldU;
+        foff[s + 1] = foff[s] + geo[s].n * std::max(1, tbs[s].nF);
+    }
+    // arena of per-set tables: each piece 256-byte aligned
+    std::vector<unsigned char> arena;
+    auto put = [&](const void* src, size_t bytes) -> size_t {
+        size_t o = (arena.size() + 255) & ~size_t(255);
+        arena.resize(o + std::max<size_t>(bytes, 16));
+        if (bytes) std::memcpy(arena.data() + o, src, bytes);
+        return o;
+    };
+    struct Offs { size_t q0, q1, w, par, ch, desc, ca, cb; };
+    std::vector<Offs> offs(ns);
+    std::vector<T> Sd(b->soff[ns], (T)0);
+    for (int s = 0; s < ns; ++s) {
+        const DeviceTables& tb = tbs[s];
+        const FactorChoice& fc = fcs[s];
+        std::vector<T> Wt(tb.Wt.size()), cA(tb.coefA.size()), cB(tb.coefB.size());
+        for (size_t q = 0; q < Wt.size(); ++q) Wt[q] = (T)tb.Wt[q];
+        for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)tb.coefA[q]; cB[q] = (T)tb.coefB[q]; }
+        offs[s].q0 = put(fc.Qmat[0].data(), sizeof(double) * fc.Qmat[0].size());
+        offs[s].q1 = put(fc.Qmat[1].data(), sizeof(double) * fc.Qmat[1].size());
+        offs[s].w = put(Wt.data(), sizeof(T) * Wt.size());
+        offs[s].par = put(tb.colpar.data(), tb.colpar.size());
+        offs[s].ch = put(tb.chains.data(), sizeof(int16_t) * tb.chains.size());
+        offs[s].desc = put(tb.desc.data(), sizeof(uint32_t) * tb.desc.size());
+        offs[s].ca = put(cA.data(), sizeof(T) * cA.size());
+        offs[s].cb = put(cB.data(), sizeof(T) * cB.size());
+        for (int64_t a = 0; a < fc.rank; ++a) Sd[b->soff[s] + a] = (T)fc.S[a];
+    }
+    HDF_CUDA(b->arena.alloc(arena.size()));
+    HDF_CUDA(cudaMemcpyAsync(b->arena.p, arena.data(), arena.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(b->S.alloc(sizeof(T) * std::max<int64_t>(1, b->soff[ns])));
+    HDF_CUDA(cudaMemcpyAsync(b->S.p, Sd.data(), sizeof(T) * Sd.size(), cudaMemcpyHostToDevice, st));
+    const size_t ubytes = sizeof(T) * (size_t)std::max<int64_t>(1, b->uoff[ns]);
+    if (b->U.alloc(ubytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HDF_ENOMEM, "hdf_build_batched: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
+    }
+    DevBuf dF;
+    if (dF.alloc(sizeof(T) * (size_t)std::max<int64_t>(1, foff[ns])) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HDF_ENOMEM, "hdf_build_batched: cannot allocate the radial factor buffer");
+    }
+    // set descriptors, shared memory need, items
+    const size_t budget = 200 * 1024;
+    std::vector<BuildSet> bs(ns);
+    std::vector<int2> bitems;
+    size_t smem = 0;
+    unsigned char* A = b->arena.as<unsigned char>();
+    for (int s = 0; s < ns; ++s) {
+        const DeviceTables& tb = tbs[s];
+        const FactorChoice& fc = fcs[s];
+        if (fc.rank == 0) continue;
+        dev::RFParams& R = bs[s].rf;
+        R.x = x + geo[s].off * d; R.n = geo[s].n; R.d = d;
+        for (int j = 0; j < d; ++j) R.c.c[j] = geo[s].c[j];
+        R.inv2R = geo[s].inv2R; R.L = geo[s].L;
+        R.Qm0 = reinterpret_cast<const double*>(A + offs[s].q0); R.nb0 = fc.nb[0]; R.m0 = fc.m[0];
+        R.Qm1 = reinterpret_cast<const double*>(A + offs[s].q1); R.nb1 = fc.nb[1]; R.m1 = fc.m[1];
+        R.Wt = A + offs[s].w; R.colpar = A + offs[s].par; R.nF = tb.nF;
+        R.F = dF.as<T>() + foff[s]; R.ldF = tb.nF;
+        dev::UWParams& P = bs[s].uw;
+        P.x = R.x; P.n = R.n; P.d = d; P.c = R.c; P.inv2R = R.inv2R;
+        P.L = tb.L_used; P.tri = tb.tri;
+        P.chains = reinterpret_cast<const int16_t*>(A + offs[s].ch); P.nH = tb.nH;
+        P.desc = reinterpret_cast<const uint32_t*>(A + offs[s].desc); P.nF = tb.nF;
+        P.F = R.F; P.ldF = R.ldF;
+        P.U = b->U.as<T>() + b->uoff[s]; P.ldU = tb.ldU;
+        P.coefA = A + offs[s].ca; P.coefB = A + offs[s].cb;
+        const int levels = d - 2;
+        const size_t fixed = sizeof(T) * 2 * levels * tb.tri;
+        const int pw_pre = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nH, tb.nF, true);
+        const int pw_fly = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nH, tb.nF, false);
+        const bool pre = fixed + sizeof(T) * 8 * (size_t)pw_pre <= budget / 2;
+        bs[s].pre = pre ? 1 : 0;
+        P.per_warp = pre ? pw_pre : pw_fly;
+        const size_t need_uw = fixed + sizeof(T) * 8 * (size_t)P.per_warp;
+        const size_t need_rf = dev::radialF_smem(geo[s].L, fc.m[0], fc.m[1], sizeof(T));
+        smem = std::max(smem, std::max(need_uw, need_rf));
+        const int64_t ntile = (geo[s].n + dev::kFTile - 1) / dev::kFTile;
+        for (int64_t t = 0; t < ntile; ++t) bitems.push_back(make_int2(s, (int)t));
+    }
+    if (smem > budget) return fail(HDF_ETOOBIG, "hdf_build_batched: per-set tables exceed shared memory");
+    HDF_CUDA(b->dsets.alloc(sizeof(BuildSet) * ns));
+    HDF_CUDA(cudaMemcpyAsync(b->dsets.p, bs.data(), sizeof(BuildSet) * ns, cudaMemcpyHostToDevice, st));
+    DevBuf ditb, dcnt;
+    HDF_CUDA(ditb.alloc(sizeof(int2) * std::max<size_t>(1, bitems.size())));
+    HDF_CUDA(dcnt.alloc(sizeof(int)));
+    if (!bitems.empty())
+        HDF_CUDA(cudaMemcpyAsync(ditb.p, bitems.data(), sizeof(int2) * bitems.size(), cudaMemcpyHostToDevice, st));
+    b->t_ms[3] = now_ms_b() - t0;
+
+    // ---- A5: one persistent launch for radial factors and U of every set
+    HDF_CUDA(cudaFuncSetAttribute(k_batch_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nsm = 0, dv = 0, occ = 0;
+    HDF_CUDA(cudaGetDevice(&dv));
+    HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_build<T>, 256, smem));
+    occ = std::max(occ, 1);
+    const int nitems_b = (int)bitems.size();
+    auto launch = [&](int per_sm) -> hdf_status {
+        HDF_CUDA(cudaMemsetAsync(dcnt.p, 0, sizeof(int), st));
+        HDF_COUNT_LAUNCH();
+        k_batch_build<T><<<nsm * per_sm, 256, smem, st>>>(b->dsets.as<BuildSet>(), ditb.as<int2>(), nitems_b,
+                                                           dcnt.as<int>());
+        HDF_CUDA(cudaGetLastError());
+        return HDF_OK;
+    };
+    // autotune the CTAs per SM of the persistent grid (cached per device, d and precision)
+    char key[96];
+    std::snprintf(key, sizeof(key), "batch_build:sm%d:d%d:%s:occ%d", nsm, d, sizeof(T) == 4 ? "fp32" : "fp64", occ);
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto m = tune_load();
+        auto itk = m.find(key);
+        if (itk != m.end() && itk->second >= 1 && itk->second <= occ) best = itk->second;
+    }
+    cudaEvent_t e0, e1;
+    HDF_CUDA(cudaEventCreate(&e0));
+    HDF_CUDA(cudaEventCreate(&e1));
+    if (best == 0 && nitems_b > 0) {
+        float best_ms = 1e30f;
+        for (int per_sm = 1; per_sm <= occ; ++per_sm) {
+            HDF_CUDA(cudaEventRecord(e0, st));
+            hdf_status s = launch(per_sm);
+            if (s != HDF_OK) return s;
+            HDF_CUDA(cudaEventRecord(e1, st));
+            HDF_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            HDF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) { best_ms = ms; best = per_sm; }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto m = tune_load();
+        m[key] = best;
+        tune_store(m);
+    }
+    if (best == 0) best = occ;
+    b->grid_build = nsm * best;
+    HDF_CUDA(cudaEventRecord(e0, st));
+    if (nitems_b > 0) {
+        hdf_status s = launch(best);
+        if (s != HDF_OK) return s;
+    }
+    HDF_CUDA(cudaEventRecord(e1, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    HDF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->t_ms[5] = ms;
+    b->t_ms[HDF_NPHASE - 1] = now_ms_b() - t_start;
+    return HDF_OK;
+}
+
+template <typename T>
+static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T* Y, int64_t ldy, cudaStream_t st) {
+    const int ns = b->nsets;
+    if (c != b->mv_c) {
+        // work space and items for this column count
+        if (b->mv_exec) { cudaGraphExecDestroy(b->mv_exec); b->mv_exec = nullptr; }
+        std::vector<MvSet> ms(ns);
+        std::vector<MvItem> iu, ir, iw;
+        const int ct = ct_for(c);
+        const int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
+        int64_t ptot = 0, wtot = 0;
+        std::vector<int64_t> poff(ns), woff(ns);
+        for (int s = 0; s < ns; ++s) {
+            const int64_t n = b->info[s].n, r = b->info[s].rank;
+            ms[s].n = n; ms[s].r = r; ms[s].ldU = b->info[s].ldu; ms[s].off = b->off[s];
+            ms[s].chunk = 4096;
+            ms[s].nchunk = (int)std::max<int64_t>(1, (n + ms[s].chunk - 1) / ms[s].chunk);
+            poff[s] = ptot;
+            ptot += (int64_t)ms[s].nchunk * c * std::max<int64_t>(1, r);
+            woff[s] = wtot;
+            wtot += std::max<int64_t>(1, r) * c;
+            if (r == 0) continue;
+            for (int q = 0; q < ms[s].nchunk; ++q)
+                for (int64_t bl = 0; bl < (r + AB - 1) / AB; ++bl) iu.push_back({s, q, bl});
+            for (int64_t bl = 0; bl < (r + 255) / 256; ++bl) ir.push_back({s, 0, bl});
+            for (int64_t bl = 0; bl < (n + RB - 1) / RB; ++bl) iw.push_back({s, 0, bl});
+        }
+        HDF_CUDA(b->mvpart.alloc(sizeof(double) * std::max<int64_t>(1, ptot)));
+        HDF_CUDA(b->mvW.alloc(sizeof(T) * std::max<int64_t>(1, wtot)));
+        for (int s = 0; s < ns; ++s) {
+            ms[s].U = b->U.as<T>() + b->uoff[s];
+            ms[s].S = b->S.as<T>() + b->soff[s];
+            ms[s].part = b->mvpart.as<double>() + poff[s];
+            ms[s].W = b->mvW.as<T>() + woff[s];
+        }
+        HDF_CUDA(b->mvsets.alloc(sizeof(MvSet) * ns));
+        HDF_CUDA(b->mvitems_utv.alloc(sizeof(MvItem) * std::max<size_t>(1, iu.size())));
+        HDF_CUDA(b->mvitems_red.alloc(sizeof(MvItem) * std::max<size_t>(1, ir.size())));
+        HDF_CUDA(b->mvitems_uw.alloc(sizeof(MvItem) * std::max<size_t>(1, iw.size())));
+        HDF_CUDA(b->counters.alloc(sizeof(int) * 2));
+        HDF_CUDA(cudaMemcpyAsync(b->mvsets.p, ms.data(), sizeof(MvSet) * ns, cudaMemcpyHostToDevice, st));
+        if (!iu.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_utv.p, iu.data(), sizeof(MvItem) * iu.size(), cudaMemcpyHostToDevice, st));
+        if (!ir.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_red.p, ir.data(), sizeof(MvItem) * ir.size(), cudaMemcpyHostToDevice, st));
+        if (!iw.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_uw.p, iw.data(), sizeof(MvItem) * iw.size(), cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+        b->n_utv = (int)iu.size();
+        b->n_red = (int)ir.size();
+        b->n_uw = (int)iw.size();
+        b->mv_c = c;
+    }
+    if (!b->mv_exec || b->mv_V != (const void*)V || b->mv_Y != (void*)Y || b->mv_ldv != ldv || b->mv_ldy != ldy) {
+        if (b->mv_exec) { cudaGraphExecDestroy(b->mv_exec); b->mv_exec = nullptr; }
+        if (!b->cap) HDF_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        int nsm = 0, dv = 0;
+        HDF_CUDA(cudaGetDevice(&dv));
+        HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+        const int ct = ct_for(c);
+        HDF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(b->counters.p, 0, sizeof(int) * 2, b->cap);
+        const MvSet* S = b->mvsets.as<MvSet>();
+        int* cnt = b->counters.as<int>();
+#define HDF_B_MV(CT)                                                                                              \
+    case CT:                                                                                                      \
+        if (b->n_utv) k_batch_utv<T, CT><<<nsm * 3, 256, 0, b->cap>>>(S, b->mvitems_utv.as<MvItem>(), b->n_utv,   \
+                                                                        cnt, V, ldv, c);                          \
+        if (b->n_red) k_batch_reduce<T><<<b->n_red, 256, 0, b->cap>>>(S, b->mvitems_red.as<MvItem>(), c);          \
+        if (b->n_uw) k_batch_uw<T, CT><<<nsm * 3, 256, 0, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw,       \
+                                                                      cnt + 1, Y, ldy, c);                        \
+        break;
+        switch (ct) { HDF_B_MV(1) HDF_B_MV(2) HDF_B_MV(4) HDF_B_MV(8) HDF_B_MV(16) HDF_B_MV(32) HDF_B_MV(64) }
+#undef HDF_B_MV
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+        if (ce != cudaSuccess) return fail(HDF_ECUDA, std::string("hdf_batch_matvec: capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->mv_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(HDF_ECUDA, std::string("hdf_batch_matvec: instantiate: ") + cudaGetErrorString(ce));
+        b->mv_V = V; b->mv_Y = Y; b->mv_ldv = ldv; b->mv_ldy = ldy;
+    }
+    hdf::g_launches.fetch_add((b->n_utv ? 1 : 0) + (b->n_red ? 1 : 0) + (b->n_uw ? 1 : 0), std::memory_order_relaxed);
+    HDF_CUDA(cudaGraphLaunch(b->mv_exec, st));
+    return HDF_OK;
+}
+
+extern "C" {
+
+hdf_status hdf_build_batched(int nsets, const int64_t* offsets, const double* x_dev, int d, hdf_kernel kernel,
+                             const double* lengthscales, double tol, hdf_precision prec, const hdf_options* opt,
+                             hdf_stream stream, hdf_batch** out) {
+    if (out) *out = nullptr;
+    if (!out || !offsets || !x_dev || !lengthscales || nsets < 1 || d < 3 || d > HDF_MAX_D || kernel < 0 ||
+        kernel > 3 || !(tol > 0 && tol < 1) || (prec != HDF_FP64 && prec != HDF_FP32))
+        return fail(HDF_EINVAL, "hdf_build_batched: bad argument");
+    if (offsets[0] != 0) return fail(HDF_EINVAL, "hdf_build_batched: offsets[0] must be 0");
+    for (int s = 0; s < nsets; ++s) {
+        if (offsets[s + 1] <= offsets[s]) return fail(HDF_EINVAL, "hdf_build_batched: every set needs >= 1 point");
+        if (!(lengthscales[s] > 0)) return fail(HDF_EINVAL, "hdf_build_batched: lengthscales must be > 0");
+    }
+    int p_max = 64;
+    double eta = 1.0;
+    if (opt) {
+        if (opt->p_max > 0) p_max = opt->p_max;
+        if (opt->eta > 0) eta = opt->eta;
+    }
+    if (p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, "hdf_build_batched: p_max > 128");
+    p_max -= p_max % 2;
+    hdf_batch* b = new hdf_batch();
+    b->nsets = nsets;
+    b->d = d;
+    b->prec = prec;
+    b->kernel = kernel;
+    b->tol = tol;
+    b->esz = (prec == HDF_FP64) ? 8 : 4;
+    b->off.assign(offsets, offsets + nsets + 1);
+    std::vector<double> ells(lengthscales, lengthscales + nsets);
+    bool reached = true;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const hdf_status s = (prec == HDF_FP64) ? batch_build_t<double>(b, x_dev, ells, tol, eta, p_max, st, &reached)
+                                             : batch_build_t<float>(b, x_dev, ells, tol, eta, p_max, st, &reached);
+    if (s != HDF_OK) { delete b; return s; }
+    *out = b;
+    if (!reached) {
+        fail(HDF_ETOL_UNREACHABLE, "hdf_build_batched: some sets were capped at p_max");
+        return HDF_ETOL_UNREACHABLE;
+    }
+    return HDF_OK;
+}
+
+hdf_status hdf_batch_info(const hdf_batch* b, int set, hdf_info* info) {
+    if (!b || !info || set < 0 || set >= b->nsets) return fail(HDF_EINVAL, "hdf_batch_info: bad argument");
+    *info = b->info[set];
+    return HDF_OK;
+}
+
+hdf_status hdf_batch_timings(const hdf_batch* b, double* t_ms) {
+    if (!b || !t_ms) return fail(HDF_EINVAL, "hdf_batch_timings: bad argument");
+    for (int q = 0; q < HDF_NPHASE; ++q) t_ms[q] = b->t_ms[q];
+    return HDF_OK;
+}
+
+hdf_status hdf_batch_matvec(hdf_batch* b, const void* V_dev, int64_t ldv, int ncols, void* Y_dev, int64_t ldy,
+                            hdf_stream stream) {
+    const int64_t ntot = b ? b->off[b->nsets] : 0;
+    if (!b || !V_dev || !Y_dev || ncols < 1 || ncols > 64 || ldv < ntot || ldy < ntot)
+        return fail(HDF_EINVAL, "hdf_batch_matvec: bad argument (1 <= ncols <= 64)");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (b->prec == HDF_FP64)
+        return batch_matvec_t<double>(b, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy, st);
+    return batch_matvec_t<float>(b, (const float*)V_dev, ldv, ncols, (float*)Y_dev, ldy, st);
+}
+
+hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S_host) {
+    if (!b || set < 0 || set >= b->nsets) return fail(HDF_EINVAL, "hdf_batch_export: bad argument");
+    const hdf_info& I = b->info[set];
+    if (U_host && I.rank > 0) {
+        const unsigned char* src = b->U.as<unsigned char>() + b->uoff[set] * b->esz;
+        HDF_CUDA(cudaMemcpy2D(U_host, I.rank * b->esz, src, I.ldu * b->esz, I.rank * b->esz, I.n,
+                              cudaMemcpyDeviceToHost));
+    }
+    if (S_host && I.rank > 0) std::memcpy(S_host, b->S_host[set].data(), sizeof(double) * I.rank);
+    return HDF_OK;
+}
+
+void hdf_batch_free(hdf_batch* b) { delete b; }
+
+}  // extern "C"

@@ -183,67 +183,83 @@ static __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, 
 // of Eq. svd) -> F[i, col] = sum_l Q_par(col)[l] Wt[l, col] (type T).  Tiles of 32 points.
 constexpr int kFTile = 32;
 
+struct RFParams {
+    const double* x; int64_t n; int d; Center c; double inv2R; int L;
+    const double* Qm0; int nb0, m0;
+    const double* Qm1; int nb1, m1;
+    const void* Wt; const uint8_t* colpar; int nF;
+    void* F; int64_t ldF;
+};
+
+// Dynamic shared memory of one radial tile, in bytes.
+__host__ __device__ inline size_t radialF_smem(int L, int m0, int m1, size_t tsize) {
+    return sizeof(double) * (kFTile * (L + 1) + kFTile) + tsize * (size_t)(m0 + m1) * kFTile;
+}
+
+// Radial factors of the points [t0, t0 + kFTile): block-wide, ends with a barrier.
 template <typename T>
-__global__ void __launch_bounds__(256) k_radial_F(
-    const double* __restrict__ x, int64_t n, int d, Center c, double inv2R, int L,
-    const double* __restrict__ Qm0, int nb0, int m0, const double* __restrict__ Qm1, int nb1, int m1,
-    const T* __restrict__ Wt, const uint8_t* __restrict__ colpar, int nF,
-    T* __restrict__ F, int64_t ldF) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LP1 = L + 1;
+__device__ __forceinline__ void radialF_tile(const RFParams& P, int64_t t0, unsigned char* smem_raw) {
+    const int LP1 = P.L + 1;
     double* Ts = reinterpret_cast<double*>(smem_raw);            // [kFTile][LP1]
     double* rh = Ts + kFTile * LP1;                              // [kFTile]
     T* Qs = reinterpret_cast<T*>(rh + kFTile);                   // [m0 + m1][kFTile]
-    const int64_t ntiles = (n + kFTile - 1) / kFTile;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t t0 = tile * kFTile;
-        const int cnt = (int)min((int64_t)kFTile, n - t0);
-        if (threadIdx.x < kFTile) {
-            const int p = threadIdx.x;
-            double* Tp = Ts + p * LP1;
-            double s = 0.0;
-            if (p < cnt) {
-                const int64_t i = t0 + p;
-                for (int j = 0; j < d; ++j) { const double y = (x[i * d + j] - c.c[j]) * inv2R; s += y * y; }
-            }
-            const double u = 8.0 * s - 1.0;
-            rh[p] = sqrt(s);
-            Tp[0] = 1.0;
-            if (L >= 1) Tp[1] = u;
-            for (int l = 2; l <= L; ++l) Tp[l] = 2.0 * u * Tp[l - 1] - Tp[l - 2];
+    const T* Wt = reinterpret_cast<const T*>(P.Wt);
+    T* F = reinterpret_cast<T*>(P.F);
+    const int cnt = (int)min((int64_t)kFTile, P.n - t0);
+    if (threadIdx.x < kFTile) {
+        const int p = threadIdx.x;
+        double* Tp = Ts + p * LP1;
+        double s = 0.0;
+        if (p < cnt) {
+            const int64_t i = t0 + p;
+            for (int j = 0; j < P.d; ++j) { const double y = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R; s += y * y; }
         }
-        __syncthreads();
-        const int mt = m0 + m1;
-        for (int idx = threadIdx.x; idx < mt * kFTile; idx += blockDim.x) {
-            const int o = idx / kFTile, p = idx % kFTile;
-            const double* Tp = Ts + p * LP1;
-            double q = 0.0;
-            if (o < m0) {
-                for (int l = 0; l < nb0; ++l) q += Tp[l] * Qm0[l * m0 + o];
-            } else {
-                const int oo = o - m0;
-                for (int l = 0; l < nb1; ++l) q += Tp[l] * Qm1[l * m1 + oo];
-                q *= rh[p];
-            }
-            Qs[o * kFTile + p] = (T)q;
-        }
-        __syncthreads();
-        for (int col = threadIdx.x; col < nF; col += blockDim.x) {
-            const int par = colpar[col];
-            const int ob = par ? m0 : 0, mp = par ? m1 : m0;
-            T acc[kFTile];
-#pragma unroll
-            for (int p = 0; p < kFTile; ++p) acc[p] = (T)0;
-            for (int l = 0; l < mp; ++l) {
-                const T w = Wt[(int64_t)l * nF + col];
-                const T* q = Qs + (ob + l) * kFTile;
-#pragma unroll
-                for (int p = 0; p < kFTile; ++p) acc[p] += q[p] * w;
-            }
-            for (int p = 0; p < cnt; ++p) F[(t0 + p) * ldF + col] = acc[p];
-        }
-        __syncthreads();
+        const double u = 8.0 * s - 1.0;
+        rh[p] = sqrt(s);
+        Tp[0] = 1.0;
+        if (P.L >= 1) Tp[1] = u;
+        for (int l = 2; l <= P.L; ++l) Tp[l] = 2.0 * u * Tp[l - 1] - Tp[l - 2];
     }
+    __syncthreads();
+    const int mt = P.m0 + P.m1;
+    for (int idx = threadIdx.x; idx < mt * kFTile; idx += blockDim.x) {
+        const int o = idx / kFTile, p = idx % kFTile;
+        const double* Tp = Ts + p * LP1;
+        double q = 0.0;
+        if (o < P.m0) {
+            for (int l = 0; l < P.nb0; ++l) q += Tp[l] * P.Qm0[l * P.m0 + o];
+        } else {
+            const int oo = o - P.m0;
+            for (int l = 0; l < P.nb1; ++l) q += Tp[l] * P.Qm1[l * P.m1 + oo];
+            q *= rh[p];
+        }
+        Qs[o * kFTile + p] = (T)q;
+    }
+    __syncthreads();
+    for (int col = threadIdx.x; col < P.nF; col += blockDim.x) {
+        const int par = P.colpar[col];
+        const int ob = par ? P.m0 : 0, mp = par ? P.m1 : P.m0;
+        T acc[kFTile];
+#pragma unroll
+        for (int p = 0; p < kFTile; ++p) acc[p] = (T)0;
+        for (int l = 0; l < mp; ++l) {
+            const T w = Wt[(int64_t)l * P.nF + col];
+            const T* q = Qs + (ob + l) * kFTile;
+#pragma unroll
+            for (int p = 0; p < kFTile; ++p) acc[p] += q[p] * w;
+        }
+        for (int p = 0; p < cnt; ++p) F[(t0 + p) * P.ldF + col] = acc[p];
+    }
+    __syncthreads();
+}
+
+// Per point: B_par (FP64) -> Q_par = B_par Qmat_par (FP64, the orthonormalised radial basis
+// of Eq. svd) -> F[i, col] = sum_l Q_par(col)[l] Wt[l, col] (type T).  Tiles of 32 points.
+template <typename T>
+__global__ void __launch_bounds__(256) k_radial_F(RFParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t ntiles = (P.n + kFTile - 1) / kFTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) radialF_tile<T>(P, tile * kFTile, smem_raw);
 }
 
 // ------------------------------------------------------- A5b: harmonics and U writer
@@ -270,8 +286,116 @@ struct UWParams {
     int per_warp;              // shared elements (type T) per warp
 };
 
-// PRE: harmonics precomputed per point into shared memory (nH values per warp); otherwise each
-// column's harmonic is multiplied out from the level tables as it is written.
+// One point's U row, executed by one warp.  cA/cB: level recurrences in shared memory;
+// base: this warp's shared area (P.per_warp elements).  pre: harmonics precomputed per point
+// into shared memory (nH values); otherwise each column's harmonic is multiplied out from
+// the level tables as it is written.
+template <typename T>
+__device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64_t i, const T* cA, const T* cB,
+                                              T* base, int lane) {
+    const int levels = P.d - 2;
+    T* tbl = base;                               // levels * tri
+    T* trig = tbl + levels * P.tri;              // 2L+1, index L + mu
+    T* Ys = trig + 2 * P.L + 1;                  // nH (pre only)
+    T* Fs = Ys + (pre ? P.nH : 0);               // nF + 1
+    const T* Fg = reinterpret_cast<const T*>(P.F);
+    T* Ug = reinterpret_cast<T*>(P.U);
+    typedef typename Vec2<T>::type VT;
+    constexpr int VW = Vec2<T>::w;
+    // direction x_hat (FP64), zero vector -> e_0
+    double xh[kMaxD];
+    double s = 0.0;
+    for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R; s += xh[j] * xh[j]; }
+    if (s > 0.0) {
+        const double inv = 1.0 / sqrt(s);
+        for (int j = 0; j < P.d; ++j) xh[j] *= inv;
+    } else {
+        for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0;
+    }
+    // level tables: lanes over mu'
+    for (int j = 0; j < levels; ++j) {
+        const int D = P.d - 1 - j;
+        double q = 0.0;
+        for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
+        const T z = (T)xh[D], qq = (T)q;
+        const T* A = cA + j * P.tri;
+        const T* B = cB + j * P.tri;
+        T* tb = tbl + j * P.tri;
+        for (int mu = lane; mu <= P.L; mu += 32) {
+            const int o = mu * (P.L + 1) - mu * (mu - 1) / 2;
+            const int nmax = P.L - mu;
+            T pm2 = A[o];
+            tb[o] = pm2;
+            if (nmax >= 1) {
+                T pm1 = A[o + 1] * z;
+                tb[o + 1] = pm1;
+                for (int nn = 2; nn <= nmax; ++nn) {
+                    const T pn = A[o + nn] * z * pm1 - B[o + nn] * qq * pm2;
+                    tb[o + nn] = pn;
+                    pm2 = pm1;
+                    pm1 = pn;
+                }
+            }
+        }
+    }
+    // trig powers (x0 + i x1)^mu by binary powering, lanes over mu
+    for (int mu = lane; mu <= P.L; mu += 32) {
+        double br = xh[0], bi = xh[1], rr = 1.0, ri = 0.0;
+        int e = mu;
+        while (e) {
+            if (e & 1) { const double t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
+            const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+            e >>= 1;
+        }
+        if (mu == 0) {
+            trig[P.L] = (T)0.3989422804014327;             // 1/sqrt(2 pi)
+        } else {
+            trig[P.L + mu] = (T)(rr * 0.5641895835477563);  // 1/sqrt(pi)
+            trig[P.L - mu] = (T)(ri * 0.5641895835477563);
+        }
+    }
+    // this point's radial factors
+    for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
+    if (lane == 0) Fs[P.nF] = (T)0;
+    __syncwarp();
+    if (pre) {
+        for (int g = lane; g < P.nH; g += 32) {
+            const int16_t* ch = P.chains + (int64_t)g * (levels + 1);
+            T v = trig[P.L + ch[levels]];
+            for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + ch[j]];
+            Ys[g] = v;
+        }
+    }
+    __syncwarp();
+    // row write, VW consecutive columns per lane per step
+    T* row = Ug + i * P.ldU;
+    for (int64_t c0 = (int64_t)lane * VW; c0 < P.ldU; c0 += 32 * VW) {
+        T v[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const uint32_t dsc = __ldg(P.desc + c0 + e);
+            if (pre) {
+                v[e] = Fs[dsc >> 20] * Ys[dsc & 0xFFFFFu];
+            } else {
+                const int16_t* ch = P.chains + (int64_t)(dsc & 0xFFFFFu) * (levels + 1);
+                T h = trig[P.L + __ldg(ch + levels)];
+                for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(ch + j)];
+                v[e] = Fs[dsc >> 20] * h;
+            }
+        }
+        VT out;
+        if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
+        else { out.x = v[0]; out.y = v[1]; }
+        *reinterpret_cast<VT*>(row + c0) = out;
+    }
+    __syncwarp();
+}
+
+// Shared elements (type T) per warp of the U writer.
+__host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int nH, int nF, bool pre) {
+    return ((levels * tri + 2 * L + 1 + (pre ? nH : 0) + nF + 1) + 3) & ~3;
+}
+
 template <typename T, bool PRE>
 __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -285,105 +409,8 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
     }
     __syncthreads();
     T* base = cB + levels * P.tri + (size_t)warp * P.per_warp;
-    T* tbl = base;                               // levels * tri
-    T* trig = tbl + levels * P.tri;              // 2L+1, index L + mu
-    T* Ys = trig + 2 * P.L + 1;                  // nH (PRE only)
-    T* Fs = Ys + (PRE ? P.nH : 0);               // nF + 1
-    const T* Fg = reinterpret_cast<const T*>(P.F);
-    T* Ug = reinterpret_cast<T*>(P.U);
-    typedef typename Vec2<T>::type VT;
-    constexpr int VW = Vec2<T>::w;
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
-    for (int64_t i = gw; i < P.n; i += nw) {
-        // direction x_hat (FP64), zero vector -> e_0
-        double xh[kMaxD];
-        double s = 0.0;
-        for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R; s += xh[j] * xh[j]; }
-        if (s > 0.0) {
-            const double inv = 1.0 / sqrt(s);
-            for (int j = 0; j < P.d; ++j) xh[j] *= inv;
-        } else {
-            for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0;
-        }
-        // level tables: lanes over mu'
-        for (int j = 0; j < levels; ++j) {
-            const int D = P.d - 1 - j;
-            double q = 0.0;
-            for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
-            const T z = (T)xh[D], qq = (T)q;
-            const T* A = cA + j * P.tri;
-            const T* B = cB + j * P.tri;
-            T* tb = tbl + j * P.tri;
-            for (int mu = lane; mu <= P.L; mu += 32) {
-                const int o = mu * (P.L + 1) - mu * (mu - 1) / 2;
-                const int nmax = P.L - mu;
-                T pm2 = A[o];
-                tb[o] = pm2;
-                if (nmax >= 1) {
-                    T pm1 = A[o + 1] * z;
-                    tb[o + 1] = pm1;
-                    for (int nn = 2; nn <= nmax; ++nn) {
-                        const T pn = A[o + nn] * z * pm1 - B[o + nn] * qq * pm2;
-                        tb[o + nn] = pn;
-                        pm2 = pm1;
-                        pm1 = pn;
-                    }
-                }
-            }
-        }
-        // trig powers (x0 + i x1)^mu by binary powering, lanes over mu
-        for (int mu = lane; mu <= P.L; mu += 32) {
-            double br = xh[0], bi = xh[1], rr = 1.0, ri = 0.0;
-            int e = mu;
-            while (e) {
-                if (e & 1) { const double t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
-                const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
-                e >>= 1;
-            }
-            if (mu == 0) {
-                trig[P.L] = (T)0.3989422804014327;             // 1/sqrt(2 pi)
-            } else {
-                trig[P.L + mu] = (T)(rr * 0.5641895835477563);  // 1/sqrt(pi)
-                trig[P.L - mu] = (T)(ri * 0.5641895835477563);
-            }
-        }
-        // this point's radial factors
-        for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
-        if (lane == 0) Fs[P.nF] = (T)0;
-        __syncwarp();
-        // harmonics
-        if (PRE) {
-            for (int g = lane; g < P.nH; g += 32) {
-                const int16_t* ch = P.chains + (int64_t)g * (levels + 1);
-                T v = trig[P.L + ch[levels]];
-                for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + ch[j]];
-                Ys[g] = v;
-            }
-        }
-        __syncwarp();
-        // row write, VW consecutive columns per lane per step
-        T* row = Ug + i * P.ldU;
-        for (int64_t c0 = (int64_t)lane * VW; c0 < P.ldU; c0 += 32 * VW) {
-            T v[VW];
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const uint32_t dsc = __ldg(P.desc + c0 + e);
-                if (PRE) {
-                    v[e] = Fs[dsc >> 20] * Ys[dsc & 0xFFFFFu];
-                } else {
-                    const int16_t* ch = P.chains + (int64_t)(dsc & 0xFFFFFu) * (levels + 1);
-                    T h = trig[P.L + __ldg(ch + levels)];
-                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(ch + j)];
-                    v[e] = Fs[dsc >> 20] * h;
-                }
-            }
-            VT out;
-            if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
-            else { out.x = v[0]; out.y = v[1]; }
-            *reinterpret_cast<VT*>(row + c0) = out;
-        }
-        __syncwarp();
-    }
+    for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, PRE, i, cA, cB, base, lane);
 }
 
 // --------------------------------------------------------------------- A7: matvec
@@ -420,18 +447,15 @@ template <> struct VecLd<double, 8> {
     static __device__ __forceinline__ void ld(const double* p, double* o) { VecLd<double, 4>::ld(p, o); VecLd<double, 4>::ld(p + 4, o + 4); }
 };
 
-// part[(chunk * c + j) * r + a] = sum_{i in chunk} U[i, a] V[i + j ldv]
+// part_chunk[j * r + a] = sum_{i0 <= i < i1} U[i, a] V[i + j ldv] for the columns [a0, a0 + AB).
 template <typename T, int CT>
-__global__ void __launch_bounds__(256) k_utv_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
-                                                  const T* __restrict__ V, int64_t ldv, int c, int64_t chunk,
-                                                  double* __restrict__ part) {
+__device__ __forceinline__ void utv_tile_body(const T* __restrict__ U, int64_t ldU, int64_t r,
+                                              const T* __restrict__ V, int64_t ldv, int c, int64_t i0, int64_t i1,
+                                              int64_t a0, double* __restrict__ part_chunk,
+                                              T (*Us)[UtvShape<CT>::AB], T (*Vs)[CT]) {
     using S = UtvShape<CT>;
-    __shared__ __align__(16) T Us[kKT][S::AB];
-    __shared__ __align__(16) T Vs[kKT][CT];
     const int t = threadIdx.x;
     const int tx = t % (S::AB / S::TA), ty = t / (S::AB / S::TA);
-    const int64_t a0 = blockIdx.y * (int64_t)S::AB;
-    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
     T acc[S::TA][S::TJ];
 #pragma unroll
     for (int p = 0; p < S::TA; ++p)
@@ -469,9 +493,21 @@ __global__ void __launch_bounds__(256) k_utv_tile(const T* __restrict__ U, int64
 #pragma unroll
         for (int q = 0; q < S::TJ; ++q) {
             const int j = ty * S::TJ + q;
-            if (a < r && j < c) part[((int64_t)blockIdx.x * c + j) * r + a] = (double)acc[p][q];
+            if (a < r && j < c) part_chunk[(int64_t)j * r + a] = (double)acc[p][q];
         }
     }
+}
+
+// part[(chunk * c + j) * r + a] = sum_{i in chunk} U[i, a] V[i + j ldv]
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_utv_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
+                                                  const T* __restrict__ V, int64_t ldv, int c, int64_t chunk,
+                                                  double* __restrict__ part) {
+    __shared__ __align__(16) T Us[kKT][UtvShape<CT>::AB];
+    __shared__ __align__(16) T Vs[kKT][CT];
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    utv_tile_body<T, CT>(U, ldU, r, V, ldv, c, i0, i1, blockIdx.y * (int64_t)UtvShape<CT>::AB,
+                         part + (int64_t)blockIdx.x * c * r, Us, Vs);
 }
 
 // W[a * c + j] = scale_a * sum_chunk part[(chunk * c + j) * r + a]; scale = S[a] or 1.
@@ -497,18 +533,17 @@ template <int CT> struct UwShape {
     static constexpr int TN = (CT * (RB / TM)) / 256;
 };
 
+constexpr int kUwPad = 4;
+
+// Rows [m0, m0 + RB) of Y = alpha U W + beta B.
 template <typename T, int CT>
-__global__ void __launch_bounds__(256) k_uw_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
-                                                 const T* __restrict__ W, int c, T alpha,
-                                                 const T* __restrict__ B, int64_t ldb, T beta,
-                                                 T* __restrict__ Y, int64_t ldy) {
+__device__ __forceinline__ void uw_tile_body(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
+                                             const T* __restrict__ W, int c, T alpha, const T* __restrict__ B,
+                                             int64_t ldb, T beta, T* __restrict__ Y, int64_t ldy, int64_t m0,
+                                             T (*Us)[UwShape<CT>::RB + kUwPad], T (*Ws)[CT]) {
     using S = UwShape<CT>;
-    constexpr int PAD = 4;
-    __shared__ __align__(16) T Us[kKT][S::RB + PAD];
-    __shared__ __align__(16) T Ws[kKT][CT];
     const int t = threadIdx.x;
     const int tx = t % (S::RB / S::TM), ty = t / (S::RB / S::TM);
-    const int64_t m0 = blockIdx.x * (int64_t)S::RB;
     T acc[S::TM][S::TN];
 #pragma unroll
     for (int p = 0; p < S::TM; ++p)
@@ -552,6 +587,17 @@ __global__ void __launch_bounds__(256) k_uw_tile(const T* __restrict__ U, int64_
             }
         }
     }
+}
+
+template <typename T, int CT>
+__global__ void __launch_bounds__(256) k_uw_tile(const T* __restrict__ U, int64_t ldU, int64_t n, int64_t r,
+                                                 const T* __restrict__ W, int c, T alpha,
+                                                 const T* __restrict__ B, int64_t ldb, T beta,
+                                                 T* __restrict__ Y, int64_t ldy) {
+    __shared__ __align__(16) T Us[kKT][UwShape<CT>::RB + kUwPad];
+    __shared__ __align__(16) T Ws[kKT][CT];
+    uw_tile_body<T, CT>(U, ldU, n, r, W, c, alpha, B, ldb, beta, Y, ldy, blockIdx.x * (int64_t)UwShape<CT>::RB,
+                        Us, Ws);
 }
 
 // ----------------------------------------------------------------- A6: Gram U^T U

@@ -196,7 +196,7 @@ static double clenshaw(const std::vector<double>& c, double u) {
     return u * b1 - b2 + c[0];
 }
 
-void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out) {
+void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out, bool threads) {
     const int L = p / 2;
     const double alpha = 0.5 * d - 1.0;
     const double area = sphere_area(d);
@@ -205,7 +205,7 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
     for (int q = 0; q <= L; ++q) deriv[0][q] = a[2 * q];
     for (int k = 1; k <= L; ++k) cheb_derivative(deriv[k - 1], deriv[k], 2.0);   // d/ds = 2 d/du
     out.assign(L + 1, std::vector<double>());
-    parallel_for(L + 1, [&](int k) {
+    auto one = [&](int k) {
         const std::vector<double>& Fk = deriv[k];
         const int nb = (k % 2 == 0) ? L + 1 : L;
         if (nb == 0) return;
@@ -251,7 +251,12 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
         for (int l = 0; l < nb; ++l)
             for (int m = 0; m < l; ++m) G[l * nb + m] = G[m * nb + l] = 0.5 * (G[l * nb + m] + G[m * nb + l]);
         out[k].swap(G);
-    });
+    };
+    if (threads) {
+        parallel_for(L + 1, one);
+    } else {
+        for (int k = 0; k <= L; ++k) one(k);
+    }
 }
 
 // --------------------------------------------------------------- harmonic tables
@@ -309,6 +314,195 @@ void append_chains(int k, int d, int L, std::vector<int16_t>& out) {
         }
     };
     rec(1);
+}
+
+}  // namespace hdf
+
+namespace hdf {
+
+void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double tol, double eta, int p_max,
+                 int d, bool threads, DegreePlan& out) {
+    const int M = cheb_nodes(p_max);
+    out.a.assign(M, 0.0);
+    cheb_coeffs(kernel, ell, 2.0 * R, M, false, out.a.data());
+    out.tail_budget = 0.5 * tol * std::sqrt(mu2);
+    out.drop_budget = 0.5 * eta * tol * (double)n * std::sqrt(mu2);
+    out.p = choose_degree(out.a.data(), M, out.tail_budget, p_max, &out.tail, &out.reached);
+    out.L = out.p / 2;
+    radial_cores(out.a.data(), out.p, d, out.cores, threads);
+}
+
+void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
+                 double drop_budget, bool threads, FactorChoice& out) {
+    const int nb0 = L + 1, nb1 = L;
+    const int npairs = nb0 * (nb0 + 1) / 2;
+    out.nb[0] = nb0;
+    out.nb[1] = nb1;
+    for (int par = 0; par < 2; ++par) {
+        const int nb = out.nb[par];
+        out.m[par] = 0;
+        out.Rf[par].clear();
+        out.Qmat[par].clear();
+        if (nb == 0) continue;
+        std::vector<double> Gm((size_t)nb * nb), w(nb), V((size_t)nb * nb);
+        int q = 0;
+        for (int l = 0; l < nb0; ++l)
+            for (int lp = l; lp < nb0; ++lp, ++q)
+                if (l < nb && lp < nb) Gm[(size_t)l * nb + lp] = Gm[(size_t)lp * nb + l] = gram[(size_t)par * npairs + q];
+        sym_eig(nb, Gm.data(), w.data(), V.data());
+        double wmax = 0.0;
+        for (int l = 0; l < nb; ++l) wmax = std::max(wmax, w[l]);
+        const double floor_ = wmax * 1e-13 * nb;
+        std::vector<int> keep;
+        for (int l = 0; l < nb; ++l) if (w[l] > floor_) keep.push_back(l);
+        const int mk = (int)keep.size();
+        out.m[par] = mk;
+        out.Rf[par].assign((size_t)mk * nb, 0.0);
+        out.Qmat[par].assign((size_t)nb * mk, 0.0);
+        for (int o = 0; o < mk; ++o) {
+            const double sq = std::sqrt(w[keep[o]]);
+            for (int l = 0; l < nb; ++l) {
+                out.Rf[par][(size_t)o * nb + l] = sq * V[(size_t)l * nb + keep[o]];
+                out.Qmat[par][(size_t)l * mk + o] = V[(size_t)l * nb + keep[o]] / sq;
+            }
+        }
+    }
+    const double area = sphere_area(d);
+    std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
+    auto one = [&](int k) {
+        const int par = k % 2, nb = out.nb[par], mk = out.m[par];
+        if (mk == 0 || nb == 0) return;
+        const std::vector<double>& Gk = cores[k];
+        const std::vector<double>& Rf = out.Rf[par];
+        std::vector<double> T1((size_t)mk * nb, 0.0), Gm((size_t)mk * mk, 0.0);
+        for (int o = 0; o < mk; ++o)
+            for (int l = 0; l < nb; ++l) {
+                double s = 0.0;
+                for (int t = 0; t < nb; ++t) s += Rf[(size_t)o * nb + t] * Gk[(size_t)t * nb + l];
+                T1[(size_t)o * nb + l] = s;
+            }
+        for (int o = 0; o < mk; ++o)
+            for (int o2 = 0; o2 <= o; ++o2) {
+                double s = 0.0;
+                for (int l = 0; l < nb; ++l) s += T1[(size_t)o * nb + l] * Rf[(size_t)o2 * nb + l];
+                Gm[(size_t)o * mk + o2] = Gm[(size_t)o2 * mk + o] = s;
+            }
+        lam[k].resize(mk);
+        vec[k].resize((size_t)mk * mk);
+        sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
+    };
+    if (threads) {
+        parallel_for(L + 1, one);
+    } else {
+        for (int k = 0; k <= L; ++k) one(k);
+    }
+    struct Item { double cost; int k, j; };
+    std::vector<Item> items;
+    for (int k = 0; k <= L; ++k) {
+        const double hk = (double)harmonic_count(k, d);
+        for (int j = 0; j < (int)lam[k].size(); ++j) items.push_back({std::fabs(lam[k][j]) * hk / area, k, j});
+    }
+    std::sort(items.begin(), items.end(), [](const Item& A, const Item& B) {
+        if (A.cost != B.cost) return A.cost < B.cost;
+        if (A.k != B.k) return A.k < B.k;
+        return A.j < B.j;
+    });
+    std::vector<std::vector<char>> dropped(L + 1);
+    for (int k = 0; k <= L; ++k) dropped[k].assign(lam[k].size(), 0);
+    double acc = 0.0;
+    for (const Item& it : items) {
+        if (acc + it.cost > drop_budget) break;
+        acc += it.cost;
+        dropped[it.k][it.j] = 1;
+    }
+    out.dropped = acc;
+    out.sk.assign(L + 1, 0);
+    out.Wk.assign(L + 1, std::vector<double>());
+    out.S.clear();
+    out.rank = 0;
+    out.nH = 0;
+    for (int k = 0; k <= L; ++k) {
+        const int64_t hcount = harmonic_count(k, d);
+        std::vector<int> idx;
+        for (int j = 0; j < (int)lam[k].size(); ++j) if (!dropped[k][j]) idx.push_back(j);
+        std::sort(idx.begin(), idx.end(), [&](int A, int B) {
+            const double fa = std::fabs(lam[k][A]), fb = std::fabs(lam[k][B]);
+            if (fa != fb) return fa > fb;
+            return A < B;
+        });
+        out.sk[k] = (int)idx.size();
+        if (out.sk[k] == 0) continue;
+        const int mk = out.m[k % 2];
+        out.Wk[k].assign((size_t)mk * out.sk[k], 0.0);
+        for (int s = 0; s < out.sk[k]; ++s)
+            for (int o = 0; o < mk; ++o) out.Wk[k][(size_t)o * out.sk[k] + s] = vec[k][(size_t)o * mk + idx[s]];
+        out.rank += hcount * out.sk[k];
+        out.nH += hcount;
+        for (int s = 0; s < out.sk[k]; ++s)
+            for (int64_t h = 0; h < hcount; ++h) out.S.push_back(lam[k][idx[s]]);
+    }
+}
+
+bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, std::string& err) {
+    const std::vector<int>& sk = fc.sk;
+    t.L_used = 0;
+    for (int k = 0; k <= L; ++k) if (sk[k] > 0) t.L_used = k;
+    t.ldU = std::max<int64_t>(vw, ((fc.rank + vw - 1) / vw) * vw);
+    t.fbase.assign(L + 2, 0);
+    for (int k = 0; k <= L; ++k) t.fbase[k + 1] = t.fbase[k] + sk[k];
+    t.nF = t.fbase[L + 1];
+    t.mmax = std::max(fc.m[0], fc.m[1]);
+    t.Wt.assign((size_t)std::max(1, t.mmax) * std::max(1, t.nF), 0.0);
+    t.colpar.assign(std::max(1, t.nF), 0);
+    t.colk.assign(std::max(1, t.nF), 0);
+    for (int k = 0; k <= L; ++k)
+        for (int s = 0; s < sk[k]; ++s) {
+            const int col = t.fbase[k] + s, mk = fc.m[k % 2];
+            t.colpar[col] = (uint8_t)(k % 2);
+            t.colk[col] = (uint8_t)k;
+            for (int o = 0; o < mk; ++o) t.Wt[(size_t)o * t.nF + col] = fc.Wk[k][(size_t)o * sk[k] + s];
+        }
+    HarmonicTables ht;
+    harmonic_tables(d, t.L_used, ht);
+    t.tri = ht.tri;
+    t.coefA = ht.coefA;
+    t.coefB = ht.coefB;
+    t.chains.clear();
+    t.hbase.assign(L + 2, 0);
+    for (int k = 0; k <= L; ++k) {
+        t.hbase[k + 1] = t.hbase[k];
+        if (sk[k] == 0) continue;
+        append_chains(k, d, t.L_used, t.chains);
+        t.hbase[k + 1] += (int)ht.count[k];
+    }
+    t.nH = t.hbase[L + 1];
+    if (t.nH >= (1 << 20) || t.nF >= 4095) {
+        err = "too many harmonics or radial columns for the column descriptors";
+        return false;
+    }
+    t.hk.assign(std::max(1, t.nH), 0);
+    t.ktab.assign(5 * (L + 1), 0);
+    t.cbase.assign(L + 2, 0);
+    for (int k = 0; k <= L; ++k) {
+        for (int g = t.hbase[k]; g < t.hbase[k + 1]; ++g) t.hk[g] = (uint8_t)k;
+        const int hkc = (sk[k] > 0) ? (int)ht.count[k] : 0;
+        t.cbase[k + 1] = t.cbase[k] + hkc * sk[k];
+        t.ktab[5 * k + 0] = t.fbase[k];
+        t.ktab[5 * k + 1] = sk[k];
+        t.ktab[5 * k + 2] = t.cbase[k];
+        t.ktab[5 * k + 3] = hkc;
+        t.ktab[5 * k + 4] = t.hbase[k];
+    }
+    t.desc.assign(t.ldU, 0);
+    int64_t col = 0;
+    for (int k = 0; k <= L; ++k) {
+        if (sk[k] == 0) continue;
+        for (int s = 0; s < sk[k]; ++s)
+            for (int h = 0; h < (int)ht.count[k]; ++h)
+                t.desc[col++] = ((uint32_t)(t.fbase[k] + s) << 20) | (uint32_t)(t.hbase[k] + h);
+    }
+    for (; col < t.ldU; ++col) t.desc[col] = ((uint32_t)t.nF << 20);
+    return true;
 }
 
 }  // namespace hdf

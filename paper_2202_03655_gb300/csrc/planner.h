@@ -43,7 +43,8 @@ void gauss_gegenbauer(int N, double lam, double* t, double* w);
 
 // Radial cores Gamma_k (k = 0..p/2) of r^(k) in the basis rho^(k%2) T_l(8 rho^2 - 1):
 // out[k] is a row-major nb_k x nb_k matrix, nb_k = L+1 (k even) or L (k odd).
-void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out);
+// threads: spread the degrees over host threads.
+void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out, bool threads = true);
 
 // Per-level normalised Gegenbauer recurrences and the chain table of H_k (App. B) used
 // by the harmonic kernel.  See hdf_kernels.cuh for the evaluation they feed.
@@ -60,5 +61,48 @@ inline int tri_index(int L, int mu, int n) { return mu * (L + 1) - mu * (mu - 1)
 // Append the chains of H_k (lexicographic in (mu_1..mu_{d-2})) as (d-1) int16 entries each:
 // (d-2) level-table offsets, then the signed mu_{d-2} (trigonometric index).
 void append_chains(int k, int d, int L, std::vector<int16_t>& out);
+
+// ---------------------------------------------------------------- build planning
+// A1-A2 for one problem: Chebyshev coefficients of kappa(r) = k(2R r; l), the degree from
+// the tail budget tol sqrt(mu2)/2, the truncation budget eta tol n sqrt(mu2)/2, the cores.
+struct DegreePlan {
+    int p = 0, L = 0;
+    bool reached = false;
+    double tail = 0.0, tail_budget = 0.0, drop_budget = 0.0;
+    std::vector<double> a;
+    std::vector<std::vector<double>> cores;
+};
+void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double tol, double eta, int p_max,
+                 int d, bool threads, DegreePlan& out);
+
+// A3-A4 for one problem from the radial-basis Gram sums (2 x npairs, pairs (l <= l') of the
+// even basis in row order; the odd basis uses the leading L x L block of the second half):
+// basis factor B = Q R_f (R_f = D^1/2 V^T, directions below 1e-13 nb lambda_max dropped),
+// eigendecompositions of G_k = R_f Gamma_k R_f^T and the global truncation.
+struct FactorChoice {
+    int nb[2] = {0, 0}, m[2] = {0, 0};
+    std::vector<double> Rf[2], Qmat[2];
+    std::vector<std::vector<double>> Wk;     // per k: m x s_k, columns by decreasing |lambda|
+    std::vector<int> sk;
+    std::vector<double> S;                   // rank entries in (k, s, h) column order
+    int64_t rank = 0, nH = 0;
+    double dropped = 0.0;
+};
+void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
+                 double drop_budget, bool threads, FactorChoice& out);
+
+// Host images of the tables the device kernels read (FP64; cast to the bulk type on upload).
+struct DeviceTables {
+    int L_used = 0, tri = 0, nF = 0, nH = 0, mmax = 0;
+    int64_t ldU = 0;
+    std::vector<double> Wt;                  // mmax x nF
+    std::vector<uint8_t> colpar, colk, hk;
+    std::vector<int16_t> chains;
+    std::vector<uint32_t> desc;              // ldU
+    std::vector<double> coefA, coefB;
+    std::vector<int> ktab, fbase, cbase, hbase;
+};
+// vw: elements per 16 bytes of the bulk type (ldU is a multiple).  False if a limit is exceeded.
+bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& out, std::string& err);
 
 }  // namespace hdf

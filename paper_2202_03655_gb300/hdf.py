@@ -54,6 +54,13 @@ SIGNATURES = {
     "hdf_choose_degree": (_c_int, [_pdbl, _c_int, _c_dbl, _c_int, ctypes.POINTER(_c_int), _pdbl,
                                    ctypes.POINTER(_c_int)]),
     "hdf_radial_cores": (_c_int, [_pdbl, _c_int, _c_int, _pdbl, ctypes.POINTER(_c_i64)]),
+    "hdf_build_batched": (_c_int, [_c_int, ctypes.POINTER(_c_i64), _vp, _c_int, _c_int, _pdbl, _c_dbl, _c_int,
+                                   ctypes.POINTER(HdfOptions), _vp, ctypes.POINTER(_vp)]),
+    "hdf_batch_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
+    "hdf_batch_info": (_c_int, [_vp, _c_int, ctypes.POINTER(HdfInfo)]),
+    "hdf_batch_timings": (_c_int, [_vp, _pdbl]),
+    "hdf_batch_export": (_c_int, [_vp, _c_int, _vp, _pdbl]),
+    "hdf_batch_free": (None, [_vp]),
     "hdf_status_string": (ctypes.c_char_p, [_c_int]),
     "hdf_last_error": (ctypes.c_char_p, []),
     "hdf_launch_count": (ctypes.c_longlong, []),
@@ -283,3 +290,82 @@ def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, s
                          ctypes.byref(h))
     _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
     return Factor(h, st)
+
+
+class Batch:
+    """Many independent factors built and applied together (hdf_build_batched)."""
+
+    def __init__(self, handle, status, offsets, precision):
+        self._h = handle
+        self.status = status
+        self.offsets = np.asarray(offsets, dtype=np.int64)
+        self.nsets = len(self.offsets) - 1
+        self.precision = precision
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hdf_batch_free(h)
+            self._h = None
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None:
+            lib().hdf_batch_free(h)
+            self._h = None
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def info(self, s):
+        I = HdfInfo()
+        _check(lib().hdf_batch_info(self._h, int(s), ctypes.byref(I)))
+        return I
+
+    def timings(self):
+        out = np.zeros(NPHASE)
+        _check(lib().hdf_batch_timings(self._h, _dptr(out)))
+        return out
+
+    def matvec_ptr(self, V_ptr, ldv, ncols, Y_ptr, ldy, stream=None):
+        _check(lib().hdf_batch_matvec(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),
+                                      _stream_handle(stream)))
+
+    def matvec(self, V, stream=None):
+        """V: (sum n, c) tensor of the bulk dtype; returns K~_s V_s stacked the same way."""
+        import torch
+        vec = V.dim() == 1
+        V2 = V.reshape(V.shape[0], -1)
+        Vc = V2.t().contiguous()
+        Yc = torch.empty_like(Vc)
+        ntot = int(self.offsets[-1])
+        self.matvec_ptr(Vc.data_ptr(), ntot, Vc.shape[0], Yc.data_ptr(), ntot, stream)
+        Y = Yc.t()
+        return Y.reshape(-1) if vec else Y
+
+    def export(self, s):
+        I = self.info(s)
+        dt = np.float64 if I.precision == 0 else np.float32
+        U = np.zeros((I.n, I.rank), dtype=dt)
+        S = np.zeros(I.rank)
+        _check(lib().hdf_batch_export(self._h, int(s), _vp(U.ctypes.data), _dptr(S)))
+        return U, S
+
+
+def build_batched(x, offsets, kernel, lengthscales, tol, precision="fp32", p_max=None, eta=None, stream=None):
+    """Factor the sets x[offsets[s]:offsets[s+1]] (x: CUDA float64 (sum n, d))."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.dim() == 2):
+        raise ValueError("x must be a CUDA float64 tensor of shape (N, d)")
+    x = x.contiguous()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ells = np.ascontiguousarray(lengthscales, dtype=np.float64)
+    opt = HdfOptions(int(p_max or 0), float(eta or 0.0), 0)
+    h = _vp()
+    st = lib().hdf_build_batched(len(off) - 1, off.ctypes.data_as(ctypes.POINTER(_c_i64)), _vp(x.data_ptr()),
+                                 x.shape[1], KERNELS[kernel], _dptr(ells), float(tol), PRECISIONS[precision],
+                                 ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h))
+    _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
+    return Batch(h, st, off, precision)
