@@ -67,8 +67,11 @@ typedef enum {
 typedef struct {
     int p_max;      /* cap on the Chebyshev degree p (even; default 64, max 128) */
     double eta;     /* share of tol given to eigenpair truncation (default 1) */
-    int flags;      /* reserved, 0 */
+    int flags;      /* HDF_FLAG_* bits, 0 for defaults */
 } hdf_options;
+
+/* Run the matvec GEMMs of an FP32 factor on the CUDA cores instead of the tensor cores. */
+#define HDF_FLAG_CUDA_CORES 1
 
 #define HDF_MAX_D 8
 #define HDF_MAX_L 64
@@ -206,6 +209,10 @@ hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host);
  * this factor, first column group: ms3[0] U^T V, ms3[1] partial reduction and scaling by S,
  * ms3[2] U W.  Waits for those events.  HDF_EINVAL if no matvec has run yet. */
 hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3);
+
+/* *flag = 1 if a device kernel working on this factor gave up a bounded wait (its results
+ * are then invalid), else 0; clears the flag.  Synchronises the device. */
+hdf_status hdf_device_errors(const hdf_factor* f, int* flag);
 
 /* Release a factor (NULL is ignored). */
 void hdf_free(hdf_factor* f);

@@ -127,6 +127,16 @@ hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) 
 
 void hdf_free(hdf_factor* f) { delete f; }
 
+hdf_status hdf_device_errors(const hdf_factor* f, int* flag) {
+    if (!f || !flag) return fail(HDF_EINVAL, "hdf_device_errors: null argument");
+    *flag = 0;
+    if (!f->dev_err.p) return HDF_OK;
+    HDF_CUDA(cudaDeviceSynchronize());
+    HDF_CUDA(cudaMemcpy(flag, f->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    HDF_CUDA(cudaMemset(f->dev_err.p, 0, sizeof(int)));
+    return HDF_OK;
+}
+
 hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3) {
     if (!f || !ms3) return fail(HDF_EINVAL, "hdf_matvec_timings: null argument");
     if (!f->mv_recorded) return fail(HDF_EINVAL, "hdf_matvec_timings: no matvec recorded yet");
@@ -149,9 +159,11 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
         return fail(HDF_EINVAL, "hdf_build: bad argument (need n>=1, 3<=d<=8, l>0, 0<tol<1)");
     int p_max = 64;
     double eta = 1.0;
+    bool use_tc = true;
     if (opt) {
         if (opt->p_max > 0) p_max = opt->p_max;
         if (opt->eta > 0) eta = opt->eta;
+        if (opt->flags & HDF_FLAG_CUDA_CORES) use_tc = false;
     }
     if (p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, "hdf_build: p_max > 128");
     p_max -= p_max % 2;
@@ -243,6 +255,7 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     plan_factor(gram, L, d, dp.cores, dp.drop_budget, true, fc);
 
     hdf_factor* f = new hdf_factor();
+    f->use_tc = use_tc;
     f->kernel = kernel;
     f->ell = lengthscale;
     f->tol = tol;
@@ -362,6 +375,55 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
     HDF_CUDA(W.alloc(sizeof(T) * (size_t)r * cmax));
     hdf_factor* fm = const_cast<hdf_factor*>(f);
     const bool rec = fm->mv_ev[0] != nullptr;
+    // FP32 factors: column groups of 9..64 go to the tensor cores when the V block can be
+    // described to TMA (16-byte aligned base and leading dimension)
+    if constexpr (sizeof(T) == 4) {
+        const bool aligned = (reinterpret_cast<uintptr_t>(V) % 16 == 0) && (ldv % 4 == 0);
+        if (f->use_tc && aligned && cmax >= 9 && tc_bn(cmax) != 0) {
+            const int tch = tc_utv_chunks(n, r);
+            DevBuf tpart, tw, twork;
+            HDF_CUDA(tpart.alloc(sizeof(double) * (size_t)tch * cmax * r));
+            HDF_CUDA(tw.alloc(sizeof(float) * (size_t)r * cmax));
+            HDF_CUDA(twork.alloc(sizeof(float) * tc_work_floats(n, r, cmax)));
+            int* err = fm->dev_err.as<int>();
+            for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
+                const int cg = std::min(kMaxGroup, ncols - j0);
+                const bool tcg = cg >= 9 && (reinterpret_cast<uintptr_t>(V + j0 * ldv) % 16 == 0);
+                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
+                if (tcg) {
+                    hdf_status s = tc_utv(reinterpret_cast<const float*>(U), f->info.ldu, n, r,
+                                          reinterpret_cast<const float*>(V + j0 * ldv), ldv, cg, tch,
+                                          tpart.as<double>(), twork.as<float>(), err, st);
+                    if (s != HDF_OK) return s;
+                } else {
+                    launch_utv<T>(ct_for(cg), U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, nchunk, chunk,
+                                  part.as<double>(), st);
+                    HDF_CUDA(cudaGetLastError());
+                }
+                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
+                HDF_COUNT_LAUNCH();
+                dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(
+                    tcg ? tpart.as<double>() : part.as<double>(), tcg ? tch : nchunk, r, cg, S_scale,
+                    tcg ? reinterpret_cast<T*>(tw.p) : W.as<T>(), nullptr);
+                HDF_CUDA(cudaGetLastError());
+                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
+                if (tcg) {
+                    hdf_status s = tc_uw(reinterpret_cast<const float*>(U), f->info.ldu, n, r, tw.as<float>(), cg,
+                                         (float)alpha, reinterpret_cast<const float*>(B ? B + j0 * ldb : nullptr), ldb,
+                                         (float)beta, reinterpret_cast<float*>(Y + j0 * ldy), ldy, twork.as<float>(),
+                                         err, st);
+                    if (s != HDF_OK) return s;
+                } else {
+                    launch_uw<T>(ct_for(cg), U, f->info.ldu, n, r, W.as<T>(), cg, alpha,
+                                 B ? B + j0 * ldb : nullptr, ldb, beta, Y + j0 * ldy, ldy, st);
+                    HDF_CUDA(cudaGetLastError());
+                }
+                if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
+            }
+            // the work buffers are freed on return; cudaFree waits for the kernels using them
+            return HDF_OK;
+        }
+    }
     for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
         const int cg = std::min(kMaxGroup, ncols - j0);
         const int ct = ct_for(cg);
@@ -589,6 +651,8 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     const int L = dp.L;
     const int64_t r = I.rank;
     const int vw = (sizeof(T) == 4) ? 4 : 2;
+    HDF_CUDA(f->dev_err.alloc(sizeof(int)));
+    HDF_CUDA(cudaMemsetAsync(f->dev_err.p, 0, sizeof(int), st));
     DeviceTables tb;
     std::string terr;
     if (!make_tables(fc, d, L, vw, tb, terr)) return fail(HDF_ETOOBIG, "hdf_build: " + terr);

@@ -16,6 +16,15 @@ hdf_status fail(hdf_status s, const std::string& msg);
 // Counter of kernel launches reported by hdf_launch_count.
 extern std::atomic<long long> g_launches;
 
+// Tensor-core GEMMs of the FP32 matvec (tc_gemm.cu).  tc_bn: padded N (16, 32, 64) or 0.
+int tc_bn(int c);
+size_t tc_work_floats(int64_t n, int64_t r, int c);
+int tc_utv_chunks(int64_t n, int64_t r);
+hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int nchunk,
+                  double* part, float* work, int* err, cudaStream_t st);
+hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
+                 int64_t ldb, float beta, float* Y, int64_t ldy, float* work, int* err, cudaStream_t st);
+
 // W = S_scale .* (U^T V) for one group of c <= 64 columns: W (r x c row-major, bulk) and/or
 // Wd (r x c, FP64).  S_scale may be null (no scaling).  Allocates its partial sums.
 template <typename T>
@@ -79,6 +88,10 @@ struct hdf_factor {
     double core_lambda = -1.0;
     std::vector<double> LU;
     std::vector<int> piv;
+    // tensor-core matvec (FP32 factors): enabled unless HDF_FLAG_CUDA_CORES; dev_err is set by
+    // a kernel whose bounded wait expired
+    bool use_tc = true;
+    DevBuf dev_err;
     // events around the kernels of the most recent matvec (first column group)
     cudaEvent_t mv_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool mv_recorded = false;

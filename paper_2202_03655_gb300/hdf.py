@@ -48,6 +48,7 @@ SIGNATURES = {
     "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "hdf_factor_export": (_c_int, [_vp, _vp, _pdbl]),
     "hdf_free": (None, [_vp]),
+    "hdf_device_errors": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "hdf_matvec_timings": (_c_int, [_vp, _pdbl]),
     "hdf_cheb_nodes": (_c_int, [_c_int]),
     "hdf_cheb_coeffs": (_c_int, [_c_int, _c_dbl, _c_dbl, _c_int, _pdbl]),
@@ -251,6 +252,12 @@ class Factor:
         _check(lib().hdf_matvec_timings(self._h, _dptr(out)))
         return out
 
+    def device_errors(self):
+        """1 if a kernel on this factor gave up a bounded wait since the last check (clears it)."""
+        fl = _c_int()
+        _check(lib().hdf_device_errors(self._h, ctypes.byref(fl)))
+        return fl.value
+
     def free(self):
         """Release the factor's device memory now."""
         h = getattr(self, "_h", None)
@@ -273,7 +280,10 @@ class Factor:
         return U, S
 
 
-def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, stream=None):
+FLAG_CUDA_CORES = 1
+
+
+def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, stream=None, flags=0):
     """Factor K(x, x) for points x (torch CUDA float64, shape (n, d)).
 
     Returns a Factor; a factor capped at p_max (HDF_ETOL_UNREACHABLE) is returned with
@@ -283,7 +293,7 @@ def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, s
     if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.dim() == 2):
         raise ValueError("x must be a CUDA float64 tensor of shape (n, d)")
     x = x.contiguous()
-    opt = HdfOptions(int(p_max or 0), float(eta or 0.0), 0)
+    opt = HdfOptions(int(p_max or 0), float(eta or 0.0), int(flags))
     h = _vp()
     st = lib().hdf_build(_vp(x.data_ptr()), x.shape[0], x.shape[1], KERNELS[kernel], float(lengthscale),
                          float(tol), PRECISIONS[precision], ctypes.byref(opt), _stream_handle(stream),
