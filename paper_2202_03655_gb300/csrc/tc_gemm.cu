@@ -3,10 +3,10 @@
 // (cp.async.bulk.tensor) through an mbarrier pipeline, warp-specialised CTAs.
 //
 // Accuracy: one TF32 product keeps about 11 bits, far from what tol = 1e-6 needs, so every
-// product is split three ways (A B ~= A B + A B_lo + A_lo B with A_lo = A - trunc_tf32(A)):
-// the tensor core reads only the top 19 bits of an FP32 operand, so A itself serves as its
-// high part and only the low parts are formed, in shared memory by converter warps.  The
-// dropped A_lo B_lo term is below 2^-21 relative.
+// product is split three ways, A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi, with
+// A_hi = A rounded to TF32 (cvt.rna.tf32.f32, exactly representable) and A_lo = A - A_hi.
+// The high and low parts of the U tiles are formed in shared memory by converter warps, those
+// of W and V by small preparation kernels.  The dropped A_lo B_lo term is ~2^-22 relative.
 //
 //   k_tc_uw  : Y = alpha U W + beta B.  M = 128 rows of U (points), N = BN >= c, K = rank.
 //              A = U tile (K-major, SW128, TMA), B = W^T tile (K-major, SW128, TMA).
@@ -15,11 +15,17 @@
 //              converter warps into K-major SW128 tiles (hi and lo), so only K-major operand
 //              layouts reach the MMA.  B = V tiles (column-major V is K-major), SW128, TMA.
 //
+// The tensor core's FP32 accumulation is not rounded to nearest, and its error grows with
+// the number of MMAs summed into one accumulator (about 1.7e-5 relative after 400 K steps).
+// So each stage (32 K values, 12 MMAs) starts a fresh TMEM accumulator and the epilogue warps
+// add it into FP32 registers (round to nearest); two TMEM buffers alternate so that the MMAs
+// of one stage overlap the promotion of the previous one.
+//
 // CTA roles (10 warps): warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-5
-// converters, warps 6-9 epilogue (TMEM -> registers -> global; warp w reads TMEM lanes
-// 32 (w mod 4) .. +31).  Two TMEM accumulator buffers let the epilogue of one tile overlap
-// the MMAs of the next.  Every wait on an mbarrier is bounded by a clock limit; on expiry the
-// kernel records an error, drains its own copies and MMAs, frees its TMEM and returns.
+// converters, warps 6-9 promotion and epilogue (TMEM -> registers -> global; warp w reads TMEM
+// lanes 32 (w mod 4) .. +31).  Every wait on an mbarrier is bounded by a clock limit; on
+// expiry the kernel records an error, drains its own copies and MMAs, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -120,7 +126,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float tf32_low(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return __uint_as_float(h);
+}
 
 template <int BN>
 __host__ __device__ constexpr uint32_t tmem_cols() {
@@ -200,30 +210,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32<BN>();
-            uint32_t it = 0, local = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
-                const uint32_t buf = local & 1, aph = (local >> 1) & 1;
-                if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d = tmem + buf * BN;
+            uint32_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 for (int kt = 0; kt < p.nkt; ++kt, ++it) {
                     const int s = it % S;
-                    const uint32_t ph = (it / S) & 1;
+                    const uint32_t ph = (it / S) & 1, buf = it & 1, aph = (it >> 1) & 1;
+                    if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
                     if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
                     tc_fence_after();
+                    const uint32_t d = tmem + buf * BN;
                     const uint64_t da = sw128_desc(A + s * BM * BK), dal = sw128_desc(Alo + s * BM * BK);
                     const uint64_t db = sw128_desc(Bh + s * BN * BK), dbl = sw128_desc(Bl + s * BN * BK);
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk) {
                         const uint64_t off = (uint64_t)(kk * 32) >> 4;     // 8 TF32 = 32 bytes
-                        mma_tf32(d, da + off, db + off, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(d, da + off, db + off, idesc, kk > 0 ? 1u : 0u);
                         mma_tf32(d, da + off, dbl + off, idesc, 1u);
                         mma_tf32(d, dal + off, db + off, idesc, 1u);
                     }
                     mma_commit(&empty[s]);
+                    mma_commit(&accf[buf]);
                 }
-                if (!ok) break;
-                mma_commit(&accf[buf]);
             }
             mma_commit(drain);                       // all MMAs of this thread complete
             if (!mbar_wait(drain, 0)) ok = false;
@@ -237,13 +244,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int s = it % S;
                 const uint32_t ph = (it / S) & 1;
                 if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-                const float4* src = reinterpret_cast<const float4*>(A + s * BM * BK) + cw * (BM * BK / 16);
-                float4* dst = reinterpret_cast<float4*>(Alo + s * BM * BK) + cw * (BM * BK / 16);
+                float4* hi4 = reinterpret_cast<float4*>(A + s * BM * BK) + cw * (BM * BK / 16);
+                float4* lo4 = reinterpret_cast<float4*>(Alo + s * BM * BK) + cw * (BM * BK / 16);
 #pragma unroll
                 for (int q = 0; q < BM * BK / 16 / 32; ++q) {
-                    float4 v = src[q * 32 + lane];
-                    v.x = tf32_low(v.x); v.y = tf32_low(v.y); v.z = tf32_low(v.z); v.w = tf32_low(v.w);
-                    dst[q * 32 + lane] = v;
+                    const float4 v = hi4[q * 32 + lane];
+                    float4 h, l;
+                    h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+                    l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+                    hi4[q * 32 + lane] = h;
+                    lo4[q * 32 + lane] = l;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -253,31 +263,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!ok && lane == 0) atomicExch(p.err, 1);
     } else {
         const int q = warp & 3;                      // TMEM lane quadrant of this warp
-        uint32_t local = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
-            const uint32_t buf = local & 1, aph = (local >> 1) & 1;
-            if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
-            tc_fence_after();
+        uint32_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            float acc[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+            for (int kt = 0; kt < p.nkt; ++kt, ++it) {
+                const uint32_t buf = it & 1, aph = (it >> 1) & 1;
+                if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int j0 = 0; j0 < BN; j0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
+            }
+            if (!ok) break;
             const int64_t row = tile * BM + 32 * q + lane;
+            if (row < p.n) {
 #pragma unroll
-            for (int j0 = 0; j0 < BN; j0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
-                if (row < p.n) {
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int j = j0 + jj;
-                        if (j < p.c) {
-                            float out = p.alpha * v[jj];
-                            if (p.B) out += p.beta * p.B[row + (int64_t)j * p.ldb];
-                            p.Y[row + (int64_t)j * p.ldy] = out;
-                        }
+                for (int j = 0; j < BN; ++j) {
+                    if (j < p.c) {
+                        float out = p.alpha * acc[j];
+                        if (p.B) out += p.beta * p.B[row + (int64_t)j * p.ldb];
+                        p.Y[row + (int64_t)j * p.ldy] = out;
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[buf]);
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     }
@@ -372,31 +389,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32<BN>();
-            uint32_t it = 0, local = 0;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++local) {
-                const uint32_t buf = local & 1, aph = (local >> 1) & 1;
-                if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d = tmem + buf * BN;
+            uint32_t it = 0;
+            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int nk = ksteps(item);
                 for (int kt = 0; kt < nk; ++kt, ++it) {
                     const int s = it % S;
-                    const uint32_t ph = (it / S) & 1;
+                    const uint32_t ph = (it / S) & 1, buf = it & 1, aph = (it >> 1) & 1;
+                    if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
                     if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
                     tc_fence_after();
+                    const uint32_t d = tmem + buf * BN;
                     const uint64_t da = sw128_desc(Ah + s * BM * BK), dal = sw128_desc(Al + s * BM * BK);
                     const uint64_t db = sw128_desc(Bh + s * BN * BK), dbl = sw128_desc(Bl + s * BN * BK);
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk) {
                         const uint64_t off = (uint64_t)(kk * 32) >> 4;
-                        mma_tf32(d, da + off, db + off, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(d, da + off, db + off, idesc, kk > 0 ? 1u : 0u);
                         mma_tf32(d, da + off, dbl + off, idesc, 1u);
                         mma_tf32(d, dal + off, db + off, idesc, 1u);
                     }
                     mma_commit(&empty[s]);
+                    mma_commit(&accf[buf]);
                 }
-                if (!ok) break;
-                mma_commit(&accf[buf]);
             }
             mma_commit(drain);
             if (!mbar_wait(drain, 0)) ok = false;
@@ -423,8 +437,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float4 h, l;
                     const float x0 = R[(4 * kc + 0) * BM + m], x1 = R[(4 * kc + 1) * BM + m];
                     const float x2 = R[(4 * kc + 2) * BM + m], x3 = R[(4 * kc + 3) * BM + m];
-                    l.x = tf32_low(x0); l.y = tf32_low(x1); l.z = tf32_low(x2); l.w = tf32_low(x3);
-                    h.x = x0; h.y = x1; h.z = x2; h.w = x3;
+                    h.x = tf32_hi(x0); h.y = tf32_hi(x1); h.z = tf32_hi(x2); h.w = tf32_hi(x3);
+                    l.x = x0 - h.x; l.y = x1 - h.y; l.z = x2 - h.z; l.w = x3 - h.w;
                     const uint32_t off = (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((kc ^ (m & 7)) << 4));
                     *reinterpret_cast<float4*>(H + off) = h;
                     *reinterpret_cast<float4*>(Lo + off) = l;
@@ -437,28 +451,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!ok && lane == 0) atomicExch(p.err, 1);
     } else {
         const int q = warp & 3;
-        uint32_t local = 0;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++local) {
-            const uint32_t buf = local & 1, aph = (local >> 1) & 1;
-            if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
-            tc_fence_after();
+        uint32_t it = 0;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            float acc[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const uint32_t buf = it & 1, aph = (it >> 1) & 1;
+                if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int j0 = 0; j0 < BN; j0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
+            }
+            if (!ok) break;
             const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
             const int64_t a = mb * BM + 32 * q + lane;
+            if (a < p.r) {
 #pragma unroll
-            for (int j0 = 0; j0 < BN; j0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
-                if (a < p.r) {
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int j = j0 + jj;
-                        if (j < p.c) p.part[((int64_t)ch * p.c + j) * p.r + a] = (double)v[jj];
-                    }
-                }
+                for (int j = 0; j < BN; ++j)
+                    if (j < p.c) p.part[((int64_t)ch * p.c + j) * p.r + a] = (double)acc[j];
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[buf]);
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     }
@@ -470,24 +491,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// Wt_hi[j * kpad + a] = W[a * c + j] and Wt_lo = its TF32 low part (zero padding to kpad x bn).
+// Wt_hi[j * kpad + a] + Wt_lo[j * kpad + a] = W[a * c + j] (TF32 split, zero padding to kpad x bn).
 __global__ void k_prep_wt(const float* __restrict__ W, int64_t r, int c, int bn, int64_t kpad, float* __restrict__ hi,
                           float* __restrict__ lo) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)bn * kpad) return;
     const int64_t j = idx / kpad, a = idx % kpad;
     const float v = (a < r && j < c) ? W[a * c + j] : 0.f;
-    hi[idx] = v;
-    lo[idx] = tf32_low(v);
+    const float h = tf32_hi(v);
+    hi[idx] = h;
+    lo[idx] = v - h;
 }
 
-// Vlo[i + j * ldo] = TF32 low part of V[i + j * ldv] (i < n, j < c).
-__global__ void k_prep_vlo(const float* __restrict__ V, int64_t ldv, int64_t n, int c, int64_t ldo,
-                           float* __restrict__ lo) {
+// Vhi[i + j * ldo] + Vlo[i + j * ldo] = V[i + j * ldv] (TF32 split; i < n, j < c).
+__global__ void k_prep_v(const float* __restrict__ V, int64_t ldv, int64_t n, int c, int64_t ldo,
+                         float* __restrict__ hi, float* __restrict__ lo) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)c * ldo) return;
     const int64_t j = idx / ldo, i = idx % ldo;
-    lo[idx] = (i < n) ? tf32_low(V[i + j * ldv]) : 0.f;
+    const float v = (i < n) ? V[i + j * ldv] : 0.f;
+    const float h = tf32_hi(v);
+    hi[idx] = h;
+    lo[idx] = v - h;
 }
 
 // ------------------------------------------------------------------------- host side
@@ -570,13 +595,14 @@ template <int BN>
 static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c,
                          int nchunk, double* part, float* work, int* err, cudaStream_t st) {
     const int64_t ldo = ((n + 3) / 4) * 4;
-    float* vlo = work;
+    float* vhi = work;
+    float* vlo = work + (size_t)c * ldo;
     HDF_COUNT_LAUNCH();
-    k_prep_vlo<<<(unsigned)(((int64_t)c * ldo + 255) / 256), 256, 0, st>>>(V, ldv, n, c, ldo, vlo);
+    k_prep_v<<<(unsigned)(((int64_t)c * ldo + 255) / 256), 256, 0, st>>>(V, ldv, n, c, ldo, vhi, vlo);
     HDF_CUDA(cudaGetLastError());
     CUtensorMap mU, mV, mVl;
     if (!make_map(&mU, U, (uint64_t)ldU, (uint64_t)n, (uint64_t)ldU * 4, BM, BK, false) ||
-        !make_map(&mV, V, (uint64_t)n, (uint64_t)c, (uint64_t)ldv * 4, BK, BN, true) ||
+        !make_map(&mV, vhi, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true) ||
         !make_map(&mVl, vlo, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true))
         return fail(HDF_ECUDA, "tensor-core matvec: cannot encode a tensor map");
     const int64_t chunk = ((((n + nchunk - 1) / nchunk) + BK - 1) / BK) * BK;
@@ -601,15 +627,18 @@ size_t tc_work_floats(int64_t n, int64_t r, int c) {
     const int bn = tc_bn(c);
     const int64_t kpad = ((r + tc::BK - 1) / tc::BK) * tc::BK;
     const int64_t ldo = ((n + 3) / 4) * 4;
-    return std::max<size_t>(2 * (size_t)bn * kpad, (size_t)c * ldo);
+    return std::max<size_t>(2 * (size_t)bn * kpad, 2 * (size_t)c * ldo);
 }
 
 // Rows-per-chunk split for U^T V on the tensor cores: enough (column block, chunk) items.
 int tc_utv_chunks(int64_t n, int64_t r) {
+    // at least enough (column block, chunk) items to fill the GPU a few times, and chunks of at
+    // most 8192 rows so that the FP32 register sums of the promoted stages stay short
     const int64_t mblocks = (r + tc::BM - 1) / tc::BM;
-    const int64_t want = 4 * 152;
-    const int64_t by_rows = std::max<int64_t>(1, n / (64 * tc::BK));
-    return (int)std::max<int64_t>(1, std::min<int64_t>((want + mblocks - 1) / mblocks, by_rows));
+    const int64_t want = (4 * 152 + mblocks - 1) / mblocks;
+    const int64_t by_len = (n + 8191) / 8192;
+    const int64_t by_rows = std::max<int64_t>(1, n / (4 * tc::BK));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::max(want, by_len), by_rows));
 }
 
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int nchunk,

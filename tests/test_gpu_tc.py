@@ -1,5 +1,7 @@
-"""Tensor-core (tcgen05, 3xTF32) matvec of FP32 factors against the CUDA-core path of the
-same factor, and against the oracle."""
+"""Tensor-core (tcgen05, 3xTF32 with per-stage promotion) matvec of FP32 factors against the
+CUDA-core path of the same factor and against an FP64 product of the exported U and S."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -9,25 +11,42 @@ from paper_2202_03655_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+CASES = {"ball3": ("ball3_gauss", 2000, "gaussian", 0.5),
+         "cube4": ("cube4_gauss", 20011, "gaussian", 0.8),
+         "normal5": ("normal5_cauchy", 3001, "cauchy", 2.0)}
 
-@pytest.mark.parametrize("name,n,kname,ell", [("ball3_gauss", 2000, "gaussian", 0.5),
-                                              ("cube4_gauss", 20011, "gaussian", 0.8),
-                                              ("normal5_cauchy", 3001, "cauchy", 2.0)])
-@pytest.mark.parametrize("c", [9, 16, 37, 64, 70])
-def test_tensor_core_matvec_matches_cuda_cores(name, n, kname, ell, c):
-    import torch
+
+@functools.lru_cache(maxsize=None)
+def _factors(case):
     from paper_2202_03655_gb300 import hdf
+    name, n, kname, ell = CASES[case]
     x = W.points(name, n=n)
     f_tc = hdf.build(to_dev(x), kname, ell, 1e-6, precision="fp32")
     f_cc = hdf.build(to_dev(x), kname, ell, 1e-6, precision="fp32", flags=hdf.FLAG_CUDA_CORES)
+    U, S = f_tc.export()
+    return x, f_tc, f_cc, U.astype(np.float64), S
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("c", [9, 16, 37, 64, 70])
+def test_tensor_core_matvec(case, c):
+    x, f_tc, f_cc, U, S = _factors(case)
+    n = x.shape[0]
     V = np.random.default_rng(c).standard_normal((n, c)).astype(np.float32)
     Y_tc = f_tc.matvec(to_dev(V)).double().cpu().numpy()
     Y_cc = f_cc.matvec(to_dev(V)).double().cpu().numpy()
     assert f_tc.device_errors() == 0
-    assert rel(Y_tc, Y_cc) <= 2e-6
-    if n <= 3001:
-        fo = ohdf.build(x, kname, ell, 1e-6)
-        assert rel(Y_tc, ohdf.matvec(fo, V.astype(np.float64))) <= 1e-5
+    exact = U @ (S[:, None] * (U.T @ V.astype(np.float64)))       # same U, FP64 products
+    assert rel(Y_tc, exact) <= 2e-6
+    assert rel(Y_cc, exact) <= 2e-6
+
+
+def test_tensor_core_vs_oracle():
+    x, f_tc, _, _, _ = _factors("ball3")
+    fo = ohdf.build(x, "gaussian", 0.5, 1e-6)
+    V = np.random.default_rng(1).standard_normal((x.shape[0], 24))
+    Y = f_tc.matvec(to_dev(V.astype(np.float32))).double().cpu().numpy()
+    assert rel(Y, ohdf.matvec(fo, V)) <= 1e-5
 
 
 def test_tensor_core_solve_refinement():
