@@ -269,17 +269,21 @@ def main():
     mv = np.array(mv_ms).mean(axis=0)            # utv, reduce, uw (first 64-column group)
     utv_bytes = n * ldu * 4 + n * c * 4
     uwm_bytes = n * ldu * 4 + n * c * 4
+    tc = c >= 9          # FP32 column groups of 9..64 run on the tensor cores (tcgen05, 3xTF32)
     kernels = {
         "k_uwriter": (float(np.mean(uw_ms)), uw_bytes),
-        "k_utv_tile": (float(mv[0]), utv_bytes),
-        "k_uw_tile": (float(mv[2]), uwm_bytes),
+        ("k_tc_utv" if tc else "k_utv_tile"): (float(mv[0]), utv_bytes),
+        ("k_tc_uw" if tc else "k_uw_tile"): (float(mv[2]), uwm_bytes),
     }
     dom = max(kernels, key=lambda k: kernels[k][0])
     t_dom, b_dom = kernels[dom]
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    if dom == "k_uwriter":
+    if dom == "k_uwriter" or tc:
         roof = {"kernel": dom, "bound": "hbm", "achieved": b_dom / (t_dom / 1e3) / 1e9, "peak": hbm,
-                "unit": "GB/s", "peak_source": peak_src}
+                "unit": "GB/s", "peak_source": peak_src + " copy bandwidth (burst)"}
+        if tc and dom != "k_uwriter":
+            flops = 3 * 2.0 * n * ldu * (16 * ((c + 15) // 16))
+            roof["tensor_tflops"] = flops / (t_dom / 1e3) / 1e12
     else:
         flops = 2.0 * n * r * c
         peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
