@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,21 @@ std::atomic<long long> g_launches(0);     // kernels launched by this library
 hdf_status fail(hdf_status s, const std::string& msg) {
     g_err = msg;
     return s;
+}
+
+void pool_setup() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
 }
 }  // namespace hdf
 
@@ -125,7 +141,14 @@ hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) 
     return HDF_OK;
 }
 
-void hdf_free(hdf_factor* f) { delete f; }
+void hdf_free(hdf_factor* f) {
+    if (!f) return;
+    // U and F come from the stream-ordered pool of the build's stream; make sure no kernel of
+    // any stream still reads them, then return them to the pool on the legacy stream
+    cudaDeviceSynchronize();
+    f->U.st = nullptr;
+    delete f;
+}
 
 hdf_status hdf_device_errors(const hdf_factor* f, int* flag) {
     if (!f || !flag) return fail(HDF_EINVAL, "hdf_device_errors: null argument");
@@ -371,8 +394,8 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
     const int nchunk = utv_chunks(n, r, cmax);
     const int64_t chunk = (n + nchunk - 1) / nchunk;
     DevBuf part, W;
-    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * cmax * r));
-    HDF_CUDA(W.alloc(sizeof(T) * (size_t)r * cmax));
+    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nchunk * cmax * r, st));
+    HDF_CUDA(W.alloc_on(sizeof(T) * (size_t)r * cmax, st));
     hdf_factor* fm = const_cast<hdf_factor*>(f);
     const bool rec = fm->mv_ev[0] != nullptr;
     // FP32 factors: column groups of 9..64 go to the tensor cores when the V block can be
@@ -380,11 +403,13 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
     if constexpr (sizeof(T) == 4) {
         const bool aligned = (reinterpret_cast<uintptr_t>(V) % 16 == 0) && (ldv % 4 == 0);
         if (f->use_tc && aligned && cmax >= 9 && tc_bn(cmax) != 0) {
-            const int tch = tc_utv_chunks(n, r);
+            int64_t tchunk = 0;
+            int tch = 0;
+            tc_utv_split(n, r, &tchunk, &tch);
             DevBuf tpart, tw, twork;
-            HDF_CUDA(tpart.alloc(sizeof(double) * (size_t)tch * cmax * r));
-            HDF_CUDA(tw.alloc(sizeof(float) * (size_t)r * cmax));
-            HDF_CUDA(twork.alloc(sizeof(float) * tc_work_floats(n, r, cmax)));
+            HDF_CUDA(tpart.alloc_on(sizeof(double) * (size_t)tch * cmax * r, st));
+            HDF_CUDA(tw.alloc_on(sizeof(float) * (size_t)r * cmax, st));
+            HDF_CUDA(twork.alloc_on(sizeof(float) * tc_work_floats(n, r, cmax), st));
             int* err = fm->dev_err.as<int>();
             for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
                 const int cg = std::min(kMaxGroup, ncols - j0);
@@ -392,7 +417,7 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
                 if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
                 if (tcg) {
                     hdf_status s = tc_utv(reinterpret_cast<const float*>(U), f->info.ldu, n, r,
-                                          reinterpret_cast<const float*>(V + j0 * ldv), ldv, cg, tch,
+                                          reinterpret_cast<const float*>(V + j0 * ldv), ldv, cg, tchunk,
                                           tpart.as<double>(), twork.as<float>(), err, st);
                     if (s != HDF_OK) return s;
                 } else {
@@ -420,7 +445,7 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
                 }
                 if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
             }
-            // the work buffers are freed on return; cudaFree waits for the kernels using them
+            // the work buffers go back to the pool in stream order on return
             return HDF_OK;
         }
     }
@@ -665,7 +690,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaMemcpyAsync(f->S.p, Sd.data(), sizeof(T) * I.ldu, cudaMemcpyHostToDevice, st));
     }
     const size_t ubytes = sizeof(T) * (size_t)n * (size_t)I.ldu;
-    if (f->U.alloc(ubytes) != cudaSuccess) {
+    if (f->U.alloc_on(ubytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
     }
@@ -706,7 +731,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
     HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
     const int64_t ldF = nF;
-    if (dF.alloc(sizeof(T) * (size_t)n * ldF) != cudaSuccess) {
+    if (dF.alloc_on(sizeof(T) * (size_t)n * ldF, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build: cannot allocate the radial factor buffer");
     }

@@ -19,8 +19,10 @@ extern std::atomic<long long> g_launches;
 // Tensor-core GEMMs of the FP32 matvec (tc_gemm.cu).  tc_bn: padded N (16, 32, 64) or 0.
 int tc_bn(int c);
 size_t tc_work_floats(int64_t n, int64_t r, int c);
-int tc_utv_chunks(int64_t n, int64_t r);
-hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int nchunk,
+// Rows per chunk (a multiple of 32) and the number of chunks of the tensor-core U^T V split;
+// tc_utv writes exactly that many partial slices.
+void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk);
+hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
                   double* part, float* work, int* err, cudaStream_t st);
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
                  int64_t ldb, float beta, float* Y, int64_t ldy, float* work, int* err, cudaStream_t st);
@@ -43,15 +45,39 @@ hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const
         }                                                                                     \
     } while (0)
 
-// Owns one device allocation.
+namespace hdf {
+// Keeps freed stream-ordered allocations of the current device in its default memory pool
+// (release threshold raised once per device), so that repeated builds and products reuse
+// memory instead of mapping it again.
+void pool_setup();
+}  // namespace hdf
+
+// Owns one device allocation.  alloc(): synchronous cudaMalloc; alloc_on(): stream-ordered
+// from the device's memory pool, freed on the same stream (no device-wide synchronisation).
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
-    ~DevBuf() { if (p) cudaFree(p); }
+    cudaStream_t st = nullptr;
+    bool pooled = false;
+    ~DevBuf() { release(); }
+    void release() {
+        if (!p) return;
+        if (pooled) cudaFreeAsync(p, st); else cudaFree(p);
+        p = nullptr;
+    }
     cudaError_t alloc(size_t b) {
-        if (p) { cudaFree(p); p = nullptr; }
+        release();
         bytes = b;
+        pooled = false;
         return b ? cudaMalloc(&p, b) : cudaSuccess;
+    }
+    cudaError_t alloc_on(size_t b, cudaStream_t s) {
+        release();
+        hdf::pool_setup();
+        bytes = b;
+        pooled = true;
+        st = s;
+        return b ? cudaMallocAsync(&p, b, s) : cudaSuccess;
     }
     template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };

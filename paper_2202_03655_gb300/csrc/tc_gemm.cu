@@ -18,8 +18,8 @@
 // The tensor core's FP32 accumulation is not rounded to nearest, and its error grows with
 // the number of MMAs summed into one accumulator (about 1.7e-5 relative after 400 K steps).
 // So each stage (32 K values, 12 MMAs) starts a fresh TMEM accumulator and the epilogue warps
-// add it into FP32 registers (round to nearest); two TMEM buffers alternate so that the MMAs
-// of one stage overlap the promotion of the previous one.
+// add it into FP32 registers (round to nearest); four TMEM buffers rotate so that the MMAs of
+// the next stages run while earlier stages are promoted.
 //
 // CTA roles (10 warps): warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-5
 // converters, warps 6-9 promotion and epilogue (TMEM -> registers -> global; warp w reads TMEM
@@ -43,6 +43,7 @@ constexpr int BK = 32;                  // K elements per stage: one 128-byte sw
 constexpr int UW_STAGES = 4;
 constexpr int UTV_STAGES = 3;
 constexpr int NTHREADS = 320;
+constexpr int NACC = 4;                 // TMEM accumulator buffers (one per stage in flight)
 constexpr long long kWaitCycles = 4000000000ll;   // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -134,7 +135,7 @@ __device__ __forceinline__ float tf32_hi(float x) {
 
 template <int BN>
 __host__ __device__ constexpr uint32_t tmem_cols() {
-    return (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : 256;
+    return (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : (NACC * BN <= 128) ? 128 : (NACC * BN <= 256) ? 256 : 512;
 }
 
 struct UwArgs {
@@ -164,13 +165,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t* lo = full + S;
     uint64_t* empty = lo + S;
     uint64_t* accf = empty + S;
-    uint64_t* acce = accf + 2;
-    uint64_t* drain = acce + 2;
+    uint64_t* acce = accf + NACC;
+    uint64_t* drain = acce + NACC;
     uint32_t* slot = reinterpret_cast<uint32_t*>(drain + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&lo[s], 4); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+        for (int b = 0; b < NACC; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 for (int kt = 0; kt < p.nkt; ++kt, ++it) {
                     const int s = it % S;
-                    const uint32_t ph = (it / S) & 1, buf = it & 1, aph = (it >> 1) & 1;
+                    const uint32_t ph = (it / S) & 1, buf = it % NACC, aph = (it / NACC) & 1;
                     if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
                     if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
                     tc_fence_after();
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
             for (int kt = 0; kt < p.nkt; ++kt, ++it) {
-                const uint32_t buf = it & 1, aph = (it >> 1) & 1;
+                const uint32_t buf = it % NACC, aph = (it / NACC) & 1;
                 if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
@@ -335,13 +336,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t* lo = full + S;
     uint64_t* empty = lo + S;
     uint64_t* accf = empty + S;
-    uint64_t* acce = accf + 2;
-    uint64_t* drain = acce + 2;
+    uint64_t* acce = accf + NACC;
+    uint64_t* drain = acce + NACC;
     uint32_t* slot = reinterpret_cast<uint32_t*>(drain + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&lo[s], 4); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
+        for (int b = 0; b < NACC; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int nk = ksteps(item);
                 for (int kt = 0; kt < nk; ++kt, ++it) {
                     const int s = it % S;
-                    const uint32_t ph = (it / S) & 1, buf = it & 1, aph = (it >> 1) & 1;
+                    const uint32_t ph = (it / S) & 1, buf = it % NACC, aph = (it / NACC) & 1;
                     if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
                     if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
                     tc_fence_after();
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
             const int nk = ksteps(item);
             for (int kt = 0; kt < nk; ++kt, ++it) {
-                const uint32_t buf = it & 1, aph = (it >> 1) & 1;
+                const uint32_t buf = it % NACC, aph = (it / NACC) & 1;
                 if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
@@ -551,11 +552,11 @@ static bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t o
 
 template <int BN>
 static size_t uw_smem() {
-    return 1024 + (size_t)UW_STAGES * (2 * BM * BK + 2 * BN * BK) * 4 + (3 * UW_STAGES + 5) * 8 + 16;
+    return 1024 + (size_t)UW_STAGES * (2 * BM * BK + 2 * BN * BK) * 4 + (3 * UW_STAGES + 2 * NACC + 1) * 8 + 16;
 }
 template <int BN>
 static size_t utv_smem() {
-    return 1024 + (size_t)UTV_STAGES * (3 * BM * BK + 2 * BN * BK) * 4 + (3 * UTV_STAGES + 5) * 8 + 16;
+    return 1024 + (size_t)UTV_STAGES * (3 * BM * BK + 2 * BN * BK) * 4 + (3 * UTV_STAGES + 2 * NACC + 1) * 8 + 16;
 }
 
 static int num_sms() {
@@ -593,7 +594,7 @@ static hdf_status uw_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const
 
 template <int BN>
 static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c,
-                         int nchunk, double* part, float* work, int* err, cudaStream_t st) {
+                         int64_t chunk, double* part, float* work, int* err, cudaStream_t st) {
     const int64_t ldo = ((n + 3) / 4) * 4;
     float* vhi = work;
     float* vlo = work + (size_t)c * ldo;
@@ -605,7 +606,6 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
         !make_map(&mV, vhi, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true) ||
         !make_map(&mVl, vlo, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true))
         return fail(HDF_ECUDA, "tensor-core matvec: cannot encode a tensor map");
-    const int64_t chunk = ((((n + nchunk - 1) / nchunk) + BK - 1) / BK) * BK;
     const int nch = (int)((n + chunk - 1) / chunk);
     UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, err};
     const size_t sm = utv_smem<BN>();
@@ -631,22 +631,26 @@ size_t tc_work_floats(int64_t n, int64_t r, int c) {
 }
 
 // Rows-per-chunk split for U^T V on the tensor cores: enough (column block, chunk) items.
-int tc_utv_chunks(int64_t n, int64_t r) {
+void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk) {
     // at least enough (column block, chunk) items to fill the GPU a few times, and chunks of at
-    // most 8192 rows so that the FP32 register sums of the promoted stages stay short
+    // most 8192 rows so that the FP32 register sums of the promoted stages stay short; chunks
+    // are whole multiples of 32 rows, and *nchunk is the number of chunks that really exist
     const int64_t mblocks = (r + tc::BM - 1) / tc::BM;
     const int64_t want = (4 * 152 + mblocks - 1) / mblocks;
     const int64_t by_len = (n + 8191) / 8192;
     const int64_t by_rows = std::max<int64_t>(1, n / (4 * tc::BK));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(std::max(want, by_len), by_rows));
+    const int64_t req = std::max<int64_t>(1, std::min<int64_t>(std::max(want, by_len), by_rows));
+    const int64_t ch = (((n + req - 1) / req + tc::BK - 1) / tc::BK) * tc::BK;
+    *chunk = ch;
+    *nchunk = (int)((n + ch - 1) / ch);
 }
 
-hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int nchunk,
+hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
                   double* part, float* work, int* err, cudaStream_t st) {
     switch (tc_bn(c)) {
-        case 16: return tc::utv_bn<16>(U, ldU, n, r, V, ldv, c, nchunk, part, work, err, st);
-        case 32: return tc::utv_bn<32>(U, ldU, n, r, V, ldv, c, nchunk, part, work, err, st);
-        case 64: return tc::utv_bn<64>(U, ldU, n, r, V, ldv, c, nchunk, part, work, err, st);
+        case 16: return tc::utv_bn<16>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
+        case 32: return tc::utv_bn<32>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
+        case 64: return tc::utv_bn<64>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
     }
     return fail(HDF_EINVAL, "tc_utv: column count");
 }
