@@ -265,10 +265,12 @@ def main():
     peaks, peak_src = load_peaks()
     r, ldu = info.rank, info.ldu
     nF = sum(info.s_k[k] for k in range(info.L + 1))
-    uw_bytes = n * ldu * 4 + n * d * 8 + n * nF * 4
+    # algorithmic bytes count the true rank r; U is stored with zero padding columns up to ldu
+    # (each (k, s) block of harmonics padded to 16 bytes), which the kernels also move
+    uw_bytes = n * r * 4 + n * d * 8 + n * nF * 4
     mv = np.array(mv_ms).mean(axis=0)            # utv, reduce, uw (first 64-column group)
-    utv_bytes = n * ldu * 4 + n * c * 4
-    uwm_bytes = n * ldu * 4 + n * c * 4
+    utv_bytes = n * r * 4 + n * c * 4
+    uwm_bytes = n * r * 4 + n * c * 4
     tc = c >= 9          # FP32 column groups of 9..64 run on the tensor cores (tcgen05, 3xTF32)
     kernels = {
         "k_uwriter": (float(np.mean(uw_ms)), uw_bytes),
@@ -294,7 +296,7 @@ def main():
     roof["traffic"] = None
     roof["algorithmic_bytes"] = b_dom
     roof["ms_per_launch"] = t_dom
-    kv_bytes = 2 * n * ldu * 4 + n * c * 8
+    kv_bytes = 2 * n * r * 4 + n * c * 8
     kv_ms = float(mv.sum())
 
     # ---- FP64 form of the same step
@@ -359,7 +361,7 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "kernel": w["kernel"], "lengthscale": w["ell"],
                        "tol": w["tol"], "ncols": c, "p_max": args.p_max, "p": info.p, "reached": bool(info.reached),
-                       "rank": r, "U_bytes": n * ldu * 4, "parallelism": f"replicas{ws}",
+                       "rank": r, "ldu": ldu, "U_bytes": n * ldu * 4, "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (U alone is ~40 GB)"},
             "e2e": e2e,
             "roofline": roof,

@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
         for (int m = 0; m < P.d; ++m) xt[m] = (T)xh[m];
         for (int gi = lane; gi < P.nH; gi += 32) {
             const int k = P.hk[gi];
-            const int* kt = P.ktab + 5 * k;
-            const int fb = kt[0], sk = kt[1], cb = kt[2], dim = kt[3], hb = kt[4];
+            const int* kt = P.ktab + hdf::kTabStride * k;
+            const int fb = kt[0], sk = kt[1], cb = kt[2], hb = kt[4], dimp = kt[5];
             const int h = gi - hb;
             T al = (T)0, be = (T)0;
             for (int s = 0; s < sk; ++s) {
-                const int64_t col = cb + (int64_t)s * dim + h;
+                const int64_t col = cb + (int64_t)s * dimp + h;
                 const T cc = wi * P.a[col * P.ab_stride] + vi * P.b[col * P.ab_stride];
                 al += cc * R1[fb + s];
                 be += cc * R2[fb + s];
@@ -301,7 +301,7 @@ template <typename T>
 hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T* Wv, int64_t ldw, int ncols,
                T* grad, double* grad_l, double* value, cudaStream_t st) {
     FactorPlan& P = f->plan;
-    const int64_t n = f->info.n, r = f->info.rank;
+    const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;   // padded width of U
     const int d = P.d;
     if (r == 0) {
         HDF_CUDA(cudaMemsetAsync(grad, 0, sizeof(T) * n * d, st));
@@ -330,9 +330,10 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
     for (int64_t col = 0; col < r; ++col)
         for (int j = 0; j < ncols; ++j) {
             const size_t q = (size_t)col * ncols + j;
-            ha[q] = (T)(f->S_host[col] * hv[q]);
-            hb[q] = (T)(f->S_host[col] * hw[q]);
-            fval += hw[q] * f->S_host[col] * hv[q];
+            const double sc = P.Spad[col];
+            ha[q] = (T)(sc * hv[q]);
+            hb[q] = (T)(sc * hw[q]);
+            fval += hw[q] * sc * hv[q];
         }
     HDF_CUDA(cudaMemcpyAsync(a, ha.data(), sizeof(T) * ha.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(b, hb.data(), sizeof(T) * hb.size(), cudaMemcpyHostToDevice, st));
@@ -378,14 +379,15 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
             const int sk = P.sk[k];
             if (sk == 0) continue;
             const int dim = (int)hdf::harmonic_count(k, d);
+            const int dimp = (k + 1 < (int)P.cbase.size() && sk > 0) ? (P.cbase[k + 1] - P.cbase[k]) / sk : dim;
             const std::vector<double>& dS = P.dSk[k];
             for (int j = 0; j < ncols; ++j)
                 for (int h = 0; h < dim; ++h)
                     for (int s_ = 0; s_ < sk; ++s_) {
-                        const int64_t cs = P.cbase[k] + (int64_t)s_ * dim + h;
+                        const int64_t cs = P.cbase[k] + (int64_t)s_ * dimp + h;
                         double acc = 0.0;
                         for (int t_ = 0; t_ < sk; ++t_) {
-                            const int64_t ct = P.cbase[k] + (int64_t)t_ * dim + h;
+                            const int64_t ct = P.cbase[k] + (int64_t)t_ * dimp + h;
                             acc += dS[(size_t)s_ * sk + t_] * hv[(size_t)ct * ncols + j];
                         }
                         gl += hw[(size_t)cs * ncols + j] * acc;

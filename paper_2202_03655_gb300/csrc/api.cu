@@ -132,10 +132,20 @@ hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void
 
 hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) {
     if (!f) return fail(HDF_EINVAL, "hdf_factor_export: null factor");
-    const int64_t n = f->info.n, r = f->info.rank;
+    const int64_t n = f->info.n, r = f->info.rank, ld = f->info.ldu;
     if (U_host && r > 0) {
-        HDF_CUDA(cudaMemcpy2D(U_host, r * f->esz, f->U.p, f->info.ldu * f->esz, r * f->esz, n,
-                              cudaMemcpyDeviceToHost));
+        // U is stored with zero padding columns; gather the true columns row by row
+        std::vector<unsigned char> row((size_t)ld * f->esz * 1024);
+        unsigned char* out = static_cast<unsigned char*>(U_host);
+        for (int64_t i0 = 0; i0 < n; i0 += 1024) {
+            const int64_t cnt = std::min<int64_t>(1024, n - i0);
+            HDF_CUDA(cudaMemcpy(row.data(), f->U.as<unsigned char>() + (size_t)i0 * ld * f->esz,
+                                (size_t)cnt * ld * f->esz, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < cnt; ++i)
+                for (int64_t t = 0; t < r; ++t)
+                    std::memcpy(out + ((size_t)(i0 + i) * r + t) * f->esz,
+                                row.data() + ((size_t)i * ld + f->plan.colmap[t]) * f->esz, f->esz);
+        }
     }
     if (S_host && r > 0) std::memcpy(S_host, f->S_host.data(), r * sizeof(double));
     return HDF_OK;
@@ -245,31 +255,26 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     tph[1] = now_ms() - t0;
     t0 = now_ms();
 
-    // ---- A3: Gram matrices of the radial basis (FP64 on the device)
-    const int nb0 = L + 1;
-    const int npairs = nb0 * (nb0 + 1) / 2;
-    std::vector<uint16_t> pairs;
-    for (int l = 0; l < nb0; ++l)
-        for (int lp = l; lp < nb0; ++lp) { pairs.push_back((uint16_t)l); pairs.push_back((uint16_t)lp); }
-    const int ggram = grid_for(n, 4096, 2 * 152);
-    const int64_t gchunk = (n + ggram - 1) / ggram;
-    DevBuf dpairs, gpart, gsumd;
-    HDF_CUDA(dpairs.alloc(pairs.size() * sizeof(uint16_t)));
-    HDF_CUDA(gpart.alloc(sizeof(double) * (size_t)ggram * 2 * npairs));
-    HDF_CUDA(gsumd.alloc(sizeof(double) * 2 * npairs));
-    HDF_CUDA(cudaMemcpyAsync(dpairs.p, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-    const size_t gsm = sizeof(double) * (dev::kGramTile * (L + 1) + dev::kGramTile);
+    // ---- A3: Chebyshev moments of the radial data (FP64 on the device) -> basis Gram matrices
+    const int nmom = 2 * L + 2;
+    const int gmom = grid_for(n, 8192, 2 * 152);
+    const int64_t mchunk = (n + gmom - 1) / gmom;
+    DevBuf mpart, msum;
+    HDF_CUDA(mpart.alloc_on(sizeof(double) * (size_t)gmom * nmom, st));
+    HDF_CUDA(msum.alloc_on(sizeof(double) * nmom, st));
+    const size_t msm = sizeof(double) * dev::kMomTile * nmom;
     HDF_COUNT_LAUNCH();
-    dev::k_radial_gram<<<ggram, 256, gsm, st>>>(x_dev, n, d, gchunk, cen, inv2R, L, dpairs.as<uint16_t>(),
-                                                 npairs, gpart.as<double>());
+    dev::k_radial_moments<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
     HDF_CUDA(cudaGetLastError());
     HDF_COUNT_LAUNCH();
-    dev::k_reduce_cols<<<grid_for(2 * npairs, 256, 1 << 20), 256, 0, st>>>(gpart.as<double>(), ggram,
-                                                                          2 * npairs, gsumd.as<double>());
+    dev::k_reduce_cols<<<grid_for(nmom, 256, 1 << 20), 256, 0, st>>>(mpart.as<double>(), gmom, nmom,
+                                                                    msum.as<double>());
     HDF_CUDA(cudaGetLastError());
-    std::vector<double> gram(2 * npairs);
-    HDF_CUDA(cudaMemcpyAsync(gram.data(), gsumd.p, gram.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> mom(nmom);
+    HDF_CUDA(cudaMemcpyAsync(mom.data(), msum.p, nmom * sizeof(double), cudaMemcpyDeviceToHost, st));
     HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> gram;
+    gram_from_moments(mom, L, gram);
     tph[2] = now_ms() - t0;
     t0 = now_ms();
 
@@ -375,7 +380,8 @@ constexpr int kMaxGroup = 64;
 template <typename T>
 static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy,
                            const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.rank;
+    // the GEMMs run over all ldu columns of U; padding columns are zero and carry S = 0
+    const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
     const T* U = f->U.as<T>();
     if (r == 0) {
         for (int j = 0; j < ncols; ++j) {
@@ -473,7 +479,7 @@ namespace hdf {
 template <typename T>
 hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const T* S_scale, T* W, double* Wd,
                       cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.rank;
+    const int64_t n = f->info.n, r = f->info.ldu;      // padded width (rows of W)
     if (c < 1 || c > kMaxGroup) return fail(HDF_EINVAL, "utv_reduce: 1 <= c <= 64");
     const int nchunk = utv_chunks(n, r, c);
     const int64_t chunk = (n + nchunk - 1) / nchunk;
@@ -552,7 +558,7 @@ static void lu_solve(int64_t r, const std::vector<double>& A, const std::vector<
 template <typename T>
 static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int64_t ldb, int ncols, T* Xout,
                                  int64_t ldx, cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.rank;
+    const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
     const T* U = f->U.as<T>();
     if (r == 0) {
         HDF_COUNT_LAUNCH();
@@ -598,8 +604,8 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
 template <typename T>
 static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb, int ncols, T* X, int64_t ldx,
                           int refine, cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.rank;
-    if (r > 4096) return fail(HDF_ETOOBIG, "hdf_solve: rank > 4096");
+    const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
+    if (r > 4096) return fail(HDF_ETOOBIG, "hdf_solve: padded rank > 4096");
     if (r > 0 && f->G.empty()) {
         DevBuf Gd;
         HDF_CUDA(Gd.alloc(sizeof(double) * (size_t)r * r));
@@ -613,7 +619,11 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
     }
     if (r > 0 && f->core_lambda != lambda) {
         f->LU = f->G;
-        for (int64_t a = 0; a < r; ++a) f->LU[a * r + a] += lambda / f->S_host[a];
+        // padding columns (S = 0, zero columns of U) get a unit diagonal and solve to zero
+        for (int64_t a = 0; a < r; ++a) {
+            const double sa = f->plan.Spad[a];
+            f->LU[a * r + a] += (sa != 0.0) ? lambda / sa : 1.0;
+        }
         if (!lu_factor(r, f->LU, f->piv)) {
             f->core_lambda = -1.0;
             return fail(HDF_ESINGULAR, "hdf_solve: singular core lambda S^-1 + U^T U");
@@ -682,10 +692,12 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     std::string terr;
     if (!make_tables(fc, d, L, vw, tb, terr)) return fail(HDF_ETOOBIG, "hdf_build: " + terr);
     I.ldu = tb.ldU;
-    // S on the device
+    f->plan.colmap = tb.colmap;
+    f->plan.Spad = tb.Spad;
+    // S on the device, on the padded columns
     {
         std::vector<T> Sd(I.ldu, (T)0);
-        for (int64_t a = 0; a < r; ++a) Sd[a] = (T)f->S_host[a];
+        for (int64_t a = 0; a < I.ldu; ++a) Sd[a] = (T)tb.Spad[a];
         HDF_CUDA(f->S.alloc(sizeof(T) * I.ldu));
         HDF_CUDA(cudaMemcpyAsync(f->S.p, Sd.data(), sizeof(T) * I.ldu, cudaMemcpyHostToDevice, st));
     }
@@ -714,8 +726,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     PL.cbase = tb.cbase;
     PL.hbase = tb.hbase;
     DevBuf dpar, dF;
-    DevBuf &dQ0 = PL.dQ0, &dQ1 = PL.dQ1, &dW = PL.dW, &dchains = PL.dchains, &ddesc = PL.ddesc, &dA = PL.dA,
-           &dB = PL.dB;
+    DevBuf &dQ0 = PL.dQ0, &dQ1 = PL.dQ1, &dW = PL.dW, &dchains = PL.dchains, &dA = PL.dA, &dB = PL.dB;
     HDF_CUDA(PL.dcolk.alloc(tb.colk.size()));
     HDF_CUDA(PL.dhk.alloc(tb.hk.size() + 1));
     HDF_CUDA(PL.dktab.alloc(sizeof(int) * tb.ktab.size()));
@@ -727,7 +738,8 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(dW.alloc(sizeof(T) * Wt.size()));
     HDF_CUDA(dpar.alloc(tb.colpar.size()));
     HDF_CUDA(dchains.alloc(sizeof(int16_t) * std::max<size_t>(1, tb.chains.size())));
-    HDF_CUDA(ddesc.alloc(sizeof(uint32_t) * tb.desc.size()));
+    HDF_CUDA(PL.dqdesc.alloc(sizeof(uint32_t) * tb.qdesc.size()));
+    HDF_CUDA(PL.dychain.alloc(sizeof(int32_t) * tb.ychain.size()));
     HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
     HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
     const int64_t ldF = nF;
@@ -741,7 +753,8 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(cudaMemcpyAsync(dpar.p, tb.colpar.data(), tb.colpar.size(), cudaMemcpyHostToDevice, st));
     if (!tb.chains.empty())
         HDF_CUDA(cudaMemcpyAsync(dchains.p, tb.chains.data(), sizeof(int16_t) * tb.chains.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(cudaMemcpyAsync(ddesc.p, tb.desc.data(), sizeof(uint32_t) * tb.desc.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dqdesc.p, tb.qdesc.data(), sizeof(uint32_t) * tb.qdesc.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dychain.p, tb.ychain.data(), sizeof(int32_t) * tb.ychain.size(), cudaMemcpyHostToDevice, st));
     if (!cA.empty()) {
         HDF_CUDA(cudaMemcpyAsync(dA.p, cA.data(), sizeof(T) * cA.size(), cudaMemcpyHostToDevice, st));
         HDF_CUDA(cudaMemcpyAsync(dB.p, cB.data(), sizeof(T) * cB.size(), cudaMemcpyHostToDevice, st));
@@ -774,15 +787,16 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         P.x = x; P.n = n; P.d = d; P.c = cen; P.inv2R = inv2R;
         P.L = L_used; P.tri = ht.tri;
         P.chains = dchains.as<int16_t>(); P.nH = (int)nH;
-        P.desc = ddesc.as<uint32_t>(); P.nF = nF;
+        P.ychain = PL.dychain.as<int32_t>(); P.nYp = tb.nYp;
+        P.qdesc = PL.dqdesc.as<uint32_t>(); P.nF = nF;
         P.F = dF.p; P.ldF = ldF;
         P.U = f->U.p; P.ldU = I.ldu;
         P.coefA = dA.p; P.coefB = dB.p;
         const int levels = d - 2;
         const size_t fixed = sizeof(T) * 2 * levels * ht.tri;
         const size_t budget = 200 * 1024;
-        const int pw_fly = dev::uwriter_per_warp(levels, ht.tri, L_used, (int)nH, nF, false);
-        const int pw_pre = dev::uwriter_per_warp(levels, ht.tri, L_used, (int)nH, nF, true);
+        const int pw_fly = dev::uwriter_per_warp(levels, ht.tri, L_used, tb.nYp, nF, false);
+        const int pw_pre = dev::uwriter_per_warp(levels, ht.tri, L_used, tb.nYp, nF, true);
         const bool pre = fixed + sizeof(T) * 4 * (size_t)pw_pre <= budget;
         const int per_warp = pre ? pw_pre : pw_fly;
         P.per_warp = per_warp;

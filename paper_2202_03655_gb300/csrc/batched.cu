@@ -212,14 +212,14 @@ __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict_
         const int64_t t0 = (int64_t)w.y * dev::kFTile;
         dev::radialF_tile<T>(S.rf, t0, smem_raw);           // F rows of the tile (global)
         const int levels = S.uw.d - 2;
-        T* cA = reinterpret_cast<T*>(smem_raw);
+        T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * S.uw.per_warp;
+        T* cA = reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * S.uw.per_warp;
         T* cB = cA + levels * S.uw.tri;
         for (int idx = threadIdx.x; idx < levels * S.uw.tri; idx += blockDim.x) {
             cA[idx] = reinterpret_cast<const T*>(S.uw.coefA)[idx];
             cB[idx] = reinterpret_cast<const T*>(S.uw.coefB)[idx];
         }
         __syncthreads();
-        T* base = cB + levels * S.uw.tri + (size_t)warp * S.uw.per_warp;
         const int64_t t1 = min(t0 + dev::kFTile, S.uw.n);
         for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, S.pre != 0, i, cA, cB, base, lane);
         __syncthreads();
@@ -352,6 +352,7 @@ struct hdf_batch {
     std::vector<hdf_info> info;
     std::vector<std::vector<double>> S_host;
     std::vector<int64_t> uoff, soff;                // element offsets of U and S per set
+    std::vector<std::vector<int64_t>> colmap;       // per set: padded column of each true column
     DevBuf U, S, arena, dsets;
     // matvec state
     DevBuf mvsets, mvitems_utv, mvitems_red, mvitems_uw, mvpart, mvW, counters;
@@ -510,6 +511,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (!ok[s]) return fail(HDF_ETOOBIG, "hdf_build_batched: set " + std::to_string(s) + ": " + errs[s]);
     *all_reached = true;
     b->info.assign(ns, hdf_info{});
+    b->colmap.assign(ns, std::vector<int64_t>());
     b->S_host.assign(ns, std::vector<double>());
     b->uoff.assign(ns + 1, 0);
     b->soff.assign(ns + 1, 0);
@@ -540,7 +542,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (bytes) std::memcpy(arena.data() + o, src, bytes);
         return o;
     };
-    struct Offs { size_t q0, q1, w, par, ch, desc, ca, cb; };
+    struct Offs { size_t q0, q1, w, par, ch, qd, yc, ca, cb; };
     std::vector<Offs> offs(ns);
     std::vector<T> Sd(b->soff[ns], (T)0);
     for (int s = 0; s < ns; ++s) {
@@ -554,10 +556,12 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         offs[s].w = put(Wt.data(), sizeof(T) * Wt.size());
         offs[s].par = put(tb.colpar.data(), tb.colpar.size());
         offs[s].ch = put(tb.chains.data(), sizeof(int16_t) * tb.chains.size());
-        offs[s].desc = put(tb.desc.data(), sizeof(uint32_t) * tb.desc.size());
+        offs[s].qd = put(tb.qdesc.data(), sizeof(uint32_t) * tb.qdesc.size());
+        offs[s].yc = put(tb.ychain.data(), sizeof(int32_t) * tb.ychain.size());
         offs[s].ca = put(cA.data(), sizeof(T) * cA.size());
         offs[s].cb = put(cB.data(), sizeof(T) * cB.size());
-        for (int64_t a = 0; a < fc.rank; ++a) Sd[b->soff[s] + a] = (T)fc.S[a];
+        for (int64_t a = 0; a < tb.ldU; ++a) Sd[b->soff[s] + a] = (T)tb.Spad[a];
+        b->colmap[s] = tb.colmap;
     }
     HDF_CUDA(b->arena.alloc(arena.size()));
     HDF_CUDA(cudaMemcpyAsync(b->arena.p, arena.data(), arena.size(), cudaMemcpyHostToDevice, st));
@@ -595,14 +599,15 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         P.x = R.x; P.n = R.n; P.d = d; P.c = R.c; P.inv2R = R.inv2R;
         P.L = tb.L_used; P.tri = tb.tri;
         P.chains = reinterpret_cast<const int16_t*>(A + offs[s].ch); P.nH = tb.nH;
-        P.desc = reinterpret_cast<const uint32_t*>(A + offs[s].desc); P.nF = tb.nF;
+        P.ychain = reinterpret_cast<const int32_t*>(A + offs[s].yc); P.nYp = tb.nYp;
+        P.qdesc = reinterpret_cast<const uint32_t*>(A + offs[s].qd); P.nF = tb.nF;
         P.F = R.F; P.ldF = R.ldF;
         P.U = b->U.as<T>() + b->uoff[s]; P.ldU = tb.ldU;
         P.coefA = A + offs[s].ca; P.coefB = A + offs[s].cb;
         const int levels = d - 2;
         const size_t fixed = sizeof(T) * 2 * levels * tb.tri;
-        const int pw_pre = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nH, tb.nF, true);
-        const int pw_fly = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nH, tb.nF, false);
+        const int pw_pre = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nYp, tb.nF, true);
+        const int pw_fly = dev::uwriter_per_warp(levels, tb.tri, tb.L_used, tb.nYp, tb.nF, false);
         const bool pre = fixed + sizeof(T) * 8 * (size_t)pw_pre <= budget / 2;
         bs[s].pre = pre ? 1 : 0;
         P.per_warp = pre ? pw_pre : pw_fly;
@@ -699,7 +704,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
         for (int s = 0; s < ns; ++s) {
-            const int64_t n = b->info[s].n, r = b->info[s].rank;
+            const int64_t n = b->info[s].n, r = (b->info[s].rank > 0) ? b->info[s].ldu : 0;   // padded width
             ms[s].n = n; ms[s].r = r; ms[s].ldU = b->info[s].ldu; ms[s].off = b->off[s];
             ms[s].chunk = 4096;
             ms[s].nchunk = (int)std::max<int64_t>(1, (n + ms[s].chunk - 1) / ms[s].chunk);
@@ -841,9 +846,15 @@ hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S
     if (!b || set < 0 || set >= b->nsets) return fail(HDF_EINVAL, "hdf_batch_export: bad argument");
     const hdf_info& I = b->info[set];
     if (U_host && I.rank > 0) {
+        std::vector<unsigned char> pad((size_t)I.n * I.ldu * b->esz);
         const unsigned char* src = b->U.as<unsigned char>() + b->uoff[set] * b->esz;
-        HDF_CUDA(cudaMemcpy2D(U_host, I.rank * b->esz, src, I.ldu * b->esz, I.rank * b->esz, I.n,
-                              cudaMemcpyDeviceToHost));
+        HDF_CUDA(cudaMemcpy(pad.data(), src, pad.size(), cudaMemcpyDeviceToHost));
+        unsigned char* out = static_cast<unsigned char*>(U_host);
+        const std::vector<int64_t>& cm = b->colmap[set];
+        for (int64_t i = 0; i < I.n; ++i)
+            for (int64_t t = 0; t < I.rank; ++t)
+                std::memcpy(out + ((size_t)i * I.rank + t) * b->esz, pad.data() + ((size_t)i * I.ldu + cm[t]) * b->esz,
+                            b->esz);
     }
     if (S_host && I.rank > 0) std::memcpy(S_host, b->S_host[set].data(), sizeof(double) * I.rank);
     return HDF_OK;

@@ -168,6 +168,53 @@ static __global__ void __launch_bounds__(256) k_radial_gram(const double* __rest
     }
 }
 
+// Chebyshev moments of the radial data: part[b][j] = sum over the block's chunk of T_j(u_i),
+// u_i = 8 rho_i^2 - 1, j < nmom.  The radial-basis Gram matrices follow from them exactly
+// (T_l T_l' = (T_{l+l'} + T_{|l-l'|}) / 2 and u T_j = (T_{j+1} + T_{|j-1|}) / 2), so the Gram
+// costs O(n L) instead of O(n L^2).
+constexpr int kMomTile = 64;
+
+static __global__ void __launch_bounds__(256) k_radial_moments(const double* __restrict__ x, int64_t n, int d,
+                                                               int64_t chunk, Center c, double inv2R, int nmom,
+                                                               double* __restrict__ part) {
+    extern __shared__ double smem[];
+    double* Ts = smem;                          // [kMomTile][nmom]
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    double acc0 = 0.0, acc1 = 0.0;              // moments threadIdx.x and threadIdx.x + 256
+    for (int64_t t0 = i0; t0 < i1; t0 += kMomTile) {
+        const int cnt = (int)min((int64_t)kMomTile, i1 - t0);
+        if (threadIdx.x < kMomTile) {
+            const int p = threadIdx.x;
+            double* T = Ts + p * nmom;
+            if (p < cnt) {
+                const int64_t i = t0 + p;
+                double s = 0.0;
+                for (int j = 0; j < d; ++j) { const double y = (x[i * d + j] - c.c[j]) * inv2R; s += y * y; }
+                const double u = 8.0 * s - 1.0;
+                T[0] = 1.0;
+                if (nmom > 1) T[1] = u;
+                for (int l = 2; l < nmom; ++l) T[l] = 2.0 * u * T[l - 1] - T[l - 2];
+            } else {
+                for (int l = 0; l < nmom; ++l) T[l] = 0.0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nmom) {
+            double s = 0.0;
+            for (int p = 0; p < cnt; ++p) s += Ts[p * nmom + threadIdx.x];
+            acc0 += s;
+        }
+        if (threadIdx.x + 256 < nmom) {
+            double s = 0.0;
+            for (int p = 0; p < cnt; ++p) s += Ts[p * nmom + threadIdx.x + 256];
+            acc1 += s;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < nmom) part[(int64_t)blockIdx.x * nmom + threadIdx.x] = acc0;
+    if (threadIdx.x + 256 < nmom) part[(int64_t)blockIdx.x * nmom + threadIdx.x + 256] = acc1;
+}
+
 // out[j] = sum_b part[b * ncols + j] in block order.
 static __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, int64_t ncols,
                               double* __restrict__ out) {
@@ -278,7 +325,9 @@ struct UWParams {
     int tri;                   // (L+1)(L+2)/2
     const int16_t* chains;     // nH x (d-1)
     int nH;
-    const uint32_t* desc;      // ldU entries: (fidx << 20) | hidx ; padding -> fidx = nF
+    const int32_t* ychain;     // nYp padded harmonic slots -> chain (-1: padding)
+    int nYp;
+    const uint32_t* qdesc;     // ldU / VW chunks: (F index << 20) | first harmonic slot
     int nF;
     const void* F; int64_t ldF;
     void* U; int64_t ldU;
@@ -286,18 +335,25 @@ struct UWParams {
     int per_warp;              // shared elements (type T) per warp
 };
 
+// Shared elements (type T) per warp of the U writer (a multiple of 16 bytes).
+__host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int nYp, int nF, bool pre) {
+    return ((levels * tri + 2 * L + 1 + (pre ? nYp : 0) + nF + 1) + 3) & ~3;
+}
+
 // One point's U row, executed by one warp.  cA/cB: level recurrences in shared memory;
-// base: this warp's shared area (P.per_warp elements).  pre: harmonics precomputed per point
-// into shared memory (nH values); otherwise each column's harmonic is multiplied out from
-// the level tables as it is written.
+// base: this warp's shared area (P.per_warp elements, 16-byte aligned), laid out as
+// [harmonic slots (pre only)] [level tables] [trig powers] [radial factors].  pre: the
+// harmonics of the point are computed once into the slots; otherwise each chunk's harmonics
+// are multiplied out from the level tables as it is written.  Every VW-wide chunk of the row
+// is one radial factor times VW consecutive harmonic slots (columns are padded per (k, s)).
 template <typename T>
 __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64_t i, const T* cA, const T* cB,
                                               T* base, int lane) {
     const int levels = P.d - 2;
-    T* tbl = base;                               // levels * tri
+    T* Ys = base;                                // nYp (pre only)
+    T* tbl = base + (pre ? P.nYp : 0);           // levels * tri
     T* trig = tbl + levels * P.tri;              // 2L+1, index L + mu
-    T* Ys = trig + 2 * P.L + 1;                  // nH (pre only)
-    T* Fs = Ys + (pre ? P.nH : 0);               // nF + 1
+    T* Fs = trig + 2 * P.L + 1;                  // nF + 1
     const T* Fg = reinterpret_cast<const T*>(P.F);
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
@@ -359,56 +415,65 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
     if (lane == 0) Fs[P.nF] = (T)0;
     __syncwarp();
     if (pre) {
-        for (int g = lane; g < P.nH; g += 32) {
-            const int16_t* ch = P.chains + (int64_t)g * (levels + 1);
-            T v = trig[P.L + ch[levels]];
-            for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + ch[j]];
+        for (int g = lane; g < P.nYp; g += 32) {
+            const int ch = __ldg(P.ychain + g);
+            T v = (T)0;
+            if (ch >= 0) {
+                const int16_t* c = P.chains + (int64_t)ch * (levels + 1);
+                v = trig[P.L + c[levels]];
+                for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + c[j]];
+            }
             Ys[g] = v;
         }
     }
     __syncwarp();
-    // row write, VW consecutive columns per lane per step
+    // row write: one VW-wide chunk per lane per step
     T* row = Ug + i * P.ldU;
-    for (int64_t c0 = (int64_t)lane * VW; c0 < P.ldU; c0 += 32 * VW) {
-        T v[VW];
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const uint32_t dsc = __ldg(P.desc + c0 + e);
-            if (pre) {
-                v[e] = Fs[dsc >> 20] * Ys[dsc & 0xFFFFFu];
-            } else {
-                const int16_t* ch = P.chains + (int64_t)(dsc & 0xFFFFFu) * (levels + 1);
-                T h = trig[P.L + __ldg(ch + levels)];
-                for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(ch + j)];
-                v[e] = Fs[dsc >> 20] * h;
-            }
-        }
+    const int64_t nq = P.ldU / VW;
+    for (int64_t q = lane; q < nq; q += 32) {
+        const uint32_t dsc = __ldg(P.qdesc + q);
+        const T f = Fs[dsc >> 20];
+        const uint32_t y0 = dsc & 0xFFFFFu;
         VT out;
-        if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
-        else { out.x = v[0]; out.y = v[1]; }
-        *reinterpret_cast<VT*>(row + c0) = out;
+        if (pre) {
+            const VT yv = *reinterpret_cast<const VT*>(Ys + y0);
+            if constexpr (VW == 4) { out.x = f * yv.x; out.y = f * yv.y; out.z = f * yv.z; out.w = f * yv.w; }
+            else { out.x = f * yv.x; out.y = f * yv.y; }
+        } else {
+            T v[VW];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const int ch = __ldg(P.ychain + y0 + e);
+                T h = (T)0;
+                if (ch >= 0) {
+                    const int16_t* c = P.chains + (int64_t)ch * (levels + 1);
+                    h = trig[P.L + __ldg(c + levels)];
+                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(c + j)];
+                }
+                v[e] = f * h;
+            }
+            if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
+            else { out.x = v[0]; out.y = v[1]; }
+        }
+        *reinterpret_cast<VT*>(row + q * VW) = out;
     }
     __syncwarp();
 }
 
-// Shared elements (type T) per warp of the U writer.
-__host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int nH, int nF, bool pre) {
-    return ((levels * tri + 2 * L + 1 + (pre ? nH : 0) + nF + 1) + 3) & ~3;
-}
-
+// Shared memory of the U writer: [nwarps x per_warp][coefA][coefB] (elements of T).
 template <typename T, bool PRE>
 __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int levels = P.d - 2;
-    T* cA = reinterpret_cast<T*>(smem_raw);
-    T* cB = cA + levels * P.tri;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * P.per_warp;
+    T* cA = reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * P.per_warp;
+    T* cB = cA + levels * P.tri;
     for (int idx = threadIdx.x; idx < levels * P.tri; idx += blockDim.x) {
         cA[idx] = reinterpret_cast<const T*>(P.coefA)[idx];
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
     __syncthreads();
-    T* base = cB + levels * P.tri + (size_t)warp * P.per_warp;
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
     for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, PRE, i, cA, cB, base, lane);
 }

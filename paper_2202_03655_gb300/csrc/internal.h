@@ -92,9 +92,12 @@ struct FactorPlan {
     std::vector<std::vector<double>> Wk;       // kept eigenvectors per k (m x s_k, row-major)
     std::vector<int> sk, fbase, cbase, hbase;  // per k: kept count, F column, U column, harmonic bases
     // device copies: Qmat0, Qmat1 (FP64), Wt (m_max x nF, bulk), colk (F column -> k),
-    // chains (nH x (d-1) int16), hk (harmonic -> k), ktab (per k: fbase, s_k, cbase, |H_k|, hbase),
-    // desc (ldU column descriptors), coefA/coefB (level recurrences, bulk)
-    DevBuf dQ0, dQ1, dW, dcolk, dchains, dhk, dktab, ddesc, dA, dB;
+    // chains (nH x (d-1) int16), hk (harmonic -> k), ktab (per k: fbase, s_k, cbase, |H_k|, hbase,
+    // padded |H_k|), qdesc (chunk descriptors), ychain (padded harmonic slots -> chain),
+    // coefA/coefB (level recurrences, bulk)
+    DevBuf dQ0, dQ1, dW, dcolk, dchains, dhk, dktab, dqdesc, dychain, dA, dB;
+    std::vector<int64_t> colmap;               // padded column of each true column of U
+    std::vector<double> Spad;                  // S on the padded columns (0 on padding)
     // d S_k / d l (s_k x s_k), computed on first use by the adjoint
     std::vector<std::vector<double>> dSk;
     bool have_dS = false;

@@ -78,7 +78,7 @@ void uw(int ct, const T* U, int64_t ldU, int64_t n, int64_t r, const T* W, int c
 
 template <typename T>
 hdf_status run(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy, cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.rank;
+    const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;   // padded width of U
     if (r == 0) {
         for (int j = 0; j < ncols; ++j) HDF_CUDA(cudaMemsetAsync(Y + j * ldy, 0, n * sizeof(T), st));
         return HDF_OK;

@@ -332,6 +332,23 @@ void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double
     radial_cores(out.a.data(), out.p, d, out.cores, threads);
 }
 
+void gram_from_moments(const std::vector<double>& m, int L, std::vector<double>& gram) {
+    const int nb0 = L + 1;
+    const int npairs = nb0 * (nb0 + 1) / 2;
+    gram.assign(2 * (size_t)npairs, 0.0);
+    auto M = [&](int j) { return m[std::abs(j)]; };
+    auto prodsum = [&](int l, int lp) { return 0.5 * (M(l + lp) + M(l - lp)); };          // sum T_l T_l'
+    auto uprod = [&](int j) { return 0.5 * (M(j + 1) + M(j - 1)); };                       // sum u T_j
+    int q = 0;
+    for (int l = 0; l < nb0; ++l)
+        for (int lp = l; lp < nb0; ++lp, ++q) {
+            gram[q] = prodsum(l, lp);
+            // sum rho^2 T_l T_l' = (1/8) sum (u + 1) T_l T_l'
+            const double su = 0.5 * (uprod(l + lp) + uprod(l - lp));
+            gram[(size_t)npairs + q] = 0.125 * (su + prodsum(l, lp));
+        }
+}
+
 void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
                  double drop_budget, bool threads, FactorChoice& out) {
     const int nb0 = L + 1, nb1 = L;
@@ -447,7 +464,6 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     const std::vector<int>& sk = fc.sk;
     t.L_used = 0;
     for (int k = 0; k <= L; ++k) if (sk[k] > 0) t.L_used = k;
-    t.ldU = std::max<int64_t>(vw, ((fc.rank + vw - 1) / vw) * vw);
     t.fbase.assign(L + 2, 0);
     for (int k = 0; k <= L; ++k) t.fbase[k + 1] = t.fbase[k] + sk[k];
     t.nF = t.fbase[L + 1];
@@ -469,39 +485,60 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     t.coefB = ht.coefB;
     t.chains.clear();
     t.hbase.assign(L + 2, 0);
+    std::vector<int> yoff(L + 2, 0), dimp(L + 1, 0);
     for (int k = 0; k <= L; ++k) {
         t.hbase[k + 1] = t.hbase[k];
+        yoff[k + 1] = yoff[k];
         if (sk[k] == 0) continue;
         append_chains(k, d, t.L_used, t.chains);
-        t.hbase[k + 1] += (int)ht.count[k];
+        const int dim = (int)ht.count[k];
+        dimp[k] = ((dim + vw - 1) / vw) * vw;
+        t.hbase[k + 1] += dim;
+        yoff[k + 1] += dimp[k];
     }
     t.nH = t.hbase[L + 1];
-    if (t.nH >= (1 << 20) || t.nF >= 4095) {
+    t.nYp = yoff[L + 1];
+    if (t.nYp >= (1 << 20) || t.nF >= 4095) {
         err = "too many harmonics or radial columns for the column descriptors";
         return false;
     }
     t.hk.assign(std::max(1, t.nH), 0);
-    t.ktab.assign(5 * (L + 1), 0);
+    t.ktab.assign(kTabStride * (L + 1), 0);
     t.cbase.assign(L + 2, 0);
+    t.ychain.assign(std::max(1, t.nYp), -1);
     for (int k = 0; k <= L; ++k) {
-        for (int g = t.hbase[k]; g < t.hbase[k + 1]; ++g) t.hk[g] = (uint8_t)k;
+        for (int g = t.hbase[k]; g < t.hbase[k + 1]; ++g) {
+            t.hk[g] = (uint8_t)k;
+            t.ychain[yoff[k] + (g - t.hbase[k])] = g;
+        }
         const int hkc = (sk[k] > 0) ? (int)ht.count[k] : 0;
-        t.cbase[k + 1] = t.cbase[k] + hkc * sk[k];
-        t.ktab[5 * k + 0] = t.fbase[k];
-        t.ktab[5 * k + 1] = sk[k];
-        t.ktab[5 * k + 2] = t.cbase[k];
-        t.ktab[5 * k + 3] = hkc;
-        t.ktab[5 * k + 4] = t.hbase[k];
+        t.cbase[k + 1] = t.cbase[k] + dimp[k] * sk[k];
+        int* kt = &t.ktab[kTabStride * k];
+        kt[0] = t.fbase[k];
+        kt[1] = sk[k];
+        kt[2] = t.cbase[k];
+        kt[3] = hkc;
+        kt[4] = t.hbase[k];
+        kt[5] = dimp[k];
     }
-    t.desc.assign(t.ldU, 0);
-    int64_t col = 0;
+    t.ldU = std::max<int64_t>(vw, t.cbase[L + 1]);
+    t.qdesc.assign(t.ldU / vw, (uint32_t)t.nF << 20);    // F index nF (a zero slot) for padding
+    t.colmap.clear();
+    t.Spad.assign(t.ldU, 0.0);
+    int64_t tcol = 0;
     for (int k = 0; k <= L; ++k) {
         if (sk[k] == 0) continue;
-        for (int s = 0; s < sk[k]; ++s)
-            for (int h = 0; h < (int)ht.count[k]; ++h)
-                t.desc[col++] = ((uint32_t)(t.fbase[k] + s) << 20) | (uint32_t)(t.hbase[k] + h);
+        const int dim = (int)ht.count[k];
+        for (int s = 0; s < sk[k]; ++s) {
+            const int64_t c0 = t.cbase[k] + (int64_t)s * dimp[k];
+            for (int q = 0; q < dimp[k] / vw; ++q)
+                t.qdesc[(c0 / vw) + q] = ((uint32_t)(t.fbase[k] + s) << 20) | (uint32_t)(yoff[k] + q * vw);
+            for (int h = 0; h < dim; ++h) {
+                t.colmap.push_back(c0 + h);
+                t.Spad[c0 + h] = fc.S[tcol++];
+            }
+        }
     }
-    for (; col < t.ldU; ++col) t.desc[col] = ((uint32_t)t.nF << 20);
     return true;
 }
 

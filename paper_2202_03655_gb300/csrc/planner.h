@@ -75,6 +75,11 @@ struct DegreePlan {
 void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double tol, double eta, int p_max,
                  int d, bool threads, DegreePlan& out);
 
+// Radial-basis Gram sums (the layout plan_factor takes) from the Chebyshev moments
+// m_j = sum_i T_j(u_i), j <= 2L+1, using T_l T_l' = (T_{l+l'} + T_{|l-l'|})/2 and
+// rho^2 = (u + 1)/8, u T_j = (T_{j+1} + T_{|j-1|})/2.
+void gram_from_moments(const std::vector<double>& m, int L, std::vector<double>& gram);
+
 // A3-A4 for one problem from the radial-basis Gram sums (2 x npairs, pairs (l <= l') of the
 // even basis in row order; the odd basis uses the leading L x L block of the second half):
 // basis factor B = Q R_f (R_f = D^1/2 V^T, directions below 1e-13 nb lambda_max dropped),
@@ -92,17 +97,26 @@ void plan_factor(const std::vector<double>& gram, int L, int d, const std::vecto
                  double drop_budget, bool threads, FactorChoice& out);
 
 // Host images of the tables the device kernels read (FP64; cast to the bulk type on upload).
+// U's columns come in blocks (k, s) of |H_k| harmonics, each block padded with zero columns
+// to a multiple of vw (16 bytes) so that every vw-wide chunk of a row holds one radial factor
+// times vw consecutive harmonics; the padded columns carry S = 0 and leave K~ unchanged.
+// Per point the harmonics are laid out the same way (Y index yoff_k + h, padded per k).
 struct DeviceTables {
-    int L_used = 0, tri = 0, nF = 0, nH = 0, mmax = 0;
-    int64_t ldU = 0;
+    int L_used = 0, tri = 0, nF = 0, nH = 0, mmax = 0, nYp = 0;
+    int64_t ldU = 0;                         // padded width of U (a multiple of vw)
     std::vector<double> Wt;                  // mmax x nF
     std::vector<uint8_t> colpar, colk, hk;
-    std::vector<int16_t> chains;
-    std::vector<uint32_t> desc;              // ldU
+    std::vector<int16_t> chains;             // nH x (d-1)
+    std::vector<int32_t> ychain;             // nYp: chain of each padded Y slot, -1 for padding
+    std::vector<uint32_t> qdesc;             // ldU / vw: (F index << 20) | first Y index of the chunk
+    std::vector<int64_t> colmap;             // rank: padded column of each true column
+    std::vector<double> Spad;                // ldU: S on the padded columns (0 on padding)
     std::vector<double> coefA, coefB;
-    std::vector<int> ktab, fbase, cbase, hbase;
+    std::vector<int> ktab;                   // per k: fbase, s_k, cbase, |H_k|, hbase, padded |H_k|
+    std::vector<int> fbase, cbase, hbase;
 };
-// vw: elements per 16 bytes of the bulk type (ldU is a multiple).  False if a limit is exceeded.
+// vw: elements per 16 bytes of the bulk type.  False if a limit is exceeded.
 bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& out, std::string& err);
+constexpr int kTabStride = 6;               // ints per k in DeviceTables::ktab
 
 }  // namespace hdf
