@@ -36,7 +36,7 @@ struct AdjParams {
     const double* Qm0; int nb0, m0;
     const double* Qm1; int nb1, m1;
     const T* Wt; const uint8_t* colk; int nF;
-    const int16_t* chains; int nH; const uint8_t* hk; const int* ktab;
+    const int16_t* chains; int nH, cstride; const uint8_t* hk; const int* ktab;
     const T* coefA; const T* coefB;
     const T* a; const T* b; int ab_stride;        // a[col * ab_stride], b[col * ab_stride]
     const T* v; const T* w;                        // this column of V and W (length n)
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
                 al += cc * R1[fb + s];
                 be += cc * R2[fb + s];
             }
-            const int16_t* ch = P.chains + (int64_t)gi * (levels + 1);
+            const int16_t* ch = P.chains + (int64_t)gi * P.cstride;
             const int tmu = ch[levels];
             T pvv[kMaxD], pzz[kMaxD], pqq[kMaxD];
             T prod = trig[P.L + tmu];
@@ -347,7 +347,8 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
     A.Qm0 = P.dQ0.as<double>(); A.nb0 = P.nb[0]; A.m0 = P.m[0];
     A.Qm1 = P.dQ1.as<double>(); A.nb1 = P.nb[1]; A.m1 = P.m[1];
     A.Wt = P.dW.as<T>(); A.colk = P.dcolk.as<uint8_t>(); A.nF = P.nF;
-    A.chains = P.dchains.as<int16_t>(); A.nH = P.nH; A.hk = P.dhk.as<uint8_t>(); A.ktab = P.dktab.as<int>();
+    A.chains = P.dchains.as<int16_t>(); A.nH = P.nH; A.cstride = hdf::chain_stride(d);
+    A.hk = P.dhk.as<uint8_t>(); A.ktab = P.dktab.as<int>();
     A.coefA = P.dA.as<T>(); A.coefB = P.dB.as<T>();
     A.grad = grad;
     const int levels = d - 2;

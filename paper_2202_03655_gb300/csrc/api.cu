@@ -740,6 +740,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(dchains.alloc(sizeof(int16_t) * std::max<size_t>(1, tb.chains.size())));
     HDF_CUDA(PL.dqdesc.alloc(sizeof(uint32_t) * tb.qdesc.size()));
     HDF_CUDA(PL.dychain.alloc(sizeof(int32_t) * tb.ychain.size()));
+    HDF_CUDA(PL.dgslot.alloc(sizeof(int32_t) * tb.gslot.size()));
     HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
     HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
     const int64_t ldF = nF;
@@ -755,6 +756,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaMemcpyAsync(dchains.p, tb.chains.data(), sizeof(int16_t) * tb.chains.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(PL.dqdesc.p, tb.qdesc.data(), sizeof(uint32_t) * tb.qdesc.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(PL.dychain.p, tb.ychain.data(), sizeof(int32_t) * tb.ychain.size(), cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(PL.dgslot.p, tb.gslot.data(), sizeof(int32_t) * tb.gslot.size(), cudaMemcpyHostToDevice, st));
     if (!cA.empty()) {
         HDF_CUDA(cudaMemcpyAsync(dA.p, cA.data(), sizeof(T) * cA.size(), cudaMemcpyHostToDevice, st));
         HDF_CUDA(cudaMemcpyAsync(dB.p, cB.data(), sizeof(T) * cB.size(), cudaMemcpyHostToDevice, st));
@@ -786,8 +788,8 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         dev::UWParams P{};
         P.x = x; P.n = n; P.d = d; P.c = cen; P.inv2R = inv2R;
         P.L = L_used; P.tri = ht.tri;
-        P.chains = dchains.as<int16_t>(); P.nH = (int)nH;
-        P.ychain = PL.dychain.as<int32_t>(); P.nYp = tb.nYp;
+        P.chains = dchains.as<int16_t>(); P.nH = (int)nH; P.cstride = chain_stride(d);
+        P.ychain = PL.dychain.as<int32_t>(); P.nYp = tb.nYp; P.gslot = PL.dgslot.as<int32_t>();
         P.qdesc = PL.dqdesc.as<uint32_t>(); P.nF = nF;
         P.F = dF.p; P.ldF = ldF;
         P.U = f->U.p; P.ldU = I.ldu;

@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict_
             cB[idx] = reinterpret_cast<const T*>(S.uw.coefB)[idx];
         }
         __syncthreads();
+        dev::uwriter_zero_slots<T>(S.uw, S.pre != 0, base, lane);     // slots of this set's layout
         const int64_t t1 = min(t0 + dev::kFTile, S.uw.n);
         for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, S.pre != 0, i, cA, cB, base, lane);
         __syncthreads();
@@ -542,7 +543,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (bytes) std::memcpy(arena.data() + o, src, bytes);
         return o;
     };
-    struct Offs { size_t q0, q1, w, par, ch, qd, yc, ca, cb; };
+    struct Offs { size_t q0, q1, w, par, ch, qd, yc, gs, ca, cb; };
     std::vector<Offs> offs(ns);
     std::vector<T> Sd(b->soff[ns], (T)0);
     for (int s = 0; s < ns; ++s) {
@@ -558,6 +559,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         offs[s].ch = put(tb.chains.data(), sizeof(int16_t) * tb.chains.size());
         offs[s].qd = put(tb.qdesc.data(), sizeof(uint32_t) * tb.qdesc.size());
         offs[s].yc = put(tb.ychain.data(), sizeof(int32_t) * tb.ychain.size());
+        offs[s].gs = put(tb.gslot.data(), sizeof(int32_t) * tb.gslot.size());
         offs[s].ca = put(cA.data(), sizeof(T) * cA.size());
         offs[s].cb = put(cB.data(), sizeof(T) * cB.size());
         for (int64_t a = 0; a < tb.ldU; ++a) Sd[b->soff[s] + a] = (T)tb.Spad[a];
@@ -598,8 +600,9 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         dev::UWParams& P = bs[s].uw;
         P.x = R.x; P.n = R.n; P.d = d; P.c = R.c; P.inv2R = R.inv2R;
         P.L = tb.L_used; P.tri = tb.tri;
-        P.chains = reinterpret_cast<const int16_t*>(A + offs[s].ch); P.nH = tb.nH;
+        P.chains = reinterpret_cast<const int16_t*>(A + offs[s].ch); P.nH = tb.nH; P.cstride = chain_stride(d);
         P.ychain = reinterpret_cast<const int32_t*>(A + offs[s].yc); P.nYp = tb.nYp;
+        P.gslot = reinterpret_cast<const int32_t*>(A + offs[s].gs);
         P.qdesc = reinterpret_cast<const uint32_t*>(A + offs[s].qd); P.nF = tb.nF;
         P.F = R.F; P.ldF = R.ldF;
         P.U = b->U.as<T>() + b->uoff[s]; P.ldU = tb.ldU;

@@ -323,9 +323,10 @@ struct UWParams {
     const double* x; int64_t n; int d; Center c; double inv2R;
     int L;                     // highest harmonic degree with kept columns
     int tri;                   // (L+1)(L+2)/2
-    const int16_t* chains;     // nH x (d-1)
-    int nH;
+    const int16_t* chains;     // nH x cstride: level offsets, trig index, zero padding
+    int nH, cstride;
     const int32_t* ychain;     // nYp padded harmonic slots -> chain (-1: padding)
+    const int32_t* gslot;      // nH: padded slot of each harmonic
     int nYp;
     const uint32_t* qdesc;     // ldU / VW chunks: (F index << 20) | first harmonic slot
     int nF;
@@ -394,20 +395,20 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
             }
         }
     }
-    // trig powers (x0 + i x1)^mu by binary powering, lanes over mu
+    // trig powers (x0 + i x1)^mu by binary powering in the bulk precision, lanes over mu
     for (int mu = lane; mu <= P.L; mu += 32) {
-        double br = xh[0], bi = xh[1], rr = 1.0, ri = 0.0;
+        T br = (T)xh[0], bi = (T)xh[1], rr = (T)1, ri = (T)0;
         int e = mu;
         while (e) {
-            if (e & 1) { const double t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
-            const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+            if (e & 1) { const T t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
+            const T t = br * br - bi * bi; bi = (T)2 * br * bi; br = t;
             e >>= 1;
         }
         if (mu == 0) {
             trig[P.L] = (T)0.3989422804014327;             // 1/sqrt(2 pi)
         } else {
-            trig[P.L + mu] = (T)(rr * 0.5641895835477563);  // 1/sqrt(pi)
-            trig[P.L - mu] = (T)(ri * 0.5641895835477563);
+            trig[P.L + mu] = rr * (T)0.5641895835477563;   // 1/sqrt(pi)
+            trig[P.L - mu] = ri * (T)0.5641895835477563;
         }
     }
     // this point's radial factors
@@ -415,22 +416,20 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
     if (lane == 0) Fs[P.nF] = (T)0;
     __syncwarp();
     if (pre) {
-        for (int g = lane; g < P.nYp; g += 32) {
-            const int ch = __ldg(P.ychain + g);
-            T v = (T)0;
-            if (ch >= 0) {
-                const int16_t* c = P.chains + (int64_t)ch * (levels + 1);
-                v = trig[P.L + c[levels]];
-                for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + c[j]];
-            }
-            Ys[g] = v;
+        // padding slots were zeroed once per warp and are never written
+        for (int g = lane; g < P.nH; g += 32) {
+            const int16_t* c = P.chains + (int64_t)g * P.cstride;
+            const int slot = __ldg(P.gslot + g);
+            T v = trig[P.L + c[levels]];
+            for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + c[j]];
+            Ys[slot] = v;
         }
     }
     __syncwarp();
-    // row write: one VW-wide chunk per lane per step
+    // row write: one VW-wide chunk per lane per step, two steps in flight
     T* row = Ug + i * P.ldU;
     const int64_t nq = P.ldU / VW;
-    for (int64_t q = lane; q < nq; q += 32) {
+    auto chunk = [&](int64_t q) {
         const uint32_t dsc = __ldg(P.qdesc + q);
         const T f = Fs[dsc >> 20];
         const uint32_t y0 = dsc & 0xFFFFFu;
@@ -446,7 +445,7 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
                 const int ch = __ldg(P.ychain + y0 + e);
                 T h = (T)0;
                 if (ch >= 0) {
-                    const int16_t* c = P.chains + (int64_t)ch * (levels + 1);
+                    const int16_t* c = P.chains + (int64_t)ch * P.cstride;
                     h = trig[P.L + __ldg(c + levels)];
                     for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(c + j)];
                 }
@@ -455,8 +454,23 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
             if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
             else { out.x = v[0]; out.y = v[1]; }
         }
-        *reinterpret_cast<VT*>(row + q * VW) = out;
+        return out;
+    };
+    int64_t q = lane;
+    for (; q + 32 < nq; q += 64) {
+        const VT o0 = chunk(q), o1 = chunk(q + 32);
+        *reinterpret_cast<VT*>(row + q * VW) = o0;
+        *reinterpret_cast<VT*>(row + (q + 32) * VW) = o1;
     }
+    if (q < nq) *reinterpret_cast<VT*>(row + q * VW) = chunk(q);
+    __syncwarp();
+}
+
+// Zeroes a warp's harmonic slots once (the padding slots are never written afterwards).
+template <typename T>
+__device__ __forceinline__ void uwriter_zero_slots(const UWParams& P, bool pre, T* base, int lane) {
+    if (pre)
+        for (int g = lane; g < P.nYp; g += 32) base[g] = (T)0;
     __syncwarp();
 }
 
@@ -474,6 +488,7 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
     __syncthreads();
+    uwriter_zero_slots<T>(P, PRE, base, lane);
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
     for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, PRE, i, cA, cB, base, lane);
 }

@@ -294,6 +294,7 @@ void harmonic_tables(int d, int L, HarmonicTables& t) {
 
 void append_chains(int k, int d, int L, std::vector<int16_t>& out) {
     const int levels = d - 2;
+    const int stride = chain_stride(d);
     std::vector<int> mu(d - 1);              // mu[0] = k, mu[1..d-2]
     mu[0] = k;
     std::function<void(int)> rec = [&](int pos) {
@@ -305,6 +306,7 @@ void append_chains(int k, int d, int L, std::vector<int16_t>& out) {
                     out.push_back((int16_t)tri_index(L, mnext, mu[j] - mnext));
                 }
                 out.push_back((int16_t)m);
+                for (int q = levels + 1; q < stride; ++q) out.push_back((int16_t)0);
             }
             return;
         }
@@ -506,10 +508,12 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     t.ktab.assign(kTabStride * (L + 1), 0);
     t.cbase.assign(L + 2, 0);
     t.ychain.assign(std::max(1, t.nYp), -1);
+    t.gslot.assign(std::max(1, t.nH), 0);
     for (int k = 0; k <= L; ++k) {
         for (int g = t.hbase[k]; g < t.hbase[k + 1]; ++g) {
             t.hk[g] = (uint8_t)k;
             t.ychain[yoff[k] + (g - t.hbase[k])] = g;
+            t.gslot[g] = yoff[k] + (g - t.hbase[k]);
         }
         const int hkc = (sk[k] > 0) ? (int)ht.count[k] : 0;
         t.cbase[k + 1] = t.cbase[k] + dimp[k] * sk[k];

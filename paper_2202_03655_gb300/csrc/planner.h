@@ -58,8 +58,10 @@ struct HarmonicTables {
 void harmonic_tables(int d, int L, HarmonicTables& t);
 // Offset of (mu', n) in a level table: rows mu' = 0..L of length L+1-mu'.
 inline int tri_index(int L, int mu, int n) { return mu * (L + 1) - mu * (mu - 1) / 2 + n; }
-// Append the chains of H_k (lexicographic in (mu_1..mu_{d-2})) as (d-1) int16 entries each:
-// (d-2) level-table offsets, then the signed mu_{d-2} (trigonometric index).
+// Append the chains of H_k (lexicographic in (mu_1..mu_{d-2})), chain_stride(d) int16 entries
+// each: (d-2) level-table offsets, the signed mu_{d-2} (trigonometric index), zero padding so
+// that one chain is one aligned 8- or 16-byte load.
+inline int chain_stride(int d) { return (d - 1 <= 4) ? 4 : 8; }
 void append_chains(int k, int d, int L, std::vector<int16_t>& out);
 
 // ---------------------------------------------------------------- build planning
@@ -108,6 +110,7 @@ struct DeviceTables {
     std::vector<uint8_t> colpar, colk, hk;
     std::vector<int16_t> chains;             // nH x (d-1)
     std::vector<int32_t> ychain;             // nYp: chain of each padded Y slot, -1 for padding
+    std::vector<int32_t> gslot;              // nH: padded Y slot of each harmonic
     std::vector<uint32_t> qdesc;             // ldU / vw: (F index << 20) | first Y index of the chunk
     std::vector<int64_t> colmap;             // rank: padded column of each true column
     std::vector<double> Spad;                // ldU: S on the padded columns (0 on padding)
