@@ -5,27 +5,35 @@
 // Accuracy: one TF32 product keeps about 11 bits, far from what tol = 1e-6 needs, so every
 // product is split three ways, A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi, with
 // A_hi = A rounded to TF32 (cvt.rna.tf32.f32, exactly representable) and A_lo = A - A_hi.
-// The high and low parts of the U tiles are formed in shared memory by converter warps, those
-// of W and V by small preparation kernels.  The dropped A_lo B_lo term is ~2^-22 relative.
+// The dropped A_lo B_lo term is ~2^-22 relative.  The high and low parts of W and V are
+// formed once per call by small preparation kernels; those of the U tiles on the fly.
 //
 //   k_tc_uw  : Y = alpha U W + beta B.  M = 128 rows of U (points), N = BN >= c, K = rank.
-//              A = U tile (K-major, SW128, TMA), B = W^T tile (K-major, SW128, TMA).
 //   k_tc_utv : partial W = U^T V over a chunk of rows.  M = 128 columns of U, N = BN, K = rows.
-//              U tiles are loaded as stored (row-major, M contiguous) and transposed by the
-//              converter warps into K-major SW128 tiles (hi and lo), so only K-major operand
-//              layouts reach the MMA.  B = V tiles (column-major V is K-major), SW128, TMA.
+//
+// Data path of one K step (64 values of K): a U-producer warp brings the raw FP32 U tile
+// (128 x 64, 32 KB) into a 4-deep ring; converter warps (thread = MMA row) read it, release the
+// slot at once, split it into hi / lo and write both into TMEM with tcgen05.st.  A B-producer
+// warp brings the K-major SW128 tiles of B_hi and B_lo, stacked into one 2 BN-row operand, into
+// their own ring.  The MMA warp then issues, per 8 values of K, A_hi x [B_hi; B_lo] (N = 2 BN)
+// and A_lo x B_hi (N = BN), both with A from TMEM.  HBM loads of U therefore wait only for the
+// converters, never for MMA completion, and the issuing warp spends its time on 16 MMAs and one
+// commit per 32 KB of U.
 //
 // The tensor core's FP32 accumulation is not rounded to nearest, and its error grows with
-// the number of MMAs summed into one accumulator (about 1.7e-5 relative after 400 K steps).
-// So each stage (32 K values, 12 MMAs) starts a fresh TMEM accumulator and the epilogue warps
-// add it into FP32 registers (round to nearest); four TMEM buffers rotate so that the MMAs of
-// the next stages run while earlier stages are promoted.
+// the number of MMAs summed into one accumulator (about 1.7e-5 relative after 400 32-deep
+// steps).  So each K step starts a fresh TMEM accumulator and the promotion warps add it
+// (both N halves) into FP32 registers (round to nearest); two TMEM accumulators alternate so
+// that the MMAs of the next step run while the last one is promoted.
 //
-// CTA roles (10 warps): warp 0 TMA producer, warp 1 MMA issuer and TMEM owner, warps 2-5
-// converters, warps 6-9 promotion and epilogue (TMEM -> registers -> global; warp w reads TMEM
-// lanes 32 (w mod 4) .. +31).  Every wait on an mbarrier is bounded by a clock limit; on
-// expiry the kernel records an error, drains its own copies and MMAs, frees its TMEM and
-// returns.
+// TMEM (512 columns, one CTA per SM): accumulators (2 BN columns) at 128 b, b < 2; A buffers
+// (hi in 64 columns, lo in the next 64) at 256 + 128 b, b < 2.
+//
+// CTA roles (11 warps): warp 0 U producer, warp 1 MMA issuer and TMEM owner, warps 2-5
+// converters, warps 6-9 promotion and epilogue, warp 10 B producer.  A warp w reads and
+// writes TMEM lanes 32 (w mod 4) .. +31, so converter and promotion warps each cover the 128
+// lanes once.  Every wait on an mbarrier is bounded by a clock limit; on expiry the kernel
+// records an error, drains its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -39,12 +47,20 @@ namespace hdf {
 namespace tc {
 
 constexpr int BM = 128;                 // MMA M
-constexpr int BK = 32;                  // K elements per stage: one 128-byte swizzle row of FP32
-constexpr int UW_STAGES = 4;
-constexpr int UTV_STAGES = 3;
-constexpr int NTHREADS = 320;
-constexpr int NACC = 4;                 // TMEM accumulator buffers (one per stage in flight)
+constexpr int BK = 64;                  // K elements per step: two 128-byte swizzle rows of FP32
+constexpr int KH = 32;                  // K elements per 128-byte swizzle row (one TMA box)
+constexpr int NTHREADS = 352;
+constexpr int S_U = 4;                  // U ring depth (32 KB per stage)
+constexpr int NACC = 2;                 // TMEM accumulators
+constexpr int NA = 2;                   // TMEM A buffers (hi + lo)
+constexpr int NDONE = 8;                // ring of "MMAs of step it complete" barriers
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAcol = 256;         // first TMEM column of the A buffers
 constexpr long long kWaitCycles = 4000000000ll;   // about 2 s at 2 GHz
+
+// B ring depth: 2 BN rows x 64 K per stage (hi and lo stacked), within 64 KB.
+template <int BN>
+__host__ __device__ constexpr int b_stages() { return BN >= 64 ? 2 : 4; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -57,20 +73,30 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 // Waits for the completion of the phase with the given parity; false if the clock limit passes.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
+    if (mbar_try(a, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(a, parity)) return true;
         if (clock64() - t0 > kWaitCycles) return false;
     }
+}
+// True in exactly one lane of a converged warp.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred;
+    asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(pred));
+    return pred != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -94,17 +120,19 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* p) {
     return d;
 }
 
-// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = BN.
-template <int BN>
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = N_.
+template <int N_>
 __host__ __device__ constexpr uint32_t idesc_tf32() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (TMEM) (+)= A (TMEM, 128 lanes x 8 columns) * B (shared memory descriptor).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
             d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -114,33 +142,263 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// 32 consecutive TMEM columns of this thread's lane -> registers (no wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+// 16 consecutive TMEM columns of this thread's lane -> registers (no wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// registers -> 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32_hi(float x) {
     uint32_t h;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
     return __uint_as_float(h);
 }
+__device__ __forceinline__ void split_tf32(float x, uint32_t& h, uint32_t& l) {
+    const float hf = tf32_hi(x);
+    h = __float_as_uint(hf);
+    l = __float_as_uint(x - hf);
+}
+
+// Shared-memory carve-up common to both kernels: S_U raw U tiles (32 KB, 1024-aligned), SB
+// stacked B tiles (per 32-K half: BN hi rows then BN lo rows of 128 bytes, K-major SW128),
+// then the mbarriers.
+template <int BN>
+struct Smem {
+    static constexpr int SB = b_stages<BN>();
+    static constexpr uint32_t UBYTES = BM * BK * 4;             // one U stage
+    static constexpr uint32_t BHALF = 2 * BN * KH * 4;          // stacked hi/lo rows of one 32-K half
+    static constexpr uint32_t BBYTES = 2 * BHALF;               // one B stage
+    unsigned char* U;
+    unsigned char* B;
+    uint64_t *ufull, *uempty, *bfull, *afull, *done, *acce, *drain;
+    uint32_t* slot;
+    __device__ explicit Smem(unsigned char* raw) {
+        unsigned char* base =
+            reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+        U = base;
+        B = U + S_U * UBYTES;
+        ufull = reinterpret_cast<uint64_t*>(B + SB * BBYTES);
+        uempty = ufull + S_U;
+        bfull = uempty + S_U;
+        afull = bfull + SB;
+        done = afull + NA;
+        acce = done + NDONE;
+        drain = acce + NACC;
+        slot = reinterpret_cast<uint32_t*>(drain + 1);
+    }
+    static constexpr size_t bytes() {
+        return 1024 + (size_t)S_U * UBYTES + (size_t)SB * BBYTES + (2 * S_U + SB + NA + NDONE + NACC + 1) * 8 + 16;
+    }
+};
+
+// Barrier set-up and TMEM allocation (warp 1 owns the TMEM); returns the TMEM base address.
+template <int BN>
+__device__ __forceinline__ uint32_t cta_setup(Smem<BN>& sm, int warp) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S_U; ++s) { mbar_init(&sm.ufull[s], 1); mbar_init(&sm.uempty[s], 4); }
+        for (int s = 0; s < Smem<BN>::SB; ++s) mbar_init(&sm.bfull[s], 1);
+        for (int b = 0; b < NA; ++b) mbar_init(&sm.afull[b], 4);
+        for (int j = 0; j < NDONE; ++j) mbar_init(&sm.done[j], 1);
+        for (int b = 0; b < NACC; ++b) mbar_init(&sm.acce[b], 4);
+        mbar_init(sm.drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sm.slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *sm.slot;
+}
 
 template <int BN>
-__host__ __device__ constexpr uint32_t tmem_cols() {
-    return (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : (NACC * BN <= 128) ? 128 : (NACC * BN <= 256) ? 256 : 512;
+__device__ __forceinline__ void cta_teardown(uint32_t tmem, int warp) {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// Waits until the MMAs of step j are complete (one tcgen05.commit per step on done[j mod 8]).
+// Every waiter has already seen step j - 8 complete, and step j + 8 cannot be issued before the
+// waiter moves on (the B producer runs at most SB <= 4 steps ahead of the MMAs, the converters
+// NA = 2, and the MMAs at most NACC = 2 steps ahead of the promotion), so the parity is
+// unambiguous.
+template <int BN>
+__device__ __forceinline__ bool wait_done(Smem<BN>& sm, uint32_t j) {
+    return mbar_wait(&sm.done[j % NDONE], (j / NDONE) & 1);
+}
+
+// The MMA warp waits on three barriers at once: lane 0 the accumulator, lane 1 the B stage,
+// the other lanes the A buffer, so one try_wait instruction covers all three.
+__device__ __forceinline__ bool mbar_wait_lanes(uint32_t a, uint32_t parity) {
+    bool mine = mbar_try(a, parity);
+    if (__all_sync(0xffffffffu, mine)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (!mine) mine = mbar_try(a, parity);
+        if (__all_sync(0xffffffffu, mine)) return true;
+        if (__any_sync(0xffffffffu, clock64() - t0 > kWaitCycles)) return false;
+    }
+}
+
+// MMA issuer (whole warp converged; one elected lane issues): per K step, 8 x (A_hi x [B_hi;
+// B_lo], A_lo x B_hi) from the A buffer in TMEM and the stacked B stage, then one commit that
+// frees the B stage and the A buffer and publishes the accumulator.
+template <int BN>
+__device__ __forceinline__ bool mma_step(Smem<BN>& sm, uint32_t tmem, uint32_t it, int lane) {
+    constexpr int SB = Smem<BN>::SB;
+    constexpr uint32_t id2 = idesc_tf32<2 * BN>(), id1 = idesc_tf32<BN>();
+    const uint32_t sb = it % SB, b = it % NA, buf = it % NACC;
+    const uint32_t a = lane == 0 ? smem_u32(&sm.acce[buf]) : lane == 1 ? smem_u32(&sm.bfull[sb]) : smem_u32(&sm.afull[b]);
+    const uint32_t par = lane == 0 ? ((it / NACC) & 1) ^ 1 : lane == 1 ? (it / SB) & 1 : (it / NA) & 1;
+    if (!mbar_wait_lanes(a, par)) return false;
+    tc_fence_after();
+    const uint32_t d = tmem + buf * 2 * BN;
+    const uint32_t ahi = tmem + kAcol + 128 * b, alo = ahi + 64;
+    const uint64_t b0 = sw128_desc(sm.B + sb * Smem<BN>::BBYTES);
+    constexpr uint64_t halfstep = Smem<BN>::BHALF >> 4;
+    if (elect_one()) {
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {
+            const uint64_t db = b0 + (kk >> 2) * halfstep + (uint64_t)(((kk & 3) * 32) >> 4);
+            mma_tf32_ts(d, ahi + 8 * kk, db, id2, kk > 0 ? 1u : 0u);     // [hi.hi | hi.lo]
+            mma_tf32_ts(d, alo + 8 * kk, db, id1, 1u);                  // lo.hi into the first half
+        }
+        mma_commit(&sm.done[it % NDONE]);
+    }
+    __syncwarp();
+    return true;
+}
+
+// Converter tail: 64 raw values of this thread's row -> hi / lo in A buffer of step `it`.
+template <int BN>
+__device__ __forceinline__ void convert_publish(Smem<BN>& sm, uint32_t tmem, uint32_t it, int q, int lane,
+                                                const float* x) {
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + kAcol + 128 * (it % NA);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t hi[32], lo[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) split_tf32(x[32 * h + k], hi[k], lo[k]);
+        tmem_st32(ta + 32 * h, hi);
+        tmem_st32(ta + 64 + 32 * h, lo);
+    }
+    tmem_st_wait();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.afull[it % NA]);
+}
+
+// Converter head: wait for the U stage of step `it` and for the A buffer, then (after the caller
+// has read the stage) release the stage.
+template <int BN>
+__device__ __forceinline__ bool convert_wait(Smem<BN>& sm, uint32_t it) {
+    if (!mbar_wait(&sm.ufull[it % S_U], (it / S_U) & 1)) return false;
+    if (it >= (uint32_t)NA && !wait_done<BN>(sm, it - NA)) return false;
+    tc_fence_after();
+    return true;
+}
+template <int BN>
+__device__ __forceinline__ void convert_release(Smem<BN>& sm, uint32_t it, int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.uempty[it % S_U]);
+}
+
+// Promotion of the accumulator of step `it` (both N halves) into FP32 registers.
+template <int BN>
+__device__ __forceinline__ bool promote(Smem<BN>& sm, uint32_t tmem, uint32_t it, int q, int lane, float* acc) {
+    const uint32_t buf = it % NACC;
+    if (!wait_done<BN>(sm, it)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + buf * 2 * BN;
+    uint32_t v[2 * BN];
+    if constexpr (BN == 16) {
+        tmem_ld32(ta, v);
+    } else {
+#pragma unroll
+        for (int j0 = 0; j0 < 2 * BN; j0 += 32) tmem_ld32(ta + j0, v + j0);
+    }
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] += __uint_as_float(v[j]) + __uint_as_float(v[BN + j]);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.acce[buf]);
+    return true;
+}
+
+// MMA warp exit: every MMA it issued is complete before the CTA frees its TMEM.
+template <int BN>
+__device__ __forceinline__ void mma_drain(Smem<BN>& sm, bool ok, int* err) {
+    if (elect_one()) mma_commit(sm.drain);
+    __syncwarp();
+    if (!mbar_wait(sm.drain, 0)) ok = false;
+    if (!ok && (threadIdx.x & 31) == 0) atomicExch(err, 1);
+}
+
+// Producer drain: every copy this thread issued on `full` (a ring of `depth`) has landed.
+__device__ __forceinline__ bool producer_drain(uint64_t* full, int depth, uint32_t it) {
+    bool ok = true;
+    for (uint32_t q = (it > (uint32_t)depth ? it - depth : 0); q < it; ++q)
+        if (!mbar_wait(&full[q % depth], (q / depth) & 1)) ok = false;
+    return ok;
+}
+
+// B producer, one step: stacked hi / lo tiles of K rows [k0, k0 + 64) (two 32-K halves).
+template <int BN>
+__device__ __forceinline__ bool load_b(Smem<BN>& sm, uint32_t it, const CUtensorMap* mhi, const CUtensorMap* mlo,
+                                       int k0) {
+    constexpr int SB = Smem<BN>::SB;
+    const uint32_t sb = it % SB;
+    if (it >= (uint32_t)SB && !wait_done<BN>(sm, it - SB)) return false;
+    mbar_expect_tx(&sm.bfull[sb], Smem<BN>::BBYTES);
+    unsigned char* dst = sm.B + sb * Smem<BN>::BBYTES;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        tma_load_2d(dst + h * Smem<BN>::BHALF, mhi, k0 + KH * h, 0, &sm.bfull[sb]);
+        tma_load_2d(dst + h * Smem<BN>::BHALF + BN * KH * 4, mlo, k0 + KH * h, 0, &sm.bfull[sb]);
+    }
+    return true;
 }
 
 struct UwArgs {
     int64_t n;          // rows of U
-    int nkt;            // K steps (ceil(rank / 32))
+    int nkt;            // K steps (ceil(rank / 64))
     int c;              // columns of W, Y
     float alpha, beta;
     const float* B; int64_t ldb;
@@ -153,37 +411,11 @@ template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_uw(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
             const __grid_constant__ CUtensorMap mWlo, UwArgs p) {
-    constexpr int S = UW_STAGES;
-    constexpr uint32_t ABYTES = BM * BK * 4, BBYTES = BN * BK * 4;
+    using SM = Smem<BN>;
     extern __shared__ unsigned char raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
-    float* A = reinterpret_cast<float*>(base);
-    float* Alo = A + S * BM * BK;
-    float* Bh = Alo + S * BM * BK;
-    float* Bl = Bh + S * BN * BK;
-    uint64_t* full = reinterpret_cast<uint64_t*>(Bl + S * BN * BK);
-    uint64_t* lo = full + S;
-    uint64_t* empty = lo + S;
-    uint64_t* accf = empty + S;
-    uint64_t* acce = accf + NACC;
-    uint64_t* drain = acce + NACC;
-    uint32_t* slot = reinterpret_cast<uint32_t*>(drain + 1);
+    SM sm(raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&lo[s], 4); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < NACC; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
-        mbar_init(drain, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                     "r"(tmem_cols<BN>()));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *slot;
+    const uint32_t tmem = cta_setup<BN>(sm, warp);
     const int64_t ntiles = (p.n + BM - 1) / BM;
     bool ok = true;
 
@@ -191,99 +423,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                for (int kt = 0; kt < p.nkt && ok; ++kt, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1;
-                    if (!mbar_wait(&empty[s], ph ^ 1)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], ABYTES + 2 * BBYTES);
-                    tma_load_2d(A + s * BM * BK, &mU, kt * BK, (int)(tile * BM), &full[s]);
-                    tma_load_2d(Bh + s * BN * BK, &mW, kt * BK, 0, &full[s]);
-                    tma_load_2d(Bl + s * BN * BK, &mWlo, kt * BK, 0, &full[s]);
+                for (int kt = 0; kt < p.nkt; ++kt, ++it) {
+                    const uint32_t s = it % S_U;
+                    if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
+                    unsigned char* dst = sm.U + s * SM::UBYTES;
+                    tma_load_2d(dst, &mU, kt * BK, (int)(tile * BM), &sm.ufull[s]);
+                    tma_load_2d(dst + SM::UBYTES / 2, &mU, kt * BK + KH, (int)(tile * BM), &sm.ufull[s]);
                 }
             }
-            // drain: every copy this thread issued has landed before the CTA leaves
-            for (uint32_t q = (it > (uint32_t)S ? it - S : 0); q < it; ++q) {
-                const int s = q % S;
-                if (!mbar_wait(&full[s], (q / S) & 1)) ok = false;
-            }
+            if (!producer_drain(sm.ufull, S_U, it)) ok = false;
+            if (!ok) atomicExch(p.err, 1);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+                for (int kt = 0; kt < p.nkt && ok; ++kt, ++it) ok = load_b<BN>(sm, it, &mW, &mWlo, kt * BK);
+            if (!producer_drain(sm.bfull, SM::SB, it)) ok = false;
             if (!ok) atomicExch(p.err, 1);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32<BN>();
-            uint32_t it = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                for (int kt = 0; kt < p.nkt; ++kt, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1, buf = it % NACC, aph = (it / NACC) & 1;
-                    if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
-                    if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d = tmem + buf * BN;
-                    const uint64_t da = sw128_desc(A + s * BM * BK), dal = sw128_desc(Alo + s * BM * BK);
-                    const uint64_t db = sw128_desc(Bh + s * BN * BK), dbl = sw128_desc(Bl + s * BN * BK);
-#pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk) {
-                        const uint64_t off = (uint64_t)(kk * 32) >> 4;     // 8 TF32 = 32 bytes
-                        mma_tf32(d, da + off, db + off, idesc, kk > 0 ? 1u : 0u);
-                        mma_tf32(d, da + off, dbl + off, idesc, 1u);
-                        mma_tf32(d, dal + off, db + off, idesc, 1u);
-                    }
-                    mma_commit(&empty[s]);
-                    mma_commit(&accf[buf]);
-                }
-            }
-            mma_commit(drain);                       // all MMAs of this thread complete
-            if (!mbar_wait(drain, 0)) ok = false;
-            if (!ok) atomicExch(p.err, 1);
-        }
+        uint32_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+            for (int kt = 0; kt < p.nkt && ok; ++kt, ++it) ok = mma_step<BN>(sm, tmem, it, lane);
+        mma_drain(sm, ok, p.err);
     } else if (warp < 6) {
-        const int cw = warp - 2;                     // converter 0..3: a quarter of each A tile
+        // thread = row m of the U tile; each 32-K half is SW128 (16-byte chunk j of row m at chunk
+        // position j ^ (m mod 8)), so the eight threads of a load phase hit distinct banks
+        const int q = warp & 3, m = 32 * q + lane;
         uint32_t it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             for (int kt = 0; kt < p.nkt; ++kt, ++it) {
-                const int s = it % S;
-                const uint32_t ph = (it / S) & 1;
-                if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-                float4* hi4 = reinterpret_cast<float4*>(A + s * BM * BK) + cw * (BM * BK / 16);
-                float4* lo4 = reinterpret_cast<float4*>(Alo + s * BM * BK) + cw * (BM * BK / 16);
+                if (!convert_wait<BN>(sm, it)) { ok = false; break; }
+                const unsigned char* R = sm.U + (it % S_U) * SM::UBYTES + m * 128;
+                float x[64];
 #pragma unroll
-                for (int q = 0; q < BM * BK / 16 / 32; ++q) {
-                    const float4 v = hi4[q * 32 + lane];
-                    float4 h, l;
-                    h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
-                    l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-                    hi4[q * 32 + lane] = h;
-                    lo4[q * 32 + lane] = l;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&lo[s]);
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 v = *reinterpret_cast<const float4*>(R + h * (SM::UBYTES / 2) + ((j ^ (m & 7)) << 4));
+                        x[32 * h + 4 * j + 0] = v.x; x[32 * h + 4 * j + 1] = v.y;
+                        x[32 * h + 4 * j + 2] = v.z; x[32 * h + 4 * j + 3] = v.w;
+                    }
+                convert_release<BN>(sm, it, lane);
+                convert_publish<BN>(sm, tmem, it, q, lane, x);
             }
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     } else {
-        const int q = warp & 3;                      // TMEM lane quadrant of this warp
+        const int q = warp & 3;
         uint32_t it = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             float acc[BN];
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
-            for (int kt = 0; kt < p.nkt; ++kt, ++it) {
-                const uint32_t buf = it % NACC, aph = (it / NACC) & 1;
-                if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
-                tc_fence_after();
-#pragma unroll
-                for (int j0 = 0; j0 < BN; j0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
-            }
+            for (int kt = 0; kt < p.nkt && ok; ++kt, ++it) ok = promote<BN>(sm, tmem, it, q, lane, acc);
             if (!ok) break;
             const int64_t row = tile * BM + 32 * q + lane;
             if (row < p.n) {
@@ -299,18 +494,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols<BN>()));
-    }
+    cta_teardown<BN>(tmem, warp);
 }
 
 struct UtvArgs {
     int64_t r;          // columns of U (M extent)
     int64_t n;          // rows of U
-    int64_t chunk;      // rows per K chunk
+    int64_t chunk;      // rows per K chunk (a multiple of 64)
     int nchunk;
     int mblocks;        // ceil(r / 128)
     int c;
@@ -323,38 +513,11 @@ template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_utv(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mV,
              const __grid_constant__ CUtensorMap mVlo, UtvArgs p) {
-    constexpr int S = UTV_STAGES;
-    constexpr uint32_t RAWBYTES = BM * BK * 4, BBYTES = BN * BK * 4;
+    using SM = Smem<BN>;
     extern __shared__ unsigned char raw_[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw_) + 1023) & ~uintptr_t(1023));
-    float* Raw = reinterpret_cast<float*>(base);          // S x [BK rows][BM cols] as stored
-    float* Ah = Raw + S * BM * BK;                        // S x K-major SW128 hi
-    float* Al = Ah + S * BM * BK;                         // S x K-major SW128 lo
-    float* Bh = Al + S * BM * BK;
-    float* Bl = Bh + S * BN * BK;
-    uint64_t* full = reinterpret_cast<uint64_t*>(Bl + S * BN * BK);
-    uint64_t* lo = full + S;
-    uint64_t* empty = lo + S;
-    uint64_t* accf = empty + S;
-    uint64_t* acce = accf + NACC;
-    uint64_t* drain = acce + NACC;
-    uint32_t* slot = reinterpret_cast<uint32_t*>(drain + 1);
+    SM sm(raw_);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&lo[s], 4); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < NACC; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 4); }
-        mbar_init(drain, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                     "r"(tmem_cols<BN>()));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *slot;
+    const uint32_t tmem = cta_setup<BN>(sm, warp);
     const int64_t nitems = (int64_t)p.mblocks * p.nchunk;
     bool ok = true;
     auto ksteps = [&](int64_t item) -> int {
@@ -370,83 +533,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
                 const int64_t i0 = ch * p.chunk;
                 const int nk = ksteps(item);
-                for (int kt = 0; kt < nk && ok; ++kt, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1;
-                    if (!mbar_wait(&empty[s], ph ^ 1)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], RAWBYTES + 2 * BBYTES);
-                    const int row = (int)(i0 + (int64_t)kt * BK);
-                    tma_load_2d(Raw + s * BM * BK, &mU, (int)(mb * BM), row, &full[s]);
-                    tma_load_2d(Bh + s * BN * BK, &mV, row, 0, &full[s]);
-                    tma_load_2d(Bl + s * BN * BK, &mVlo, row, 0, &full[s]);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const uint32_t s = it % S_U;
+                    if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
+                    tma_load_2d(sm.U + s * SM::UBYTES, &mU, (int)(mb * BM), (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
                 }
             }
-            for (uint32_t q = (it > (uint32_t)S ? it - S : 0); q < it; ++q) {
-                const int s = q % S;
-                if (!mbar_wait(&full[s], (q / S) & 1)) ok = false;
+            if (!producer_drain(sm.ufull, S_U, it)) ok = false;
+            if (!ok) atomicExch(p.err, 1);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int64_t i0 = (item / p.mblocks) * p.chunk;
+                const int nk = ksteps(item);
+                for (int kt = 0; kt < nk && ok; ++kt, ++it)
+                    ok = load_b<BN>(sm, it, &mV, &mVlo, (int)(i0 + (int64_t)kt * BK));
             }
+            if (!producer_drain(sm.bfull, SM::SB, it)) ok = false;
             if (!ok) atomicExch(p.err, 1);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32<BN>();
-            uint32_t it = 0;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                const int nk = ksteps(item);
-                for (int kt = 0; kt < nk; ++kt, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1, buf = it % NACC, aph = (it / NACC) & 1;
-                    if (!mbar_wait(&acce[buf], aph ^ 1)) { ok = false; break; }
-                    if (!mbar_wait(&full[s], ph) || !mbar_wait(&lo[s], ph)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d = tmem + buf * BN;
-                    const uint64_t da = sw128_desc(Ah + s * BM * BK), dal = sw128_desc(Al + s * BM * BK);
-                    const uint64_t db = sw128_desc(Bh + s * BN * BK), dbl = sw128_desc(Bl + s * BN * BK);
-#pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk) {
-                        const uint64_t off = (uint64_t)(kk * 32) >> 4;
-                        mma_tf32(d, da + off, db + off, idesc, kk > 0 ? 1u : 0u);
-                        mma_tf32(d, da + off, dbl + off, idesc, 1u);
-                        mma_tf32(d, dal + off, db + off, idesc, 1u);
-                    }
-                    mma_commit(&empty[s]);
-                    mma_commit(&accf[buf]);
-                }
-            }
-            mma_commit(drain);
-            if (!mbar_wait(drain, 0)) ok = false;
-            if (!ok) atomicExch(p.err, 1);
+        uint32_t it = 0;
+        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = mma_step<BN>(sm, tmem, it, lane);
         }
+        mma_drain(sm, ok, p.err);
     } else if (warp < 6) {
-        // transpose the stored tile Raw[k][m] into K-major SW128 hi / lo tiles:
-        // element (m, k) at byte (m/8)*1024 + (m%8)*128 + (((k/4) ^ (m%8)) * 16) + (k%4)*4
-        const int cw = warp - 2;
+        // thread = column m of the U block (row m of A = U^T); the stored tile is [64 rows][128
+        // columns], so each load of the warp reads 32 consecutive floats of one row
+        const int q = warp & 3, m = 32 * q + lane;
         uint32_t it = 0;
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int nk = ksteps(item);
             for (int kt = 0; kt < nk; ++kt, ++it) {
-                const int s = it % S;
-                const uint32_t ph = (it / S) & 1;
-                if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-                const float* R = Raw + s * BM * BK;
-                unsigned char* H = reinterpret_cast<unsigned char*>(Ah + s * BM * BK);
-                unsigned char* Lo = reinterpret_cast<unsigned char*>(Al + s * BM * BK);
-                // this warp: rows m in [32 cw, 32 cw + 32), all 8 k-chunks
-                const int m = 32 * cw + lane;
+                if (!convert_wait<BN>(sm, it)) { ok = false; break; }
+                const float* R = reinterpret_cast<const float*>(sm.U + (it % S_U) * SM::UBYTES) + m;
+                float x[64];
 #pragma unroll
-                for (int kc = 0; kc < BK / 4; ++kc) {
-                    float4 h, l;
-                    const float x0 = R[(4 * kc + 0) * BM + m], x1 = R[(4 * kc + 1) * BM + m];
-                    const float x2 = R[(4 * kc + 2) * BM + m], x3 = R[(4 * kc + 3) * BM + m];
-                    h.x = tf32_hi(x0); h.y = tf32_hi(x1); h.z = tf32_hi(x2); h.w = tf32_hi(x3);
-                    l.x = x0 - h.x; l.y = x1 - h.y; l.z = x2 - h.z; l.w = x3 - h.w;
-                    const uint32_t off = (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((kc ^ (m & 7)) << 4));
-                    *reinterpret_cast<float4*>(H + off) = h;
-                    *reinterpret_cast<float4*>(Lo + off) = l;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&lo[s]);
+                for (int k = 0; k < BK; ++k) x[k] = R[k * BM];
+                convert_release<BN>(sm, it, lane);
+                convert_publish<BN>(sm, tmem, it, q, lane, x);
             }
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
@@ -458,21 +588,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
             const int nk = ksteps(item);
-            for (int kt = 0; kt < nk; ++kt, ++it) {
-                const uint32_t buf = it % NACC, aph = (it / NACC) & 1;
-                if (!mbar_wait(&accf[buf], aph)) { ok = false; break; }
-                tc_fence_after();
-#pragma unroll
-                for (int j0 = 0; j0 < BN; j0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + buf * BN + j0, v);
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) acc[j0 + jj] += v[jj];
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
-            }
+            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = promote<BN>(sm, tmem, it, q, lane, acc);
             if (!ok) break;
             const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
             const int64_t a = mb * BM + 32 * q + lane;
@@ -484,12 +600,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols<BN>()));
-    }
+    cta_teardown<BN>(tmem, warp);
 }
 
 // Wt_hi[j * kpad + a] + Wt_lo[j * kpad + a] = W[a * c + j] (TF32 split, zero padding to kpad x bn).
@@ -550,15 +661,6 @@ static bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t o
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
-static size_t uw_smem() {
-    return 1024 + (size_t)UW_STAGES * (2 * BM * BK + 2 * BN * BK) * 4 + (3 * UW_STAGES + 2 * NACC + 1) * 8 + 16;
-}
-template <int BN>
-static size_t utv_smem() {
-    return 1024 + (size_t)UTV_STAGES * (3 * BM * BK + 2 * BN * BK) * 4 + (3 * UTV_STAGES + 2 * NACC + 1) * 8 + 16;
-}
-
 static int num_sms() {
     int dv = 0, nsm = 0;
     cudaGetDevice(&dv);
@@ -577,12 +679,12 @@ static hdf_status uw_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const
     k_prep_wt<<<(unsigned)(((int64_t)BN * kpad + 255) / 256), 256, 0, st>>>(W, r, c, BN, kpad, hi, lo);
     HDF_CUDA(cudaGetLastError());
     CUtensorMap mU, mW, mWl;
-    if (!make_map(&mU, U, (uint64_t)ldU, (uint64_t)n, (uint64_t)ldU * 4, BK, BM, true) ||
-        !make_map(&mW, hi, (uint64_t)kpad, BN, (uint64_t)kpad * 4, BK, BN, true) ||
-        !make_map(&mWl, lo, (uint64_t)kpad, BN, (uint64_t)kpad * 4, BK, BN, true))
+    if (!make_map(&mU, U, (uint64_t)ldU, (uint64_t)n, (uint64_t)ldU * 4, KH, BM, true) ||     // SW128 halves
+        !make_map(&mW, hi, (uint64_t)kpad, BN, (uint64_t)kpad * 4, KH, BN, true) ||
+        !make_map(&mWl, lo, (uint64_t)kpad, BN, (uint64_t)kpad * 4, KH, BN, true))
         return fail(HDF_ECUDA, "tensor-core matvec: cannot encode a tensor map");
     UwArgs a{n, (int)(kpad / BK), c, alpha, beta, B, ldb, Y, ldy, err};
-    const size_t sm = uw_smem<BN>();
+    const size_t sm = Smem<BN>::bytes();
     HDF_CUDA(cudaFuncSetAttribute(k_tc_uw<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t ntiles = (n + BM - 1) / BM;
     const int grid = (int)std::min<int64_t>(ntiles, num_sms());
@@ -603,12 +705,12 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
     HDF_CUDA(cudaGetLastError());
     CUtensorMap mU, mV, mVl;
     if (!make_map(&mU, U, (uint64_t)ldU, (uint64_t)n, (uint64_t)ldU * 4, BM, BK, false) ||
-        !make_map(&mV, vhi, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true) ||
-        !make_map(&mVl, vlo, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, BK, BN, true))
+        !make_map(&mV, vhi, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, KH, BN, true) ||
+        !make_map(&mVl, vlo, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, KH, BN, true))
         return fail(HDF_ECUDA, "tensor-core matvec: cannot encode a tensor map");
     const int nch = (int)((n + chunk - 1) / chunk);
     UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, err};
-    const size_t sm = utv_smem<BN>();
+    const size_t sm = Smem<BN>::bytes();
     HDF_CUDA(cudaFuncSetAttribute(k_tc_utv<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t nitems = (int64_t)a.mblocks * nch;
     const int grid = (int)std::min<int64_t>(nitems, num_sms());
@@ -633,8 +735,9 @@ size_t tc_work_floats(int64_t n, int64_t r, int c) {
 // Rows-per-chunk split for U^T V on the tensor cores: enough (column block, chunk) items.
 void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk) {
     // at least enough (column block, chunk) items to fill the GPU a few times, and chunks of at
-    // most 8192 rows so that the FP32 register sums of the promoted stages stay short; chunks
-    // are whole multiples of 32 rows, and *nchunk is the number of chunks that really exist
+    // most 8192 rows so that the FP32 register sums of the promoted steps stay short; chunks
+    // are whole multiples of 64 rows (one K step), and *nchunk is the number of chunks that
+    // really exist
     const int64_t mblocks = (r + tc::BM - 1) / tc::BM;
     const int64_t want = (4 * 152 + mblocks - 1) / mblocks;
     const int64_t by_len = (n + 8191) / 8192;
