@@ -54,13 +54,17 @@ constexpr int S_U = 4;                  // U ring depth (32 KB per stage)
 constexpr int NACC = 2;                 // TMEM accumulators
 constexpr int NA = 2;                   // TMEM A buffers (hi + lo)
 constexpr int NDONE = 8;                // ring of "MMAs of step it complete" barriers
+constexpr int IR = 16;                  // ring of work items handed from the U producer to the other roles
+constexpr int NCONS = 10;               // item consumers: B producer, MMA warp, 4 converter and 4 promotion warps
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAcol = 256;         // first TMEM column of the A buffers
 constexpr long long kWaitCycles = 4000000000ll;   // about 2 s at 2 GHz
 
-// B ring depth: 2 BN rows x 64 K per stage (hi and lo stacked), within 64 KB.
+// B ring depth (2 BN rows x 64 K per stage, hi and lo stacked): the B tiles come mostly from L2
+// but with ~2000 cycles of latency, so the ring takes what shared memory leaves beside the U
+// ring (at most 224 KB in all).  At most 7, which the done-ring parity argument needs.
 template <int BN>
-__host__ __device__ constexpr int b_stages() { return BN >= 64 ? 2 : 4; }
+__host__ __device__ constexpr int b_stages() { return BN >= 64 ? 3 : 6; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -199,7 +203,8 @@ struct Smem {
     static constexpr uint32_t BBYTES = 2 * BHALF;               // one B stage
     unsigned char* U;
     unsigned char* B;
-    uint64_t *ufull, *uempty, *bfull, *afull, *done, *acce, *drain;
+    uint64_t *ufull, *uempty, *bfull, *afull, *done, *acce, *drain, *itfull, *itempty;
+    int64_t* items;
     uint32_t* slot;
     __device__ explicit Smem(unsigned char* raw) {
         unsigned char* base =
@@ -213,10 +218,14 @@ struct Smem {
         done = afull + NA;
         acce = done + NDONE;
         drain = acce + NACC;
-        slot = reinterpret_cast<uint32_t*>(drain + 1);
+        itfull = drain + 1;
+        itempty = itfull + IR;
+        items = reinterpret_cast<int64_t*>(itempty + IR);
+        slot = reinterpret_cast<uint32_t*>(items + IR);
     }
     static constexpr size_t bytes() {
-        return 1024 + (size_t)S_U * UBYTES + (size_t)SB * BBYTES + (2 * S_U + SB + NA + NDONE + NACC + 1) * 8 + 16;
+        return 1024 + (size_t)S_U * UBYTES + (size_t)SB * BBYTES + (2 * S_U + SB + NA + NDONE + NACC + 1 + 3 * IR) * 8 +
+               16;
     }
 };
 
@@ -230,6 +239,7 @@ __device__ __forceinline__ uint32_t cta_setup(Smem<BN>& sm, int warp) {
         for (int j = 0; j < NDONE; ++j) mbar_init(&sm.done[j], 1);
         for (int b = 0; b < NACC; ++b) mbar_init(&sm.acce[b], 4);
         mbar_init(sm.drain, 1);
+        for (int j = 0; j < IR; ++j) { mbar_init(&sm.itfull[j], 1); mbar_init(&sm.itempty[j], NCONS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -255,7 +265,7 @@ __device__ __forceinline__ void cta_teardown(uint32_t tmem, int warp) {
 
 // Waits until the MMAs of step j are complete (one tcgen05.commit per step on done[j mod 8]).
 // Every waiter has already seen step j - 8 complete, and step j + 8 cannot be issued before the
-// waiter moves on (the B producer runs at most SB <= 4 steps ahead of the MMAs, the converters
+// waiter moves on (the B producer runs at most SB <= 7 steps ahead of the MMAs, the converters
 // NA = 2, and the MMAs at most NACC = 2 steps ahead of the promotion), so the parity is
 // unambiguous.
 template <int BN>
@@ -396,6 +406,30 @@ __device__ __forceinline__ bool load_b(Smem<BN>& sm, uint32_t it, const CUtensor
     return true;
 }
 
+// Work-item hand-off (dynamic scheduling).  The U producer takes item k of this CTA (its block
+// index first, then from a global counter), publishes it in slot k mod 16 and moves on; every
+// other role reads the slot once and releases it.  A value >= nitems ends the sequence.
+template <int BN>
+__device__ __forceinline__ bool publish_item(Smem<BN>& sm, uint32_t k, int64_t item) {
+    const uint32_t j = k % IR;
+    if (!mbar_wait(&sm.itempty[j], ((k / IR) & 1) ^ 1)) return false;
+    sm.items[j] = item;
+    mbar_arrive(&sm.itfull[j]);
+    return true;
+}
+// Called by one thread (whole_warp false) or by a whole converged warp; -1 on a timeout.
+template <int BN>
+__device__ __forceinline__ int64_t take_item(Smem<BN>& sm, uint32_t k, bool whole_warp) {
+    const uint32_t j = k % IR;
+    bool ok = mbar_wait(&sm.itfull[j], (k / IR) & 1);
+    if (whole_warp) ok = __all_sync(0xffffffffu, ok);
+    if (!ok) return -1;
+    const int64_t item = sm.items[j];
+    if (whole_warp) __syncwarp();
+    if (!whole_warp || (threadIdx.x & 31) == 0) mbar_arrive(&sm.itempty[j]);
+    return item;
+}
+
 struct UwArgs {
     int64_t n;          // rows of U
     int nkt;            // K steps (ceil(rank / 64))
@@ -506,6 +540,7 @@ struct UtvArgs {
     int c;
     double* part;       // part[(chunk * c + j) * r + a]
     int* err;
+    int* next;          // work-item counter, zero at launch
 };
 
 // Partial U^T V: items (column block of U, chunk of rows), persistent over items.
@@ -528,17 +563,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            uint32_t it = 0;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            uint32_t it = 0, k = 0;
+            int64_t item = blockIdx.x;
+            while (ok) {
+                if (!publish_item<BN>(sm, k++, item)) { ok = false; break; }
+                if (item >= nitems) break;
                 const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
                 const int64_t i0 = ch * p.chunk;
                 const int nk = ksteps(item);
+                // the next item is claimed 8 steps before the end of this one, so that the
+                // atomic's latency overlaps the copies still to be issued
+                const int claim_at = nk > 8 ? nk - 8 : 0;
+                int64_t nxt = nitems;
                 for (int kt = 0; kt < nk; ++kt, ++it) {
+                    if (kt == claim_at) nxt = (int64_t)gridDim.x + atomicAdd(p.next, 1);
                     const uint32_t s = it % S_U;
                     if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
                     mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
                     tma_load_2d(sm.U + s * SM::UBYTES, &mU, (int)(mb * BM), (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
                 }
+                item = nxt;
             }
             if (!producer_drain(sm.ufull, S_U, it)) ok = false;
             if (!ok) atomicExch(p.err, 1);
@@ -546,7 +590,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 10) {
         if (lane == 0) {
             uint32_t it = 0;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (uint32_t k = 0; ok; ++k) {
+                const int64_t item = take_item<BN>(sm, k, false);
+                if (item < 0) { ok = false; break; }
+                if (item >= nitems) break;
                 const int64_t i0 = (item / p.mblocks) * p.chunk;
                 const int nk = ksteps(item);
                 for (int kt = 0; kt < nk && ok; ++kt, ++it)
@@ -557,7 +604,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp == 1) {
         uint32_t it = 0;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
             const int nk = ksteps(item);
             for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = mma_step<BN>(sm, tmem, it, lane);
         }
@@ -567,14 +617,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // columns], so each load of the warp reads 32 consecutive floats of one row
         const int q = warp & 3, m = 32 * q + lane;
         uint32_t it = 0;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
             const int nk = ksteps(item);
             for (int kt = 0; kt < nk; ++kt, ++it) {
                 if (!convert_wait<BN>(sm, it)) { ok = false; break; }
                 const float* R = reinterpret_cast<const float*>(sm.U + (it % S_U) * SM::UBYTES) + m;
                 float x[64];
 #pragma unroll
-                for (int k = 0; k < BK; ++k) x[k] = R[k * BM];
+                for (int k2 = 0; k2 < BK; ++k2) x[k2] = R[k2 * BM];
                 convert_release<BN>(sm, it, lane);
                 convert_publish<BN>(sm, tmem, it, q, lane, x);
             }
@@ -583,7 +636,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else {
         const int q = warp & 3;
         uint32_t it = 0;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
             float acc[BN];
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
@@ -709,7 +765,9 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
         !make_map(&mVl, vlo, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, KH, BN, true))
         return fail(HDF_ECUDA, "tensor-core matvec: cannot encode a tensor map");
     const int nch = (int)((n + chunk - 1) / chunk);
-    UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, err};
+    int* next = reinterpret_cast<int*>(vlo + (size_t)c * ldo);      // one int past the split V
+    HDF_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
+    UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, err, next};
     const size_t sm = Smem<BN>::bytes();
     HDF_CUDA(cudaFuncSetAttribute(k_tc_utv<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t nitems = (int64_t)a.mblocks * nch;
@@ -729,7 +787,7 @@ size_t tc_work_floats(int64_t n, int64_t r, int c) {
     const int bn = tc_bn(c);
     const int64_t kpad = ((r + tc::BK - 1) / tc::BK) * tc::BK;
     const int64_t ldo = ((n + 3) / 4) * 4;
-    return std::max<size_t>(2 * (size_t)bn * kpad, 2 * (size_t)c * ldo);
+    return std::max<size_t>(2 * (size_t)bn * kpad, 2 * (size_t)c * ldo + 4);   // + the U^T V item counter
 }
 
 // Rows-per-chunk split for U^T V on the tensor cores: enough (column block, chunk) items.
