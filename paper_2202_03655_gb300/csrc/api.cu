@@ -795,17 +795,29 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         P.U = f->U.p; P.ldU = I.ldu;
         P.coefA = dA.p; P.coefB = dB.p;
         const int levels = d - 2;
-        const size_t fixed = sizeof(T) * 2 * levels * ht.tri;
-        const size_t budget = 200 * 1024;
-        const int pw_fly = dev::uwriter_per_warp(levels, ht.tri, L_used, tb.nYp, nF, false);
-        const int pw_pre = dev::uwriter_per_warp(levels, ht.tri, L_used, tb.nYp, nF, true);
-        const bool pre = fixed + sizeof(T) * 4 * (size_t)pw_pre <= budget;
-        const int per_warp = pre ? pw_pre : pw_fly;
-        P.per_warp = per_warp;
-        int warps = 8;
-        while (warps > 1 && fixed + sizeof(T) * (size_t)warps * per_warp > budget) warps >>= 1;
-        const size_t sm = fixed + sizeof(T) * (size_t)warps * per_warp;
-        if (sm > budget) return fail(HDF_ETOOBIG, "hdf_build: harmonic tables exceed shared memory");
+        // One CTA per SM with as many warps as shared memory holds (up to 32): the coefficient
+        // tables and, when they fit, the per-point index tables are shared by all its warps.
+        // Preference: harmonics precomputed per point (pre) with staged tables, then the
+        // on-the-fly variant with staged tables, then either with tables read from global.
+        const size_t coef = dev::align16(sizeof(T) * 2 * (size_t)levels * ht.tri);
+        const size_t budget = 226 * 1024;
+        const int64_t nq = I.ldu / (int64_t)(sizeof(T) == 4 ? 4 : 2);
+        struct Cfg { bool pre, staged; int warps; size_t pw; size_t tabs; };
+        Cfg pick{false, false, 0, 0, 0};
+        for (int attempt = 0; attempt < 4 && pick.warps == 0; ++attempt) {
+            const bool pre = (attempt % 2) == 0, staged = attempt < 2;
+            const size_t pw = sizeof(T) * (size_t)dev::uwriter_per_warp(levels, ht.tri, L_used, tb.nYp, nF, pre);
+            const size_t tabs = staged ? dev::uwriter_tab_bytes(nq, (int)nH, chain_stride(d), tb.nYp, pre) : 0;
+            if (coef + tabs >= budget) continue;
+            const int w = (int)std::min<size_t>(32, (budget - coef - tabs) / pw);
+            if (w >= (attempt < 3 ? 8 : 1)) pick = Cfg{pre, staged, w, pw, tabs};
+        }
+        if (pick.warps == 0) return fail(HDF_ETOOBIG, "hdf_build: harmonic tables exceed shared memory");
+        const bool pre = pick.pre;
+        const int warps = pick.warps;
+        P.per_warp = (int)(pick.pw / sizeof(T));
+        P.tab_bytes = (int)pick.tabs;
+        const size_t sm = dev::align16((size_t)warps * pick.pw + sizeof(T) * 2 * (size_t)levels * ht.tri) + pick.tabs;
         auto kern = pre ? dev::k_uwriter<T, true> : dev::k_uwriter<T, false>;
         HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         int occ = 0;
@@ -815,7 +827,7 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
         const int grid = std::max(1, std::min<int>(nsm * std::max(occ, 1), (int)((n + warps - 1) / warps)));
         HDF_COUNT_LAUNCH();
-        kern<<<grid, warps * 32, sm, st>>>(P);
+        kern<<<grid, warps * 32, sm, st>>>(P);   // P.tab_bytes: staged index tables
         HDF_CUDA(cudaGetLastError());
     }
     HDF_CUDA(cudaEventRecord(ev[2], st));

@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict_
         __syncthreads();
         dev::uwriter_zero_slots<T>(S.uw, S.pre != 0, base, lane);     // slots of this set's layout
         const int64_t t1 = min(t0 + dev::kFTile, S.uw.n);
-        for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, S.pre != 0, i, cA, cB, base, lane);
+        const dev::UWTabs X{S.uw.qdesc, S.uw.chains, S.uw.gslot, S.uw.ychain};
+        for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, X, S.pre != 0, i, cA, cB, base, lane);
         __syncthreads();
     }
 }

@@ -334,7 +334,25 @@ struct UWParams {
     void* U; int64_t ldU;
     const void* coefA; const void* coefB;   // (d-2) x tri, type T
     int per_warp;              // shared elements (type T) per warp
+    int tab_bytes;             // bytes of index tables staged in shared memory (0: read from global)
 };
+
+// The index tables the U writer reads for every point (global, or staged in shared memory).
+struct UWTabs {
+    const uint32_t* qdesc;
+    const int16_t* chains;
+    const int32_t* gslot;
+    const int32_t* ychain;
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Bytes of the staged index tables: qdesc, chains, gslot, and ychain when harmonics are not
+// precomputed; the kernel lays them out in this order, each 16-byte aligned.
+__host__ __device__ inline size_t uwriter_tab_bytes(int64_t nq, int nH, int cstride, int nYp, bool pre) {
+    return align16(sizeof(uint32_t) * nq) + align16(sizeof(int16_t) * (size_t)nH * cstride) +
+           align16(sizeof(int32_t) * (size_t)nH) + (pre ? 0 : align16(sizeof(int32_t) * (size_t)nYp));
+}
 
 // Shared elements (type T) per warp of the U writer (a multiple of 16 bytes).
 __host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int nYp, int nF, bool pre) {
@@ -348,8 +366,8 @@ __host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int 
 // are multiplied out from the level tables as it is written.  Every VW-wide chunk of the row
 // is one radial factor times VW consecutive harmonic slots (columns are padded per (k, s)).
 template <typename T>
-__device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64_t i, const T* cA, const T* cB,
-                                              T* base, int lane) {
+__device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X, bool pre, int64_t i, const T* cA,
+                                              const T* cB, T* base, int lane) {
     const int levels = P.d - 2;
     T* Ys = base;                                // nYp (pre only)
     T* tbl = base + (pre ? P.nYp : 0);           // levels * tri
@@ -418,8 +436,8 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
     if (pre) {
         // padding slots were zeroed once per warp and are never written
         for (int g = lane; g < P.nH; g += 32) {
-            const int16_t* c = P.chains + (int64_t)g * P.cstride;
-            const int slot = __ldg(P.gslot + g);
+            const int16_t* c = X.chains + (int64_t)g * P.cstride;
+            const int slot = X.gslot[g];
             T v = trig[P.L + c[levels]];
             for (int j = 0; j < levels; ++j) v *= tbl[j * P.tri + c[j]];
             Ys[slot] = v;
@@ -430,7 +448,7 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
     T* row = Ug + i * P.ldU;
     const int64_t nq = P.ldU / VW;
     auto chunk = [&](int64_t q) {
-        const uint32_t dsc = __ldg(P.qdesc + q);
+        const uint32_t dsc = X.qdesc[q];
         const T f = Fs[dsc >> 20];
         const uint32_t y0 = dsc & 0xFFFFFu;
         VT out;
@@ -442,12 +460,12 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, bool pre, int64
             T v[VW];
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                const int ch = __ldg(P.ychain + y0 + e);
+                const int ch = X.ychain[y0 + e];
                 T h = (T)0;
                 if (ch >= 0) {
-                    const int16_t* c = P.chains + (int64_t)ch * P.cstride;
-                    h = trig[P.L + __ldg(c + levels)];
-                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + __ldg(c + j)];
+                    const int16_t* c = X.chains + (int64_t)ch * P.cstride;
+                    h = trig[P.L + c[levels]];
+                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + c[j]];
                 }
                 v[e] = f * h;
             }
@@ -475,8 +493,9 @@ __device__ __forceinline__ void uwriter_zero_slots(const UWParams& P, bool pre, 
 }
 
 // Shared memory of the U writer: [nwarps x per_warp][coefA][coefB] (elements of T).
+// Shared memory: [nwarps x per_warp elements][cA][cB][staged index tables (tab_bytes)].
 template <typename T, bool PRE>
-__global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
+__global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int levels = P.d - 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -487,10 +506,31 @@ __global__ void __launch_bounds__(256) k_uwriter(UWParams P) {
         cA[idx] = reinterpret_cast<const T*>(P.coefA)[idx];
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
+    UWTabs X{P.qdesc, P.chains, P.gslot, P.ychain};
+    if (P.tab_bytes) {
+        unsigned char* tp = reinterpret_cast<unsigned char*>(smem_raw) +
+                            align16(sizeof(T) * ((size_t)nwarps * P.per_warp + 2 * (size_t)levels * P.tri));
+        const int64_t nq = P.ldU / Vec2<T>::w;
+        uint32_t* q = reinterpret_cast<uint32_t*>(tp);
+        for (int64_t k = threadIdx.x; k < nq; k += blockDim.x) q[k] = P.qdesc[k];
+        tp += align16(sizeof(uint32_t) * nq);
+        int16_t* ch = reinterpret_cast<int16_t*>(tp);
+        for (int64_t k = threadIdx.x; k < (int64_t)P.nH * P.cstride; k += blockDim.x) ch[k] = P.chains[k];
+        tp += align16(sizeof(int16_t) * (size_t)P.nH * P.cstride);
+        int32_t* gs = reinterpret_cast<int32_t*>(tp);
+        for (int k = threadIdx.x; k < P.nH; k += blockDim.x) gs[k] = P.gslot[k];
+        tp += align16(sizeof(int32_t) * (size_t)P.nH);
+        X.qdesc = q; X.chains = ch; X.gslot = gs;
+        if (!PRE) {
+            int32_t* yc = reinterpret_cast<int32_t*>(tp);
+            for (int k = threadIdx.x; k < P.nYp; k += blockDim.x) yc[k] = P.ychain[k];
+            X.ychain = yc;
+        }
+    }
     __syncthreads();
     uwriter_zero_slots<T>(P, PRE, base, lane);
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
-    for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, PRE, i, cA, cB, base, lane);
+    for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, X, PRE, i, cA, cB, base, lane);
 }
 
 // --------------------------------------------------------------------- A7: matvec
