@@ -98,10 +98,11 @@ typedef struct {
                                on |K - K~|_F / |K|_F */
     int s_k[HDF_MAX_L + 1]; /* kept radial rank per harmonic degree k (Sec. 3.4) */
     double t_ms[HDF_NPHASE];/* build phase times in ms: 0 centre/radius/mu2 reductions,
-                               1 Chebyshev + degree + radial cores (host), 2 radial-basis Gram
-                               (device), 3 basis factor + eigendecompositions + truncation
-                               (host), 4 radial factors (device), 5 harmonics + U (device),
-                               6 unused, 7 whole build */
+                               1 Chebyshev + degree + radial cores (host, while the device
+                               sums the radial moments), 2 rest of the moments + radial-basis
+                               Gram, 3 basis factor + eigendecompositions + truncation (host),
+                               4 radial factors (device), 5 harmonics + U (device), 6 unused,
+                               7 whole build */
 } hdf_info;
 
 /* ---------------------------------------------------------------- factorization ---- */

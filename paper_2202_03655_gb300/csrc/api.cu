@@ -248,12 +248,10 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
 
     tph[0] = now_ms() - t_start;
     double t0 = now_ms();
-    // ---- A1-A2: Chebyshev coefficients, degree, radial cores (host)
+    // ---- A1: Chebyshev coefficients and degree (host)
     DegreePlan dp;
-    plan_degree(kernel, lengthscale, R, mu2, n, tol, eta, p_max, d, true, dp);
+    plan_degree(kernel, lengthscale, R, mu2, n, tol, eta, p_max, d, true, dp, false);
     const int p = dp.p, L = dp.L;
-    tph[1] = now_ms() - t0;
-    t0 = now_ms();
 
     // ---- A3: Chebyshev moments of the radial data (FP64 on the device) -> basis Gram matrices
     const int nmom = 2 * L + 2;
@@ -272,6 +270,10 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     HDF_CUDA(cudaGetLastError());
     std::vector<double> mom(nmom);
     HDF_CUDA(cudaMemcpyAsync(mom.data(), msum.p, nmom * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // ---- A2 (host, while the device sums the moments): radial cores of each degree
+    radial_cores(dp.a.data(), dp.p, d, dp.cores, true);
+    tph[1] = now_ms() - t0;
+    t0 = now_ms();
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<double> gram;
     gram_from_moments(mom, L, gram);

@@ -1,6 +1,9 @@
 // Host-side planning of the HDF factorization (FP64).  See planner.h.
 #include "planner.h"
 
+#include <condition_variable>
+#include <mutex>
+
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -36,20 +39,64 @@ double kernel_dell(int kernel, double r, double ell) {
     return kernel_dz(kernel, z) * (-z / ell);
 }
 
+// Persistent worker pool: the workers are created once and sleep between jobs, so a planning
+// step pays no thread start-up.  One job at a time; a concurrent or nested call runs serially.
+namespace {
+struct Pool {
+    std::mutex m;
+    std::condition_variable go, done;
+    std::mutex busy;
+    const std::function<void(int)>* job = nullptr;
+    int n = 0, active = 0, workers = 0;
+    uint64_t gen = 0;
+    std::atomic<int> next{0};
+    Pool() {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        workers = std::min(hw, 32) - 1;
+        for (int t = 0; t < workers; ++t) std::thread([this]() { loop(); }).detach();
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            std::unique_lock<std::mutex> lk(m);
+            go.wait(lk, [&]() { return gen != seen; });
+            seen = gen;
+            const std::function<void(int)>* f = job;
+            const int N = n;
+            lk.unlock();
+            for (int i = next.fetch_add(1); i < N; i = next.fetch_add(1)) (*f)(i);
+            lk.lock();
+            if (--active == 0) done.notify_all();
+        }
+    }
+};
+Pool& pool() {
+    static Pool* p = new Pool();     // never destroyed: detached workers outlive static destructors
+    return *p;
+}
+}  // namespace
+
 void parallel_for(int n, const std::function<void(int)>& fn) {
-    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(std::min(n, hw), 32);
-    if (nt <= 1) {
+    Pool& P = pool();
+    if (n <= 1 || P.workers == 0 || !P.busy.try_lock()) {
         for (int i = 0; i < n; ++i) fn(i);
         return;
     }
-    std::atomic<int> next(0);
-    std::vector<std::thread> pool;
-    for (int t = 0; t < nt; ++t)
-        pool.emplace_back([&]() {
-            for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
-        });
-    for (auto& th : pool) th.join();
+    {
+        std::lock_guard<std::mutex> lk(P.m);
+        P.job = &fn;
+        P.n = n;
+        P.next.store(0);
+        P.active = P.workers;
+        ++P.gen;
+    }
+    P.go.notify_all();
+    for (int i = P.next.fetch_add(1); i < n; i = P.next.fetch_add(1)) fn(i);
+    {
+        std::unique_lock<std::mutex> lk(P.m);
+        P.done.wait(lk, [&]() { return P.active == 0; });
+    }
+    P.busy.unlock();
 }
 
 // ----------------------------------------------------------------------- Chebyshev
@@ -107,44 +154,95 @@ static int64_t binom(int64_t n, int64_t k) {
 int64_t harmonic_count(int k, int d) { return binom(k + d - 1, k) - binom(k + d - 3, k - 2); }
 
 // -------------------------------------------------------------- symmetric eigen
+// Symmetric eigendecomposition A = V diag(w) V^T (row-major, V's columns the eigenvectors, in
+// no particular order; A is overwritten).  Householder reduction to tridiagonal form, then the
+// implicit symmetric QR iteration with Wilkinson shifts and deflation, rotations accumulated
+// into V (Golub and Van Loan, Matrix Computations, Alg. 8.3.1 and 8.3.3).
 void sym_eig(int n, double* A, double* w, double* V) {
     for (int i = 0; i < n * n; ++i) V[i] = 0.0;
     for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int p = 0; p < n; ++p) {
-            tot += A[p * n + p] * A[p * n + p];
-            for (int q = p + 1; q < n; ++q) off += 2.0 * A[p * n + q] * A[p * n + q];
+    if (n == 1) { w[0] = A[0]; return; }
+    std::vector<double> v(n), pv(n), e(n, 0.0);
+    // Householder: for column k, H = I - beta v v^T maps A[k+1:, k] to (alpha, 0, ..., 0)
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        double xn = 0.0;
+        for (int i = 0; i < m; ++i) { v[i] = A[(k + 1 + i) * n + k]; xn += v[i] * v[i]; }
+        xn = std::sqrt(xn);
+        if (xn == 0.0) continue;
+        const double alpha = v[0] > 0.0 ? -xn : xn;
+        v[0] -= alpha;
+        double vn2 = 0.0;
+        for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+        if (vn2 == 0.0) continue;
+        const double beta = 2.0 / vn2;
+        // p = beta A_sub v, K = (beta / 2) v^T p, q = p - K v, A_sub -= v q^T + q v^T
+        double K = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double t = 0.0;
+            const double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+            for (int j = 0; j < m; ++j) t += row[j] * v[j];
+            pv[i] = beta * t;
+            K += v[i] * pv[i];
         }
-        if (off <= 1e-32 * (tot + off) || off == 0.0) break;
-        for (int p = 0; p < n; ++p) {
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
-                if (apq == 0.0) continue;
-                const double app = A[p * n + p], aqq = A[q * n + q];
-                const double theta = (aqq - app) / (2.0 * apq);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {          // A <- A J
-                    const double akp = A[k * n + p], akq = A[k * n + q];
-                    A[k * n + p] = c * akp - s * akq;
-                    A[k * n + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {          // A <- J^T A
-                    const double apk = A[p * n + k], aqk = A[q * n + k];
-                    A[p * n + k] = c * apk - s * aqk;
-                    A[q * n + k] = s * apk + c * aqk;
-                }
-                A[p * n + q] = A[q * n + p] = 0.0;
-                for (int k = 0; k < n; ++k) {          // V <- V J
-                    const double vkp = V[k * n + p], vkq = V[k * n + q];
-                    V[k * n + p] = c * vkp - s * vkq;
-                    V[k * n + q] = s * vkp + c * vkq;
-                }
-            }
+        K *= 0.5 * beta;
+        for (int i = 0; i < m; ++i) pv[i] -= K * v[i];
+        for (int i = 0; i < m; ++i) {
+            double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+            for (int j = 0; j < m; ++j) row[j] -= v[i] * pv[j] + pv[i] * v[j];
+        }
+        A[(k + 1) * n + k] = A[k * n + k + 1] = alpha;
+        for (int i = 1; i < m; ++i) A[(k + 1 + i) * n + k] = A[k * n + k + 1 + i] = 0.0;
+        // V <- V H on columns k+1 .. n-1
+        for (int r = 0; r < n; ++r) {
+            double* row = V + (size_t)r * n + (k + 1);
+            double t = 0.0;
+            for (int j = 0; j < m; ++j) t += row[j] * v[j];
+            t *= beta;
+            for (int j = 0; j < m; ++j) row[j] -= t * v[j];
         }
     }
     for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+    for (int i = 0; i + 1 < n; ++i) e[i] = A[i * n + i + 1];
+    // implicit QR on the tridiagonal (w, e); rotation G in plane (k, k+1) with G_kk = G_k+1,k+1 = c,
+    // G_k,k+1 = s, G_k+1,k = -s, T <- G^T T G, V <- V G
+    const double eps = 2.220446049250313e-16;
+    int q = n - 1, iters = 0;
+    while (q > 0 && iters < 64 * n) {
+        for (int i = 0; i < q; ++i)
+            if (std::fabs(e[i]) <= eps * (std::fabs(w[i]) + std::fabs(w[i + 1]))) e[i] = 0.0;
+        while (q > 0 && e[q - 1] == 0.0) --q;
+        if (q == 0) break;
+        int p = q - 1;
+        while (p > 0 && e[p - 1] != 0.0) --p;
+        ++iters;
+        // Wilkinson shift from the trailing 2 x 2 block
+        const double dl = 0.5 * (w[q - 1] - w[q]), eq = e[q - 1];
+        const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * std::hypot(dl, eq);
+        const double mu = w[q] - eq * eq / den;
+        double x = w[p] - mu, z = e[p];
+        for (int k = p; k < q; ++k) {
+            const double r = std::hypot(x, z);
+            const double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : -z / r;
+            if (k > p) e[k - 1] = r;
+            const double a = w[k], f = e[k], g = w[k + 1];
+            w[k] = c * c * a - 2.0 * c * s * f + s * s * g;
+            w[k + 1] = s * s * a + 2.0 * c * s * f + c * c * g;
+            e[k] = c * s * (a - g) + (c * c - s * s) * f;
+            if (k + 1 < q) {
+                const double h = e[k + 1];
+                z = -s * h;                   // bulge T[k, k+2]
+                e[k + 1] = c * h;
+                x = e[k];
+            }
+            for (int r2 = 0; r2 < n; ++r2) {
+                double* row = V + (size_t)r2 * n;
+                const double vk = row[k], vk1 = row[k + 1];
+                row[k] = c * vk - s * vk1;
+                row[k + 1] = s * vk + c * vk1;
+            }
+        }
+    }
 }
 
 void gauss_gegenbauer(int N, double lam, double* t, double* w) {
@@ -323,7 +421,7 @@ void append_chains(int k, int d, int L, std::vector<int16_t>& out) {
 namespace hdf {
 
 void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double tol, double eta, int p_max,
-                 int d, bool threads, DegreePlan& out) {
+                 int d, bool threads, DegreePlan& out, bool with_cores) {
     const int M = cheb_nodes(p_max);
     out.a.assign(M, 0.0);
     cheb_coeffs(kernel, ell, 2.0 * R, M, false, out.a.data());
@@ -331,7 +429,7 @@ void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double
     out.drop_budget = 0.5 * eta * tol * (double)n * std::sqrt(mu2);
     out.p = choose_degree(out.a.data(), M, out.tail_budget, p_max, &out.tail, &out.reached);
     out.L = out.p / 2;
-    radial_cores(out.a.data(), out.p, d, out.cores, threads);
+    if (with_cores) radial_cores(out.a.data(), out.p, d, out.cores, threads);
 }
 
 void gram_from_moments(const std::vector<double>& m, int L, std::vector<double>& gram) {

@@ -74,8 +74,10 @@ struct DegreePlan {
     std::vector<double> a;
     std::vector<std::vector<double>> cores;
 };
+// with_cores false leaves out.cores empty (the caller runs radial_cores itself, e.g. while the
+// device computes the radial moments).
 void plan_degree(int kernel, double ell, double R, double mu2, int64_t n, double tol, double eta, int p_max,
-                 int d, bool threads, DegreePlan& out);
+                 int d, bool threads, DegreePlan& out, bool with_cores = true);
 
 // Radial-basis Gram sums (the layout plan_factor takes) from the Chebyshev moments
 // m_j = sum_i T_j(u_i), j <= 2L+1, using T_l T_l' = (T_{l+l'} + T_{|l-l'|})/2 and
