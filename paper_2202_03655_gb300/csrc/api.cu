@@ -745,13 +745,31 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(PL.dgslot.alloc(sizeof(int32_t) * tb.gslot.size()));
     HDF_CUDA(dA.alloc(sizeof(T) * cA.size() + 16));
     HDF_CUDA(dB.alloc(sizeof(T) * cB.size() + 16));
-    const int64_t ldF = nF;
+    const int64_t ldF = ((int64_t)nF + 31) / 32 * 32;       // 128-byte rows (FP32): whole-sector stores
     if (dF.alloc_on(sizeof(T) * (size_t)n * ldF, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build: cannot allocate the radial factor buffer");
     }
     if (!Qmat[0].empty()) HDF_CUDA(cudaMemcpyAsync(dQ0.p, Qmat[0].data(), sizeof(double) * Qmat[0].size(), cudaMemcpyHostToDevice, st));
     if (!Qmat[1].empty()) HDF_CUDA(cudaMemcpyAsync(dQ1.p, Qmat[1].data(), sizeof(double) * Qmat[1].size(), cudaMemcpyHostToDevice, st));
+    // FP32 factors: [Qmat0 | Qmat1] as (hi, lo) float pairs for the compensated radial basis,
+    // (L+1) x mtp with the odd columns zero in row L and mtp a multiple of 8
+    const int mtp = ((m0 + m1 + 7) / 8) * 8;
+    if (sizeof(T) == 4) {
+        std::vector<float> qc((size_t)2 * (L + 1) * mtp, 0.f);
+        auto put = [&](int l, int o, double v) {
+            const float h = (float)v;
+            qc[2 * ((size_t)l * mtp + o)] = h;
+            qc[2 * ((size_t)l * mtp + o) + 1] = (float)(v - (double)h);
+        };
+        for (int l = 0; l < nb0; ++l)
+            for (int o = 0; o < m0; ++o) put(l, o, Qmat[0][(size_t)l * m0 + o]);
+        for (int l = 0; l < nb1; ++l)
+            for (int o = 0; o < m1; ++o) put(l, m0 + o, Qmat[1][(size_t)l * m1 + o]);
+        HDF_CUDA(PL.dQC.alloc(sizeof(float) * qc.size()));
+        HDF_CUDA(cudaMemcpyAsync(PL.dQC.p, qc.data(), sizeof(float) * qc.size(), cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaStreamSynchronize(st));      // qc is a local buffer
+    }
     HDF_CUDA(cudaMemcpyAsync(dW.p, Wt.data(), sizeof(T) * Wt.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(dpar.p, tb.colpar.data(), tb.colpar.size(), cudaMemcpyHostToDevice, st));
     if (!tb.chains.empty())
@@ -770,18 +788,35 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
     HDF_CUDA(cudaEventRecord(ev[0], st));
     // A5a: radial factors F
     {
-        const size_t sm = dev::radialF_smem(L, m0, m1, sizeof(T));
-        if (sm > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
-        HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        const int grid = grid_for((n + dev::kFTile - 1) / dev::kFTile, 1, 152 * 8);
         dev::RFParams R{};
         R.x = x; R.n = n; R.d = d; R.c = cen; R.inv2R = inv2R; R.L = L;
         R.Qm0 = dQ0.as<double>(); R.nb0 = nb0; R.m0 = m0;
         R.Qm1 = dQ1.as<double>(); R.nb1 = nb1; R.m1 = m1;
         R.Wt = dW.p; R.colpar = dpar.as<uint8_t>(); R.nF = nF;
         R.F = dF.p; R.ldF = ldF;
-        HDF_COUNT_LAUNCH();
-        dev::k_radial_F<T><<<grid, 256, sm, st>>>(R);
+        const int grid = grid_for((n + dev::kFTile - 1) / dev::kFTile, 1, 152 * 8);
+        const size_t sm64 = dev::radialF_smem(L, m0, m1, sizeof(T));
+        size_t sm32 = dev::radialF_df_smem(L, m0, m1, mtp, nF, true);
+        R.stage_wt = 1;
+        if (sm32 > 200 * 1024) { sm32 = dev::radialF_df_smem(L, m0, m1, mtp, nF, false); R.stage_wt = 0; }
+        if (sizeof(T) == 4 && sm32 <= 200 * 1024) {
+            R.QC = PL.dQC.as<float2>();
+            R.mtp = mtp;
+            HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32));
+            int occ = 0, nsm = 0, dv = 0;
+            HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_radial_F_df, dev::kRfThreads, sm32));
+            HDF_CUDA(cudaGetDevice(&dv));
+            HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
+            const int g32 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
+                                                                          (n + dev::kFTile - 1) / dev::kFTile));
+            HDF_COUNT_LAUNCH();
+            dev::k_radial_F_df<<<g32, dev::kRfThreads, sm32, st>>>(R);
+        } else {
+            if (sm64 > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
+            HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));
+            HDF_COUNT_LAUNCH();
+            dev::k_radial_F<T><<<grid, 256, sm64, st>>>(R);
+        }
         HDF_CUDA(cudaGetLastError());
     }
     HDF_CUDA(cudaEventRecord(ev[1], st));

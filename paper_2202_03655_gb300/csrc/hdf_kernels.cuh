@@ -225,6 +225,8 @@ static __global__ void k_reduce_cols(const double* __restrict__ part, int nblk, 
     out[j] = s;
 }
 
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 // ------------------------------------------------------------- A5a: radial factors
 // Per point: B_par (FP64) -> Q_par = B_par Qmat_par (FP64, the orthonormalised radial basis
 // of Eq. svd) -> F[i, col] = sum_l Q_par(col)[l] Wt[l, col] (type T).  Tiles of 32 points.
@@ -234,6 +236,8 @@ struct RFParams {
     const double* x; int64_t n; int d; Center c; double inv2R; int L;
     const double* Qm0; int nb0, m0;
     const double* Qm1; int nb1, m1;
+    const float2* QC; int mtp;   // FP32 factors: [Qm0 | Qm1] as (hi, lo) float pairs, (L+1) x mtp
+    int stage_wt;                // FP32 factors: copy Wt into shared memory
     const void* Wt; const uint8_t* colpar; int nF;
     void* F; int64_t ldF;
 };
@@ -241,6 +245,149 @@ struct RFParams {
 // Dynamic shared memory of one radial tile, in bytes.
 __host__ __device__ inline size_t radialF_smem(int L, int m0, int m1, size_t tsize) {
     return sizeof(double) * (kFTile * (L + 1) + kFTile) + tsize * (size_t)(m0 + m1) * kFTile;
+}
+
+// Compensated FP32 arithmetic for the radial basis of FP32 factors.  Q = B Qmat cancels (Qmat
+// grows like the inverse square root of the smallest kept Gram eigenvalue), so a plain FP32
+// sum is not enough; FP64 is, but runs at a small fraction of the FP32 rate on this GPU.  The
+// basis values and Qmat are carried as unevaluated (hi, lo) float pairs (about 48 bits) and the
+// dot product uses error-free transformations: TwoProd by fma (Dekker/Kahan) and TwoSum
+// (Knuth), the "Dot2" scheme of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005), whose
+// result is as accurate as a sum in twice the working precision.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// One Dot2 step: (sh, c) accumulates a * (bh + bl), a = (hi, lo).
+__device__ __forceinline__ void dot2_step(float2 a, float bh, float bl, float& sh, float& c) {
+    const float ph = a.x * bh;
+    float pe = fmaf(a.x, bh, -ph);
+    pe = fmaf(a.x, bl, fmaf(a.y, bh, pe));
+    float s2, es;
+    two_sum(sh, ph, s2, es);
+    sh = s2;
+    c += es + pe;
+}
+
+// FP32 factors (k_radial_F_df), one tile of kFTile points in three parts:
+//   basis: u = 8 rho^2 - 1 and T_l(u) by the FP64 recurrence, split into (hi, lo) float pairs;
+//   Q:     Q[o][p] = sum_l T_l(u_p) Qmat[l][o] by Dot2 against QC, the combined even | odd Qmat as
+//          float pairs ((L+1) x mtp, odd columns zero in row L, mtp a multiple of 8), times rho
+//          for the odd outputs;
+//   F:     F[p][col] = sum_l Q[par(col) block + l][p] Wt[l][col] in FP32.
+// The basis of the next tile is computed by a separate warp while the others work on this one.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+// Basis values of one point in double-float arithmetic (FP32 pairs, about 48 bits): u and rho
+// from FP64 coordinates (a few FP64 operations), then T_l(u) = 2 u T_{l-1} - T_{l-2} with
+// error-free products and sums; the recurrence is stable on [-1, 1].
+__device__ __forceinline__ void radialF_df_basis(const RFParams& P, int64_t t0, int p, float2* Ts, float* rh) {
+    const int LP1 = P.L + 1;
+    const int cnt = (int)min((int64_t)kFTile, P.n - t0);
+    float2* Tp = Ts + p * LP1;
+    double s = 0.0;
+    if (p < cnt) {
+        const int64_t i = t0 + p;
+        for (int j = 0; j < P.d; ++j) { const double y = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R; s += y * y; }
+    }
+    const double u = 8.0 * s - 1.0;
+    rh[p] = sqrtf((float)s);
+    const float uh = (float)u, ul = (float)(u - (double)uh);
+    const float u2h = 2.f * uh, u2l = 2.f * ul;                     // 2u, exact
+    float ah = 1.f, al = 0.f, bh = uh, bl = ul;                       // T_{l-2}, T_{l-1}
+    Tp[0] = make_float2(1.f, 0.f);
+    if (P.L >= 1) Tp[1] = make_float2(uh, ul);
+    for (int l = 2; l <= P.L; ++l) {
+        // (ph, pl) = 2u * T_{l-1}
+        const float ph = u2h * bh;
+        float pl = fmaf(u2h, bh, -ph);
+        pl = fmaf(u2h, bl, fmaf(u2l, bh, pl));
+        // T_l = (ph, pl) - T_{l-2}
+        float sh, se;
+        two_sum(ph, -ah, sh, se);
+        se += pl - al;
+        float th, tl;
+        fast_two_sum(sh, se, th, tl);
+        Tp[l] = make_float2(th, tl);
+        ah = bh; al = bl;
+        bh = th; bl = tl;
+    }
+}
+
+// Q part, by the nth compute threads (thread = point p and a group of kOpt outputs: each basis
+// value read from shared memory serves kOpt outputs, one 16-byte load brings two outputs).
+__device__ __forceinline__ void radialF_df_q(const RFParams& P, const float2* Ts, const float* rh, const float2* QC,
+                                             float* Qs, int tid, int nth) {
+    constexpr int kOpt = 8;
+    const int LP1 = P.L + 1;
+    const int mt = P.m0 + P.m1;
+    const int p = tid % kFTile;
+    const float2* Tp = Ts + p * LP1;
+    for (int o0 = (tid / kFTile) * kOpt; o0 < mt; o0 += (nth / kFTile) * kOpt) {
+        float sh[kOpt], c[kOpt];
+#pragma unroll
+        for (int j = 0; j < kOpt; ++j) { sh[j] = 0.f; c[j] = 0.f; }
+        for (int l = 0; l < LP1; ++l) {
+            const float2 a = Tp[l];
+            const float4* qr = reinterpret_cast<const float4*>(QC + (size_t)l * P.mtp + o0);
+#pragma unroll
+            for (int j2 = 0; j2 < kOpt / 2; ++j2) {
+                const float4 b = qr[j2];
+                dot2_step(a, b.x, b.y, sh[2 * j2], c[2 * j2]);
+                dot2_step(a, b.z, b.w, sh[2 * j2 + 1], c[2 * j2 + 1]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kOpt; ++j) {
+            const int o = o0 + j;
+            if (o < mt) {
+                float q = sh[j] + c[j];
+                if (o >= P.m0) q *= rh[p];
+                Qs[o * kFTile + p] = q;
+            }
+        }
+    }
+}
+
+// F part: thread = column; Wt from shared memory (Ws, max(m0, m1) x nF) when staged.
+__device__ __forceinline__ void radialF_df_f(const RFParams& P, int64_t t0, const float* Qs, const float* Ws,
+                                             int tid, int nth) {
+    const int cnt = (int)min((int64_t)kFTile, P.n - t0);
+    float* F = reinterpret_cast<float*>(P.F);
+    for (int col = tid; col < P.ldF; col += nth) {
+        if (col >= P.nF) {                       // row padding: zeros, so that sectors are whole
+#pragma unroll
+            for (int p = 0; p < kFTile; ++p)
+                if (p < cnt) F[(t0 + p) * P.ldF + col] = 0.f;
+            continue;
+        }
+        const int par = P.colpar[col];
+        const int ob = par ? P.m0 : 0, mp = par ? P.m1 : P.m0;
+        float acc[kFTile];
+#pragma unroll
+        for (int p = 0; p < kFTile; ++p) acc[p] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < mp; ++l) {
+            const float w = Ws[(size_t)l * P.nF + col];
+            const float4* q = reinterpret_cast<const float4*>(Qs + (ob + l) * kFTile);
+#pragma unroll
+            for (int p4 = 0; p4 < kFTile / 4; ++p4) {
+                const float4 v = q[p4];
+                acc[4 * p4 + 0] += v.x * w;
+                acc[4 * p4 + 1] += v.y * w;
+                acc[4 * p4 + 2] += v.z * w;
+                acc[4 * p4 + 3] += v.w * w;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kFTile; ++p)
+            if (p < cnt) F[(t0 + p) * P.ldF + col] = acc[p];
+    }
 }
 
 // Radial factors of the points [t0, t0 + kFTile): block-wide, ends with a barrier.
@@ -295,7 +442,9 @@ __device__ __forceinline__ void radialF_tile(const RFParams& P, int64_t t0, unsi
 #pragma unroll
             for (int p = 0; p < kFTile; ++p) acc[p] += q[p] * w;
         }
-        for (int p = 0; p < cnt; ++p) F[(t0 + p) * P.ldF + col] = acc[p];
+#pragma unroll
+        for (int p = 0; p < kFTile; ++p)
+            if (p < cnt) F[(t0 + p) * P.ldF + col] = acc[p];
     }
     __syncthreads();
 }
@@ -307,6 +456,49 @@ __global__ void __launch_bounds__(256) k_radial_F(RFParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t ntiles = (P.n + kFTile - 1) / kFTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) radialF_tile<T>(P, tile * kFTile, smem_raw);
+}
+
+// Shared memory of k_radial_F_df: QC, Wt (when staged), basis values, Q.
+__host__ __device__ inline size_t radialF_df_smem(int L, int m0, int m1, int mtp, int nF, bool stage_wt) {
+    const int mmax = m0 > m1 ? m0 : m1;
+    return align16(sizeof(float2) * (size_t)(L + 1) * mtp) +
+           (stage_wt ? align16(sizeof(float) * (size_t)mmax * nF) : 0) +
+           align16(sizeof(float2) * kFTile * (L + 1) + sizeof(float) * kFTile) +
+           sizeof(float) * (size_t)(m0 + m1) * kFTile;
+}
+
+// FP32 factors: per tile, warp 0 computes the basis values, then all warps Q and F.  QC (and Wt
+// when P.stage_wt) are staged per CTA; two CTAs per SM.
+constexpr int kRfThreads = 256;
+static __global__ void __launch_bounds__(kRfThreads, 2) k_radial_F_df(RFParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int LP1 = P.L + 1;
+    const int mmax = P.m0 > P.m1 ? P.m0 : P.m1;
+    unsigned char* sp = smem_raw;
+    float2* QC = reinterpret_cast<float2*>(sp);
+    sp += align16(sizeof(float2) * (size_t)LP1 * P.mtp);
+    const float* Ws = reinterpret_cast<const float*>(P.Wt);
+    if (P.stage_wt) {
+        float* w = reinterpret_cast<float*>(sp);
+        for (int t = threadIdx.x; t < mmax * P.nF; t += blockDim.x) w[t] = reinterpret_cast<const float*>(P.Wt)[t];
+        Ws = w;
+        sp += align16(sizeof(float) * (size_t)mmax * P.nF);
+    }
+    float2* Ts = reinterpret_cast<float2*>(sp);
+    float* rh = reinterpret_cast<float*>(Ts + kFTile * LP1);
+    sp += align16(sizeof(float2) * kFTile * LP1 + sizeof(float) * kFTile);
+    float* Qs = reinterpret_cast<float*>(sp);
+    for (int t = threadIdx.x; t < LP1 * P.mtp; t += blockDim.x) QC[t] = P.QC[t];
+    __syncthreads();
+    const int64_t ntiles = (P.n + kFTile - 1) / kFTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (threadIdx.x < kFTile) radialF_df_basis(P, tile * kFTile, threadIdx.x, Ts, rh);
+        __syncthreads();
+        radialF_df_q(P, Ts, rh, QC, Qs, threadIdx.x, kRfThreads);
+        __syncthreads();
+        radialF_df_f(P, tile * kFTile, Qs, Ws, threadIdx.x, kRfThreads);
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------- A5b: harmonics and U writer
@@ -345,8 +537,6 @@ struct UWTabs {
     const int32_t* ychain;
 };
 
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
 // Bytes of the staged index tables: qdesc, chains, gslot, and ychain when harmonics are not
 // precomputed; the kernel lays them out in this order, each 16-byte aligned.
 __host__ __device__ inline size_t uwriter_tab_bytes(int64_t nq, int nH, int cstride, int nYp, bool pre) {
@@ -377,20 +567,21 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
     constexpr int VW = Vec2<T>::w;
-    // direction x_hat (FP64), zero vector -> e_0
-    double xh[kMaxD];
-    double s = 0.0;
-    for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R; s += xh[j] * xh[j]; }
-    if (s > 0.0) {
-        const double inv = 1.0 / sqrt(s);
+    // direction x_hat, zero vector -> e_0.  The differences are taken in FP64; the normalisation
+    // runs in the bulk precision T (every lane computes it, and FP64 is slow on this GPU).
+    T xh[kMaxD];
+    T s = (T)0;
+    for (int j = 0; j < P.d; ++j) { xh[j] = (T)((P.x[i * P.d + j] - P.c.c[j]) * P.inv2R); s += xh[j] * xh[j]; }
+    if (s > (T)0) {
+        const T inv = (T)1 / sqrt(s);
         for (int j = 0; j < P.d; ++j) xh[j] *= inv;
     } else {
-        for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0;
+        for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? (T)1 : (T)0;
     }
     // level tables: lanes over mu'
     for (int j = 0; j < levels; ++j) {
         const int D = P.d - 1 - j;
-        double q = 0.0;
+        T q = (T)0;
         for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
         const T z = (T)xh[D], qq = (T)q;
         const T* A = cA + j * P.tri;

@@ -95,7 +95,7 @@ struct FactorPlan {
     // chains (nH x (d-1) int16), hk (harmonic -> k), ktab (per k: fbase, s_k, cbase, |H_k|, hbase,
     // padded |H_k|), qdesc (chunk descriptors), ychain (padded harmonic slots -> chain),
     // coefA/coefB (level recurrences, bulk)
-    DevBuf dQ0, dQ1, dW, dcolk, dchains, dhk, dktab, dqdesc, dychain, dgslot, dA, dB;
+    DevBuf dQ0, dQ1, dQC, dW, dcolk, dchains, dhk, dktab, dqdesc, dychain, dgslot, dA, dB;
     std::vector<int64_t> colmap;               // padded column of each true column of U
     std::vector<double> Spad;                  // S on the padded columns (0 on padding)
     // d S_k / d l (s_k x s_k), computed on first use by the adjoint

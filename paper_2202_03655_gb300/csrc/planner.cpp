@@ -623,7 +623,11 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
         kt[4] = t.hbase[k];
         kt[5] = dimp[k];
     }
-    t.ldU = std::max<int64_t>(vw, t.cbase[L + 1]);
+    // rows padded to an odd number of 8-element groups (32 bytes in FP32): every row of U starts
+    // on a 32-byte sector (whole-sector stores and loads), and the odd stride spreads the rows of
+    // a tile over the DRAM channels (a stride that is a multiple of 128 bytes measured slower)
+    t.ldU = ((std::max<int64_t>(vw, t.cbase[L + 1]) + 7) / 8) * 8;
+    if ((t.ldU / 8) % 2 == 0) t.ldU += 8;
     t.qdesc.assign(t.ldU / vw, (uint32_t)t.nF << 20);    // F index nF (a zero slot) for padding
     t.colmap.clear();
     t.Spad.assign(t.ldU, 0.0);
