@@ -16,6 +16,14 @@ ranks; e2e = the same through the C ABI from pinned host buffers (H2D of x and V
 K~ V, D2H of Y).  The roofline object describes the dominant kernel of the step.  The
 FP64-bulk form of the same step is timed beside it (detail.fp64).
 
+Other workloads (--workload):
+  cube4_gauss     the differentiation row: n = 500,000 points in [-1,1]^4, Gaussian l = 0.8,
+                  tol 1e-6, FP32; step = hdf_build + hdf_matvec_adjoint (gradient of w^T K~ v
+                  with respect to the points and l); the dominant kernel is the adjoint kernel.
+  batch512_gauss  the batching row: 512 ragged sets (n log-uniform in [1000, 65536]), FP32;
+                  step = hdf_build_batched + hdf_batch_matvec with 8 columns per set; value =
+                  points of all sets per second.
+
 --impl reference times the CPU oracle (the only other implementation of this method here)
 on a bounded sample of the same workload.
 """
@@ -33,6 +41,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+METRICS = {
+    "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
+    "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
+}
 FP32_LANES_PER_SM, NSM, SM_MAX_MHZ = 128, 152, 2070.0
 
 
@@ -153,6 +165,37 @@ def cpu_oracle_step(x, w, V, p_max):
     return time.perf_counter() - t
 
 
+def oracle_sample(args, w):
+    """(x, offsets, lengthscales) of the bounded CPU sample of a workload."""
+    import numpy as np
+    from paper_2202_03655_gb300 import workloads as W
+    if args.workload == "batch512_gauss":
+        xb, off, ells = W.batch_sets(W.rng(w["idx"]), nsets=w["nsets"], d=w["d"])
+        k = 1
+        while k < len(ells) and off[k] < args.cpu_n:
+            k += 1
+        return xb[:off[k]], off[:k + 1], ells[:k]
+    ns = min(args.cpu_n if args.workload != "cube4_gauss" else min(args.cpu_n, 2000), w["n"])
+    return W.points(args.workload, n=ns), np.array([0, ns]), np.array([w["ell"]])
+
+
+def cpu_oracle_work(args, w, x, off, ells):
+    """The oracle's form of one step on the sample; returns seconds."""
+    import numpy as np
+    from oracle import hdf as ohdf
+    t = time.perf_counter()
+    for s in range(len(ells)):
+        xs = x[off[s]:off[s + 1]]
+        g = np.random.default_rng(1)
+        fo = ohdf.build(xs, w["kernel"], float(ells[s]), w["tol"], p_max=args.p_max)
+        if args.workload == "cube4_gauss":
+            v, wv = g.standard_normal(len(xs)), g.standard_normal(len(xs))
+            ohdf.adjoint_fd(fo, xs, v, wv)
+        else:
+            ohdf.matvec(fo, g.standard_normal((len(xs), w["ncols"])))
+    return time.perf_counter() - t
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: bounded samples of the workload, steps timed."""
     ws, rank, _ = dist()
@@ -161,6 +204,27 @@ def run_reference(args):
     import numpy as np
     from paper_2202_03655_gb300 import workloads as W
     w = workload_params(args)
+    if args.workload in ("cube4_gauss", "batch512_gauss"):
+        x, off, ells = oracle_sample(args, w)
+        for _ in range(args.warmup):
+            cpu_oracle_work(args, w, x, off, ells)
+        ts = [cpu_oracle_work(args, w, x, off, ells) for _ in range(args.steps)]
+        tot = sum(ts)
+        ns = int(off[-1])
+        val = ns * args.steps / tot
+        what = ("build + frozen-structure adjoint by central differences (oracle.hdf.adjoint_fd)"
+                if args.workload == "cube4_gauss" else f"build + K~V ({w['ncols']} columns) of each set")
+        line = {"impl": "reference", "metric": METRICS[args.workload], "value": val, "unit": "points/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n_sample": ns, "sets": len(ells), "d": w["d"],
+                           "kernel": w["kernel"], "tol": w["tol"], "ncols": w["ncols"], "p_max": args.p_max},
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"{ns} points ({len(ells)} set(s)) of the workload, {what}"},
+                "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     ns = min(args.cpu_n, w["n"])
     x = W.points(args.workload, n=ns)
     V = np.random.default_rng(1).standard_normal((ns, w["ncols"]))
@@ -183,10 +247,255 @@ def run_reference(args):
     return 0
 
 
+def _setup(args):
+    import torch
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    return ws, rank, dev
+
+
+def _timed(args, ws, rank, dev, stream, one_step):
+    """W warm-up steps, then K steps between CUDA events with clocks sampled; max over ranks."""
+    import torch
+    from paper_2202_03655_gb300 import hdf
+    for _ in range(max(args.warmup, 0)):
+        one_step(False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    l0 = hdf.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    recs = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        recs.append(one_step(True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = hdf.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, recs, launches, clocks
+
+
+def _cpu_baseline(args, w):
+    x, off, ells = oracle_sample(args, w)
+    ts = cpu_oracle_work(args, w, x, off, ells)
+    ns = int(off[-1])
+    what = ("build + frozen-structure adjoint by central differences" if args.workload == "cube4_gauss"
+            else f"build + K~V ({w['ncols']} columns) of each set")
+    return {"value": ns / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{ns} points ({len(ells)} set(s)) of the workload, {what}, FP64 numpy"}
+
+
+def bench_adjoint(args):
+    """Differentiation row: build + adjoint (gradient of w^T K~ v w.r.t. the points and l)."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    n, d = w["n"], w["d"]
+    x_np = W.points(args.workload, n=n)
+    g = W.rng(w["idx"] + 100)
+    v_np = g.standard_normal(n).astype(np.float32)
+    w_np = g.standard_normal(n).astype(np.float32)
+    x = torch.from_numpy(x_np).to(dev)
+    v, wv = torch.from_numpy(v_np).to(dev), torch.from_numpy(w_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one(keep):
+        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        a0.record(stream)
+        G, dl, val = f.adjoint(x, v, wv, stream=stream)
+        a1.record(stream)
+        a1.synchronize()
+        rec = (f.info, a0.elapsed_time(a1), val) if keep else None
+        f.free()
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    info = recs[-1][0]
+    adj_ms = float(np.mean([r[1] for r in recs]))
+    value = ws * n * args.steps / (ms_total / 1e3)
+    # accuracy outside the timed region: sampled rows of K~ v against the exact kernel
+    f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+    y = f.matvec(v)
+    rows = np.sort(W.rng(7).choice(n, 512, replace=False))
+    exact = exact_rows_matvec(x, w["kernel"], w["ell"], v.double(), rows)
+    approx = y[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+    rel_err = float(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    f.free()
+    # roofline of the adjoint: per point the contraction (w_i a + v_i b) . dU_i/dx_i over the r
+    # columns and d + 1 derivative directions, 2 r (d + 1) FP32 flops, against the FP32 FMA peak
+    r = info.rank
+    flops = 2.0 * n * r * (d + 1)
+    peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"kernel": "k_adjoint (with its U^T v, U^T w)", "bound": "alu",
+            "achieved": flops / (adj_ms / 1e3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+            "traffic": None, "algorithmic_flops": flops, "ms_per_launch": adj_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D x, v, w; build; adjoint; D2H of the gradient
+    xh = torch.from_numpy(x_np).pin_memory()
+    vh, wh = torch.from_numpy(v_np).pin_memory(), torch.from_numpy(w_np).pin_memory()
+    Gh = torch.empty((n, d), dtype=torch.float32).pin_memory()
+    xd, vd, wd = torch.empty_like(x), torch.empty_like(v), torch.empty_like(wv)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 3))
+    b0.record(stream)
+    for _ in range(k2):
+        xd.copy_(xh, non_blocking=True); vd.copy_(vh, non_blocking=True); wd.copy_(wh, non_blocking=True)
+        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        G, dl, val = f.adjoint(xd, vd, wd, stream=stream)
+        Gh.copy_(G, non_blocking=True)
+        f.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / k2
+    e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8 + 2 * n * 4,
+           "d2h_bytes_per_step": n * d * 4 + 16, "ms_per_step": e2e_ms}
+    cpu = _cpu_baseline(args, w) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "d": d, "kernel": w["kernel"], "lengthscale": w["ell"],
+                           "tol": w["tol"], "p_max": args.p_max, "p": info.p, "rank": r, "ldu": info.ldu,
+                           "parallelism": f"replicas{ws}", "l2": f"inputs larger than L2 (U is {n * info.ldu * 4 / 1e9:.1f} GB)"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"adjoint_ms": adj_ms, "build_ms": float(info.t_ms[7]),
+                           "rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound,
+                           "value_f": recs[-1][2]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_batch(args):
+    """Batching row: hdf_build_batched + hdf_batch_matvec over 512 ragged sets."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    c, d = w["ncols"], w["d"]
+    xb, off, ells = W.batch_sets(W.rng(w["idx"]), nsets=w["nsets"], d=d)
+    N = int(off[-1])
+    x = torch.from_numpy(xb).to(dev)
+    V_np = W.rng(w["idx"] + 100).standard_normal((c, N)).astype(np.float32)     # column-major N x c
+    Vc = torch.from_numpy(V_np).to(dev)
+    Yc = torch.empty_like(Vc)
+    stream = torch.cuda.current_stream(dev)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one(keep):
+        b = hdf.build_batched(x, off, w["kernel"], ells, w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        m0.record(stream)
+        b.matvec_ptr(Vc.data_ptr(), N, c, Yc.data_ptr(), N, stream=stream)
+        m1.record(stream)
+        rec = None
+        if keep:
+            m1.synchronize()
+            infos = [b.info(s) for s in range(b.nsets)]
+            rec = (b.timings(), m0.elapsed_time(m1), infos)
+        b.free()
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    value = ws * N * args.steps / (ms_total / 1e3)
+    tms, mv_ms, infos = recs[-1]
+    ranks = np.array([i.rank for i in infos])
+    ldus = np.array([i.ldu for i in infos])
+    sizes = np.diff(off)
+    u_bytes = int(np.sum(sizes * ranks) * 4)
+    # accuracy outside the timed region: 4 sets, 256 sampled rows each, against the exact kernel
+    b = hdf.build_batched(x, off, w["kernel"], ells, w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+    b.matvec_ptr(Vc.data_ptr(), N, c, Yc.data_ptr(), N, stream=stream)
+    torch.cuda.synchronize()
+    errs = []
+    for s in np.linspace(0, len(ells) - 1, 4).astype(int):
+        a, e = int(off[s]), int(off[s + 1])
+        rows = np.sort(W.rng(7 + s).choice(e - a, min(256, e - a), replace=False))
+        exact = exact_rows_matvec(x[a:e], w["kernel"], float(ells[s]), Vc[0, a:e].double(), rows)
+        approx = Yc[0, a:e][torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        errs.append(float(np.linalg.norm(approx - exact) / np.linalg.norm(exact)))
+    b.free()
+    # roofline: the persistent build kernel writes every set's U (HBM write bound)
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    build_kernel_ms = float(tms[5])
+    roof = {"kernel": "k_batch_build (radial factors + harmonics + U of all sets)", "bound": "hbm",
+            "achieved": u_bytes / (build_kernel_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None,
+            "algorithmic_bytes": u_bytes, "ms_per_launch": build_kernel_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D x and V, batched build + matvec, D2H Y
+    xh = torch.from_numpy(xb).pin_memory()
+    Vh = torch.from_numpy(V_np).pin_memory()
+    Yh = torch.empty_like(Vh).pin_memory()
+    xd = torch.empty_like(x)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 3))
+    b0.record(stream)
+    for _ in range(k2):
+        xd.copy_(xh, non_blocking=True); Vc.copy_(Vh, non_blocking=True)
+        bb = hdf.build_batched(xd, off, w["kernel"], ells, w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        bb.matvec_ptr(Vc.data_ptr(), N, c, Yc.data_ptr(), N, stream=stream)
+        Yh.copy_(Yc, non_blocking=True)
+        bb.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / k2
+    e2e = {"value": ws * N / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": N * d * 8 + N * c * 4,
+           "d2h_bytes_per_step": N * c * 4, "ms_per_step": e2e_ms}
+    cpu = _cpu_baseline(args, w) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "sets": len(ells), "points": N, "d": d, "kernel": w["kernel"],
+                           "tol": w["tol"], "ncols": c, "p_max": args.p_max, "U_bytes": int(np.sum(sizes * ldus) * 4),
+                           "parallelism": f"replicas{ws}", "l2": "inputs larger than L2"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"build_phase_ms": [float(t) for t in tms], "kv_ms": mv_ms,
+                           "kv_gbs": (2 * u_bytes + N * c * 8) / (mv_ms / 1e3) / 1e9,
+                           "rel_err_sampled_vs_exact": errs, "rank_total": int(ranks.sum()),
+                           "p_range": [int(min(i.p for i in infos)), int(max(i.p for i in infos))]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "cube4_gauss":
+        return bench_adjoint(args)
+    if args.workload == "batch512_gauss":
+        return bench_batch(args)
     import numpy as np
     import torch
     from paper_2202_03655_gb300 import hdf, workloads as W
