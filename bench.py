@@ -41,6 +41,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes (read + write) per stored U element, from one ncu capture of each kernel on the
+# 200,000-point case of the default workload (dram__bytes_read.sum + dram__bytes_write.sum over
+# n * ldU); the roofline's traffic is this figure scaled to the timed launch.  Set an entry to
+# None when its kernel changes, until it is captured again.
+TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1659, "k_tc_utv": 4.1502, "k_tc_uw": 4.0656}
 METRICS = {
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
@@ -602,7 +607,9 @@ def main():
                 "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
                 "hbm_achieved_gbs": b_dom / (t_dom / 1e3) / 1e9}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    tpe = TRAFFIC_PER_U_ELEMENT.get(dom)
+    roof["traffic"] = (tpe * n * ldu) if tpe else None
+    roof["traffic_source"] = "ncu dram bytes per U element at n = 200,000, scaled by n * ldU" if tpe else None
     roof["algorithmic_bytes"] = b_dom
     roof["ms_per_launch"] = t_dom
     kv_bytes = 2 * n * r * 4 + n * c * 8
