@@ -296,6 +296,203 @@ __global__ void __launch_bounds__(256) k_batch_uw(const MvSet* __restrict__ sets
     }
 }
 
+// ------------------------------------------------ skinny FP32 matvec (c <= 16)
+// Streaming kernels for few columns, where a register-tiled GEMM is bound by its shared-memory
+// instructions rather than by HBM.  U^T V: lane = TA consecutive columns of U (one 8- or 16-byte
+// load per row), the warps of a CTA stride over the rows of a chunk, V rows are staged in shared
+// memory and read as broadcasts; the eight warps' partial sums are added in a fixed order.
+// U W: a warp owns R rows and every column of them (lane = 4 columns per 128-column pass), W
+// is staged in 512-column blocks, and each row's sums are reduced across the warp by shuffles.
+template <int CT> struct SkinnyShape {
+    static constexpr int TA = CT <= 8 ? 4 : 2;      // U^T V: columns per lane
+    static constexpr int AB = 32 * TA;              // U^T V: columns per item
+    static constexpr int VR = 128;                  // U^T V: V rows staged per pass
+    static constexpr int R = CT <= 8 ? 4 : 2;       // U W: rows per warp
+    static constexpr int RB = 8 * R;                // U W: rows per item
+    static constexpr int WB = 512;                  // U W: W columns staged per pass
+};
+
+template <int N> struct FVec;
+template <> struct FVec<2> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) {
+        const float2 v = *reinterpret_cast<const float2*>(p); o[0] = v.x; o[1] = v.y;
+    }
+};
+template <> struct FVec<4> {
+    static __device__ __forceinline__ void ld(const float* p, float* o) {
+        const float4 v = *reinterpret_cast<const float4*>(p); o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+
+template <int CT>
+__device__ __forceinline__ void ld_row(const float* p, float* o) {
+    if constexpr (CT % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < CT; j += 4) FVec<4>::ld(p + j, o + j);
+    } else if constexpr (CT == 2) {
+        FVec<2>::ld(p, o);
+    } else {
+        o[0] = p[0];
+    }
+}
+
+template <int CT>
+__global__ void __launch_bounds__(256) k_batch_utv_s(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                     int nitems, int* counter, const float* __restrict__ V,
+                                                     int64_t ldv, int c) {
+    using SS = SkinnyShape<CT>;
+    constexpr int TA = SS::TA, AB = SS::AB, VR = SS::VR, UNR = 4;
+    __shared__ __align__(16) float Vs[VR][CT];
+    __shared__ __align__(16) float red[8][AB][CT];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        const float* U = reinterpret_cast<const float*>(S.U);
+        const int64_t i0 = (int64_t)w.chunk * S.chunk, i1 = min(S.n, i0 + S.chunk);
+        const int64_t a0 = w.blk * AB, a = a0 + (int64_t)lane * TA;
+        const bool act = a < S.r;                    // S.r is a multiple of 4 (padded width)
+        float acc[TA][CT];
+#pragma unroll
+        for (int q = 0; q < TA; ++q)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) acc[q][j] = 0.f;
+        for (int64_t k0 = i0; k0 < i1; k0 += VR) {
+            const int nr = (int)min((int64_t)VR, i1 - k0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < VR * CT; e += blockDim.x) {
+                const int rr = e % VR, j = e / VR;
+                Vs[rr][j] = (rr < nr && j < c) ? V[S.off + k0 + rr + (int64_t)j * ldv] : 0.f;
+            }
+            __syncthreads();
+            if (!act) continue;
+            for (int r0 = warp; r0 < nr; r0 += 8 * UNR) {
+                float u[UNR][TA];
+#pragma unroll
+                for (int t = 0; t < UNR; ++t) {
+                    const int rr = r0 + 8 * t;
+                    if (rr < nr) {
+                        FVec<TA>::ld(U + (k0 + rr) * S.ldU + a, u[t]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < TA; ++q) u[t][q] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < UNR; ++t) {
+                    const int rr = min(r0 + 8 * t, VR - 1);    // rows past nr carry u = 0
+                    float v[CT];
+                    ld_row<CT>(&Vs[rr][0], v);
+#pragma unroll
+                    for (int q = 0; q < TA; ++q)
+#pragma unroll
+                        for (int j = 0; j < CT; ++j) acc[q][j] += u[t][q] * v[j];
+                }
+            }
+        }
+        // partial sums of the eight warps, added in warp order
+#pragma unroll
+        for (int q = 0; q < TA; ++q)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) red[warp][lane * TA + q][j] = acc[q][j];
+        __syncthreads();
+        for (int e = threadIdx.x; e < AB * CT; e += blockDim.x) {
+            const int col = e / CT, j = e % CT;
+            float sum = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) sum += red[ww][col][j];
+            const int64_t aa = a0 + col;
+            if (aa < S.r && j < c) S.part[((int64_t)w.chunk * c + j) * S.r + aa] = (double)sum;
+        }
+        __syncthreads();
+    }
+}
+
+template <int CT>
+__global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                    int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
+                                                    int c) {
+    using SS = SkinnyShape<CT>;
+    constexpr int R = SS::R, RB = SS::RB, WB = SS::WB;
+    __shared__ __align__(16) float Ws[WB][CT];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        const float* U = reinterpret_cast<const float*>(S.U);
+        const float* W = reinterpret_cast<const float*>(S.W);
+        const int64_t row0 = w.blk * RB + (int64_t)warp * R;
+        float acc[R][CT];
+#pragma unroll
+        for (int t = 0; t < R; ++t)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) acc[t][j] = 0.f;
+        for (int64_t cb0 = 0; cb0 < S.r; cb0 += WB) {
+            const int nc = (int)min((int64_t)WB, S.r - cb0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < WB * CT; e += blockDim.x) {
+                const int t = e / CT, j = e % CT;
+                Ws[t][j] = (t < nc && j < c) ? W[(cb0 + t) * c + j] : 0.f;
+            }
+            __syncthreads();
+            for (int cb = 0; cb < nc; cb += 128) {
+                const int al = cb + 4 * lane;             // column within the staged block
+                if (al >= nc) continue;
+                float u[R][4];
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    const int64_t i = row0 + t;
+                    if (i < S.n) {
+                        FVec<4>::ld(U + i * S.ldU + cb0 + al, u[t]);
+                    } else {
+                        u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float wv[CT];
+                    ld_row<CT>(&Ws[al + q][0], wv);
+#pragma unroll
+                    for (int t = 0; t < R; ++t)
+#pragma unroll
+                        for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) {
+                float v = acc[t][j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[t][j] = v;
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int64_t i = row0 + t;
+                if (i < S.n)
+#pragma unroll
+                    for (int j = 0; j < CT; ++j)
+                        if (j < c) Y[S.off + i + (int64_t)j * ldy] = acc[t][j];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ autotuner
 std::mutex g_tune_mu;
 
@@ -704,7 +901,12 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         std::vector<MvSet> ms(ns);
         std::vector<MvItem> iu, ir, iw;
         const int ct = ct_for(c);
-        const int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
+        const bool skinny = sizeof(T) == 4 && ct <= 16;
+        int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
+        if (skinny) {
+            AB = 32 * (ct <= 8 ? 4 : 2);
+            RB = 8 * (ct <= 8 ? 4 : 2);
+        }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
         for (int s = 0; s < ns; ++s) {
@@ -752,10 +954,41 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         HDF_CUDA(cudaGetDevice(&dv));
         HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
         const int ct = ct_for(c);
+        const bool skinny = sizeof(T) == 4 && ct <= 16;
+        int occ_u = 1, occ_w = 1;
+        if (skinny) {
+            switch (ct) {
+#define HDF_B_OCC(CT)                                                                                             \
+    case CT:                                                                                                      \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_s<CT>, 256, 0));               \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<CT>, 256, 0));                \
+        break;
+                HDF_B_OCC(1) HDF_B_OCC(2) HDF_B_OCC(4) HDF_B_OCC(8) HDF_B_OCC(16)
+#undef HDF_B_OCC
+            }
+        }
         HDF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(b->counters.p, 0, sizeof(int) * 2, b->cap);
         const MvSet* S = b->mvsets.as<MvSet>();
         int* cnt = b->counters.as<int>();
+        if (skinny) {
+            switch (ct) {
+#define HDF_B_SK(CT)                                                                                              \
+    case CT:                                                                                                      \
+        if (b->n_utv)                                                                                             \
+            k_batch_utv_s<CT><<<nsm * std::max(occ_u, 1), 256, 0, b->cap>>>(                                      \
+                S, b->mvitems_utv.as<MvItem>(), b->n_utv, cnt, reinterpret_cast<const float*>(V), ldv, c);        \
+        if (b->n_red) k_batch_reduce<T><<<b->n_red, 256, 0, b->cap>>>(S, b->mvitems_red.as<MvItem>(), c);          \
+        if (b->n_uw)                                                                                              \
+            k_batch_uw_s<CT><<<nsm * std::max(occ_w, 1), 256, 0, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw, \
+                                                                         cnt + 1, reinterpret_cast<float*>(Y),    \
+                                                                         ldy, c);                                 \
+        break;
+                HDF_B_SK(1) HDF_B_SK(2) HDF_B_SK(4) HDF_B_SK(8) HDF_B_SK(16)
+#undef HDF_B_SK
+            }
+        } else
+        switch (ct) {
 #define HDF_B_MV(CT)                                                                                              \
     case CT:                                                                                                      \
         if (b->n_utv) k_batch_utv<T, CT><<<nsm * 3, 256, 0, b->cap>>>(S, b->mvitems_utv.as<MvItem>(), b->n_utv,   \
@@ -764,7 +997,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         if (b->n_uw) k_batch_uw<T, CT><<<nsm * 3, 256, 0, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw,       \
                                                                       cnt + 1, Y, ldy, c);                        \
         break;
-        switch (ct) { HDF_B_MV(1) HDF_B_MV(2) HDF_B_MV(4) HDF_B_MV(8) HDF_B_MV(16) HDF_B_MV(32) HDF_B_MV(64) }
+        HDF_B_MV(1) HDF_B_MV(2) HDF_B_MV(4) HDF_B_MV(8) HDF_B_MV(16) HDF_B_MV(32) HDF_B_MV(64) }
 #undef HDF_B_MV
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(b->cap, &g);

@@ -60,3 +60,24 @@ def test_batch512_full_size_sampled():
         exact = dense_rows_matvec_torch(xs, "gaussian", ells[s], Vs, rows)
         err = rel(Y[off[s]:off[s + 1]][rows], exact)
         assert err <= (1e-5 if I.reached else 10 * I.err_bound + 1e-5), (s, err, I.p, I.reached)
+
+
+@pytest.mark.parametrize("c", [1, 2, 5, 8, 13, 16, 20])
+def test_batch_matvec_column_counts(c):
+    """FP32 batched K~V for every column-tile width (the streaming kernels for c <= 16, the
+    register-tiled ones above) against hdf_build + hdf_matvec on the same sets."""
+    import torch
+    from paper_2202_03655_gb300 import hdf
+    sizes = [3, 900, 131, 2049]
+    x, off, ells = _ragged(23, sizes)
+    tol = 1e-6
+    b = hdf.build_batched(to_dev(x), off, "gaussian", ells, tol, precision="fp32")
+    V = np.random.default_rng(c).standard_normal((off[-1], c)).astype(np.float32)
+    Y = b.matvec(to_dev(V, torch.float32)).double().cpu().numpy().reshape(off[-1], c)
+    Y2 = b.matvec(to_dev(V, torch.float32)).double().cpu().numpy().reshape(off[-1], c)
+    assert np.array_equal(Y, Y2)                                   # deterministic replay
+    for s in range(len(sizes)):
+        xs, Vs = x[off[s]:off[s + 1]], V[off[s]:off[s + 1]]
+        f1 = hdf.build(to_dev(xs), "gaussian", ells[s], tol, precision="fp32")
+        Y1 = f1.matvec(to_dev(Vs, torch.float32)).double().cpu().numpy().reshape(-1, c)
+        assert rel(Y[off[s]:off[s + 1]], Y1) <= 1e-5, (s, c)
