@@ -260,9 +260,16 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     DevBuf mpart, msum;
     HDF_CUDA(mpart.alloc_on(sizeof(double) * (size_t)gmom * nmom, st));
     HDF_CUDA(msum.alloc_on(sizeof(double) * nmom, st));
-    const size_t msm = sizeof(double) * dev::kMomTile * nmom;
     HDF_COUNT_LAUNCH();
-    dev::k_radial_moments<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
+    const size_t msm_df = sizeof(float2) * 256 * (size_t)(nmom + 1);
+    if (prec == HDF_FP32 && msm_df <= 200 * 1024) {        // double-float recurrences (FP32 pipe)
+        const size_t msm = msm_df;
+        HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_moments_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
+        dev::k_radial_moments_df<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
+    } else {
+        const size_t msm = sizeof(double) * dev::kMomTile * nmom;
+        dev::k_radial_moments<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
+    }
     HDF_CUDA(cudaGetLastError());
     HDF_COUNT_LAUNCH();
     dev::k_reduce_cols<<<grid_for(nmom, 256, 1 << 20), 256, 0, st>>>(mpart.as<double>(), gmom, nmom,

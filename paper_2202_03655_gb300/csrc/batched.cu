@@ -95,24 +95,48 @@ __global__ void k_seg_maxnorm(const double* __restrict__ x, int d, const SegItem
 }
 
 // rows: (set, t) pairs; part[row] = sum_u k(|x_idx(t) - x_idx(u)|)^2 over the set's subsample
-__global__ void k_seg_mu2(const double* __restrict__ x, int d, const int2* __restrict__ rows,
-                          const SetGeom* __restrict__ geo, int kernel, double* __restrict__ part) {
+// Sum over pairs i < j of K(x_i, x_j)^2 for sample rows i in [32 t, 32 t + 32) of set s
+// (item (s, t)); the set's m strided sample points are staged in shared memory.  The host adds
+// the diagonal m k(0)^2 and doubles nothing: part holds 2 x the half sum.
+constexpr int kMu2Rows = 32;
+__global__ void __launch_bounds__(256) k_seg_mu2_pairs(const double* __restrict__ x, int d,
+                                                       const int2* __restrict__ items,
+                                                       const SetGeom* __restrict__ geo, int kernel,
+                                                       double* __restrict__ part) {
+    __shared__ double xs[kMu2Sample * dev::kMaxD];
     __shared__ double sh[256];
-    const int2 rw = rows[blockIdx.x];
-    const SetGeom& g = geo[rw.x];
-    const int64_t i = g.off + ((int64_t)rw.y * g.n) / g.m;
-    double xi[dev::kMaxD];
-    for (int j = 0; j < d; ++j) xi[j] = x[i * d + j];
-    double acc = 0.0;
+    const int2 it = items[blockIdx.x];
+    const SetGeom& g = geo[it.x];
     for (int u = threadIdx.x; u < g.m; u += blockDim.x) {
         const int64_t jj = g.off + ((int64_t)u * g.n) / g.m;
-        double s = 0.0;
-        for (int j = 0; j < d; ++j) { const double y = xi[j] - x[jj * d + j]; s += y * y; }
-        const double kv = dev::kernel_value(kernel, sqrt(s), g.ell);
-        acc += kv * kv;
+        for (int j = 0; j < d; ++j) xs[u * d + j] = x[jj * d + j];
+    }
+    __syncthreads();
+    double acc = 0.0;
+    const int r0 = it.y * kMu2Rows, r1 = min(g.m, r0 + kMu2Rows);
+    for (int i = r0; i < r1; ++i) {
+        for (int u = i + 1 + threadIdx.x; u < g.m; u += blockDim.x) {
+            double s2 = 0.0;
+            for (int j = 0; j < d; ++j) { const double y = xs[i * d + j] - xs[u * d + j]; s2 += y * y; }
+            const double kv = dev::kernel_value(kernel, sqrt(s2), g.ell);
+            acc += kv * kv;
+        }
     }
     const double tot = dev::block_sum_256(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * tot;
+}
+
+// Chebyshev moments of one item (FP32 factors): part[poff + l], l < 2 L_s + 2.
+__global__ void __launch_bounds__(256) k_seg_moments_df(const double* __restrict__ x, int d,
+                                                        const SegItem* __restrict__ items,
+                                                        const int64_t* __restrict__ poff,
+                                                        const SetGeom* __restrict__ geo, double* __restrict__ part) {
+    extern __shared__ float2 tsm_seg[];
+    const SegItem it = items[blockIdx.x];
+    const SetGeom& g = geo[it.set];
+    const int nmom = 2 * g.L + 2;
+    const double v = dev::moments_df_range(x, d, g.c, g.inv2R, nmom, it.i0, it.i1, tsm_seg);
+    if (threadIdx.x < nmom) part[poff[blockIdx.x] + threadIdx.x] = v;
 }
 
 // Radial-basis Gram sums of one item: part[poff + q] (q < npairs) and part[poff + npairs + q].
@@ -195,6 +219,16 @@ struct BuildSet {
     int pre;
 };
 
+// Items of kBatchTiles radial tiles (128 points): the radial factors of each tile, then the U
+// rows of all the item's points, so that the per-set coefficient tables are loaded once per item.
+constexpr int kBatchTiles = 4;
+
+// Shared memory of one double-float radial tile (basis pairs, rho, Q) in the batched build.
+inline size_t batch_df_tile_smem(int L, int m0, int m1) {
+    return dev::align16(sizeof(float2) * dev::kFTile * (L + 1) + sizeof(float) * dev::kFTile) +
+           sizeof(float) * (size_t)(m0 + m1) * dev::kFTile;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict__ sets, const int2* __restrict__ items,
                                                      int nitems, int* counter) {
@@ -209,8 +243,28 @@ __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict_
         if (it >= nitems) break;
         const int2 w = items[it];
         const BuildSet& S = sets[w.x];
-        const int64_t t0 = (int64_t)w.y * dev::kFTile;
-        dev::radialF_tile<T>(S.rf, t0, smem_raw);           // F rows of the tile (global)
+        const int64_t t0 = (int64_t)w.y * kBatchTiles * dev::kFTile;
+        for (int q = 0; q < kBatchTiles; ++q) {                // F rows of the item's tiles (global)
+            const int64_t tq = t0 + (int64_t)q * dev::kFTile;
+            if (tq >= S.rf.n) break;
+            if constexpr (sizeof(T) == 4) {
+                if (S.rf.QC != nullptr) {
+                    const int LP1 = S.rf.L + 1;
+                    float2* Ts = reinterpret_cast<float2*>(smem_raw);
+                    float* rh = reinterpret_cast<float*>(Ts + dev::kFTile * LP1);
+                    float* Qs = reinterpret_cast<float*>(
+                        smem_raw + dev::align16(sizeof(float2) * dev::kFTile * LP1 + sizeof(float) * dev::kFTile));
+                    if (threadIdx.x < dev::kFTile) dev::radialF_df_basis(S.rf, tq, threadIdx.x, Ts, rh);
+                    __syncthreads();
+                    dev::radialF_df_q(S.rf, Ts, rh, S.rf.QC, Qs, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    dev::radialF_df_f(S.rf, tq, Qs, reinterpret_cast<const float*>(S.rf.Wt), threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    continue;
+                }
+            }
+            dev::radialF_tile<T>(S.rf, tq, smem_raw);
+        }
         const int levels = S.uw.d - 2;
         T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * S.uw.per_warp;
         T* cA = reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * S.uw.per_warp;
@@ -221,7 +275,7 @@ __global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict_
         }
         __syncthreads();
         dev::uwriter_zero_slots<T>(S.uw, S.pre != 0, base, lane);     // slots of this set's layout
-        const int64_t t1 = min(t0 + dev::kFTile, S.uw.n);
+        const int64_t t1 = min(t0 + (int64_t)kBatchTiles * dev::kFTile, S.uw.n);
         const dev::UWTabs X{S.uw.qdesc, S.uw.chains, S.uw.gslot, S.uw.ychain};
         for (int64_t i = t0 + warp; i < t1; i += nwarps) dev::uwriter_point<T>(S.uw, X, S.pre != 0, i, cA, cB, base, lane);
         __syncthreads();
@@ -591,14 +645,14 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         for (int64_t i0 = 0; i0 < geo[s].n; i0 += kSegChunk)
             items.push_back({s, 0, geo[s].off + i0, geo[s].off + std::min<int64_t>(geo[s].n, i0 + kSegChunk)});
     const int nit = (int)items.size();
-    std::vector<int2> mrows;
+    std::vector<int2> mrows;                      // (set, tile of kMu2Rows sample rows)
     for (int s = 0; s < ns; ++s)
-        for (int t = 0; t < geo[s].m; ++t) mrows.push_back(make_int2(s, t));
+        for (int t = 0; t * kMu2Rows < geo[s].m; ++t) mrows.push_back(make_int2(s, t));
     DevBuf ditems, dgeo, dpart, drows;
-    HDF_CUDA(ditems.alloc(sizeof(SegItem) * nit));
-    HDF_CUDA(dgeo.alloc(sizeof(SetGeom) * ns));
-    HDF_CUDA(drows.alloc(sizeof(int2) * mrows.size()));
-    HDF_CUDA(dpart.alloc(sizeof(double) * std::max<size_t>((size_t)nit * d, mrows.size())));
+    HDF_CUDA(ditems.alloc_on(sizeof(SegItem) * nit, st));
+    HDF_CUDA(dgeo.alloc_on(sizeof(SetGeom) * ns, st));
+    HDF_CUDA(drows.alloc_on(sizeof(int2) * mrows.size(), st));
+    HDF_CUDA(dpart.alloc_on(sizeof(double) * std::max<size_t>((size_t)nit * d, mrows.size()), st));
     HDF_CUDA(cudaMemcpyAsync(ditems.p, items.data(), sizeof(SegItem) * nit, cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(drows.p, mrows.data(), sizeof(int2) * mrows.size(), cudaMemcpyHostToDevice, st));
     HDF_COUNT_LAUNCH();
@@ -633,15 +687,18 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     }
     HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
     HDF_COUNT_LAUNCH();
-    k_seg_mu2<<<(unsigned)mrows.size(), 256, 0, st>>>(x, d, drows.as<int2>(), dgeo.as<SetGeom>(), b->kernel,
-                                                     dpart.as<double>());
+    k_seg_mu2_pairs<<<(unsigned)mrows.size(), 256, 0, st>>>(x, d, drows.as<int2>(), dgeo.as<SetGeom>(), b->kernel,
+                                                           dpart.as<double>());
     HDF_CUDA(cudaGetLastError());
     std::vector<double> mp(mrows.size());
     HDF_CUDA(cudaMemcpyAsync(mp.data(), dpart.p, sizeof(double) * mp.size(), cudaMemcpyDeviceToHost, st));
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<double> mu2(ns, 0.0);
     for (size_t q = 0; q < mrows.size(); ++q) mu2[mrows[q].x] += mp[q];
-    for (int s = 0; s < ns; ++s) mu2[s] /= (double)geo[s].m * (double)geo[s].m;
+    for (int s = 0; s < ns; ++s) {
+        const double k0 = kernel_value(b->kernel, 0.0, ells[s]);
+        mu2[s] = (mu2[s] + geo[s].m * k0 * k0) / ((double)geo[s].m * (double)geo[s].m);
+    }
     b->t_ms[0] = now_ms_b() - t_start;
 
     // ---- A1-A2 per set on host threads
@@ -653,8 +710,47 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     for (int s = 0; s < ns; ++s) geo[s].L = dps[s].L;
     b->t_ms[1] = now_ms_b() - t0;
 
-    // ---- A3: segmented radial-basis Gram
+    // ---- A3: segmented radial-basis Gram (FP32 factors: from Chebyshev moments, O(nL))
     t0 = now_ms_b();
+    int Lmax = 0;
+    for (int s = 0; s < ns; ++s) Lmax = std::max(Lmax, geo[s].L);
+    std::vector<std::vector<double>> grams(ns);
+    const size_t msm = sizeof(float2) * 256 * (size_t)(2 * Lmax + 3);
+    if (sizeof(T) == 4 && msm <= 200 * 1024) {
+        std::vector<SegItem> gitems;
+        std::vector<int64_t> gpoff;
+        int64_t gtot = 0;
+        for (int s = 0; s < ns; ++s) {
+            const int nmom = 2 * geo[s].L + 2;
+            for (int64_t i0 = 0; i0 < geo[s].n; i0 += kGramChunk) {
+                gitems.push_back({s, 0, geo[s].off + i0, geo[s].off + std::min<int64_t>(geo[s].n, i0 + kGramChunk)});
+                gpoff.push_back(gtot);
+                gtot += nmom;
+            }
+        }
+        DevBuf dgi, dgpoff, dgpart;
+        HDF_CUDA(dgi.alloc_on(sizeof(SegItem) * gitems.size(), st));
+        HDF_CUDA(dgpoff.alloc_on(sizeof(int64_t) * gpoff.size(), st));
+        HDF_CUDA(dgpart.alloc_on(sizeof(double) * gtot, st));
+        HDF_CUDA(cudaMemcpyAsync(dgi.p, gitems.data(), sizeof(SegItem) * gitems.size(), cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaMemcpyAsync(dgpoff.p, gpoff.data(), sizeof(int64_t) * gpoff.size(), cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
+        HDF_CUDA(cudaFuncSetAttribute(k_seg_moments_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
+        HDF_COUNT_LAUNCH();
+        k_seg_moments_df<<<(unsigned)gitems.size(), 256, msm, st>>>(x, d, dgi.as<SegItem>(), dgpoff.as<int64_t>(),
+                                                                     dgeo.as<SetGeom>(), dgpart.as<double>());
+        HDF_CUDA(cudaGetLastError());
+        std::vector<double> gp(gtot);
+        HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+        std::vector<std::vector<double>> moms(ns);
+        for (int s = 0; s < ns; ++s) moms[s].assign(2 * geo[s].L + 2, 0.0);
+        for (size_t q = 0; q < gitems.size(); ++q) {
+            std::vector<double>& m = moms[gitems[q].set];
+            for (size_t e = 0; e < m.size(); ++e) m[e] += gp[gpoff[q] + e];
+        }
+        parallel_for(ns, [&](int s) { gram_from_moments(moms[s], geo[s].L, grams[s]); });
+    } else {
     std::vector<SegItem> gitems;
     std::vector<int64_t> gpoff;
     int64_t gtot = 0;
@@ -666,12 +762,10 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
             gtot += 2 * npairs;
         }
     }
-    int Lmax = 0;
-    for (int s = 0; s < ns; ++s) Lmax = std::max(Lmax, geo[s].L);
     DevBuf dgi, dgpoff, dgpart;
-    HDF_CUDA(dgi.alloc(sizeof(SegItem) * gitems.size()));
-    HDF_CUDA(dgpoff.alloc(sizeof(int64_t) * gpoff.size()));
-    HDF_CUDA(dgpart.alloc(sizeof(double) * gtot));
+    HDF_CUDA(dgi.alloc_on(sizeof(SegItem) * gitems.size(), st));
+    HDF_CUDA(dgpoff.alloc_on(sizeof(int64_t) * gpoff.size(), st));
+    HDF_CUDA(dgpart.alloc_on(sizeof(double) * gtot, st));
     HDF_CUDA(cudaMemcpyAsync(dgi.p, gitems.data(), sizeof(SegItem) * gitems.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(dgpoff.p, gpoff.data(), sizeof(int64_t) * gpoff.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(dgeo.p, geo.data(), sizeof(SetGeom) * ns, cudaMemcpyHostToDevice, st));
@@ -684,7 +778,6 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     std::vector<double> gp(gtot);
     HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
     HDF_CUDA(cudaStreamSynchronize(st));
-    std::vector<std::vector<double>> grams(ns);
     for (int s = 0; s < ns; ++s) {
         const int LP1 = geo[s].L + 1;
         grams[s].assign(LP1 * (LP1 + 1), 0.0);
@@ -692,6 +785,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     for (size_t q = 0; q < gitems.size(); ++q) {
         std::vector<double>& G = grams[gitems[q].set];
         for (size_t e = 0; e < G.size(); ++e) G[e] += gp[gpoff[q] + e];
+    }
     }
     b->t_ms[2] = now_ms_b() - t0;
 
@@ -741,7 +835,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (bytes) std::memcpy(arena.data() + o, src, bytes);
         return o;
     };
-    struct Offs { size_t q0, q1, w, par, ch, qd, yc, gs, ca, cb; };
+    struct Offs { size_t q0, q1, qc, w, par, ch, qd, yc, gs, ca, cb; int mtp; };
     std::vector<Offs> offs(ns);
     std::vector<T> Sd(b->soff[ns], (T)0);
     for (int s = 0; s < ns; ++s) {
@@ -752,6 +846,24 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)tb.coefA[q]; cB[q] = (T)tb.coefB[q]; }
         offs[s].q0 = put(fc.Qmat[0].data(), sizeof(double) * fc.Qmat[0].size());
         offs[s].q1 = put(fc.Qmat[1].data(), sizeof(double) * fc.Qmat[1].size());
+        offs[s].qc = 0;
+        offs[s].mtp = 0;
+        if (sizeof(T) == 4) {
+            // [Qmat0 | Qmat1] as (hi, lo) float pairs, (L+1) x mtp, odd columns zero in row L
+            const int m0 = fc.m[0], m1 = fc.m[1], L = geo[s].L, mtp = ((m0 + m1 + 7) / 8) * 8;
+            std::vector<float> qc((size_t)2 * (L + 1) * std::max(mtp, 8), 0.f);
+            auto putq = [&](int l, int o, double v) {
+                const float h = (float)v;
+                qc[2 * ((size_t)l * mtp + o)] = h;
+                qc[2 * ((size_t)l * mtp + o) + 1] = (float)(v - (double)h);
+            };
+            for (int l = 0; l < fc.nb[0]; ++l)
+                for (int o = 0; o < m0; ++o) putq(l, o, fc.Qmat[0][(size_t)l * m0 + o]);
+            for (int l = 0; l < fc.nb[1]; ++l)
+                for (int o = 0; o < m1; ++o) putq(l, m0 + o, fc.Qmat[1][(size_t)l * m1 + o]);
+            offs[s].qc = put(qc.data(), sizeof(float) * qc.size());
+            offs[s].mtp = mtp;
+        }
         offs[s].w = put(Wt.data(), sizeof(T) * Wt.size());
         offs[s].par = put(tb.colpar.data(), tb.colpar.size());
         offs[s].ch = put(tb.chains.data(), sizeof(int16_t) * tb.chains.size());
@@ -763,17 +875,17 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         for (int64_t a = 0; a < tb.ldU; ++a) Sd[b->soff[s] + a] = (T)tb.Spad[a];
         b->colmap[s] = tb.colmap;
     }
-    HDF_CUDA(b->arena.alloc(arena.size()));
+    HDF_CUDA(b->arena.alloc_on(arena.size(), st));
     HDF_CUDA(cudaMemcpyAsync(b->arena.p, arena.data(), arena.size(), cudaMemcpyHostToDevice, st));
-    HDF_CUDA(b->S.alloc(sizeof(T) * std::max<int64_t>(1, b->soff[ns])));
+    HDF_CUDA(b->S.alloc_on(sizeof(T) * std::max<int64_t>(1, b->soff[ns]), st));
     HDF_CUDA(cudaMemcpyAsync(b->S.p, Sd.data(), sizeof(T) * Sd.size(), cudaMemcpyHostToDevice, st));
     const size_t ubytes = sizeof(T) * (size_t)std::max<int64_t>(1, b->uoff[ns]);
-    if (b->U.alloc(ubytes) != cudaSuccess) {
+    if (b->U.alloc_on(ubytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build_batched: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
     }
     DevBuf dF;
-    if (dF.alloc(sizeof(T) * (size_t)std::max<int64_t>(1, foff[ns])) != cudaSuccess) {
+    if (dF.alloc_on(sizeof(T) * (size_t)std::max<int64_t>(1, foff[ns]), st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build_batched: cannot allocate the radial factor buffer");
     }
@@ -794,6 +906,10 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         R.Qm0 = reinterpret_cast<const double*>(A + offs[s].q0); R.nb0 = fc.nb[0]; R.m0 = fc.m[0];
         R.Qm1 = reinterpret_cast<const double*>(A + offs[s].q1); R.nb1 = fc.nb[1]; R.m1 = fc.m[1];
         R.Wt = A + offs[s].w; R.colpar = A + offs[s].par; R.nF = tb.nF;
+        if (sizeof(T) == 4 && offs[s].mtp > 0) {
+            R.QC = reinterpret_cast<const float2*>(A + offs[s].qc);
+            R.mtp = offs[s].mtp;
+        }
         R.F = dF.as<T>() + foff[s]; R.ldF = tb.nF;
         dev::UWParams& P = bs[s].uw;
         P.x = R.x; P.n = R.n; P.d = d; P.c = R.c; P.inv2R = R.inv2R;
@@ -813,17 +929,19 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         bs[s].pre = pre ? 1 : 0;
         P.per_warp = pre ? pw_pre : pw_fly;
         const size_t need_uw = fixed + sizeof(T) * 8 * (size_t)P.per_warp;
-        const size_t need_rf = dev::radialF_smem(geo[s].L, fc.m[0], fc.m[1], sizeof(T));
+        const size_t need_rf = (sizeof(T) == 4) ? batch_df_tile_smem(geo[s].L, fc.m[0], fc.m[1])
+                                                : dev::radialF_smem(geo[s].L, fc.m[0], fc.m[1], sizeof(T));
         smem = std::max(smem, std::max(need_uw, need_rf));
-        const int64_t ntile = (geo[s].n + dev::kFTile - 1) / dev::kFTile;
-        for (int64_t t = 0; t < ntile; ++t) bitems.push_back(make_int2(s, (int)t));
+        const int64_t per_item = (int64_t)kBatchTiles * dev::kFTile;
+        const int64_t nitem = (geo[s].n + per_item - 1) / per_item;
+        for (int64_t t = 0; t < nitem; ++t) bitems.push_back(make_int2(s, (int)t));
     }
     if (smem > budget) return fail(HDF_ETOOBIG, "hdf_build_batched: per-set tables exceed shared memory");
-    HDF_CUDA(b->dsets.alloc(sizeof(BuildSet) * ns));
+    HDF_CUDA(b->dsets.alloc_on(sizeof(BuildSet) * ns, st));
     HDF_CUDA(cudaMemcpyAsync(b->dsets.p, bs.data(), sizeof(BuildSet) * ns, cudaMemcpyHostToDevice, st));
     DevBuf ditb, dcnt;
-    HDF_CUDA(ditb.alloc(sizeof(int2) * std::max<size_t>(1, bitems.size())));
-    HDF_CUDA(dcnt.alloc(sizeof(int)));
+    HDF_CUDA(ditb.alloc_on(sizeof(int2) * std::max<size_t>(1, bitems.size()), st));
+    HDF_CUDA(dcnt.alloc_on(sizeof(int), st));
     if (!bitems.empty())
         HDF_CUDA(cudaMemcpyAsync(ditb.p, bitems.data(), sizeof(int2) * bitems.size(), cudaMemcpyHostToDevice, st));
     b->t_ms[3] = now_ms_b() - t0;
@@ -924,19 +1042,19 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             for (int64_t bl = 0; bl < (r + 255) / 256; ++bl) ir.push_back({s, 0, bl});
             for (int64_t bl = 0; bl < (n + RB - 1) / RB; ++bl) iw.push_back({s, 0, bl});
         }
-        HDF_CUDA(b->mvpart.alloc(sizeof(double) * std::max<int64_t>(1, ptot)));
-        HDF_CUDA(b->mvW.alloc(sizeof(T) * std::max<int64_t>(1, wtot)));
+        HDF_CUDA(b->mvpart.alloc_on(sizeof(double) * std::max<int64_t>(1, ptot), st));
+        HDF_CUDA(b->mvW.alloc_on(sizeof(T) * std::max<int64_t>(1, wtot), st));
         for (int s = 0; s < ns; ++s) {
             ms[s].U = b->U.as<T>() + b->uoff[s];
             ms[s].S = b->S.as<T>() + b->soff[s];
             ms[s].part = b->mvpart.as<double>() + poff[s];
             ms[s].W = b->mvW.as<T>() + woff[s];
         }
-        HDF_CUDA(b->mvsets.alloc(sizeof(MvSet) * ns));
-        HDF_CUDA(b->mvitems_utv.alloc(sizeof(MvItem) * std::max<size_t>(1, iu.size())));
-        HDF_CUDA(b->mvitems_red.alloc(sizeof(MvItem) * std::max<size_t>(1, ir.size())));
-        HDF_CUDA(b->mvitems_uw.alloc(sizeof(MvItem) * std::max<size_t>(1, iw.size())));
-        HDF_CUDA(b->counters.alloc(sizeof(int) * 2));
+        HDF_CUDA(b->mvsets.alloc_on(sizeof(MvSet) * ns, st));
+        HDF_CUDA(b->mvitems_utv.alloc_on(sizeof(MvItem) * std::max<size_t>(1, iu.size()), st));
+        HDF_CUDA(b->mvitems_red.alloc_on(sizeof(MvItem) * std::max<size_t>(1, ir.size()), st));
+        HDF_CUDA(b->mvitems_uw.alloc_on(sizeof(MvItem) * std::max<size_t>(1, iw.size()), st));
+        HDF_CUDA(b->counters.alloc_on(sizeof(int) * 2, st));
         HDF_CUDA(cudaMemcpyAsync(b->mvsets.p, ms.data(), sizeof(MvSet) * ns, cudaMemcpyHostToDevice, st));
         if (!iu.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_utv.p, iu.data(), sizeof(MvItem) * iu.size(), cudaMemcpyHostToDevice, st));
         if (!ir.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_red.p, ir.data(), sizeof(MvItem) * ir.size(), cudaMemcpyHostToDevice, st));
@@ -1097,6 +1215,15 @@ hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S
     return HDF_OK;
 }
 
-void hdf_batch_free(hdf_batch* b) { delete b; }
+void hdf_batch_free(hdf_batch* b) {
+    if (!b) return;
+    // the buffers come from the stream-ordered pool of the build / matvec streams: make sure no
+    // kernel still reads them, then return them on the legacy stream
+    cudaDeviceSynchronize();
+    for (DevBuf* d : {&b->U, &b->S, &b->arena, &b->dsets, &b->mvsets, &b->mvitems_utv, &b->mvitems_red,
+                      &b->mvitems_uw, &b->mvpart, &b->mvW, &b->counters})
+        d->st = nullptr;
+    delete b;
+}
 
 }  // extern "C"

@@ -283,6 +283,71 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     e = b - (s - a);
 }
 
+// Chebyshev moments for FP32 factors: sum over the points [i0, i1) of T_l(u), l < nmom,
+// u = 8 rho^2 - 1, by one 256-thread block.  Each thread runs one point's recurrence in
+// double-float arithmetic (FP32 pairs; FP64 runs at a small fraction of the FP32 rate here),
+// the values pass through shared memory (Tsm: 256 rows of nmom + 1 float2, an odd stride that
+// keeps the 8-byte accesses conflict-free), thread l < nmom adds moment l over the tile with
+// error-free sums, and the tile sums are added in FP64.  Thread l returns moment l.
+__device__ __forceinline__ double moments_df_range(const double* __restrict__ x, int d, const double* cc,
+                                                   double inv2R, int nmom, int64_t i0, int64_t i1, float2* Tsm) {
+    const int S = nmom + 1;
+    double acc = 0.0;
+    for (int64_t t0 = i0; t0 < i1; t0 += 256) {
+        const int cnt = (int)min((int64_t)256, i1 - t0);
+        const int p = threadIdx.x;
+        if (p < cnt) {
+            float2* T = Tsm + p * S;
+            const int64_t i = t0 + p;
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) { const double y = (x[i * d + j] - cc[j]) * inv2R; s += y * y; }
+            const double u = 8.0 * s - 1.0;
+            const float uh = (float)u, ul = (float)(u - (double)uh);
+            const float u2h = 2.f * uh, u2l = 2.f * ul;
+            float ah = 1.f, al = 0.f, bh = uh, bl = ul;
+            T[0] = make_float2(1.f, 0.f);
+            if (nmom > 1) T[1] = make_float2(uh, ul);
+            for (int l = 2; l < nmom; ++l) {
+                const float ph = u2h * bh;
+                float pl = fmaf(u2h, bh, -ph);
+                pl = fmaf(u2h, bl, fmaf(u2l, bh, pl));
+                float sh, se;
+                two_sum(ph, -ah, sh, se);
+                se += pl - al;
+                float th, tl;
+                fast_two_sum(sh, se, th, tl);
+                T[l] = make_float2(th, tl);
+                ah = bh; al = bl;
+                bh = th; bl = tl;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nmom) {
+            float mh = 0.f, ml = 0.f;
+            for (int q = 0; q < cnt; ++q) {
+                const float2 v = Tsm[q * S + threadIdx.x];
+                float sh, se;
+                two_sum(mh, v.x, sh, se);
+                se += ml + v.y;
+                fast_two_sum(sh, se, mh, ml);
+            }
+            acc += (double)mh + (double)ml;
+        }
+        __syncthreads();
+    }
+    return acc;
+}
+
+// Drop-in for k_radial_moments (same part layout) for FP32 factors.
+static __global__ void __launch_bounds__(256) k_radial_moments_df(const double* __restrict__ x, int64_t n, int d,
+                                                                  int64_t chunk, Center c, double inv2R, int nmom,
+                                                                  double* __restrict__ part) {
+    extern __shared__ float2 tsm_raw[];
+    const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    const double v = moments_df_range(x, d, c.c, inv2R, nmom, i0, i1, tsm_raw);
+    if (threadIdx.x < nmom) part[(int64_t)blockIdx.x * nmom + threadIdx.x] = v;
+}
+
 // Basis values of one point in double-float arithmetic (FP32 pairs, about 48 bits): u and rho
 // from FP64 coordinates (a few FP64 operations), then T_l(u) = 2 u T_{l-1} - T_{l-2} with
 // error-free products and sums; the recurrence is stable on [-1, 1].
