@@ -838,31 +838,47 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     struct Offs { size_t q0, q1, qc, w, par, ch, qd, yc, gs, ca, cb; int mtp; };
     std::vector<Offs> offs(ns);
     std::vector<T> Sd(b->soff[ns], (T)0);
-    for (int s = 0; s < ns; ++s) {
+    // per-set conversions to the bulk type (and the FP32 Qmat pairs) on the worker pool
+    struct Conv { std::vector<T> Wt, cA, cB; std::vector<float> qc; int mtp = 0; };
+    std::vector<Conv> cv(ns);
+    parallel_for(ns, [&](int s) {
         const DeviceTables& tb = tbs[s];
         const FactorChoice& fc = fcs[s];
-        std::vector<T> Wt(tb.Wt.size()), cA(tb.coefA.size()), cB(tb.coefB.size());
-        for (size_t q = 0; q < Wt.size(); ++q) Wt[q] = (T)tb.Wt[q];
-        for (size_t q = 0; q < cA.size(); ++q) { cA[q] = (T)tb.coefA[q]; cB[q] = (T)tb.coefB[q]; }
-        offs[s].q0 = put(fc.Qmat[0].data(), sizeof(double) * fc.Qmat[0].size());
-        offs[s].q1 = put(fc.Qmat[1].data(), sizeof(double) * fc.Qmat[1].size());
-        offs[s].qc = 0;
-        offs[s].mtp = 0;
+        Conv& c = cv[s];
+        c.Wt.resize(tb.Wt.size());
+        c.cA.resize(tb.coefA.size());
+        c.cB.resize(tb.coefB.size());
+        for (size_t q = 0; q < c.Wt.size(); ++q) c.Wt[q] = (T)tb.Wt[q];
+        for (size_t q = 0; q < c.cA.size(); ++q) { c.cA[q] = (T)tb.coefA[q]; c.cB[q] = (T)tb.coefB[q]; }
         if (sizeof(T) == 4) {
             // [Qmat0 | Qmat1] as (hi, lo) float pairs, (L+1) x mtp, odd columns zero in row L
             const int m0 = fc.m[0], m1 = fc.m[1], L = geo[s].L, mtp = ((m0 + m1 + 7) / 8) * 8;
-            std::vector<float> qc((size_t)2 * (L + 1) * std::max(mtp, 8), 0.f);
+            c.qc.assign((size_t)2 * (L + 1) * std::max(mtp, 8), 0.f);
             auto putq = [&](int l, int o, double v) {
                 const float h = (float)v;
-                qc[2 * ((size_t)l * mtp + o)] = h;
-                qc[2 * ((size_t)l * mtp + o) + 1] = (float)(v - (double)h);
+                c.qc[2 * ((size_t)l * mtp + o)] = h;
+                c.qc[2 * ((size_t)l * mtp + o) + 1] = (float)(v - (double)h);
             };
             for (int l = 0; l < fc.nb[0]; ++l)
                 for (int o = 0; o < m0; ++o) putq(l, o, fc.Qmat[0][(size_t)l * m0 + o]);
             for (int l = 0; l < fc.nb[1]; ++l)
                 for (int o = 0; o < m1; ++o) putq(l, m0 + o, fc.Qmat[1][(size_t)l * m1 + o]);
-            offs[s].qc = put(qc.data(), sizeof(float) * qc.size());
-            offs[s].mtp = mtp;
+            c.mtp = mtp;
+        }
+    });
+    for (int s = 0; s < ns; ++s) {
+        const DeviceTables& tb = tbs[s];
+        const FactorChoice& fc = fcs[s];
+        const std::vector<T>& Wt = cv[s].Wt;
+        const std::vector<T>& cA = cv[s].cA;
+        const std::vector<T>& cB = cv[s].cB;
+        offs[s].q0 = put(fc.Qmat[0].data(), sizeof(double) * fc.Qmat[0].size());
+        offs[s].q1 = put(fc.Qmat[1].data(), sizeof(double) * fc.Qmat[1].size());
+        offs[s].qc = 0;
+        offs[s].mtp = 0;
+        if (sizeof(T) == 4) {
+            offs[s].qc = put(cv[s].qc.data(), sizeof(float) * cv[s].qc.size());
+            offs[s].mtp = cv[s].mtp;
         }
         offs[s].w = put(Wt.data(), sizeof(T) * Wt.size());
         offs[s].par = put(tb.colpar.data(), tb.colpar.size());
@@ -963,8 +979,12 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         return HDF_OK;
     };
     // autotune the CTAs per SM of the persistent grid (cached per device, d and precision)
-    char key[96];
-    std::snprintf(key, sizeof(key), "batch_build:sm%d:d%d:%s:occ%d", nsm, d, sizeof(T) == 4 ? "fp32" : "fp64", occ);
+    // the best grid depends on how much work there is: the key carries log2 of the item count
+    int size_bucket = 0;
+    while ((int64_t(1) << (size_bucket + 1)) <= (int64_t)std::max(1, nitems_b)) ++size_bucket;
+    char key[128];
+    std::snprintf(key, sizeof(key), "batch_build_v2:sm%d:d%d:%s:occ%d:items2^%d", nsm, d,
+                  sizeof(T) == 4 ? "fp32" : "fp64", occ, size_bucket);
     int best = 0;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -977,16 +997,19 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     HDF_CUDA(cudaEventCreate(&e1));
     if (best == 0 && nitems_b > 0) {
         float best_ms = 1e30f;
-        for (int per_sm = 1; per_sm <= occ; ++per_sm) {
-            HDF_CUDA(cudaEventRecord(e0, st));
-            hdf_status s = launch(per_sm);
-            if (s != HDF_OK) return s;
-            HDF_CUDA(cudaEventRecord(e1, st));
-            HDF_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            HDF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) { best_ms = ms; best = per_sm; }
-        }
+        // each candidate is timed twice (the first launch can include one-time costs) and
+        // its faster run counts
+        for (int rep = 0; rep < 2; ++rep)
+            for (int per_sm = 1; per_sm <= occ; ++per_sm) {
+                HDF_CUDA(cudaEventRecord(e0, st));
+                hdf_status s = launch(per_sm);
+                if (s != HDF_OK) return s;
+                HDF_CUDA(cudaEventRecord(e1, st));
+                HDF_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                HDF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) { best_ms = ms; best = per_sm; }
+            }
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto m = tune_load();
         m[key] = best;

@@ -1,5 +1,6 @@
 // Host-side planning of the HDF factorization (FP64).  See planner.h.
 #include "planner.h"
+#include <map>
 
 #include <condition_variable>
 #include <mutex>
@@ -102,17 +103,38 @@ void parallel_for(int n, const std::function<void(int)>& fn) {
 // ----------------------------------------------------------------------- Chebyshev
 int cheb_nodes(int p_max) { return 4 * (p_max + 2); }
 
+// cos(pi q / (2M)) for q < 4M, built once per node count (the DCT below reads it with exact
+// integer angle reduction instead of calling cos M^2/2 times per kernel).
+static const std::vector<double>& dct_cos_table(int M) {
+    static std::mutex mu;
+    static std::map<int, std::vector<double>> tabs;
+    std::lock_guard<std::mutex> lk(mu);
+    std::vector<double>& t = tabs[M];
+    if (t.empty()) {
+        t.resize((size_t)4 * M);
+        for (int q = 0; q < 4 * M; ++q) t[q] = std::cos(kPi * q / (2.0 * M));
+    }
+    return t;
+}
+
 void cheb_coeffs(int kernel, double ell, double two_r, int M, bool dell, double* a) {
-    std::vector<double> th(M), v(M);
+    // a_i = (2/M) sum_j cos(i th_j) v_j, th_j = pi (j + 1/2) / M (first-kind nodes), halved at i = 0;
+    // v_j depends on |cos th_j| only, so v_{M-1-j} = v_j, and for even i the two halves of the
+    // sum are equal; odd a_i are zero exactly.
+    const std::vector<double>& tab = dct_cos_table(M);
+    const int M4 = 4 * M;
+    std::vector<double> v(M);
     for (int j = 0; j < M; ++j) {
-        th[j] = kPi * (j + 0.5) / M;
-        const double r = std::fabs(std::cos(th[j]));
+        const double r = std::fabs(tab[(2 * j + 1) % M4]);
         v[j] = dell ? kernel_dell(kernel, two_r * r, ell) : kernel_value(kernel, two_r * r, ell);
     }
+    const int half = M / 2;
     for (int i = 0; i < M; ++i) {
         if (i & 1) { a[i] = 0.0; continue; }
         double s = 0.0;
-        for (int j = 0; j < M; ++j) s += std::cos(i * th[j]) * v[j];
+        for (int j = 0; j < half; ++j) s += tab[((int64_t)i * (2 * j + 1)) % M4] * v[j];
+        s *= 2.0;
+        if (M & 1) s += tab[((int64_t)i * M) % M4] * v[half];
         a[i] = (2.0 / M) * s;
     }
     a[0] *= 0.5;
@@ -265,6 +287,30 @@ void gauss_gegenbauer(int N, double lam, double* t, double* w) {
     }
 }
 
+// Gauss-Gegenbauer rules are shared by every problem of the same dimension: computed once per
+// (N, lambda) and reused.
+void gauss_gegenbauer_cached(int N, double lam, std::vector<double>& t, std::vector<double>& w) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int64_t>, std::pair<std::vector<double>, std::vector<double>>> cache;
+    const std::pair<int, int64_t> key(N, (int64_t)std::llround(lam * 1024.0));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end() && it->first.second * (1.0 / 1024.0) == lam) {
+            t = it->second.first;
+            w = it->second.second;
+            return;
+        }
+    }
+    t.assign(N, 0.0);
+    w.assign(N, 0.0);
+    gauss_gegenbauer(N, lam, t.data(), w.data());
+    if ((double)key.second * (1.0 / 1024.0) == lam) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = std::make_pair(t, w);
+    }
+}
+
 // ------------------------------------------------------------------- radial cores
 // F(s) = sum_q f_q T_q(2s - 1), f_q = a_{2q} (T_{2q}(r) = T_q(2 r^2 - 1)).  By Rodrigues'
 // formula and k integrations by parts, the Gegenbauer coefficient of F(a^2+b^2-2abt) times
@@ -303,13 +349,21 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
     for (int q = 0; q <= L; ++q) deriv[0][q] = a[2 * q];
     for (int k = 1; k <= L; ++k) cheb_derivative(deriv[k - 1], deriv[k], 2.0);   // d/ds = 2 d/du
     out.assign(L + 1, std::vector<double>());
+    std::vector<double> Dmat[2];                   // interpolation-to-coefficient maps, nb = L+1, L
+    for (int par = 0; par < 2; ++par) {
+        const int nb = par == 0 ? L + 1 : L;
+        Dmat[par].resize((size_t)nb * nb);
+        for (int l = 0; l < nb; ++l)
+            for (int j = 0; j < nb; ++j)
+                Dmat[par][(size_t)l * nb + j] = (l == 0 ? 1.0 : 2.0) / nb * std::cos(l * kPi * (j + 0.5) / nb);
+    }
     auto one = [&](int k) {
         const std::vector<double>& Fk = deriv[k];
         const int nb = (k % 2 == 0) ? L + 1 : L;
         if (nb == 0) return;
         const int Nq = (L - k) / 2 + 2;
-        std::vector<double> tq(Nq), wq(Nq);
-        gauss_gegenbauer(Nq, k + alpha, tq.data(), wq.data());
+        std::vector<double> tq, wq;
+        gauss_gegenbauer_cached(Nq, k + alpha, tq, wq);
         const double lpref = std::log(area) + std::lgamma(alpha + 1.0) - 0.5 * std::log(kPi)
                              - std::lgamma(k + alpha + 0.5);
         const double pref = ((k & 1) ? -1.0 : 1.0) * std::exp(lpref);
@@ -318,22 +372,38 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
             u[j] = std::cos(kPi * (j + 0.5) / nb);
             rho[j] = std::sqrt((u[j] + 1.0) / 8.0);
         }
-        std::vector<double> Vv(nb * nb);
+        std::vector<double> Vv(nb * nb), rpow(nb), uqv(Nq), b1v(Nq), b2v(Nq);
+        double* uq = uqv.data();
+        double* b1 = b1v.data();
+        double* b2 = b2v.data();
+        for (int i = 0; i < nb; ++i) rpow[i] = std::pow(rho[i], (double)(k - (k & 1)));   // (ab)^k' = a^k' b^k'
         for (int i = 0; i < nb; ++i) {
             for (int j = 0; j <= i; ++j) {
                 const double ab = rho[i] * rho[j];
                 const double s0 = rho[i] * rho[i] + rho[j] * rho[j];
+                // Clenshaw at all Nq nodes together (independent recurrences side by side)
+                for (int q = 0; q < Nq; ++q) {
+                    uq[q] = 2.0 * (s0 - 2.0 * ab * tq[q]) - 1.0;
+                    b1[q] = 0.0;
+                    b2[q] = 0.0;
+                }
+                for (int m = (int)Fk.size() - 1; m >= 1; --m) {
+                    const double cm = Fk[m];
+                    for (int q = 0; q < Nq; ++q) {
+                        const double b0 = 2.0 * uq[q] * b1[q] - b2[q] + cm;
+                        b2[q] = b1[q];
+                        b1[q] = b0;
+                    }
+                }
                 double integ = 0.0;
-                for (int q = 0; q < Nq; ++q) integ += wq[q] * clenshaw(Fk, 2.0 * (s0 - 2.0 * ab * tq[q]) - 1.0);
-                const double v = pref * std::pow(ab, (double)(k - (k & 1))) * integ;
+                for (int q = 0; q < Nq; ++q) integ += wq[q] * (uq[q] * b1[q] - b2[q] + Fk[0]);
+                const double v = pref * rpow[i] * rpow[j] * integ;
                 Vv[i * nb + j] = Vv[j * nb + i] = v;
             }
         }
         // Gamma = D V D^T with D[l][j] = (2 - delta_l0)/nb cos(l pi (j+1/2)/nb)
-        std::vector<double> D(nb * nb), T(nb * nb, 0.0), G(nb * nb, 0.0);
-        for (int l = 0; l < nb; ++l)
-            for (int j = 0; j < nb; ++j)
-                D[l * nb + j] = (l == 0 ? 1.0 : 2.0) / nb * std::cos(l * kPi * (j + 0.5) / nb);
+        const std::vector<double>& D = Dmat[k % 2];
+        std::vector<double> T(nb * nb, 0.0), G(nb * nb, 0.0);
         for (int l = 0; l < nb; ++l)
             for (int j = 0; j < nb; ++j) {
                 double s = 0.0;

@@ -40,6 +40,8 @@ int64_t harmonic_count(int k, int d);
 void sym_eig(int n, double* A, double* w, double* V);
 // Gauss-Gegenbauer rule for the weight (1-t^2)^(lam-1/2) on [-1,1], N nodes (Golub-Welsch).
 void gauss_gegenbauer(int N, double lam, double* t, double* w);
+// The same, memoised per (N, lambda) for lambda a multiple of 1/1024 (half-integers here).
+void gauss_gegenbauer_cached(int N, double lam, std::vector<double>& t, std::vector<double>& w);
 
 // Radial cores Gamma_k (k = 0..p/2) of r^(k) in the basis rho^(k%2) T_l(8 rho^2 - 1):
 // out[k] is a row-major nb_k x nb_k matrix, nb_k = L+1 (k even) or L (k odd).
