@@ -21,6 +21,8 @@
 
 #include "hdf_kernels.cuh"
 #include "internal.h"
+
+#include <type_traits>
 #include "planner.h"
 
 namespace {
@@ -35,6 +37,7 @@ struct AdjParams {
     int tri;
     const double* Qm0; int nb0, m0;
     const double* Qm1; int nb1, m1;
+    const float2* QC; int mtp;                     // FP32 factors: [Qm0 | Qm1] as float pairs, (Lr+1) x mtp
     const T* Wt; const uint8_t* colk; int nF;
     const int16_t* chains; int nH, cstride; const uint8_t* hk; const int* ktab;
     const T* coefA; const T* coefB;
@@ -44,6 +47,38 @@ struct AdjParams {
     int per_warp_d;                                // doubles per warp
     int per_warp_t;                                // T elements per warp
 };
+
+// Double-float helpers for the FP32 form (FP32 pairs, error-free products and sums).
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float2 df_norm(float s, float e) {
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {          // a * b
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return df_norm(p, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {          // a + b
+    float s, e;
+    df_two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    return df_norm(s, e);
+}
+__device__ __forceinline__ void df_dot_step(float2 a, float2 b, float& sh, float& c) {   // Dot2 step
+    const float ph = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -ph);
+    pe = fmaf(a.x, b.y, fmaf(a.y, b.x, pe));
+    float s2, es;
+    df_two_sum(sh, ph, s2, es);
+    sh = s2;
+    c += es + pe;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
@@ -70,7 +105,71 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
         double xh[kMaxD];
         double s2 = 0.0;
         for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
-        const double rho = sqrt(s2);
+        double rho;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 factors: the radial part in double-float / FP32 arithmetic (FP64 is slow here)
+            const float s2f = (float)s2;
+            const float rhof = sqrtf(s2f);
+            rho = rhof;
+            if (s2 > 0.0) { const double inv = 1.0 / (double)rhof; for (int j = 0; j < P.d; ++j) xh[j] *= inv; }
+            else { for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+            float2* Tl2 = reinterpret_cast<float2*>(Tl);
+            float2* dTl2 = reinterpret_cast<float2*>(dTl);
+            float* Qf = reinterpret_cast<float*>(Q);
+            float* dQf = reinterpret_cast<float*>(dQ);
+            if (lane == 0) {
+                const double u = 8.0 * s2 - 1.0;
+                const float uh = (float)u, ul = (float)(u - (double)uh);
+                const float2 u2 = make_float2(2.f * uh, 2.f * ul);
+                float2 t2 = make_float2(1.f, 0.f), t1 = make_float2(uh, ul);       // T_{l-2}, T_{l-1}
+                float2 d2 = make_float2(0.f, 0.f), d1 = make_float2(1.f, 0.f);     // T'_{l-2}, T'_{l-1}
+                Tl2[0] = t2; dTl2[0] = d2;
+                if (P.Lr >= 1) { Tl2[1] = t1; dTl2[1] = d1; }
+                for (int l = 2; l <= P.Lr; ++l) {
+                    const float2 tn = df_add(df_mul(u2, t1), make_float2(-t2.x, -t2.y));
+                    const float2 dn = df_add(df_add(make_float2(2.f * t1.x, 2.f * t1.y), df_mul(u2, d1)),
+                                             make_float2(-d2.x, -d2.y));
+                    Tl2[l] = tn; dTl2[l] = dn;
+                    t2 = t1; t1 = tn;
+                    d2 = d1; d1 = dn;
+                }
+            }
+            __syncwarp();
+            // S_T[o] = sum_l T_l Qmat[l][o], S_dT[o] = sum_l T'_l Qmat[l][o] (Dot2); then
+            // even: Q = S_T, dQ = 16 rho S_dT;  odd: Q = rho S_T, dQ = S_T + 16 rho^2 S_dT
+            for (int o = lane; o < P.m0 + P.m1; o += 32) {
+                const bool odd = o >= P.m0;
+                const int nb = odd ? P.nb1 : P.nb0;
+                float th = 0.f, tc = 0.f, dh = 0.f, dc = 0.f;
+                for (int l = 0; l < nb; ++l) {
+                    const float2 qm = P.QC[(size_t)l * P.mtp + o];
+                    df_dot_step(Tl2[l], qm, th, tc);
+                    df_dot_step(dTl2[l], qm, dh, dc);
+                }
+                const float st = th + tc, sd = dh + dc;
+                if (!odd) { Qf[o] = st; dQf[o] = 16.f * rhof * sd; }
+                else { Qf[o] = rhof * st; dQf[o] = st + 16.f * s2f * sd; }
+            }
+            __syncwarp();
+            for (int col = lane; col < P.nF; col += 32) {
+                const int k = P.colk[col];
+                const int par = k & 1, ob = par ? P.m0 : 0, mp = par ? P.m1 : P.m0;
+                float F = 0.f, dF = 0.f;
+                for (int l = 0; l < mp; ++l) {
+                    const float wv = (float)P.Wt[(int64_t)l * P.nF + col];
+                    F += Qf[ob + l] * wv;
+                    dF += dQf[ob + l] * wv;
+                }
+                if (rhof > 1e-30f) {
+                    R1[col] = (T)(dF - k * F / rhof);
+                    R2[col] = (T)(F / rhof);
+                } else {
+                    R1[col] = (T)dF;
+                    R2[col] = (T)0;
+                }
+            }
+        } else {
+        rho = sqrt(s2);
         if (s2 > 0.0) { for (int j = 0; j < P.d; ++j) xh[j] /= rho; }
         else { for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
         const double u = 8.0 * s2 - 1.0;
@@ -122,6 +221,7 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
                 R2[col] = (T)0;
             }
         }
+        }
         // level tables with d/dz and d/dq
         for (int j = 0; j < levels; ++j) {
             const int D = P.d - 1 - j;
@@ -154,20 +254,21 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             }
         }
         // (x0 + i x1)^mu and its derivatives, normalised as the harmonics
+        typedef typename std::conditional<sizeof(T) == 4, float, double>::type TP;   // trig precision
         for (int mu = lane; mu <= P.L; mu += 32) {
-            double br = xh[0], bi = xh[1], rr = 1.0, ri = 0.0;     // z^mu
-            double pr = 1.0, pi = 0.0;                              // z^(mu-1)
+            TP br = (TP)xh[0], bi = (TP)xh[1], rr = 1, ri = 0;     // z^mu
+            TP pr = 1, pi = 0;                                      // z^(mu-1)
             int e = mu;
             while (e) {
-                if (e & 1) { const double t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
-                const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+                if (e & 1) { const TP t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
+                const TP t = br * br - bi * bi; bi = (TP)2 * br * bi; br = t;
                 e >>= 1;
             }
             if (mu >= 1) {
-                br = xh[0]; bi = xh[1]; e = mu - 1;
+                br = (TP)xh[0]; bi = (TP)xh[1]; e = mu - 1;
                 while (e) {
-                    if (e & 1) { const double t = pr * br - pi * bi; pi = pr * bi + pi * br; pr = t; }
-                    const double t = br * br - bi * bi; bi = 2.0 * br * bi; br = t;
+                    if (e & 1) { const TP t = pr * br - pi * bi; pi = pr * bi + pi * br; pr = t; }
+                    const TP t = br * br - bi * bi; bi = (TP)2 * br * bi; br = t;
                     e >>= 1;
                 }
             }
@@ -176,7 +277,7 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
                 trx[P.L] = (T)0;
                 try_[P.L] = (T)0;
             } else {
-                const double nm = 0.5641895835477563;
+                const TP nm = (TP)0.5641895835477563;
                 trig[P.L + mu] = (T)(rr * nm);            // Re z^mu
                 trig[P.L - mu] = (T)(ri * nm);            // Im z^mu
                 trx[P.L + mu] = (T)(mu * pr * nm);        // d Re / dx0
@@ -346,6 +447,8 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
     A.L = P.L_used; A.Lr = P.L; A.tri = P.tri;
     A.Qm0 = P.dQ0.as<double>(); A.nb0 = P.nb[0]; A.m0 = P.m[0];
     A.Qm1 = P.dQ1.as<double>(); A.nb1 = P.nb[1]; A.m1 = P.m[1];
+    A.QC = P.dQC.as<float2>(); A.mtp = ((P.m[0] + P.m[1] + 7) / 8) * 8;
+    if (sizeof(T) == 4 && A.QC == nullptr) return hdf::fail(HDF_EINVAL, "hdf_matvec_adjoint: factor lacks its FP32 radial tables");
     A.Wt = P.dW.as<T>(); A.colk = P.dcolk.as<uint8_t>(); A.nF = P.nF;
     A.chains = P.dchains.as<int16_t>(); A.nH = P.nH; A.cstride = hdf::chain_stride(d);
     A.hk = P.dhk.as<uint8_t>(); A.ktab = P.dktab.as<int>();

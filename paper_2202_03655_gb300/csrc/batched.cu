@@ -287,7 +287,8 @@ struct MvSet {
     const void* U; int64_t ldU, n, r, off;
     const void* S;
     double* part;                    // nchunk x c x r
-    void* W;                         // r x c (bulk type)
+    void* W;                         // r x ldw (bulk type), row a = the c values of column a
+    int ldw;                         // c, or the column tile width (zero-padded) for the streaming kernels
     int64_t chunk;
     int nchunk;
 };
@@ -323,10 +324,11 @@ __global__ void k_batch_reduce(const MvSet* __restrict__ sets, const MvItem* __r
     if (a >= S.r) return;
     const T* Sv = reinterpret_cast<const T*>(S.S);
     T* W = reinterpret_cast<T*>(S.W);
-    for (int j = 0; j < c; ++j) {
+    for (int j = 0; j < S.ldw; ++j) {
         double s = 0.0;
-        for (int b = 0; b < S.nchunk; ++b) s += S.part[((int64_t)b * c + j) * S.r + a];
-        W[a * c + j] = (T)(s * (double)Sv[a]);
+        if (j < c)
+            for (int b = 0; b < S.nchunk; ++b) s += S.part[((int64_t)b * c + j) * S.r + a];
+        W[a * S.ldw + j] = (T)(s * (double)Sv[a]);
     }
 }
 
@@ -360,7 +362,8 @@ __global__ void __launch_bounds__(256) k_batch_uw(const MvSet* __restrict__ sets
 template <int CT> struct SkinnyShape {
     static constexpr int TA = CT <= 8 ? 4 : 2;      // U^T V: columns per lane
     static constexpr int AB = 32 * TA;              // U^T V: columns per item
-    static constexpr int VR = 128;                  // U^T V: V rows staged per pass
+    static constexpr int VR = CT <= 4 ? 512 : (CT == 8 ? 384 : 128);   // U^T V: V rows staged per pass
+                                                                        // (static shared memory < 48 KB)
     static constexpr int R = CT <= 8 ? 4 : 2;       // U W: rows per warp
     static constexpr int RB = 8 * R;                // U W: rows per item
     static constexpr int WB = 512;                  // U W: W columns staged per pass
@@ -472,9 +475,10 @@ template <int CT>
 __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
                                                     int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
                                                     int c) {
+    // W rows (CT floats, zero-padded) are read straight from L1/L2: a lane's four columns are
+    // 4 CT consecutive floats, shared by its R rows; no shared memory and no barrier in the loop
     using SS = SkinnyShape<CT>;
-    constexpr int R = SS::R, RB = SS::RB, WB = SS::WB;
-    __shared__ __align__(16) float Ws[WB][CT];
+    constexpr int R = SS::R, RB = SS::RB;
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -493,36 +497,26 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
         for (int t = 0; t < R; ++t)
 #pragma unroll
             for (int j = 0; j < CT; ++j) acc[t][j] = 0.f;
-        for (int64_t cb0 = 0; cb0 < S.r; cb0 += WB) {
-            const int nc = (int)min((int64_t)WB, S.r - cb0);
-            __syncthreads();
-            for (int e = threadIdx.x; e < WB * CT; e += blockDim.x) {
-                const int t = e / CT, j = e % CT;
-                Ws[t][j] = (t < nc && j < c) ? W[(cb0 + t) * c + j] : 0.f;
+#pragma unroll 2
+        for (int64_t a = 4 * lane; a < S.r; a += 128) {        // S.r is a multiple of 4
+            float u[R][4];
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int64_t i = row0 + t;
+                if (i < S.n) {
+                    FVec<4>::ld(U + i * S.ldU + a, u[t]);
+                } else {
+                    u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
+                }
             }
-            __syncthreads();
-            for (int cb = 0; cb < nc; cb += 128) {
-                const int al = cb + 4 * lane;             // column within the staged block
-                if (al >= nc) continue;
-                float u[R][4];
 #pragma unroll
-                for (int t = 0; t < R; ++t) {
-                    const int64_t i = row0 + t;
-                    if (i < S.n) {
-                        FVec<4>::ld(U + i * S.ldU + cb0 + al, u[t]);
-                    } else {
-                        u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
-                    }
-                }
+            for (int q = 0; q < 4; ++q) {
+                float wv[CT];
+                ld_row<CT>(W + (a + q) * CT, wv);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float wv[CT];
-                    ld_row<CT>(&Ws[al + q][0], wv);
+                for (int t = 0; t < R; ++t)
 #pragma unroll
-                    for (int t = 0; t < R; ++t)
-#pragma unroll
-                        for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
-                }
+                    for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
             }
         }
 #pragma unroll
@@ -1058,7 +1052,8 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             poff[s] = ptot;
             ptot += (int64_t)ms[s].nchunk * c * std::max<int64_t>(1, r);
             woff[s] = wtot;
-            wtot += std::max<int64_t>(1, r) * c;
+            ms[s].ldw = skinny ? ct : c;
+            wtot += std::max<int64_t>(1, r) * ms[s].ldw;
             if (r == 0) continue;
             for (int q = 0; q < ms[s].nchunk; ++q)
                 for (int64_t bl = 0; bl < (r + AB - 1) / AB; ++bl) iu.push_back({s, q, bl});
