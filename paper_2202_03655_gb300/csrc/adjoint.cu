@@ -80,11 +80,13 @@ __device__ __forceinline__ void df_dot_step(float2 a, float2 b, float& sh, float
     c += es + pe;
 }
 
-template <typename T>
+// DD = the dimension d (a template parameter, so that the per-thread coordinate and gradient
+// arrays stay in registers).
+template <typename T, int DD>
 __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int levels = P.d - 2;
+    constexpr int levels = DD - 2;
     double* dbase = reinterpret_cast<double*>(smem_raw) + (size_t)warp * P.per_warp_d;
     double* Tl = dbase;                        // Lr+1: T_l(u)
     double* dTl = Tl + (P.Lr + 1);             // Lr+1: T_l'(u)
@@ -104,15 +106,16 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
     for (int64_t i = gw; i < P.n; i += nw) {
         double xh[kMaxD];
         double s2 = 0.0;
-        for (int j = 0; j < P.d; ++j) { xh[j] = (P.x[i * P.d + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
+#pragma unroll
+        for (int j = 0; j < DD; ++j) { xh[j] = (P.x[i * DD + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
         double rho;
         if constexpr (sizeof(T) == 4) {
             // FP32 factors: the radial part in double-float / FP32 arithmetic (FP64 is slow here)
             const float s2f = (float)s2;
             const float rhof = sqrtf(s2f);
             rho = rhof;
-            if (s2 > 0.0) { const double inv = 1.0 / (double)rhof; for (int j = 0; j < P.d; ++j) xh[j] *= inv; }
-            else { for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+            if (s2 > 0.0) { const double inv = 1.0 / (double)rhof; for (int j = 0; j < DD; ++j) xh[j] *= inv; }
+            else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
             float2* Tl2 = reinterpret_cast<float2*>(Tl);
             float2* dTl2 = reinterpret_cast<float2*>(dTl);
             float* Qf = reinterpret_cast<float*>(Q);
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             }
         } else {
         rho = sqrt(s2);
-        if (s2 > 0.0) { for (int j = 0; j < P.d; ++j) xh[j] /= rho; }
-        else { for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+        if (s2 > 0.0) { for (int j = 0; j < DD; ++j) xh[j] /= rho; }
+        else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
         const double u = 8.0 * s2 - 1.0;
         if (lane == 0) {
             Tl[0] = 1.0; dTl[0] = 0.0;
@@ -224,9 +227,11 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
         }
         // level tables with d/dz and d/dq
         for (int j = 0; j < levels; ++j) {
-            const int D = P.d - 1 - j;
+            const int D = DD - 1 - j;
             double q = 0.0;
-            for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
+#pragma unroll
+            for (int m = 0; m < DD; ++m)
+                if (m <= D) q += xh[m] * xh[m];
             const T z = (T)xh[D], qq = (T)q;
             const T* A = P.coefA + j * P.tri;
             const T* B = P.coefB + j * P.tri;
@@ -292,7 +297,8 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
 #pragma unroll
         for (int m = 0; m < kMaxD; ++m) g[m] = (T)0;
         T xt[kMaxD];
-        for (int m = 0; m < P.d; ++m) xt[m] = (T)xh[m];
+#pragma unroll
+        for (int m = 0; m < DD; ++m) xt[m] = (T)xh[m];
         for (int gi = lane; gi < P.nH; gi += 32) {
             const int k = P.hk[gi];
             const int* kt = P.ktab + hdf::kTabStride * k;
@@ -309,6 +315,7 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             const int tmu = ch[levels];
             T pvv[kMaxD], pzz[kMaxD], pqq[kMaxD];
             T prod = trig[P.L + tmu];
+#pragma unroll
             for (int j = 0; j < levels; ++j) {
                 pvv[j] = tv[j * P.tri + ch[j]];
                 pzz[j] = tz[j * P.tri + ch[j]];
@@ -316,33 +323,43 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
                 prod *= pvv[j];
             }
             // Y x_hat term
-            for (int m = 0; m < P.d; ++m) g[m] += al * prod * xt[m];
+#pragma unroll
+    #pragma unroll
+        for (int m = 0; m < DD; ++m) g[m] += al * prod * xt[m];
             // grad H: level terms
+#pragma unroll
             for (int j = 0; j < levels; ++j) {
                 T other = trig[P.L + tmu];
+#pragma unroll
                 for (int j2 = 0; j2 < levels; ++j2)
                     if (j2 != j) other *= pvv[j2];
-                const int D = P.d - 1 - j;
+                const int D = DD - 1 - j;
                 const T cz = be * other * pzz[j], cq = be * other * pqq[j] * (T)2;
                 g[D] += cz;
-                for (int m = 0; m <= D; ++m) g[m] += cq * xt[m];
+#pragma unroll
+                for (int m = 0; m < DD; ++m)
+                    if (m <= D) g[m] += cq * xt[m];
             }
             // grad H: trigonometric factor
             T pl = (T)1;
+#pragma unroll
             for (int j = 0; j < levels; ++j) pl *= pvv[j];
             g[0] += be * pl * trx[P.L + tmu];
             g[1] += be * pl * try_[P.L + tmu];
         }
-        for (int m = 0; m < P.d; ++m) {
+#pragma unroll
+        for (int m = 0; m < DD; ++m) {
             T vsum = g[m];
             for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
             g[m] = vsum;
         }
-        if (lane < P.d) {
+        if (lane < DD) {
             T vsum = (T)0;
-            for (int m = 0; m < P.d; ++m) if (m == lane) vsum = g[m];
+#pragma unroll
+    #pragma unroll
+        for (int m = 0; m < DD; ++m) if (m == lane) vsum = g[m];
             const T out = vsum * (T)P.inv2R;
-            T* dst = P.grad + i * P.d + lane;
+            T* dst = P.grad + i * DD + lane;
             *dst = P.accumulate ? *dst + out : out;
         }
         __syncwarp();
@@ -460,18 +477,20 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
     const int warps = 4;
     const size_t sm = sizeof(double) * warps * A.per_warp_d + sizeof(T) * warps * A.per_warp_t;
     if (sm > 200 * 1024) return hdf::fail(HDF_ETOOBIG, "hdf_matvec_adjoint: per-point tables exceed shared memory");
-    HDF_CUDA(cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    void (*kern)(AdjParams<T>) = d == 3 ? k_adjoint<T, 3> : d == 4 ? k_adjoint<T, 4> : d == 5 ? k_adjoint<T, 5>
+                               : d == 6 ? k_adjoint<T, 6> : d == 7 ? k_adjoint<T, 7> : k_adjoint<T, 8>;
+    HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int nsm = 0, dv = 0, occ = 0;
     HDF_CUDA(cudaGetDevice(&dv));
     HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
-    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<T>, warps * 32, sm));
+    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm));
     const int grid = std::max(1, std::min<int>(nsm * std::max(occ, 1), (int)((n + warps - 1) / warps)));
     for (int j = 0; j < ncols; ++j) {
         A.a = a + j; A.b = b + j; A.ab_stride = ncols;
         A.v = V + j * ldv; A.w = Wv + j * ldw;
         A.accumulate = (j > 0);
         HDF_COUNT_LAUNCH();
-        k_adjoint<T><<<grid, warps * 32, sm, st>>>(A);
+        kern<<<grid, warps * 32, sm, st>>>(A);
         HDF_CUDA(cudaGetLastError());
     }
     // d f / d l on the host from U^T V, U^T W and the frozen dS_k/dl

@@ -364,8 +364,9 @@ template <int CT> struct SkinnyShape {
     static constexpr int AB = 32 * TA;              // U^T V: columns per item
     static constexpr int VR = CT <= 4 ? 512 : (CT == 8 ? 384 : 128);   // U^T V: V rows staged per pass
                                                                         // (static shared memory < 48 KB)
-    static constexpr int R = CT <= 8 ? 4 : 2;       // U W: rows per warp
-    static constexpr int RB = 8 * R;                // U W: rows per item
+    static constexpr int R = CT <= 8 ? 4 : 2;       // U W: rows per warp and group
+    static constexpr int G = 4;                     // U W: row groups per warp and item
+    static constexpr int RB = 8 * R * G;            // U W: rows per item
     static constexpr int WB = 512;                  // U W: W columns staged per pass
 };
 
@@ -476,9 +477,12 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
                                                     int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
                                                     int c) {
     // W rows (CT floats, zero-padded) are read straight from L1/L2: a lane's four columns are
-    // 4 CT consecutive floats, shared by its R rows; no shared memory and no barrier in the loop
+    // 4 CT consecutive floats, shared by its R rows; no barrier in the loop.  Each warp takes G
+    // groups of R rows per item; a group's R x CT sums are reduced across the warp through
+    // shared memory (lane o adds output o over the 32 lanes).
     using SS = SkinnyShape<CT>;
-    constexpr int R = SS::R, RB = SS::RB;
+    constexpr int R = SS::R, G = SS::G, RB = SS::RB, NO = R * CT;     // NO <= 32
+    __shared__ __align__(16) float red[8][32][NO + 1];        // odd row stride: conflict-free
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -491,52 +495,50 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
         const MvSet& S = sets[w.set];
         const float* U = reinterpret_cast<const float*>(S.U);
         const float* W = reinterpret_cast<const float*>(S.W);
-        const int64_t row0 = w.blk * RB + (int64_t)warp * R;
-        float acc[R][CT];
+        for (int gq = 0; gq < G; ++gq) {
+            const int64_t row0 = w.blk * RB + ((int64_t)gq * 8 + warp) * R;
+            if (row0 >= S.n) break;
+            float acc[R][CT];
 #pragma unroll
-        for (int t = 0; t < R; ++t)
+            for (int t = 0; t < R; ++t)
 #pragma unroll
-            for (int j = 0; j < CT; ++j) acc[t][j] = 0.f;
+                for (int j = 0; j < CT; ++j) acc[t][j] = 0.f;
 #pragma unroll 2
-        for (int64_t a = 4 * lane; a < S.r; a += 128) {        // S.r is a multiple of 4
-            float u[R][4];
+            for (int64_t a = 4 * lane; a < S.r; a += 128) {        // S.r is a multiple of 4
+                float u[R][4];
 #pragma unroll
-            for (int t = 0; t < R; ++t) {
-                const int64_t i = row0 + t;
-                if (i < S.n) {
-                    FVec<4>::ld(U + i * S.ldU + a, u[t]);
-                } else {
-                    u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
+                for (int t = 0; t < R; ++t) {
+                    const int64_t i = row0 + t;
+                    if (i < S.n) {
+                        FVec<4>::ld(U + i * S.ldU + a, u[t]);
+                    } else {
+                        u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float wv[CT];
+                    ld_row<CT>(W + (a + q) * CT, wv);
+#pragma unroll
+                    for (int t = 0; t < R; ++t)
+#pragma unroll
+                        for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float wv[CT];
-                ld_row<CT>(W + (a + q) * CT, wv);
+            for (int t = 0; t < R; ++t)
 #pragma unroll
-                for (int t = 0; t < R; ++t)
-#pragma unroll
-                    for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < R; ++t)
-#pragma unroll
-            for (int j = 0; j < CT; ++j) {
-                float v = acc[t][j];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                acc[t][j] = v;
-            }
-        if (lane == 0) {
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
+                for (int j = 0; j < CT; ++j) red[warp][lane][t * CT + j] = acc[t][j];
+            __syncwarp();
+            if (lane < NO) {
+                float v = 0.f;
+#pragma unroll 8
+                for (int l2 = 0; l2 < 32; ++l2) v += red[warp][l2][lane];
+                const int t = lane / CT, j = lane % CT;
                 const int64_t i = row0 + t;
-                if (i < S.n)
-#pragma unroll
-                    for (int j = 0; j < CT; ++j)
-                        if (j < c) Y[S.off + i + (int64_t)j * ldy] = acc[t][j];
+                if (i < S.n && j < c) Y[S.off + i + (int64_t)j * ldy] = v;
             }
+            __syncwarp();
         }
     }
 }
