@@ -41,6 +41,31 @@ using namespace hdf;
 namespace {
 
 constexpr int kMu2Sample = 512;
+
+// Pinned host staging buffer for the batched build's table upload, kept between builds (grown
+// on demand).  The caller holds the lock until the copy has completed; a build that finds it
+// held uses pageable memory instead.
+unsigned char* staging_acquire(size_t bytes, std::unique_lock<std::mutex>& lk) {
+    static std::mutex mu;
+    static unsigned char* buf = nullptr;
+    static size_t cap = 0;
+    std::unique_lock<std::mutex> l(mu, std::try_to_lock);
+    if (!l.owns_lock()) return nullptr;
+    if (cap < bytes) {
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        cap = 0;
+        const size_t want = std::max(bytes, size_t(64) << 20);
+        if (cudaMallocHost(reinterpret_cast<void**>(&buf), want) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+            return nullptr;
+        }
+        cap = want;
+    }
+    lk = std::move(l);
+    return buf;
+}
 constexpr int kSegChunk = 8192;      // points per reduction item
 constexpr int kGramChunk = 4096;     // points per Gram item
 
@@ -823,12 +848,16 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         b->soff[s + 1] = b->soff[s] + tbs[s].ldU;
         foff[s + 1] = foff[s] + geo[s].n * std::max(1, tbs[s].nF);
     }
-    // arena of per-set tables: each piece 256-byte aligned
-    std::vector<unsigned char> arena;
+    // arena of per-set tables, each piece 256-byte aligned: offsets first (serial), then the
+    // pieces are copied on the worker pool into a pinned staging buffer and uploaded at once
+    size_t arena_size = 0;
+    struct Piece { const void* src; size_t bytes, off; };
+    std::vector<std::vector<Piece>> pieces(ns);
+    int cur_set = 0;
     auto put = [&](const void* src, size_t bytes) -> size_t {
-        size_t o = (arena.size() + 255) & ~size_t(255);
-        arena.resize(o + std::max<size_t>(bytes, 16));
-        if (bytes) std::memcpy(arena.data() + o, src, bytes);
+        const size_t o = (arena_size + 255) & ~size_t(255);
+        arena_size = o + std::max<size_t>(bytes, 16);
+        pieces[cur_set].push_back({src, bytes, o});
         return o;
     };
     struct Offs { size_t q0, q1, qc, w, par, ch, qd, yc, gs, ca, cb; int mtp; };
@@ -863,6 +892,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         }
     });
     for (int s = 0; s < ns; ++s) {
+        cur_set = s;
         const DeviceTables& tb = tbs[s];
         const FactorChoice& fc = fcs[s];
         const std::vector<T>& Wt = cv[s].Wt;
@@ -887,8 +917,19 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         for (int64_t a = 0; a < tb.ldU; ++a) Sd[b->soff[s] + a] = (T)tb.Spad[a];
         b->colmap[s] = tb.colmap;
     }
-    HDF_CUDA(b->arena.alloc_on(arena.size(), st));
-    HDF_CUDA(cudaMemcpyAsync(b->arena.p, arena.data(), arena.size(), cudaMemcpyHostToDevice, st));
+    std::unique_lock<std::mutex> staging_lock;
+    unsigned char* stage = staging_acquire(arena_size, staging_lock);
+    std::vector<unsigned char> arena_pageable;
+    if (!stage) {                                    // another build holds the pinned buffer
+        arena_pageable.resize(arena_size);
+        stage = arena_pageable.data();
+    }
+    parallel_for(ns, [&](int s) {
+        for (const Piece& pc : pieces[s])
+            if (pc.bytes) std::memcpy(stage + pc.off, pc.src, pc.bytes);
+    });
+    HDF_CUDA(b->arena.alloc_on(arena_size, st));
+    HDF_CUDA(cudaMemcpyAsync(b->arena.p, stage, arena_size, cudaMemcpyHostToDevice, st));
     HDF_CUDA(b->S.alloc_on(sizeof(T) * std::max<int64_t>(1, b->soff[ns]), st));
     HDF_CUDA(cudaMemcpyAsync(b->S.p, Sd.data(), sizeof(T) * Sd.size(), cudaMemcpyHostToDevice, st));
     const size_t ubytes = sizeof(T) * (size_t)std::max<int64_t>(1, b->uoff[ns]);
