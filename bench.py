@@ -341,6 +341,27 @@ def bench_adjoint(args):
     # accuracy outside the timed region: sampled rows of K~ v against the exact kernel
     f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
     y = f.matvec(v)
+    # the solve on this factor (A6 Gram U^T U on the tensor cores + host LU of the core, A8
+    # Woodbury apply with one refinement step); the second solve reuses the factored core.
+    # lambda grows with n as in kernel ridge regression, so that the condition number of
+    # lambda I + K~ (largest eigenvalue ~ n times the mean kernel value) stays within what an
+    # FP32 factor resolves; the work timed does not depend on lambda
+    lam = 1e-4 * n
+    s0 = time.perf_counter()
+    xs = f.solve(lam, v, refine_steps=1)
+    torch.cuda.synchronize()
+    solve_first_ms = 1e3 * (time.perf_counter() - s0)
+    s0 = time.perf_counter()
+    xs = f.solve(lam, v, refine_steps=1)
+    torch.cuda.synchronize()
+    solve_again_ms = 1e3 * (time.perf_counter() - s0)
+    gram_ms = float(f.info.t_ms[6])
+    res = lam * xs + f.matvec(xs) - v
+    solve_res = float(torch.linalg.norm(res.double()) / torch.linalg.norm(v.double()))
+    ldu_s = f.info.ldu
+    gram_flops = 3 * 2.0 * n * ldu_s * ldu_s        # three TF32 products per multiply-add
+    pk, _ = load_peaks()
+    tf32_peak = float(pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])) * 1.1 / 2.25
     rows = np.sort(W.rng(7).choice(n, 512, replace=False))
     exact = exact_rows_matvec(x, w["kernel"], w["ell"], v.double(), rows)
     approx = y[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
@@ -387,6 +408,12 @@ def bench_adjoint(args):
                            "parallelism": f"replicas{ws}", "l2": f"inputs larger than L2 (U is {n * info.ldu * 4 / 1e9:.1f} GB)"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
                 "detail": {"adjoint_ms": adj_ms, "build_ms": float(info.t_ms[7]),
+                           "solve": {"lambda": lam, "first_ms": solve_first_ms, "again_ms": solve_again_ms,
+                                     "gram_ms": gram_ms, "residual": solve_res,
+                                     "gram_tensor_tflops": gram_flops / (gram_ms / 1e3) / 1e12 if gram_ms > 0 else None,
+                                     "gram_tensor_frac_of_tf32": (gram_flops / (gram_ms / 1e3) / 1e12 / tf32_peak)
+                                     if gram_ms > 0 else None,
+                                     "tf32_peak_source": "measured bf16 cuBLAS burst x 1.1/2.25 (nominal TF32/BF16)"},
                            "rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound,
                            "value_f": recs[-1][2]}}
         print(json.dumps(line), flush=True)

@@ -101,7 +101,8 @@ typedef struct {
                                1 Chebyshev + degree + radial cores (host, while the device
                                sums the radial moments), 2 rest of the moments + radial-basis
                                Gram, 3 basis factor + eigendecompositions + truncation (host),
-                               4 radial factors (device), 5 harmonics + U (device), 6 unused,
+                               4 radial factors (device), 5 harmonics + U (device), 6 the
+                               Gram U^T U of the first hdf_solve (device; 0 before it),
                                7 whole build */
 } hdf_info;
 

@@ -523,27 +523,71 @@ extern "C" hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t
 
 // --------------------------------------------------------------------------- solve
 
-// Host LU with partial pivoting of the r x r core (row-major, in place).
+// Host LU with partial pivoting of the r x r core (row-major, in place), blocked right-looking:
+// each 64-column panel is factored serially, then the block row U12 (forward substitution with
+// the panel's unit lower triangle) and the trailing matrix (A22 -= L21 U12, four rows at a time
+// against each U12 row) are updated on the worker pool.  Row interchanges cover whole rows, so
+// pivots and factors equal those of the unblocked algorithm up to rounding order.
 static bool lu_factor(int64_t r, std::vector<double>& A, std::vector<int>& piv) {
     piv.resize(r);
-    for (int64_t k = 0; k < r; ++k) {
-        int64_t p = k;
-        double best = std::fabs(A[k * r + k]);
-        for (int64_t i = k + 1; i < r; ++i)
-            if (std::fabs(A[i * r + k]) > best) { best = std::fabs(A[i * r + k]); p = i; }
-        piv[k] = (int)p;
-        if (best == 0.0 || !std::isfinite(best)) return false;
-        if (p != k)
-            for (int64_t j = 0; j < r; ++j) std::swap(A[k * r + j], A[p * r + j]);
-        const double inv = 1.0 / A[k * r + k];
-        for (int64_t i = k + 1; i < r; ++i) {
-            double* Ai = &A[i * r];
-            const double l = Ai[k] * inv;
-            Ai[k] = l;
-            if (l == 0.0) continue;
+    const int64_t NB = 64, RB = 32, CB = 128;
+    for (int64_t kb = 0; kb < r; kb += NB) {
+        const int64_t ke = std::min(r, kb + NB);
+        for (int64_t k = kb; k < ke; ++k) {
+            int64_t p = k;
+            double best = std::fabs(A[k * r + k]);
+            for (int64_t i = k + 1; i < r; ++i)
+                if (std::fabs(A[i * r + k]) > best) { best = std::fabs(A[i * r + k]); p = i; }
+            piv[k] = (int)p;
+            if (best == 0.0 || !std::isfinite(best)) return false;
+            if (p != k)
+                for (int64_t j = 0; j < r; ++j) std::swap(A[k * r + j], A[p * r + j]);
+            const double inv = 1.0 / A[k * r + k];
             const double* Ak = &A[k * r];
-            for (int64_t j = k + 1; j < r; ++j) Ai[j] -= l * Ak[j];
+            for (int64_t i = k + 1; i < r; ++i) {
+                double* Ai = &A[i * r];
+                const double l = Ai[k] * inv;
+                Ai[k] = l;
+                if (l == 0.0) continue;
+                for (int64_t j = k + 1; j < ke; ++j) Ai[j] -= l * Ak[j];
+            }
         }
+        if (ke == r) break;
+        const int64_t nt = r - ke;
+        parallel_for((int)((nt + CB - 1) / CB), [&](int cbk) {
+            const int64_t j0 = ke + cbk * CB, j1 = std::min(r, j0 + CB);
+            for (int64_t i = kb + 1; i < ke; ++i) {
+                double* Ai = &A[i * r];
+                for (int64_t q = kb; q < i; ++q) {
+                    const double l = Ai[q];
+                    const double* Aq = &A[q * r];
+                    for (int64_t j = j0; j < j1; ++j) Ai[j] -= l * Aq[j];
+                }
+            }
+        });
+        parallel_for((int)((nt + RB - 1) / RB), [&](int rbk) {
+            const int64_t i0 = ke + rbk * RB, i1 = std::min(r, i0 + RB);
+            int64_t i = i0;
+            for (; i + 4 <= i1; i += 4) {
+                double *A0 = &A[i * r], *A1 = A0 + r, *A2 = A1 + r, *A3 = A2 + r;
+                for (int64_t q = kb; q < ke; ++q) {
+                    const double l0 = A0[q], l1 = A1[q], l2 = A2[q], l3 = A3[q];
+                    const double* Aq = &A[q * r];
+                    for (int64_t j = ke; j < r; ++j) {
+                        const double u = Aq[j];
+                        A0[j] -= l0 * u; A1[j] -= l1 * u; A2[j] -= l2 * u; A3[j] -= l3 * u;
+                    }
+                }
+            }
+            for (; i < i1; ++i) {
+                double* Ai = &A[i * r];
+                for (int64_t q = kb; q < ke; ++q) {
+                    const double l = Ai[q];
+                    const double* Aq = &A[q * r];
+                    for (int64_t j = ke; j < r; ++j) Ai[j] -= l * Aq[j];
+                }
+            }
+        });
     }
     return true;
 }
@@ -618,13 +662,35 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
     if (r > 0 && f->G.empty()) {
         DevBuf Gd;
         HDF_CUDA(Gd.alloc(sizeof(double) * (size_t)r * r));
-        const unsigned nt = (unsigned)((r + 63) / 64);
-        HDF_COUNT_LAUNCH();
-        dev::k_gram<T><<<dim3(nt, nt), 256, 0, st>>>(f->U.as<T>(), f->info.ldu, n, r, Gd.as<double>());
-        HDF_CUDA(cudaGetLastError());
+        cudaEvent_t g0, g1;
+        HDF_CUDA(cudaEventCreate(&g0));
+        HDF_CUDA(cudaEventCreate(&g1));
+        HDF_CUDA(cudaEventRecord(g0, st));
+        const bool aligned = (reinterpret_cast<uintptr_t>(f->U.p) % 16 == 0) && (f->info.ldu % 4 == 0);
+        if (sizeof(T) == 4 && f->use_tc && aligned && r >= 64 && n >= 32) {
+            // U^T U on the tensor cores (FP32 factors)
+            if (!f->dev_err.p) {
+                HDF_CUDA(f->dev_err.alloc(sizeof(int)));
+                HDF_CUDA(cudaMemsetAsync(f->dev_err.p, 0, sizeof(int), st));
+            }
+            hdf_status s = tc_gram(reinterpret_cast<const float*>(f->U.p), f->info.ldu, n, r, Gd.as<double>(),
+                                   f->dev_err.as<int>(), st);
+            if (s != HDF_OK) return s;
+        } else {
+            const unsigned nt = (unsigned)((r + 63) / 64);
+            HDF_COUNT_LAUNCH();
+            dev::k_gram<T><<<dim3(nt, nt), 256, 0, st>>>(f->U.as<T>(), f->info.ldu, n, r, Gd.as<double>());
+            HDF_CUDA(cudaGetLastError());
+        }
+        HDF_CUDA(cudaEventRecord(g1, st));
         f->G.resize((size_t)r * r);
         HDF_CUDA(cudaMemcpyAsync(f->G.data(), Gd.p, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
         HDF_CUDA(cudaStreamSynchronize(st));
+        float gms = 0.f;
+        cudaEventElapsedTime(&gms, g0, g1);
+        f->info.t_ms[6] = gms;
+        cudaEventDestroy(g0);
+        cudaEventDestroy(g1);
     }
     if (r > 0 && f->core_lambda != lambda) {
         f->LU = f->G;

@@ -24,6 +24,7 @@ size_t tc_work_floats(int64_t n, int64_t r, int c);
 void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk);
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
                   double* part, float* work, int* err, cudaStream_t st);
+hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G, int* err, cudaStream_t st);
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
                  int64_t ldb, float beta, float* Y, int64_t ldy, float* work, int* err, cudaStream_t st);
 

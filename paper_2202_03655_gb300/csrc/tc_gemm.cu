@@ -683,6 +683,44 @@ __global__ void k_prep_v(const float* __restrict__ V, int64_t ldv, int64_t n, in
     lo[idx] = v - h;
 }
 
+// Gram G = U^T U on the tensor cores, 64 columns at a time: the column block U[:, j0 : j0 + 64)
+// is transposed through shared memory into the column-major TF32 hi / lo arrays that the U^T V
+// kernel takes as its V operand.  hi[j ldo + i] + lo[j ldo + i] = U[i, j0 + j] (zero outside).
+__global__ void __launch_bounds__(256) k_prep_ucols(const float* __restrict__ U, int64_t ldU, int64_t n,
+                                                    int64_t r, int64_t j0, int64_t ldo, float* __restrict__ hi,
+                                                    float* __restrict__ lo) {
+    __shared__ float t[64][65];
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {        // rows i0 + e / 64, columns j0 + e % 64
+        const int ii = e / 64, jj = e % 64;
+        const int64_t i = i0 + ii, j = j0 + jj;
+        t[ii][jj] = (i < n && j < r) ? U[i * ldU + j] : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {        // columns e / 64, rows i0 + e % 64
+        const int jj = e / 64, ii = e % 64;
+        const int64_t i = i0 + ii;
+        if (i >= ldo) continue;
+        const float v = t[ii][jj];
+        const float h = tf32_hi(v);
+        hi[(int64_t)jj * ldo + i] = h;
+        lo[(int64_t)jj * ldo + i] = v - h;
+    }
+}
+
+// G[a * ldg + j0 + j] = sum over the row chunks of part[(chunk * 64 + j) * r + a], a < r, j0 + j < r.
+__global__ void k_reduce_gram(const double* __restrict__ part, int nchunk, int64_t r, int64_t j0,
+                              double* __restrict__ G, int64_t ldg) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= r * 64) return;
+    const int64_t a = idx / 64;
+    const int j = (int)(idx % 64);
+    if (j0 + j >= r) return;
+    double s = 0.0;
+    for (int b = 0; b < nchunk; ++b) s += part[((int64_t)b * 64 + j) * r + a];
+    G[a * ldg + j0 + j] = s;
+}
+
 // ------------------------------------------------------------------------- host side
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -756,9 +794,11 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
     const int64_t ldo = ((n + 3) / 4) * 4;
     float* vhi = work;
     float* vlo = work + (size_t)c * ldo;
-    HDF_COUNT_LAUNCH();
-    k_prep_v<<<(unsigned)(((int64_t)c * ldo + 255) / 256), 256, 0, st>>>(V, ldv, n, c, ldo, vhi, vlo);
-    HDF_CUDA(cudaGetLastError());
+    if (V) {                     // V == nullptr: the caller has written the split into work
+        HDF_COUNT_LAUNCH();
+        k_prep_v<<<(unsigned)(((int64_t)c * ldo + 255) / 256), 256, 0, st>>>(V, ldv, n, c, ldo, vhi, vlo);
+        HDF_CUDA(cudaGetLastError());
+    }
     CUtensorMap mU, mV, mVl;
     if (!make_map(&mU, U, (uint64_t)ldU, (uint64_t)n, (uint64_t)ldU * 4, BM, BK, false) ||
         !make_map(&mV, vhi, (uint64_t)n, (uint64_t)c, (uint64_t)ldo * 4, KH, BN, true) ||
@@ -814,6 +854,31 @@ hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float
         case 64: return tc::utv_bn<64>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
     }
     return fail(HDF_EINVAL, "tc_utv: column count");
+}
+
+// G = U^T U (r x r, FP64, row-major) on the tensor cores (3xTF32 products, FP32 sums per row
+// chunk, FP64 across chunks).  Work space from the stream-ordered pool.
+hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G, int* err, cudaStream_t st) {
+    int64_t chunk = 0;
+    int nch = 0;
+    tc_utv_split(n, r, &chunk, &nch);
+    const int64_t ldo = ((n + 3) / 4) * 4;
+    DevBuf work, part;
+    HDF_CUDA(work.alloc_on(sizeof(float) * (2 * (size_t)64 * ldo + 4), st));
+    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * 64 * r, st));
+    float* hi = work.as<float>();
+    float* lo = hi + (size_t)64 * ldo;
+    for (int64_t j0 = 0; j0 < r; j0 += 64) {
+        HDF_COUNT_LAUNCH();
+        tc::k_prep_ucols<<<(unsigned)((ldo + 63) / 64), 256, 0, st>>>(U, ldU, n, r, j0, ldo, hi, lo);
+        HDF_CUDA(cudaGetLastError());
+        hdf_status s = tc::utv_bn<64>(U, ldU, n, r, nullptr, 0, 64, chunk, part.as<double>(), work.as<float>(), err, st);
+        if (s != HDF_OK) return s;
+        HDF_COUNT_LAUNCH();
+        tc::k_reduce_gram<<<(unsigned)((r * 64 + 255) / 256), 256, 0, st>>>(part.as<double>(), nch, r, j0, G, r);
+        HDF_CUDA(cudaGetLastError());
+    }
+    return HDF_OK;
 }
 
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,

@@ -243,6 +243,7 @@ class Factor:
         Xc = torch.empty_like(Bc)
         _check(lib().hdf_solve(self._h, float(lam), _vp(Bc.data_ptr()), self.n, c, _vp(Xc.data_ptr()), self.n,
                                int(refine_steps), _stream_handle(stream)))
+        _check(lib().hdf_factor_info(self._h, ctypes.byref(self.info)))     # t_ms[6]: Gram time
         X = Xc.t()
         return X.reshape(-1) if vec else X
 

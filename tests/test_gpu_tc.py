@@ -63,3 +63,24 @@ def test_tensor_core_solve_refinement():
     X = f.solve(1e-2, to_dev(B, torch.float32), refine_steps=1).double().cpu().numpy()
     assert f.device_errors() == 0
     assert rel(X, ohdf.solve(fo, 1e-2, B)) <= 2e-3
+
+
+@pytest.mark.parametrize("case", ["ball3", "cube4"])
+def test_tensor_core_gram_solve(case):
+    """hdf_solve with U^T U on the tensor cores (FP32 factors) against the same solve with the
+    CUDA-core Gram, and the residual of (lam I + K~) X = B through the factor."""
+    import torch
+    x, f_tc, f_cc, U, S = _factors(case)
+    n = x.shape[0]
+    lam = 1e-2
+    B = np.random.default_rng(17).standard_normal((n, 3)).astype(np.float32)
+    X_tc = f_tc.solve(lam, to_dev(B), refine_steps=1).double().cpu().numpy()
+    X_cc = f_cc.solve(lam, to_dev(B), refine_steps=1).double().cpu().numpy()
+    assert f_tc.device_errors() == 0
+    assert rel(X_tc, X_cc) <= 1e-4
+    # the FP32 residual is bounded by the conditioning of lam I + K~ (X is ~ B / lam in the
+    # directions K~ does not reach); the tensor-core Gram must not make it worse
+    Bd = B.astype(np.float64)
+    res = lambda X: rel(lam * X + U @ (S[:, None] * (U.T @ X)), Bd)
+    assert res(X_tc) <= 2 * res(X_cc) + 1e-6
+    assert res(X_tc) <= 1e-2
