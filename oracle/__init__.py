@@ -21,6 +21,8 @@ Approximation via Hyperspherical Harmonics" (ICML 2022) that it follows:
 * ``hdf``        -- Algorithm 1 in its symmetric form (Remark 1): scaling, expansion,
                     QR, eigendecomposition, truncation, U and S, then matvec, solve,
                     the frozen-structure adjoint and the dense checker.
+* ``cross``      -- Algorithm 1 in its general form for two sets, K(X, Y) ~= U S V^T:
+                    joint scaling, two QRs per parity, SVD, truncation, both factors.
 
 Functions that have no independent pin are marked "parity unpinned" in their docstring.
 At present every function used by the parity tests is pinned (see tests/test_oracle_*.py).
