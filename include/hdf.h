@@ -104,6 +104,8 @@ typedef struct {
                                4 radial factors (device), 5 harmonics + U (device), 6 the
                                Gram U^T U of the first hdf_solve (device; 0 before it),
                                7 whole build */
+    int64_t n_y;            /* cross factor (hdf_build_cross): points of the second set Y, the
+                               rows of its factor V; 0 for a symmetric factor U S U^T */
 } hdf_info;
 
 /* ---------------------------------------------------------------- factorization ---- */
@@ -120,11 +122,36 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel,
                      double lengthscale, double tol, hdf_precision prec,
                      const hdf_options* opt, hdf_stream stream, hdf_factor** out);
 
+/* Build K(X, Y) ~= U S V^T for two point sets -- Algorithm 1 in its general form: X = x_dev
+ * (row-major m x d FP64, device) and Y = y_dev (row-major n x d).  Both sets are centred and
+ * scaled by one map (centre = mean of the union, R = the largest distance of a point of
+ * either set from it) so that every |x' - y'| <= 1 (Sec. 3.3); mu2 is the mean of
+ * k(x_i, y_j)^2 over cross pairs (strided 512-point samples of each set), the degree
+ * budget is tol sqrt(mu2) / 2 and the truncation budget eta tol sqrt(m n mu2) / 2.  The
+ * radial bases of X and Y are factored separately (the two QRs of Eq. svd), each block
+ * R_X Gamma_k R_Y^T is split by an SVD, and singular triples are dropped by the rule of the
+ * symmetric build with sigma in place of |lambda|.  S holds the kept singular values; U
+ * (m rows) and V (n rows) share the column order (k, s, h) of hdf_build.  The factor
+ * answers hdf_matvec (K~ V for blocks of n rows, results of m rows), hdf_matvec_transpose,
+ * hdf_factor_info (n = m, n_y = n), hdf_factor_export (U, S), hdf_factor_export_y (V) and
+ * hdf_free; hdf_solve, hdf_matvec_adjoint and hdf_matvec_noalloc return HDF_EINVAL for it.
+ * Limits, statuses and synchronisation as hdf_build. */
+hdf_status hdf_build_cross(const double* x_dev, int64_t m, const double* y_dev, int64_t n, int d,
+                           hdf_kernel kernel, double lengthscale, double tol, hdf_precision prec,
+                           const hdf_options* opt, hdf_stream stream, hdf_factor** out);
+
 /* Y = K~ V = U (S (U^T V)) (Sec. 3.6: O(n r) per column).  V_dev and Y_dev are column-major
  * n x ncols blocks (leading dimensions ldv, ldy >= n) of the factor's bulk type; they must
- * not overlap.  1 <= ncols <= 1024.  Asynchronous on the stream. */
+ * not overlap.  1 <= ncols <= 1024.  Asynchronous on the stream.  For a cross factor
+ * Y = U (S (V^T V_dev)): V_dev has n_y rows (ldv >= n_y) and Y_dev has n rows. */
 hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
                       void* Y_dev, int64_t ldy, hdf_stream stream);
+
+/* Y = K~^T V.  For a cross factor Y = V (S (U^T V_dev)): V_dev has n rows (ldv >= n), Y_dev
+ * has n_y rows (ldy >= n_y).  For a symmetric factor the same product as hdf_matvec.
+ * Otherwise as hdf_matvec. */
+hdf_status hdf_matvec_transpose(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
+                                void* Y_dev, int64_t ldy, hdf_stream stream);
 
 /* Same product as hdf_matvec, for callers that must not allocate device memory during the
  * call: code running while a stream is being captured, code whose device memory belongs to
@@ -206,6 +233,10 @@ hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void
 /* Copy U (n x rank, row-major, bulk type, packed: leading dimension rank) and S (FP64) to
  * host buffers the caller allocated.  Either pointer may be NULL.  Synchronises. */
 hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host);
+
+/* Copy the second factor V of a cross factor (n_y x rank, row-major, bulk type, packed) to a
+ * host buffer.  HDF_EINVAL for a symmetric factor.  Synchronises. */
+hdf_status hdf_factor_export_y(const hdf_factor* f, void* V_host);
 
 /* Device times (ms, CUDA events on the launching stream) of the most recent hdf_matvec on
  * this factor, first column group: ms3[0] U^T V, ms3[1] partial reduction and scaling by S,

@@ -531,6 +531,7 @@ extern "C" hdf_status hdf_matvec_adjoint(hdf_factor* f, const double* x_dev, con
     if (!f || !x_dev || !V_dev || !W_dev || !grad_x_dev || ncols < 1 || ncols > 64 || ldv < f->info.n ||
         ldw < f->info.n)
         return hdf::fail(HDF_EINVAL, "hdf_matvec_adjoint: bad argument (1 <= ncols <= 64)");
+    if (f->ypart) return hdf::fail(HDF_EINVAL, "hdf_matvec_adjoint: symmetric factors only");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (f->prec == HDF_FP64)
         return run<double>(f, x_dev, (const double*)V_dev, ldv, (const double*)W_dev, ldw, ncols, (double*)grad_x_dev,

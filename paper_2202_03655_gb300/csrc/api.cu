@@ -130,25 +130,40 @@ hdf_status hdf_factor_device(const hdf_factor* f, const void** U_dev, const void
     return HDF_OK;
 }
 
+}  // extern "C"
+
+// Packed copy of a factor's U (true columns only) to the host.
+static hdf_status export_u(const hdf_factor* f, void* U_host) {
+    const int64_t n = f->info.n, r = f->info.rank, ld = f->info.ldu;
+    if (!U_host || r == 0) return HDF_OK;
+    // U is stored with zero padding columns; gather the true columns row by row
+    std::vector<unsigned char> row((size_t)ld * f->esz * 1024);
+    unsigned char* out = static_cast<unsigned char*>(U_host);
+    for (int64_t i0 = 0; i0 < n; i0 += 1024) {
+        const int64_t cnt = std::min<int64_t>(1024, n - i0);
+        HDF_CUDA(cudaMemcpy(row.data(), f->U.as<unsigned char>() + (size_t)i0 * ld * f->esz,
+                            (size_t)cnt * ld * f->esz, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < cnt; ++i)
+            for (int64_t t = 0; t < r; ++t)
+                std::memcpy(out + ((size_t)(i0 + i) * r + t) * f->esz,
+                            row.data() + ((size_t)i * ld + f->plan.colmap[t]) * f->esz, f->esz);
+    }
+    return HDF_OK;
+}
+
+extern "C" {
+
 hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) {
     if (!f) return fail(HDF_EINVAL, "hdf_factor_export: null factor");
-    const int64_t n = f->info.n, r = f->info.rank, ld = f->info.ldu;
-    if (U_host && r > 0) {
-        // U is stored with zero padding columns; gather the true columns row by row
-        std::vector<unsigned char> row((size_t)ld * f->esz * 1024);
-        unsigned char* out = static_cast<unsigned char*>(U_host);
-        for (int64_t i0 = 0; i0 < n; i0 += 1024) {
-            const int64_t cnt = std::min<int64_t>(1024, n - i0);
-            HDF_CUDA(cudaMemcpy(row.data(), f->U.as<unsigned char>() + (size_t)i0 * ld * f->esz,
-                                (size_t)cnt * ld * f->esz, cudaMemcpyDeviceToHost));
-            for (int64_t i = 0; i < cnt; ++i)
-                for (int64_t t = 0; t < r; ++t)
-                    std::memcpy(out + ((size_t)(i0 + i) * r + t) * f->esz,
-                                row.data() + ((size_t)i * ld + f->plan.colmap[t]) * f->esz, f->esz);
-        }
-    }
-    if (S_host && r > 0) std::memcpy(S_host, f->S_host.data(), r * sizeof(double));
+    if (hdf_status e = export_u(f, U_host); e != HDF_OK) return e;
+    if (S_host && f->info.rank > 0) std::memcpy(S_host, f->S_host.data(), f->info.rank * sizeof(double));
     return HDF_OK;
+}
+
+hdf_status hdf_factor_export_y(const hdf_factor* f, void* V_host) {
+    if (!f) return fail(HDF_EINVAL, "hdf_factor_export_y: null factor");
+    if (!f->ypart) return fail(HDF_EINVAL, "hdf_factor_export_y: not a cross factor");
+    return export_u(f->ypart, V_host);
 }
 
 void hdf_free(hdf_factor* f) {
@@ -157,16 +172,21 @@ void hdf_free(hdf_factor* f) {
     // any stream still reads them, then return them to the pool on the legacy stream
     cudaDeviceSynchronize();
     f->U.st = nullptr;
+    if (f->ypart) f->ypart->U.st = nullptr;
     delete f;
 }
 
 hdf_status hdf_device_errors(const hdf_factor* f, int* flag) {
     if (!f || !flag) return fail(HDF_EINVAL, "hdf_device_errors: null argument");
     *flag = 0;
-    if (!f->dev_err.p) return HDF_OK;
     HDF_CUDA(cudaDeviceSynchronize());
-    HDF_CUDA(cudaMemcpy(flag, f->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-    HDF_CUDA(cudaMemset(f->dev_err.p, 0, sizeof(int)));
+    for (const hdf_factor* g : {f, (const hdf_factor*)f->ypart}) {
+        if (!g || !g->dev_err.p) continue;
+        int fl = 0;
+        HDF_CUDA(cudaMemcpy(&fl, g->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        HDF_CUDA(cudaMemset(g->dev_err.p, 0, sizeof(int)));
+        *flag |= fl;
+    }
     return HDF_OK;
 }
 
@@ -182,7 +202,143 @@ hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3) {
     return HDF_OK;
 }
 
+}  // extern "C"
+
 // --------------------------------------------------------------------------- build
+namespace {
+
+struct BuildOpts {
+    int p_max = 64;
+    double eta = 1.0;
+    bool use_tc = true;
+};
+
+hdf_status parse_opts(const hdf_options* opt, const char* who, BuildOpts& o) {
+    if (opt) {
+        if (opt->p_max > 0) o.p_max = opt->p_max;
+        if (opt->eta > 0) o.eta = opt->eta;
+        if (opt->flags & HDF_FLAG_CUDA_CORES) o.use_tc = false;
+    }
+    if (o.p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, std::string(who) + ": p_max > 128");
+    o.p_max -= o.p_max % 2;
+    return HDF_OK;
+}
+
+// Column sums of the row-major n x d points into sum[0..d) (two-stage reduction; synchronises).
+hdf_status point_sums(const double* x, int64_t n, int d, DevBuf& part, double* sum, cudaStream_t st) {
+    const int g = grid_for(n, 2048, 1024);
+    const int64_t chunk = (n + g - 1) / g;
+    HDF_COUNT_LAUNCH();
+    dev::k_sum_partial<<<g, 256, 0, st>>>(x, n, d, chunk, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)g * d);
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < d; ++j) {
+        double t = 0.0;
+        for (int b = 0; b < g; ++b) t += hp[(size_t)b * d + j];
+        sum[j] = t;
+    }
+    return HDF_OK;
+}
+
+// max_i |x_i - c|^2 (two-stage reduction; synchronises).
+hdf_status max_norm2(const double* x, int64_t n, int d, const dev::Center& cen, DevBuf& part, double* R2,
+                     cudaStream_t st) {
+    const int g = grid_for(n, 2048, 1024);
+    const int64_t chunk = (n + g - 1) / g;
+    HDF_COUNT_LAUNCH();
+    dev::k_maxnorm_partial<<<g, 256, 0, st>>>(x, n, d, chunk, cen, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> hp(g);
+    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, g * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    double r2 = 0.0;
+    for (int b = 0; b < g; ++b) r2 = std::max(r2, hp[b]);
+    *R2 = r2;
+    return HDF_OK;
+}
+
+// Chebyshev moments sum_i T_j(8 rho_i^2 - 1), j <= 2L+1, of one point set, FP64 partial sums
+// (double-float recurrences for FP32 factors).  Enqueued on the stream with an asynchronous
+// copy into mom; the caller synchronises before reading it.
+struct MomentJob {
+    DevBuf mpart, msum;
+    std::vector<double> mom;
+};
+
+hdf_status radial_moments(const double* x, int64_t n, int d, const dev::Center& cen, double inv2R, int L, int prec,
+                          MomentJob& job, cudaStream_t st) {
+    const int nmom = 2 * L + 2;
+    const int gmom = grid_for(n, 8192, 2 * 152);
+    const int64_t mchunk = (n + gmom - 1) / gmom;
+    HDF_CUDA(job.mpart.alloc_on(sizeof(double) * (size_t)gmom * nmom, st));
+    HDF_CUDA(job.msum.alloc_on(sizeof(double) * nmom, st));
+    HDF_COUNT_LAUNCH();
+    const size_t msm_df = sizeof(float2) * 256 * (size_t)(nmom + 1);
+    if (prec == HDF_FP32 && msm_df <= 200 * 1024) {
+        HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_moments_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)msm_df));
+        dev::k_radial_moments_df<<<gmom, 256, msm_df, st>>>(x, n, d, mchunk, cen, inv2R, nmom, job.mpart.as<double>());
+    } else {
+        const size_t msm = sizeof(double) * dev::kMomTile * nmom;
+        dev::k_radial_moments<<<gmom, 256, msm, st>>>(x, n, d, mchunk, cen, inv2R, nmom, job.mpart.as<double>());
+    }
+    HDF_CUDA(cudaGetLastError());
+    HDF_COUNT_LAUNCH();
+    dev::k_reduce_cols<<<grid_for(nmom, 256, 1 << 20), 256, 0, st>>>(job.mpart.as<double>(), gmom, nmom,
+                                                                    job.msum.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    job.mom.assign(nmom, 0.0);
+    HDF_CUDA(cudaMemcpyAsync(job.mom.data(), job.msum.p, nmom * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return HDF_OK;
+}
+
+// A new factor object with the build's metadata; npts = rows of its U.
+hdf_factor* new_factor(int64_t npts, int d, hdf_kernel kernel, double ell, double tol, hdf_precision prec,
+                       const BuildOpts& o, const dev::Center& cen, double R, double inv2R, double mu2,
+                       const DegreePlan& dp, const FactorChoice& fc) {
+    hdf_factor* f = new hdf_factor();
+    f->use_tc = o.use_tc;
+    f->kernel = kernel;
+    f->ell = ell;
+    f->tol = tol;
+    f->prec = prec;
+    f->esz = (prec == HDF_FP64) ? 8 : 4;
+    hdf_info& I = f->info;
+    I.n = npts;
+    I.d = d;
+    I.precision = prec;
+    I.p = dp.p;
+    I.L = dp.L;
+    I.reached = dp.reached ? 1 : 0;
+    I.rank = fc.rank;
+    I.nharm = fc.nH;
+    for (int j = 0; j < d; ++j) I.center[j] = cen.c[j];
+    I.radius = R;
+    I.mu2 = mu2;
+    I.cheb_tail = dp.tail;
+    I.tail_budget = dp.tail_budget;
+    I.drop_budget = dp.drop_budget;
+    I.dropped_cost = fc.dropped;
+    for (int k = 0; k <= std::min(dp.L, HDF_MAX_L); ++k) I.s_k[k] = fc.sk[k];
+    f->S_host = fc.S;
+    FactorPlan& P = f->plan;
+    P.d = d;
+    P.L = dp.L;
+    P.p_max = o.p_max;
+    for (int j = 0; j < d; ++j) P.c[j] = cen.c[j];
+    P.inv2R = inv2R;
+    for (int q = 0; q < 2; ++q) { P.nb[q] = fc.nb[q]; P.m[q] = fc.m[q]; P.Rf[q] = fc.Rf[q]; P.Qmat[q] = fc.Qmat[q]; }
+    P.Wk = fc.Wk;
+    P.sk = fc.sk;
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
 hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, double lengthscale,
                      double tol, hdf_precision prec, const hdf_options* opt, hdf_stream stream,
                      hdf_factor** out) {
@@ -190,45 +346,24 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     if (!x_dev || !out || n < 1 || d < 3 || d > HDF_MAX_D || kernel < 0 || kernel > 3 ||
         !(lengthscale > 0) || !(tol > 0 && tol < 1) || (prec != HDF_FP64 && prec != HDF_FP32))
         return fail(HDF_EINVAL, "hdf_build: bad argument (need n>=1, 3<=d<=8, l>0, 0<tol<1)");
-    int p_max = 64;
-    double eta = 1.0;
-    bool use_tc = true;
-    if (opt) {
-        if (opt->p_max > 0) p_max = opt->p_max;
-        if (opt->eta > 0) eta = opt->eta;
-        if (opt->flags & HDF_FLAG_CUDA_CORES) use_tc = false;
-    }
-    if (p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, "hdf_build: p_max > 128");
-    p_max -= p_max % 2;
+    BuildOpts o;
+    if (hdf_status e = parse_opts(opt, "hdf_build", o); e != HDF_OK) return e;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     double tph[HDF_NPHASE] = {};
     const double t_start = now_ms();
 
     // ---- A0: centre (mean) and radius (max norm), two-stage reductions
-    const int gsum = grid_for(n, 2048, 1024);
-    const int64_t chunk = (n + gsum - 1) / gsum;
     DevBuf part;
-    HDF_CUDA(part.alloc(sizeof(double) * std::max<int64_t>(gsum * d, 2048)));
-    HDF_COUNT_LAUNCH();
-    dev::k_sum_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, part.as<double>());
-    HDF_CUDA(cudaGetLastError());
-    std::vector<double> hp((size_t)gsum * d);
-    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HDF_CUDA(cudaStreamSynchronize(st));
+    HDF_CUDA(part.alloc(sizeof(double) * std::max<int64_t>(1024 * d, 2048)));
     dev::Center cen{};
+    double sum[HDF_MAX_D];
+    if (hdf_status e = point_sums(x_dev, n, d, part, sum, st); e != HDF_OK) return e;
     for (int j = 0; j < d; ++j) {
-        double s = 0.0;
-        for (int b = 0; b < gsum; ++b) s += hp[(size_t)b * d + j];
-        cen.c[j] = s / (double)n;
+        cen.c[j] = sum[j] / (double)n;
         if (!std::isfinite(cen.c[j])) return fail(HDF_ENOTFINITE, "hdf_build: non-finite point coordinates");
     }
-    HDF_COUNT_LAUNCH();
-    dev::k_maxnorm_partial<<<gsum, 256, 0, st>>>(x_dev, n, d, chunk, cen, part.as<double>());
-    HDF_CUDA(cudaGetLastError());
-    HDF_CUDA(cudaMemcpyAsync(hp.data(), part.p, gsum * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HDF_CUDA(cudaStreamSynchronize(st));
     double R2 = 0.0;
-    for (int b = 0; b < gsum; ++b) R2 = std::max(R2, hp[b]);
+    if (hdf_status e = max_norm2(x_dev, n, d, cen, part, &R2, st); e != HDF_OK) return e;
     double R = std::sqrt(R2);
     if (!std::isfinite(R)) return fail(HDF_ENOTFINITE, "hdf_build: non-finite point coordinates");
     if (R == 0.0) R = 1.0;
@@ -250,40 +385,19 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     double t0 = now_ms();
     // ---- A1: Chebyshev coefficients and degree (host)
     DegreePlan dp;
-    plan_degree(kernel, lengthscale, R, mu2, n, tol, eta, p_max, d, true, dp, false);
-    const int p = dp.p, L = dp.L;
+    plan_degree(kernel, lengthscale, R, mu2, n, tol, o.eta, o.p_max, d, true, dp, false);
+    const int L = dp.L;
 
-    // ---- A3: Chebyshev moments of the radial data (FP64 on the device) -> basis Gram matrices
-    const int nmom = 2 * L + 2;
-    const int gmom = grid_for(n, 8192, 2 * 152);
-    const int64_t mchunk = (n + gmom - 1) / gmom;
-    DevBuf mpart, msum;
-    HDF_CUDA(mpart.alloc_on(sizeof(double) * (size_t)gmom * nmom, st));
-    HDF_CUDA(msum.alloc_on(sizeof(double) * nmom, st));
-    HDF_COUNT_LAUNCH();
-    const size_t msm_df = sizeof(float2) * 256 * (size_t)(nmom + 1);
-    if (prec == HDF_FP32 && msm_df <= 200 * 1024) {        // double-float recurrences (FP32 pipe)
-        const size_t msm = msm_df;
-        HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_moments_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm));
-        dev::k_radial_moments_df<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
-    } else {
-        const size_t msm = sizeof(double) * dev::kMomTile * nmom;
-        dev::k_radial_moments<<<gmom, 256, msm, st>>>(x_dev, n, d, mchunk, cen, inv2R, nmom, mpart.as<double>());
-    }
-    HDF_CUDA(cudaGetLastError());
-    HDF_COUNT_LAUNCH();
-    dev::k_reduce_cols<<<grid_for(nmom, 256, 1 << 20), 256, 0, st>>>(mpart.as<double>(), gmom, nmom,
-                                                                    msum.as<double>());
-    HDF_CUDA(cudaGetLastError());
-    std::vector<double> mom(nmom);
-    HDF_CUDA(cudaMemcpyAsync(mom.data(), msum.p, nmom * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // ---- A3: Chebyshev moments of the radial data (device) -> basis Gram matrices
+    MomentJob mj;
+    if (hdf_status e = radial_moments(x_dev, n, d, cen, inv2R, L, prec, mj, st); e != HDF_OK) return e;
     // ---- A2 (host, while the device sums the moments): radial cores of each degree
     radial_cores(dp.a.data(), dp.p, d, dp.cores, true);
     tph[1] = now_ms() - t0;
     t0 = now_ms();
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<double> gram;
-    gram_from_moments(mom, L, gram);
+    gram_from_moments(mj.mom, L, gram);
     tph[2] = now_ms() - t0;
     t0 = now_ms();
 
@@ -291,46 +405,11 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     FactorChoice fc;
     plan_factor(gram, L, d, dp.cores, dp.drop_budget, true, fc);
 
-    hdf_factor* f = new hdf_factor();
-    f->use_tc = use_tc;
-    f->kernel = kernel;
-    f->ell = lengthscale;
-    f->tol = tol;
-    f->prec = prec;
-    f->esz = (prec == HDF_FP64) ? 8 : 4;
+    hdf_factor* f = new_factor(n, d, kernel, lengthscale, tol, prec, o, cen, R, inv2R, mu2, dp, fc);
     hdf_info& I = f->info;
-    I.n = n;
-    I.d = d;
-    I.precision = prec;
-    I.p = p;
-    I.L = L;
-    I.reached = dp.reached ? 1 : 0;
-    I.rank = fc.rank;
-    I.nharm = fc.nH;
-    for (int j = 0; j < d; ++j) I.center[j] = cen.c[j];
-    I.radius = R;
-    I.mu2 = mu2;
-    I.cheb_tail = dp.tail;
-    I.tail_budget = dp.tail_budget;
-    I.drop_budget = dp.drop_budget;
-    I.dropped_cost = fc.dropped;
     I.err_bound = ((double)n * dp.tail + fc.dropped) / ((double)n * std::sqrt(mu2));
-    for (int k = 0; k <= std::min(L, HDF_MAX_L); ++k) I.s_k[k] = fc.sk[k];
-    f->S_host = fc.S;
-
     tph[3] = now_ms() - t0;
     for (int q = 0; q < 4; ++q) I.t_ms[q] = tph[q];
-    {
-        FactorPlan& P = f->plan;
-        P.d = d;
-        P.L = L;
-        P.p_max = p_max;
-        for (int j = 0; j < d; ++j) P.c[j] = cen.c[j];
-        P.inv2R = inv2R;
-        for (int q = 0; q < 2; ++q) { P.nb[q] = fc.nb[q]; P.m[q] = fc.m[q]; P.Rf[q] = fc.Rf[q]; P.Qmat[q] = fc.Qmat[q]; }
-        P.Wk = fc.Wk;
-        P.sk = fc.sk;
-    }
     hdf_status st_dev = (prec == HDF_FP64)
         ? build_device<double>(f, x_dev, n, d, cen, inv2R, dp, fc, st)
         : build_device<float>(f, x_dev, n, d, cen, inv2R, dp, fc, st);
@@ -339,6 +418,113 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     *out = f;
     if (!dp.reached) {
         g_err = "hdf_build: tolerance not reached at p_max; factor built at the cap";
+        return HDF_ETOL_UNREACHABLE;
+    }
+    return HDF_OK;
+}
+
+hdf_status hdf_build_cross(const double* x_dev, int64_t m, const double* y_dev, int64_t n, int d,
+                           hdf_kernel kernel, double lengthscale, double tol, hdf_precision prec,
+                           const hdf_options* opt, hdf_stream stream, hdf_factor** out) {
+    if (out) *out = nullptr;
+    if (!x_dev || !y_dev || !out || m < 1 || n < 1 || d < 3 || d > HDF_MAX_D || kernel < 0 || kernel > 3 ||
+        !(lengthscale > 0) || !(tol > 0 && tol < 1) || (prec != HDF_FP64 && prec != HDF_FP32))
+        return fail(HDF_EINVAL, "hdf_build_cross: bad argument (need m,n>=1, 3<=d<=8, l>0, 0<tol<1)");
+    BuildOpts o;
+    if (hdf_status e = parse_opts(opt, "hdf_build_cross", o); e != HDF_OK) return e;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double tph[HDF_NPHASE] = {};
+    const double t_start = now_ms();
+
+    // ---- A0 for both sets with one map: centre = mean of the union, R = max distance from it
+    DevBuf part;
+    HDF_CUDA(part.alloc(sizeof(double) * std::max<int64_t>(1024 * d, 2048)));
+    double sx[HDF_MAX_D], sy[HDF_MAX_D];
+    if (hdf_status e = point_sums(x_dev, m, d, part, sx, st); e != HDF_OK) return e;
+    if (hdf_status e = point_sums(y_dev, n, d, part, sy, st); e != HDF_OK) return e;
+    dev::Center cen{};
+    for (int j = 0; j < d; ++j) {
+        cen.c[j] = (sx[j] + sy[j]) / ((double)m + (double)n);
+        if (!std::isfinite(cen.c[j])) return fail(HDF_ENOTFINITE, "hdf_build_cross: non-finite point coordinates");
+    }
+    double R2x = 0.0, R2y = 0.0;
+    if (hdf_status e = max_norm2(x_dev, m, d, cen, part, &R2x, st); e != HDF_OK) return e;
+    if (hdf_status e = max_norm2(y_dev, n, d, cen, part, &R2y, st); e != HDF_OK) return e;
+    double R = std::sqrt(std::max(R2x, R2y));
+    if (!std::isfinite(R)) return fail(HDF_ENOTFINITE, "hdf_build_cross: non-finite point coordinates");
+    if (R == 0.0) R = 1.0;
+    const double inv2R = 1.0 / (2.0 * R);
+
+    // ---- mean-square kernel value over cross pairs of the strided subsamples
+    const int mx = (int)std::min<int64_t>(m, kMu2Sample), my = (int)std::min<int64_t>(n, kMu2Sample);
+    HDF_COUNT_LAUNCH();
+    dev::k_mu2_cross<<<mx, 256, 0, st>>>(x_dev, m, mx, y_dev, n, my, d, kernel, lengthscale, part.as<double>());
+    HDF_CUDA(cudaGetLastError());
+    std::vector<double> mu_part(mx);
+    HDF_CUDA(cudaMemcpyAsync(mu_part.data(), part.p, mx * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HDF_CUDA(cudaStreamSynchronize(st));
+    double mu2 = 0.0;
+    for (int t = 0; t < mx; ++t) mu2 += mu_part[t];
+    mu2 /= (double)mx * (double)my;
+
+    tph[0] = now_ms() - t_start;
+    double t0 = now_ms();
+    // ---- A1: coefficients and degree; the truncation budget is eta tol |K_XY|_F / 2 with
+    //      |K_XY|_F = sqrt(m n mu2)
+    DegreePlan dp;
+    plan_degree(kernel, lengthscale, R, mu2, m, tol, o.eta, o.p_max, d, true, dp, false);
+    dp.drop_budget = 0.5 * o.eta * tol * std::sqrt((double)m * (double)n) * std::sqrt(mu2);
+    const int L = dp.L;
+
+    // ---- A3: radial moments of both sets (device) while the host computes the cores
+    MomentJob jx, jy;
+    if (hdf_status e = radial_moments(x_dev, m, d, cen, inv2R, L, prec, jx, st); e != HDF_OK) return e;
+    if (hdf_status e = radial_moments(y_dev, n, d, cen, inv2R, L, prec, jy, st); e != HDF_OK) return e;
+    radial_cores(dp.a.data(), dp.p, d, dp.cores, true);
+    tph[1] = now_ms() - t0;
+    t0 = now_ms();
+    HDF_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> gx, gy;
+    gram_from_moments(jx.mom, L, gx);
+    gram_from_moments(jy.mom, L, gy);
+    tph[2] = now_ms() - t0;
+    t0 = now_ms();
+
+    // ---- A3-A4 (host): both basis factors, per-degree SVDs, truncation
+    FactorChoice fx, fy;
+    plan_factor_cross(gx, gy, L, d, dp.cores, dp.drop_budget, true, fx, fy);
+
+    hdf_factor* f = new_factor(m, d, kernel, lengthscale, tol, prec, o, cen, R, inv2R, mu2, dp, fx);
+    f->ypart = new_factor(n, d, kernel, lengthscale, tol, prec, o, cen, R, inv2R, mu2, dp, fy);
+    const double nrm = std::sqrt((double)m * (double)n);
+    for (hdf_factor* g : {f, f->ypart}) {
+        g->info.n_y = n;
+        g->info.err_bound = (nrm * dp.tail + fx.dropped) / (nrm * std::sqrt(mu2));
+    }
+    f->ypart->info.n = n;
+    tph[3] = now_ms() - t0;
+    hdf_info& I = f->info;
+    for (int q = 0; q < 4; ++q) I.t_ms[q] = tph[q];
+    hdf_status st_dev = (prec == HDF_FP64)
+        ? build_device<double>(f, x_dev, m, d, cen, inv2R, dp, fx, st)
+        : build_device<float>(f, x_dev, m, d, cen, inv2R, dp, fx, st);
+    if (st_dev == HDF_OK) {
+        const float tx4 = (float)I.t_ms[4], tx5 = (float)I.t_ms[5];
+        st_dev = (prec == HDF_FP64)
+            ? build_device<double>(f->ypart, y_dev, n, d, cen, inv2R, dp, fy, st)
+            : build_device<float>(f->ypart, y_dev, n, d, cen, inv2R, dp, fy, st);
+        I.t_ms[4] = tx4 + f->ypart->info.t_ms[4];           // both sides' radial factors and U
+        I.t_ms[5] = tx5 + f->ypart->info.t_ms[5];
+    }
+    if (st_dev != HDF_OK) { delete f; return st_dev; }
+    if (f->info.ldu != f->ypart->info.ldu) {
+        delete f;
+        return fail(HDF_ECUDA, "hdf_build_cross: the two factors disagree on the padded width");
+    }
+    I.t_ms[HDF_NPHASE - 1] = now_ms() - t_start;
+    *out = f;
+    if (!dp.reached) {
+        g_err = "hdf_build_cross: tolerance not reached at p_max; factor built at the cap";
         return HDF_ETOL_UNREACHABLE;
     }
     return HDF_OK;
@@ -387,11 +573,17 @@ static int utv_chunks(int64_t n, int64_t r, int cg) {
 constexpr int kMaxGroup = 64;
 
 template <typename T>
-static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy,
-                           const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
+// Y = alpha U_f (S_scale .* (U_in^T V)) + beta B, where U_in is the factor of fin (rows of V)
+// and U_f that of f (rows of Y): fin = f for K~ V of a symmetric factor; for a cross factor
+// K(X, Y) ~= U S V^T, (f, fin) = (X side, Y side) gives K~ V and the reverse gives K~^T V.
+// Both factors have the same columns.
+static hdf_status matvec_t(const hdf_factor* f, const hdf_factor* fin, const T* V, int64_t ldv, int ncols, T* Y,
+                           int64_t ldy, const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
     // the GEMMs run over all ldu columns of U; padding columns are zero and carry S = 0
     const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
+    const int64_t nin = fin->info.n;
     const T* U = f->U.as<T>();
+    const T* Uin = fin->U.as<T>();
     if (r == 0) {
         for (int j = 0; j < ncols; ++j) {
             if (B) {
@@ -406,8 +598,8 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
         return HDF_OK;
     }
     const int cmax = std::min(ncols, kMaxGroup);
-    const int nchunk = utv_chunks(n, r, cmax);
-    const int64_t chunk = (n + nchunk - 1) / nchunk;
+    const int nchunk = utv_chunks(nin, r, cmax);
+    const int64_t chunk = (nin + nchunk - 1) / nchunk;
     DevBuf part, W;
     HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nchunk * cmax * r, st));
     HDF_CUDA(W.alloc_on(sizeof(T) * (size_t)r * cmax, st));
@@ -420,23 +612,23 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
         if (f->use_tc && aligned && cmax >= 9 && tc_bn(cmax) != 0) {
             int64_t tchunk = 0;
             int tch = 0;
-            tc_utv_split(n, r, &tchunk, &tch);
+            tc_utv_split(nin, r, &tchunk, &tch);
             DevBuf tpart, tw, twork;
             HDF_CUDA(tpart.alloc_on(sizeof(double) * (size_t)tch * cmax * r, st));
             HDF_CUDA(tw.alloc_on(sizeof(float) * (size_t)r * cmax, st));
-            HDF_CUDA(twork.alloc_on(sizeof(float) * tc_work_floats(n, r, cmax), st));
+            HDF_CUDA(twork.alloc_on(sizeof(float) * tc_work_floats(std::max(n, nin), r, cmax), st));
             int* err = fm->dev_err.as<int>();
             for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
                 const int cg = std::min(kMaxGroup, ncols - j0);
                 const bool tcg = cg >= 9 && (reinterpret_cast<uintptr_t>(V + j0 * ldv) % 16 == 0);
                 if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
                 if (tcg) {
-                    hdf_status s = tc_utv(reinterpret_cast<const float*>(U), f->info.ldu, n, r,
+                    hdf_status s = tc_utv(reinterpret_cast<const float*>(Uin), f->info.ldu, nin, r,
                                           reinterpret_cast<const float*>(V + j0 * ldv), ldv, cg, tchunk,
                                           tpart.as<double>(), twork.as<float>(), err, st);
                     if (s != HDF_OK) return s;
                 } else {
-                    launch_utv<T>(ct_for(cg), U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, nchunk, chunk,
+                    launch_utv<T>(ct_for(cg), Uin, f->info.ldu, nin, r, V + j0 * ldv, ldv, cg, nchunk, chunk,
                                   part.as<double>(), st);
                     HDF_CUDA(cudaGetLastError());
                 }
@@ -468,7 +660,7 @@ static hdf_status matvec_t(const hdf_factor* f, const T* V, int64_t ldv, int nco
         const int cg = std::min(kMaxGroup, ncols - j0);
         const int ct = ct_for(cg);
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
-        launch_utv<T>(ct, U, f->info.ldu, n, r, V + j0 * ldv, ldv, cg, nchunk, chunk, part.as<double>(), st);
+        launch_utv<T>(ct, Uin, f->info.ldu, nin, r, V + j0 * ldv, ldv, cg, nchunk, chunk, part.as<double>(), st);
         HDF_CUDA(cudaGetLastError());
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
         HDF_COUNT_LAUNCH();
@@ -509,16 +701,30 @@ template hdf_status utv_reduce<double>(const hdf_factor*, const double*, int64_t
                                        double*, cudaStream_t);
 }  // namespace hdf
 
+// K~ V through the output side fout and the input side fin (see matvec_t).
+static hdf_status matvec_sides(const hdf_factor* fout, const hdf_factor* fin, const void* V_dev, int64_t ldv,
+                               int ncols, void* Y_dev, int64_t ldy, cudaStream_t st, const char* who) {
+    if (!V_dev || !Y_dev || ncols < 1 || ncols > 1024 || ldv < fin->info.n || ldy < fout->info.n)
+        return fail(HDF_EINVAL, std::string(who) + ": bad argument");
+    if (fout->prec == HDF_FP64)
+        return matvec_t<double>(fout, fin, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy,
+                                fout->S.as<double>(), 1.0, nullptr, 0, 0.0, st);
+    return matvec_t<float>(fout, fin, (const float*)V_dev, ldv, ncols, (float*)Y_dev, ldy, fout->S.as<float>(),
+                           1.0f, nullptr, 0, 0.0f, st);
+}
+
 extern "C" hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols, void* Y_dev, int64_t ldy,
                       hdf_stream stream) {
-    if (!f || !V_dev || !Y_dev || ncols < 1 || ncols > 1024 || ldv < f->info.n || ldy < f->info.n)
-        return fail(HDF_EINVAL, "hdf_matvec: bad argument");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (f->prec == HDF_FP64)
-        return matvec_t<double>(f, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy, f->S.as<double>(), 1.0,
-                                nullptr, 0, 0.0, st);
-    return matvec_t<float>(f, (const float*)V_dev, ldv, ncols, (float*)Y_dev, ldy, f->S.as<float>(), 1.0f,
-                           nullptr, 0, 0.0f, st);
+    if (!f) return fail(HDF_EINVAL, "hdf_matvec: null factor");
+    return matvec_sides(f, f->ypart ? f->ypart : f, V_dev, ldv, ncols, Y_dev, ldy,
+                        reinterpret_cast<cudaStream_t>(stream), "hdf_matvec");
+}
+
+extern "C" hdf_status hdf_matvec_transpose(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
+                                           void* Y_dev, int64_t ldy, hdf_stream stream) {
+    if (!f) return fail(HDF_EINVAL, "hdf_matvec_transpose: null factor");
+    return matvec_sides(f->ypart ? f->ypart : f, f, V_dev, ldv, ncols, Y_dev, ldy,
+                        reinterpret_cast<cudaStream_t>(stream), "hdf_matvec_transpose");
 }
 
 // --------------------------------------------------------------------------- solve
@@ -713,7 +919,7 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
     HDF_CUDA(dX.alloc(sizeof(T) * (size_t)n * ncols));
     for (int it = 0; it < refine; ++it) {
         // Rb = B - lambda X - K~ X
-        s = matvec_t<T>(f, X, ldx, ncols, KX.as<T>(), n, f->S.as<T>(), (T)1, nullptr, 0, (T)0, st);
+        s = matvec_t<T>(f, f, X, ldx, ncols, KX.as<T>(), n, f->S.as<T>(), (T)1, nullptr, 0, (T)0, st);
         if (s != HDF_OK) return s;
         for (int j = 0; j < ncols; ++j)
             HDF_CUDA(cudaMemcpyAsync(Rb.as<T>() + j * n, B + j * ldb, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
@@ -740,6 +946,7 @@ extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev,
     if (!f || !B_dev || !X_dev || ncols < 1 || ncols > 1024 || !(lambda > 0) || ldb < f->info.n ||
         ldx < f->info.n || refine_steps < 0)
         return fail(HDF_EINVAL, "hdf_solve: bad argument");
+    if (f->ypart) return fail(HDF_EINVAL, "hdf_solve: a cross factor K(X, Y) has no (lambda I + K~) system");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (f->prec == HDF_FP64)
         return solve_t<double>(f, lambda, (const double*)B_dev, ldb, ncols, (double*)X_dev, ldx, refine_steps, st);

@@ -102,6 +102,27 @@ static __global__ void k_mu2_rows(const double* __restrict__ x, int64_t n, int d
     if (threadIdx.x == 0) part[t] = tot;
 }
 
+// Cross-pair version for K(X, Y): part[t] = sum_u k(|x_ix(t) - y_iy(u)|)^2 over the strided
+// subsamples ix(t) = floor(t m / mx), t < mx, of X and iy(u) = floor(u n / my), u < my, of Y.
+static __global__ void k_mu2_cross(const double* __restrict__ x, int64_t m, int mx, const double* __restrict__ y,
+                                   int64_t n, int my, int d, int kernel, double ell, double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int t = blockIdx.x;
+    const int64_t i = ((int64_t)t * m) / mx;
+    double xi[kMaxD];
+    for (int j = 0; j < d; ++j) xi[j] = x[i * d + j];
+    double acc = 0.0;
+    for (int u = threadIdx.x; u < my; u += blockDim.x) {
+        const int64_t jj = ((int64_t)u * n) / my;
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) { const double z = xi[j] - y[jj * d + j]; s += z * z; }
+        const double kv = kernel_value(kernel, sqrt(s), ell);
+        acc += kv * kv;
+    }
+    const double tot = block_sum_256(acc, sh);
+    if (threadIdx.x == 0) part[t] = tot;
+}
+
 // ----------------------------------------------------- A3: radial-basis Gram matrices
 // B0[l] = T_l(u), l <= L and B1[l] = rho T_l(u), l < L, u = 8 rho^2 - 1, rho = |x - c|/(2R).
 // part[b][q] (q < npairs) = sum_i B0[l] B0[l'] and part[b][npairs + q] = sum_i rho^2 T_l T_l'

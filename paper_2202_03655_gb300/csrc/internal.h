@@ -125,5 +125,10 @@ struct hdf_factor {
     // events around the kernels of the most recent matvec (first column group)
     cudaEvent_t mv_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool mv_recorded = false;
-    ~hdf_factor() { for (auto& e : mv_ev) if (e) cudaEventDestroy(e); }
+    // cross factor K(X, Y) ~= U S V^T: the Y side (its U is V, same columns and S); owned
+    hdf_factor* ypart = nullptr;
+    ~hdf_factor() {
+        for (auto& e : mv_ev) if (e) cudaEventDestroy(e);
+        delete ypart;
+    }
 };

@@ -125,6 +125,7 @@ extern "C" hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev,
                                          void* Y_dev, int64_t ldy, hdf_stream stream) {
     if (!f || !V_dev || !Y_dev || ncols < 1 || ncols > 1024 || ldv < f->info.n || ldy < f->info.n)
         return hdf::fail(HDF_EINVAL, "hdf_matvec_noalloc: bad argument");
+    if (f->ypart) return hdf::fail(HDF_EINVAL, "hdf_matvec_noalloc: symmetric factors only (use hdf_matvec)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (f->prec == HDF_FP64)
         return run<double>(f, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy, st);

@@ -519,70 +519,65 @@ void gram_from_moments(const std::vector<double>& m, int L, std::vector<double>&
         }
 }
 
-void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
-                 double drop_budget, bool threads, FactorChoice& out) {
-    const int nb0 = L + 1, nb1 = L;
+// Radial-basis factor of one parity from its Gram sums: B = Q R_f with R_f = D^1/2 V^T and
+// Q = B Qmat, Qmat = V D^-1/2, over the eigen-directions above 1e-13 nb lambda_max.
+static void basis_factor(const std::vector<double>& gram, int L, int par, FactorChoice& out) {
+    const int nb0 = L + 1, nb = out.nb[par];
     const int npairs = nb0 * (nb0 + 1) / 2;
-    out.nb[0] = nb0;
-    out.nb[1] = nb1;
-    for (int par = 0; par < 2; ++par) {
-        const int nb = out.nb[par];
-        out.m[par] = 0;
-        out.Rf[par].clear();
-        out.Qmat[par].clear();
-        if (nb == 0) continue;
-        std::vector<double> Gm((size_t)nb * nb), w(nb), V((size_t)nb * nb);
-        int q = 0;
-        for (int l = 0; l < nb0; ++l)
-            for (int lp = l; lp < nb0; ++lp, ++q)
-                if (l < nb && lp < nb) Gm[(size_t)l * nb + lp] = Gm[(size_t)lp * nb + l] = gram[(size_t)par * npairs + q];
-        sym_eig(nb, Gm.data(), w.data(), V.data());
-        double wmax = 0.0;
-        for (int l = 0; l < nb; ++l) wmax = std::max(wmax, w[l]);
-        const double floor_ = wmax * 1e-13 * nb;
-        std::vector<int> keep;
-        for (int l = 0; l < nb; ++l) if (w[l] > floor_) keep.push_back(l);
-        const int mk = (int)keep.size();
-        out.m[par] = mk;
-        out.Rf[par].assign((size_t)mk * nb, 0.0);
-        out.Qmat[par].assign((size_t)nb * mk, 0.0);
-        for (int o = 0; o < mk; ++o) {
-            const double sq = std::sqrt(w[keep[o]]);
-            for (int l = 0; l < nb; ++l) {
-                out.Rf[par][(size_t)o * nb + l] = sq * V[(size_t)l * nb + keep[o]];
-                out.Qmat[par][(size_t)l * mk + o] = V[(size_t)l * nb + keep[o]] / sq;
-            }
+    out.m[par] = 0;
+    out.Rf[par].clear();
+    out.Qmat[par].clear();
+    if (nb == 0) return;
+    std::vector<double> Gm((size_t)nb * nb), w(nb), V((size_t)nb * nb);
+    int q = 0;
+    for (int l = 0; l < nb0; ++l)
+        for (int lp = l; lp < nb0; ++lp, ++q)
+            if (l < nb && lp < nb) Gm[(size_t)l * nb + lp] = Gm[(size_t)lp * nb + l] = gram[(size_t)par * npairs + q];
+    sym_eig(nb, Gm.data(), w.data(), V.data());
+    double wmax = 0.0;
+    for (int l = 0; l < nb; ++l) wmax = std::max(wmax, w[l]);
+    const double floor_ = wmax * 1e-13 * nb;
+    std::vector<int> keep;
+    for (int l = 0; l < nb; ++l) if (w[l] > floor_) keep.push_back(l);
+    const int mk = (int)keep.size();
+    out.m[par] = mk;
+    out.Rf[par].assign((size_t)mk * nb, 0.0);
+    out.Qmat[par].assign((size_t)nb * mk, 0.0);
+    for (int o = 0; o < mk; ++o) {
+        const double sq = std::sqrt(w[keep[o]]);
+        for (int l = 0; l < nb; ++l) {
+            out.Rf[par][(size_t)o * nb + l] = sq * V[(size_t)l * nb + keep[o]];
+            out.Qmat[par][(size_t)l * mk + o] = V[(size_t)l * nb + keep[o]] / sq;
         }
     }
+}
+
+// T = Ra Gamma_k Rb^T (ma x mb) for basis factors Ra (ma x nb) and Rb (mb x nb).
+static void sandwich(const std::vector<double>& Ra, int ma, const std::vector<double>& Gk, int nb,
+                     const std::vector<double>& Rb, int mb, std::vector<double>& T) {
+    std::vector<double> T1((size_t)ma * nb, 0.0);
+    for (int o = 0; o < ma; ++o)
+        for (int l = 0; l < nb; ++l) {
+            double s = 0.0;
+            for (int t = 0; t < nb; ++t) s += Ra[(size_t)o * nb + t] * Gk[(size_t)t * nb + l];
+            T1[(size_t)o * nb + l] = s;
+        }
+    T.assign((size_t)ma * mb, 0.0);
+    for (int o = 0; o < ma; ++o)
+        for (int o2 = 0; o2 < mb; ++o2) {
+            double s = 0.0;
+            for (int l = 0; l < nb; ++l) s += T1[(size_t)o * nb + l] * Rb[(size_t)o2 * nb + l];
+            T[(size_t)o * mb + o2] = s;
+        }
+}
+
+// Global truncation (Sec. 3.4-3.5): item j of block k costs |lam[k][j]| |H_k| / |S^{d-1}|;
+// items are dropped in increasing (cost, k, j) order while the summed cost stays within the
+// budget.  Returns per k the kept indices by decreasing |lam| (ties by index) and the cost.
+static double select_kept(const std::vector<std::vector<double>>& lam, int d, double budget,
+                          std::vector<std::vector<int>>& kept) {
+    const int L = (int)lam.size() - 1;
     const double area = sphere_area(d);
-    std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
-    auto one = [&](int k) {
-        const int par = k % 2, nb = out.nb[par], mk = out.m[par];
-        if (mk == 0 || nb == 0) return;
-        const std::vector<double>& Gk = cores[k];
-        const std::vector<double>& Rf = out.Rf[par];
-        std::vector<double> T1((size_t)mk * nb, 0.0), Gm((size_t)mk * mk, 0.0);
-        for (int o = 0; o < mk; ++o)
-            for (int l = 0; l < nb; ++l) {
-                double s = 0.0;
-                for (int t = 0; t < nb; ++t) s += Rf[(size_t)o * nb + t] * Gk[(size_t)t * nb + l];
-                T1[(size_t)o * nb + l] = s;
-            }
-        for (int o = 0; o < mk; ++o)
-            for (int o2 = 0; o2 <= o; ++o2) {
-                double s = 0.0;
-                for (int l = 0; l < nb; ++l) s += T1[(size_t)o * nb + l] * Rf[(size_t)o2 * nb + l];
-                Gm[(size_t)o * mk + o2] = Gm[(size_t)o2 * mk + o] = s;
-            }
-        lam[k].resize(mk);
-        vec[k].resize((size_t)mk * mk);
-        sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
-    };
-    if (threads) {
-        parallel_for(L + 1, one);
-    } else {
-        for (int k = 0; k <= L; ++k) one(k);
-    }
     struct Item { double cost; int k, j; };
     std::vector<Item> items;
     for (int k = 0; k <= L; ++k) {
@@ -598,11 +593,28 @@ void plan_factor(const std::vector<double>& gram, int L, int d, const std::vecto
     for (int k = 0; k <= L; ++k) dropped[k].assign(lam[k].size(), 0);
     double acc = 0.0;
     for (const Item& it : items) {
-        if (acc + it.cost > drop_budget) break;
+        if (acc + it.cost > budget) break;
         acc += it.cost;
         dropped[it.k][it.j] = 1;
     }
-    out.dropped = acc;
+    kept.assign(L + 1, std::vector<int>());
+    for (int k = 0; k <= L; ++k) {
+        std::vector<int>& idx = kept[k];
+        for (int j = 0; j < (int)lam[k].size(); ++j) if (!dropped[k][j]) idx.push_back(j);
+        std::sort(idx.begin(), idx.end(), [&](int A, int B) {
+            const double fa = std::fabs(lam[k][A]), fb = std::fabs(lam[k][B]);
+            if (fa != fb) return fa > fb;
+            return A < B;
+        });
+    }
+    return acc;
+}
+
+// Kept columns of the per-k vectors (vec[k]: m x q row-major) into out.Wk, out.sk, out.S (lam
+// per column, repeated over the |H_k| harmonics), out.rank and out.nH.
+static void fill_choice(const std::vector<std::vector<double>>& lam, const std::vector<std::vector<double>>& vec,
+                        const std::vector<int>& qk, const std::vector<std::vector<int>>& kept, int d, int L,
+                        FactorChoice& out) {
     out.sk.assign(L + 1, 0);
     out.Wk.assign(L + 1, std::vector<double>());
     out.S.clear();
@@ -610,24 +622,147 @@ void plan_factor(const std::vector<double>& gram, int L, int d, const std::vecto
     out.nH = 0;
     for (int k = 0; k <= L; ++k) {
         const int64_t hcount = harmonic_count(k, d);
-        std::vector<int> idx;
-        for (int j = 0; j < (int)lam[k].size(); ++j) if (!dropped[k][j]) idx.push_back(j);
-        std::sort(idx.begin(), idx.end(), [&](int A, int B) {
-            const double fa = std::fabs(lam[k][A]), fb = std::fabs(lam[k][B]);
-            if (fa != fb) return fa > fb;
-            return A < B;
-        });
+        const std::vector<int>& idx = kept[k];
         out.sk[k] = (int)idx.size();
         if (out.sk[k] == 0) continue;
-        const int mk = out.m[k % 2];
+        const int mk = out.m[k % 2], q = qk[k];
         out.Wk[k].assign((size_t)mk * out.sk[k], 0.0);
         for (int s = 0; s < out.sk[k]; ++s)
-            for (int o = 0; o < mk; ++o) out.Wk[k][(size_t)o * out.sk[k] + s] = vec[k][(size_t)o * mk + idx[s]];
+            for (int o = 0; o < mk; ++o) out.Wk[k][(size_t)o * out.sk[k] + s] = vec[k][(size_t)o * q + idx[s]];
         out.rank += hcount * out.sk[k];
         out.nH += hcount;
         for (int s = 0; s < out.sk[k]; ++s)
             for (int64_t h = 0; h < hcount; ++h) out.S.push_back(lam[k][idx[s]]);
     }
+}
+
+void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
+                 double drop_budget, bool threads, FactorChoice& out) {
+    out.nb[0] = L + 1;
+    out.nb[1] = L;
+    for (int par = 0; par < 2; ++par) basis_factor(gram, L, par, out);
+    std::vector<std::vector<double>> lam(L + 1), vec(L + 1);
+    std::vector<int> qk(L + 1, 0);
+    auto one = [&](int k) {
+        const int par = k % 2, nb = out.nb[par], mk = out.m[par];
+        if (mk == 0 || nb == 0) return;
+        std::vector<double> Gm;
+        sandwich(out.Rf[par], mk, cores[k], nb, out.Rf[par], mk, Gm);
+        for (int o = 0; o < mk; ++o)                       // exact symmetry: mirror the lower triangle
+            for (int o2 = 0; o2 < o; ++o2) Gm[(size_t)o2 * mk + o] = Gm[(size_t)o * mk + o2];
+        lam[k].resize(mk);
+        vec[k].resize((size_t)mk * mk);
+        qk[k] = mk;
+        sym_eig(mk, Gm.data(), lam[k].data(), vec[k].data());
+    };
+    if (threads) {
+        parallel_for(L + 1, one);
+    } else {
+        for (int k = 0; k <= L; ++k) one(k);
+    }
+    std::vector<std::vector<int>> kept;
+    out.dropped = select_kept(lam, d, drop_budget, kept);
+    fill_choice(lam, vec, qk, kept, d, L, out);
+}
+
+// ------------------------------------------------------------------ SVD (one-sided Jacobi)
+// A = U diag(s) V^T for an m x n row-major A, q = min(m, n) triples by decreasing s: U (m x q),
+// V (n x q), row-major.  Hestenes' one-sided Jacobi method: pairs of columns of W = A are
+// rotated until all are mutually orthogonal to working precision; then s_j = |w_j|,
+// U[:, j] = w_j / s_j, and V is the product of the rotations (Golub and Van Loan, Matrix
+// Computations, Sec. 8.6.3).  A wide A is handled through its transpose.  Columns with
+// s_j = 0 leave U[:, j] = 0.
+void svd_jacobi(int m, int n, const double* A, double* U, double* s, double* V) {
+    if (m < n) {                       // A^T = V S U^T
+        std::vector<double> At((size_t)n * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) At[(size_t)j * m + i] = A[(size_t)i * n + j];
+        svd_jacobi(n, m, At.data(), V, s, U);
+        return;
+    }
+    // column-major working copies: W (m x n), Vw (n x n)
+    std::vector<double> W((size_t)m * n), Vw((size_t)n * n, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) W[(size_t)j * m + i] = A[(size_t)i * n + j];
+    for (int j = 0; j < n; ++j) Vw[(size_t)j * n + j] = 1.0;
+    const double eps = 2.220446049250313e-16;
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p + 1 < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double* wp = &W[(size_t)p * m];
+                double* wq = &W[(size_t)q * m];
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < m; ++i) { al += wp[i] * wp[i]; be += wq[i] * wq[i]; ga += wp[i] * wq[i]; }
+                if (al == 0.0 || be == 0.0) continue;
+                const double rel = std::fabs(ga) / std::sqrt(al * be);
+                if (!(rel > eps * m)) continue;
+                off = std::max(off, rel);
+                // rotation that zeroes the inner product of the two columns
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int i = 0; i < m; ++i) {
+                    const double a = wp[i], b = wq[i];
+                    wp[i] = c * a - sn * b;
+                    wq[i] = sn * a + c * b;
+                }
+                double* vp = &Vw[(size_t)p * n];
+                double* vq = &Vw[(size_t)q * n];
+                for (int i = 0; i < n; ++i) {
+                    const double a = vp[i], b = vq[i];
+                    vp[i] = c * a - sn * b;
+                    vq[i] = sn * a + c * b;
+                }
+            }
+        if (off == 0.0) break;
+    }
+    std::vector<double> nrm(n);
+    std::vector<int> order(n);
+    for (int j = 0; j < n; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t += W[(size_t)j * m + i] * W[(size_t)j * m + i];
+        nrm[j] = std::sqrt(t);
+        order[j] = j;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nrm[a] > nrm[b]; });
+    for (int o = 0; o < n; ++o) {
+        const int j = order[o];
+        s[o] = nrm[j];
+        const double inv = nrm[j] > 0.0 ? 1.0 / nrm[j] : 0.0;
+        for (int i = 0; i < m; ++i) U[(size_t)i * n + o] = W[(size_t)j * m + i] * inv;
+        for (int i = 0; i < n; ++i) V[(size_t)i * n + o] = Vw[(size_t)j * n + i];
+    }
+}
+
+void plan_factor_cross(const std::vector<double>& gram_x, const std::vector<double>& gram_y, int L, int d,
+                       const std::vector<std::vector<double>>& cores, double drop_budget, bool threads,
+                       FactorChoice& fx, FactorChoice& fy) {
+    for (FactorChoice* f : {&fx, &fy}) { f->nb[0] = L + 1; f->nb[1] = L; }
+    for (int par = 0; par < 2; ++par) { basis_factor(gram_x, L, par, fx); basis_factor(gram_y, L, par, fy); }
+    std::vector<std::vector<double>> sig(L + 1), ux(L + 1), vy(L + 1);
+    std::vector<int> qk(L + 1, 0);
+    auto one = [&](int k) {
+        const int par = k % 2, nb = fx.nb[par], mx = fx.m[par], my = fy.m[par];
+        if (mx == 0 || my == 0 || nb == 0) return;
+        std::vector<double> T;
+        sandwich(fx.Rf[par], mx, cores[k], nb, fy.Rf[par], my, T);
+        const int q = std::min(mx, my);
+        sig[k].resize(q);
+        ux[k].resize((size_t)mx * q);
+        vy[k].resize((size_t)my * q);
+        qk[k] = q;
+        svd_jacobi(mx, my, T.data(), ux[k].data(), sig[k].data(), vy[k].data());
+    };
+    if (threads) {
+        parallel_for(L + 1, one);
+    } else {
+        for (int k = 0; k <= L; ++k) one(k);
+    }
+    std::vector<std::vector<int>> kept;
+    fx.dropped = fy.dropped = select_kept(sig, d, drop_budget, kept);
+    fill_choice(sig, ux, qk, kept, d, L, fx);
+    fill_choice(sig, vy, qk, kept, d, L, fy);
 }
 
 bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, std::string& err) {

@@ -102,6 +102,18 @@ struct FactorChoice {
 void plan_factor(const std::vector<double>& gram, int L, int d, const std::vector<std::vector<double>>& cores,
                  double drop_budget, bool threads, FactorChoice& out);
 
+// A = U diag(s) V^T of an m x n row-major matrix, q = min(m, n) triples by decreasing s:
+// U (m x q), s (q), V (n x q), row-major (one-sided Jacobi).
+void svd_jacobi(int m, int n, const double* A, double* U, double* s, double* V);
+
+// A3-A4 for the cross block K(X, Y) (Algorithm 1, general form): basis factors of X and of Y
+// from their Gram sums, SVDs of R_X Gamma_k R_Y^T = W_X Sigma W_Y^T and the global truncation
+// with sigma in place of |lambda|.  fx gets W_X, fy gets W_Y; both get sigma as S, the same
+// s_k, rank and column order.
+void plan_factor_cross(const std::vector<double>& gram_x, const std::vector<double>& gram_y, int L, int d,
+                       const std::vector<std::vector<double>>& cores, double drop_budget, bool threads,
+                       FactorChoice& fx, FactorChoice& fy);
+
 // Host images of the tables the device kernels read (FP64; cast to the bulk type on upload).
 // U's columns come in blocks (k, s) of |H_k| harmonics, each block padded with zero columns
 // to a multiple of vw (16 bytes) so that every vw-wide chunk of a row holds one radial factor

@@ -34,19 +34,24 @@ class HdfInfo(ctypes.Structure):
                 ("reached", _c_int), ("rank", _c_i64), ("ldu", _c_i64), ("nharm", _c_i64),
                 ("center", _c_dbl * MAX_D), ("radius", _c_dbl), ("mu2", _c_dbl), ("cheb_tail", _c_dbl),
                 ("tail_budget", _c_dbl), ("drop_budget", _c_dbl), ("dropped_cost", _c_dbl),
-                ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1)), ("t_ms", _c_dbl * NPHASE)]
+                ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1)), ("t_ms", _c_dbl * NPHASE),
+                ("n_y", _c_i64)]
 
 
 SIGNATURES = {
     "hdf_build": (_c_int, [_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(HdfOptions),
                            _vp, ctypes.POINTER(_vp)]),
+    "hdf_build_cross": (_c_int, [_vp, _c_i64, _vp, _c_i64, _c_int, _c_int, _c_dbl, _c_dbl, _c_int,
+                                 ctypes.POINTER(HdfOptions), _vp, ctypes.POINTER(_vp)]),
     "hdf_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
+    "hdf_matvec_transpose": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_matvec_noalloc": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_solve": (_c_int, [_vp, _c_dbl, _vp, _c_i64, _c_int, _vp, _c_i64, _c_int, _vp]),
     "hdf_matvec_adjoint": (_c_int, [_vp, _vp, _vp, _c_i64, _vp, _c_i64, _c_int, _vp, _pdbl, _pdbl, _vp]),
     "hdf_factor_info": (_c_int, [_vp, ctypes.POINTER(HdfInfo)]),
     "hdf_factor_device": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "hdf_factor_export": (_c_int, [_vp, _vp, _pdbl]),
+    "hdf_factor_export_y": (_c_int, [_vp, _vp]),
     "hdf_free": (None, [_vp]),
     "hdf_device_errors": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "hdf_matvec_timings": (_c_int, [_vp, _pdbl]),
@@ -151,7 +156,8 @@ def _stream_handle(stream):
 
 
 class Factor:
-    """K ~= U diag(S) U^T held by the library (U and S in device memory)."""
+    """K ~= U diag(S) U^T held by the library (U and S in device memory), or, from
+    build_cross, K(X, Y) ~= U diag(S) V^T with n = |X| rows of U and n_y = |Y| rows of V."""
 
     def __init__(self, handle, status):
         self._h = handle
@@ -175,6 +181,15 @@ class Factor:
         return self.info.n
 
     @property
+    def n_y(self):
+        """Rows of the second factor (points of Y) of a cross factor; 0 if symmetric."""
+        return self.info.n_y
+
+    @property
+    def cross(self):
+        return self.info.n_y > 0
+
+    @property
     def rank(self):
         return self.info.rank
 
@@ -182,27 +197,43 @@ class Factor:
     def s_k(self):
         return [self.info.s_k[k] for k in range(self.info.L + 1)]
 
-    def _block(self, V):
+    def _block(self, V, rows=None):
         import torch
+        rows = self.n if rows is None else rows
         if not (V.is_cuda and V.dtype == self.dtype):
             raise ValueError(f"expected a CUDA tensor of dtype {self.dtype}")
         if V.dim() == 1:
             V = V.reshape(-1, 1)
-        if V.shape[0] != self.n:
-            raise ValueError("first dimension must be n")
+        if V.shape[0] != rows:
+            raise ValueError(f"first dimension must be {rows}")
         # column-major n x c: a (c, n) row-major tensor transposed
         Vc = V.t().contiguous()
         return Vc
 
     def matvec(self, V, stream=None):
-        """Y = K~ V for V of shape (n,) or (n, c) on the device (Sec. 3.6)."""
+        """Y = K~ V for V of shape (n,) or (n, c) on the device (Sec. 3.6).  For a cross
+        factor V has n_y rows and Y has n rows."""
         import torch
         vec = V.dim() == 1
-        Vc = self._block(V)
+        nin = self.n_y if self.cross else self.n
+        Vc = self._block(V, nin)
         c = Vc.shape[0]
-        Yc = torch.empty_like(Vc)
-        _check(lib().hdf_matvec(self._h, _vp(Vc.data_ptr()), self.n, c, _vp(Yc.data_ptr()), self.n,
+        Yc = torch.empty((c, self.n), dtype=Vc.dtype, device=Vc.device)
+        _check(lib().hdf_matvec(self._h, _vp(Vc.data_ptr()), nin, c, _vp(Yc.data_ptr()), self.n,
                                 _stream_handle(stream)))
+        Y = Yc.t()
+        return Y.reshape(-1) if vec else Y
+
+    def matvec_t(self, W, stream=None):
+        """Y = K~^T W (hdf_matvec_transpose).  For a cross factor W has n rows and Y has n_y."""
+        import torch
+        vec = W.dim() == 1
+        nout = self.n_y if self.cross else self.n
+        Wc = self._block(W, self.n)
+        c = Wc.shape[0]
+        Yc = torch.empty((c, nout), dtype=Wc.dtype, device=Wc.device)
+        _check(lib().hdf_matvec_transpose(self._h, _vp(Wc.data_ptr()), self.n, c, _vp(Yc.data_ptr()), nout,
+                                          _stream_handle(stream)))
         Y = Yc.t()
         return Y.reshape(-1) if vec else Y
 
@@ -280,6 +311,13 @@ class Factor:
         _check(lib().hdf_factor_export(self._h, _vp(U.ctypes.data), _dptr(S)))
         return U, S
 
+    def export_y(self):
+        """The second factor V of a cross factor as numpy (n_y, rank)."""
+        dt = np.float64 if self.info.precision == 0 else np.float32
+        V = np.zeros((self.n_y, self.rank), dtype=dt)
+        _check(lib().hdf_factor_export_y(self._h, _vp(V.ctypes.data)))
+        return V
+
 
 FLAG_CUDA_CORES = 1
 
@@ -299,6 +337,25 @@ def build(x, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, s
     st = lib().hdf_build(_vp(x.data_ptr()), x.shape[0], x.shape[1], KERNELS[kernel], float(lengthscale),
                          float(tol), PRECISIONS[precision], ctypes.byref(opt), _stream_handle(stream),
                          ctypes.byref(h))
+    _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
+    return Factor(h, st)
+
+
+def build_cross(x, y, kernel, lengthscale, tol, precision="fp64", p_max=None, eta=None, stream=None, flags=0):
+    """Factor K(x, y) ~= U S V^T for two point sets (torch CUDA float64, shapes (m, d), (n, d)),
+    Algorithm 1 in its general form (hdf_build_cross)."""
+    import torch
+    for t in (x, y):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+            raise ValueError("x and y must be CUDA float64 tensors of shape (m, d), (n, d)")
+    if x.shape[1] != y.shape[1]:
+        raise ValueError("x and y must have the same dimension")
+    x, y = x.contiguous(), y.contiguous()
+    opt = HdfOptions(int(p_max or 0), float(eta or 0.0), int(flags))
+    h = _vp()
+    st = lib().hdf_build_cross(_vp(x.data_ptr()), x.shape[0], _vp(y.data_ptr()), y.shape[0], x.shape[1],
+                               KERNELS[kernel], float(lengthscale), float(tol), PRECISIONS[precision],
+                               ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h))
     _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
     return Factor(h, st)
 
