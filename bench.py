@@ -23,6 +23,10 @@ Other workloads (--workload):
   batch512_gauss  the batching row: 512 ragged sets (n log-uniform in [1000, 65536]), FP32;
                   step = hdf_build_batched + hdf_batch_matvec with 8 columns per set; value =
                   points of all sets per second.
+  cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a
+                  wider Gaussian cloud, Gaussian l = 1.5, tol 1e-6, FP32; step = hdf_build_cross
+                  + K~ V (V: 16 columns over Y) + K~^T W (W: 16 columns over X); value = points
+                  of both sets per second.
 
 --impl reference times the CPU oracle (the only other implementation of this method here)
 on a bounded sample of the same workload.
@@ -49,6 +53,8 @@ TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1659, "k_tc_utv": 4.1502, "k_tc_uw": 4.0
 METRICS = {
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
+    "cross3_gauss": "cross factor-build points/s (build of K(X,Y) ~= U S V^T + 16-column K~V and K~^T W), "
+                    "FP32 bulk",
 }
 FP32_LANES_PER_SM, NSM, SM_MAX_MHZ = 128, 152, 2070.0
 
@@ -201,6 +207,26 @@ def cpu_oracle_work(args, w, x, off, ells):
     return time.perf_counter() - t
 
 
+def cross_oracle_sample(args, w):
+    """Bounded CPU sample of the cross workload: the first 4/5 of cpu_n points of X and 1/5 of Y."""
+    from paper_2202_03655_gb300 import workloads as W
+    mx, ny = max(1, (4 * args.cpu_n) // 5), max(1, args.cpu_n // 5)
+    x, y = W.cross_sets(args.workload)
+    return x[:mx], y[:ny]
+
+
+def cross_oracle_work(w, x, y, p_max):
+    """The oracle's form of one cross step on the sample; returns seconds."""
+    import numpy as np
+    from oracle import cross as ocross
+    g = np.random.default_rng(1)
+    t = time.perf_counter()
+    fo = ocross.build_xy(x, y, w["kernel"], w["ell"], w["tol"], p_max=p_max)
+    ocross.matvec_xy(fo, g.standard_normal((len(y), w["ncols"])))
+    ocross.matvec_xy_t(fo, g.standard_normal((len(x), w["ncols"])))
+    return time.perf_counter() - t
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: bounded samples of the workload, steps timed."""
     ws, rank, _ = dist()
@@ -209,6 +235,27 @@ def run_reference(args):
     import numpy as np
     from paper_2202_03655_gb300 import workloads as W
     w = workload_params(args)
+    if args.workload == "cross3_gauss":
+        x, y = cross_oracle_sample(args, w)
+        for _ in range(args.warmup):
+            cross_oracle_work(w, x, y, args.p_max)
+        ts = [cross_oracle_work(w, x, y, args.p_max) for _ in range(args.steps)]
+        tot = sum(ts)
+        ns = len(x) + len(y)
+        val = ns * args.steps / tot
+        line = {"impl": "reference", "metric": METRICS[args.workload], "value": val, "unit": "points/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "m_sample": len(x), "n_sample": len(y), "d": w["d"],
+                           "kernel": w["kernel"], "lengthscale": w["ell"], "tol": w["tol"], "ncols": w["ncols"],
+                           "p_max": args.p_max},
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"first {len(x)} points of X and {len(y)} of Y, build_xy + K~V + "
+                                           f"K~^T W ({w['ncols']} columns), FP64 numpy"},
+                "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload in ("cube4_gauss", "batch512_gauss"):
         x, off, ells = oracle_sample(args, w)
         for _ in range(args.warmup):
@@ -520,6 +567,135 @@ def bench_batch(args):
     return 0
 
 
+def bench_cross(args):
+    """Non-symmetric row: hdf_build_cross + K~ V + K~^T W."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    c, d = w["ncols"], w["d"]
+    x_np, y_np = W.cross_sets(args.workload)
+    m, n = len(x_np), len(y_np)
+    g = W.rng(w["idx"] + 100)
+    V_np = g.standard_normal((c, n)).astype(np.float32)        # column-major n x c (over Y)
+    W_np = g.standard_normal((c, m)).astype(np.float32)        # column-major m x c (over X)
+    x, y = torch.from_numpy(x_np).to(dev), torch.from_numpy(y_np).to(dev)
+    Vc, Wc = torch.from_numpy(V_np).to(dev), torch.from_numpy(W_np).to(dev)
+    Yc = torch.empty((c, m), dtype=torch.float32, device=dev)
+    Zc = torch.empty((c, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = hdf.lib()
+    t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+
+    def products(f):
+        hdf._check(lib.hdf_matvec(f._h, hdf._vp(Vc.data_ptr()), n, c, hdf._vp(Yc.data_ptr()), m,
+                                  hdf._vp(stream.cuda_stream)))
+        t1.record(stream)
+        hdf._check(lib.hdf_matvec_transpose(f._h, hdf._vp(Wc.data_ptr()), m, c, hdf._vp(Zc.data_ptr()), n,
+                                            hdf._vp(stream.cuda_stream)))
+
+    def one(keep):
+        f = hdf.build_cross(x, y, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max,
+                            stream=stream)
+        t0.record(stream)
+        products(f)
+        t2.record(stream)
+        rec = None
+        if keep:
+            t2.synchronize()
+            rec = (f.info, t0.elapsed_time(t1), t1.elapsed_time(t2), f.matvec_timings())
+        f.free()
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    value = ws * (m + n) * args.steps / (ms_total / 1e3)
+    info = recs[-1][0]
+    kv_ms = float(np.mean([r[1] for r in recs]))
+    kvt_ms = float(np.mean([r[2] for r in recs]))
+    mv = np.mean([r[3] for r in recs], axis=0)          # K~ V: U_Y^T V, reduce, U_X W
+    uw_ms = float(np.mean([r[0].t_ms[5] for r in recs]))
+    r, ldu = info.rank, info.ldu
+    nF = sum(info.s_k[k] for k in range(info.L + 1))
+    # accuracy outside the timed region: sampled rows of K~ V and K~^T W against the exact kernel
+    f = hdf.build_cross(x, y, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+    products(f)
+    torch.cuda.synchronize()
+    f.free()
+    rows = torch.from_numpy(np.sort(W.rng(7).choice(m, 256, replace=False))).to(dev)
+    cols = torch.from_numpy(np.sort(W.rng(8).choice(n, 256, replace=False))).to(dev)
+    ell = w["ell"]
+    Kr = torch.exp(-0.5 * (torch.cdist(x[rows], y) / ell) ** 2)
+    err_y = float(torch.linalg.norm(Yc[0, rows].double() - Kr @ Vc[0].double()) / torch.linalg.norm(Kr @ Vc[0].double()))
+    del Kr
+    Kc = torch.exp(-0.5 * (torch.cdist(y[cols], x) / ell) ** 2)
+    err_z = float(torch.linalg.norm(Zc[0, cols].double() - Kc @ Wc[0].double()) / torch.linalg.norm(Kc @ Wc[0].double()))
+    del Kc
+    # roofline of the dominant kernel of the step
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    kernels = {
+        "k_uwriter (X and Y sides, two launches)": (uw_ms, (m + n) * (r * 4 + d * 8 + nF * 4)),
+        "k_tc_utv (U_Y^T V)": (float(mv[0]), n * r * 4 + n * c * 4),
+        "k_tc_uw (U_X W)": (float(mv[2]), m * r * 4 + m * c * 4),
+    }
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_dom, b_dom = kernels[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": b_dom / (t_dom / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None,
+            "algorithmic_bytes": b_dom, "ms_per_launch": t_dom}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D of X, Y, V, W; build; both products; D2H of both
+    xh, yh = torch.from_numpy(x_np).pin_memory(), torch.from_numpy(y_np).pin_memory()
+    Vh, Wh = torch.from_numpy(V_np).pin_memory(), torch.from_numpy(W_np).pin_memory()
+    Yh, Zh = torch.empty_like(Yc, device="cpu").pin_memory(), torch.empty_like(Zc, device="cpu").pin_memory()
+    xd, yd = torch.empty_like(x), torch.empty_like(y)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 3))
+    b0.record(stream)
+    for _ in range(k2):
+        xd.copy_(xh, non_blocking=True); yd.copy_(yh, non_blocking=True)
+        Vc.copy_(Vh, non_blocking=True); Wc.copy_(Wh, non_blocking=True)
+        f = hdf.build_cross(xd, yd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max,
+                            stream=stream)
+        products(f)
+        Yh.copy_(Yc, non_blocking=True); Zh.copy_(Zc, non_blocking=True)
+        f.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / k2
+    e2e = {"value": ws * (m + n) / (e2e_ms / 1e3), "unit": "points/s",
+           "h2d_bytes_per_step": (m + n) * d * 8 + (m + n) * c * 4, "d2h_bytes_per_step": (m + n) * c * 4,
+           "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        xs, ys = cross_oracle_sample(args, w)
+        ts = cross_oracle_work(w, xs, ys, args.p_max)
+        cpu = {"value": (len(xs) + len(ys)) / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {len(xs)} points of X and {len(ys)} of Y, build_xy + K~V + K~^T W "
+                         f"({c} columns), FP64 numpy"}
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "m": m, "n": n, "d": d, "kernel": w["kernel"],
+                           "lengthscale": w["ell"], "tol": w["tol"], "ncols": c, "p_max": args.p_max, "p": info.p,
+                           "rank": r, "ldu": ldu, "U_bytes": (m + n) * ldu * 4, "parallelism": f"replicas{ws}",
+                           "l2": "inputs larger than L2"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"build_ms": float(np.mean([r_[0].t_ms[7] for r_ in recs])),
+                           "build_phase_ms": [float(t) for t in info.t_ms], "kv_ms": kv_ms, "kvt_ms": kvt_ms,
+                           "kernel_ms": {k: v[0] for k, v in kernels.items()},
+                           "rel_err_sampled_vs_exact": {"K~V": err_y, "K~^T W": err_z},
+                           "err_bound": info.err_bound}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -528,6 +704,8 @@ def main():
         return bench_adjoint(args)
     if args.workload == "batch512_gauss":
         return bench_batch(args)
+    if args.workload == "cross3_gauss":
+        return bench_cross(args)
     import numpy as np
     import torch
     from paper_2202_03655_gb300 import hdf, workloads as W

@@ -428,20 +428,40 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
         if (value) *value = 0.0;
         return HDF_OK;
     }
-    DevBuf ab, zd;
+    DevBuf ab, zd, vw;
     HDF_CUDA(ab.alloc(sizeof(T) * (size_t)r * ncols * 2));
-    HDF_CUDA(zd.alloc(sizeof(double) * (size_t)r * ncols * 2));
+    HDF_CUDA(zd.alloc_on(sizeof(double) * (size_t)r * ncols * 2, st));
     T* a = ab.as<T>();                         // S U^T V  (r x ncols)
     T* b = a + (size_t)r * ncols;              // S U^T W
-    double* zv = zd.as<double>();              // U^T V (FP64)
-    double* zw = zv + (size_t)r * ncols;
-    hdf_status s = hdf::utv_reduce<T>(f, V, ldv, ncols, nullptr, nullptr, zv, st);
-    if (s != HDF_OK) return s;
-    s = hdf::utv_reduce<T>(f, Wv, ldw, ncols, nullptr, nullptr, zw, st);
-    if (s != HDF_OK) return s;
-    std::vector<double> hv((size_t)r * ncols), hw((size_t)r * ncols);
-    HDF_CUDA(cudaMemcpyAsync(hv.data(), zv, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
-    HDF_CUDA(cudaMemcpyAsync(hw.data(), zw, sizeof(double) * hw.size(), cudaMemcpyDeviceToHost, st));
+    // U^T [V W] (FP64, r x 2 ncols row-major) in one pass over U when the 2 ncols columns fit
+    // one group: [V W] is gathered into an n x 2 ncols column-major block first
+    std::vector<double> hz((size_t)r * ncols * 2);
+    const int c2 = 2 * ncols;
+    if (c2 <= 64) {
+        HDF_CUDA(vw.alloc_on(sizeof(T) * (size_t)n * c2, st));
+        HDF_CUDA(cudaMemcpy2DAsync(vw.p, sizeof(T) * n, V, sizeof(T) * ldv, sizeof(T) * n, ncols,
+                                   cudaMemcpyDeviceToDevice, st));
+        HDF_CUDA(cudaMemcpy2DAsync(vw.as<T>() + (size_t)n * ncols, sizeof(T) * n, Wv, sizeof(T) * ldw, sizeof(T) * n,
+                                   ncols, cudaMemcpyDeviceToDevice, st));
+        hdf_status s = hdf::utv_reduce<T>(f, vw.as<T>(), n, c2, nullptr, nullptr, zd.as<double>(), st);
+        if (s != HDF_OK) return s;
+        HDF_CUDA(cudaMemcpyAsync(hz.data(), zd.p, sizeof(double) * hz.size(), cudaMemcpyDeviceToHost, st));
+    } else {
+        double* zv = zd.as<double>();
+        double* zw = zv + (size_t)r * ncols;
+        hdf_status s = hdf::utv_reduce<T>(f, V, ldv, ncols, nullptr, nullptr, zv, st);
+        if (s != HDF_OK) return s;
+        s = hdf::utv_reduce<T>(f, Wv, ldw, ncols, nullptr, nullptr, zw, st);
+        if (s != HDF_OK) return s;
+        std::vector<double> hv((size_t)r * ncols * 2);
+        HDF_CUDA(cudaMemcpyAsync(hv.data(), zd.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+        HDF_CUDA(cudaStreamSynchronize(st));
+        for (int64_t col = 0; col < r; ++col)          // into the [V W] row layout
+            for (int j = 0; j < ncols; ++j) {
+                hz[(size_t)col * c2 + j] = hv[(size_t)col * ncols + j];
+                hz[(size_t)col * c2 + ncols + j] = hv[(size_t)r * ncols + (size_t)col * ncols + j];
+            }
+    }
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<T> ha((size_t)r * ncols), hb((size_t)r * ncols);
     double fval = 0.0;
@@ -449,9 +469,10 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
         for (int j = 0; j < ncols; ++j) {
             const size_t q = (size_t)col * ncols + j;
             const double sc = P.Spad[col];
-            ha[q] = (T)(sc * hv[q]);
-            hb[q] = (T)(sc * hw[q]);
-            fval += hw[q] * sc * hv[q];
+            const double zv = hz[(size_t)col * c2 + j], zw = hz[(size_t)col * c2 + ncols + j];
+            ha[q] = (T)(sc * zv);
+            hb[q] = (T)(sc * zw);
+            fval += zw * sc * zv;
         }
     HDF_CUDA(cudaMemcpyAsync(a, ha.data(), sizeof(T) * ha.size(), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(b, hb.data(), sizeof(T) * hb.size(), cudaMemcpyHostToDevice, st));
@@ -511,9 +532,9 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
                         double acc = 0.0;
                         for (int t_ = 0; t_ < sk; ++t_) {
                             const int64_t ct = P.cbase[k] + (int64_t)t_ * dimp + h;
-                            acc += dS[(size_t)s_ * sk + t_] * hv[(size_t)ct * ncols + j];
+                            acc += dS[(size_t)s_ * sk + t_] * hz[(size_t)ct * c2 + j];
                         }
-                        gl += hw[(size_t)cs * ncols + j] * acc;
+                        gl += hz[(size_t)cs * c2 + ncols + j] * acc;
                     }
         }
         *grad_l = gl;

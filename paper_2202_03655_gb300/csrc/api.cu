@@ -572,6 +572,77 @@ static int utv_chunks(int64_t n, int64_t r, int cg) {
 
 constexpr int kMaxGroup = 64;
 
+// Per-column-group products U_in^T V and U W.  FP32 factors run both on the tensor cores
+// (tcgen05, 3xTF32 with FP32 sums per row chunk) whenever the factor allows it (not disabled
+// by HDF_FLAG_CUDA_CORES, 16-byte aligned rows, at least 256 rows and 64 columns); below that
+// and for FP64 factors the CUDA-core tile kernels run.  One GroupWork serves every group of up
+// to cmax columns of one call; its buffers come from the stream-ordered pool.
+struct GroupWork {
+    bool tc = false;
+    int nchunk = 0, tch = 0;
+    int64_t chunk = 0, tchunk = 0;
+    DevBuf part;             // partial sums: nchunk (or tch) x cmax x r, FP64
+    DevBuf twork;            // tensor-core operand splits (V hi/lo, W hi/lo)
+};
+
+static bool tc_usable(const hdf_factor* f, int64_t n, int64_t r) {
+    return f->prec == HDF_FP32 && f->use_tc && n >= 256 && r >= 64 &&
+           reinterpret_cast<uintptr_t>(f->U.p) % 16 == 0 && f->info.ldu % 4 == 0;
+}
+
+static hdf_status group_setup(const hdf_factor* fin, const hdf_factor* fout, int64_t r, int cmax, GroupWork& g,
+                              cudaStream_t st) {
+    const int64_t nin = fin->info.n, nout = fout->info.n;
+    g.tc = tc_usable(fin, nin, r) && tc_usable(fout, nout, r);
+    if (g.tc) {
+        tc_utv_split(nin, r, &g.tchunk, &g.tch);
+        HDF_CUDA(g.part.alloc_on(sizeof(double) * (size_t)g.tch * cmax * r, st));
+        HDF_CUDA(g.twork.alloc_on(sizeof(float) * tc_work_floats(std::max(nin, nout), r, cmax), st));
+    } else {
+        g.nchunk = utv_chunks(nin, r, cmax);
+        g.chunk = (nin + g.nchunk - 1) / g.nchunk;
+        HDF_CUDA(g.part.alloc_on(sizeof(double) * (size_t)g.nchunk * cmax * r, st));
+    }
+    return HDF_OK;
+}
+
+// Partial sums of U_in^T V for cg columns into g.part (*np slices of cg x r).
+template <typename T>
+static hdf_status group_utv(const hdf_factor* fin, int64_t r, const T* V, int64_t ldv, int cg, GroupWork& g,
+                            int* np, cudaStream_t st) {
+    const int64_t nin = fin->info.n;
+    if constexpr (sizeof(T) == 4) {
+        if (g.tc) {
+            *np = g.tch;
+            return tc_utv(reinterpret_cast<const float*>(fin->U.p), fin->info.ldu, nin, r,
+                          reinterpret_cast<const float*>(V), ldv, cg, g.tchunk, g.part.as<double>(),
+                          g.twork.as<float>(), fin->dev_err.as<int>(), st);
+        }
+    }
+    *np = g.nchunk;
+    launch_utv<T>(ct_for(cg), fin->U.as<T>(), fin->info.ldu, nin, r, V, ldv, cg, g.nchunk, g.chunk,
+                  g.part.as<double>(), st);
+    HDF_CUDA(cudaGetLastError());
+    return HDF_OK;
+}
+
+// Y = alpha U_out W + beta B for cg columns (W: r x cg row-major, bulk type).
+template <typename T>
+static hdf_status group_uw(const hdf_factor* fout, int64_t r, const T* W, int cg, T alpha, const T* B, int64_t ldb,
+                           T beta, T* Y, int64_t ldy, GroupWork& g, cudaStream_t st) {
+    const int64_t nout = fout->info.n;
+    if constexpr (sizeof(T) == 4) {
+        if (g.tc)
+            return tc_uw(reinterpret_cast<const float*>(fout->U.p), fout->info.ldu, nout, r,
+                         reinterpret_cast<const float*>(W), cg, (float)alpha, reinterpret_cast<const float*>(B), ldb,
+                         (float)beta, reinterpret_cast<float*>(Y), ldy, g.twork.as<float>(), fout->dev_err.as<int>(),
+                         st);
+    }
+    launch_uw<T>(ct_for(cg), fout->U.as<T>(), fout->info.ldu, nout, r, W, cg, alpha, B, ldb, beta, Y, ldy, st);
+    HDF_CUDA(cudaGetLastError());
+    return HDF_OK;
+}
+
 template <typename T>
 // Y = alpha U_f (S_scale .* (U_in^T V)) + beta B, where U_in is the factor of fin (rows of V)
 // and U_f that of f (rows of Y): fin = f for K~ V of a symmetric factor; for a cross factor
@@ -581,9 +652,6 @@ static hdf_status matvec_t(const hdf_factor* f, const hdf_factor* fin, const T* 
                            int64_t ldy, const T* S_scale, T alpha, const T* B, int64_t ldb, T beta, cudaStream_t st) {
     // the GEMMs run over all ldu columns of U; padding columns are zero and carry S = 0
     const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
-    const int64_t nin = fin->info.n;
-    const T* U = f->U.as<T>();
-    const T* Uin = fin->U.as<T>();
     if (r == 0) {
         for (int j = 0; j < ncols; ++j) {
             if (B) {
@@ -598,81 +666,30 @@ static hdf_status matvec_t(const hdf_factor* f, const hdf_factor* fin, const T* 
         return HDF_OK;
     }
     const int cmax = std::min(ncols, kMaxGroup);
-    const int nchunk = utv_chunks(nin, r, cmax);
-    const int64_t chunk = (nin + nchunk - 1) / nchunk;
-    DevBuf part, W;
-    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nchunk * cmax * r, st));
+    GroupWork g;
+    if (hdf_status e = group_setup(fin, f, r, cmax, g, st); e != HDF_OK) return e;
+    DevBuf W;
     HDF_CUDA(W.alloc_on(sizeof(T) * (size_t)r * cmax, st));
     hdf_factor* fm = const_cast<hdf_factor*>(f);
     const bool rec = fm->mv_ev[0] != nullptr;
-    // FP32 factors: column groups of 9..64 go to the tensor cores when the V block can be
-    // described to TMA (16-byte aligned base and leading dimension)
-    if constexpr (sizeof(T) == 4) {
-        const bool aligned = (reinterpret_cast<uintptr_t>(V) % 16 == 0) && (ldv % 4 == 0);
-        if (f->use_tc && aligned && cmax >= 9 && tc_bn(cmax) != 0) {
-            int64_t tchunk = 0;
-            int tch = 0;
-            tc_utv_split(nin, r, &tchunk, &tch);
-            DevBuf tpart, tw, twork;
-            HDF_CUDA(tpart.alloc_on(sizeof(double) * (size_t)tch * cmax * r, st));
-            HDF_CUDA(tw.alloc_on(sizeof(float) * (size_t)r * cmax, st));
-            HDF_CUDA(twork.alloc_on(sizeof(float) * tc_work_floats(std::max(n, nin), r, cmax), st));
-            int* err = fm->dev_err.as<int>();
-            for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
-                const int cg = std::min(kMaxGroup, ncols - j0);
-                const bool tcg = cg >= 9 && (reinterpret_cast<uintptr_t>(V + j0 * ldv) % 16 == 0);
-                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
-                if (tcg) {
-                    hdf_status s = tc_utv(reinterpret_cast<const float*>(Uin), f->info.ldu, nin, r,
-                                          reinterpret_cast<const float*>(V + j0 * ldv), ldv, cg, tchunk,
-                                          tpart.as<double>(), twork.as<float>(), err, st);
-                    if (s != HDF_OK) return s;
-                } else {
-                    launch_utv<T>(ct_for(cg), Uin, f->info.ldu, nin, r, V + j0 * ldv, ldv, cg, nchunk, chunk,
-                                  part.as<double>(), st);
-                    HDF_CUDA(cudaGetLastError());
-                }
-                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
-                HDF_COUNT_LAUNCH();
-                dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(
-                    tcg ? tpart.as<double>() : part.as<double>(), tcg ? tch : nchunk, r, cg, S_scale,
-                    tcg ? reinterpret_cast<T*>(tw.p) : W.as<T>(), nullptr);
-                HDF_CUDA(cudaGetLastError());
-                if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
-                if (tcg) {
-                    hdf_status s = tc_uw(reinterpret_cast<const float*>(U), f->info.ldu, n, r, tw.as<float>(), cg,
-                                         (float)alpha, reinterpret_cast<const float*>(B ? B + j0 * ldb : nullptr), ldb,
-                                         (float)beta, reinterpret_cast<float*>(Y + j0 * ldy), ldy, twork.as<float>(),
-                                         err, st);
-                    if (s != HDF_OK) return s;
-                } else {
-                    launch_uw<T>(ct_for(cg), U, f->info.ldu, n, r, W.as<T>(), cg, alpha,
-                                 B ? B + j0 * ldb : nullptr, ldb, beta, Y + j0 * ldy, ldy, st);
-                    HDF_CUDA(cudaGetLastError());
-                }
-                if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
-            }
-            // the work buffers go back to the pool in stream order on return
-            return HDF_OK;
-        }
-    }
     for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
         const int cg = std::min(kMaxGroup, ncols - j0);
-        const int ct = ct_for(cg);
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
-        launch_utv<T>(ct, Uin, f->info.ldu, nin, r, V + j0 * ldv, ldv, cg, nchunk, chunk, part.as<double>(), st);
-        HDF_CUDA(cudaGetLastError());
+        int np = 0;
+        if (hdf_status e = group_utv<T>(fin, r, V + j0 * ldv, ldv, cg, g, &np, st); e != HDF_OK) return e;
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
         HDF_COUNT_LAUNCH();
-        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg,
                                                                                S_scale, W.as<T>(), nullptr);
         HDF_CUDA(cudaGetLastError());
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
-        launch_uw<T>(ct, U, f->info.ldu, n, r, W.as<T>(), cg, alpha, B ? B + j0 * ldb : nullptr, ldb, beta,
-                     Y + j0 * ldy, ldy, st);
-        HDF_CUDA(cudaGetLastError());
+        if (hdf_status e = group_uw<T>(f, r, W.as<T>(), cg, alpha, B ? B + j0 * ldb : nullptr, ldb, beta,
+                                       Y + j0 * ldy, ldy, g, st);
+            e != HDF_OK)
+            return e;
         if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
     }
+    // the work buffers go back to the pool in stream order on return
     return HDF_OK;
 }
 
@@ -680,20 +697,17 @@ namespace hdf {
 template <typename T>
 hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const T* S_scale, T* W, double* Wd,
                       cudaStream_t st) {
-    const int64_t n = f->info.n, r = f->info.ldu;      // padded width (rows of W)
+    const int64_t r = f->info.ldu;      // padded width (rows of W)
     if (c < 1 || c > kMaxGroup) return fail(HDF_EINVAL, "utv_reduce: 1 <= c <= 64");
-    const int nchunk = utv_chunks(n, r, c);
-    const int64_t chunk = (n + nchunk - 1) / nchunk;
-    DevBuf part;
-    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * c * r));
-    launch_utv<T>(ct_for(c), f->U.as<T>(), f->info.ldu, n, r, V, ldv, c, nchunk, chunk, part.as<double>(), st);
-    HDF_CUDA(cudaGetLastError());
+    GroupWork g;
+    if (hdf_status e = group_setup(f, f, r, c, g, st); e != HDF_OK) return e;
+    int np = 0;
+    if (hdf_status e = group_utv<T>(f, r, V, ldv, c, g, &np, st); e != HDF_OK) return e;
     HDF_COUNT_LAUNCH();
-    dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, c, S_scale,
+    dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, c, S_scale,
                                                                           W, Wd);
     HDF_CUDA(cudaGetLastError());
-    HDF_CUDA(cudaStreamSynchronize(st));     // part is freed on return
-    return HDF_OK;
+    return HDF_OK;      // the partial sums return to the pool in stream order
 }
 template hdf_status utv_reduce<float>(const hdf_factor*, const float*, int64_t, int, const float*, float*, double*,
                                       cudaStream_t);
@@ -818,7 +832,6 @@ template <typename T>
 static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int64_t ldb, int ncols, T* Xout,
                                  int64_t ldx, cudaStream_t st) {
     const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
-    const T* U = f->U.as<T>();
     if (r == 0) {
         HDF_COUNT_LAUNCH();
         dev::k_axpby<T><<<grid_for(n * ncols, 256, 1 << 30), 256, 0, st>>>(n, ncols, (T)(1.0 / lambda), Bin, ldb,
@@ -827,21 +840,19 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
         return HDF_OK;
     }
     const int cmax = std::min(ncols, kMaxGroup);
-    const int nchunk = utv_chunks(n, r, cmax);
-    const int64_t chunk = (n + nchunk - 1) / nchunk;
-    DevBuf part, Wd, Wt;
-    HDF_CUDA(part.alloc(sizeof(double) * (size_t)nchunk * cmax * r));
-    HDF_CUDA(Wd.alloc(sizeof(double) * (size_t)r * cmax));
-    HDF_CUDA(Wt.alloc(sizeof(T) * (size_t)r * cmax));
+    GroupWork g;
+    if (hdf_status e = group_setup(f, f, r, cmax, g, st); e != HDF_OK) return e;
+    DevBuf Wd, Wt;
+    HDF_CUDA(Wd.alloc_on(sizeof(double) * (size_t)r * cmax, st));
+    HDF_CUDA(Wt.alloc_on(sizeof(T) * (size_t)r * cmax, st));
     std::vector<double> z((size_t)r * cmax), col(r);
     std::vector<T> y((size_t)r * cmax);
     for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
         const int cg = std::min(kMaxGroup, ncols - j0);
-        const int ct = ct_for(cg);
-        launch_utv<T>(ct, U, f->info.ldu, n, r, Bin + j0 * ldb, ldb, cg, nchunk, chunk, part.as<double>(), st);
-        HDF_CUDA(cudaGetLastError());
+        int np = 0;
+        if (hdf_status e = group_utv<T>(f, r, Bin + j0 * ldb, ldb, cg, g, &np, st); e != HDF_OK) return e;
         HDF_COUNT_LAUNCH();
-        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), nchunk, r, cg,
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg,
                                                                                nullptr, nullptr, Wd.as<double>());
         HDF_CUDA(cudaGetLastError());
         HDF_CUDA(cudaMemcpyAsync(z.data(), Wd.p, sizeof(double) * r * cg, cudaMemcpyDeviceToHost, st));
@@ -852,10 +863,11 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
             for (int64_t a = 0; a < r; ++a) y[a * cg + j] = (T)col[a];
         }
         HDF_CUDA(cudaMemcpyAsync(Wt.p, y.data(), sizeof(T) * r * cg, cudaMemcpyHostToDevice, st));
-        launch_uw<T>(ct, U, f->info.ldu, n, r, Wt.as<T>(), cg, (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
-                     (T)(1.0 / lambda), Xout + j0 * ldx, ldx, st);
-        HDF_CUDA(cudaGetLastError());
-        HDF_CUDA(cudaStreamSynchronize(st));
+        if (hdf_status e = group_uw<T>(f, r, Wt.as<T>(), cg, (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
+                                       (T)(1.0 / lambda), Xout + j0 * ldx, ldx, g, st);
+            e != HDF_OK)
+            return e;
+        HDF_CUDA(cudaStreamSynchronize(st));      // y is reused by the next group
     }
     return HDF_OK;
 }

@@ -18,6 +18,10 @@ that to the point distributions the factorization is expected to meet):
   4  batch512_gauss   512 sets, n log-uniform in [1000, 65536], d=3, uniform in a ball of
                       radius U[0.5, 2], Gaussian l ~ U[0.3, 1.5], tol 1e-6, V with 8 columns
   5  fig1_cauchy      Sec. 4.1 Fig. 1 shape: N(0,I) points scaled to max norm 1, Cauchy l=1
+  6  cross3_gauss     the non-symmetric row K(X, Y): X = 1,000,000 points of the 8-component
+                      mixture of workload 1, Y = 250,000 points of N(0, 1.2^2 I) (a wider
+                      cloud around them: off-diagonal and cross-kernel blocks, Sec. 2 and 5),
+                      Gaussian l=1.5, tol 1e-6, V and W with 16 N(0,1) columns
 """
 import numpy as np
 
@@ -86,7 +90,20 @@ WORKLOADS = {
     "normal5_cauchy": dict(idx=2, n=4_000_000, d=5, kernel="cauchy", ell=2.0, tol=1e-4, ncols=16),
     "cube4_gauss": dict(idx=3, n=500_000, d=4, kernel="gaussian", ell=0.8, tol=1e-6, ncols=1),
     "batch512_gauss": dict(idx=4, nsets=512, d=3, kernel="gaussian", tol=1e-6, ncols=8),
+    "cross3_gauss": dict(idx=6, n=1_000_000, n_y=250_000, d=3, kernel="gaussian", ell=1.5, tol=1e-6,
+                         ncols=16),
 }
+
+
+def cross_sets(name="cross3_gauss", m=None, n=None):
+    """(X, Y) of a two-set workload: X from the mixture, Y from N(0, 1.2^2 I)."""
+    w = WORKLOADS[name]
+    m = w["n"] if m is None else int(m)
+    n = w["n_y"] if n is None else int(n)
+    g = rng(w["idx"])
+    x = gaussian_mixture(g, m, w["d"])
+    y = g.standard_normal((n, w["d"])) * 1.2
+    return x, y
 
 
 def points(name, n=None, idx=None):

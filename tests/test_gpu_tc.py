@@ -28,7 +28,7 @@ def _factors(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("c", [9, 16, 37, 64, 70])
+@pytest.mark.parametrize("c", [1, 2, 5, 8, 9, 16, 37, 64, 70])
 def test_tensor_core_matvec(case, c):
     x, f_tc, f_cc, U, S = _factors(case)
     n = x.shape[0]
