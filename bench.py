@@ -23,6 +23,14 @@ Other workloads (--workload):
   batch512_gauss  the batching row: 512 ragged sets (n log-uniform in [1000, 65536]), FP32;
                   step = hdf_build_batched + hdf_batch_matvec with 8 columns per set; value =
                   points of all sets per second.
+  fig1_cauchy     the time-vs-n row (Fig. 1): N(0,I) points scaled to max norm 1, Cauchy l = 1,
+                  tol 1e-3, FP32; step = one hdf_build at every (d, n), d in {3,4,5,6}, n in
+                  {1e4, 1e5, 1e6, 1e7}; value = points of the sweep per second; detail holds
+                  the build time of each (d, n) and the slope of log time against log n.
+  fig3_rank5      the error-vs-rank row (Fig. 3, HDF only): 5,000 points in d = 5, four kernels
+                  (sigma = 1) and ten tolerances, FP64; step = one hdf_build per (kernel, tol);
+                  detail holds rank and the achieved |K - K~|_F / |K|_F of each against the
+                  dense kernel matrix.
   cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a
                   wider Gaussian cloud, Gaussian l = 1.5, tol 1e-6, FP32; step = hdf_build_cross
                   + K~ V (V: 16 columns over Y) + K~^T W (W: 16 columns over X); value = points
@@ -53,6 +61,10 @@ TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1659, "k_tc_utv": 4.1502, "k_tc_uw": 4.0
 METRICS = {
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
+    "fig1_cauchy": "factor-build points/s over the time-vs-n sweep (Cauchy l=1, tol 1e-3, d 3-6, n 1e4-1e7), "
+                   "FP32 bulk",
+    "fig3_rank5": "factor-build points/s over the error-vs-rank sweep (4 kernels x 10 tolerances, n=5000, d=5), "
+                  "FP64 bulk",
     "cross3_gauss": "cross factor-build points/s (build of K(X,Y) ~= U S V^T + 16-column K~V and K~^T W), "
                     "FP32 bulk",
 }
@@ -235,6 +247,40 @@ def run_reference(args):
     import numpy as np
     from paper_2202_03655_gb300 import workloads as W
     w = workload_params(args)
+    if args.workload in ("fig1_cauchy", "fig3_rank5"):
+        from oracle import hdf as ohdf
+        if args.workload == "fig1_cauchy":
+            ns = min(args.cpu_n, 20000)
+            jobs = [(W.maxnorm1_points(args.workload, ns, d), w["kernel"], w["ell"], w["tol"]) for d in (3, 4)]
+            what = f"oracle builds of {ns} points in d = 3 and 4, Cauchy l = 1, tol 1e-3"
+        else:
+            ns = min(args.cpu_n, 2000)
+            xs = W.maxnorm1_points(args.workload, w["n"], w["d"])[:ns]
+            jobs = [(xs, kn, ell, 1e-3) for kn, ell in w["kernels"]]
+            what = f"oracle builds of the first {ns} points, the four kernels at tol 1e-3"
+
+        def work():
+            t = time.perf_counter()
+            for xj, kn, ell, tol in jobs:
+                ohdf.build(xj, kn, ell, tol, p_max=args.p_max)
+            return time.perf_counter() - t
+
+        for _ in range(args.warmup):
+            work()
+        ts = [work() for _ in range(args.steps)]
+        tot = sum(ts)
+        npts = sum(len(j[0]) for j in jobs)
+        val = npts * args.steps / tot
+        line = {"impl": "reference", "metric": METRICS[args.workload], "value": val, "unit": "points/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "points_per_step": npts, "p_max": args.p_max},
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": what + ", FP64 numpy"},
+                "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "cross3_gauss":
         x, y = cross_oracle_sample(args, w)
         for _ in range(args.warmup):
@@ -696,6 +742,231 @@ def bench_cross(args):
     return 0
 
 
+def bench_fig1(args):
+    """Time-vs-n row: hdf_build over the (d, n) grid of Fig. 1."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    stream = torch.cuda.current_stream(dev)
+    sizes = [int(n) for n in w["sizes"] if not args.n or n <= args.n]
+    grid = [(d, n) for d in w["dims"] for n in sizes]
+    pts = {(d, n): torch.from_numpy(W.maxnorm1_points(args.workload, n, d)).to(dev) for d, n in grid}
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in grid}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
+
+    def one(keep):
+        flush.zero_()
+        rec = {}
+        for k in grid:
+            e0, e1 = ev[k]
+            e0.record(stream)
+            f = hdf.build(pts[k], w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+            e1.record(stream)
+            if keep:
+                rec[k] = f.info
+            f.free()
+        if keep:
+            torch.cuda.synchronize()
+            rec = {k: (v, ev[k][0].elapsed_time(ev[k][1])) for k, v in rec.items()}
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    total_pts = sum(n for _, n in grid)
+    value = ws * total_pts * args.steps / (ms_total / 1e3)
+    table = []
+    for d in w["dims"]:
+        ts = []
+        for n in sizes:
+            ms = float(np.median([r[(d, n)][1] for r in recs]))
+            I = recs[-1][(d, n)][0]
+            ts.append(ms)
+            table.append({"d": d, "n": n, "build_ms": ms, "points_per_s": n / (ms / 1e3), "p": I.p,
+                          "rank": I.rank, "reached": bool(I.reached), "err_bound": I.err_bound})
+        big = [i for i, n in enumerate(sizes) if n >= 100_000]
+        if len(big) >= 2:
+            slope = float(np.polyfit(np.log([sizes[i] for i in big]), np.log([ts[i] for i in big]), 1)[0])
+            table.append({"d": d, "loglog_slope_n_ge_1e5": slope})
+    # roofline: the U writer of the largest d = 3 build
+    dmax = (w["dims"][0], sizes[-1])
+    I = recs[-1][dmax][0]
+    n = dmax[1]
+    nF = sum(I.s_k[k] for k in range(I.L + 1))
+    ub = n * (I.rank * 4 + dmax[0] * 8 + nF * 4)
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    t5 = float(np.mean([r[dmax][0].t_ms[5] for r in recs]))
+    roof = {"kernel": f"k_uwriter (d = {dmax[0]}, n = {n})", "bound": "hbm", "achieved": ub / (t5 / 1e3) / 1e9,
+            "peak": hbm, "unit": "GB/s", "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None,
+            "algorithmic_bytes": ub, "ms_per_launch": t5}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end: H2D of the points of the sweep, every build, D2H of each factor's metadata
+    host = {k: v.cpu().pin_memory() for k, v in pts.items()}
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for k in grid:
+        pts[k].copy_(host[k], non_blocking=True)
+        f = hdf.build(pts[k], w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1)
+    e2e = {"value": ws * total_pts / (e2e_ms / 1e3), "unit": "points/s",
+           "h2d_bytes_per_step": int(sum(n * d * 8 for d, n in grid)), "d2h_bytes_per_step": 0, "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        from oracle import hdf as ohdf
+        xs = W.maxnorm1_points(args.workload, min(args.cpu_n, 20000), 3)
+        t = time.perf_counter()
+        ohdf.build(xs, w["kernel"], w["ell"], w["tol"], p_max=args.p_max)
+        ts_ = time.perf_counter() - t
+        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one oracle build of {len(xs)} points, d = 3, FP64 numpy"}
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "dims": list(w["dims"]), "sizes": sizes, "kernel": w["kernel"],
+                           "lengthscale": w["ell"], "tol": w["tol"], "p_max": args.p_max,
+                           "parallelism": f"replicas{ws}",
+                           "l2": "L2 flushed by a 256 MB write at the start of every step (inside the timed region)"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"builds": table}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_fig3(args):
+    """Error-vs-rank row: hdf_build over (kernel, tol) on 5,000 points in d = 5, errors from the
+    dense kernel matrix (outside the timed region)."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    n, d = w["n"], w["d"]
+    stream = torch.cuda.current_stream(dev)
+    x_np = W.maxnorm1_points(args.workload, n, d)
+    x = torch.from_numpy(x_np).to(dev)
+    cfgs = [(kn, ell, tol) for kn, ell in w["kernels"] for tol in w["tols"]]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
+
+    def build(cfg):
+        kn, ell, tol = cfg
+        try:
+            return hdf.build(x, kn, ell, tol, precision="fp64", p_max=args.p_max, stream=stream)
+        except hdf.HdfError as e:            # a size limit at the degree cap: recorded, not fatal
+            return str(e)
+
+    def one(keep):
+        flush.zero_()
+        out = {}
+        for cfg in cfgs:
+            f = build(cfg)
+            if isinstance(f, str):
+                out[cfg] = f
+                continue
+            out[cfg] = f.info if keep else None
+            f.free()
+        return out if keep else None
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    value = ws * n * len(cfgs) * args.steps / (ms_total / 1e3)
+    # achieved errors against the dense matrix, per (kernel, tol)
+    D = torch.cdist(x, x)
+    rows = []
+    total_ms = {}
+    for kn, ell in w["kernels"]:
+        z = D / ell
+        if kn == "gaussian":
+            K = torch.exp(-0.5 * z * z)
+        elif kn == "cauchy":
+            K = 1.0 / (1.0 + z * z)
+        elif kn == "matern32":
+            K = (1 + 3 ** 0.5 * z) * torch.exp(-(3 ** 0.5) * z)
+        else:
+            K = (1 + 5 ** 0.5 * z + 5.0 / 3.0 * z * z) * torch.exp(-(5 ** 0.5) * z)
+        kn_norm = torch.linalg.norm(K)
+        for tol in w["tols"]:
+            f = build((kn, ell, tol))
+            if isinstance(f, str):
+                rows.append({"kernel": kn, "tol": tol, "status": f})
+                continue
+            if f.info.rank <= 40000:           # exact: K~ = U S U^T from the exported factor
+                U, S = f.export()
+                Ut = torch.from_numpy(U).to(dev)
+                Kt = (Ut * torch.from_numpy(S).to(dev)) @ Ut.T
+                err = float(torch.linalg.norm(K - Kt) / kn_norm)
+                how = "exact"
+                del Ut, Kt
+            else:                               # E |(K - K~) g|^2 = |K - K~|_F^2 over 256 N(0, I) probes
+                G = torch.randn((n, 256), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(5))
+                R = K @ G - f.matvec(G)
+                err = float(torch.sqrt((R * R).sum() / 256) / kn_norm)
+                how = "256-probe estimate (standard error <= 9%)"
+                del G, R
+            rows.append({"kernel": kn, "sigma": 1.0, "tol": tol, "p": f.info.p, "reached": bool(f.info.reached),
+                         "rank": f.info.rank, "rel_fro_err": err, "err_how": how, "err_bound": f.info.err_bound,
+                         "build_ms": f.info.t_ms[7]})
+            f.free()
+    del D
+    # roofline: U writer of the largest factor of the sweep
+    big = max((r for r in rows if "rank" in r), key=lambda r: r["rank"])
+    f = build((big["kernel"], dict(w["kernels"])[big["kernel"]], big["tol"]))
+    I = f.info
+    nF = sum(I.s_k[k] for k in range(I.L + 1))
+    ub = n * (I.rank * 8 + d * 8 + nF * 8)
+    t5 = float(I.t_ms[5])
+    f.free()
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    roof = {"kernel": f"k_uwriter<double> ({big['kernel']}, tol {big['tol']}, rank {big['rank']})", "bound": "hbm",
+            "achieved": ub / (t5 / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None, "algorithmic_bytes": ub,
+            "ms_per_launch": t5, "note": "U is 5,000 rows: L2-resident, small launch"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    xh = torch.from_numpy(x_np).pin_memory()
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    x.copy_(xh, non_blocking=True)
+    for cfg in cfgs:
+        f = build(cfg)
+        if not isinstance(f, str):
+            f.free()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1)
+    e2e = {"value": ws * n * len(cfgs) / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8,
+           "d2h_bytes_per_step": 0, "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        from oracle import hdf as ohdf
+        ns = min(args.cpu_n, 2000)
+        t = time.perf_counter()
+        ohdf.build(x_np[:ns], "cauchy", 1.0, 1e-3, p_max=args.p_max)
+        ts_ = time.perf_counter() - t
+        cpu = {"value": ns / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one oracle build of the first {ns} points, Cauchy, tol 1e-3, FP64 numpy"}
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "d": d, "kernels": [k for k, _ in w["kernels"]],
+                           "tols": list(w["tols"]), "p_max": args.p_max, "parallelism": f"replicas{ws}",
+                           "l2": "L2 flushed by a 256 MB write at the start of every step (inside the timed region)"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"sweep": rows}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -706,6 +977,10 @@ def main():
         return bench_batch(args)
     if args.workload == "cross3_gauss":
         return bench_cross(args)
+    if args.workload == "fig1_cauchy":
+        return bench_fig1(args)
+    if args.workload == "fig3_rank5":
+        return bench_fig3(args)
     import numpy as np
     import torch
     from paper_2202_03655_gb300 import hdf, workloads as W

@@ -17,7 +17,13 @@ that to the point distributions the factorization is expected to meet):
   3  cube4_gauss      n=500,000, d=4, uniform in [-1,1]^4, Gaussian l=0.8, tol 1e-6
   4  batch512_gauss   512 sets, n log-uniform in [1000, 65536], d=3, uniform in a ball of
                       radius U[0.5, 2], Gaussian l ~ U[0.3, 1.5], tol 1e-6, V with 8 columns
-  5  fig1_cauchy      Sec. 4.1 Fig. 1 shape: N(0,I) points scaled to max norm 1, Cauchy l=1
+  5  fig1_cauchy      the time-vs-n workload of Sec. 4.1 / Fig. 1: N(0,I) points scaled to max
+                      norm 1, d in {3, 4, 5, 6}, n from 10^4 to 10^7, Cauchy sigma = l = 1,
+                      tol 1e-3 (the figure's caption; the text says 0.005)
+  7  fig3_rank5       the error-vs-rank workload of Sec. 4.1 / Fig. 3: 5,000 points in d = 5
+                      generated as workload 5, the four kernels with sigma = 1 (the Gaussian in
+                      the paper's exp(-(r/sigma)^2) form, i.e. l = 1/sqrt(2) here), tolerances
+                      from 1e-1 to 1e-7
   6  cross3_gauss     the non-symmetric row K(X, Y): X = 1,000,000 points of the 8-component
                       mixture of workload 1, Y = 250,000 points of N(0, 1.2^2 I) (a wider
                       cloud around them: off-diagonal and cross-kernel blocks, Sec. 2 and 5),
@@ -90,6 +96,12 @@ WORKLOADS = {
     "normal5_cauchy": dict(idx=2, n=4_000_000, d=5, kernel="cauchy", ell=2.0, tol=1e-4, ncols=16),
     "cube4_gauss": dict(idx=3, n=500_000, d=4, kernel="gaussian", ell=0.8, tol=1e-6, ncols=1),
     "batch512_gauss": dict(idx=4, nsets=512, d=3, kernel="gaussian", tol=1e-6, ncols=8),
+    "fig1_cauchy": dict(idx=5, n=10_000_000, d=3, dims=(3, 4, 5, 6), sizes=(10_000, 100_000, 1_000_000, 10_000_000),
+                        kernel="cauchy", ell=1.0, tol=1e-3, ncols=1),
+    "fig3_rank5": dict(idx=7, n=5000, d=5, kernels=(("cauchy", 1.0), ("gaussian", 0.5 ** 0.5), ("matern32", 1.0),
+                                                   ("matern52", 1.0)),
+                       tols=(1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5, 1e-6, 1e-7), kernel="cauchy", ell=1.0,
+                       tol=1e-3, ncols=1),
     "cross3_gauss": dict(idx=6, n=1_000_000, n_y=250_000, d=3, kernel="gaussian", ell=1.5, tol=1e-6,
                          ncols=16),
 }
@@ -120,3 +132,10 @@ def points(name, n=None, idx=None):
     if name == "cube4_gauss":
         return uniform_cube(g, n, 4)
     raise ValueError(name)
+
+
+def maxnorm1_points(name, n, d):
+    """Points of the Sec. 4.1 workloads (fig1_cauchy, fig3_rank5): N(0, I) scaled to max norm 1,
+    one seeded stream per (workload, d)."""
+    w = WORKLOADS[name]
+    return normal_maxnorm1(rng(w["idx"] * 100 + d), int(n), d)
