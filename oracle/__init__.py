@@ -23,6 +23,8 @@ Approximation via Hyperspherical Harmonics" (ICML 2022) that it follows:
                     the frozen-structure adjoint and the dense checker.
 * ``cross``      -- Algorithm 1 in its general form for two sets, K(X, Y) ~= U S V^T:
                     joint scaling, two QRs per parity, SVD, truncation, both factors.
+* ``krr``        -- kernel ridge regression of Sec. 4.2: k-means blocks, HDF diagonal
+                    blocks with exact off-diagonal blocks, the block preconditioner, PCG.
 
 Functions that have no independent pin are marked "parity unpinned" in their docstring.
 At present every function used by the parity tests is pinned (see tests/test_oracle_*.py).

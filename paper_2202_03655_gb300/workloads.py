@@ -24,6 +24,12 @@ that to the point distributions the factorization is expected to meet):
                       generated as workload 5, the four kernels with sigma = 1 (the Gaussian in
                       the paper's exp(-(r/sigma)^2) form, i.e. l = 1/sqrt(2) here), tolerances
                       from 1e-1 to 1e-7
+  8  krr8_clusters    the kernel-ridge-regression row (Sec. 4.2) on synthetic data shaped like
+                      its dataset (20,640 points, 8 features scaled to [0, 1], a 2/3 - 1/3
+                      train/test split): a 24-component mixture with anisotropic spreads,
+                      targets = a random smooth function (four random plane waves) plus noise;
+                      30 k-means clusters from seeded initial centres; Gaussian l = 0.5,
+                      lambda = 0.1, HDF blocks at tol 1e-3
   6  cross3_gauss     the non-symmetric row K(X, Y): X = 1,000,000 points of the 8-component
                       mixture of workload 1, Y = 250,000 points of N(0, 1.2^2 I) (a wider
                       cloud around them: off-diagonal and cross-kernel blocks, Sec. 2 and 5),
@@ -102,6 +108,8 @@ WORKLOADS = {
                                                    ("matern52", 1.0)),
                        tols=(1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5, 1e-6, 1e-7), kernel="cauchy", ell=1.0,
                        tol=1e-3, ncols=1),
+    "krr8_clusters": dict(idx=8, n=20640, d=8, kernel="gaussian", ell=0.5, lam=0.1, tol=1e-3, clusters=30,
+                          components=24, ncols=1),
     "cross3_gauss": dict(idx=6, n=1_000_000, n_y=250_000, d=3, kernel="gaussian", ell=1.5, tol=1e-6,
                          ncols=16),
 }
@@ -139,3 +147,30 @@ def maxnorm1_points(name, n, d):
     one seeded stream per (workload, d)."""
     w = WORKLOADS[name]
     return normal_maxnorm1(rng(w["idx"] * 100 + d), int(n), d)
+
+
+def krr_data(name="krr8_clusters", n=None):
+    """(x_train, y_train, x_test, y_test, init_idx) of the regression workload: features are
+    min-max scaled to [0, 1]; init_idx are distinct training indices for the k-means centres."""
+    w = WORKLOADS[name]
+    n = w["n"] if n is None else int(n)
+    d, q = w["d"], w["components"]
+    g = rng(w["idx"])
+    means = g.uniform(0.2, 0.8, size=(q, d))
+    spreads = g.uniform(0.03, 0.12, size=(q, d))
+    weights = g.dirichlet(np.full(q, 2.0))
+    comp = g.choice(q, size=n, p=weights)
+    x = means[comp] + spreads[comp] * g.standard_normal((n, d))
+    x = (x - x.min(axis=0)) / (x.max(axis=0) - x.min(axis=0))
+    dirs = g.standard_normal((4, d))
+    freqs = g.uniform(1.0, 3.0, size=4)
+    phases = g.uniform(0.0, 2 * np.pi, size=4)
+    amps = g.uniform(0.5, 1.5, size=4)
+    y = (amps[None, :] * np.sin(freqs[None, :] * (x @ dirs.T) + phases[None, :])).sum(axis=1)
+    y = y + 0.1 * g.standard_normal(n)
+    perm = g.permutation(n)
+    ntr = (2 * n) // 3
+    tr, te = perm[:ntr], perm[ntr:]
+    init = g.choice(ntr, size=w["clusters"], replace=False)
+    return x[tr], y[tr], x[te], y[te], np.sort(init).astype(np.int64)
+
