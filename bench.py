@@ -31,6 +31,11 @@ Other workloads (--workload):
                   (sigma = 1) and ten tolerances, FP64; step = one hdf_build per (kernel, tol);
                   detail holds rank and the achieved |K - K~|_F / |K|_F of each against the
                   dense kernel matrix.
+  krr8_clusters   the kernel-ridge-regression row (Sec. 4.2): 13,760 training and 6,880 test
+                  points in d = 8 (synthetic stand-in for the paper's dataset), 30 k-means
+                  clusters, Gaussian l = 0.5, lambda = 0.1, HDF blocks at tol 1e-3 (FP32 bulk);
+                  step = hdf_kmeans + hdf_krr_build + hdf_krr_solve (rtol 1e-6) +
+                  hdf_kernel_matvec for the test predictions; value = training points / s.
   cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a
                   wider Gaussian cloud, Gaussian l = 1.5, tol 1e-6, FP32; step = hdf_build_cross
                   + K~ V (V: 16 columns over Y) + K~^T W (W: 16 columns over X); value = points
@@ -65,6 +70,8 @@ METRICS = {
                    "FP32 bulk",
     "fig3_rank5": "factor-build points/s over the error-vs-rank sweep (4 kernels x 10 tolerances, n=5000, d=5), "
                   "FP64 bulk",
+    "krr8_clusters": "kernel ridge regression training points/s (k-means + HDF diagonal blocks + block-"
+                     "preconditioned CG to rtol 1e-6 + test predictions), FP64 solve",
     "cross3_gauss": "cross factor-build points/s (build of K(X,Y) ~= U S V^T + 16-column K~V and K~^T W), "
                     "FP32 bulk",
 }
@@ -247,6 +254,32 @@ def run_reference(args):
     import numpy as np
     from paper_2202_03655_gb300 import workloads as W
     w = workload_params(args)
+    if args.workload == "krr8_clusters":
+        from oracle import krr as okrr
+        xs, ys, xq, _, init_s = W.krr_data(args.workload, n=min(args.cpu_n, 3000))
+
+        def work():
+            t = time.perf_counter()
+            lab, _, _ = okrr.kmeans(xs, init_s)
+            wo, _, _, _ = okrr.krr_fit(xs, ys, lab, w["kernel"], w["ell"], w["lam"], w["tol"], rtol=1e-6)
+            okrr.kernel_matvec(xq, xs, w["kernel"], w["ell"], wo)
+            return time.perf_counter() - t
+
+        for _ in range(args.warmup):
+            work()
+        ts = [work() for _ in range(args.steps)]
+        tot = sum(ts)
+        val = len(xs) * args.steps / tot
+        line = {"impl": "reference", "metric": METRICS[args.workload], "value": val, "unit": "points/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n_train_sample": len(xs), "d": w["d"], "p_max": args.p_max},
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"the regression recipe at {len(xs)} training points, FP64 numpy"},
+                "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload in ("fig1_cauchy", "fig3_rank5"):
         from oracle import hdf as ohdf
         if args.workload == "fig1_cauchy":
@@ -967,6 +1000,118 @@ def bench_fig3(args):
     return 0
 
 
+def bench_krr(args):
+    """Kernel-ridge-regression row: k-means, block operator, PCG, predictions."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    xtr_np, ytr_np, xte_np, yte_np, init = W.krr_data(args.workload)
+    ntr, nte, d = len(xtr_np), len(xte_np), w["d"]
+    xtr, ytr, xte = (torch.from_numpy(a).to(dev) for a in (xtr_np, ytr_np, xte_np))
+    stream = torch.cuda.current_stream(dev)
+    rtol, max_iter = 1e-6, 5000
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
+
+    def fit_predict(xa, ya, xq):
+        labels, _, km_it = hdf.kmeans(xa, init, stream=stream)
+        K = hdf.KRR(xa, labels, w["kernel"], w["ell"], w["lam"], w["tol"], precision="fp32", p_max=args.p_max,
+                    stream=stream)
+        wv, it, res = K.solve(ya, rtol=rtol, max_iter=max_iter, stream=stream)
+        pred = hdf.kernel_matvec(xq, xa, w["kernel"], w["ell"], wv, stream=stream)
+        return K, km_it, it, res, pred
+
+    def one(keep):
+        flush.zero_()
+        K, km_it, it, res, pred = fit_predict(xtr, ytr, xte)
+        rec = (K.info(), km_it, it, res, pred) if keep else None
+        K.free()
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    value = ws * ntr * args.steps / (ms_total / 1e3)
+    (nc, rank_tot, tms), km_it, it, res, pred = recs[-1]
+    pred_np = pred.cpu().numpy()
+    mse = float(np.mean((pred_np - yte_np) ** 2))
+    # the dense KRR solution of Eq. (opt) with the exact kernel, for reference (outside the timed region)
+    Kd = torch.cdist(xtr, xtr)
+    Kd = torch.exp(-0.5 * (Kd / w["ell"]) ** 2)
+    Kd.diagonal().add_(w["lam"])
+    wd = torch.linalg.solve(Kd, ytr)
+    del Kd
+    pd = torch.exp(-0.5 * (torch.cdist(xte, xtr) / w["ell"]) ** 2) @ wd
+    mse_dense = float(torch.mean((pd - torch.from_numpy(yte_np).to(dev)) ** 2))
+    pred_rel = float(torch.linalg.norm(pred - pd) / torch.linalg.norm(pd))
+    # roofline of the direct kernel evaluation (the off-diagonal blocks in every CG product and
+    # the predictions): one launch over nte x ntr pairs
+    wr = torch.randn(ntr, dtype=torch.float64, device=dev)
+    hdf.kernel_matvec(xte, xtr, w["kernel"], w["ell"], wr, stream=stream)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(10):
+        hdf.kernel_matvec(xte, xtr, w["kernel"], w["ell"], wr, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    km_ms = a0.elapsed_time(a1) / 10
+    pairs = nte * ntr
+    flops = pairs * (3 * d + 8)
+    peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"kernel": "k_direct_kernel (K(x*, x) w, 6,880 x 13,760 pairs)", "bound": "alu",
+            "achieved": flops / (km_ms / 1e3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+            "traffic": None, "algorithmic_flops": flops, "flops_per_pair": 3 * d + 8, "ms_per_launch": km_ms,
+            "pairs_per_s": pairs / (km_ms / 1e3)}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D of the training and test data, the whole fit,
+    # D2H of the predictions
+    hx, hy, hq = (torch.from_numpy(a).pin_memory() for a in (xtr_np, ytr_np, xte_np))
+    ph = torch.empty(nte, dtype=torch.float64).pin_memory()
+    xd, yd, qd = torch.empty_like(xtr), torch.empty_like(ytr), torch.empty_like(xte)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    xd.copy_(hx, non_blocking=True); yd.copy_(hy, non_blocking=True); qd.copy_(hq, non_blocking=True)
+    K, _, _, _, pr2 = fit_predict(xd, yd, qd)
+    ph.copy_(pr2, non_blocking=True)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    K.free()
+    e2e_ms = b0.elapsed_time(b1)
+    e2e = {"value": ws * ntr / (e2e_ms / 1e3), "unit": "points/s",
+           "h2d_bytes_per_step": (ntr + nte) * d * 8 + ntr * 8, "d2h_bytes_per_step": nte * 8, "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        from oracle import krr as okrr
+        xs, ys, xq, _, init_s = W.krr_data(args.workload, n=min(args.cpu_n, 3000))
+        t = time.perf_counter()
+        lab, _, _ = okrr.kmeans(xs, init_s)
+        wo, _, _, _ = okrr.krr_fit(xs, ys, lab, w["kernel"], w["ell"], w["lam"], w["tol"], rtol=rtol)
+        okrr.kernel_matvec(xq, xs, w["kernel"], w["ell"], wo)
+        ts_ = time.perf_counter() - t
+        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the same recipe at {len(xs)} training points (k-means, oracle HDF blocks, PCG, "
+                         f"predictions), FP64 numpy"}
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "n_train": ntr, "n_test": nte, "d": d, "kernel": w["kernel"],
+                           "lengthscale": w["ell"], "lambda": w["lam"], "tol": w["tol"], "clusters": w["clusters"],
+                           "cg_rtol": rtol, "bulk": "fp32", "parallelism": f"replicas{ws}",
+                           "l2": "L2 flushed by a 256 MB write at the start of every step (inside the timed region)"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"kmeans_passes": km_it, "cg_iterations": it, "cg_relres": res, "clusters": nc,
+                           "rank_total": rank_tot, "factor_ms": tms[0], "precond_ms": tms[1],
+                           "test_mse": mse, "test_mse_dense_exact": mse_dense,
+                           "pred_rel_diff_vs_dense": pred_rel, "target_variance": float(np.var(yte_np))}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -979,6 +1124,8 @@ def main():
         return bench_cross(args)
     if args.workload == "fig1_cauchy":
         return bench_fig1(args)
+    if args.workload == "krr8_clusters":
+        return bench_krr(args)
     if args.workload == "fig3_rank5":
         return bench_fig3(args)
     import numpy as np

@@ -224,6 +224,66 @@ hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S
 
 void hdf_batch_free(hdf_batch* b);
 
+/* ------------------------------------------------------ kernel ridge regression ---- */
+/* Sec. 4.2 of the paper: the regularised system (lambda I + K) w = y of Eq. (opt) for the
+ * training points, with K replaced by K^ = the HDF factors of its diagonal blocks K_{C_i C_i}
+ * (clusters C_i of the points) plus the exact off-diagonal blocks, solved by conjugate
+ * gradients preconditioned by the inverses of the exact blocks lambda I + K_{C_i C_i}.
+ * Predictions y* = K(x*, x) w use the exact kernel (hdf_kernel_matvec). */
+typedef struct hdf_krr hdf_krr;              /* opaque, owned by the library */
+
+/* k-means clustering by Lloyd's iteration (the clusters of Sec. 4.2): from the centres
+ * x[init_host[c]] (c < k; the caller draws them), assign every point to its nearest centre
+ * (squared distance, lowest index on ties) and move each centre to the mean of its points (a
+ * centre without points stays), until no assignment changes or max_iter assignment passes.
+ * x_dev: row-major n x d FP64.  Output labels_dev (n ints, device), optionally centres_dev
+ * (k x d FP64, device) and *iterations (assignment passes made).  1 <= d <= 8, 1 <= k <= n,
+ * k d <= 6144.  Synchronises. */
+hdf_status hdf_kmeans(const double* x_dev, int64_t n, int d, int k, const int64_t* init_host, int max_iter,
+                      int* labels_dev, double* centres_dev, int* iterations, hdf_stream stream);
+
+/* out[i] = sum_j k(|xq_i - x_j|) w_j for all m query points (the predictions of Sec. 4.2):
+ * direct evaluation with coordinates shifted by x_0 and rounded to FP32, FP32 kernel values
+ * and sums over tiles of 128 points, FP64 sums across tiles (relative error ~1e-6).  xq_dev
+ * (m x d), x_dev (n x d) row-major FP64; w_dev (n), out_dev (m) FP64.  Asynchronous. */
+hdf_status hdf_kernel_matvec(const double* xq_dev, int64_t m, const double* x_dev, int64_t n, int d,
+                             hdf_kernel kernel, double lengthscale, const double* w_dev, double* out_dev,
+                             hdf_stream stream);
+
+/* Build the operator of Sec. 4.2 for the points x_dev (row-major n x d FP64) grouped by
+ * labels_dev (n non-negative ints, device; empty labels are skipped): the points are permuted
+ * cluster by cluster, the diagonal blocks are factored by one hdf_build_batched call (kernel,
+ * lengthscale, tol, prec, opt as there), the exact blocks lambda I + K_{C_i C_i} are formed on
+ * the device and inverted on the host (Cholesky, FP64), and the off-diagonal blocks are
+ * evaluated on the fly in every product (as hdf_kernel_matvec, pairs within one cluster
+ * skipped).  lambda > 0.  Limit: sum of squared cluster sizes <= 2^28 (HDF_ETOOBIG).  Returns
+ * HDF_ETOL_UNREACHABLE (with a usable operator) if a block was capped at p_max; HDF_ESINGULAR
+ * if a block lambda I + K_cc is not positive definite.  Synchronises. */
+hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* labels_dev, hdf_kernel kernel,
+                         double lengthscale, double lambda, double tol, hdf_precision prec,
+                         const hdf_options* opt, hdf_stream stream, hdf_krr** out);
+
+/* out = (lambda I + K^) v (v_dev, out_dev: n FP64 in the caller's point order).  Asynchronous. */
+hdf_status hdf_krr_apply(hdf_krr* K, const double* v_dev, double* out_dev, hdf_stream stream);
+
+/* z = M r with M the block-diagonal preconditioner (inverses of lambda I + K_{C_i C_i}).
+ * Asynchronous. */
+hdf_status hdf_krr_precond(hdf_krr* K, const double* r_dev, double* z_dev, hdf_stream stream);
+
+/* w = (lambda I + K^)^{-1} y by preconditioned CG from w_0 = 0, stopped when the recurrence
+ * residual |r| / |y| <= rtol or after max_iter iterations (then HDF_ETOL_UNREACHABLE with the
+ * last iterate in w_dev).  y_dev, w_dev: n FP64 in the caller's order.  *iterations and
+ * *relres (may be NULL) receive the count and the final relative residual.  Synchronises
+ * once per iteration (the CG scalars are formed on the host). */
+hdf_status hdf_krr_solve(hdf_krr* K, const double* y_dev, double rtol, int max_iter, double* w_dev,
+                         int* iterations, double* relres, hdf_stream stream);
+
+/* Number of clusters, total HDF rank of the diagonal blocks and build times in ms (t_ms2[0]:
+ * permutation + batched factorization, t_ms2[1]: block preconditioner).  Pointers may be NULL. */
+hdf_status hdf_krr_info(const hdf_krr* K, int* nclusters, int64_t* rank_total, double* t_ms2);
+
+void hdf_krr_free(hdf_krr* K);
+
 /* Metadata of a factor (sizes, scaling, degree, ranks, error budget and bound). */
 hdf_status hdf_factor_info(const hdf_factor* f, hdf_info* info);
 

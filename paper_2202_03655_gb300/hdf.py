@@ -67,6 +67,16 @@ SIGNATURES = {
     "hdf_batch_timings": (_c_int, [_vp, _pdbl]),
     "hdf_batch_export": (_c_int, [_vp, _c_int, _vp, _pdbl]),
     "hdf_batch_free": (None, [_vp]),
+    "hdf_kmeans": (_c_int, [_vp, _c_i64, _c_int, _c_int, ctypes.POINTER(_c_i64), _c_int, _vp, _vp,
+                            ctypes.POINTER(_c_int), _vp]),
+    "hdf_kernel_matvec": (_c_int, [_vp, _c_i64, _vp, _c_i64, _c_int, _c_int, _c_dbl, _vp, _vp, _vp]),
+    "hdf_krr_build": (_c_int, [_vp, _c_i64, _c_int, _vp, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_int,
+                               ctypes.POINTER(HdfOptions), _vp, ctypes.POINTER(_vp)]),
+    "hdf_krr_apply": (_c_int, [_vp, _vp, _vp, _vp]),
+    "hdf_krr_precond": (_c_int, [_vp, _vp, _vp, _vp]),
+    "hdf_krr_solve": (_c_int, [_vp, _vp, _c_dbl, _c_int, _vp, ctypes.POINTER(_c_int), _pdbl, _vp]),
+    "hdf_krr_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_i64), _pdbl]),
+    "hdf_krr_free": (None, [_vp]),
     "hdf_status_string": (ctypes.c_char_p, [_c_int]),
     "hdf_last_error": (ctypes.c_char_p, []),
     "hdf_launch_count": (ctypes.c_longlong, []),
@@ -437,3 +447,103 @@ def build_batched(x, offsets, kernel, lengthscales, tol, precision="fp32", p_max
                                  ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h))
     _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
     return Batch(h, st, off, precision)
+
+
+# ---------------------------------------------------------- kernel ridge regression
+
+def _f64_vec(v, n):
+    import torch
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.numel() == n):
+        raise ValueError(f"expected a CUDA float64 tensor of {n} entries")
+    return v.contiguous().reshape(-1)
+
+
+def kmeans(x, init_idx, max_iter=100, stream=None):
+    """Lloyd's k-means (hdf_kmeans) from the centres x[init_idx]: (labels int32, centres, passes)."""
+    import torch
+    x = x.contiguous()
+    init = np.ascontiguousarray(np.asarray(init_idx, dtype=np.int64))
+    k = len(init)
+    labels = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+    C = torch.empty((k, x.shape[1]), dtype=torch.float64, device=x.device)
+    it = _c_int()
+    _check(lib().hdf_kmeans(_vp(x.data_ptr()), x.shape[0], x.shape[1], k, init.ctypes.data_as(ctypes.POINTER(_c_i64)),
+                            int(max_iter), _vp(labels.data_ptr()), _vp(C.data_ptr()), ctypes.byref(it),
+                            _stream_handle(stream)))
+    return labels, C, it.value
+
+
+def kernel_matvec(xq, x, kernel, lengthscale, w, stream=None):
+    """K(xq, x) w by direct evaluation (hdf_kernel_matvec)."""
+    import torch
+    xq, x = xq.contiguous(), x.contiguous()
+    w = _f64_vec(w, x.shape[0])
+    out = torch.empty(xq.shape[0], dtype=torch.float64, device=x.device)
+    _check(lib().hdf_kernel_matvec(_vp(xq.data_ptr()), xq.shape[0], _vp(x.data_ptr()), x.shape[0], x.shape[1],
+                                   KERNELS[kernel], float(lengthscale), _vp(w.data_ptr()), _vp(out.data_ptr()),
+                                   _stream_handle(stream)))
+    return out
+
+
+class KRR:
+    """(lambda I + K^) of Sec. 4.2 held by the library (hdf_krr_*)."""
+
+    def __init__(self, x, labels, kernel, lengthscale, lam, tol, precision="fp64", p_max=None, eta=None,
+                 stream=None):
+        import torch
+        x = x.contiguous()
+        labels = labels.to(torch.int32).contiguous()
+        self.n = x.shape[0]
+        opt = HdfOptions(int(p_max or 0), float(eta or 0.0), 0)
+        h = _vp()
+        st = lib().hdf_krr_build(_vp(x.data_ptr()), x.shape[0], x.shape[1], _vp(labels.data_ptr()), KERNELS[kernel],
+                                 float(lengthscale), float(lam), float(tol), PRECISIONS[precision], ctypes.byref(opt),
+                                 _stream_handle(stream), ctypes.byref(h))
+        _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
+        self._h = h
+        self.status = st
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hdf_krr_free(h)
+            self._h = None
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None:
+            lib().hdf_krr_free(h)
+            self._h = None
+
+    def apply(self, v, stream=None):
+        import torch
+        v = _f64_vec(v, self.n)
+        out = torch.empty_like(v)
+        _check(lib().hdf_krr_apply(self._h, _vp(v.data_ptr()), _vp(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def precond(self, r, stream=None):
+        import torch
+        r = _f64_vec(r, self.n)
+        out = torch.empty_like(r)
+        _check(lib().hdf_krr_precond(self._h, _vp(r.data_ptr()), _vp(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def solve(self, y, rtol=1e-8, max_iter=1000, stream=None):
+        """(w, iterations, relative residual) of PCG for (lambda I + K^) w = y."""
+        import torch
+        y = _f64_vec(y, self.n)
+        w = torch.empty_like(y)
+        it, res = _c_int(), _c_dbl()
+        st = lib().hdf_krr_solve(self._h, _vp(y.data_ptr()), float(rtol), int(max_iter), _vp(w.data_ptr()),
+                                 ctypes.byref(it), ctypes.byref(res), _stream_handle(stream))
+        _check(st, allow=(HDF_OK, HDF_ETOL_UNREACHABLE))
+        return w, it.value, res.value
+
+    def info(self):
+        """(clusters, total rank of the diagonal blocks, (factorization ms, preconditioner ms))."""
+        nc, rk = _c_int(), _c_i64()
+        t = np.zeros(2)
+        _check(lib().hdf_krr_info(self._h, ctypes.byref(nc), ctypes.byref(rk), _dptr(t)))
+        return nc.value, rk.value, (float(t[0]), float(t[1]))
+
