@@ -243,9 +243,11 @@ hdf_status hdf_kmeans(const double* x_dev, int64_t n, int d, int k, const int64_
                       int* labels_dev, double* centres_dev, int* iterations, hdf_stream stream);
 
 /* out[i] = sum_j k(|xq_i - x_j|) w_j for all m query points (the predictions of Sec. 4.2):
- * direct evaluation with coordinates shifted by x_0 and rounded to FP32, FP32 kernel values
- * and sums over tiles of 128 points, FP64 sums across tiles (relative error ~1e-6).  xq_dev
- * (m x d), x_dev (n x d) row-major FP64; w_dev (n), out_dev (m) FP64.  Asynchronous. */
+ * direct evaluation with coordinates shifted by x_0 and rounded to FP32 and FP32 kernel values
+ * (relative error ~1e-7 per value); the products with w and their sums are formed in
+ * double-float arithmetic within tiles of 128 points and in FP64 across tiles, so the result is
+ * linear in w to ~1e-14.  xq_dev (m x d), x_dev (n x d) row-major FP64; w_dev (n), out_dev (m)
+ * FP64.  Asynchronous. */
 hdf_status hdf_kernel_matvec(const double* xq_dev, int64_t m, const double* x_dev, int64_t n, int d,
                              hdf_kernel kernel, double lengthscale, const double* w_dev, double* out_dev,
                              hdf_stream stream);

@@ -111,15 +111,18 @@ constexpr int kDkTile = 128;     // columns staged per tile
 
 // part[s m + i] = sum over columns j of split s of k(|a_i - b_j|) w_j, skipping j with
 // cb[j] == ca[i] when ca is given (the off-diagonal blocks of K^).  Coordinates are FP32 copies
-// shifted by a common point; kernel values and the products of one tile are FP32, tiles are
-// added in FP64 in column order.
+// shifted by a common point and the kernel values k_ij are FP32 (one fixed, exactly symmetric
+// matrix); w_j = w_hi + w_lo as two FP32 numbers, each product k_ij w_hi formed exactly (fma)
+// and the sums of one tile kept as FP32 pairs (TwoSum), so that the product is linear in w to
+// about 1e-14 -- conjugate gradients need the same linear operator in every iteration.  Tiles
+// are added in FP64 in column order.
 __global__ void __launch_bounds__(kDkRows) k_direct_kernel(const float* __restrict__ a, int64_t m,
                                                           const float* __restrict__ b, int64_t n, int d,
                                                           int kernel, float inv_ell, const double* __restrict__ w,
                                                           const int* __restrict__ ca, const int* __restrict__ cb,
                                                           int64_t split, double* __restrict__ part) {
     __shared__ float bs[kDkTile][dev::kMaxD];
-    __shared__ float ws[kDkTile];
+    __shared__ float ws[kDkTile], wl[kDkTile];
     __shared__ int cs[kDkTile];
     const int64_t i = blockIdx.x * (int64_t)kDkRows + threadIdx.x;
     const bool act = i < m;
@@ -136,18 +139,27 @@ __global__ void __launch_bounds__(kDkRows) k_direct_kernel(const float* __restri
             bs[r][q] = (r < nt) ? b[(t0 + r) * d + q] : 0.f;
         }
         for (int r = threadIdx.x; r < kDkTile; r += blockDim.x) {
-            ws[r] = (r < nt) ? (float)w[t0 + r] : 0.f;
+            const double wv = (r < nt) ? w[t0 + r] : 0.0;
+            const float hi = (float)wv;
+            ws[r] = hi;
+            wl[r] = (float)(wv - (double)hi);
             cs[r] = (r < nt && cb) ? cb[t0 + r] : -2;
         }
         __syncthreads();
-        float tsum = 0.f;
+        float sh_ = 0.f, sl_ = 0.f;                  // tile sum as an unevaluated FP32 pair
         for (int r = 0; r < nt; ++r) {
             if (cs[r] == myc) continue;
             float s = 0.f;
             for (int q = 0; q < d; ++q) { const float t = ai[q] - bs[r][q]; s = fmaf(t, t, s); }
-            tsum = fmaf(kernel_value_f(kernel, sqrtf(s), inv_ell), ws[r], tsum);
+            const float kv = kernel_value_f(kernel, sqrtf(s), inv_ell);
+            const float p = kv * ws[r];
+            const float e = fmaf(kv, wl[r], fmaf(kv, ws[r], -p));      // exact error of p, plus k w_lo
+            float t1, t2;
+            dev::two_sum(sh_, p, t1, t2);
+            sh_ = t1;
+            sl_ += t2 + e;
         }
-        acc += (double)tsum;
+        acc += (double)sh_ + (double)sl_;
     }
     if (act) part[blockIdx.y * m + i] = acc;
 }

@@ -70,8 +70,11 @@ def test_krr_operator_preconditioner_and_solve(prec):
     assert rel(K.precond(to_dev(v)).cpu().numpy(), M(v)) <= 1e-10
     w, it, res = K.solve(to_dev(ytr), rtol=1e-8, max_iter=3000)
     assert res <= 1e-8
+    # the true residual follows the recurrence when the operator is linear to working
+    # precision: FP64 blocks and the double-float direct product; FP32 blocks round their
+    # input to FP32 (relative 6e-8, amplified by the condition number ~1e4)
     true_res = rel(K.apply(w).cpu().numpy(), ytr)
-    assert true_res <= 1e-6
+    assert true_res <= (1e-7 if prec == "fp64" else 1e-3)
     wo, ito, reso = okrr.pcg(lambda u: lam * u + op.apply(u), M, ytr, 1e-8, 3000)
     pr = hdf.kernel_matvec(to_dev(xte), x, "gaussian", ell, w).cpu().numpy()
     po = okrr.kernel_matvec(xte, xtr, "gaussian", ell, wo)
