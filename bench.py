@@ -33,7 +33,7 @@ Other workloads (--workload):
                   dense kernel matrix.
   krr8_clusters   the kernel-ridge-regression row (Sec. 4.2): 13,760 training and 6,880 test
                   points in d = 8 (synthetic stand-in for the paper's dataset), 30 k-means
-                  clusters, Gaussian l = 0.5, lambda = 0.1, HDF blocks at tol 1e-3 (FP32 bulk);
+                  clusters, Gaussian l = 0.5, lambda = 1, HDF blocks at tol 1e-3 (FP32 bulk);
                   step = hdf_kmeans + hdf_krr_build + hdf_krr_solve (rtol 1e-6) +
                   hdf_kernel_matvec for the test predictions; value = training points / s.
   cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a

@@ -29,7 +29,8 @@ that to the point distributions the factorization is expected to meet):
                       train/test split): a 24-component mixture with anisotropic spreads,
                       targets = a random smooth function (four random plane waves) plus noise;
                       30 k-means clusters from seeded initial centres; Gaussian l = 0.5,
-                      lambda = 0.1, HDF blocks at tol 1e-3
+                      lambda = 1, HDF blocks at tol 1e-3 (lambda above tol max_i |K_ii|_F keeps
+                      lambda I + K^ positive definite)
   6  cross3_gauss     the non-symmetric row K(X, Y): X = 1,000,000 points of the 8-component
                       mixture of workload 1, Y = 250,000 points of N(0, 1.2^2 I) (a wider
                       cloud around them: off-diagonal and cross-kernel blocks, Sec. 2 and 5),
@@ -108,7 +109,7 @@ WORKLOADS = {
                                                    ("matern52", 1.0)),
                        tols=(1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 1e-5, 1e-6, 1e-7), kernel="cauchy", ell=1.0,
                        tol=1e-3, ncols=1),
-    "krr8_clusters": dict(idx=8, n=20640, d=8, kernel="gaussian", ell=0.5, lam=0.1, tol=1e-3, clusters=30,
+    "krr8_clusters": dict(idx=8, n=20640, d=8, kernel="gaussian", ell=0.5, lam=1.0, tol=1e-3, clusters=30,
                           components=24, ncols=1),
     "cross3_gauss": dict(idx=6, n=1_000_000, n_y=250_000, d=3, kernel="gaussian", ell=1.5, tol=1e-6,
                          ncols=16),
