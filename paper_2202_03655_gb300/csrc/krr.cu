@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -116,52 +117,72 @@ constexpr int kDkTile = 128;     // columns staged per tile
 // and the sums of one tile kept as FP32 pairs (TwoSum), so that the product is linear in w to
 // about 1e-14 -- conjugate gradients need the same linear operator in every iteration.  Tiles
 // are added in FP64 in column order.
+template <int DD>
 __global__ void __launch_bounds__(kDkRows) k_direct_kernel(const float* __restrict__ a, int64_t m,
-                                                          const float* __restrict__ b, int64_t n, int d,
-                                                          int kernel, float inv_ell, const double* __restrict__ w,
+                                                          const float* __restrict__ b, int64_t n, int kernel,
+                                                          float inv_ell, const double* __restrict__ w,
                                                           const int* __restrict__ ca, const int* __restrict__ cb,
                                                           int64_t split, double* __restrict__ part) {
-    __shared__ float bs[kDkTile][dev::kMaxD];
+    constexpr int U = 4;                         // independent accumulators (pairs in flight)
+    __shared__ float bs[kDkTile][DD];
     __shared__ float ws[kDkTile], wl[kDkTile];
     __shared__ int cs[kDkTile];
     const int64_t i = blockIdx.x * (int64_t)kDkRows + threadIdx.x;
     const bool act = i < m;
-    float ai[dev::kMaxD];
-    for (int j = 0; j < d; ++j) ai[j] = act ? a[i * d + j] : 0.f;
+    float ai[DD];
+#pragma unroll
+    for (int j = 0; j < DD; ++j) ai[j] = act ? a[i * DD + j] : 0.f;
     const int myc = (ca && act) ? ca[i] : -1;
     const int64_t j0 = blockIdx.y * split, j1 = min(n, j0 + split);
     double acc = 0.0;
     for (int64_t t0 = j0; t0 < j1; t0 += kDkTile) {
         const int nt = (int)min((int64_t)kDkTile, j1 - t0);
         __syncthreads();
-        for (int e = threadIdx.x; e < kDkTile * d; e += blockDim.x) {
-            const int r = e / d, q = e % d;
-            bs[r][q] = (r < nt) ? b[(t0 + r) * d + q] : 0.f;
+        for (int e = threadIdx.x; e < kDkTile * DD; e += blockDim.x) {
+            const int r = e / DD, q = e % DD;
+            bs[r][q] = (r < nt) ? b[(t0 + r) * DD + q] : 0.f;
         }
         for (int r = threadIdx.x; r < kDkTile; r += blockDim.x) {
             const double wv = (r < nt) ? w[t0 + r] : 0.0;
             const float hi = (float)wv;
             ws[r] = hi;
             wl[r] = (float)(wv - (double)hi);
-            cs[r] = (r < nt && cb) ? cb[t0 + r] : -2;
+            cs[r] = (r < nt && cb) ? cb[t0 + r] : -2;        // rows past the tile carry w = 0
         }
         __syncthreads();
-        float sh_ = 0.f, sl_ = 0.f;                  // tile sum as an unevaluated FP32 pair
-        for (int r = 0; r < nt; ++r) {
-            if (cs[r] == myc) continue;
-            float s = 0.f;
-            for (int q = 0; q < d; ++q) { const float t = ai[q] - bs[r][q]; s = fmaf(t, t, s); }
-            const float kv = kernel_value_f(kernel, sqrtf(s), inv_ell);
-            const float p = kv * ws[r];
-            const float e = fmaf(kv, wl[r], fmaf(kv, ws[r], -p));      // exact error of p, plus k w_lo
-            float t1, t2;
-            dev::two_sum(sh_, p, t1, t2);
-            sh_ = t1;
-            sl_ += t2 + e;
+        float sh_[U], sl_[U];                    // tile sums as unevaluated FP32 pairs
+#pragma unroll
+        for (int u = 0; u < U; ++u) sh_[u] = sl_[u] = 0.f;
+        const int ntu = (nt + U - 1) / U * U;    // the padded tail adds exact zeros (w = 0, k <= 1)
+        for (int r0 = 0; r0 < ntu; r0 += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u;
+                float s = 0.f;
+#pragma unroll
+                for (int q = 0; q < DD; ++q) { const float t = ai[q] - bs[r][q]; s = fmaf(t, t, s); }
+                float kv = kernel_value_f(kernel, sqrtf(s), inv_ell);
+                kv = (cs[r] == myc) ? 0.f : kv;
+                const float p = kv * ws[r];
+                const float e = fmaf(kv, wl[r], fmaf(kv, ws[r], -p));    // exact error of p, plus k w_lo
+                float t1, t2;
+                dev::two_sum(sh_[u], p, t1, t2);
+                sh_[u] = t1;
+                sl_[u] += t2 + e;
+            }
         }
-        acc += (double)sh_ + (double)sl_;
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += (double)sh_[u] + (double)sl_[u];
     }
     if (act) part[blockIdx.y * m + i] = acc;
+}
+
+// Launch of k_direct_kernel for the dimension d.
+void launch_direct(int d, dim3 g, cudaStream_t st, const float* a, int64_t m, const float* b, int64_t n, int kernel,
+                   float inv_ell, const double* w, const int* ca, const int* cb, int64_t split, double* part) {
+#define HDF_DK(DD) case DD: k_direct_kernel<DD><<<g, kDkRows, 0, st>>>(a, m, b, n, kernel, inv_ell, w, ca, cb, split, part); break;
+    switch (d) { HDF_DK(1) HDF_DK(2) HDF_DK(3) HDF_DK(4) HDF_DK(5) HDF_DK(6) HDF_DK(7) HDF_DK(8) }
+#undef HDF_DK
 }
 
 // out[i] = alpha v[i] + (add ? add[i] : 0) + sum_s part[s m + i]
@@ -279,40 +300,73 @@ __global__ void k_block_gemv(const double* __restrict__ inv, const int64_t* __re
     if (lane == 0) z[row] = s;
 }
 
-// In-place inverse of a symmetric positive definite matrix (row-major n x n) by Cholesky
-// A = L L^T, then L^-1 by forward substitution and A^-1 = L^-T L^-1.  False if A is not
-// positive definite to working precision.
-bool spd_inverse(int64_t n, double* A) {
-    std::vector<double> L((size_t)n * n, 0.0);
-    for (int64_t j = 0; j < n; ++j) {
-        double s = A[j * n + j];
-        for (int64_t q = 0; q < j; ++q) s -= L[j * n + q] * L[j * n + q];
-        if (!(s > 0.0)) return false;
-        const double ljj = std::sqrt(s);
-        L[j * n + j] = ljj;
-        for (int64_t i = j + 1; i < n; ++i) {
-            double t = A[i * n + j];
-            for (int64_t q = 0; q < j; ++q) t -= L[i * n + q] * L[j * n + q];
-            L[i * n + j] = t / ljj;
+// In-place inverse of a symmetric positive definite matrix (row-major n x n, both triangles
+// read from the lower one) by a blocked right-looking Cholesky A = L L^T (64-column panels:
+// the panel's rows below the diagonal block and the trailing update A22 -= L21 L21^T run on the
+// worker pool when par), then L^-1 one column at a time (forward substitution, stored
+// transposed so that every inner loop is a contiguous dot product) and A^-1 = L^-T L^-1.
+// False if A is not positive definite to working precision.
+bool spd_inverse(int64_t n, double* A, bool par) {
+    const int64_t NB = 64, RB = 16;
+    auto run = [&](int64_t cnt, const std::function<void(int64_t)>& fn) {
+        if (par && cnt > 1) parallel_for((int)cnt, [&](int t) { fn(t); });
+        else for (int64_t t = 0; t < cnt; ++t) fn(t);
+    };
+    auto dot = [](const double* a, const double* b, int64_t len) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t q = 0;
+        for (; q + 4 <= len; q += 4) { s0 += a[q] * b[q]; s1 += a[q + 1] * b[q + 1]; s2 += a[q + 2] * b[q + 2]; s3 += a[q + 3] * b[q + 3]; }
+        for (; q < len; ++q) s0 += a[q] * b[q];
+        return (s0 + s1) + (s2 + s3);
+    };
+    bool ok = true;
+    for (int64_t kb = 0; kb < n && ok; kb += NB) {
+        const int64_t ke = std::min(n, kb + NB);
+        for (int64_t k = kb; k < ke; ++k) {                    // diagonal block
+            double* Ak = A + k * n;
+            const double s = Ak[k] - dot(Ak + kb, Ak + kb, k - kb);
+            if (!(s > 0.0)) { ok = false; break; }
+            Ak[k] = std::sqrt(s);
+            for (int64_t i = k + 1; i < ke; ++i) {
+                double* Ai = A + i * n;
+                Ai[k] = (Ai[k] - dot(Ai + kb, Ak + kb, k - kb)) / Ak[k];
+            }
         }
+        if (!ok || ke == n) break;
+        const int64_t nt = n - ke, nrb = (nt + RB - 1) / RB;
+        run(nrb, [&](int64_t b) {                                // panel rows below the block
+            for (int64_t i = ke + b * RB; i < std::min(n, ke + (b + 1) * RB); ++i) {
+                double* Ai = A + i * n;
+                for (int64_t k = kb; k < ke; ++k) {
+                    const double* Ak = A + k * n;
+                    Ai[k] = (Ai[k] - dot(Ai + kb, Ak + kb, k - kb)) / Ak[k];
+                }
+            }
+        });
+        run(nrb, [&](int64_t b) {                                // A22 -= L21 L21^T (lower)
+            for (int64_t i = ke + b * RB; i < std::min(n, ke + (b + 1) * RB); ++i) {
+                double* Ai = A + i * n;
+                for (int64_t j = ke; j <= i; ++j) Ai[j] -= dot(Ai + kb, A + j * n + kb, ke - kb);
+            }
+        });
     }
-    // Linv (lower): solve L X = I column by column
-    std::vector<double> Li((size_t)n * n, 0.0);
-    for (int64_t c = 0; c < n; ++c) {
-        Li[c * n + c] = 1.0 / L[c * n + c];
-        for (int64_t i = c + 1; i < n; ++i) {
-            double t = 0.0;
-            for (int64_t q = c; q < i; ++q) t -= L[i * n + q] * Li[q * n + c];
-            Li[i * n + c] = t / L[i * n + i];
+    if (!ok) return false;
+    // T = (L^-1)^T: row c of T is column c of L^-1 (entries c..n-1)
+    std::vector<double> T((size_t)n * n, 0.0);
+    run((n + RB - 1) / RB, [&](int64_t b) {
+        for (int64_t c = b * RB; c < std::min(n, (b + 1) * RB); ++c) {
+            double* x = T.data() + c * n;
+            x[c] = 1.0 / A[c * n + c];
+            for (int64_t i = c + 1; i < n; ++i) x[i] = -dot(A + i * n + c, x + c, i - c) / A[i * n + i];
         }
-    }
-    // A^-1 = Linv^T Linv: (i, j) = sum_{q >= max(i, j)} Linv[q, i] Linv[q, j]
+    });
+    // A^-1[i][j] = sum_{q >= i} T[i][q] T[j][q], j <= i
+    run((n + RB - 1) / RB, [&](int64_t b) {
+        for (int64_t i = b * RB; i < std::min(n, (b + 1) * RB); ++i)
+            for (int64_t j = 0; j <= i; ++j) A[i * n + j] = dot(T.data() + i * n + i, T.data() + j * n + i, n - i);
+    });
     for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j <= i; ++j) {
-            double t = 0.0;
-            for (int64_t q = i; q < n; ++q) t += Li[q * n + i] * Li[q * n + j];
-            A[i * n + j] = A[j * n + i] = t;
-        }
+        for (int64_t j = i + 1; j < n; ++j) A[i * n + j] = A[j * n + i];
     return true;
 }
 
@@ -352,9 +406,8 @@ hdf_status apply_perm(hdf_krr* K, const double* vp, double* tp, cudaStream_t st)
     }
     dim3 g((unsigned)((n + kDkRows - 1) / kDkRows), (unsigned)K->S);
     HDF_COUNT_LAUNCH();
-    k_direct_kernel<<<g, kDkRows, 0, st>>>(K->xp32.as<float>(), n, K->xp32.as<float>(), n, K->d, K->kernel,
-                                           (float)(1.0 / K->ell), vp, K->cl.as<int>(), K->cl.as<int>(), K->split,
-                                           K->part.as<double>());
+    launch_direct(K->d, g, st, K->xp32.as<float>(), n, K->xp32.as<float>(), n, K->kernel, (float)(1.0 / K->ell), vp,
+                  K->cl.as<int>(), K->cl.as<int>(), K->split, K->part.as<double>());
     HDF_COUNT_LAUNCH();
     k_direct_finish<<<gb, 256, 0, st>>>(K->part.as<double>(), K->S, n, K->lam, vp, K->hd.as<double>(), tp);
     HDF_CUDA(cudaGetLastError());
@@ -456,8 +509,8 @@ hdf_status hdf_kernel_matvec(const double* xq_dev, int64_t m, const double* x_de
     HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)S * m, st));
     dim3 g((unsigned)((m + kDkRows - 1) / kDkRows), (unsigned)S);
     HDF_COUNT_LAUNCH();
-    k_direct_kernel<<<g, kDkRows, 0, st>>>(a.as<float>(), m, b.as<float>(), n, d, kernel, (float)(1.0 / lengthscale),
-                                           w_dev, nullptr, nullptr, split, part.as<double>());
+    launch_direct(d, g, st, a.as<float>(), m, b.as<float>(), n, kernel, (float)(1.0 / lengthscale), w_dev, nullptr,
+                  nullptr, split, part.as<double>());
     HDF_COUNT_LAUNCH();
     k_direct_finish<<<blocks_for(m, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), S, m, 0.0, nullptr, nullptr,
                                                                  out_dev);
@@ -551,9 +604,18 @@ hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* label
     std::vector<double> hinv(K->ioff.back());
     KRR_CUDA(cudaMemcpyAsync(hinv.data(), K->inv.p, sizeof(double) * hinv.size(), cudaMemcpyDeviceToHost, st));
     KRR_CUDA(cudaStreamSynchronize(st));
+    // clusters of 256 points or more one at a time with the work of each spread over the pool
+    // (largest first), the smaller ones side by side
     std::vector<char> ok(K->nclus, 1);
-    parallel_for(K->nclus, [&](int c) {
-        ok[c] = spd_inverse(K->offs[c + 1] - K->offs[c], hinv.data() + K->ioff[c]) ? 1 : 0;
+    std::vector<int> big, small;
+    for (int c = 0; c < K->nclus; ++c) (K->offs[c + 1] - K->offs[c] >= 256 ? big : small).push_back(c);
+    std::sort(big.begin(), big.end(), [&](int a, int b) {
+        return K->offs[a + 1] - K->offs[a] > K->offs[b + 1] - K->offs[b];
+    });
+    for (int c : big) ok[c] = spd_inverse(K->offs[c + 1] - K->offs[c], hinv.data() + K->ioff[c], true) ? 1 : 0;
+    parallel_for((int)small.size(), [&](int t) {
+        const int c = small[t];
+        ok[c] = spd_inverse(K->offs[c + 1] - K->offs[c], hinv.data() + K->ioff[c], false) ? 1 : 0;
     });
     for (int c = 0; c < K->nclus; ++c)
         if (!ok[c]) return bail(fail(HDF_ESINGULAR, "hdf_krr_build: a block lambda I + K_cc is not positive definite"));
