@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--p-max", type=int, default=64)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--nsets", type=int, default=None, help="batch512_gauss: number of sets (default 512)")
     ap.add_argument("--cpu-n", type=int, default=12000, help="oracle sample size")
     return ap.parse_args()
 
@@ -556,7 +557,7 @@ def bench_batch(args):
     ws, rank, dev = _setup(args)
     w = workload_params(args)
     c, d = w["ncols"], w["d"]
-    xb, off, ells = W.batch_sets(W.rng(w["idx"]), nsets=w["nsets"], d=d)
+    xb, off, ells = W.batch_sets(W.rng(w["idx"]), nsets=args.nsets or w["nsets"], d=d)
     N = int(off[-1])
     x = torch.from_numpy(xb).to(dev)
     V_np = W.rng(w["idx"] + 100).standard_normal((c, N)).astype(np.float32)     # column-major N x c

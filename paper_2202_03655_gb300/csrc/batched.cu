@@ -119,33 +119,39 @@ __global__ void k_seg_maxnorm(const double* __restrict__ x, int d, const SegItem
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// rows: (set, t) pairs; part[row] = sum_u k(|x_idx(t) - x_idx(u)|)^2 over the set's subsample
 // Sum over pairs i < j of K(x_i, x_j)^2 for sample rows i in [32 t, 32 t + 32) of set s
 // (item (s, t)); the set's m strided sample points are staged in shared memory.  The host adds
-// the diagonal m k(0)^2 and doubles nothing: part holds 2 x the half sum.
+// the diagonal m k(0)^2 and doubles nothing: part holds 2 x the half sum.  mu2 only sets the
+// two error budgets, so the pairs run on the FP32 pipe (GB300's FP64 rate is a small fraction
+// of it): coordinates relative to the set's centre (differences in FP64, then FP32), FP32
+// kernel values (relative error ~1e-7), each thread's sum over one row in FP32 and the rest in
+// FP64.
 constexpr int kMu2Rows = 32;
 __global__ void __launch_bounds__(256) k_seg_mu2_pairs(const double* __restrict__ x, int d,
                                                        const int2* __restrict__ items,
                                                        const SetGeom* __restrict__ geo, int kernel,
                                                        double* __restrict__ part) {
-    __shared__ double xs[kMu2Sample * dev::kMaxD];
+    __shared__ float xs[kMu2Sample * dev::kMaxD];
     __shared__ double sh[256];
     const int2 it = items[blockIdx.x];
     const SetGeom& g = geo[it.x];
     for (int u = threadIdx.x; u < g.m; u += blockDim.x) {
         const int64_t jj = g.off + ((int64_t)u * g.n) / g.m;
-        for (int j = 0; j < d; ++j) xs[u * d + j] = x[jj * d + j];
+        for (int j = 0; j < d; ++j) xs[u * d + j] = (float)(x[jj * d + j] - g.c[j]);
     }
     __syncthreads();
+    const float inv_ell = (float)(1.0 / g.ell);
     double acc = 0.0;
     const int r0 = it.y * kMu2Rows, r1 = min(g.m, r0 + kMu2Rows);
     for (int i = r0; i < r1; ++i) {
+        float row = 0.f;
         for (int u = i + 1 + threadIdx.x; u < g.m; u += blockDim.x) {
-            double s2 = 0.0;
-            for (int j = 0; j < d; ++j) { const double y = xs[i * d + j] - xs[u * d + j]; s2 += y * y; }
-            const double kv = dev::kernel_value(kernel, sqrt(s2), g.ell);
-            acc += kv * kv;
+            float s2 = 0.f;
+            for (int j = 0; j < d; ++j) { const float y = xs[i * d + j] - xs[u * d + j]; s2 = fmaf(y, y, s2); }
+            const float kv = dev::kernel_value_f(kernel, sqrtf(s2), inv_ell);
+            row = fmaf(kv, kv, row);
         }
+        acc += (double)row;
     }
     const double tot = dev::block_sum_256(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * tot;
@@ -1081,9 +1087,9 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         const int ct = ct_for(c);
         const bool skinny = sizeof(T) == 4 && ct <= 16;
         int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
-        if (skinny) {
-            AB = 32 * (ct <= 8 ? 4 : 2);
-            RB = 8 * (ct <= 8 ? 4 : 2);
+        if (skinny) {                     // the streaming kernels' columns / rows per item
+            AB = (ct <= 8) ? SkinnyShape<8>::AB : SkinnyShape<16>::AB;
+            RB = (ct <= 8) ? SkinnyShape<8>::RB : SkinnyShape<16>::RB;
         }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);

@@ -31,6 +31,17 @@ __device__ __forceinline__ double kernel_value(int kernel, double r, double ell)
     }
 }
 
+// The same kernels in FP32 (r >= 0, inv_ell = 1 / l); values <= 1.
+__device__ __forceinline__ float kernel_value_f(int kernel, float r, float inv_ell) {
+    const float z = r * inv_ell;
+    switch (kernel) {
+        case 0: return expf(-0.5f * z * z);
+        case 1: return 1.0f / (1.0f + z * z);
+        case 2: { const float s = 1.7320508f * z; return (1.0f + s) * expf(-s); }
+        default: { const float s = 2.2360680f * z; return (1.0f + s + s * s * (1.0f / 3.0f)) * expf(-s); }
+    }
+}
+
 // Deterministic tree sum of one double per thread over the block (blockDim = 256).
 __device__ __forceinline__ double block_sum_256(double v, double* sh) {
     sh[threadIdx.x] = v;

@@ -97,16 +97,6 @@ __global__ void k_gather_rows(const double* __restrict__ x, int d, const int64_t
 }
 
 // --------------------------------------------------------- direct kernel evaluation
-__device__ __forceinline__ float kernel_value_f(int kernel, float r, float inv_ell) {
-    const float z = r * inv_ell;
-    switch (kernel) {
-        case 0: return expf(-0.5f * z * z);
-        case 1: return 1.0f / (1.0f + z * z);
-        case 2: { const float s = 1.7320508f * z; return (1.0f + s) * expf(-s); }
-        default: { const float s = 2.2360680f * z; return (1.0f + s + s * s * (1.0f / 3.0f)) * expf(-s); }
-    }
-}
-
 constexpr int kDkRows = 128;     // rows (outputs) per block
 constexpr int kDkTile = 128;     // columns staged per tile
 
@@ -161,7 +151,7 @@ __global__ void __launch_bounds__(kDkRows) k_direct_kernel(const float* __restri
                 float s = 0.f;
 #pragma unroll
                 for (int q = 0; q < DD; ++q) { const float t = ai[q] - bs[r][q]; s = fmaf(t, t, s); }
-                float kv = kernel_value_f(kernel, sqrtf(s), inv_ell);
+                float kv = dev::kernel_value_f(kernel, sqrtf(s), inv_ell);
                 kv = (cs[r] == myc) ? 0.f : kv;
                 const float p = kv * ws[r];
                 const float e = fmaf(kv, wl[r], fmaf(kv, ws[r], -p));    // exact error of p, plus k w_lo
