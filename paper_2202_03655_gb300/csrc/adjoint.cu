@@ -104,18 +104,36 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
     T* try_ = trx + 2 * P.L + 1;               // d/dx1
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
     for (int64_t i = gw; i < P.n; i += nw) {
-        double xh[kMaxD];
+        T xh[kMaxD];
         double s2 = 0.0;
+        if constexpr (sizeof(T) == 4) {
+            // lane j forms coordinate j in FP64 once; |x'|^2 by an FP64 shuffle tree over the
+            // first eight lanes; the warp shares the coordinates in FP32 (FP64 issues at a small
+            // fraction of the FP32 rate on this GPU)
+            double xd = 0.0;
 #pragma unroll
-        for (int j = 0; j < DD; ++j) { xh[j] = (P.x[i * DD + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
+            for (int j = 0; j < DD; ++j)
+                if (lane == j) xd = (P.x[i * DD + j] - P.c[j]) * P.inv2R;
+            double sq = xd * xd;
+            sq += __shfl_xor_sync(0xffffffffu, sq, 4);
+            sq += __shfl_xor_sync(0xffffffffu, sq, 2);
+            sq += __shfl_xor_sync(0xffffffffu, sq, 1);
+            s2 = __shfl_sync(0xffffffffu, sq, 0);
+            const float xf = (float)xd;
+#pragma unroll
+            for (int j = 0; j < DD; ++j) xh[j] = __shfl_sync(0xffffffffu, xf, j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < DD; ++j) { xh[j] = (P.x[i * DD + j] - P.c[j]) * P.inv2R; s2 += xh[j] * xh[j]; }
+        }
         double rho;
         if constexpr (sizeof(T) == 4) {
             // FP32 factors: the radial part in double-float / FP32 arithmetic (FP64 is slow here)
             const float s2f = (float)s2;
             const float rhof = sqrtf(s2f);
             rho = rhof;
-            if (s2 > 0.0) { const double inv = 1.0 / (double)rhof; for (int j = 0; j < DD; ++j) xh[j] *= inv; }
-            else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+            if (s2 > 0.0) { const float inv = 1.f / rhof; for (int j = 0; j < DD; ++j) xh[j] *= inv; }
+            else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? 1.f : 0.f; }
             float2* Tl2 = reinterpret_cast<float2*>(Tl);
             float2* dTl2 = reinterpret_cast<float2*>(dTl);
             float* Qf = reinterpret_cast<float*>(Q);
@@ -173,8 +191,8 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             }
         } else {
         rho = sqrt(s2);
-        if (s2 > 0.0) { for (int j = 0; j < DD; ++j) xh[j] /= rho; }
-        else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? 1.0 : 0.0; }
+        if (s2 > 0.0) { for (int j = 0; j < DD; ++j) xh[j] = (T)(xh[j] / rho); }
+        else { for (int j = 0; j < DD; ++j) xh[j] = (j == 0) ? (T)1 : (T)0; }
         const double u = 8.0 * s2 - 1.0;
         if (lane == 0) {
             Tl[0] = 1.0; dTl[0] = 0.0;
@@ -228,11 +246,11 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
         // level tables with d/dz and d/dq
         for (int j = 0; j < levels; ++j) {
             const int D = DD - 1 - j;
-            double q = 0.0;
+            T q = (T)0;
 #pragma unroll
             for (int m = 0; m < DD; ++m)
                 if (m <= D) q += xh[m] * xh[m];
-            const T z = (T)xh[D], qq = (T)q;
+            const T z = xh[D], qq = q;
             const T* A = P.coefA + j * P.tri;
             const T* B = P.coefB + j * P.tri;
             T* pv = tv + j * P.tri;

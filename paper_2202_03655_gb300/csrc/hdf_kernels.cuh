@@ -664,11 +664,21 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
     constexpr int VW = Vec2<T>::w;
-    // direction x_hat, zero vector -> e_0.  The differences are taken in FP64; the normalisation
-    // runs in the bulk precision T (every lane computes it, and FP64 is slow on this GPU).
+    // direction x_hat, zero vector -> e_0.  The differences are taken in FP64 and the
+    // normalisation in the bulk precision T.  FP32 factors: lane j forms coordinate j once and
+    // the warp shares it by shuffles (FP64 issues at a small fraction of the FP32 rate here).
     T xh[kMaxD];
     T s = (T)0;
-    for (int j = 0; j < P.d; ++j) { xh[j] = (T)((P.x[i * P.d + j] - P.c.c[j]) * P.inv2R); s += xh[j] * xh[j]; }
+    if constexpr (sizeof(T) == 4) {
+        double xd = 0.0;
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j)
+            if (j < P.d && lane == j) xd = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R;
+        const float xf = (float)xd;
+        for (int j = 0; j < P.d; ++j) { xh[j] = __shfl_sync(0xffffffffu, xf, j); s += xh[j] * xh[j]; }
+    } else {
+        for (int j = 0; j < P.d; ++j) { xh[j] = (T)((P.x[i * P.d + j] - P.c.c[j]) * P.inv2R); s += xh[j] * xh[j]; }
+    }
     if (s > (T)0) {
         const T inv = (T)1 / sqrt(s);
         for (int j = 0; j < P.d; ++j) xh[j] *= inv;
