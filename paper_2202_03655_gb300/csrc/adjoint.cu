@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             // lane j forms coordinate j in FP64 once; |x'|^2 by an FP64 shuffle tree over the
             // first eight lanes; the warp shares the coordinates in FP32 (FP64 issues at a small
             // fraction of the FP32 rate on this GPU)
-            double xd = 0.0;
+            double cj = P.c[0];                  // this lane's centre coordinate (register selects)
 #pragma unroll
-            for (int j = 0; j < DD; ++j)
-                if (lane == j) xd = (P.x[i * DD + j] - P.c[j]) * P.inv2R;
+            for (int j = 1; j < DD; ++j) cj = (lane == j) ? P.c[j] : cj;
+            const double xd = (lane < DD) ? (P.x[i * DD + lane] - cj) * P.inv2R : 0.0;   // one FP64 sub, mul
             double sq = xd * xd;
             sq += __shfl_xor_sync(0xffffffffu, sq, 4);
             sq += __shfl_xor_sync(0xffffffffu, sq, 2);

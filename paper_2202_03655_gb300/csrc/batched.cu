@@ -261,7 +261,7 @@ inline size_t batch_df_tile_smem(int L, int m0, int m1) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_batch_build(const BuildSet* __restrict__ sets, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256) k_batch_build(const BuildSet* __restrict__ sets, const int2* __restrict__ items,
                                                      int nitems, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;

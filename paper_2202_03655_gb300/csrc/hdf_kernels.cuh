@@ -670,10 +670,10 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
     T xh[kMaxD];
     T s = (T)0;
     if constexpr (sizeof(T) == 4) {
-        double xd = 0.0;
+        double cj = P.c.c[0];                    // this lane's centre coordinate (register selects)
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j)
-            if (j < P.d && lane == j) xd = (P.x[i * P.d + j] - P.c.c[j]) * P.inv2R;
+        for (int j = 1; j < kMaxD; ++j) cj = (lane == j) ? P.c.c[j] : cj;
+        const double xd = (lane < P.d) ? (P.x[i * P.d + lane] - cj) * P.inv2R : 0.0;   // one FP64 sub, mul
         const float xf = (float)xd;
         for (int j = 0; j < P.d; ++j) { xh[j] = __shfl_sync(0xffffffffu, xf, j); s += xh[j] * xh[j]; }
     } else {
