@@ -574,6 +574,235 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
     }
 }
 
+// ------------------------------------------------ pipelined streaming kernels (c <= 8)
+// The loads of the streaming kernels above land in registers, which caps the bytes a SM keeps
+// in flight well below what HBM latency needs.  These variants stream U through a per-warp
+// ring of shared-memory stages filled by cp.async (16 bytes per lane, zero fill outside the
+// set), NS tiles ahead of the arithmetic, so that registers hold only sums.
+constexpr int kPipeStages = 4;      // tiles in flight per warp
+constexpr int kPipeRows = 4;        // rows per tile
+constexpr int kPipeCols = 128;      // columns per tile (4 per lane)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// floats of one U^T V stage: the U tile, then its kPipeRows x CT values of V
+template <int CT> constexpr int utv_stage_floats() { return kPipeRows * kPipeCols + kPipeRows * CT; }
+template <int CT> constexpr size_t utv_pipe_smem() {
+    return sizeof(float) * (size_t)8 * kPipeStages * utv_stage_floats<CT>();
+}
+
+// Partial sums of U^T V as k_batch_utv_s (same items: set, 4096-row chunk, 128-column block).
+// Warp w takes the row groups i0 + 4 (w + 8 t) .. + 3; each stage holds such a group's U tile and
+// its V rows.  The eight warps' sums are added in warp order through shared memory that
+// reuses the drained ring.
+template <int CT>
+__global__ void __launch_bounds__(256) k_batch_utv_p(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                     int nitems, int* counter, const float* __restrict__ V,
+                                                     int64_t ldv, int c) {
+    static_assert(kPipeRows * CT <= 32, "one V value per lane and stage");
+    constexpr int SF = utv_stage_floats<CT>();
+    extern __shared__ __align__(16) float smp[];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* ring = smp + (size_t)warp * kPipeStages * SF;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        const float* U = reinterpret_cast<const float*>(S.U);
+        const int64_t i0 = (int64_t)w.chunk * S.chunk, i1 = min(S.n, i0 + S.chunk);
+        const int64_t a0 = w.blk * kPipeCols, a = a0 + 4 * lane;
+        const bool act = a < S.r;                     // S.r is a multiple of 4 (padded width)
+        const int ntiles = (int)((i1 - i0 + kPipeRows * 8 - 1) / (kPipeRows * 8));
+        auto issue = [&](int t) {
+            float* st = ring + (t % kPipeStages) * SF;
+            const int64_t rb = i0 + (int64_t)kPipeRows * (warp + 8 * t);
+#pragma unroll
+            for (int q = 0; q < kPipeRows; ++q) {
+                const int64_t i = rb + q;
+                const bool ok = act && i < i1;
+                cp_async16(st + q * kPipeCols + 4 * lane, ok ? (const void*)(U + i * S.ldU + a) : (const void*)U,
+                           ok ? 16 : 0);
+            }
+            if (lane < kPipeRows * CT) {
+                const int q = lane / CT, j = lane % CT;
+                const int64_t i = rb + q;
+                const bool ok = i < i1 && j < c;
+                cp_async4(st + kPipeRows * kPipeCols + lane, ok ? (const void*)(V + S.off + i + (int64_t)j * ldv)
+                                                                : (const void*)V, ok ? 4 : 0);
+            }
+        };
+        float acc[4][CT];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) acc[q][j] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kPipeStages - 1; ++t) {
+            if (t < ntiles) issue(t);
+            cp_commit();
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            if (t + kPipeStages - 1 < ntiles) issue(t + kPipeStages - 1);
+            cp_commit();
+            cp_wait<kPipeStages - 1>();
+            __syncwarp();
+            const float* st = ring + (t % kPipeStages) * SF;
+#pragma unroll
+            for (int q = 0; q < kPipeRows; ++q) {
+                const float4 u = *reinterpret_cast<const float4*>(st + q * kPipeCols + 4 * lane);
+                const float* vq = st + kPipeRows * kPipeCols + q * CT;
+#pragma unroll
+                for (int j = 0; j < CT; ++j) {
+                    const float v = vq[j];
+                    acc[0][j] = fmaf(u.x, v, acc[0][j]);
+                    acc[1][j] = fmaf(u.y, v, acc[1][j]);
+                    acc[2][j] = fmaf(u.z, v, acc[2][j]);
+                    acc[3][j] = fmaf(u.w, v, acc[3][j]);
+                }
+            }
+            __syncwarp();                              // the stage is refilled next iteration
+        }
+        cp_wait<0>();
+        __syncthreads();                               // every warp's ring drained: reuse it
+        float* red = smp;                              // [8][kPipeCols][CT]
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < CT; ++j) red[((size_t)warp * kPipeCols + 4 * lane + q) * CT + j] = acc[q][j];
+        __syncthreads();
+        for (int e = threadIdx.x; e < kPipeCols * CT; e += blockDim.x) {
+            const int col = e / CT, j = e % CT;
+            float sum = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) sum += red[((size_t)ww * kPipeCols + col) * CT + j];
+            const int64_t aa = a0 + col;
+            if (aa < S.r && j < c) S.part[((int64_t)w.chunk * c + j) * S.r + aa] = (double)sum;
+        }
+        __syncthreads();
+    }
+}
+
+template <int CT> constexpr int uw_red_floats() { return 32 * (kPipeRows * CT + 1); }
+template <int CT> constexpr size_t uw_pipe_smem() {
+    return sizeof(float) * (size_t)8 * (kPipeStages * kPipeRows * kPipeCols + uw_red_floats<CT>());
+}
+
+// Y = U W as k_batch_uw_s (same items: set, 128-row block; each warp G groups of 4 rows).  The
+// warp's tiles (group, 128-column pass) stream through its ring; W rows are read from L1/L2;
+// a group's 4 x CT sums are reduced across the warp through its own shared-memory slice.
+template <int CT>
+__global__ void __launch_bounds__(256) k_batch_uw_p(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
+                                                    int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
+                                                    int c) {
+    constexpr int R = kPipeRows, G = 4, NO = R * CT;
+    constexpr int TF = kPipeRows * kPipeCols;      // floats per stage
+    static_assert(NO <= 32, "one output per lane");
+    extern __shared__ __align__(16) float smp[];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* ring = smp + (size_t)warp * (kPipeStages * TF + uw_red_floats<CT>());
+    float* red = ring + kPipeStages * TF;          // [32][NO + 1]
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const MvItem w = items[it];
+        const MvSet& S = sets[w.set];
+        const float* U = reinterpret_cast<const float*>(S.U);
+        const float* W = reinterpret_cast<const float*>(S.W);
+        const int npass = (int)((S.r + kPipeCols - 1) / kPipeCols);
+        const int ntiles = G * npass;                   // tile t: group t / npass, pass t % npass
+        auto rows0 = [&](int g) { return w.blk * (int64_t)(8 * R * G) + ((int64_t)g * 8 + warp) * R; };
+        auto issue = [&](int t) {
+            float* st = ring + (t % kPipeStages) * TF;
+            const int g = t / npass, ps = t % npass;
+            const int64_t row0 = rows0(g), a = (int64_t)ps * kPipeCols + 4 * lane;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int64_t i = row0 + q;
+                const bool ok = i < S.n && a < S.r;
+                cp_async16(st + q * kPipeCols + 4 * lane, ok ? (const void*)(U + i * S.ldU + a) : (const void*)U,
+                           ok ? 16 : 0);
+            }
+        };
+#pragma unroll
+        for (int t = 0; t < kPipeStages - 1; ++t) {
+            if (t < ntiles) issue(t);
+            cp_commit();
+        }
+        float acc[R][CT];
+        for (int t = 0; t < ntiles; ++t) {
+            const int g = t / npass, ps = t % npass;
+            if (ps == 0) {
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+#pragma unroll
+                    for (int j = 0; j < CT; ++j) acc[q][j] = 0.f;
+            }
+            if (t + kPipeStages - 1 < ntiles) issue(t + kPipeStages - 1);
+            cp_commit();
+            cp_wait<kPipeStages - 1>();
+            __syncwarp();
+            const float* st = ring + (t % kPipeStages) * TF;
+            const int64_t a = (int64_t)ps * kPipeCols + 4 * lane;
+            if (a < S.r) {
+                float u[R][4];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(st + q * kPipeCols + 4 * lane);
+                    u[q][0] = v4.x; u[q][1] = v4.y; u[q][2] = v4.z; u[q][3] = v4.w;
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float wv[CT];
+                    ld_row<CT>(W + (a + e) * CT, wv);
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+#pragma unroll
+                        for (int j = 0; j < CT; ++j) acc[q][j] = fmaf(u[q][e], wv[j], acc[q][j]);
+                }
+            }
+            __syncwarp();                              // the stage is refilled next iteration
+            if (ps == npass - 1) {                     // group done: reduce over the lanes
+                const int64_t row0 = rows0(g);
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+#pragma unroll
+                    for (int j = 0; j < CT; ++j) red[lane * (NO + 1) + q * CT + j] = acc[q][j];
+                __syncwarp();
+                if (lane < NO) {
+                    float v = 0.f;
+#pragma unroll 8
+                    for (int l2 = 0; l2 < 32; ++l2) v += red[l2 * (NO + 1) + lane];
+                    const int q = lane / CT, j = lane % CT;
+                    const int64_t i = row0 + q;
+                    if (i < S.n && j < c) Y[S.off + i + (int64_t)j * ldy] = v;
+                }
+                __syncwarp();
+            }
+        }
+        cp_wait<0>();
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ autotuner
 std::mutex g_tune_mu;
 
@@ -1145,11 +1374,19 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             switch (ct) {
 #define HDF_B_OCC(CT)                                                                                             \
     case CT:                                                                                                      \
-        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_s<CT>, 256, 0));               \
-        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<CT>, 256, 0));                \
+        HDF_CUDA(cudaFuncSetAttribute(k_batch_utv_p<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                      (int)utv_pipe_smem<CT>()));                                                 \
+        HDF_CUDA(cudaFuncSetAttribute(k_batch_uw_p<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                      (int)uw_pipe_smem<CT>()));                                                  \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_p<CT>, 256, utv_pipe_smem<CT>())); \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_p<CT>, 256, uw_pipe_smem<CT>()));  \
         break;
-                HDF_B_OCC(1) HDF_B_OCC(2) HDF_B_OCC(4) HDF_B_OCC(8) HDF_B_OCC(16)
+                HDF_B_OCC(1) HDF_B_OCC(2) HDF_B_OCC(4) HDF_B_OCC(8)
 #undef HDF_B_OCC
+                case 16:
+                    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_s<16>, 256, 0));
+                    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<16>, 256, 0));
+                    break;
             }
         }
         HDF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -1158,18 +1395,21 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         int* cnt = b->counters.as<int>();
         if (skinny) {
             switch (ct) {
-#define HDF_B_SK(CT)                                                                                              \
+#define HDF_B_SK(CT, UTV, UW, SU, SW)                                                                             \
     case CT:                                                                                                      \
         if (b->n_utv)                                                                                             \
-            k_batch_utv_s<CT><<<nsm * std::max(occ_u, 1), 256, 0, b->cap>>>(                                      \
+            UTV<<<nsm * std::max(occ_u, 1), 256, SU, b->cap>>>(                                                   \
                 S, b->mvitems_utv.as<MvItem>(), b->n_utv, cnt, reinterpret_cast<const float*>(V), ldv, c);        \
         if (b->n_red) k_batch_reduce<T><<<b->n_red, 256, 0, b->cap>>>(S, b->mvitems_red.as<MvItem>(), c);          \
         if (b->n_uw)                                                                                              \
-            k_batch_uw_s<CT><<<nsm * std::max(occ_w, 1), 256, 0, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw, \
-                                                                         cnt + 1, reinterpret_cast<float*>(Y),    \
-                                                                         ldy, c);                                 \
+            UW<<<nsm * std::max(occ_w, 1), 256, SW, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw, cnt + 1,     \
+                                                            reinterpret_cast<float*>(Y), ldy, c);                 \
         break;
-                HDF_B_SK(1) HDF_B_SK(2) HDF_B_SK(4) HDF_B_SK(8) HDF_B_SK(16)
+                HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_p<1>, utv_pipe_smem<1>(), uw_pipe_smem<1>())
+                HDF_B_SK(2, k_batch_utv_p<2>, k_batch_uw_p<2>, utv_pipe_smem<2>(), uw_pipe_smem<2>())
+                HDF_B_SK(4, k_batch_utv_p<4>, k_batch_uw_p<4>, utv_pipe_smem<4>(), uw_pipe_smem<4>())
+                HDF_B_SK(8, k_batch_utv_p<8>, k_batch_uw_p<8>, utv_pipe_smem<8>(), uw_pipe_smem<8>())
+                HDF_B_SK(16, k_batch_utv_s<16>, k_batch_uw_s<16>, 0, 0)
 #undef HDF_B_SK
             }
         } else
