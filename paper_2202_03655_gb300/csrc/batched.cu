@@ -582,6 +582,8 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
 constexpr int kPipeStages = 4;      // tiles in flight per warp
 constexpr int kPipeRows = 4;        // rows per tile
 constexpr int kPipeCols = 128;      // columns per tile (4 per lane)
+constexpr int kPipeGroups = 16;     // U W: row groups per warp and item (512 rows per item), so that
+                                    // the ring's start-up latency is paid once per 64 tiles
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -702,14 +704,14 @@ template <int CT> constexpr size_t uw_pipe_smem() {
     return sizeof(float) * (size_t)8 * (kPipeStages * kPipeRows * kPipeCols + uw_red_floats<CT>());
 }
 
-// Y = U W as k_batch_uw_s (same items: set, 128-row block; each warp G groups of 4 rows).  The
+// Y = U W for items of 512 rows of one set (each warp kPipeGroups groups of 4 rows).  The
 // warp's tiles (group, 128-column pass) stream through its ring; W rows are read from L1/L2;
 // a group's 4 x CT sums are reduced across the warp through its own shared-memory slice.
 template <int CT>
 __global__ void __launch_bounds__(256) k_batch_uw_p(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
                                                     int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
                                                     int c) {
-    constexpr int R = kPipeRows, G = 4, NO = R * CT;
+    constexpr int R = kPipeRows, G = kPipeGroups, NO = R * CT;
     constexpr int TF = kPipeRows * kPipeCols;      // floats per stage
     static_assert(NO <= 32, "one output per lane");
     extern __shared__ __align__(16) float smp[];
@@ -1317,8 +1319,8 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         const bool skinny = sizeof(T) == 4 && ct <= 16;
         int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
         if (skinny) {                     // the streaming kernels' columns / rows per item
-            AB = (ct <= 8) ? SkinnyShape<8>::AB : SkinnyShape<16>::AB;
-            RB = (ct <= 8) ? SkinnyShape<8>::RB : SkinnyShape<16>::RB;
+            AB = (ct <= 8) ? kPipeCols : SkinnyShape<16>::AB;
+            RB = (ct <= 8) ? 8 * kPipeRows * kPipeGroups : SkinnyShape<16>::RB;
         }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
