@@ -62,7 +62,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # 200,000-point case of the default workload (dram__bytes_read.sum + dram__bytes_write.sum over
 # n * ldU); the roofline's traffic is this figure scaled to the timed launch.  Set an entry to
 # None when its kernel changes, until it is captured again.
-TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1659, "k_tc_utv": 4.1502, "k_tc_uw": 4.0656}
+TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1663, "k_tc_utv": 4.1500, "k_tc_uw": 4.0655}
 METRICS = {
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",

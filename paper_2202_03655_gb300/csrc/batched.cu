@@ -574,16 +574,16 @@ __global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ se
     }
 }
 
-// ------------------------------------------------ pipelined streaming kernels (c <= 8)
-// The loads of the streaming kernels above land in registers, which caps the bytes a SM keeps
-// in flight well below what HBM latency needs.  These variants stream U through a per-warp
-// ring of shared-memory stages filled by cp.async (16 bytes per lane, zero fill outside the
-// set), NS tiles ahead of the arithmetic, so that registers hold only sums.
+// ------------------------------------------------ pipelined U^T V (c <= 8)
+// The loads of k_batch_utv_s land in registers, which caps the bytes a SM keeps in flight
+// well below what HBM latency needs.  This variant streams U through a per-warp ring of
+// shared-memory stages filled by cp.async (16 bytes per lane, zero fill outside the set),
+// three tiles ahead of the arithmetic, so that registers hold only sums.  (The same ring for
+// U W measured slower than k_batch_uw_s: its shared memory leaves L1 too small to keep the
+// set's W resident, and every W read then waits on L2.)
 constexpr int kPipeStages = 4;      // tiles in flight per warp
 constexpr int kPipeRows = 4;        // rows per tile
 constexpr int kPipeCols = 128;      // columns per tile (4 per lane)
-constexpr int kPipeGroups = 16;     // U W: row groups per warp and item (512 rows per item), so that
-                                    // the ring's start-up latency is paid once per 64 tiles
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -696,112 +696,6 @@ __global__ void __launch_bounds__(256) k_batch_utv_p(const MvSet* __restrict__ s
             if (aa < S.r && j < c) S.part[((int64_t)w.chunk * c + j) * S.r + aa] = (double)sum;
         }
         __syncthreads();
-    }
-}
-
-template <int CT> constexpr int uw_red_floats() { return 32 * (kPipeRows * CT + 1); }
-template <int CT> constexpr size_t uw_pipe_smem() {
-    return sizeof(float) * (size_t)8 * (kPipeStages * kPipeRows * kPipeCols + uw_red_floats<CT>());
-}
-
-// Y = U W for items of 512 rows of one set (each warp kPipeGroups groups of 4 rows).  The
-// warp's tiles (group, 128-column pass) stream through its ring; W rows are read from L1/L2;
-// a group's 4 x CT sums are reduced across the warp through its own shared-memory slice.
-template <int CT>
-__global__ void __launch_bounds__(256) k_batch_uw_p(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
-                                                    int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
-                                                    int c) {
-    constexpr int R = kPipeRows, G = kPipeGroups, NO = R * CT;
-    constexpr int TF = kPipeRows * kPipeCols;      // floats per stage
-    static_assert(NO <= 32, "one output per lane");
-    extern __shared__ __align__(16) float smp[];
-    __shared__ int s_item;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* ring = smp + (size_t)warp * (kPipeStages * TF + uw_red_floats<CT>());
-    float* red = ring + kPipeStages * TF;          // [32][NO + 1]
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= nitems) break;
-        const MvItem w = items[it];
-        const MvSet& S = sets[w.set];
-        const float* U = reinterpret_cast<const float*>(S.U);
-        const float* W = reinterpret_cast<const float*>(S.W);
-        const int npass = (int)((S.r + kPipeCols - 1) / kPipeCols);
-        const int ntiles = G * npass;                   // tile t: group t / npass, pass t % npass
-        auto rows0 = [&](int g) { return w.blk * (int64_t)(8 * R * G) + ((int64_t)g * 8 + warp) * R; };
-        auto issue = [&](int t) {
-            float* st = ring + (t % kPipeStages) * TF;
-            const int g = t / npass, ps = t % npass;
-            const int64_t row0 = rows0(g), a = (int64_t)ps * kPipeCols + 4 * lane;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int64_t i = row0 + q;
-                const bool ok = i < S.n && a < S.r;
-                cp_async16(st + q * kPipeCols + 4 * lane, ok ? (const void*)(U + i * S.ldU + a) : (const void*)U,
-                           ok ? 16 : 0);
-            }
-        };
-#pragma unroll
-        for (int t = 0; t < kPipeStages - 1; ++t) {
-            if (t < ntiles) issue(t);
-            cp_commit();
-        }
-        float acc[R][CT];
-        for (int t = 0; t < ntiles; ++t) {
-            const int g = t / npass, ps = t % npass;
-            if (ps == 0) {
-#pragma unroll
-                for (int q = 0; q < R; ++q)
-#pragma unroll
-                    for (int j = 0; j < CT; ++j) acc[q][j] = 0.f;
-            }
-            if (t + kPipeStages - 1 < ntiles) issue(t + kPipeStages - 1);
-            cp_commit();
-            cp_wait<kPipeStages - 1>();
-            __syncwarp();
-            const float* st = ring + (t % kPipeStages) * TF;
-            const int64_t a = (int64_t)ps * kPipeCols + 4 * lane;
-            if (a < S.r) {
-                float u[R][4];
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const float4 v4 = *reinterpret_cast<const float4*>(st + q * kPipeCols + 4 * lane);
-                    u[q][0] = v4.x; u[q][1] = v4.y; u[q][2] = v4.z; u[q][3] = v4.w;
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float wv[CT];
-                    ld_row<CT>(W + (a + e) * CT, wv);
-#pragma unroll
-                    for (int q = 0; q < R; ++q)
-#pragma unroll
-                        for (int j = 0; j < CT; ++j) acc[q][j] = fmaf(u[q][e], wv[j], acc[q][j]);
-                }
-            }
-            __syncwarp();                              // the stage is refilled next iteration
-            if (ps == npass - 1) {                     // group done: reduce over the lanes
-                const int64_t row0 = rows0(g);
-#pragma unroll
-                for (int q = 0; q < R; ++q)
-#pragma unroll
-                    for (int j = 0; j < CT; ++j) red[lane * (NO + 1) + q * CT + j] = acc[q][j];
-                __syncwarp();
-                if (lane < NO) {
-                    float v = 0.f;
-#pragma unroll 8
-                    for (int l2 = 0; l2 < 32; ++l2) v += red[l2 * (NO + 1) + lane];
-                    const int q = lane / CT, j = lane % CT;
-                    const int64_t i = row0 + q;
-                    if (i < S.n && j < c) Y[S.off + i + (int64_t)j * ldy] = v;
-                }
-                __syncwarp();
-            }
-        }
-        cp_wait<0>();
-        __syncwarp();
     }
 }
 
@@ -1320,7 +1214,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
         if (skinny) {                     // the streaming kernels' columns / rows per item
             AB = (ct <= 8) ? kPipeCols : SkinnyShape<16>::AB;
-            RB = (ct <= 8) ? 8 * kPipeRows * kPipeGroups : SkinnyShape<16>::RB;
+            RB = (ct <= 8) ? SkinnyShape<8>::RB : SkinnyShape<16>::RB;
         }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
@@ -1378,10 +1272,8 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
     case CT:                                                                                                      \
         HDF_CUDA(cudaFuncSetAttribute(k_batch_utv_p<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
                                       (int)utv_pipe_smem<CT>()));                                                 \
-        HDF_CUDA(cudaFuncSetAttribute(k_batch_uw_p<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-                                      (int)uw_pipe_smem<CT>()));                                                  \
         HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_p<CT>, 256, utv_pipe_smem<CT>())); \
-        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_p<CT>, 256, uw_pipe_smem<CT>()));  \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<CT>, 256, 0));                \
         break;
                 HDF_B_OCC(1) HDF_B_OCC(2) HDF_B_OCC(4) HDF_B_OCC(8)
 #undef HDF_B_OCC
@@ -1407,10 +1299,10 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             UW<<<nsm * std::max(occ_w, 1), 256, SW, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw, cnt + 1,     \
                                                             reinterpret_cast<float*>(Y), ldy, c);                 \
         break;
-                HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_p<1>, utv_pipe_smem<1>(), uw_pipe_smem<1>())
-                HDF_B_SK(2, k_batch_utv_p<2>, k_batch_uw_p<2>, utv_pipe_smem<2>(), uw_pipe_smem<2>())
-                HDF_B_SK(4, k_batch_utv_p<4>, k_batch_uw_p<4>, utv_pipe_smem<4>(), uw_pipe_smem<4>())
-                HDF_B_SK(8, k_batch_utv_p<8>, k_batch_uw_p<8>, utv_pipe_smem<8>(), uw_pipe_smem<8>())
+                HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_s<1>, utv_pipe_smem<1>(), 0)
+                HDF_B_SK(2, k_batch_utv_p<2>, k_batch_uw_s<2>, utv_pipe_smem<2>(), 0)
+                HDF_B_SK(4, k_batch_utv_p<4>, k_batch_uw_s<4>, utv_pipe_smem<4>(), 0)
+                HDF_B_SK(8, k_batch_utv_p<8>, k_batch_uw_s<8>, utv_pipe_smem<8>(), 0)
                 HDF_B_SK(16, k_batch_utv_s<16>, k_batch_uw_s<16>, 0, 0)
 #undef HDF_B_SK
             }
