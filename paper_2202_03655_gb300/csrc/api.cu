@@ -745,8 +745,8 @@ extern "C" hdf_status hdf_matvec_transpose(const hdf_factor* f, const void* V_de
 
 // Host LU with partial pivoting of the r x r core (row-major, in place), blocked right-looking:
 // each 64-column panel is factored serially, then the block row U12 (forward substitution with
-// the panel's unit lower triangle) and the trailing matrix (A22 -= L21 U12, four rows at a time
-// against each U12 row) are updated on the worker pool.  Row interchanges cover whole rows, so
+// the panel's unit lower triangle) and the trailing matrix (A22 -= L21 U12, in 4 x 8 register
+// blocks) are updated on the worker pool.  Row interchanges cover whole rows, so
 // pivots and factors equal those of the unblocked algorithm up to rounding order.
 static bool lu_factor(int64_t r, std::vector<double>& A, std::vector<int>& piv) {
     piv.resize(r);
@@ -785,28 +785,10 @@ static bool lu_factor(int64_t r, std::vector<double>& A, std::vector<int>& piv) 
                 }
             }
         });
+        // A22 -= L21 U12: row blocks of RB rows on the pool, register-blocked in each
         parallel_for((int)((nt + RB - 1) / RB), [&](int rbk) {
             const int64_t i0 = ke + rbk * RB, i1 = std::min(r, i0 + RB);
-            int64_t i = i0;
-            for (; i + 4 <= i1; i += 4) {
-                double *A0 = &A[i * r], *A1 = A0 + r, *A2 = A1 + r, *A3 = A2 + r;
-                for (int64_t q = kb; q < ke; ++q) {
-                    const double l0 = A0[q], l1 = A1[q], l2 = A2[q], l3 = A3[q];
-                    const double* Aq = &A[q * r];
-                    for (int64_t j = ke; j < r; ++j) {
-                        const double u = Aq[j];
-                        A0[j] -= l0 * u; A1[j] -= l1 * u; A2[j] -= l2 * u; A3[j] -= l3 * u;
-                    }
-                }
-            }
-            for (; i < i1; ++i) {
-                double* Ai = &A[i * r];
-                for (int64_t q = kb; q < ke; ++q) {
-                    const double l = Ai[q];
-                    const double* Aq = &A[q * r];
-                    for (int64_t j = ke; j < r; ++j) Ai[j] -= l * Aq[j];
-                }
-            }
+            gemm_minus(i1 - i0, nt, ke - kb, &A[i0 * r + kb], r, &A[kb * r + ke], r, &A[i0 * r + ke], r);
         });
     }
     return true;

@@ -292,10 +292,11 @@ __global__ void k_block_gemv(const double* __restrict__ inv, const int64_t* __re
 
 // In-place inverse of a symmetric positive definite matrix (row-major n x n, both triangles
 // read from the lower one) by a blocked right-looking Cholesky A = L L^T (64-column panels:
-// the panel's rows below the diagonal block and the trailing update A22 -= L21 L21^T run on the
-// worker pool when par), then L^-1 one column at a time (forward substitution, stored
-// transposed so that every inner loop is a contiguous dot product) and A^-1 = L^-T L^-1.
-// False if A is not positive definite to working precision.
+// the panel's rows below the diagonal block and the trailing update A22 -= L21 L21^T, in
+// register blocks against the transposed panel, run on the worker pool when par), then L^-1
+// one column at a time (forward substitution, stored transposed so that every inner loop is a
+// contiguous dot product) and A^-1 = L^-T L^-1 in register blocks.  False if A is not positive
+// definite to working precision.
 bool spd_inverse(int64_t n, double* A, bool par) {
     const int64_t NB = 64, RB = 16;
     auto run = [&](int64_t cnt, const std::function<void(int64_t)>& fn) {
@@ -310,6 +311,7 @@ bool spd_inverse(int64_t n, double* A, bool par) {
         return (s0 + s1) + (s2 + s3);
     };
     bool ok = true;
+    std::vector<double> Pt;                                    // transposed panel, NB x (n - ke)
     for (int64_t kb = 0; kb < n && ok; kb += NB) {
         const int64_t ke = std::min(n, kb + NB);
         for (int64_t k = kb; k < ke; ++k) {                    // diagonal block
@@ -323,7 +325,7 @@ bool spd_inverse(int64_t n, double* A, bool par) {
             }
         }
         if (!ok || ke == n) break;
-        const int64_t nt = n - ke, nrb = (nt + RB - 1) / RB;
+        const int64_t nt = n - ke, nrb = (nt + RB - 1) / RB, w = ke - kb;
         run(nrb, [&](int64_t b) {                                // panel rows below the block
             for (int64_t i = ke + b * RB; i < std::min(n, ke + (b + 1) * RB); ++i) {
                 double* Ai = A + i * n;
@@ -333,16 +335,17 @@ bool spd_inverse(int64_t n, double* A, bool par) {
                 }
             }
         });
-        run(nrb, [&](int64_t b) {                                // A22 -= L21 L21^T (lower)
-            for (int64_t i = ke + b * RB; i < std::min(n, ke + (b + 1) * RB); ++i) {
-                double* Ai = A + i * n;
-                for (int64_t j = ke; j <= i; ++j) Ai[j] -= dot(Ai + kb, A + j * n + kb, ke - kb);
-            }
+        Pt.assign((size_t)w * nt, 0.0);
+        for (int64_t i = 0; i < nt; ++i)
+            for (int64_t q = 0; q < w; ++q) Pt[(size_t)q * nt + i] = A[(ke + i) * n + kb + q];
+        run(nrb, [&](int64_t b) {                                // A22 -= L21 L21^T (lower blocks)
+            const int64_t i0 = ke + b * RB, i1 = std::min(n, i0 + RB);
+            gemm_minus(i1 - i0, i1 - ke, w, A + i0 * n + kb, n, Pt.data(), nt, A + i0 * n + ke, n);
         });
     }
     if (!ok) return false;
-    // T = (L^-1)^T: row c of T is column c of L^-1 (entries c..n-1)
-    std::vector<double> T((size_t)n * n, 0.0);
+    // T = (L^-1)^T: row c of T is column c of L^-1 (entries c..n-1); Li = L^-1 row-major
+    std::vector<double> T((size_t)n * n, 0.0), Li((size_t)n * n, 0.0);
     run((n + RB - 1) / RB, [&](int64_t b) {
         for (int64_t c = b * RB; c < std::min(n, (b + 1) * RB); ++c) {
             double* x = T.data() + c * n;
@@ -350,10 +353,17 @@ bool spd_inverse(int64_t n, double* A, bool par) {
             for (int64_t i = c + 1; i < n; ++i) x[i] = -dot(A + i * n + c, x + c, i - c) / A[i * n + i];
         }
     });
-    // A^-1[i][j] = sum_{q >= i} T[i][q] T[j][q], j <= i
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t i = c; i < n; ++i) Li[i * n + c] = T[c * n + i];
+    // A^-1 = T Li for the lower blocks: rows [i0, i1), columns [0, i1), sums over q >= i0 (T[i][q]
+    // is zero below q = i); the negated product is accumulated into a zeroed block
     run((n + RB - 1) / RB, [&](int64_t b) {
-        for (int64_t i = b * RB; i < std::min(n, (b + 1) * RB); ++i)
-            for (int64_t j = 0; j <= i; ++j) A[i * n + j] = dot(T.data() + i * n + i, T.data() + j * n + i, n - i);
+        const int64_t i0 = b * RB, i1 = std::min(n, i0 + RB);
+        for (int64_t i = i0; i < i1; ++i)
+            for (int64_t j = 0; j < i1; ++j) A[i * n + j] = 0.0;
+        gemm_minus(i1 - i0, i1, n - i0, T.data() + i0 * n + i0, n, Li.data() + i0 * n, n, A + i0 * n, n);
+        for (int64_t i = i0; i < i1; ++i)
+            for (int64_t j = 0; j < i1; ++j) A[i * n + j] = -A[i * n + j];
     });
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = i + 1; j < n; ++j) A[i * n + j] = A[j * n + i];

@@ -519,6 +519,43 @@ void gram_from_moments(const std::vector<double>& m, int L, std::vector<double>&
         }
 }
 
+// C (m x n, row stride ldc) -= A (m x kk, stride lda) * B (kk x n, stride ldb), all row-major,
+// in 4 x 8 register blocks (the sums over kk stay in registers; the fixed-size inner loops are
+// left to the compiler's vectoriser).
+void gemm_minus(int64_t m, int64_t n, int64_t kk, const double* A, int64_t lda, const double* B, int64_t ldb,
+                       double* C, int64_t ldc) {
+    int64_t i0 = 0;
+    for (; i0 + 4 <= m; i0 += 4) {
+        int64_t j0 = 0;
+        for (; j0 + 8 <= n; j0 += 8) {
+            double acc[4][8] = {};
+            for (int64_t q = 0; q < kk; ++q) {
+                const double* b = B + q * ldb + j0;
+#pragma GCC unroll 4
+                for (int r = 0; r < 4; ++r) {
+                    const double a = A[(i0 + r) * lda + q];
+#pragma GCC unroll 8
+                    for (int c = 0; c < 8; ++c) acc[r][c] += a * b[c];
+                }
+            }
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 8; ++c) C[(i0 + r) * ldc + j0 + c] -= acc[r][c];
+        }
+        for (; j0 < n; ++j0)
+            for (int r = 0; r < 4; ++r) {
+                double s = 0.0;
+                for (int64_t q = 0; q < kk; ++q) s += A[(i0 + r) * lda + q] * B[q * ldb + j0];
+                C[(i0 + r) * ldc + j0] -= s;
+            }
+    }
+    for (; i0 < m; ++i0)
+        for (int64_t j0 = 0; j0 < n; ++j0) {
+            double s = 0.0;
+            for (int64_t q = 0; q < kk; ++q) s += A[i0 * lda + q] * B[q * ldb + j0];
+            C[i0 * ldc + j0] -= s;
+        }
+}
+
 // Radial-basis factor of one parity from its Gram sums: B = Q R_f with R_f = D^1/2 V^T and
 // Q = B Qmat, Qmat = V D^-1/2, over the eigen-directions above 1e-13 nb lambda_max.
 static void basis_factor(const std::vector<double>& gram, int L, int par, FactorChoice& out) {

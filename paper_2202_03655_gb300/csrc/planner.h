@@ -43,6 +43,11 @@ void gauss_gegenbauer(int N, double lam, double* t, double* w);
 // The same, memoised per (N, lambda) for lambda a multiple of 1/1024 (half-integers here).
 void gauss_gegenbauer_cached(int N, double lam, std::vector<double>& t, std::vector<double>& w);
 
+// C (m x n, row stride ldc) -= A (m x kk, stride lda) B (kk x n, stride ldb), row-major, in
+// 4 x 8 register blocks: the rank-kk update of the blocked host factorisations.
+void gemm_minus(int64_t m, int64_t n, int64_t kk, const double* A, int64_t lda, const double* B, int64_t ldb,
+                double* C, int64_t ldc);
+
 // Radial cores Gamma_k (k = 0..p/2) of r^(k) in the basis rho^(k%2) T_l(8 rho^2 - 1):
 // out[k] is a row-major nb_k x nb_k matrix, nb_k = L+1 (k even) or L (k odd).
 // threads: spread the degrees over host threads.
