@@ -512,13 +512,19 @@ def bench_adjoint(args):
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k2 = max(1, min(args.steps, 3))
-    b0.record(stream)
-    for _ in range(k2):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True); vd.copy_(vh, non_blocking=True); wd.copy_(wh, non_blocking=True)
         f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
         G, dl, val = f.adjoint(xd, vd, wd, stream=stream)
         Gh.copy_(G, non_blocking=True)
         f.free()
+
+    e2e_step()              # one untimed step
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(k2):
+        e2e_step()
     b1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = b0.elapsed_time(b1) / k2
@@ -615,13 +621,19 @@ def bench_batch(args):
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k2 = max(1, min(args.steps, 3))
-    b0.record(stream)
-    for _ in range(k2):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True); Vc.copy_(Vh, non_blocking=True)
         bb = hdf.build_batched(xd, off, w["kernel"], ells, w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
         bb.matvec_ptr(Vc.data_ptr(), N, c, Yc.data_ptr(), N, stream=stream)
         Yh.copy_(Yc, non_blocking=True)
         bb.free()
+
+    e2e_step()              # one untimed step
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(k2):
+        e2e_step()
     b1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = b0.elapsed_time(b1) / k2
@@ -733,8 +745,8 @@ def bench_cross(args):
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k2 = max(1, min(args.steps, 3))
-    b0.record(stream)
-    for _ in range(k2):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True); yd.copy_(yh, non_blocking=True)
         Vc.copy_(Vh, non_blocking=True); Wc.copy_(Wh, non_blocking=True)
         f = hdf.build_cross(xd, yd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max,
@@ -742,6 +754,12 @@ def bench_cross(args):
         products(f)
         Yh.copy_(Yc, non_blocking=True); Zh.copy_(Zc, non_blocking=True)
         f.free()
+
+    e2e_step()              # one untimed step
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(k2):
+        e2e_step()
     b1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = b0.elapsed_time(b1) / k2
@@ -1273,14 +1291,20 @@ def main():
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 3))
-    b0.record(stream)
-    for _ in range(e2e_steps):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True)
         Vc.copy_(Vh, non_blocking=True)
         f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
         f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
         Yh.copy_(Yc, non_blocking=True)
         f.free()
+
+    e2e_step()              # one untimed step: after the FP64 form the memory pool maps U again
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
     b1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = b0.elapsed_time(b1) / e2e_steps
