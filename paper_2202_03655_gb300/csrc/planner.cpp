@@ -330,16 +330,6 @@ static void cheb_derivative(const std::vector<double>& c, std::vector<double>& d
     for (int q = 0; q < N; ++q) dc[q] = scale * e[q];
 }
 
-static double clenshaw(const std::vector<double>& c, double u) {
-    double b1 = 0.0, b2 = 0.0;
-    for (int q = (int)c.size() - 1; q >= 1; --q) {
-        const double b0 = 2.0 * u * b1 - b2 + c[q];
-        b2 = b1;
-        b1 = b0;
-    }
-    return u * b1 - b2 + c[0];
-}
-
 void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>>& out, bool threads) {
     const int L = p / 2;
     const double alpha = 0.5 * d - 1.0;
