@@ -1,0 +1,111 @@
+// Checks of the library's host numerics (planner.cpp) against their defining properties:
+// the one-sided Jacobi SVD (A = U S V^T, orthonormal factors, sorted values, rank-deficient
+// and wide inputs), the register-blocked rank-k update (against the plain triple loop), and
+// the symmetric eigensolver (A V = V diag(w), V orthonormal).  Prints one line per check and
+// exits non-zero on the first failure.
+#include <cmath>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "planner.h"
+
+using namespace hdf;
+
+static int fails = 0;
+static void report(const char* what, double err, double bound) {
+    const bool ok = err <= bound;
+    std::printf("%s %s err %.3e bound %.1e\n", ok ? "ok  " : "FAIL", what, err, bound);
+    if (!ok) ++fails;
+}
+
+int main() {
+    std::mt19937_64 g(7);
+    std::normal_distribution<double> nd;
+    // SVD
+    const int shapes[][2] = {{1, 1}, {4, 1}, {1, 5}, {6, 3}, {3, 6}, {17, 17}, {40, 23}, {23, 40}, {65, 65}};
+    for (auto& sh : shapes) {
+        const int m = sh[0], n = sh[1], q = std::min(m, n);
+        std::vector<double> A((size_t)m * n);
+        for (auto& v : A) v = nd(g);
+        if (m > 5 && n > 5)
+            for (int j = 0; j < n; ++j) A[(size_t)3 * n + j] = 2.0 * A[(size_t)1 * n + j];   // rank drop
+        std::vector<double> U((size_t)m * q), s(q), V((size_t)n * q);
+        svd_jacobi(m, n, A.data(), U.data(), s.data(), V.data());
+        double rec = 0.0, amax = 0.0, orth = 0.0, order = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double t = 0.0;
+                for (int o = 0; o < q; ++o) t += U[(size_t)i * q + o] * s[o] * V[(size_t)j * q + o];
+                rec = std::max(rec, std::fabs(t - A[(size_t)i * n + j]));
+                amax = std::max(amax, std::fabs(A[(size_t)i * n + j]));
+            }
+        for (int a = 0; a < q; ++a) {
+            if (a > 0) order = std::max(order, s[a] - s[a - 1]);
+            for (int b = 0; b < q; ++b) {
+                double vv = 0.0, uu = 0.0;
+                for (int j = 0; j < n; ++j) vv += V[(size_t)j * q + a] * V[(size_t)j * q + b];
+                orth = std::max(orth, std::fabs(vv - (a == b)));
+                if (s[a] > 1e-10 * s[0] && s[b] > 1e-10 * s[0]) {
+                    for (int i = 0; i < m; ++i) uu += U[(size_t)i * q + a] * U[(size_t)i * q + b];
+                    orth = std::max(orth, std::fabs(uu - (a == b)));
+                }
+            }
+        }
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "svd %dx%d reconstruction", m, n);
+        report(buf, rec / amax, 1e-13);
+        std::snprintf(buf, sizeof(buf), "svd %dx%d orthonormality", m, n);
+        report(buf, orth, 1e-12);
+        std::snprintf(buf, sizeof(buf), "svd %dx%d decreasing values", m, n);
+        report(buf, std::max(0.0, order), 0.0);
+    }
+    // rank-k update C -= A B
+    const int dims[][3] = {{1, 1, 1}, {4, 8, 3}, {5, 9, 64}, {33, 70, 17}, {128, 131, 64}};
+    for (auto& dm : dims) {
+        const int m = dm[0], n = dm[1], k = dm[2];
+        const int lda = k + 3, ldb = n + 5, ldc = n + 2;
+        std::vector<double> A((size_t)m * lda), B((size_t)k * ldb), C((size_t)m * ldc), R;
+        for (auto& v : A) v = nd(g);
+        for (auto& v : B) v = nd(g);
+        for (auto& v : C) v = nd(g);
+        R = C;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double t = 0.0;
+                for (int q = 0; q < k; ++q) t += A[(size_t)i * lda + q] * B[(size_t)q * ldb + j];
+                R[(size_t)i * ldc + j] -= t;
+            }
+        gemm_minus(m, n, k, A.data(), lda, B.data(), ldb, C.data(), ldc);
+        double err = 0.0;
+        for (size_t e = 0; e < C.size(); ++e) err = std::max(err, std::fabs(C[e] - R[e]));
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "gemm_minus %dx%dx%d (padding columns untouched)", m, n, k);
+        report(buf, err, 1e-12 * k);
+    }
+    // symmetric eigensolver
+    for (int n : {1, 2, 9, 40}) {
+        std::vector<double> A((size_t)n * n), Ac, w(n), V((size_t)n * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j <= i; ++j) A[(size_t)i * n + j] = A[(size_t)j * n + i] = nd(g);
+        Ac = A;
+        sym_eig(n, Ac.data(), w.data(), V.data());
+        double res = 0.0, orth = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < n; ++c) {
+                double t = 0.0, o = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    t += A[(size_t)i * n + j] * V[(size_t)j * n + c];
+                    o += V[(size_t)j * n + i] * V[(size_t)j * n + c];
+                }
+                res = std::max(res, std::fabs(t - w[c] * V[(size_t)i * n + c]));
+                orth = std::max(orth, std::fabs(o - (i == c)));
+            }
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "sym_eig %d residual", n);
+        report(buf, res, 1e-12 * n);
+        std::snprintf(buf, sizeof(buf), "sym_eig %d orthonormality", n);
+        report(buf, orth, 1e-12 * n);
+    }
+    return fails ? 1 : 0;
+}
