@@ -6,7 +6,7 @@
 // and would break or be refused by the capture), code whose device memory is owned by
 // another allocator (a framework's caching pool holds the free memory, so a raw cudaMalloc
 // can fail even though the framework has room), and latency-critical or real-time loops
-// that reserve everything at start-up and must not enter the driver's allocator.  For them
+// that reserve everything at start-up and must not enter the CUDA allocator.  For them
 // the per-call partial sums live in g_noalloc_scratch below.
 #include <cuda_runtime.h>
 
