@@ -158,6 +158,23 @@ def dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms, ws, dev):
+    """The slowest rank's time (all-reduce MAX over the process group; the value itself for
+    one process).  dev: the device the group's backend reduces on (cuda for NCCL, cpu for gloo)."""
+    if ws <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, steps, ms_total):
+    """Units processed by all ranks per second over the slowest rank's time (replicas: every
+    rank processes the same units_per_rank each step)."""
+    return ws * units_per_rank * steps / (ms_total / 1e3)
+
+
 def workload_params(args):
     from paper_2202_03655_gb300 import workloads as W
     w = dict(W.WORKLOADS[args.workload])
@@ -416,11 +433,7 @@ def _timed(args, ws, rank, dev, stream, one_step):
         torch.distributed.barrier()
     launches = hdf.launch_count() - l0
     clocks = sampler.stop() if sampler else None
-    ms_total = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     return ms_total, recs, launches, clocks
 
 
@@ -464,7 +477,7 @@ def bench_adjoint(args):
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
     info = recs[-1][0]
     adj_ms = float(np.mean([r[1] for r in recs]))
-    value = ws * n * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(n, ws, args.steps, ms_total)
     # accuracy outside the timed region: sampled rows of K~ v against the exact kernel
     f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
     y = f.matvec(v)
@@ -586,7 +599,7 @@ def bench_batch(args):
         return rec
 
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
-    value = ws * N * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(N, ws, args.steps, ms_total)
     tms, mv_ms, infos = recs[-1]
     ranks = np.array([i.rank for i in infos])
     ldus = np.array([i.ldu for i in infos])
@@ -701,7 +714,7 @@ def bench_cross(args):
         return rec
 
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
-    value = ws * (m + n) * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(m + n, ws, args.steps, ms_total)
     info = recs[-1][0]
     kv_ms = float(np.mean([r[1] for r in recs]))
     kvt_ms = float(np.mean([r[2] for r in recs]))
@@ -826,7 +839,7 @@ def bench_fig1(args):
 
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
     total_pts = sum(n for _, n in grid)
-    value = ws * total_pts * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(total_pts, ws, args.steps, ms_total)
     table = []
     for d in w["dims"]:
         ts = []
@@ -927,7 +940,7 @@ def bench_fig3(args):
         return out if keep else None
 
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
-    value = ws * n * len(cfgs) * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(n * len(cfgs), ws, args.steps, ms_total)
     # achieved errors against the dense matrix, per (kernel, tol)
     D = torch.cdist(x, x)
     rows = []
@@ -1049,7 +1062,7 @@ def bench_krr(args):
         return rec
 
     ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
-    value = ws * ntr * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(ntr, ws, args.steps, ms_total)
     (nc, rank_tot, tms), km_it, it, res, pred = recs[-1]
     pred_np = pred.cpu().numpy()
     mse = float(np.mean((pred_np - yte_np) ** 2))
@@ -1238,13 +1251,9 @@ def main():
     barrier()
     launches = hdf.launch_count() - l0
     clocks = sampler.stop() if sampler else None
-    ms_total = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     ms_step = ms_total / args.steps
-    value = ws * n * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(n, ws, args.steps, ms_total)
 
     # ---- accuracy of the benchmarked factor (outside the timed region)
     info = infos[-1]
