@@ -63,3 +63,21 @@ def test_planner_radial_cores_match_oracle(d, kname, ell):
     for k, (cl, co) in enumerate(zip(lib_cores, orc_cores)):
         assert cl.shape == co.shape
         assert np.abs(cl - co).max() <= 1e-12 * scale, k
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libhdf.so every call raises: the binding has no CPU fallback."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2202_03655_gb300 import hdf\n"
+            "hdf.LIB_PATH = %r\n"
+            "hdf._lib = None\n"
+            "try:\n"
+            "    hdf.cheb_nodes(16)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'missing' in str(e))\n"
+            "else:\n"
+            "    print('no error')\n") % (ROOT, str(tmp_path / "absent" / "libhdf.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
