@@ -227,7 +227,11 @@ void sym_eig(int n, double* A, double* w, double* V) {
     for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
     for (int i = 0; i + 1 < n; ++i) e[i] = A[i * n + i + 1];
     // implicit QR on the tridiagonal (w, e); rotation G in plane (k, k+1) with G_kk = G_k+1,k+1 = c,
-    // G_k,k+1 = s, G_k+1,k = -s, T <- G^T T G, V <- V G
+    // G_k,k+1 = s, G_k+1,k = -s, T <- G^T T G, V <- V G.  The rotations are accumulated into
+    // Vt = V^T, where columns k and k+1 of V are contiguous rows (the same arithmetic per entry).
+    std::vector<double> Vt((size_t)n * n);
+    for (int r2 = 0; r2 < n; ++r2)
+        for (int c2 = 0; c2 < n; ++c2) Vt[(size_t)c2 * n + r2] = V[(size_t)r2 * n + c2];
     const double eps = 2.220446049250313e-16;
     int q = n - 1, iters = 0;
     while (q > 0 && iters < 64 * n) {
@@ -257,14 +261,17 @@ void sym_eig(int n, double* A, double* w, double* V) {
                 e[k + 1] = c * h;
                 x = e[k];
             }
+            double* ck = Vt.data() + (size_t)k * n;
+            double* ck1 = ck + n;
             for (int r2 = 0; r2 < n; ++r2) {
-                double* row = V + (size_t)r2 * n;
-                const double vk = row[k], vk1 = row[k + 1];
-                row[k] = c * vk - s * vk1;
-                row[k + 1] = s * vk + c * vk1;
+                const double vk = ck[r2], vk1 = ck1[r2];
+                ck[r2] = c * vk - s * vk1;
+                ck1[r2] = s * vk + c * vk1;
             }
         }
     }
+    for (int r2 = 0; r2 < n; ++r2)
+        for (int c2 = 0; c2 < n; ++c2) V[(size_t)r2 * n + c2] = Vt[(size_t)c2 * n + r2];
 }
 
 void gauss_gegenbauer(int N, double lam, double* t, double* w) {
