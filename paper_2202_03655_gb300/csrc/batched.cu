@@ -853,12 +853,16 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     }
     b->t_ms[0] = now_ms_b() - t_start;
 
-    // ---- A1-A2 per set on host threads
+    // ---- A1 per set on host threads (the radial cores, A2, follow while the device sums the
+    //      radial moments below)
     double t0 = now_ms_b();
     std::vector<DegreePlan> dps(ns);
     parallel_for(ns, [&](int s) {
-        plan_degree(b->kernel, ells[s], Rs[s], mu2[s], geo[s].n, tol, eta, p_max, d, false, dps[s]);
+        plan_degree(b->kernel, ells[s], Rs[s], mu2[s], geo[s].n, tol, eta, p_max, d, false, dps[s], false);
     });
+    auto cores_all = [&]() {
+        parallel_for(ns, [&](int s) { radial_cores(dps[s].a.data(), dps[s].p, d, dps[s].cores, false); });
+    };
     for (int s = 0; s < ns; ++s) geo[s].L = dps[s].L;
     b->t_ms[1] = now_ms_b() - t0;
 
@@ -894,6 +898,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         HDF_CUDA(cudaGetLastError());
         std::vector<double> gp(gtot);
         HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
+        cores_all();                                    // A2 on the host while the device works
         HDF_CUDA(cudaStreamSynchronize(st));
         std::vector<std::vector<double>> moms(ns);
         for (int s = 0; s < ns; ++s) moms[s].assign(2 * geo[s].L + 2, 0.0);
@@ -929,6 +934,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     HDF_CUDA(cudaGetLastError());
     std::vector<double> gp(gtot);
     HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
+    cores_all();                                        // A2 on the host while the device works
     HDF_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < ns; ++s) {
         const int LP1 = geo[s].L + 1;
