@@ -260,8 +260,9 @@ hdf_status max_norm2(const double* x, int64_t n, int d, const dev::Center& cen, 
 }
 
 // Chebyshev moments sum_i T_j(8 rho_i^2 - 1), j <= 2L+1, of one point set, FP64 partial sums
-// (double-float recurrences for FP32 factors).  Enqueued on the stream with an asynchronous
-// copy into mom; the caller synchronises before reading it.
+// (double-float recurrences for FP32 factors), enqueued on the stream into job.msum;
+// moments_to_host copies them into job.mom (a copy into pageable memory waits for the
+// kernels, so host work meant to overlap them goes before it).
 struct MomentJob {
     DevBuf mpart, msum;
     std::vector<double> mom;
@@ -290,7 +291,11 @@ hdf_status radial_moments(const double* x, int64_t n, int d, const dev::Center& 
                                                                     job.msum.as<double>());
     HDF_CUDA(cudaGetLastError());
     job.mom.assign(nmom, 0.0);
-    HDF_CUDA(cudaMemcpyAsync(job.mom.data(), job.msum.p, nmom * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return HDF_OK;
+}
+
+hdf_status moments_to_host(MomentJob& job, cudaStream_t st) {
+    HDF_CUDA(cudaMemcpyAsync(job.mom.data(), job.msum.p, job.mom.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     return HDF_OK;
 }
 
@@ -395,6 +400,7 @@ hdf_status hdf_build(const double* x_dev, int64_t n, int d, hdf_kernel kernel, d
     radial_cores(dp.a.data(), dp.p, d, dp.cores, true);
     tph[1] = now_ms() - t0;
     t0 = now_ms();
+    if (hdf_status e = moments_to_host(mj, st); e != HDF_OK) return e;
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<double> gram;
     gram_from_moments(mj.mom, L, gram);
@@ -483,6 +489,8 @@ hdf_status hdf_build_cross(const double* x_dev, int64_t m, const double* y_dev, 
     radial_cores(dp.a.data(), dp.p, d, dp.cores, true);
     tph[1] = now_ms() - t0;
     t0 = now_ms();
+    if (hdf_status e = moments_to_host(jx, st); e != HDF_OK) return e;
+    if (hdf_status e = moments_to_host(jy, st); e != HDF_OK) return e;
     HDF_CUDA(cudaStreamSynchronize(st));
     std::vector<double> gx, gy;
     gram_from_moments(jx.mom, L, gx);

@@ -896,9 +896,10 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         k_seg_moments_df<<<(unsigned)gitems.size(), 256, msm, st>>>(x, d, dgi.as<SegItem>(), dgpoff.as<int64_t>(),
                                                                      dgeo.as<SetGeom>(), dgpart.as<double>());
         HDF_CUDA(cudaGetLastError());
+        cores_all();            // A2 on the host while the device works (before the copy into
+                                // pageable memory, which would wait for the kernel)
         std::vector<double> gp(gtot);
         HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
-        cores_all();                                    // A2 on the host while the device works
         HDF_CUDA(cudaStreamSynchronize(st));
         std::vector<std::vector<double>> moms(ns);
         for (int s = 0; s < ns; ++s) moms[s].assign(2 * geo[s].L + 2, 0.0);
@@ -932,9 +933,9 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     k_seg_gram<<<(unsigned)gitems.size(), 256, gsm, st>>>(x, d, dgi.as<SegItem>(), dgpoff.as<int64_t>(),
                                                            dgeo.as<SetGeom>(), dgpart.as<double>());
     HDF_CUDA(cudaGetLastError());
+    cores_all();                // A2 on the host while the device works (before the copy)
     std::vector<double> gp(gtot);
     HDF_CUDA(cudaMemcpyAsync(gp.data(), dgpart.p, sizeof(double) * gtot, cudaMemcpyDeviceToHost, st));
-    cores_all();                                        // A2 on the host while the device works
     HDF_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < ns; ++s) {
         const int LP1 = geo[s].L + 1;
