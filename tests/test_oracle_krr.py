@@ -95,3 +95,16 @@ def test_kernel_matvec_is_the_dense_product():
     x, xq, w = g.standard_normal((50, 3)), g.standard_normal((7, 3)), g.standard_normal(50)
     K = np.array([[np.exp(-0.5 * np.sum((a - b) ** 2) / 0.7 ** 2) for b in x] for a in xq])
     assert np.allclose(krr.kernel_matvec(xq, x, "gaussian", 0.7, w), K @ w)
+
+
+def test_single_cluster_exact_preconditioner_converges_in_one_step():
+    """One cluster: K^ is that block's HDF factor and M^-1 = lambda I + K exactly; with the block
+    tolerance near rounding, M is the inverse of the system and PCG stops after one step."""
+    g = np.random.default_rng(8)
+    xtr = W.uniform_ball(g, 300, 3, 1.0)
+    ytr = np.sin(3.0 * xtr[:, 0]) + 0.1 * g.standard_normal(300)
+    labels = np.zeros(len(xtr), dtype=int)
+    op = krr.BlockOperator(xtr, labels, "gaussian", 0.5, 1e-12)
+    M = krr.block_preconditioner(op, 1.0)
+    w, it, res = krr.pcg(lambda v: 1.0 * v + op.apply(v), M, ytr, rtol=1e-9, max_iter=50)
+    assert it == 1 and res <= 1e-9
