@@ -40,7 +40,7 @@ def tail_sums(a):
 
         tails[p] = sum_{p < i < M} |a_i|  +  sum_{M/2 <= i < M} |a_i|.
 
-    Remark 3 only says the tail "may be easily approximated".  The second sum stands in for
+    Remark 3 says only that the tail can be estimated cheaply.  The second sum stands in for
     the coefficients beyond M that the DCT cannot see: when |a_i| decays like i^-q with
     q >= 2 (Matern-3/2 decays like i^-4) the upper half of the computed coefficients
     carries at least as much mass as everything beyond M; for geometric decay it is at

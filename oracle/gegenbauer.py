@@ -10,7 +10,7 @@
 * ``inv_Z(k, d)``          -- 1/Z_k of the addition theorem (Eq. additiontheorem) for
       orthonormal real harmonics on S^{d-1}:  sum_h Y_k^h(x) Y_k^h(y) = C_k^alpha(x.y)/Z_k,
       1/Z_k = (k + alpha) / (alpha |S^{d-1}|), alpha = d/2 - 1, d >= 3.
-      The paper calls Z_k "a normalization term" without a formula; this value follows
+      The paper names Z_k as a normaliser but gives no formula for it; this value follows
       from the harmonics' orthonormality (pinned in tests by the addition theorem itself).
 * ``gegen_norm(n, lam)``   -- h_n^lam = int_{-1}^{1} (C_n^lam)^2 (1-t^2)^{lam-1/2} dt.
 * ``harmonic_count(k, d)`` -- |H_k| = C(k+d-1, k) - C(k+d-3, k-2) (App. B).

@@ -2,7 +2,7 @@
 
 Steps, in the paper's order:
 
-1. Scale (Sec. 3.3 footnote "absorb the diameter into the lengthscale"; Sec. 4.1 scales
+1. Scale (Sec. 3.3 footnote: the point set's diameter is folded into the lengthscale; Sec. 4.1 scales
    points by their maximum norm).  c = mean(x), R = max |x_i - c|, x' = (x - c) / (2R),
    so |x'| <= 1/2 and |x'_i - x'_j| <= 1.  The scaled kernel is kappa(r) = k(2 R r).
    If all points coincide (R = 0) the scale is arbitrary and R = 1 is used.
@@ -14,7 +14,7 @@ Steps, in the paper's order:
 5. QR (Eq. svd): the paper factors each Vandermonde block Y^(k) (Eq. vandermonde).  The
    radial functions of all even k (odd k) lie in the span of one basis
    B_par = rho^par [T_l(8 rho^2 - 1)]_l, so one QR per parity serves every k -- the
-   "Vandermonde outside the k loop" of Sec. 3.6.  Then G_k = R_par Gamma_k R_par^T.
+   Vandermonde matrix formed once, outside the loop over k (Sec. 3.6).  Then G_k = R_par Gamma_k R_par^T.
 6. Eigendecomposition (Remark 1) G_k = W_k Lambda_k W_k^T and truncation (Sec. 3.4 with the
    tau of Sec. 3.5 made concrete): dropping eigenpair (lambda, w) of block k changes K by
    at most |lambda| |H_k| / |S^{d-1}| in Frobenius norm (addition theorem at angle 0).
