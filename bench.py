@@ -64,6 +64,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # None when its kernel changes, until it is captured again.
 TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1663, "k_tc_utv": 4.1500, "k_tc_uw": 4.0655}
 METRICS = {
+    "mixture3_matern": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
     "fig1_cauchy": "factor-build points/s over the time-vs-n sweep (Cauchy l=1, tol 1e-3, d 3-6, n 1e4-1e7), "
@@ -91,6 +92,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--nsets", type=int, default=None, help="batch512_gauss: number of sets (default 512)")
     ap.add_argument("--cpu-n", type=int, default=12000, help="oracle sample size")
+    ap.add_argument("--oracle-once", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -173,6 +175,91 @@ def whole_job_rate(units_per_rank, ws, steps, ms_total):
     """Units processed by all ranks per second over the slowest rank's time (replicas: every
     rank processes the same units_per_rank each step)."""
     return ws * units_per_rank * steps / (ms_total / 1e3)
+
+
+def blas_threads():
+    """Threads of the BLAS that numpy loaded (threadpoolctl when present, else the OpenBLAS
+    query function found in the process's mapped libraries); None if unknown."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(n[0])
+    except Exception:
+        pass
+    import ctypes
+    import numpy  # noqa: F401  (loads the BLAS)
+    try:
+        with open("/proc/self/maps") as fh:
+            libs = sorted({ln.split()[-1] for ln in fh if "openblas" in ln.lower() and ".so" in ln})
+    except OSError:
+        libs = []
+    for path in libs:
+        try:
+            L = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for sym in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_", "openblas_get_num_threads"):
+            fn = getattr(L, sym, None)
+            if fn is not None:
+                fn.restype = ctypes.c_int
+                return int(fn())
+    return None
+
+
+SINGLE_THREAD_WORKLOADS = ("mixture3_matern", "cube4_gauss", "batch512_gauss")
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def oracle_single_thread(args, workload):
+    """The same oracle sample timed in a child process whose BLAS runs one thread (the paper's
+    setting, Sec. 4: single-threaded).  Returns (seconds, points, blas threads) or None."""
+    env = dict(os.environ)
+    env.update(SINGLE_THREAD_ENV)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-once", "--workload", workload,
+           "--cpu-n", str(args.cpu_n), "--p-max", str(args.p_max)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        for ln in out.stdout.splitlines()[::-1]:
+            if ln.startswith("{"):
+                r = json.loads(ln)
+                return r["seconds"], r["points"], r["blas_threads"]
+    except Exception:
+        pass
+    return None
+
+
+def oracle_once(args):
+    """Child side of oracle_single_thread: one untimed and one timed oracle step of the sample."""
+    import numpy as np
+    from paper_2202_03655_gb300 import workloads as W
+    w = workload_params(args)
+    if args.workload == "mixture3_matern":
+        ns = min(args.cpu_n, w["n"])
+        x = W.points(args.workload, n=ns)
+        V = np.random.default_rng(1).standard_normal((ns, w["ncols"]))
+        cpu_oracle_step(x, w, V, args.p_max)
+        sec = cpu_oracle_step(x, w, V, args.p_max)
+    else:
+        x, off, ells = oracle_sample(args, w)
+        ns = int(off[-1])
+        cpu_oracle_work(args, w, x, off, ells)
+        sec = cpu_oracle_work(args, w, x, off, ells)
+    print(json.dumps({"seconds": sec, "points": ns, "blas_threads": blas_threads()}), flush=True)
+    return 0
+
+
+def cpu_baseline_line(value, sample, args, workload, cores=None):
+    """cpu_baseline object: the all-cores figure (value), the BLAS thread count it used, and the
+    single-threaded figure of the same sample."""
+    bt = blas_threads()
+    out = {"value": value, "unit": "points/s", "cores": cores or bt or os.cpu_count(), "kind": "oracle",
+           "sample": sample, "host_cpus": os.cpu_count(), "blas_threads": bt}
+    one = oracle_single_thread(args, workload) if workload in SINGLE_THREAD_WORKLOADS else None
+    if one:
+        sec, pts, bt1 = one
+        out["single_thread"] = {"value": pts / sec, "unit": "points/s", "cores": 1, "blas_threads": bt1}
+    return out
 
 
 def workload_params(args):
@@ -293,7 +380,7 @@ def run_reference(args):
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "n_train_sample": len(xs), "d": w["d"], "p_max": args.p_max},
-                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                                  "sample": f"the regression recipe at {len(xs)} training points, FP64 numpy"},
                 "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -327,7 +414,7 @@ def run_reference(args):
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "points_per_step": npts, "p_max": args.p_max},
-                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                                  "sample": what + ", FP64 numpy"},
                 "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -344,10 +431,11 @@ def run_reference(args):
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "m_sample": len(x), "n_sample": len(y), "d": w["d"],
+                "config": {"workload": args.workload, "m": w.get("n"), "n": w.get("n_y"), "m_sample": len(x),
+                           "n_sample": len(y), "d": w["d"],
                            "kernel": w["kernel"], "lengthscale": w["ell"], "tol": w["tol"], "ncols": w["ncols"],
                            "p_max": args.p_max},
-                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                                  "sample": f"first {len(x)} points of X and {len(y)} of Y, build_xy + K~V + "
                                            f"K~^T W ({w['ncols']} columns), FP64 numpy"},
                 "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -367,9 +455,9 @@ def run_reference(args):
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "n_sample": ns, "sets": len(ells), "d": w["d"],
+                "config": {"workload": args.workload, "n": w.get("n"), "n_sample": ns, "sets": len(ells), "d": w["d"],
                            "kernel": w["kernel"], "tol": w["tol"], "ncols": w["ncols"], "p_max": args.p_max},
-                "cpu_baseline": {"value": val, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                "cpu_baseline": {"value": val, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                                  "sample": f"{ns} points ({len(ells)} set(s)) of the workload, {what}"},
                 "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -382,15 +470,16 @@ def run_reference(args):
     ts = [cpu_oracle_step(x, w, V, args.p_max) for _ in range(args.steps)]
     tot = sum(ts)
     val = ns * args.steps / tot
-    cores = os.cpu_count()
-    line = {"impl": "reference", "metric": "factor-build points/s (build + K~V step)", "value": val,
+    cores = blas_threads() or os.cpu_count()
+    line = {"impl": "reference", "metric": METRICS[args.workload], "value": val,
             "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_sample": ns, "d": w["d"], "kernel": w["kernel"],
+            "config": {"workload": args.workload, "n": w["n"], "n_sample": ns, "d": w["d"], "kernel": w["kernel"],
                        "lengthscale": w["ell"], "tol": w["tol"], "ncols": w["ncols"], "p_max": args.p_max},
-            "cpu_baseline": {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {ns} points of the workload, full step (build + K~V)"},
+            "cpu_baseline": cpu_baseline_line(val, f"first {ns} of the {w['n']} points of the workload, full step "
+                                                   f"(build + K~V, {w['ncols']} columns), FP64 numpy",
+                                              args, args.workload, cores),
             "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -443,8 +532,8 @@ def _cpu_baseline(args, w):
     ns = int(off[-1])
     what = ("build + frozen-structure adjoint by central differences" if args.workload == "cube4_gauss"
             else f"build + K~V ({w['ncols']} columns) of each set")
-    return {"value": ns / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{ns} points ({len(ells)} set(s)) of the workload, {what}, FP64 numpy"}
+    return cpu_baseline_line(ns / ts, f"{ns} points ({len(ells)} set(s)) of the workload, {what}, FP64 numpy",
+                             args, args.workload)
 
 
 def bench_adjoint(args):
@@ -783,7 +872,7 @@ def bench_cross(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         xs, ys = cross_oracle_sample(args, w)
         ts = cross_oracle_work(w, xs, ys, args.p_max)
-        cpu = {"value": (len(xs) + len(ys)) / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": (len(xs) + len(ys)) / ts, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                "sample": f"first {len(xs)} points of X and {len(ys)} of Y, build_xy + K~V + K~^T W "
                          f"({c} columns), FP64 numpy"}
     if rank == 0:
@@ -887,7 +976,7 @@ def bench_fig1(args):
         t = time.perf_counter()
         ohdf.build(xs, w["kernel"], w["ell"], w["tol"], p_max=args.p_max)
         ts_ = time.perf_counter() - t
-        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                "sample": f"one oracle build of {len(xs)} points, d = 3, FP64 numpy"}
     if rank == 0:
         line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
@@ -1015,7 +1104,7 @@ def bench_fig3(args):
         t = time.perf_counter()
         ohdf.build(x_np[:ns], "cauchy", 1.0, 1e-3, p_max=args.p_max)
         ts_ = time.perf_counter() - t
-        cpu = {"value": ns / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": ns / ts_, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                "sample": f"one oracle build of the first {ns} points, Cauchy, tol 1e-3, FP64 numpy"}
     if rank == 0:
         line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
@@ -1155,7 +1244,7 @@ def bench_krr(args):
         wo, _, _, _ = okrr.krr_fit(xs, ys, lab, w["kernel"], w["ell"], w["lam"], w["tol"], rtol=rtol)
         okrr.kernel_matvec(xq, xs, w["kernel"], w["ell"], wo)
         ts_ = time.perf_counter() - t
-        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": len(xs) / ts_, "unit": "points/s", "cores": blas_threads() or os.cpu_count(), "kind": "oracle",
                "sample": f"the same recipe at {len(xs)} training points (k-means, oracle HDF blocks, PCG, "
                          f"predictions), FP64 numpy"}
     if rank == 0:
@@ -1180,6 +1269,8 @@ def bench_krr(args):
 
 def main():
     args = parse()
+    if args.oracle_once:
+        return oracle_once(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "cube4_gauss":
@@ -1361,12 +1452,12 @@ def main():
         xs = x_np[:ns]
         Vs = V_np[:ns].astype(np.float64)
         ts = cpu_oracle_step(xs, w, Vs, args.p_max)
-        cpu = {"value": ns / ts, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"first {ns} of the {n} points, one full step (build + K~V, {c} columns), FP64 numpy"}
+        cpu = cpu_baseline_line(ns / ts, f"first {ns} of the {n} points, one full step (build + K~V, {c} columns), "
+                                         "FP64 numpy", args, args.workload)
 
     if rank == 0:
         line = {
-            "metric": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
+            "metric": METRICS[args.workload],
             "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
