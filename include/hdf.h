@@ -153,18 +153,21 @@ hdf_status hdf_matvec(const hdf_factor* f, const void* V_dev, int64_t ldv, int n
 hdf_status hdf_matvec_transpose(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
                                 void* Y_dev, int64_t ldy, hdf_stream stream);
 
-/* Same product as hdf_matvec, for callers that must not allocate device memory during the
- * call: code running while a stream is being captured, code whose device memory belongs to
- * another allocator's pool, or loops that reserve all memory up front.  The paper has no
- * counterpart; this is a library convenience.  The partial sums live in a fixed 32 MiB
- * array inside the library (held on every device that loads it until the process exits)
- * instead of memory obtained per call; no cudaMalloc, cudaFree or allocating library routine
- * is called.  Limit: rank * min(ncols, 64) * (8 + element size) bytes <= 32 MiB, otherwise
- * HDF_ETOOBIG.  The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.  All calls share
- * the one array (each call overwrites every entry it reads), so calls whose executions
- * overlap on the GPU -- on different streams or from different threads -- race and must
- * be serialised by the caller.  Arguments and layout as hdf_matvec. */
+/* K~ V as hdf_matvec computes it, for callers that cannot allocate device memory during the
+ * call: code whose device memory belongs to another allocator's pool (a raw cudaMalloc may
+ * fail while that pool holds the free memory), or loops that reserve all memory up front and
+ * must not enter the CUDA allocator.  The paper has no counterpart; this is a library
+ * convenience.  The partial sums live in a fixed 32 MiB array inside the library (held on
+ * every device that loads it until the process exits) instead of memory obtained per call; no
+ * cudaMalloc, cudaFree or allocating library routine is called.  Limit: ldu (the padded width
+ * of U that hdf_factor_info reports) * min(ncols, 64) * (8 + element size) bytes <= 32 MiB,
+ * otherwise HDF_ETOOBIG.  The products run on the CUDA-core kernels: for an FP64 factor the
+ * result equals hdf_matvec's, for an FP32 factor (where hdf_matvec may use the tensor cores) it
+ * agrees to FP32 rounding.  The first call on each device looks up the array's device address
+ * with that device current; make that first call before any stream capture.  All calls share
+ * the one array (each call overwrites every entry it reads), so calls whose executions overlap
+ * on the GPU -- on different streams or from different threads -- race and must be serialised
+ * by the caller.  Arguments and layout as hdf_matvec. */
 hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev, int64_t ldv, int ncols,
                               void* Y_dev, int64_t ldy, hdf_stream stream);
 
@@ -306,8 +309,28 @@ hdf_status hdf_factor_export_y(const hdf_factor* f, void* V_host);
 hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3);
 
 /* *flag = 1 if a device kernel working on this factor gave up a bounded wait (its results
- * are then invalid), else 0; clears the flag.  Synchronises the device. */
+ * are then invalid), else 0; clears the flag.  Synchronises the device.  The synchronising
+ * calls (hdf_solve, hdf_matvec_adjoint) make the same check themselves and return
+ * HDF_ETIMEOUT, with their outputs invalid, when a wait of theirs ran out. */
 hdf_status hdf_device_errors(const hdf_factor* f, int* flag);
+
+/* ------------------------------------------------------------- failure detection ---- */
+/* Not part of the method (the paper has no failure model): hooks that let a caller or a test
+ * drive the library's failure paths without faulting the GPU. */
+
+/* Limit, in clock cycles of the current device, of every wait of the tensor-core kernels on
+ * work (a tile, a buffer, an accumulator); cycles <= 0 restores the default (4e9, about 2 s).
+ * A kernel whose wait runs out sets its factor's error flag, lets every copy and MMA it issued
+ * finish (those drains keep the default limit), frees its tensor memory and returns; the
+ * factor stays usable.  *previous (may be NULL) receives the old limit.  Applies to every
+ * later launch on the current device until changed; synchronous. */
+hdf_status hdf_set_wait_limit(long long cycles, long long* previous);
+
+/* Host-side fault injection: the device allocation `after` allocations from now (0 = the next
+ * one) made by the library reports out-of-memory without allocating, once; a negative value
+ * cancels a pending injection.  The call that meets it returns HDF_ENOMEM with its output
+ * buffers untouched (hdf_build and friends set *out = NULL).  Process-wide. */
+void hdf_debug_fail_alloc(long long after);
 
 /* Release a factor (NULL is ignored). */
 void hdf_free(hdf_factor* f);

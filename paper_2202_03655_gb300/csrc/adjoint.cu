@@ -559,7 +559,7 @@ hdf_status run(hdf_factor* f, const double* x, const T* V, int64_t ldv, const T*
     }
     if (value) *value = fval;
     HDF_CUDA(cudaStreamSynchronize(st));
-    return HDF_OK;
+    return hdf::take_device_error(f);
 }
 
 }  // namespace

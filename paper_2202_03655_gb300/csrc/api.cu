@@ -23,6 +23,20 @@ static thread_local std::string g_err;
 constexpr int kMu2Sample = 512;     // mu2 from all pairs of at most this many strided points
 namespace hdf {
 std::atomic<long long> g_launches(0);     // kernels launched by this library
+std::atomic<long long> g_alloc_fail_at(-1);
+
+hdf_status take_device_error(const hdf_factor* f) {
+    int flag = 0;
+    HDF_CUDA(cudaDeviceSynchronize());
+    for (const hdf_factor* g : {f, (const hdf_factor*)f->ypart}) {
+        if (!g || !g->dev_err.p) continue;
+        int fl = 0;
+        HDF_CUDA(cudaMemcpy(&fl, g->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (fl) HDF_CUDA(cudaMemset(g->dev_err.p, 0, sizeof(int)));
+        flag |= fl;
+    }
+    return flag ? fail(HDF_ETIMEOUT, "a device kernel gave up a bounded wait; its results are invalid") : HDF_OK;
+}
 
 hdf_status fail(hdf_status s, const std::string& msg) {
     g_err = msg;
@@ -179,15 +193,17 @@ void hdf_free(hdf_factor* f) {
 hdf_status hdf_device_errors(const hdf_factor* f, int* flag) {
     if (!f || !flag) return fail(HDF_EINVAL, "hdf_device_errors: null argument");
     *flag = 0;
-    HDF_CUDA(cudaDeviceSynchronize());
-    for (const hdf_factor* g : {f, (const hdf_factor*)f->ypart}) {
-        if (!g || !g->dev_err.p) continue;
-        int fl = 0;
-        HDF_CUDA(cudaMemcpy(&fl, g->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        HDF_CUDA(cudaMemset(g->dev_err.p, 0, sizeof(int)));
-        *flag |= fl;
-    }
-    return HDF_OK;
+    const hdf_status s = take_device_error(f);
+    if (s == HDF_ETIMEOUT) *flag = 1;
+    return s == HDF_ETIMEOUT ? HDF_OK : s;
+}
+
+hdf_status hdf_set_wait_limit(long long cycles, long long* previous) {
+    return hdf::set_wait_limit(cycles, previous);
+}
+
+void hdf_debug_fail_alloc(long long after) {
+    hdf::g_alloc_fail_at.store(after >= 0 ? after : -1);
 }
 
 hdf_status hdf_matvec_timings(const hdf_factor* f, double* ms3) {
@@ -891,14 +907,17 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
             HDF_CUDA(cudaGetLastError());
         }
         HDF_CUDA(cudaEventRecord(g1, st));
-        f->G.resize((size_t)r * r);
-        HDF_CUDA(cudaMemcpyAsync(f->G.data(), Gd.p, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
+        std::vector<double> G((size_t)r * r);
+        HDF_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
         HDF_CUDA(cudaStreamSynchronize(st));
         float gms = 0.f;
         cudaEventElapsedTime(&gms, g0, g1);
-        f->info.t_ms[6] = gms;
         cudaEventDestroy(g0);
         cudaEventDestroy(g1);
+        // a Gram matrix from a kernel that gave up a wait is not kept
+        if (hdf_status e = take_device_error(f); e != HDF_OK) return e;
+        f->G.swap(G);
+        f->info.t_ms[6] = gms;
     }
     if (r > 0 && f->core_lambda != lambda) {
         f->LU = f->G;
@@ -914,7 +933,8 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
         f->core_lambda = lambda;
     }
     hdf_status s = woodbury_apply<T>(f, lambda, B, ldb, ncols, X, ldx, st);
-    if (s != HDF_OK || refine <= 0) return s;
+    if (s != HDF_OK) return s;
+    if (refine <= 0) return take_device_error(f);
     DevBuf Rb, KX, dX;
     HDF_CUDA(Rb.alloc(sizeof(T) * (size_t)n * ncols));
     HDF_CUDA(KX.alloc(sizeof(T) * (size_t)n * ncols));
@@ -940,7 +960,7 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
         HDF_CUDA(cudaGetLastError());
     }
     HDF_CUDA(cudaStreamSynchronize(st));
-    return HDF_OK;
+    return take_device_error(f);
 }
 
 extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev, int64_t ldb, int ncols,

@@ -25,6 +25,11 @@ void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk);
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
                   double* part, float* work, int* err, cudaStream_t st);
 hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G, int* err, cudaStream_t st);
+// Work-wait limit (clock cycles) of the tensor-core kernels on the current device.
+hdf_status set_wait_limit(long long cycles, long long* previous);
+// HDF_ETIMEOUT (and the flag cleared) if a kernel on f gave up a bounded wait since the last
+// check; synchronises the device.
+hdf_status take_device_error(const hdf_factor* f);
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
                  int64_t ldb, float beta, float* Y, int64_t ldy, float* work, int* err, cudaStream_t st);
 
@@ -38,15 +43,28 @@ hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const
 
 #define HDF_COUNT_LAUNCH() hdf::g_launches.fetch_add(1, std::memory_order_relaxed)
 
+// A failed CUDA call returns HDF_ECUDA, or HDF_ENOMEM when it could not allocate memory.
 #define HDF_CUDA(call)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
         if (e_ != cudaSuccess) {                                                              \
-            return hdf::fail(HDF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+            if (e_ == cudaErrorMemoryAllocation) cudaGetLastError();                          \
+            return hdf::fail(e_ == cudaErrorMemoryAllocation ? HDF_ENOMEM : HDF_ECUDA,        \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));             \
         }                                                                                     \
     } while (0)
 
 namespace hdf {
+// Host-side fault injection for tests (hdf_debug_fail_alloc): while g_alloc_fail_at >= 0 each
+// device allocation through DevBuf counts it down, and the one that finds it at 0 reports
+// cudaErrorMemoryAllocation without allocating (the countdown then stays off at -1).
+extern std::atomic<long long> g_alloc_fail_at;
+inline bool injected_alloc_failure() {
+    long long v = g_alloc_fail_at.load(std::memory_order_relaxed);
+    while (v >= 0)
+        if (g_alloc_fail_at.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
 // Keeps freed stream-ordered allocations of the current device in its default memory pool
 // (release threshold raised once per device), so that repeated builds and products reuse
 // memory instead of mapping it again.
@@ -70,6 +88,7 @@ struct DevBuf {
         release();
         bytes = b;
         pooled = false;
+        if (b && hdf::injected_alloc_failure()) return cudaErrorMemoryAllocation;
         return b ? cudaMalloc(&p, b) : cudaSuccess;
     }
     cudaError_t alloc_on(size_t b, cudaStream_t s) {
@@ -78,6 +97,7 @@ struct DevBuf {
         bytes = b;
         pooled = true;
         st = s;
+        if (b && hdf::injected_alloc_failure()) return cudaErrorMemoryAllocation;
         return b ? cudaMallocAsync(&p, b, s) : cudaSuccess;
     }
     template <typename T> T* as() const { return reinterpret_cast<T*>(p); }

@@ -557,7 +557,9 @@ hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* label
 #define KRR_CUDA(call)                                                                            \
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess) return bail(fail(HDF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+        if (e_ != cudaSuccess)                                                                    \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? HDF_ENOMEM : HDF_ECUDA,                \
+                             std::string(#call) + ": " + cudaGetErrorString(e_)));                    \
     } while (0)
     KRR_CUDA(K->perm.alloc(sizeof(int64_t) * n));
     KRR_CUDA(K->xp.alloc(sizeof(double) * n * d));

@@ -58,7 +58,14 @@ constexpr int IR = 16;                  // ring of work items handed from the U 
 constexpr int NCONS = 10;               // item consumers: B producer, MMA warp, 4 converter and 4 promotion warps
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAcol = 256;         // first TMEM column of the A buffers
-constexpr long long kWaitCycles = 4000000000ll;   // about 2 s at 2 GHz
+// Bounded waits.  A wait on work (a tile, a buffer, an accumulator, a work item) gives up after
+// d_wait_cycles clock cycles of this device (about 2 s by default; hdf_set_wait_limit changes it,
+// so that tests can make a wait run out).  The drains at exit -- every copy a producer issued
+// has landed, every MMA the issuing warp committed has completed -- keep kDrainCycles whatever
+// the work limit, so a CTA never frees its TMEM or leaves while its own copies are in flight.
+constexpr long long kDefaultWaitCycles = 4000000000ll;   // about 2 s at 2 GHz
+constexpr long long kDrainCycles = 4000000000ll;
+__device__ long long d_wait_cycles = kDefaultWaitCycles;
 
 // B ring depth (2 BN rows x 64 K per stage, hi and lo stacked): the B tiles come mostly from L2
 // but with ~2000 cycles of latency, so the ring takes what shared memory leaves beside the U
@@ -86,15 +93,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Waits for the completion of the phase with the given parity; false if the clock limit passes.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// The work-wait limit of this device (read on the slow path of a wait only).
+__device__ __forceinline__ long long wait_limit() { return *reinterpret_cast<volatile long long*>(&d_wait_cycles); }
+// Waits for the completion of the phase with the given parity; false once `limit` cycles pass.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit) {
     const uint32_t a = smem_u32(bar);
     if (mbar_try(a, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try(a, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+// A wait on work: the device's work-wait limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    if (mbar_try(a, parity)) return true;
+    return mbar_wait_for(bar, parity, wait_limit());
 }
 // True in exactly one lane of a converged warp.
 __device__ __forceinline__ bool elect_one() {
@@ -278,11 +293,12 @@ __device__ __forceinline__ bool wait_done(Smem<BN>& sm, uint32_t j) {
 __device__ __forceinline__ bool mbar_wait_lanes(uint32_t a, uint32_t parity) {
     bool mine = mbar_try(a, parity);
     if (__all_sync(0xffffffffu, mine)) return true;
+    const long long lim = wait_limit();
     const long long t0 = clock64();
     for (;;) {
         if (!mine) mine = mbar_try(a, parity);
         if (__all_sync(0xffffffffu, mine)) return true;
-        if (__any_sync(0xffffffffu, clock64() - t0 > kWaitCycles)) return false;
+        if (__any_sync(0xffffffffu, clock64() - t0 > lim)) return false;
     }
 }
 
@@ -377,7 +393,7 @@ template <int BN>
 __device__ __forceinline__ void mma_drain(Smem<BN>& sm, bool ok, int* err) {
     if (elect_one()) mma_commit(sm.drain);
     __syncwarp();
-    if (!mbar_wait(sm.drain, 0)) ok = false;
+    if (!mbar_wait_for(sm.drain, 0, kDrainCycles)) ok = false;
     if (!ok && (threadIdx.x & 31) == 0) atomicExch(err, 1);
 }
 
@@ -385,7 +401,7 @@ __device__ __forceinline__ void mma_drain(Smem<BN>& sm, bool ok, int* err) {
 __device__ __forceinline__ bool producer_drain(uint64_t* full, int depth, uint32_t it) {
     bool ok = true;
     for (uint32_t q = (it > (uint32_t)depth ? it - depth : 0); q < it; ++q)
-        if (!mbar_wait(&full[q % depth], (q / depth) & 1)) ok = false;
+        if (!mbar_wait_for(&full[q % depth], (q / depth) & 1, kDrainCycles)) ok = false;
     return ok;
 }
 
@@ -878,6 +894,16 @@ hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G,
         tc::k_reduce_gram<<<(unsigned)((r * 64 + 255) / 256), 256, 0, st>>>(part.as<double>(), nch, r, j0, G, r);
         HDF_CUDA(cudaGetLastError());
     }
+    return HDF_OK;
+}
+
+// Work-wait limit of the current device in clock cycles (<= 0: the default, about 2 s).
+hdf_status set_wait_limit(long long cycles, long long* previous) {
+    long long prev = 0;
+    HDF_CUDA(cudaMemcpyFromSymbol(&prev, tc::d_wait_cycles, sizeof(prev)));
+    const long long v = cycles > 0 ? cycles : tc::kDefaultWaitCycles;
+    HDF_CUDA(cudaMemcpyToSymbol(tc::d_wait_cycles, &v, sizeof(v)));
+    if (previous) *previous = prev;
     return HDF_OK;
 }
 

@@ -77,6 +77,8 @@ SIGNATURES = {
     "hdf_krr_solve": (_c_int, [_vp, _vp, _c_dbl, _c_int, _vp, ctypes.POINTER(_c_int), _pdbl, _vp]),
     "hdf_krr_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_i64), _pdbl]),
     "hdf_krr_free": (None, [_vp]),
+    "hdf_set_wait_limit": (_c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    "hdf_debug_fail_alloc": (None, [ctypes.c_longlong]),
     "hdf_status_string": (ctypes.c_char_p, [_c_int]),
     "hdf_last_error": (ctypes.c_char_p, []),
     "hdf_launch_count": (ctypes.c_longlong, []),
@@ -150,6 +152,20 @@ def radial_cores(a, p, d):
         out.append(buf[off:off + nb * nb].reshape(nb, nb))
         off += nb * nb
     return out
+
+
+def set_wait_limit(cycles):
+    """Limit (clock cycles) of the tensor-core kernels' waits on the current device; <= 0 restores
+    the default.  Returns the previous limit."""
+    prev = ctypes.c_longlong()
+    _check(lib().hdf_set_wait_limit(int(cycles), ctypes.byref(prev)))
+    return prev.value
+
+
+def debug_fail_alloc(after):
+    """Make the device allocation `after` allocations from now report out-of-memory (once);
+    a negative value cancels."""
+    lib().hdf_debug_fail_alloc(int(after))
 
 
 def launch_count():
