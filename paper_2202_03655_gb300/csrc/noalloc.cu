@@ -1,13 +1,15 @@
-// hdf_matvec_noalloc: K~ V through the same kernels as hdf_matvec, with its work space in a
-// fixed array that is part of the loaded library instead of memory obtained at call time.
+// hdf_matvec_noalloc: K~ V with its work space in a fixed array that is part of the loaded
+// library instead of memory obtained at call time.
 //
-// Some callers cannot allocate device memory at the moment they need a product: code that
-// runs while a CUDA stream is being captured (cudaMalloc/cudaFree are not stream operations
-// and would break or be refused by the capture), code whose device memory is owned by
-// another allocator (a framework's caching pool holds the free memory, so a raw cudaMalloc
-// can fail even though the framework has room), and latency-critical or real-time loops
-// that reserve everything at start-up and must not enter the CUDA allocator.  For them
-// the per-call partial sums live in g_noalloc_scratch below.
+// Some callers cannot allocate device memory at the moment they need a product: code whose
+// device memory is owned by another allocator (a framework's caching pool holds the free
+// memory, so a raw cudaMalloc can fail even though the framework has room), and latency-
+// critical or real-time loops that reserve everything at start-up and must not enter the CUDA
+// allocator.  For them the per-call partial sums live in g_noalloc_scratch below.
+//
+// The products always run on the CUDA-core tile kernels (k_utv_tile, k_uw_tile, as hdf_matvec
+// does for FP64 factors).  For FP32 factors hdf_matvec uses the tensor cores where it can, so
+// there the two entry points agree to FP32 rounding, not bit for bit, and this one is slower.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,7 +90,7 @@ hdf_status run(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, in
     const int64_t w_doubles = (r * cmax * (int64_t)sizeof(T) + 7) / 8;
     const int64_t per_chunk = r * cmax;
     if (w_doubles + per_chunk > (int64_t)kScratchDoubles)
-        return hdf::fail(HDF_ETOOBIG, "hdf_matvec_noalloc: rank * min(ncols, 64) * (8 + element size) bytes "
+        return hdf::fail(HDF_ETOOBIG, "hdf_matvec_noalloc: ldu * min(ncols, 64) * (8 + element size) bytes "
                                       "exceeds the fixed 32 MiB work space");
     double* base = nullptr;
     hdf_status s = scratch_address(&base);
