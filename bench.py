@@ -36,6 +36,11 @@ Other workloads (--workload):
                   clusters, Gaussian l = 0.5, lambda = 1, HDF blocks at tol 1e-3 (FP32 bulk);
                   step = hdf_kmeans + hdf_krr_build + hdf_krr_solve (rtol 1e-6) +
                   hdf_kernel_matvec for the test predictions; value = training points / s.
+  normal5_cauchy  the large-rank row: n = 4,000,000 points in d = 5 (rotated standard normal,
+                  standardised), Cauchy l = 2, tol 1e-4, FP32, 16 columns; U would take about
+                  1.4 TB, so hdf_build keeps the matrix-free rows (the harmonic tails Z and the
+                  first level factor times the radial factor) and K~V runs over them; step =
+                  hdf_build + K~V; the dominant kernels are FP32-ALU-bound GEMMs.
   cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a
                   wider Gaussian cloud, Gaussian l = 1.5, tol 1e-6, FP32; step = hdf_build_cross
                   + K~ V (V: 16 columns over Y) + K~^T W (W: 16 columns over X); value = points
@@ -65,6 +70,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1663, "k_tc_utv": 4.1500, "k_tc_uw": 4.0655}
 METRICS = {
     "mixture3_matern": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
+    "normal5_cauchy": "factor-build points/s (build + 16-column K~V of a matrix-free factor: U not stored), FP32 bulk",
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
     "batch512_gauss": "batched factor-build points/s (512 sets, build + 8-column K~V each), FP32 bulk",
     "fig1_cauchy": "factor-build points/s over the time-vs-n sweep (Cauchy l=1, tol 1e-3, d 3-6, n 1e4-1e7), "
@@ -77,6 +83,8 @@ METRICS = {
                     "FP32 bulk",
 }
 FP32_LANES_PER_SM, NSM, SM_MAX_MHZ = 128, 152, 2070.0
+# points of the oracle's bounded sample where its U (n x rank, FP64) grows fast with the rank
+ORACLE_CAP = {"normal5_cauchy": 1500}
 
 
 def parse():
@@ -207,7 +215,7 @@ def blas_threads():
     return None
 
 
-SINGLE_THREAD_WORKLOADS = ("mixture3_matern", "cube4_gauss", "batch512_gauss")
+SINGLE_THREAD_WORKLOADS = ("mixture3_matern", "normal5_cauchy", "cube4_gauss", "batch512_gauss")
 SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
@@ -234,8 +242,8 @@ def oracle_once(args):
     import numpy as np
     from paper_2202_03655_gb300 import workloads as W
     w = workload_params(args)
-    if args.workload == "mixture3_matern":
-        ns = min(args.cpu_n, w["n"])
+    if args.workload in ("mixture3_matern", "normal5_cauchy"):
+        ns = min(args.cpu_n, w["n"], ORACLE_CAP.get(args.workload, w["n"]))
         x = W.points(args.workload, n=ns)
         V = np.random.default_rng(1).standard_normal((ns, w["ncols"]))
         cpu_oracle_step(x, w, V, args.p_max)
@@ -462,7 +470,7 @@ def run_reference(args):
                 "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
-    ns = min(args.cpu_n, w["n"])
+    ns = min(args.cpu_n, w["n"], ORACLE_CAP.get(args.workload, w["n"]))
     x = W.points(args.workload, n=ns)
     V = np.random.default_rng(1).standard_normal((ns, w["ncols"]))
     for _ in range(args.warmup):
@@ -651,6 +659,108 @@ def bench_adjoint(args):
                                      "tf32_peak_source": "measured bf16 cuBLAS burst x 1.1/2.25 (nominal TF32/BF16)"},
                            "rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound,
                            "value_f": recs[-1][2]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_mfree(args):
+    """Large-rank row: hdf_build (matrix-free rows, chosen by the build) + K~V with 16 columns."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    n, d, c = w["n"], w["d"], w["ncols"]
+    x_np = W.points(args.workload, n=n)
+    V_np = np.asfortranarray(W.rng(w["idx"] + 100).standard_normal((n, c)).astype(np.float32))
+    x = torch.from_numpy(x_np).to(dev)
+    Vc = torch.from_numpy(np.ascontiguousarray(V_np.T)).to(dev)
+    Yc = torch.empty_like(Vc)
+    stream = torch.cuda.current_stream(dev)
+
+    def one(keep):
+        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
+        rec = (f.info, f.matvec_timings()) if keep else None
+        f.free()
+        return rec
+
+    ms_total, recs, launches, clocks = _timed(args, ws, rank, dev, stream, one)
+    info = recs[-1][0]
+    mv = np.array([r[1] for r in recs]).mean(axis=0)          # U^T V, reduce, U W (ms)
+    value = whole_job_rate(n, ws, args.steps, ms_total)
+    # accuracy outside the timed region: sampled rows of K~ V against the exact kernel
+    f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+    f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
+    rows = np.sort(W.rng(7).choice(n, 256, replace=False))
+    exact = exact_rows_matvec(x, w["kernel"], w["ell"], Vc.t().double(), rows)
+    approx = Yc.t()[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+    rel_err = float(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    f.free()
+    # roofline: the two products are FP32 GEMMs on the CUDA cores over the stored Z rows; the
+    # algorithmic work is that of K~V on the factor, 2 n r c flops per product
+    r = info.rank
+    flops = 2.0 * n * r * c
+    peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    kern = {"k_mf_utv": float(mv[0]), "k_mf_uw": float(mv[2])}
+    dom = max(kern, key=kern.get)
+    roof = {"kernel": dom, "bound": "alu", "achieved": flops / (kern[dom] / 1e3) / 1e12, "peak": peak_alu,
+            "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
+            "traffic": None, "algorithmic_flops": flops, "ms_per_launch": kern[dom]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D x and V; build; K~V; D2H of Y
+    xh = torch.from_numpy(x_np).pin_memory()
+    Vh = torch.from_numpy(np.ascontiguousarray(V_np.T)).pin_memory()
+    Yh = torch.empty_like(Vh).pin_memory()
+    xd = torch.empty_like(x)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 2))
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        Vc.copy_(Vh, non_blocking=True)
+        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
+        Yh.copy_(Yc, non_blocking=True)
+        f.free()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / k2
+    e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8 + n * c * 4,
+           "d2h_bytes_per_step": n * c * 4, "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        ns = min(args.cpu_n, n, ORACLE_CAP[args.workload])
+        ts = cpu_oracle_step(x_np[:ns], w, V_np[:ns].astype(np.float64), args.p_max)
+        cpu = cpu_baseline_line(ns / ts, f"first {ns} of the {n} points, one full step (build + K~V, {c} columns), "
+                                         "FP64 numpy", args, args.workload)
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "d": d, "kernel": w["kernel"], "lengthscale": w["ell"],
+                           "tol": w["tol"], "ncols": c, "p_max": args.p_max, "p": info.p, "reached": bool(info.reached),
+                           "rank": r, "ldu": info.ldu, "matrix_free": bool(info.matrix_free),
+                           "U_bytes_if_stored": n * info.ldu * 4, "stored_bytes": n * info.mf_row * 4,
+                           "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (the stored rows are "
+                           f"{n * info.mf_row * 4 / 1e9:.0f} GB)"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound,
+                           "cheb_tail": info.cheb_tail, "build_ms": float(info.t_ms[7]),
+                           "build_phase_ms": [float(info.t_ms[q]) for q in range(8)],
+                           "kv_ms": float(mv.sum()), "kernel_ms": {"k_mf_utv": float(mv[0]), "k_reduce_scale": float(mv[1]),
+                                                                    "k_mf_uw": float(mv[2])},
+                           "s_k": [int(info.s_k[k]) for k in range(info.L + 1)]}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -1275,6 +1385,8 @@ def main():
         return run_reference(args)
     if args.workload == "cube4_gauss":
         return bench_adjoint(args)
+    if args.workload == "normal5_cauchy":
+        return bench_mfree(args)
     if args.workload == "batch512_gauss":
         return bench_batch(args)
     if args.workload == "cross3_gauss":

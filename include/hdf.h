@@ -72,6 +72,17 @@ typedef struct {
 
 /* Run the matvec GEMMs of an FP32 factor on the CUDA cores instead of the tensor cores. */
 #define HDF_FLAG_CUDA_CORES 1
+/* Build the matrix-free form (d >= 4): U is not stored.  Every harmonic of degree k with chain
+ * (m = mu_1, mu_2, ...) is P_0(m, k - m) times a harmonic Z_m of degree m in d - 1 dimensions
+ * (the product form of the chain construction), so per point the factor keeps the Z row
+ * (sum_m |H_m^(d-1)| values) and the row of P_0(m, k - m) F[k, s] (sum_k s_k (k + 1) values)
+ * instead of the U row (sum_k s_k |H_k| values), and hdf_matvec / hdf_matvec_transpose /
+ * hdf_matvec_adjoint form U^T V and U W from them.  hdf_build selects this form by itself
+ * (for d >= 4) when U would take more than 80% of the device's memory -- the cost that
+ * Sec. 3.6 counts and Sec. 3.7 names as the method's limit.  A matrix-free factor has no
+ * solve (HDF_EINVAL), no hdf_matvec_noalloc (HDF_EINVAL), hdf_factor_device gives U_dev = NULL
+ * and hdf_factor_export accepts U_host = NULL only.  hdf_info.matrix_free reports the form. */
+#define HDF_FLAG_MATRIX_FREE 2
 
 #define HDF_MAX_D 8
 #define HDF_MAX_L 64
@@ -106,6 +117,8 @@ typedef struct {
                                7 whole build */
     int64_t n_y;            /* cross factor (hdf_build_cross): points of the second set Y, the
                                rows of its factor V; 0 for a symmetric factor U S U^T */
+    int matrix_free;        /* 1 if U is not stored (HDF_FLAG_MATRIX_FREE) */
+    int64_t mf_row;         /* matrix-free form: stored values per point (Z and P_0 F rows) */
 } hdf_info;
 
 /* ---------------------------------------------------------------- factorization ---- */

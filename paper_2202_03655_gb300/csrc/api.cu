@@ -169,6 +169,7 @@ extern "C" {
 
 hdf_status hdf_factor_export(const hdf_factor* f, void* U_host, double* S_host) {
     if (!f) return fail(HDF_EINVAL, "hdf_factor_export: null factor");
+    if (f->mf.on && U_host) return fail(HDF_EINVAL, "hdf_factor_export: a matrix-free factor stores no U");
     if (hdf_status e = export_u(f, U_host); e != HDF_OK) return e;
     if (S_host && f->info.rank > 0) std::memcpy(S_host, f->S_host.data(), f->info.rank * sizeof(double));
     return HDF_OK;
@@ -186,6 +187,8 @@ void hdf_free(hdf_factor* f) {
     // any stream still reads them, then return them to the pool on the legacy stream
     cudaDeviceSynchronize();
     f->U.st = nullptr;
+    f->mf.Z.st = nullptr;
+    f->mf.A0F.st = nullptr;
     if (f->ypart) f->ypart->U.st = nullptr;
     delete f;
 }
@@ -227,6 +230,7 @@ struct BuildOpts {
     int p_max = 64;
     double eta = 1.0;
     bool use_tc = true;
+    bool matrix_free = false;
 };
 
 hdf_status parse_opts(const hdf_options* opt, const char* who, BuildOpts& o) {
@@ -234,6 +238,7 @@ hdf_status parse_opts(const hdf_options* opt, const char* who, BuildOpts& o) {
         if (opt->p_max > 0) o.p_max = opt->p_max;
         if (opt->eta > 0) o.eta = opt->eta;
         if (opt->flags & HDF_FLAG_CUDA_CORES) o.use_tc = false;
+        if (opt->flags & HDF_FLAG_MATRIX_FREE) o.matrix_free = true;
     }
     if (o.p_max > 2 * HDF_MAX_L) return fail(HDF_ETOOBIG, std::string(who) + ": p_max > 128");
     o.p_max -= o.p_max % 2;
@@ -321,6 +326,7 @@ hdf_factor* new_factor(int64_t npts, int d, hdf_kernel kernel, double ell, doubl
                        const DegreePlan& dp, const FactorChoice& fc) {
     hdf_factor* f = new hdf_factor();
     f->use_tc = o.use_tc;
+    f->mf.on = o.matrix_free;           // requested; build_device may also choose it
     f->kernel = kernel;
     f->ell = ell;
     f->tol = tol;
@@ -454,6 +460,7 @@ hdf_status hdf_build_cross(const double* x_dev, int64_t m, const double* y_dev, 
         return fail(HDF_EINVAL, "hdf_build_cross: bad argument (need m,n>=1, 3<=d<=8, l>0, 0<tol<1)");
     BuildOpts o;
     if (hdf_status e = parse_opts(opt, "hdf_build_cross", o); e != HDF_OK) return e;
+    if (o.matrix_free) return fail(HDF_EINVAL, "hdf_build_cross: the matrix-free form is for symmetric factors");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     double tph[HDF_NPHASE] = {};
     const double t_start = now_ms();
@@ -667,6 +674,37 @@ static hdf_status group_uw(const hdf_factor* fout, int64_t r, const T* W, int cg
     return HDF_OK;
 }
 
+// K~ V of a matrix-free factor (symmetric; alpha = 1, beta = 0), per group of <= 64 columns:
+// partial sums of U^T V over chunks of points, their FP64 sum scaled by S, then U W.
+template <typename T>
+static hdf_status matvec_free(const hdf_factor* f, const T* V, int64_t ldv, int ncols, T* Y, int64_t ldy,
+                              const T* S_scale, T alpha, const T* B, T beta, cudaStream_t st) {
+    if (B || alpha != (T)1 || beta != (T)0) return fail(HDF_EINVAL, "matrix-free factor: plain products only");
+    const int64_t n = f->info.n, r = f->info.ldu;
+    const int cmax = std::min(ncols, kMaxGroup);
+    const int64_t nch = (n + FreeFactor::kChunk - 1) / FreeFactor::kChunk;
+    DevBuf part, W;
+    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * cmax * r, st));
+    HDF_CUDA(W.alloc_on(sizeof(T) * (size_t)r * cmax, st));
+    hdf_factor* fm = const_cast<hdf_factor*>(f);
+    const bool rec = fm->mv_ev[0] != nullptr;
+    for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
+        const int cg = std::min(kMaxGroup, ncols - j0);
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
+        int np = 0;
+        if (hdf_status e = mf_utv<T>(f, V + j0 * ldv, ldv, cg, part.as<double>(), &np, st); e != HDF_OK) return e;
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
+        HDF_COUNT_LAUNCH();
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), np, r, cg, S_scale,
+                                                                               W.as<T>(), nullptr);
+        HDF_CUDA(cudaGetLastError());
+        if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
+        if (hdf_status e = mf_uw<T>(f, W.as<T>(), cg, Y + j0 * ldy, ldy, st); e != HDF_OK) return e;
+        if (rec && j0 == 0) { HDF_CUDA(cudaEventRecord(fm->mv_ev[3], st)); fm->mv_recorded = true; }
+    }
+    return HDF_OK;
+}
+
 template <typename T>
 // Y = alpha U_f (S_scale .* (U_in^T V)) + beta B, where U_in is the factor of fin (rows of V)
 // and U_f that of f (rows of Y): fin = f for K~ V of a symmetric factor; for a cross factor
@@ -690,6 +728,7 @@ static hdf_status matvec_t(const hdf_factor* f, const hdf_factor* fin, const T* 
         return HDF_OK;
     }
     const int cmax = std::min(ncols, kMaxGroup);
+    if (f->mf.on) return matvec_free<T>(f, V, ldv, ncols, Y, ldy, S_scale, alpha, B, beta, st);
     GroupWork g;
     if (hdf_status e = group_setup(fin, f, r, cmax, g, st); e != HDF_OK) return e;
     DevBuf W;
@@ -723,6 +762,18 @@ hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const
                       cudaStream_t st) {
     const int64_t r = f->info.ldu;      // padded width (rows of W)
     if (c < 1 || c > kMaxGroup) return fail(HDF_EINVAL, "utv_reduce: 1 <= c <= 64");
+    if (f->mf.on) {
+        const int64_t nch = (f->info.n + FreeFactor::kChunk - 1) / FreeFactor::kChunk;
+        DevBuf part;
+        HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * c * r, st));
+        int np = 0;
+        if (hdf_status e = mf_utv<T>(f, V, ldv, c, part.as<double>(), &np, st); e != HDF_OK) return e;
+        HDF_COUNT_LAUNCH();
+        dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), np, r, c, S_scale,
+                                                                              W, Wd);
+        HDF_CUDA(cudaGetLastError());
+        return HDF_OK;
+    }
     GroupWork g;
     if (hdf_status e = group_setup(f, f, r, c, g, st); e != HDF_OK) return e;
     int np = 0;
@@ -969,6 +1020,7 @@ extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev,
         ldx < f->info.n || refine_steps < 0)
         return fail(HDF_EINVAL, "hdf_solve: bad argument");
     if (f->ypart) return fail(HDF_EINVAL, "hdf_solve: a cross factor K(X, Y) has no (lambda I + K~) system");
+    if (f->mf.on) return fail(HDF_EINVAL, "hdf_solve: the Woodbury core needs the stored U (matrix-free factor)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (f->prec == HDF_FP64)
         return solve_t<double>(f, lambda, (const double*)B_dev, ldb, ncols, (double*)X_dev, ldx, refine_steps, st);
@@ -976,6 +1028,14 @@ extern "C" hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev,
 }
 
 // ---------------------------------------------------------- device part of build
+namespace hdf {
+// The matrix-free rows of a factor (mfree.cu): Z and P_0 F per point from the radial factors F.
+template <typename T>
+hdf_status mf_write(hdf_factor* f, const double* x, int64_t n, int d, const dev::Center& cen, double inv2R,
+                    const FactorChoice& fc, const DeviceTables& tb, const void* F, int64_t ldF, const void* coefA,
+                    const void* coefB, cudaStream_t st);
+}  // namespace hdf
+
 template <typename T>
 static std::vector<T> cast_vec(const std::vector<double>& v) {
     std::vector<T> o(v.size());
@@ -1006,7 +1066,12 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaMemcpyAsync(f->S.p, Sd.data(), sizeof(T) * I.ldu, cudaMemcpyHostToDevice, st));
     }
     const size_t ubytes = sizeof(T) * (size_t)n * (size_t)I.ldu;
-    if (f->U.alloc_on(ubytes, st) != cudaSuccess) {
+    // the matrix-free form when asked for, or when U would not fit (d >= 4 only)
+    bool mfree = f->mf.on && r > 0;
+    if (mfree && d < 4) return fail(HDF_EINVAL, "hdf_build: the matrix-free form needs d >= 4");
+    if (!mfree && d >= 4 && r > 0 && !FreeFactor::fits((int64_t)ubytes)) mfree = true;
+    f->mf.on = false;                    // set by mf_write once the rows exist
+    if (!mfree && f->U.alloc_on(ubytes, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(HDF_ENOMEM, "hdf_build: cannot allocate U (" + std::to_string(ubytes) + " bytes)");
     }
@@ -1122,8 +1187,14 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         HDF_CUDA(cudaGetLastError());
     }
     HDF_CUDA(cudaEventRecord(ev[1], st));
+    if (mfree) {
+        // A5b, matrix-free: the Z and P_0 F rows instead of U
+        if (hdf_status e = mf_write<T>(f, x, n, d, cen, inv2R, fc, tb, dF.p, ldF, dA.p, dB.p, st); e != HDF_OK)
+            return e;
+        I.matrix_free = 1;
+        I.mf_row = (int64_t)f->mf.ldZ + f->mf.ldA;
+    } else {
     // A5b: harmonics and U
-    {
         dev::UWParams P{};
         P.x = x; P.n = n; P.d = d; P.c = cen; P.inv2R = inv2R;
         P.L = L_used; P.tri = ht.tri;

@@ -646,6 +646,79 @@ __host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int 
     return ((levels * tri + 2 * L + 1 + (pre ? nYp : 0) + nF + 1) + 3) & ~3;
 }
 
+// Direction x_hat of point i (differences in FP64, normalisation in the bulk precision T; the
+// zero vector gets e_0), then the level tables of the normalised three-term recurrences
+// (levels x tri, lanes over mu') and the trigonometric powers (x0 + i x1)^mu times the
+// normalisers (2L+1, index L + mu), written by one warp into its shared tbl and trig.
+template <typename T>
+__device__ __forceinline__ void point_harmonic_tables(const double* __restrict__ x, int d, const Center& cen,
+                                                      double inv2R, int L, int tri, const T* cA, const T* cB,
+                                                      T* tbl, T* trig, int64_t i, int lane) {
+    const int levels = d - 2;
+    // FP32 factors: lane j forms coordinate j once and the warp shares it by shuffles (FP64
+    // issues at a small fraction of the FP32 rate here).
+    T xh[kMaxD];
+    T s = (T)0;
+    if constexpr (sizeof(T) == 4) {
+        double cj = cen.c[0];                    // this lane's centre coordinate (register selects)
+#pragma unroll
+        for (int j = 1; j < kMaxD; ++j) cj = (lane == j) ? cen.c[j] : cj;
+        const double xd = (lane < d) ? (x[i * d + lane] - cj) * inv2R : 0.0;   // one FP64 sub, mul
+        const float xf = (float)xd;
+        for (int j = 0; j < d; ++j) { xh[j] = __shfl_sync(0xffffffffu, xf, j); s += xh[j] * xh[j]; }
+    } else {
+        for (int j = 0; j < d; ++j) { xh[j] = (T)((x[i * d + j] - cen.c[j]) * inv2R); s += xh[j] * xh[j]; }
+    }
+    if (s > (T)0) {
+        const T inv = (T)1 / sqrt(s);
+        for (int j = 0; j < d; ++j) xh[j] *= inv;
+    } else {
+        for (int j = 0; j < d; ++j) xh[j] = (j == 0) ? (T)1 : (T)0;
+    }
+    // level tables: lanes over mu'
+    for (int j = 0; j < levels; ++j) {
+        const int D = d - 1 - j;
+        T q = (T)0;
+        for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
+        const T z = (T)xh[D], qq = (T)q;
+        const T* A = cA + j * tri;
+        const T* B = cB + j * tri;
+        T* tb = tbl + j * tri;
+        for (int mu = lane; mu <= L; mu += 32) {
+            const int o = mu * (L + 1) - mu * (mu - 1) / 2;
+            const int nmax = L - mu;
+            T pm2 = A[o];
+            tb[o] = pm2;
+            if (nmax >= 1) {
+                T pm1 = A[o + 1] * z;
+                tb[o + 1] = pm1;
+                for (int nn = 2; nn <= nmax; ++nn) {
+                    const T pn = A[o + nn] * z * pm1 - B[o + nn] * qq * pm2;
+                    tb[o + nn] = pn;
+                    pm2 = pm1;
+                    pm1 = pn;
+                }
+            }
+        }
+    }
+    // trig powers (x0 + i x1)^mu by binary powering in the bulk precision, lanes over mu
+    for (int mu = lane; mu <= L; mu += 32) {
+        T br = (T)xh[0], bi = (T)xh[1], rr = (T)1, ri = (T)0;
+        int e = mu;
+        while (e) {
+            if (e & 1) { const T t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
+            const T t = br * br - bi * bi; bi = (T)2 * br * bi; br = t;
+            e >>= 1;
+        }
+        if (mu == 0) {
+            trig[L] = (T)0.3989422804014327;             // 1/sqrt(2 pi)
+        } else {
+            trig[L + mu] = rr * (T)0.5641895835477563;   // 1/sqrt(pi)
+            trig[L - mu] = ri * (T)0.5641895835477563;
+        }
+    }
+}
+
 // One point's U row, executed by one warp.  cA/cB: level recurrences in shared memory;
 // base: this warp's shared area (P.per_warp elements, 16-byte aligned), laid out as
 // [harmonic slots (pre only)] [level tables] [trig powers] [radial factors].  pre: the
@@ -664,69 +737,7 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
     constexpr int VW = Vec2<T>::w;
-    // direction x_hat, zero vector -> e_0.  The differences are taken in FP64 and the
-    // normalisation in the bulk precision T.  FP32 factors: lane j forms coordinate j once and
-    // the warp shares it by shuffles (FP64 issues at a small fraction of the FP32 rate here).
-    T xh[kMaxD];
-    T s = (T)0;
-    if constexpr (sizeof(T) == 4) {
-        double cj = P.c.c[0];                    // this lane's centre coordinate (register selects)
-#pragma unroll
-        for (int j = 1; j < kMaxD; ++j) cj = (lane == j) ? P.c.c[j] : cj;
-        const double xd = (lane < P.d) ? (P.x[i * P.d + lane] - cj) * P.inv2R : 0.0;   // one FP64 sub, mul
-        const float xf = (float)xd;
-        for (int j = 0; j < P.d; ++j) { xh[j] = __shfl_sync(0xffffffffu, xf, j); s += xh[j] * xh[j]; }
-    } else {
-        for (int j = 0; j < P.d; ++j) { xh[j] = (T)((P.x[i * P.d + j] - P.c.c[j]) * P.inv2R); s += xh[j] * xh[j]; }
-    }
-    if (s > (T)0) {
-        const T inv = (T)1 / sqrt(s);
-        for (int j = 0; j < P.d; ++j) xh[j] *= inv;
-    } else {
-        for (int j = 0; j < P.d; ++j) xh[j] = (j == 0) ? (T)1 : (T)0;
-    }
-    // level tables: lanes over mu'
-    for (int j = 0; j < levels; ++j) {
-        const int D = P.d - 1 - j;
-        T q = (T)0;
-        for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
-        const T z = (T)xh[D], qq = (T)q;
-        const T* A = cA + j * P.tri;
-        const T* B = cB + j * P.tri;
-        T* tb = tbl + j * P.tri;
-        for (int mu = lane; mu <= P.L; mu += 32) {
-            const int o = mu * (P.L + 1) - mu * (mu - 1) / 2;
-            const int nmax = P.L - mu;
-            T pm2 = A[o];
-            tb[o] = pm2;
-            if (nmax >= 1) {
-                T pm1 = A[o + 1] * z;
-                tb[o + 1] = pm1;
-                for (int nn = 2; nn <= nmax; ++nn) {
-                    const T pn = A[o + nn] * z * pm1 - B[o + nn] * qq * pm2;
-                    tb[o + nn] = pn;
-                    pm2 = pm1;
-                    pm1 = pn;
-                }
-            }
-        }
-    }
-    // trig powers (x0 + i x1)^mu by binary powering in the bulk precision, lanes over mu
-    for (int mu = lane; mu <= P.L; mu += 32) {
-        T br = (T)xh[0], bi = (T)xh[1], rr = (T)1, ri = (T)0;
-        int e = mu;
-        while (e) {
-            if (e & 1) { const T t = rr * br - ri * bi; ri = rr * bi + ri * br; rr = t; }
-            const T t = br * br - bi * bi; bi = (T)2 * br * bi; br = t;
-            e >>= 1;
-        }
-        if (mu == 0) {
-            trig[P.L] = (T)0.3989422804014327;             // 1/sqrt(2 pi)
-        } else {
-            trig[P.L + mu] = rr * (T)0.5641895835477563;   // 1/sqrt(pi)
-            trig[P.L - mu] = ri * (T)0.5641895835477563;
-        }
-    }
+    point_harmonic_tables<T>(P.x, P.d, P.c, P.inv2R, P.L, P.tri, cA, cB, tbl, trig, i, lane);
     // this point's radial factors
     for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
     if (lane == 0) Fs[P.nF] = (T)0;

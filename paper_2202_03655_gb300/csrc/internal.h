@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,12 @@ hdf_status set_wait_limit(long long cycles, long long* previous);
 // HDF_ETIMEOUT (and the flag cleared) if a kernel on f gave up a bounded wait since the last
 // check; synchronises the device.
 hdf_status take_device_error(const hdf_factor* f);
+// Matrix-free products (mfree.cu): partial sums of U^T V (c <= 64) into part (ceil(n / 8192)
+// chunks of c x ldu, FP64; *nchunk gets the count) and Y = U W (W: ldu x c row-major, c <= 64).
+template <typename T>
+hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* part, int* nchunk, cudaStream_t st);
+template <typename T>
+hdf_status mf_uw(const hdf_factor* f, const T* W, int c, T* Y, int64_t ldy, cudaStream_t st);
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
                  int64_t ldb, float beta, float* Y, int64_t ldy, float* work, int* err, cudaStream_t st);
 
@@ -124,8 +131,28 @@ struct FactorPlan {
     bool have_dS = false;
 };
 
+// Matrix-free form (mfree.cu): U is not stored; per point the Z row (tails of the harmonic
+// chains) and the A0F row (first level factor times radial factor) replace the U row, and the
+// products run over them.  Host and device copies of the layout of planner.h's FreeTables.
+struct FreeFactor {
+    static constexpr int64_t kChunk = 8192;          // points per partial sum of U^T V
+    struct Items {                                  // U^T V tiles for one column count
+        DevBuf buf;
+        int count = 0;
+    };
+    bool on = false;
+    int L_used = 0, nZ = 0, ldZ = 0, nA = 0, ldA = 0;
+    DevBuf Z, A0F;                                  // n x ldZ, n x ldA (bulk type)
+    DevBuf dzoff, dzcnt, daoff, dacnt, dwcol;
+    std::vector<int> zoff, zcnt, aoff, acnt;
+    std::unique_ptr<Items> items[128];              // FP32 c = 1..64, then FP64
+    // true if a U of ubytes bytes may be stored on the current device (at most 80% of its memory)
+    static bool fits(int64_t ubytes);
+};
+
 struct hdf_factor {
     FactorPlan plan;
+    FreeFactor mf;
     hdf_info info{};
     int kernel = 0;
     double ell = 0, tol = 0;

@@ -128,6 +128,7 @@ extern "C" hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev,
     if (!f || !V_dev || !Y_dev || ncols < 1 || ncols > 1024 || ldv < f->info.n || ldy < f->info.n)
         return hdf::fail(HDF_EINVAL, "hdf_matvec_noalloc: bad argument");
     if (f->ypart) return hdf::fail(HDF_EINVAL, "hdf_matvec_noalloc: symmetric factors only (use hdf_matvec)");
+    if (f->mf.on) return hdf::fail(HDF_EINVAL, "hdf_matvec_noalloc: the factor stores no U (use hdf_matvec)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (f->prec == HDF_FP64)
         return run<double>(f, (const double*)V_dev, ldv, ncols, (double*)Y_dev, ldy, st);

@@ -887,4 +887,79 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     return true;
 }
 
+bool make_free_tables(const FactorChoice& fc, int d, int L, const DeviceTables& tb, FreeTables& ft,
+                      std::string& err) {
+    if (d < 4) {
+        err = "the matrix-free layout needs d >= 4";
+        return false;
+    }
+    const std::vector<int>& sk = fc.sk;
+    const int Lu = tb.L_used, levels = d - 2, stride = chain_stride(d);
+    ft.L_used = Lu;
+    ft.zoff.assign(Lu + 2, 0);
+    ft.zcnt.assign(Lu + 1, 0);
+    ft.aoff.assign(Lu + 2, 0);
+    ft.acnt.assign(Lu + 1, 0);
+    ft.zchain.clear();
+    // tails of degree m in the order of H_k: (mu_2, ..., mu_{d-2}) lexicographic, the last signed
+    std::vector<int> mu(d - 1);
+    for (int m = 0; m <= Lu; ++m) {
+        const int cnt = (int)harmonic_count(m, d - 1);
+        ft.zcnt[m] = cnt;
+        mu[1] = m;
+        std::function<void(int)> rec = [&](int pos) {
+            if (pos == d - 2) {
+                for (int v = -mu[pos - 1]; v <= mu[pos - 1]; ++v) {
+                    mu[pos] = v;
+                    for (int j = 1; j < levels; ++j) {
+                        const int mnext = std::abs(mu[j + 1]);
+                        ft.zchain.push_back((int16_t)tri_index(Lu, mnext, mu[j] - mnext));
+                    }
+                    ft.zchain.push_back((int16_t)v);
+                    for (int q = levels; q < stride; ++q) ft.zchain.push_back((int16_t)0);
+                }
+                return;
+            }
+            for (int v = 0; v <= mu[pos - 1]; ++v) {
+                mu[pos] = v;
+                rec(pos + 1);
+            }
+        };
+        rec(2);
+        const int padded = (cnt + 7) / 8 * 8;               // each block starts on a 32-byte sector
+        for (int q = cnt; q < padded; ++q)                   // padding tails: a zero trig slot
+            for (int e = 0; e < stride; ++e) ft.zchain.push_back((int16_t)(e == levels - 1 ? 0x7fff : 0));
+        ft.zoff[m + 1] = ft.zoff[m] + padded;
+    }
+    ft.nZ = ft.zoff[Lu + 1];
+    ft.ldZ = ft.nZ;                                          // a multiple of 8
+    if ((int64_t)ft.zchain.size() != (int64_t)ft.nZ * stride) {
+        err = "matrix-free tail enumeration disagrees with the harmonic counts";
+        return false;
+    }
+    // hoff[m]: offset of the tails of degree m inside H_k (the same for every k >= m)
+    std::vector<int64_t> hoff(Lu + 2, 0);
+    for (int m = 0; m <= Lu; ++m) hoff[m + 1] = hoff[m] + ft.zcnt[m];
+    ft.a0off.clear();
+    ft.afcol.clear();
+    ft.wcol.clear();
+    for (int m = 0; m <= Lu; ++m) {
+        ft.aoff[m] = (int)ft.a0off.size();
+        for (int k = m; k <= Lu; ++k) {
+            if (k > L || sk[k] == 0) continue;
+            const int dimp = tb.ktab[kTabStride * k + 5];
+            for (int s2 = 0; s2 < sk[k]; ++s2) {
+                ft.a0off.push_back(tri_index(Lu, m, k - m));
+                ft.afcol.push_back(tb.fbase[k] + s2);
+                ft.wcol.push_back((int64_t)tb.cbase[k] + (int64_t)s2 * dimp + hoff[m]);
+            }
+        }
+        ft.acnt[m] = (int)ft.a0off.size() - ft.aoff[m];
+    }
+    ft.aoff[Lu + 1] = (int)ft.a0off.size();
+    ft.nA = ft.aoff[Lu + 1];
+    ft.ldA = (std::max(ft.nA, 1) + 3) / 4 * 4;
+    return true;
+}
+
 }  // namespace hdf

@@ -141,6 +141,29 @@ struct DeviceTables {
 };
 // vw: elements per 16 bytes of the bulk type.  False if a limit is exceeded.
 bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& out, std::string& err);
+
+// Matrix-free layout (d >= 4): U is never stored.  In the chain of a harmonic of degree k,
+// (mu_1, ..., mu_{d-2}) with k >= mu_1 = m, the first level factor P_0(m, k - m) is the only
+// one that depends on k; the rest -- the levels 1..d-3 and the trigonometric factor -- form
+// Z_m^j, a harmonic of degree m in d-1 dimensions (j indexes the tails (mu_2..mu_{d-2}) in the
+// order of H_k, the same for every k >= m).  So
+//     U[i, (k, s, h = (m, j))] = F_i[k, s] P_0(m, k - m)(x_i) Z_m^j(x_i) = A0F[i, (m, k, s)] Z[i, (m, j)],
+// and per point the library keeps the Z row (sum_m |H_m^(d-1)| values) and the A0F row
+// (sum_k s_k (k + 1) values) instead of the U row (sum_k s_k |H_k|).
+struct FreeTables {
+    int L_used = 0;
+    int nZ = 0, ldZ = 0;                     // Z columns (blocks padded to 8) and row stride
+    int nA = 0, ldA = 0;                     // A0F columns and row stride (a multiple of 4)
+    std::vector<int> zoff, zcnt;             // per m <= L_used: first Z column, |H_m^(d-1)|
+    std::vector<int> aoff, acnt;             // per m: first A0F column, number of (k, s) with k >= m
+    std::vector<int16_t> zchain;             // nZ x chain_stride(d): level-1..d-3 offsets, trig index
+    std::vector<int32_t> a0off;              // nA: level-0 table offset of P_0(m, k - m)
+    std::vector<int32_t> afcol;              // nA: F column fbase[k] + s
+    std::vector<int64_t> wcol;               // nA: padded U column of (k, s, h = first tail of m)
+};
+// From the tables of make_tables (its cbase, dimp, fbase); false (with err) if d < 4.
+bool make_free_tables(const FactorChoice& fc, int d, int L, const DeviceTables& tb, FreeTables& out,
+                      std::string& err);
 constexpr int kTabStride = 6;               // ints per k in DeviceTables::ktab
 
 }  // namespace hdf

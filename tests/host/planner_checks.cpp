@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "planner.h"
@@ -106,6 +107,60 @@ int main() {
         report(buf, res, 1e-12 * n);
         std::snprintf(buf, sizeof(buf), "sym_eig %d orthonormality", n);
         report(buf, orth, 1e-12 * n);
+    }
+    // Matrix-free layout: for every kept U column (k, s, h) the chain of h splits into the level-0
+    // offset of P_0(m, k - m) (a0off of the A0F column (m, k, s)) and the tail of degree m (the
+    // zchain entry (m, j)), and wcol + j is the column's padded position; the tails are exactly
+    // the chains of H_k with mu_1 = m, in the same order, for every k >= m.
+    for (int d = 4; d <= 6; ++d) {
+        const int L = 9;
+        FactorChoice fc;
+        fc.sk.assign(L + 1, 0);
+        for (int k = 0; k <= L; ++k) fc.sk[k] = (k % 4 == 3) ? 0 : 1 + (L - k) % 3;   // gaps and varied ranks
+        fc.m[0] = fc.m[1] = 3;
+        fc.Wk.assign(L + 1, std::vector<double>());
+        for (int k = 0; k <= L; ++k) fc.Wk[k].assign((size_t)3 * fc.sk[k], 0.5);
+        int64_t rank = 0;
+        for (int k = 0; k <= L; ++k) rank += harmonic_count(k, d) * fc.sk[k];
+        fc.S.assign(rank, 1.0);
+        DeviceTables tb;
+        std::string err;
+        FreeTables ft;
+        if (!make_tables(fc, d, L, 4, tb, err) || !make_free_tables(fc, d, L, tb, ft, err)) {
+            report("matrix-free tables built", 1.0, 0.0);
+            continue;
+        }
+        const int levels = d - 2, stride = chain_stride(d);
+        double bad = 0.0;
+        int64_t cols = 0;
+        for (int k = 0; k <= tb.L_used; ++k) {
+            if (fc.sk[k] == 0) continue;
+            const int hk = (int)harmonic_count(k, d);
+            // chains of H_k in order; walk the groups of equal mu_1
+            int h = 0;
+            for (int m = 0; m <= k; ++m) {
+                for (int j = 0; j < ft.zcnt[m]; ++j, ++h) {
+                    const int16_t* full = &tb.chains[(size_t)(tb.hbase[k] + h) * stride];
+                    const int16_t* tail = &ft.zchain[(size_t)(ft.zoff[m] + j) * stride];
+                    for (int l = 1; l < levels; ++l) bad += (full[l] != tail[l - 1]);
+                    bad += (full[levels] != tail[levels - 1]);
+                    for (int s = 0; s < fc.sk[k]; ++s) {
+                        int q = -1;
+                        for (int t = ft.aoff[m]; t < ft.aoff[m] + ft.acnt[m]; ++t)
+                            if (ft.afcol[t] == tb.fbase[k] + s) q = t;
+                        if (q < 0) { bad += 1; continue; }
+                        bad += (ft.a0off[q] != full[0]);
+                        const int64_t col = tb.cbase[k] + (int64_t)s * tb.ktab[kTabStride * k + 5] + h;
+                        bad += (ft.wcol[q] + j != col);
+                        ++cols;
+                    }
+                }
+            }
+            bad += (h != hk);
+        }
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "matrix-free layout d=%d (%lld columns)", d, (long long)cols);
+        report(buf, bad + (cols != rank ? 1.0 : 0.0), 0.0);
     }
     return fails ? 1 : 0;
 }
