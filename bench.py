@@ -39,8 +39,8 @@ Other workloads (--workload):
   normal5_cauchy  the large-rank row: n = 4,000,000 points in d = 5 (rotated standard normal,
                   standardised), Cauchy l = 2, tol 1e-4, FP32, 16 columns; U would take about
                   1.4 TB, so hdf_build keeps the matrix-free rows (the harmonic tails Z and the
-                  first level factor times the radial factor) and K~V runs over them; step =
-                  hdf_build + K~V; the dominant kernels are FP32-ALU-bound GEMMs.
+                  first level factor times the radial factor) and K~V runs over them on the
+                  tensor cores; step = hdf_build + K~V.
   cross3_gauss    the non-symmetric row: X = 1,000,000 mixture points, Y = 250,000 points of a
                   wider Gaussian cloud, Gaussian l = 1.5, tol 1e-6, FP32; step = hdf_build_cross
                   + K~ V (V: 16 columns over Y) + K~^T W (W: 16 columns over X); value = points
@@ -699,16 +699,20 @@ def bench_mfree(args):
     approx = Yc.t()[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
     rel_err = float(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
     f.free()
-    # roofline: the two products are FP32 GEMMs on the CUDA cores over the stored Z rows; the
-    # algorithmic work is that of K~V on the factor, 2 n r c flops per product
+    # roofline: the two products are tensor-core GEMMs over the stored Z rows (tcgen05, 3xTF32:
+    # three TF32 products per multiply-add for FP32 accuracy); the algorithmic work is that of
+    # K~V on the factor, 2 n r c flops per product, i.e. 3 x 2 n r c TF32 flops, against the TF32
+    # rate (measured BF16 cuBLAS burst x 1.1 / 2.25, the nominal TF32 / BF16 ratio)
     r = info.rank
     flops = 2.0 * n * r * c
-    peak_alu = NSM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kern = {"k_mf_utv": float(mv[0]), "k_mf_uw": float(mv[2])}
+    pk, pk_src = load_peaks()
+    tf32_peak = float(pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])) * 1.1 / 2.25
+    kern = {"k_tc_mf_utv": float(mv[0]), "k_tc_mf_uw": float(mv[2])}
     dom = max(kern, key=kern.get)
-    roof = {"kernel": dom, "bound": "alu", "achieved": flops / (kern[dom] / 1e3) / 1e12, "peak": peak_alu,
-            "unit": "TFLOP/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
-            "traffic": None, "algorithmic_flops": flops, "ms_per_launch": kern[dom]}
+    roof = {"kernel": dom, "bound": "tensor", "achieved": 3 * flops / (kern[dom] / 1e3) / 1e12, "peak": tf32_peak,
+            "unit": "TFLOP/s", "peak_source": f"{pk_src} bf16 cuBLAS burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
+            "traffic": None, "algorithmic_flops": 3 * flops, "useful_fp32_tflops": flops / (kern[dom] / 1e3) / 1e12,
+            "ms_per_launch": kern[dom]}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # end to end from pinned host buffers: H2D x and V; build; K~V; D2H of Y
     xh = torch.from_numpy(x_np).pin_memory()
@@ -758,8 +762,9 @@ def bench_mfree(args):
                 "detail": {"rel_err_sampled_vs_exact": rel_err, "err_bound": info.err_bound,
                            "cheb_tail": info.cheb_tail, "build_ms": float(info.t_ms[7]),
                            "build_phase_ms": [float(info.t_ms[q]) for q in range(8)],
-                           "kv_ms": float(mv.sum()), "kernel_ms": {"k_mf_utv": float(mv[0]), "k_reduce_scale": float(mv[1]),
-                                                                    "k_mf_uw": float(mv[2])},
+                           "kv_ms": float(mv.sum()), "kernel_ms": {"k_tc_mf_utv": float(mv[0]),
+                                                                    "k_reduce_scale": float(mv[1]),
+                                                                    "k_tc_mf_uw": float(mv[2])},
                            "s_k": [int(info.s_k[k]) for k in range(info.L + 1)]}}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -682,9 +682,8 @@ static hdf_status matvec_free(const hdf_factor* f, const T* V, int64_t ldv, int 
     if (B || alpha != (T)1 || beta != (T)0) return fail(HDF_EINVAL, "matrix-free factor: plain products only");
     const int64_t n = f->info.n, r = f->info.ldu;
     const int cmax = std::min(ncols, kMaxGroup);
-    const int64_t nch = (n + FreeFactor::kChunk - 1) / FreeFactor::kChunk;
+    (void)n;
     DevBuf part, W;
-    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * cmax * r, st));
     HDF_CUDA(W.alloc_on(sizeof(T) * (size_t)r * cmax, st));
     hdf_factor* fm = const_cast<hdf_factor*>(f);
     const bool rec = fm->mv_ev[0] != nullptr;
@@ -692,7 +691,7 @@ static hdf_status matvec_free(const hdf_factor* f, const T* V, int64_t ldv, int 
         const int cg = std::min(kMaxGroup, ncols - j0);
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[0], st));
         int np = 0;
-        if (hdf_status e = mf_utv<T>(f, V + j0 * ldv, ldv, cg, part.as<double>(), &np, st); e != HDF_OK) return e;
+        if (hdf_status e = mf_utv<T>(f, V + j0 * ldv, ldv, cg, part, &np, st); e != HDF_OK) return e;
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
         HDF_COUNT_LAUNCH();
         dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), np, r, cg, S_scale,
@@ -763,11 +762,9 @@ hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const
     const int64_t r = f->info.ldu;      // padded width (rows of W)
     if (c < 1 || c > kMaxGroup) return fail(HDF_EINVAL, "utv_reduce: 1 <= c <= 64");
     if (f->mf.on) {
-        const int64_t nch = (f->info.n + FreeFactor::kChunk - 1) / FreeFactor::kChunk;
         DevBuf part;
-        HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * c * r, st));
         int np = 0;
-        if (hdf_status e = mf_utv<T>(f, V, ldv, c, part.as<double>(), &np, st); e != HDF_OK) return e;
+        if (hdf_status e = mf_utv<T>(f, V, ldv, c, part, &np, st); e != HDF_OK) return e;
         HDF_COUNT_LAUNCH();
         dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(part.as<double>(), np, r, c, S_scale,
                                                                               W, Wd);

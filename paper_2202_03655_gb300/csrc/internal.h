@@ -10,6 +10,8 @@
 
 #include "../../include/hdf.h"
 
+struct DevBuf;
+
 namespace hdf {
 
 // Sets the thread-local message returned by hdf_last_error and returns s.
@@ -26,15 +28,34 @@ void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk);
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
                   double* part, float* work, int* err, cudaStream_t st);
 hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G, int* err, cudaStream_t st);
+// Matrix-free products on the tensor cores (tc_gemm.cu) over the device views of a matrix-free
+// factor: the U^T V tiles (m, j0, n0) and the U W phases (m, n0, K steps, B row) for c columns
+// (tc_mf_lists), partial sums of U^T V into part (chunks x c x r, zeroed by the call), and Y = U W.
+struct MfTcView {
+    const float* Z; int ldZ;
+    const float* A0F; int ldA;
+    int64_t n, r;
+    const int* zoff; const int* zcnt; const int* aoff; const int* acnt; const int64_t* wcol;
+};
+int tc_mf_cp(int c);
+void tc_mf_lists(const std::vector<int>& zcnt, const std::vector<int>& acnt, int c, std::vector<int4>& tiles,
+                 std::vector<int4>& phases, int* kpad);
+// Points per chunk and chunks of the tensor-core U^T V partial sums (part holds nchunk x c x r).
+void tc_mf_chunks(int64_t n, int ntiles, int64_t* chunk, int* nchunk);
+hdf_status tc_mf_utv(const MfTcView& v, const int4* tiles, int ntiles, const float* V, int64_t ldv, int c, double* part,
+                     int* nchunk, int* err, cudaStream_t st);
+hdf_status tc_mf_uw(const MfTcView& v, const int4* phases, int nphase, int kpad, const float* W, int c, float* Y,
+                    int64_t ldy, int* err, cudaStream_t st);
 // Work-wait limit (clock cycles) of the tensor-core kernels on the current device.
 hdf_status set_wait_limit(long long cycles, long long* previous);
 // HDF_ETIMEOUT (and the flag cleared) if a kernel on f gave up a bounded wait since the last
 // check; synchronises the device.
 hdf_status take_device_error(const hdf_factor* f);
-// Matrix-free products (mfree.cu): partial sums of U^T V (c <= 64) into part (ceil(n / 8192)
-// chunks of c x ldu, FP64; *nchunk gets the count) and Y = U W (W: ldu x c row-major, c <= 64).
+// Matrix-free products (mfree.cu): partial sums of U^T V (c <= 64) into part (allocated by the
+// call from the stream-ordered pool: *nchunk chunks of c x ldu, FP64) and Y = U W (W: ldu x c
+// row-major, c <= 64).  FP32 factors run on the tensor cores unless HDF_FLAG_CUDA_CORES.
 template <typename T>
-hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* part, int* nchunk, cudaStream_t st);
+hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, DevBuf& part, int* nchunk, cudaStream_t st);
 template <typename T>
 hdf_status mf_uw(const hdf_factor* f, const T* W, int c, T* Y, int64_t ldy, cudaStream_t st);
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,
@@ -146,6 +167,11 @@ struct FreeFactor {
     DevBuf dzoff, dzcnt, daoff, dacnt, dwcol;
     std::vector<int> zoff, zcnt, aoff, acnt;
     std::unique_ptr<Items> items[128];              // FP32 c = 1..64, then FP64
+    struct TcLists {                                // tensor-core tiles and phases for one column count
+        DevBuf tiles, phases;
+        int ntiles = 0, nphase = 0, kpad = 0;
+    };
+    std::unique_ptr<TcLists> tc[65];
     // true if a U of ubytes bytes may be stored on the current device (at most 80% of its memory)
     static bool fits(int64_t ubytes);
 };

@@ -429,12 +429,63 @@ template hdf_status mf_write<double>(hdf_factor*, const double*, int64_t, int, c
                                      const FactorChoice&, const DeviceTables&, const void*, int64_t, const void*,
                                      const void*, cudaStream_t);
 
-// Partial sums of U^T V (c <= 64 columns) into part[(chunk * c + cc) * r + a], r = ldu; returns
-// the number of chunks.  part must hold ceil(n / kMfChunk) * c * r doubles.
+namespace {
+// Device views and cached tensor-core lists of a matrix-free factor for c columns.
+MfTcView tc_view(const hdf_factor* f) {
+    const FreeFactor& mf = f->mf;
+    return MfTcView{mf.Z.as<float>(), mf.ldZ, mf.A0F.as<float>(), mf.ldA, f->info.n, f->info.ldu,
+                    mf.dzoff.as<int>(), mf.dzcnt.as<int>(), mf.daoff.as<int>(), mf.dacnt.as<int>(),
+                    mf.dwcol.as<int64_t>()};
+}
+
+hdf_status tc_lists(const hdf_factor* f, int c, FreeFactor::TcLists** out) {
+    FreeFactor& mf = const_cast<FreeFactor&>(f->mf);
+    auto& slot = mf.tc[c];
+    if (!slot) {
+        std::vector<int4> tiles, phases;
+        int kpad = 0;
+        tc_mf_lists(mf.zcnt, mf.acnt, c, tiles, phases, &kpad);
+        std::unique_ptr<FreeFactor::TcLists> L(new FreeFactor::TcLists());
+        L->ntiles = (int)tiles.size();
+        L->nphase = (int)phases.size();
+        L->kpad = kpad;
+        HDF_CUDA(L->tiles.alloc(sizeof(int4) * std::max<size_t>(1, tiles.size())));
+        HDF_CUDA(L->phases.alloc(sizeof(int4) * std::max<size_t>(1, phases.size())));
+        if (!tiles.empty()) HDF_CUDA(cudaMemcpy(L->tiles.p, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
+        if (!phases.empty())
+            HDF_CUDA(cudaMemcpy(L->phases.p, phases.data(), sizeof(int4) * phases.size(), cudaMemcpyHostToDevice));
+        slot = std::move(L);
+    }
+    *out = slot.get();
+    return HDF_OK;
+}
+
+bool use_tensor_cores(const hdf_factor* f) { return f->prec == HDF_FP32 && f->use_tc; }
+}  // namespace
+
+// Partial sums of U^T V (c <= 64 columns) into part[(chunk * c + cc) * r + a], r = ldu, part
+// allocated here; *nchunk gets the number of chunks.
 template <typename T>
-hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* part, int* nchunk, cudaStream_t st) {
+hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, DevBuf& part, int* nchunk, cudaStream_t st) {
     FreeFactor& mf = const_cast<FreeFactor&>(f->mf);
     const int64_t n = f->info.n, r = f->info.ldu;
+    if constexpr (sizeof(T) == 4) {
+        if (use_tensor_cores(f)) {
+            FreeFactor::TcLists* L = nullptr;
+            if (hdf_status e = tc_lists(f, c, &L); e != HDF_OK) return e;
+            int64_t chunk = 0;
+            int nch = 0;
+            tc_mf_chunks(n, L->ntiles, &chunk, &nch);
+            HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * c * r, st));
+            int got = 0;
+            if (hdf_status e = tc_mf_utv(tc_view(f), L->tiles.as<int4>(), L->ntiles, reinterpret_cast<const float*>(V),
+                                         ldv, c, part.as<double>(), &got, f->dev_err.as<int>(), st);
+                e != HDF_OK)
+                return e;
+            *nchunk = got;
+            return HDF_OK;
+        }
+    }
     auto& slot = mf.items[(sizeof(T) == 4 ? 0 : 64) + c - 1];
     if (!slot) {
         const std::vector<int4> it = utv_items(mf, c, sizeof(T) == 4);
@@ -446,7 +497,8 @@ hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* p
     const int64_t chunk = FreeFactor::kChunk;
     const int nch = (int)((n + chunk - 1) / chunk);
     *nchunk = nch;
-    HDF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nch * c * r, st));
+    HDF_CUDA(part.alloc_on(sizeof(double) * (size_t)nch * c * r, st));
+    HDF_CUDA(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)nch * c * r, st));
     if (slot->count == 0) return HDF_OK;
     dev::MfUtvArgs a{};
     a.Z = mf.Z.p; a.ldZ = mf.ldZ; a.A0F = mf.A0F.p; a.ldA = mf.ldA;
@@ -455,7 +507,7 @@ hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* p
     a.items = slot->buf.as<int4>();
     a.zoff = mf.dzoff.as<int>(); a.zcnt = mf.dzcnt.as<int>(); a.aoff = mf.daoff.as<int>(); a.acnt = mf.dacnt.as<int>();
     a.wcol = mf.dwcol.as<int64_t>();
-    a.part = part; a.r = r;
+    a.part = part.as<double>(); a.r = r;
     const size_t sm = sizeof(T) * (size_t)dev::MfShape<T>::SMEM;
     HDF_CUDA(cudaFuncSetAttribute(dev::k_mf_utv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HDF_COUNT_LAUNCH();
@@ -463,14 +515,22 @@ hdf_status mf_utv(const hdf_factor* f, const T* V, int64_t ldv, int c, double* p
     HDF_CUDA(cudaGetLastError());
     return HDF_OK;
 }
-template hdf_status mf_utv<float>(const hdf_factor*, const float*, int64_t, int, double*, int*, cudaStream_t);
-template hdf_status mf_utv<double>(const hdf_factor*, const double*, int64_t, int, double*, int*, cudaStream_t);
+template hdf_status mf_utv<float>(const hdf_factor*, const float*, int64_t, int, DevBuf&, int*, cudaStream_t);
+template hdf_status mf_utv<double>(const hdf_factor*, const double*, int64_t, int, DevBuf&, int*, cudaStream_t);
 
 // Y = U W for W (ldu x c row-major, bulk type), c <= 64.
 template <typename T>
 hdf_status mf_uw(const hdf_factor* f, const T* W, int c, T* Y, int64_t ldy, cudaStream_t st) {
     const FreeFactor& mf = f->mf;
     const int64_t n = f->info.n;
+    if constexpr (sizeof(T) == 4) {
+        if (use_tensor_cores(f)) {
+            FreeFactor::TcLists* L = nullptr;
+            if (hdf_status e = tc_lists(f, c, &L); e != HDF_OK) return e;
+            return tc_mf_uw(tc_view(f), L->phases.as<int4>(), L->nphase, L->kpad, reinterpret_cast<const float*>(W), c,
+                            reinterpret_cast<float*>(Y), ldy, f->dev_err.as<int>(), st);
+        }
+    }
     dev::MfUwArgs a{};
     a.Z = mf.Z.p; a.ldZ = mf.ldZ; a.A0F = mf.A0F.p; a.ldA = mf.ldA;
     a.W = W; a.c = c; a.cp = pow2_at_least(c, 4);

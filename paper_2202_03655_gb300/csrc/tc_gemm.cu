@@ -245,16 +245,18 @@ struct Smem {
 };
 
 // Barrier set-up and TMEM allocation (warp 1 owns the TMEM); returns the TMEM base address.
+// ncons: item consumers (warps and threads that release an item slot); bcount: arrivals that
+// complete a B stage (1 for a TMA producer, the warp count for B-generator warps).
 template <int BN>
-__device__ __forceinline__ uint32_t cta_setup(Smem<BN>& sm, int warp) {
+__device__ __forceinline__ uint32_t cta_setup(Smem<BN>& sm, int warp, int ncons = NCONS, int bcount = 1) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < S_U; ++s) { mbar_init(&sm.ufull[s], 1); mbar_init(&sm.uempty[s], 4); }
-        for (int s = 0; s < Smem<BN>::SB; ++s) mbar_init(&sm.bfull[s], 1);
+        for (int s = 0; s < Smem<BN>::SB; ++s) mbar_init(&sm.bfull[s], bcount);
         for (int b = 0; b < NA; ++b) mbar_init(&sm.afull[b], 4);
         for (int j = 0; j < NDONE; ++j) mbar_init(&sm.done[j], 1);
         for (int b = 0; b < NACC; ++b) mbar_init(&sm.acce[b], 4);
         mbar_init(sm.drain, 1);
-        for (int j = 0; j < IR; ++j) { mbar_init(&sm.itfull[j], 1); mbar_init(&sm.itempty[j], NCONS); }
+        for (int j = 0; j < IR; ++j) { mbar_init(&sm.itfull[j], 1); mbar_init(&sm.itempty[j], ncons); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -388,6 +390,37 @@ __device__ __forceinline__ bool promote(Smem<BN>& sm, uint32_t tmem, uint32_t it
     return true;
 }
 
+// The same promotion 32 accumulator columns at a time (half the registers of promote), for
+// kernels whose promotion warps keep more state beside the sums.
+template <int BN>
+__device__ __forceinline__ bool promote_lean(Smem<BN>& sm, uint32_t tmem, uint32_t it, int q, int lane, float* acc) {
+    const uint32_t buf = it % NACC;
+    if (!wait_done<BN>(sm, it)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + buf * 2 * BN;
+    if constexpr (BN == 16) {
+        uint32_t v[32];
+        tmem_ld32(ta, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] += __uint_as_float(v[j]) + __uint_as_float(v[16 + j]);
+    } else {
+#pragma unroll
+        for (int j0 = 0; j0 < BN; j0 += 32) {
+            uint32_t a[32], b[32];
+            tmem_ld32(ta + j0, a);
+            tmem_ld32(ta + BN + j0, b);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j0 + j] += __uint_as_float(a[j]) + __uint_as_float(b[j]);
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.acce[buf]);
+    return true;
+}
+
 // MMA warp exit: every MMA it issued is complete before the CTA frees its TMEM.
 template <int BN>
 __device__ __forceinline__ void mma_drain(Smem<BN>& sm, bool ok, int* err) {
@@ -405,10 +438,11 @@ __device__ __forceinline__ bool producer_drain(uint64_t* full, int depth, uint32
     return ok;
 }
 
-// B producer, one step: stacked hi / lo tiles of K rows [k0, k0 + 64) (two 32-K halves).
+// B producer, one step: stacked hi / lo tiles of K rows [k0, k0 + 64) (two 32-K halves) and
+// operand rows [y0, y0 + BN).
 template <int BN>
 __device__ __forceinline__ bool load_b(Smem<BN>& sm, uint32_t it, const CUtensorMap* mhi, const CUtensorMap* mlo,
-                                       int k0) {
+                                       int k0, int y0 = 0) {
     constexpr int SB = Smem<BN>::SB;
     const uint32_t sb = it % SB;
     if (it >= (uint32_t)SB && !wait_done<BN>(sm, it - SB)) return false;
@@ -416,8 +450,8 @@ __device__ __forceinline__ bool load_b(Smem<BN>& sm, uint32_t it, const CUtensor
     unsigned char* dst = sm.B + sb * Smem<BN>::BBYTES;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        tma_load_2d(dst + h * Smem<BN>::BHALF, mhi, k0 + KH * h, 0, &sm.bfull[sb]);
-        tma_load_2d(dst + h * Smem<BN>::BHALF + BN * KH * 4, mlo, k0 + KH * h, 0, &sm.bfull[sb]);
+        tma_load_2d(dst + h * Smem<BN>::BHALF, mhi, k0 + KH * h, y0, &sm.bfull[sb]);
+        tma_load_2d(dst + h * Smem<BN>::BHALF + BN * KH * 4, mlo, k0 + KH * h, y0, &sm.bfull[sb]);
     }
     return true;
 }
@@ -675,6 +709,337 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     cta_teardown<BN>(tmem, warp);
 }
 
+// ------------------------------------------------ matrix-free products on the tensor cores
+// The products of a matrix-free factor (mfree.cu): the stored Z rows are the A operand, brought
+// by TMA exactly like the U tiles of k_tc_utv / k_tc_uw; only the small second operand changes.
+//   k_tc_mf_utv: W[(k,s,m,j), c] = sum_i Z[i, zoff_m + j] (A0F[i, aoff_m + q] V[i, c]).
+//     M = 128 rows j of the tails of degree m, N = BN columns n = (q, c), K = points.  The B
+//     tiles A0F (.) V are formed in shared memory by four generator warps (10..13), in the
+//     K-major 128-byte-swizzle layout the TMA would write, TF32 hi / lo stacked.
+//   k_tc_mf_uw: Y[i, c] = sum over phases (m, n0) of sum_q A0F[i, aoff_m + q] Q[i, (q, c)],
+//     Q = Z[:, zoff_m + j] W_m[j, (q, c)]: M = 128 points, N = BN columns, K = the tails of m.
+//     The B tiles come by TMA from W gathered per phase (k_prep_mf_w); the promotion warps
+//     contract each phase's accumulator with A0F into y and write Y once per tile.
+constexpr int NGEN = 2;                 // B-generator warps (10, 11)
+constexpr int NTHREADS_MF = 32 * (10 + NGEN);   // the roles of k_tc_utv, the generators in place of the B producer
+constexpr int NCONS_MF = NGEN + 9;      // item consumers: generators, MMA, 4 converters, 4 promotion
+
+struct MfUtvTcArgs {
+    int64_t n, chunk;                   // points, points per K chunk (a multiple of 64)
+    int nchunk, ntiles;
+    const int4* tiles;                  // (m, j0, n0, -): rows j0.. of the tails of m, columns n0..
+    const float* A0F; int ldA;
+    const float* V; int64_t ldv; int c;
+    const int* zoff; const int* zcnt; const int* aoff; const int* acnt; const int64_t* wcol;
+    double* part; int64_t r;            // part[(chunk * c + cc) * r + a]
+    int* err; int* next;
+};
+
+// CP: c padded to 16, 32 or 64 (a divisor of BN); column n of the product is (q, cc) =
+// (n / CP, n mod CP), zero for cc >= c.
+template <int BN, int CP>
+__global__ void __launch_bounds__(NTHREADS_MF, 1)
+    k_tc_mf_utv(const __grid_constant__ CUtensorMap mZ, MfUtvTcArgs p) {
+    using SM = Smem<BN>;
+    static_assert(BN % CP == 0, "column groups must not straddle a tile");
+    constexpr int SB = SM::SB;
+    extern __shared__ unsigned char raw_[];
+    SM sm(raw_);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tmem = cta_setup<BN>(sm, warp, NCONS_MF, NGEN);
+    const int64_t nitems = (int64_t)p.ntiles * p.nchunk;
+    bool ok = true;
+    auto ksteps = [&](int64_t item) -> int {
+        const int64_t ch = item / p.ntiles;
+        const int64_t i0 = ch * p.chunk, i1 = min(p.n, i0 + p.chunk);
+        return (int)((i1 - i0 + BK - 1) / BK);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0, k = 0;
+            int64_t item = blockIdx.x;
+            while (ok) {
+                if (!publish_item<BN>(sm, k++, item)) { ok = false; break; }
+                if (item >= nitems) break;
+                const int4 tl = p.tiles[item % p.ntiles];
+                const int64_t i0 = (item / p.ntiles) * p.chunk;
+                const int zx = p.zoff[tl.x] + tl.y;
+                const int nk = ksteps(item);
+                const int claim_at = nk > 8 ? nk - 8 : 0;
+                int64_t nxt = nitems;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    if (kt == claim_at) nxt = (int64_t)gridDim.x + atomicAdd(p.next, 1);
+                    const uint32_t s = it % S_U;
+                    if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
+                    tma_load_2d(sm.U + s * SM::UBYTES, &mZ, zx, (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
+                }
+                item = nxt;
+            }
+            if (!producer_drain(sm.ufull, S_U, it)) ok = false;
+            if (!ok) atomicExch(p.err, 1);
+        }
+    } else if (warp >= 10) {
+        // B generators: thread t (t < 64) = point kk of the step; per step it loads the point's
+        // BN / CP values of A0F and its CP values of V once and forms the BN products
+        static_assert(NGEN * 32 == BK, "one generator thread per point of a step");
+        const int kk = (warp - 10) * 32 + lane;
+        const int h = kk >> 5, jc = (kk & 31) >> 2, e = kk & 3;
+        constexpr int NQ = BN / CP;
+        uint32_t it = 0;
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
+            const int4 tl = p.tiles[item % p.ntiles];
+            const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
+            const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const uint32_t sb = it % SB;
+                const int64_t i = i0 + (int64_t)kt * BK + kk;
+                const bool pv = i < i1;
+                float av[NQ], vv[CP];
+#pragma unroll
+                for (int g = 0; g < NQ; ++g) av[g] = (pv && q0 + g < nq) ? __ldg(p.A0F + i * p.ldA + ao + q0 + g) : 0.f;
+#pragma unroll
+                for (int cc = 0; cc < CP; ++cc) vv[cc] = (pv && cc < p.c) ? __ldg(p.V + i + (int64_t)cc * p.ldv) : 0.f;
+                bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
+                free_ = __all_sync(0xffffffffu, free_);
+                if (!free_) { ok = false; break; }
+                unsigned char* col = sm.B + sb * SM::BBYTES + h * SM::BHALF + e * 4;
+#pragma unroll
+                for (int g = 0; g < NQ; ++g)
+#pragma unroll
+                    for (int cc = 0; cc < CP; ++cc) {
+                        const int nrow = g * CP + cc;
+                        uint32_t hi, lo;
+                        split_tf32(av[g] * vv[cc], hi, lo);
+                        const uint32_t off = (uint32_t)nrow * 128u + ((uint32_t)(jc ^ (nrow & 7)) << 4);
+                        *reinterpret_cast<uint32_t*>(col + off) = hi;
+                        *reinterpret_cast<uint32_t*>(col + BN * 128 + off) = lo;
+                    }
+                // the tensor core reads the stage through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.bfull[sb]);
+            }
+            if (!ok) break;
+        }
+        if (!ok && lane == 0) atomicExch(p.err, 1);
+    } else if (warp == 1) {
+        uint32_t it = 0;
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = mma_step<BN>(sm, tmem, it, lane);
+        }
+        mma_drain(sm, ok, p.err);
+    } else if (warp < 6) {
+        // thread = row m of A (column j0 + m of the Z block); the stored tile is [64 points][128 columns]
+        const int q = warp & 3, mrow = 32 * q + lane;
+        uint32_t it = 0;
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                if (!convert_wait<BN>(sm, it)) { ok = false; break; }
+                const float* R = reinterpret_cast<const float*>(sm.U + (it % S_U) * SM::UBYTES) + mrow;
+                float x[64];
+#pragma unroll
+                for (int k2 = 0; k2 < BK; ++k2) x[k2] = R[k2 * BM];
+                convert_release<BN>(sm, it, lane);
+                convert_publish<BN>(sm, tmem, it, q, lane, x);
+            }
+        }
+        if (!ok && lane == 0) atomicExch(p.err, 1);
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        for (uint32_t k = 0; ok; ++k) {
+            const int64_t item = take_item<BN>(sm, k, true);
+            if (item < 0) { ok = false; break; }
+            if (item >= nitems) break;
+            float acc[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+            const int nk = ksteps(item);
+            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = promote_lean<BN>(sm, tmem, it, q, lane, acc);
+            if (!ok) break;
+            const int4 tl = p.tiles[item % p.ntiles];
+            const int m = tl.x, ao = p.aoff[m], nq = p.acnt[m], q0 = tl.z / CP;
+            const int64_t ch = item / p.ntiles;
+            const int jr = tl.y + 32 * q + lane;             // row of the tails of m
+            if (jr < p.zcnt[m]) {
+#pragma unroll
+                for (int g = 0; g < BN / CP; ++g) {
+                    if (q0 + g >= nq) continue;
+                    const int64_t a = p.wcol[ao + q0 + g] + jr;
+#pragma unroll
+                    for (int cc = 0; cc < CP; ++cc)
+                        if (cc < p.c) p.part[(ch * p.c + cc) * p.r + a] = (double)acc[g * CP + cc];
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(p.err, 1);
+    }
+    cta_teardown<BN>(tmem, warp);
+}
+
+struct MfPhase {
+    int m, n0, nk, y0;                  // tail degree, first column (q, c), K steps, row of its B tiles
+};
+
+struct MfUwTcArgs {
+    int64_t n;                          // points
+    int nphase;
+    const MfPhase* phases;
+    const int* zoff; const int* aoff; const int* acnt;
+    const float* A0F; int ldA;
+    int c;
+    float* Y; int64_t ldy;
+    int* err;
+};
+
+// Y for 128-point tiles (persistent over tiles), phases in order; CP = c padded to 16, 32 or
+// 64 (a divisor of BN), so the column (q, cc) of accumulator entry j is q = (n0 + j) / CP,
+// cc = j mod CP.
+template <int BN, int CP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_mf_uw(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mW,
+               const __grid_constant__ CUtensorMap mWlo, MfUwTcArgs p) {
+    using SM = Smem<BN>;
+    static_assert(BN % CP == 0, "column groups must not straddle a tile");
+    extern __shared__ unsigned char raw[];
+    SM sm(raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tmem = cta_setup<BN>(sm, warp);
+    const int64_t ntiles = (p.n + BM - 1) / BM;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int ph = 0; ph < p.nphase && ok; ++ph) {
+                    const MfPhase P = p.phases[ph];
+                    const int z0 = p.zoff[P.m];
+                    for (int kt = 0; kt < P.nk; ++kt, ++it) {
+                        const uint32_t s = it % S_U;
+                        if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
+                        mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
+                        unsigned char* dst = sm.U + s * SM::UBYTES;
+                        tma_load_2d(dst, &mZ, z0 + kt * BK, (int)(tile * BM), &sm.ufull[s]);
+                        tma_load_2d(dst + SM::UBYTES / 2, &mZ, z0 + kt * BK + KH, (int)(tile * BM), &sm.ufull[s]);
+                    }
+                }
+            }
+            if (!producer_drain(sm.ufull, S_U, it)) ok = false;
+            if (!ok) atomicExch(p.err, 1);
+        }
+    } else if (warp == 10) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+                for (int ph = 0; ph < p.nphase && ok; ++ph) {
+                    const MfPhase P = p.phases[ph];
+                    for (int kt = 0; kt < P.nk && ok; ++kt, ++it) ok = load_b<BN>(sm, it, &mW, &mWlo, kt * BK, P.y0);
+                }
+            if (!producer_drain(sm.bfull, SM::SB, it)) ok = false;
+            if (!ok) atomicExch(p.err, 1);
+        }
+    } else if (warp == 1) {
+        uint32_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+            for (int ph = 0; ph < p.nphase && ok; ++ph) {
+                const int nk = p.phases[ph].nk;
+                for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = mma_step<BN>(sm, tmem, it, lane);
+            }
+        mma_drain(sm, ok, p.err);
+    } else if (warp < 6) {
+        const int q = warp & 3, m = 32 * q + lane;
+        uint32_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int ph = 0; ph < p.nphase && ok; ++ph) {
+                const int nk = p.phases[ph].nk;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    if (!convert_wait<BN>(sm, it)) { ok = false; break; }
+                    const unsigned char* R = sm.U + (it % S_U) * SM::UBYTES + m * 128;
+                    float x[64];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 v = *reinterpret_cast<const float4*>(R + h * (SM::UBYTES / 2) + ((j ^ (m & 7)) << 4));
+                            x[32 * h + 4 * j + 0] = v.x; x[32 * h + 4 * j + 1] = v.y;
+                            x[32 * h + 4 * j + 2] = v.z; x[32 * h + 4 * j + 3] = v.w;
+                        }
+                    convert_release<BN>(sm, it, lane);
+                    convert_publish<BN>(sm, tmem, it, q, lane, x);
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(p.err, 1);
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t row = tile * BM + 32 * q + lane;
+            const bool rv = row < p.n;
+            float y[CP];
+#pragma unroll
+            for (int j = 0; j < CP; ++j) y[j] = 0.f;
+            for (int ph = 0; ph < p.nphase && ok; ++ph) {
+                const MfPhase P = p.phases[ph];
+                float acc[BN];
+#pragma unroll
+                for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+                for (int kt = 0; kt < P.nk && ok; ++kt, ++it) ok = promote_lean<BN>(sm, tmem, it, q, lane, acc);
+                if (!ok) break;
+                const int ao = p.aoff[P.m], nq = p.acnt[P.m], q0 = P.n0 / CP;
+#pragma unroll
+                for (int g = 0; g < BN / CP; ++g) {
+                    const float f = (rv && q0 + g < nq) ? __ldg(p.A0F + row * p.ldA + ao + q0 + g) : 0.f;
+#pragma unroll
+                    for (int j = 0; j < CP; ++j) y[j] += f * acc[g * CP + j];
+                }
+            }
+            if (!ok) break;
+            if (rv) {
+#pragma unroll
+                for (int j = 0; j < CP; ++j)
+                    if (j < p.c) p.Y[row + (int64_t)j * p.ldy] = y[j];
+            }
+        }
+        if (!ok && lane == 0) atomicExch(p.err, 1);
+    }
+    cta_teardown<BN>(tmem, warp);
+}
+
+// B operand of k_tc_mf_uw: for phase p (rows y0 .. y0 + BN of hi / lo) and K index kk (a tail j),
+// hi + lo = W[(wcol[aoff_m + q] + kk) c + cc] with (q, cc) = ((n0 + row) / CP, (n0 + row) mod CP),
+// zero where q >= acnt_m, cc >= c or kk >= zcnt_m.  Row-major [nphase BN][kpad].
+__global__ void k_prep_mf_w(const float* __restrict__ W, int c, int cp, const MfPhase* __restrict__ phases, int nphase,
+                            int bn, int64_t kpad, const int* __restrict__ zcnt, const int* __restrict__ aoff,
+                            const int* __restrict__ acnt, const int64_t* __restrict__ wcol, float* __restrict__ hi,
+                            float* __restrict__ lo) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nphase * bn * kpad) return;
+    const int64_t rowg = idx / kpad, kk = idx % kpad;
+    const MfPhase P = phases[rowg / bn];
+    const int nidx = P.n0 + (int)(rowg % bn), q = nidx / cp, cc = nidx % cp;
+    float v = 0.f;
+    if (q < acnt[P.m] && cc < c && kk < zcnt[P.m]) v = W[(wcol[aoff[P.m] + q] + kk) * c + cc];
+    const float h = tf32_hi(v);
+    hi[idx] = h;
+    lo[idx] = v - h;
+}
+
 // Wt_hi[j * kpad + a] + Wt_lo[j * kpad + a] = W[a * c + j] (TF32 split, zero padding to kpad x bn).
 __global__ void k_prep_wt(const float* __restrict__ W, int64_t r, int c, int bn, int64_t kpad, float* __restrict__ hi,
                           float* __restrict__ lo) {
@@ -905,6 +1270,108 @@ hdf_status set_wait_limit(long long cycles, long long* previous) {
     HDF_CUDA(cudaMemcpyToSymbol(tc::d_wait_cycles, &v, sizeof(v)));
     if (previous) *previous = prev;
     return HDF_OK;
+}
+
+// ---------------------------------------------------------- matrix-free products (host)
+int tc_mf_cp(int c) { return c <= 16 ? 16 : c <= 32 ? 32 : 64; }
+
+void tc_mf_lists(const std::vector<int>& zcnt, const std::vector<int>& acnt, int c, std::vector<int4>& tiles,
+                 std::vector<int4>& phases, int* kpad) {
+    tiles.clear();
+    phases.clear();
+    const int cp = tc_mf_cp(c);
+    int kmax = tc::BK;
+    for (size_t m = 0; m < zcnt.size(); ++m) {
+        const int J = zcnt[m], Np = acnt[m] * cp;
+        if (J == 0 || acnt[m] == 0) continue;
+        for (int j0 = 0; j0 < J; j0 += tc::BM)
+            for (int n0 = 0; n0 < Np; n0 += 64) tiles.push_back(make_int4((int)m, j0, n0, 0));
+        const int nk = (J + tc::BK - 1) / tc::BK;
+        kmax = std::max(kmax, nk * tc::BK);
+        for (int n0 = 0; n0 < Np; n0 += 64)
+            phases.push_back(make_int4((int)m, n0, nk, (int)phases.size() * 64));
+    }
+    *kpad = kmax;
+}
+
+void tc_mf_chunks(int64_t n, int ntiles, int64_t* chunk, int* nchunk) {
+    // chunks of at most 8192 points (short FP32 sums), enough items to fill the GPU a few times
+    const int64_t want = (4 * 152 + std::max(ntiles, 1) - 1) / std::max(ntiles, 1);
+    const int64_t by_len = (n + 8191) / 8192;
+    const int64_t req = std::max<int64_t>(1, std::max(want, by_len));
+    const int64_t ch = std::max<int64_t>(tc::BK, (((n + req - 1) / req + tc::BK - 1) / tc::BK) * tc::BK);
+    *chunk = ch;
+    *nchunk = (int)((n + ch - 1) / ch);
+}
+
+hdf_status tc_mf_utv(const MfTcView& v, const int4* tiles, int ntiles, const float* V, int64_t ldv, int c, double* part,
+                     int* nchunk, int* err, cudaStream_t st) {
+    int64_t chunk = 0;
+    int nch = 0;
+    tc_mf_chunks(v.n, ntiles, &chunk, &nch);
+    *nchunk = nch;
+    HDF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nch * c * v.r, st));
+    if (ntiles == 0) return HDF_OK;
+    CUtensorMap mZ;
+    if (!tc::make_map(&mZ, v.Z, (uint64_t)v.ldZ, (uint64_t)v.n, (uint64_t)v.ldZ * 4, tc::BM, tc::BK, false))
+        return fail(HDF_ECUDA, "matrix-free product: cannot encode a tensor map");
+    DevBuf next;
+    HDF_CUDA(next.alloc_on(sizeof(int), st));
+    HDF_CUDA(cudaMemsetAsync(next.p, 0, sizeof(int), st));
+    tc::MfUtvTcArgs a{v.n, chunk, nch, ntiles, tiles, v.A0F, v.ldA, V, ldv, c,
+                      v.zoff, v.zcnt, v.aoff, v.acnt, v.wcol, part, v.r, err, next.as<int>()};
+    const size_t sm = tc::Smem<64>::bytes();
+    const int64_t nitems = (int64_t)ntiles * nch;
+    const int grid = (int)std::min<int64_t>(nitems, tc::num_sms());
+    auto kern = c <= 16 ? tc::k_tc_mf_utv<64, 16> : c <= 32 ? tc::k_tc_mf_utv<64, 32> : tc::k_tc_mf_utv<64, 64>;
+    HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HDF_COUNT_LAUNCH();
+    kern<<<grid, tc::NTHREADS_MF, sm, st>>>(mZ, a);
+    HDF_CUDA(cudaGetLastError());
+    return HDF_OK;
+}
+
+template <int CP>
+static hdf_status mf_uw_cp(const MfTcView& v, const tc::MfPhase* phases, int nphase, int kpad, const float* hi,
+                           const float* lo, int c, float* Y, int64_t ldy, int* err, cudaStream_t st) {
+    CUtensorMap mZ, mW, mWl;
+    if (!tc::make_map(&mZ, v.Z, (uint64_t)v.ldZ, (uint64_t)v.n, (uint64_t)v.ldZ * 4, tc::KH, tc::BM, true) ||
+        !tc::make_map(&mW, hi, (uint64_t)kpad, (uint64_t)nphase * 64, (uint64_t)kpad * 4, tc::KH, 64, true) ||
+        !tc::make_map(&mWl, lo, (uint64_t)kpad, (uint64_t)nphase * 64, (uint64_t)kpad * 4, tc::KH, 64, true))
+        return fail(HDF_ECUDA, "matrix-free product: cannot encode a tensor map");
+    tc::MfUwTcArgs a{v.n, nphase, phases, v.zoff, v.aoff, v.acnt, v.A0F, v.ldA, c, Y, ldy, err};
+    const size_t sm = tc::Smem<64>::bytes();
+    HDF_CUDA(cudaFuncSetAttribute(tc::k_tc_mf_uw<64, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int64_t ntiles = (v.n + tc::BM - 1) / tc::BM;
+    const int grid = (int)std::min<int64_t>(ntiles, tc::num_sms());
+    HDF_COUNT_LAUNCH();
+    tc::k_tc_mf_uw<64, CP><<<grid, tc::NTHREADS, sm, st>>>(mZ, mW, mWl, a);
+    HDF_CUDA(cudaGetLastError());
+    return HDF_OK;
+}
+
+hdf_status tc_mf_uw(const MfTcView& v, const int4* phases, int nphase, int kpad, const float* W, int c, float* Y,
+                    int64_t ldy, int* err, cudaStream_t st) {
+    if (nphase == 0) {
+        for (int j = 0; j < c; ++j) HDF_CUDA(cudaMemsetAsync(Y + j * ldy, 0, sizeof(float) * v.n, st));
+        return HDF_OK;
+    }
+    const int cp = tc_mf_cp(c);
+    DevBuf work;
+    const size_t per = (size_t)nphase * 64 * kpad;
+    HDF_CUDA(work.alloc_on(sizeof(float) * 2 * per, st));
+    float* hi = work.as<float>();
+    float* lo = hi + per;
+    const tc::MfPhase* ph = reinterpret_cast<const tc::MfPhase*>(phases);
+    HDF_COUNT_LAUNCH();
+    tc::k_prep_mf_w<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(W, c, cp, ph, nphase, 64, kpad, v.zcnt, v.aoff,
+                                                                   v.acnt, v.wcol, hi, lo);
+    HDF_CUDA(cudaGetLastError());
+    switch (cp) {
+        case 16: return mf_uw_cp<16>(v, ph, nphase, kpad, hi, lo, c, Y, ldy, err, st);
+        case 32: return mf_uw_cp<32>(v, ph, nphase, kpad, hi, lo, c, Y, ldy, err, st);
+        default: return mf_uw_cp<64>(v, ph, nphase, kpad, hi, lo, c, Y, ldy, err, st);
+    }
 }
 
 hdf_status tc_uw(const float* U, int64_t ldU, int64_t n, int64_t r, const float* W, int c, float alpha, const float* B,

@@ -62,14 +62,22 @@ def test_matrix_free_equals_stored(d, kname, ell, tol, n, prec):
 
 @pytest.mark.parametrize("c", [1, 3, 16, 37, 64, 70])
 def test_matrix_free_column_counts(c):
+    """FP32 matrix-free products on the tensor cores (the default) and on the CUDA cores
+    (HDF_FLAG_CUDA_CORES) against the stored factor, column by column."""
     import torch
+    from paper_2202_03655_gb300 import hdf
     x = W.points("normal5_cauchy", n=2003)
     fs, fm = _pair(x, "cauchy", 2.0, 1e-3, "fp32")
+    fc = hdf.build(to_dev(x), "cauchy", 2.0, 1e-3, precision="fp32",
+                   flags=hdf.FLAG_MATRIX_FREE | hdf.FLAG_CUDA_CORES)
     V = to_dev(np.random.default_rng(c).standard_normal((x.shape[0], c)), torch.float32)
     Ys = fs.matvec(V).double().cpu().numpy()
     Ym = fm.matvec(V).double().cpu().numpy()
+    Yc = fc.matvec(V).double().cpu().numpy()
+    assert fm.device_errors() == 0
     for j in range(c):
         assert rel(Ym[:, j], Ys[:, j]) <= 2e-5, j
+        assert rel(Yc[:, j], Ys[:, j]) <= 2e-5, j
 
 
 @pytest.fixture(scope="module")
