@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--p-max", type=int, default=64)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-solve", action="store_true", help="skip the solve measurement of the default workload")
     ap.add_argument("--nsets", type=int, default=None, help="batch512_gauss: number of sets (default 512)")
     ap.add_argument("--cpu-n", type=int, default=12000, help="oracle sample size")
     ap.add_argument("--oracle-once", action="store_true", help=argparse.SUPPRESS)
@@ -1540,6 +1541,38 @@ def main():
     e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8 + n * c * 4,
            "d2h_bytes_per_step": n * c * 4, "ms_per_step": e2e_ms}
 
+    # ---- the solve on the benchmarked factor (outside the timed region): U^T U on the tensor
+    # cores and the LU of the core lambda S^-1 + U^T U on the first call, the device triangular
+    # solves and one refinement step on every call; lambda grows with n as in kernel ridge
+    # regression
+    solve = None
+    if not args.no_solve:
+        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        lam = 1e-4 * n
+        b = Vc[0]
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        xs = f.solve(lam, b, refine_steps=1)
+        torch.cuda.synchronize()
+        first = 1e3 * (time.perf_counter() - s0)
+        s0 = time.perf_counter()
+        xs = f.solve(lam, b, refine_steps=1)
+        torch.cuda.synchronize()
+        again = 1e3 * (time.perf_counter() - s0)
+        res = lam * xs.double() + f.matvec(xs).double() - b.double()
+        ldu_s = f.info.ldu
+        pk, _ = load_peaks()
+        tf32_peak = float(pk.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])) * 1.1 / 2.25
+        gram_ms = float(f.info.t_ms[6])
+        gram_flops = 3 * 2.0 * n * ldu_s * ldu_s
+        solve = {"lambda": lam, "ldu": ldu_s, "first_ms": first, "again_ms": again, "gram_ms": gram_ms,
+                 "lu_ms": float(f.info.lu_ms), "lu_fp64_tflops": (2.0 / 3.0) * ldu_s ** 3 / (f.info.lu_ms / 1e3) / 1e12
+                 if f.info.lu_ms > 0 else None,
+                 "gram_tensor_frac_of_tf32": gram_flops / (gram_ms / 1e3) / 1e12 / tf32_peak if gram_ms > 0 else None,
+                 "residual": float(torch.linalg.norm(res) / torch.linalg.norm(b.double()))}
+        f.free()
+        del xs, res
+
     # ---- FP64 form of the same step
     fp64 = None
     if not args.no_fp64:
@@ -1594,6 +1627,7 @@ def main():
                 "build_points_per_s": n / (np.mean([i.t_ms[7] for i in infos]) / 1e3),
                 "kv_ms": kv_ms, "kv_gbs": kv_bytes / (kv_ms / 1e3) / 1e9,
                 "kernel_ms": {k: v[0] for k, v in kernels.items()},
+                "solve": solve,
                 "fp64": fp64,
             },
         }

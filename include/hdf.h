@@ -119,6 +119,7 @@ typedef struct {
                                rows of its factor V; 0 for a symmetric factor U S U^T */
     int matrix_free;        /* 1 if U is not stored (HDF_FLAG_MATRIX_FREE) */
     int64_t mf_row;         /* matrix-free form: stored values per point (Z and P_0 F rows) */
+    double lu_ms;           /* time of the last factorization of the solve's core (ms; 0 before) */
 } hdf_info;
 
 /* ---------------------------------------------------------------- factorization ---- */
@@ -186,8 +187,13 @@ hdf_status hdf_matvec_noalloc(const hdf_factor* f, const void* V_dev, int64_t ld
 
 /* X = (lambda I + K~)^{-1} B (Eq. opt with the Woodbury identity of Sec. 1), followed by
  * refine_steps steps of iterative refinement X += (lambda I + K~)^{-1} (B - lambda X - K~ X).
- * lambda > 0.  The r x r core lambda S^{-1} + U^T U is factored on the host in FP64 (LU
- * with partial pivoting) and cached per lambda; rank r must be <= 4096.  Synchronises. */
+ * lambda > 0.  U^T U is formed on the device on the first call (tensor cores for FP32 factors)
+ * and kept; the r x r core lambda S^-1 + U^T U (indefinite: S has eigenvalues of both signs) is
+ * factored in FP64 by a blocked LU with partial pivoting -- each 64-column panel on the host
+ * threads, the interchanges and the trailing updates on the device -- and its factors are kept
+ * on the device per lambda; the triangular solves run on the device.  The padded rank (ldu) must
+ * be <= 32768 (HDF_ETOOBIG); device memory for two r x r FP64 matrices is needed.  HDF_ESINGULAR
+ * if the core is singular.  Synchronises. */
 hdf_status hdf_solve(hdf_factor* f, double lambda, const void* B_dev, int64_t ldb, int ncols,
                      void* X_dev, int64_t ldx, int refine_steps, hdf_stream stream);
 

@@ -602,6 +602,7 @@ static int utv_chunks(int64_t n, int64_t r, int cg) {
 }
 
 constexpr int kMaxGroup = 64;
+constexpr int64_t kMaxSolveRank = 32768;      // the solve's r x r core and its factors on the device
 
 // Per-column-group products U_in^T V and U W.  FP32 factors run both on the tensor cores
 // (tcgen05, 3xTF32 with FP32 sums per row chunk) whenever the factor allows it (not disabled
@@ -815,73 +816,26 @@ extern "C" hdf_status hdf_matvec_transpose(const hdf_factor* f, const void* V_de
 
 // --------------------------------------------------------------------------- solve
 
-// Host LU with partial pivoting of the r x r core (row-major, in place), blocked right-looking:
-// each 64-column panel is factored serially, then the block row U12 (forward substitution with
-// the panel's unit lower triangle) and the trailing matrix (A22 -= L21 U12, in 4 x 8 register
-// blocks) are updated on the worker pool.  Row interchanges cover whole rows, so
-// pivots and factors equal those of the unblocked algorithm up to rounding order.
-static bool lu_factor(int64_t r, std::vector<double>& A, std::vector<int>& piv) {
-    piv.resize(r);
-    const int64_t NB = 64, RB = 32, CB = 128;
-    for (int64_t kb = 0; kb < r; kb += NB) {
-        const int64_t ke = std::min(r, kb + NB);
-        for (int64_t k = kb; k < ke; ++k) {
-            int64_t p = k;
-            double best = std::fabs(A[k * r + k]);
-            for (int64_t i = k + 1; i < r; ++i)
-                if (std::fabs(A[i * r + k]) > best) { best = std::fabs(A[i * r + k]); p = i; }
-            piv[k] = (int)p;
-            if (best == 0.0 || !std::isfinite(best)) return false;
-            if (p != k)
-                for (int64_t j = 0; j < r; ++j) std::swap(A[k * r + j], A[p * r + j]);
-            const double inv = 1.0 / A[k * r + k];
-            const double* Ak = &A[k * r];
-            for (int64_t i = k + 1; i < r; ++i) {
-                double* Ai = &A[i * r];
-                const double l = Ai[k] * inv;
-                Ai[k] = l;
-                if (l == 0.0) continue;
-                for (int64_t j = k + 1; j < ke; ++j) Ai[j] -= l * Ak[j];
-            }
-        }
-        if (ke == r) break;
-        const int64_t nt = r - ke;
-        parallel_for((int)((nt + CB - 1) / CB), [&](int cbk) {
-            const int64_t j0 = ke + cbk * CB, j1 = std::min(r, j0 + CB);
-            for (int64_t i = kb + 1; i < ke; ++i) {
-                double* Ai = &A[i * r];
-                for (int64_t q = kb; q < i; ++q) {
-                    const double l = Ai[q];
-                    const double* Aq = &A[q * r];
-                    for (int64_t j = j0; j < j1; ++j) Ai[j] -= l * Aq[j];
-                }
-            }
-        });
-        // A22 -= L21 U12: row blocks of RB rows on the pool, register-blocked in each
-        parallel_for((int)((nt + RB - 1) / RB), [&](int rbk) {
-            const int64_t i0 = ke + rbk * RB, i1 = std::min(r, i0 + RB);
-            gemm_minus(i1 - i0, nt, ke - kb, &A[i0 * r + kb], r, &A[kb * r + ke], r, &A[i0 * r + ke], r);
-        });
-    }
-    return true;
-}
+namespace hdf {
+// The device LU of the Woodbury core (lu.cu).
+hdf_status lu_factor_device(int64_t r, double* C, DevBuf& dperm, cudaStream_t st);
+hdf_status lu_solve_device(int64_t r, const double* LU, const int* dperm, const double* zi, double* z, int nc,
+                           cudaStream_t st);
+hdf_status core_init_device(const double* G, const double* Spad, double lambda, int64_t r, double* C, cudaStream_t st);
+}  // namespace hdf
 
-// Solve LU z = b in place for one column b (length r).
-static void lu_solve(int64_t r, const std::vector<double>& A, const std::vector<int>& piv, double* b) {
-    for (int64_t k = 0; k < r; ++k) if (piv[k] != k) std::swap(b[k], b[piv[k]]);
-    for (int64_t i = 0; i < r; ++i) {
-        double s = b[i];
-        for (int64_t j = 0; j < i; ++j) s -= A[i * r + j] * b[j];
-        b[i] = s;
-    }
-    for (int64_t i = r - 1; i >= 0; --i) {
-        double s = b[i];
-        for (int64_t j = i + 1; j < r; ++j) s -= A[i * r + j] * b[j];
-        b[i] = s / A[i * r + i];
-    }
+namespace {
+// y (bulk type) = z (FP64), n values.
+template <typename T>
+__global__ void k_cast_from_double(const double* __restrict__ z, T* __restrict__ y, int64_t n) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx < n) y[idx] = (T)z[idx];
 }
+}  // namespace
 
-// Xout = (lambda I + U S U^T)^{-1} Bin = (Bin - U C^{-1} U^T Bin) / lambda, C = lambda S^{-1} + U^T U.
+// Xout = (lambda I + U S U^T)^{-1} Bin = (Bin - U C^{-1} U^T Bin) / lambda, C = lambda S^{-1} + U^T U,
+// with C's LU factors on the device (f->core): per group of <= 64 columns, U^T Bin (FP64 sums),
+// the two triangular solves on the device, then U times the result.
 template <typename T>
 static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int64_t ldb, int ncols, T* Xout,
                                  int64_t ldx, cudaStream_t st) {
@@ -896,11 +850,10 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
     const int cmax = std::min(ncols, kMaxGroup);
     GroupWork g;
     if (hdf_status e = group_setup(f, f, r, cmax, g, st); e != HDF_OK) return e;
-    DevBuf Wd, Wt;
+    DevBuf Wd, Zd, Wt;
     HDF_CUDA(Wd.alloc_on(sizeof(double) * (size_t)r * cmax, st));
+    HDF_CUDA(Zd.alloc_on(sizeof(double) * (size_t)r * cmax, st));
     HDF_CUDA(Wt.alloc_on(sizeof(T) * (size_t)r * cmax, st));
-    std::vector<double> z((size_t)r * cmax), col(r);
-    std::vector<T> y((size_t)r * cmax);
     for (int j0 = 0; j0 < ncols; j0 += kMaxGroup) {
         const int cg = std::min(kMaxGroup, ncols - j0);
         int np = 0;
@@ -909,19 +862,17 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
         dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg,
                                                                                nullptr, nullptr, Wd.as<double>());
         HDF_CUDA(cudaGetLastError());
-        HDF_CUDA(cudaMemcpyAsync(z.data(), Wd.p, sizeof(double) * r * cg, cudaMemcpyDeviceToHost, st));
-        HDF_CUDA(cudaStreamSynchronize(st));
-        for (int j = 0; j < cg; ++j) {
-            for (int64_t a = 0; a < r; ++a) col[a] = z[a * cg + j];
-            lu_solve(r, f->LU, f->piv, col.data());
-            for (int64_t a = 0; a < r; ++a) y[a * cg + j] = (T)col[a];
-        }
-        HDF_CUDA(cudaMemcpyAsync(Wt.p, y.data(), sizeof(T) * r * cg, cudaMemcpyHostToDevice, st));
+        if (hdf_status e = lu_solve_device(r, f->core_lu.as<double>(), f->core_perm.as<int>(), Wd.as<double>(),
+                                           Zd.as<double>(), cg, st);
+            e != HDF_OK)
+            return e;
+        HDF_COUNT_LAUNCH();
+        k_cast_from_double<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(Zd.as<double>(), Wt.as<T>(), r * cg);
+        HDF_CUDA(cudaGetLastError());
         if (hdf_status e = group_uw<T>(f, r, Wt.as<T>(), cg, (T)(-1.0 / lambda), Bin + j0 * ldb, ldb,
                                        (T)(1.0 / lambda), Xout + j0 * ldx, ldx, g, st);
             e != HDF_OK)
             return e;
-        HDF_CUDA(cudaStreamSynchronize(st));      // y is reused by the next group
     }
     return HDF_OK;
 }
@@ -930,8 +881,8 @@ template <typename T>
 static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb, int ncols, T* X, int64_t ldx,
                           int refine, cudaStream_t st) {
     const int64_t n = f->info.n, r = (f->info.rank > 0) ? f->info.ldu : 0;
-    if (r > 4096) return fail(HDF_ETOOBIG, "hdf_solve: padded rank > 4096");
-    if (r > 0 && f->G.empty()) {
+    if (r > kMaxSolveRank) return fail(HDF_ETOOBIG, "hdf_solve: padded rank > 32768");
+    if (r > 0 && !f->core_G.p) {
         DevBuf Gd;
         HDF_CUDA(Gd.alloc(sizeof(double) * (size_t)r * r));
         cudaEvent_t g0, g1;
@@ -955,8 +906,6 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
             HDF_CUDA(cudaGetLastError());
         }
         HDF_CUDA(cudaEventRecord(g1, st));
-        std::vector<double> G((size_t)r * r);
-        HDF_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
         HDF_CUDA(cudaStreamSynchronize(st));
         float gms = 0.f;
         cudaEventElapsedTime(&gms, g0, g1);
@@ -964,25 +913,35 @@ static hdf_status solve_t(hdf_factor* f, double lambda, const T* B, int64_t ldb,
         cudaEventDestroy(g1);
         // a Gram matrix from a kernel that gave up a wait is not kept
         if (hdf_status e = take_device_error(f); e != HDF_OK) return e;
-        f->G.swap(G);
+        std::swap(f->core_G.p, Gd.p);
+        std::swap(f->core_G.bytes, Gd.bytes);
         f->info.t_ms[6] = gms;
+        f->core_lambda = -1.0;
     }
     if (r > 0 && f->core_lambda != lambda) {
-        f->LU = f->G;
-        // padding columns (S = 0, zero columns of U) get a unit diagonal and solve to zero
-        for (int64_t a = 0; a < r; ++a) {
-            const double sa = f->plan.Spad[a];
-            f->LU[a * r + a] += (sa != 0.0) ? lambda / sa : 1.0;
+        // C = lambda S^-1 + U^T U (padding columns: zero columns of U with S = 0 get a unit
+        // diagonal and solve to zero), factored on the device
+        const double t0 = now_ms();
+        if (!f->core_S.p) {
+            HDF_CUDA(f->core_S.alloc(sizeof(double) * (size_t)r));
+            HDF_CUDA(cudaMemcpy(f->core_S.p, f->plan.Spad.data(), sizeof(double) * r, cudaMemcpyHostToDevice));
         }
-        if (!lu_factor(r, f->LU, f->piv)) {
-            f->core_lambda = -1.0;
-            return fail(HDF_ESINGULAR, "hdf_solve: singular core lambda S^-1 + U^T U");
-        }
+        if (!f->core_lu.p) HDF_CUDA(f->core_lu.alloc(sizeof(double) * (size_t)r * r));
+        f->core_lambda = -1.0;
+        if (hdf_status e = core_init_device(f->core_G.as<double>(), f->core_S.as<double>(), lambda, r,
+                                            f->core_lu.as<double>(), st);
+            e != HDF_OK)
+            return e;
+        if (hdf_status e = lu_factor_device(r, f->core_lu.as<double>(), f->core_perm, st); e != HDF_OK) return e;
         f->core_lambda = lambda;
+        f->info.lu_ms = now_ms() - t0;
     }
     hdf_status s = woodbury_apply<T>(f, lambda, B, ldb, ncols, X, ldx, st);
     if (s != HDF_OK) return s;
-    if (refine <= 0) return take_device_error(f);
+    if (refine <= 0) {
+        HDF_CUDA(cudaStreamSynchronize(st));
+        return take_device_error(f);
+    }
     DevBuf Rb, KX, dX;
     HDF_CUDA(Rb.alloc(sizeof(T) * (size_t)n * ncols));
     HDF_CUDA(KX.alloc(sizeof(T) * (size_t)n * ncols));

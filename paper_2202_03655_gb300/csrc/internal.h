@@ -186,11 +186,11 @@ struct hdf_factor {
     size_t esz = 8;                 // bytes per bulk element
     DevBuf U, S;                    // U n x ldu, S rank (bulk type)
     std::vector<double> S_host;
-    // solve core (lambda S^-1 + U^T U), LU factors on the host
-    std::vector<double> G;
+    // solve core: U^T U (FP64, r x r, kept after the first solve), the LU factors of
+    // lambda S^-1 + U^T U for core_lambda (row-major, in place) and their row permutation, S on
+    // the padded columns (FP64), all on the device
+    DevBuf core_G, core_lu, core_perm, core_S;
     double core_lambda = -1.0;
-    std::vector<double> LU;
-    std::vector<int> piv;
     // tensor-core matvec (FP32 factors): enabled unless HDF_FLAG_CUDA_CORES; dev_err is set by
     // a kernel whose bounded wait expired
     bool use_tc = true;

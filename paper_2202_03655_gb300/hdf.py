@@ -35,7 +35,7 @@ class HdfInfo(ctypes.Structure):
                 ("center", _c_dbl * MAX_D), ("radius", _c_dbl), ("mu2", _c_dbl), ("cheb_tail", _c_dbl),
                 ("tail_budget", _c_dbl), ("drop_budget", _c_dbl), ("dropped_cost", _c_dbl),
                 ("err_bound", _c_dbl), ("s_k", _c_int * (MAX_L + 1)), ("t_ms", _c_dbl * NPHASE),
-                ("n_y", _c_i64), ("matrix_free", _c_int), ("mf_row", _c_i64)]
+                ("n_y", _c_i64), ("matrix_free", _c_int), ("mf_row", _c_i64), ("lu_ms", _c_dbl)]
 
 
 SIGNATURES = {
