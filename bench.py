@@ -826,7 +826,7 @@ def bench_batch(args):
     peaks, peak_src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     build_kernel_ms = float(tms[5])
-    roof = {"kernel": "k_batch_build (radial factors + harmonics + U of all sets)", "bound": "hbm",
+    roof = {"kernel": "batched build graph (k_batch_radial + k_batch_urows per size class)", "bound": "hbm",
             "achieved": u_bytes / (build_kernel_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
             "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None,
             "algorithmic_bytes": u_bytes, "ms_per_launch": build_kernel_ms}

@@ -237,8 +237,8 @@ hdf_status hdf_batch_matvec(hdf_batch* b, const void* V_dev, int64_t ldv, int nc
 /* Metadata of set s (as hdf_factor_info). */
 hdf_status hdf_batch_info(const hdf_batch* b, int set, hdf_info* info);
 
-/* Phase times of the batched build in ms (layout of hdf_info.t_ms; index 5 is the persistent
- * radial-factor + U kernel). */
+/* Phase times of the batched build in ms (layout of hdf_info.t_ms; index 5 is the CUDA graph of
+ * the radial-factor phase and the U phases of every size class, index 4 is 0). */
 hdf_status hdf_batch_timings(const hdf_batch* b, double* t_ms);
 
 /* Copy set s's U (n_s x rank_s, packed row-major, bulk type) and S (FP64) to the host. */
