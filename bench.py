@@ -681,8 +681,12 @@ def bench_mfree(args):
     Yc = torch.empty_like(Vc)
     stream = torch.cuda.current_stream(dev)
 
+    # the matrix-free form is what the build picks at the full size (U would not fit); the flag
+    # keeps it at reduced --n too
+    mf = hdf.FLAG_MATRIX_FREE
+
     def one(keep):
-        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream, flags=mf)
         f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
         rec = (f.info, f.matvec_timings()) if keep else None
         f.free()
@@ -693,7 +697,7 @@ def bench_mfree(args):
     mv = np.array([r[1] for r in recs]).mean(axis=0)          # U^T V, reduce, U W (ms)
     value = whole_job_rate(n, ws, args.steps, ms_total)
     # accuracy outside the timed region: sampled rows of K~ V against the exact kernel
-    f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+    f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream, flags=mf)
     f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
     rows = np.sort(W.rng(7).choice(n, 256, replace=False))
     exact = exact_rows_matvec(x, w["kernel"], w["ell"], Vc.t().double(), rows)
@@ -727,7 +731,8 @@ def bench_mfree(args):
     def e2e_step():
         xd.copy_(xh, non_blocking=True)
         Vc.copy_(Vh, non_blocking=True)
-        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream)
+        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp32", p_max=args.p_max, stream=stream,
+                      flags=mf)
         f.matvec_ptr(Vc.data_ptr(), n, c, Yc.data_ptr(), n, stream=stream)
         Yh.copy_(Yc, non_blocking=True)
         f.free()

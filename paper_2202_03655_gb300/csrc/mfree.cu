@@ -40,7 +40,13 @@ struct ZWParams {
     void* Z; void* A0F;
     const void* coefA; const void* coefB;
     int per_warp;                    // shared elements per warp
+    int stage;                       // 1: zchain, a0off and afcol are copied to shared memory per CTA
 };
+
+// Bytes of the index tables k_zwriter stages in shared memory (each part 16-byte aligned).
+__host__ __device__ inline size_t zwriter_tab_bytes(int ldZ, int cstride, int ldA) {
+    return align16(sizeof(int16_t) * (size_t)ldZ * cstride) + 2 * align16(sizeof(int32_t) * (size_t)ldA);
+}
 
 // Per warp shared: level tables (levels x tri), trig (2L+1), the point's F row (nF).
 __host__ __device__ inline int zwriter_per_warp(int levels, int tri, int L, int nF) {
@@ -59,6 +65,22 @@ __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
         cA[idx] = reinterpret_cast<const T*>(P.coefA)[idx];
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
+    const int16_t* zchain = P.zchain;
+    const int32_t* a0off = P.a0off;
+    const int32_t* afcol = P.afcol;
+    if (P.stage) {
+        unsigned char* tp = reinterpret_cast<unsigned char*>(cB + levels * P.tri);
+        tp = reinterpret_cast<unsigned char*>(align16(reinterpret_cast<size_t>(tp)));
+        int16_t* zc = reinterpret_cast<int16_t*>(tp);
+        for (int64_t k = threadIdx.x; k < (int64_t)P.ldZ * P.cstride; k += blockDim.x) zc[k] = P.zchain[k];
+        tp += align16(sizeof(int16_t) * (size_t)P.ldZ * P.cstride);
+        int32_t* ao = reinterpret_cast<int32_t*>(tp);
+        int32_t* af = ao + align16(sizeof(int32_t) * (size_t)P.ldA) / sizeof(int32_t);
+        for (int k = threadIdx.x; k < P.nA; k += blockDim.x) { ao[k] = P.a0off[k]; af[k] = P.afcol[k]; }
+        zchain = zc;
+        a0off = ao;
+        afcol = af;
+    }
     __syncthreads();
     T* tbl = base;
     T* trig = tbl + levels * P.tri;
@@ -72,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
         __syncwarp();
         T* zr = reinterpret_cast<T*>(P.Z) + i * (int64_t)P.ldZ;
         for (int t = lane; t < P.ldZ; t += 32) {
-            const int16_t* ch = P.zchain + (int64_t)t * P.cstride;
+            const int16_t* ch = zchain + (int64_t)t * P.cstride;
             const int tr = ch[tl];
             T v = (T)0;
             if (tr != 0x7fff) {                  // 0x7fff marks a padding column
@@ -82,7 +104,7 @@ __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
             zr[t] = v;
         }
         T* ar = reinterpret_cast<T*>(P.A0F) + i * (int64_t)P.ldA;
-        for (int q = lane; q < P.ldA; q += 32) ar[q] = (q < P.nA) ? tbl[P.a0off[q]] * Fs[P.afcol[q]] : (T)0;
+        for (int q = lane; q < P.ldA; q += 32) ar[q] = (q < P.nA) ? tbl[a0off[q]] * Fs[afcol[q]] : (T)0;
         __syncwarp();
     }
 }
@@ -406,10 +428,14 @@ hdf_status mf_write(hdf_factor* f, const double* x, int64_t n, int d, const dev:
     P.per_warp = dev::zwriter_per_warp(levels, tb.tri, ft.L_used, tb.nF);
     const size_t coef = sizeof(T) * 2 * (size_t)levels * tb.tri;
     const size_t budget = 200 * 1024;
-    const int warps = (int)std::min<size_t>(16, (budget - coef) / (sizeof(T) * P.per_warp));
-    if (coef + sizeof(T) * P.per_warp > budget || warps < 1)
+    const size_t tabs = dev::zwriter_tab_bytes(ft.ldZ, chain_stride(d), ft.ldA) + 16;
+    // stage the index tables only when 16 warps still fit beside them (fewer warps measured slower)
+    P.stage = (coef + tabs + 16 * sizeof(T) * (size_t)P.per_warp <= budget) ? 1 : 0;
+    const size_t fixed = coef + (P.stage ? tabs : 0);
+    const int warps = (int)std::min<size_t>(16, (budget - std::min(budget, fixed)) / (sizeof(T) * P.per_warp));
+    if (fixed + sizeof(T) * P.per_warp > budget || warps < 1)
         return fail(HDF_ETOOBIG, "hdf_build: matrix-free harmonic tables exceed shared memory");
-    const size_t sm = coef + sizeof(T) * (size_t)warps * P.per_warp;
+    const size_t sm = fixed + sizeof(T) * (size_t)warps * P.per_warp;
     HDF_CUDA(cudaFuncSetAttribute(dev::k_zwriter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int occ = 0, nsm = 0, dv = 0;
     HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_zwriter<T>, warps * 32, sm));

@@ -796,15 +796,26 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
             const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
             const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
             const int nk = ksteps(item);
+            // the point's values for step kt; with CP <= 32 the next step's are loaded while this
+            // step's products are formed (the loads' latency is the generators' main stall)
+            constexpr bool PF = CP <= 32;
+            float av[NQ], vv[CP], an[NQ], vn[CP];
+            auto load = [&](int kt2, float* a_, float* v_) {
+                const int64_t i = i0 + (int64_t)kt2 * BK + kk;
+                const bool pv = kt2 < nk && i < i1;
+#pragma unroll
+                for (int g = 0; g < NQ; ++g) a_[g] = (pv && q0 + g < nq) ? __ldg(p.A0F + i * p.ldA + ao + q0 + g) : 0.f;
+#pragma unroll
+                for (int cc = 0; cc < CP; ++cc) v_[cc] = (pv && cc < p.c) ? __ldg(p.V + i + (int64_t)cc * p.ldv) : 0.f;
+            };
+            if (PF) load(0, av, vv);
             for (int kt = 0; kt < nk; ++kt, ++it) {
                 const uint32_t sb = it % SB;
-                const int64_t i = i0 + (int64_t)kt * BK + kk;
-                const bool pv = i < i1;
-                float av[NQ], vv[CP];
-#pragma unroll
-                for (int g = 0; g < NQ; ++g) av[g] = (pv && q0 + g < nq) ? __ldg(p.A0F + i * p.ldA + ao + q0 + g) : 0.f;
-#pragma unroll
-                for (int cc = 0; cc < CP; ++cc) vv[cc] = (pv && cc < p.c) ? __ldg(p.V + i + (int64_t)cc * p.ldv) : 0.f;
+                if (PF) {
+                    load(kt + 1, an, vn);
+                } else {
+                    load(kt, av, vv);
+                }
                 bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
                 free_ = __all_sync(0xffffffffu, free_);
                 if (!free_) { ok = false; break; }
@@ -824,6 +835,12 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.bfull[sb]);
+                if (PF) {
+#pragma unroll
+                    for (int g = 0; g < NQ; ++g) av[g] = an[g];
+#pragma unroll
+                    for (int cc = 0; cc < CP; ++cc) vv[cc] = vn[cc];
+                }
             }
             if (!ok) break;
         }
