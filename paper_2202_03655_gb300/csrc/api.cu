@@ -1125,15 +1125,17 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         if (sizeof(T) == 4 && sm32 <= 200 * 1024) {
             R.QC = PL.dQC.as<float2>();
             R.mtp = mtp;
-            HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32));
+            const int kopt = dev::radialF_df_kopt(m0 + m1, dev::kRfThreads / 32 - 1);
+            auto rk = kopt == 2 ? dev::k_radial_F_df<2> : kopt == 4 ? dev::k_radial_F_df<4> : dev::k_radial_F_df<8>;
+            HDF_CUDA(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32));
             int occ = 0, nsm = 0, dv = 0;
-            HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::k_radial_F_df, dev::kRfThreads, sm32));
+            HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk, dev::kRfThreads, sm32));
             HDF_CUDA(cudaGetDevice(&dv));
             HDF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dv));
             const int g32 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
                                                                           (n + dev::kFTile - 1) / dev::kFTile));
             HDF_COUNT_LAUNCH();
-            dev::k_radial_F_df<<<g32, dev::kRfThreads, sm32, st>>>(R);
+            rk<<<g32, dev::kRfThreads, sm32, st>>>(R);
         } else {
             if (sm64 > 200 * 1024) return fail(HDF_ETOOBIG, "hdf_build: radial tile exceeds shared memory");
             HDF_CUDA(cudaFuncSetAttribute(dev::k_radial_F<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));

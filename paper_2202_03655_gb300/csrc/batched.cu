@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_radial(const BuildSet* __restr
                         smem_raw + dev::align16(sizeof(float2) * dev::kFTile * LP1 + sizeof(float) * dev::kFTile));
                     if (threadIdx.x < dev::kFTile) dev::radialF_df_basis(S.rf, tq, threadIdx.x, Ts, rh);
                     __syncthreads();
-                    dev::radialF_df_q(S.rf, Ts, rh, S.rf.QC, Qs, threadIdx.x, blockDim.x);
+                    dev::radialF_df_q<8>(S.rf, Ts, rh, S.rf.QC, Qs, threadIdx.x, blockDim.x);
                     __syncthreads();
                     dev::radialF_df_f(S.rf, tq, Qs, reinterpret_cast<const float*>(S.rf.Wt), threadIdx.x, blockDim.x);
                     __syncthreads();

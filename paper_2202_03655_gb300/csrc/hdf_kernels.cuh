@@ -309,7 +309,7 @@ __device__ __forceinline__ void dot2_step(float2 a, float bh, float bl, float& s
 //          float pairs ((L+1) x mtp, odd columns zero in row L, mtp a multiple of 8), times rho
 //          for the odd outputs;
 //   F:     F[p][col] = sum_l Q[par(col) block + l][p] Wt[l][col] in FP32.
-// The basis of the next tile is computed by a separate warp while the others work on this one.
+// The basis of the next tile is computed by one warp while the others form this tile's Q.
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     e = b - (s - a);
@@ -418,9 +418,9 @@ __device__ __forceinline__ void radialF_df_basis(const RFParams& P, int64_t t0, 
 
 // Q part, by the nth compute threads (thread = point p and a group of kOpt outputs: each basis
 // value read from shared memory serves kOpt outputs, one 16-byte load brings two outputs).
+template <int kOpt = 8>
 __device__ __forceinline__ void radialF_df_q(const RFParams& P, const float2* Ts, const float* rh, const float2* QC,
                                              float* Qs, int tid, int nth) {
-    constexpr int kOpt = 8;
     const int LP1 = P.L + 1;
     const int mt = P.m0 + P.m1;
     const int p = tid % kFTile;
@@ -555,19 +555,36 @@ __global__ void __launch_bounds__(256) k_radial_F(RFParams P) {
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) radialF_tile<T>(P, tile * kFTile, smem_raw);
 }
 
-// Shared memory of k_radial_F_df: QC, Wt (when staged), basis values, Q.
+// Shared memory of k_radial_F_df: QC, Wt (when staged), two buffers of basis values, Q.
+__host__ __device__ inline size_t radialF_df_basis_bytes(int L) {
+    return align16(sizeof(float2) * kFTile * (L + 1) + sizeof(float) * kFTile);
+}
 __host__ __device__ inline size_t radialF_df_smem(int L, int m0, int m1, int mtp, int nF, bool stage_wt) {
     const int mmax = m0 > m1 ? m0 : m1;
     return align16(sizeof(float2) * (size_t)(L + 1) * mtp) +
-           (stage_wt ? align16(sizeof(float) * (size_t)mmax * nF) : 0) +
-           align16(sizeof(float2) * kFTile * (L + 1) + sizeof(float) * kFTile) +
+           (stage_wt ? align16(sizeof(float) * (size_t)mmax * nF) : 0) + 2 * radialF_df_basis_bytes(L) +
            sizeof(float) * (size_t)(m0 + m1) * kFTile;
 }
 
-// FP32 factors: per tile, warp 0 computes the basis values, then all warps Q and F.  QC (and Wt
-// when P.stage_wt) are staged per CTA; two CTAs per SM.
-constexpr int kRfThreads = 256;
-static __global__ void __launch_bounds__(kRfThreads, 2) k_radial_F_df(RFParams P) {
+// Outputs per thread of the Q part (2, 4 or 8) for mt outputs over qwarps warps: the fewest
+// outputs per thread after rounding (each warp takes whole groups of kOpt outputs for its 32
+// points), larger groups on ties (fewer shared loads per output).
+__host__ __device__ inline int radialF_df_kopt(int mt, int qwarps) {
+    int best = 8, cost = 1 << 30;
+    for (int k = 8; k >= 2; k /= 2) {
+        const int groups = (mt + k - 1) / k;
+        const int c = ((groups + qwarps - 1) / qwarps) * k;
+        if (c < cost) { cost = c; best = k; }
+    }
+    return best;
+}
+
+// FP32 factors, one CTA of kRfThreads per SM.  Per tile of kFTile points: warps 1.. form Q while
+// warp 0 computes the basis values of the CTA's next tile into the other buffer, then all warps
+// form F.  QC (and Wt when P.stage_wt) are staged per CTA.
+constexpr int kRfThreads = 512;
+template <int KOPT>
+static __global__ void __launch_bounds__(kRfThreads, 1) k_radial_F_df(RFParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LP1 = P.L + 1;
     const int mmax = P.m0 > P.m1 ? P.m0 : P.m1;
@@ -581,20 +598,30 @@ static __global__ void __launch_bounds__(kRfThreads, 2) k_radial_F_df(RFParams P
         Ws = w;
         sp += align16(sizeof(float) * (size_t)mmax * P.nF);
     }
-    float2* Ts = reinterpret_cast<float2*>(sp);
-    float* rh = reinterpret_cast<float*>(Ts + kFTile * LP1);
-    sp += align16(sizeof(float2) * kFTile * LP1 + sizeof(float) * kFTile);
+    float2* Tb[2];
+    float* rb[2];
+    for (int b = 0; b < 2; ++b) {
+        Tb[b] = reinterpret_cast<float2*>(sp);
+        rb[b] = reinterpret_cast<float*>(Tb[b] + kFTile * LP1);
+        sp += radialF_df_basis_bytes(P.L);
+    }
     float* Qs = reinterpret_cast<float*>(sp);
     for (int t = threadIdx.x; t < LP1 * P.mtp; t += blockDim.x) QC[t] = P.QC[t];
-    __syncthreads();
     const int64_t ntiles = (P.n + kFTile - 1) / kFTile;
+    if (threadIdx.x < kFTile && blockIdx.x < ntiles) radialF_df_basis(P, blockIdx.x * kFTile, threadIdx.x, Tb[0], rb[0]);
+    __syncthreads();
+    int cur = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (threadIdx.x < kFTile) radialF_df_basis(P, tile * kFTile, threadIdx.x, Ts, rh);
-        __syncthreads();
-        radialF_df_q(P, Ts, rh, QC, Qs, threadIdx.x, kRfThreads);
+        if (threadIdx.x < 32) {
+            const int64_t nxt = tile + gridDim.x;
+            if (nxt < ntiles && threadIdx.x < kFTile) radialF_df_basis(P, nxt * kFTile, threadIdx.x, Tb[cur ^ 1], rb[cur ^ 1]);
+        } else {
+            radialF_df_q<KOPT>(P, Tb[cur], rb[cur], QC, Qs, threadIdx.x - 32, kRfThreads - 32);
+        }
         __syncthreads();
         radialF_df_f(P, tile * kFTile, Qs, Ws, threadIdx.x, kRfThreads);
         __syncthreads();
+        cur ^= 1;
     }
 }
 
@@ -617,7 +644,7 @@ struct UWParams {
     const int32_t* ychain;     // nYp padded harmonic slots -> chain (-1: padding)
     const int32_t* gslot;      // nH: padded slot of each harmonic
     int nYp;
-    const uint32_t* qdesc;     // ldU / VW chunks: (F index << 20) | first harmonic slot
+    const uint32_t* qdesc;     // ldU / VW chunks, two words each (see make_tables)
     int nF;
     const void* F; int64_t ldF;
     void* U; int64_t ldU;
@@ -628,7 +655,7 @@ struct UWParams {
 
 // The index tables the U writer reads for every point (global, or staged in shared memory).
 struct UWTabs {
-    const uint32_t* qdesc;
+    const uint32_t* qdesc;     // two words per chunk (see make_tables)
     const int16_t* chains;
     const int32_t* gslot;
     const int32_t* ychain;
@@ -637,7 +664,7 @@ struct UWTabs {
 // Bytes of the staged index tables: qdesc, chains, gslot, and ychain when harmonics are not
 // precomputed; the kernel lays them out in this order, each 16-byte aligned.
 __host__ __device__ inline size_t uwriter_tab_bytes(int64_t nq, int nH, int cstride, int nYp, bool pre) {
-    return align16(sizeof(uint32_t) * nq) + align16(sizeof(int16_t) * (size_t)nH * cstride) +
+    return align16(sizeof(uint32_t) * 2 * nq) + align16(sizeof(int16_t) * (size_t)nH * cstride) +
            align16(sizeof(int32_t) * (size_t)nH) + (pre ? 0 : align16(sizeof(int32_t) * (size_t)nYp));
 }
 
@@ -723,8 +750,9 @@ __device__ __forceinline__ void point_harmonic_tables(const double* __restrict__
 // base: this warp's shared area (P.per_warp elements, 16-byte aligned), laid out as
 // [harmonic slots (pre only)] [level tables] [trig powers] [radial factors].  pre: the
 // harmonics of the point are computed once into the slots; otherwise each chunk's harmonics
-// are multiplied out from the level tables as it is written.  Every VW-wide chunk of the row
-// is one radial factor times VW consecutive harmonic slots (columns are padded per (k, s)).
+// are multiplied out from the level tables as it is written.  A VW-wide chunk of the row meets
+// one or two (k, s) blocks; its two descriptor words give each block's radial factor and first
+// harmonic slot.
 template <typename T>
 __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X, bool pre, int64_t i, const T* cA,
                                               const T* cB, T* base, int lane) {
@@ -753,43 +781,65 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
         }
     }
     __syncwarp();
-    // row write: one VW-wide chunk per lane per step, two steps in flight
+    // row write: one VW-wide chunk per lane per step, four (FP64: two) steps in flight.  A chunk
+    // is one radial factor times VW consecutive harmonic slots, or (where it meets the end of a
+    // (k, s) block) the first e columns from one block and the rest from the next.
     T* row = Ug + i * P.ldU;
     const int64_t nq = P.ldU / VW;
-    auto chunk = [&](int64_t q) {
-        const uint32_t dsc = X.qdesc[q];
-        const T f = Fs[dsc >> 20];
-        const uint32_t y0 = dsc & 0xFFFFFu;
-        VT out;
-        if (pre) {
-            const VT yv = *reinterpret_cast<const VT*>(Ys + y0);
-            if constexpr (VW == 4) { out.x = f * yv.x; out.y = f * yv.y; out.z = f * yv.z; out.w = f * yv.w; }
-            else { out.x = f * yv.x; out.y = f * yv.y; }
-        } else {
-            T v[VW];
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const int ch = X.ychain[y0 + e];
-                T h = (T)0;
-                if (ch >= 0) {
-                    const int16_t* c = X.chains + (int64_t)ch * P.cstride;
-                    h = trig[P.L + c[levels]];
-                    for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + c[j]];
-                }
-                v[e] = f * h;
-            }
-            if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
-            else { out.x = v[0]; out.y = v[1]; }
+    auto harm = [&](uint32_t y) -> T {          // the harmonic in slot y (0 for a padding slot)
+        if (pre) return Ys[y];
+        const int ch = X.ychain[y];
+        T h = (T)0;
+        if (ch >= 0) {
+            const int16_t* c = X.chains + (int64_t)ch * P.cstride;
+            h = trig[P.L + c[levels]];
+            for (int j = 0; j < levels; ++j) h *= tbl[j * P.tri + c[j]];
         }
+        return h;
+    };
+    auto chunk = [&](int64_t q) {
+        const uint2 w = *reinterpret_cast<const uint2*>(X.qdesc + 2 * q);
+        const uint32_t e = (w.x >> 18) & 3u;
+        const T fa = Fs[w.x >> 20];
+        const uint32_t ya = w.x & 0x3FFFFu;
+        VT out;
+        T v[VW];
+        if (pre) {
+            // one branch-free form for whole and split chunks (e = 0 reads as e = VW; the second
+            // word of a whole chunk names valid slots and is never selected), so that the lanes of
+            // a warp, whose chunks differ in kind and alignment, do not diverge
+            const uint32_t ea = e ? e : (uint32_t)VW;
+            const T fb = Fs[w.y >> 20];
+            const uint32_t yb = (w.y & 0xFFFFFu) - ea;
+            v[0] = fa * Ys[ya];
+#pragma unroll
+            for (int u = 1; u < VW; ++u) {
+                const bool a = (uint32_t)u < ea;
+                v[u] = (a ? fa : fb) * Ys[a ? ya + u : yb + u];
+            }
+        } else if (e == 0) {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) v[u] = fa * harm(ya + u);
+        } else {
+            const T fb = Fs[w.y >> 20];
+            const uint32_t yb = w.y & 0xFFFFFu;
+#pragma unroll
+            for (int u = 0; u < VW; ++u) v[u] = ((uint32_t)u < e) ? fa * harm(ya + u) : fb * harm(yb + u - e);
+        }
+        if constexpr (VW == 4) { out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3]; }
+        else { out.x = v[0]; out.y = v[1]; }
         return out;
     };
+    constexpr int NF = (VW == 4) ? 4 : 2;        // chunks in flight per lane
     int64_t q = lane;
-    for (; q + 32 < nq; q += 64) {
-        const VT o0 = chunk(q), o1 = chunk(q + 32);
-        *reinterpret_cast<VT*>(row + q * VW) = o0;
-        *reinterpret_cast<VT*>(row + (q + 32) * VW) = o1;
+    for (; q + 32 * (NF - 1) < nq; q += 32 * NF) {
+        VT o[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) o[f] = chunk(q + 32 * f);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) *reinterpret_cast<VT*>(row + (q + 32 * f) * VW) = o[f];
     }
-    if (q < nq) *reinterpret_cast<VT*>(row + q * VW) = chunk(q);
+    for (; q < nq; q += 32) *reinterpret_cast<VT*>(row + q * VW) = chunk(q);
     __syncwarp();
 }
 
@@ -821,8 +871,8 @@ __global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
                             align16(sizeof(T) * ((size_t)nwarps * P.per_warp + 2 * (size_t)levels * P.tri));
         const int64_t nq = P.ldU / Vec2<T>::w;
         uint32_t* q = reinterpret_cast<uint32_t*>(tp);
-        for (int64_t k = threadIdx.x; k < nq; k += blockDim.x) q[k] = P.qdesc[k];
-        tp += align16(sizeof(uint32_t) * nq);
+        for (int64_t k = threadIdx.x; k < 2 * nq; k += blockDim.x) q[k] = P.qdesc[k];
+        tp += align16(sizeof(uint32_t) * 2 * nq);
         int16_t* ch = reinterpret_cast<int16_t*>(tp);
         for (int64_t k = threadIdx.x; k < (int64_t)P.nH * P.cstride; k += blockDim.x) ch[k] = P.chains[k];
         tp += align16(sizeof(int16_t) * (size_t)P.nH * P.cstride);

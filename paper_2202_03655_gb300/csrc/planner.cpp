@@ -846,6 +846,10 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     t.cbase.assign(L + 2, 0);
     t.ychain.assign(std::max(1, t.nYp), -1);
     t.gslot.assign(std::max(1, t.nH), 0);
+    // U's column blocks (k, s) follow each other without padding, except that a block of fewer
+    // than vw harmonics (degree 0, and degree 1 in d = 3) is padded to vw zero-extended columns, so
+    // that every vw-wide chunk of a row meets at most two blocks
+    std::vector<int> ucols(L + 1, 0);
     for (int k = 0; k <= L; ++k) {
         for (int g = t.hbase[k]; g < t.hbase[k + 1]; ++g) {
             t.hk[g] = (uint8_t)k;
@@ -853,36 +857,64 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
             t.gslot[g] = yoff[k] + (g - t.hbase[k]);
         }
         const int hkc = (sk[k] > 0) ? (int)ht.count[k] : 0;
-        t.cbase[k + 1] = t.cbase[k] + dimp[k] * sk[k];
+        ucols[k] = (hkc > 0 && hkc < vw) ? vw : hkc;
+        t.cbase[k + 1] = t.cbase[k] + ucols[k] * sk[k];
         int* kt = &t.ktab[kTabStride * k];
         kt[0] = t.fbase[k];
         kt[1] = sk[k];
         kt[2] = t.cbase[k];
         kt[3] = hkc;
         kt[4] = t.hbase[k];
-        kt[5] = dimp[k];
+        kt[5] = ucols[k];
     }
     // rows padded to an odd number of 8-element groups (32 bytes in FP32): every row of U starts
     // on a 32-byte sector (whole-sector stores and loads), and the odd stride spreads the rows of
     // a tile over the DRAM channels (a stride that is a multiple of 128 bytes measured slower)
     t.ldU = ((std::max<int64_t>(vw, t.cbase[L + 1]) + 7) / 8) * 8;
     if ((t.ldU / 8) % 2 == 0) t.ldU += 8;
-    t.qdesc.assign(t.ldU / vw, (uint32_t)t.nF << 20);    // F index nF (a zero slot) for padding
+    if (t.nYp >= (1 << 18)) {
+        err = "too many harmonic slots for the column descriptors";
+        return false;
+    }
     t.colmap.clear();
     t.Spad.assign(t.ldU, 0.0);
+    // per padded column: radial-factor index and harmonic slot (F index nF is a zero slot)
+    std::vector<uint32_t> colF(t.ldU, (uint32_t)t.nF), colY(t.ldU, 0);
+    std::vector<int64_t> blk_end(t.ldU, t.ldU);          // first column after the column's block
     int64_t tcol = 0;
     for (int k = 0; k <= L; ++k) {
         if (sk[k] == 0) continue;
         const int dim = (int)ht.count[k];
         for (int s = 0; s < sk[k]; ++s) {
-            const int64_t c0 = t.cbase[k] + (int64_t)s * dimp[k];
-            for (int q = 0; q < dimp[k] / vw; ++q)
-                t.qdesc[(c0 / vw) + q] = ((uint32_t)(t.fbase[k] + s) << 20) | (uint32_t)(yoff[k] + q * vw);
+            const int64_t c0 = t.cbase[k] + (int64_t)s * ucols[k];
+            for (int h = 0; h < ucols[k]; ++h) {         // padding columns read zero slots
+                colF[c0 + h] = (uint32_t)(t.fbase[k] + s);
+                colY[c0 + h] = (uint32_t)(yoff[k] + h);
+                blk_end[c0 + h] = c0 + ucols[k];
+            }
             for (int h = 0; h < dim; ++h) {
                 t.colmap.push_back(c0 + h);
                 t.Spad[c0 + h] = fc.S[tcol++];
             }
         }
+    }
+    for (int64_t c = t.cbase[L + 1]; c < t.ldU; ++c) blk_end[c] = t.ldU;
+    // chunk q (columns q vw .. q vw + vw - 1): two words.  w0 = (F << 20) | (e << 18) | slot of the
+    // chunk's first column; e = 0 if the chunk lies in one block, else the number of its columns in
+    // the first block; then w1 = (F << 20) | slot of the first column of the second block.
+    const int64_t nq = t.ldU / vw;
+    t.qdesc.assign(2 * nq, 0);
+    for (int64_t q = 0; q < nq; ++q) {
+        const int64_t c0 = q * vw;
+        const int64_t e = std::min<int64_t>(vw, blk_end[c0] - c0);
+        uint32_t w0 = (colF[c0] << 20) | colY[c0], w1 = 0;
+        if (e < vw) {
+            const int64_t cb = c0 + e;
+            w0 |= (uint32_t)e << 18;
+            w1 = (colF[cb] << 20) | colY[cb];
+        }
+        t.qdesc[2 * q] = w0;
+        t.qdesc[2 * q + 1] = w1;
     }
     return true;
 }

@@ -120,10 +120,11 @@ void plan_factor_cross(const std::vector<double>& gram_x, const std::vector<doub
                        FactorChoice& fx, FactorChoice& fy);
 
 // Host images of the tables the device kernels read (FP64; cast to the bulk type on upload).
-// U's columns come in blocks (k, s) of |H_k| harmonics, each block padded with zero columns
-// to a multiple of vw (16 bytes) so that every vw-wide chunk of a row holds one radial factor
-// times vw consecutive harmonics; the padded columns carry S = 0 and leave K~ unchanged.
-// Per point the harmonics are laid out the same way (Y index yoff_k + h, padded per k).
+// U's columns come in blocks (k, s) of |H_k| harmonics, one after another; only a block of fewer
+// than vw (16 bytes) harmonics is padded with zero columns to vw, so that a vw-wide chunk of a
+// row meets at most two blocks (two radial factors, two runs of consecutive harmonic slots).
+// Per point the harmonic slots are laid out per degree k (slot yoff_k + h, padded per k to vw).
+// The padding columns of U carry S = 0 and leave K~ unchanged.
 struct DeviceTables {
     int L_used = 0, tri = 0, nF = 0, nH = 0, mmax = 0, nYp = 0;
     int64_t ldU = 0;                         // padded width of U (a multiple of vw)
@@ -132,11 +133,11 @@ struct DeviceTables {
     std::vector<int16_t> chains;             // nH x (d-1)
     std::vector<int32_t> ychain;             // nYp: chain of each padded Y slot, -1 for padding
     std::vector<int32_t> gslot;              // nH: padded Y slot of each harmonic
-    std::vector<uint32_t> qdesc;             // ldU / vw: (F index << 20) | first Y index of the chunk
+    std::vector<uint32_t> qdesc;             // 2 ldU / vw: per chunk (F << 20 | split << 18 | slot, F << 20 | slot)
     std::vector<int64_t> colmap;             // rank: padded column of each true column
     std::vector<double> Spad;                // ldU: S on the padded columns (0 on padding)
     std::vector<double> coefA, coefB;
-    std::vector<int> ktab;                   // per k: fbase, s_k, cbase, |H_k|, hbase, padded |H_k|
+    std::vector<int> ktab;                   // per k: fbase, s_k, cbase, |H_k|, hbase, columns per (k, s) block
     std::vector<int> fbase, cbase, hbase;
 };
 // vw: elements per 16 bytes of the bulk type.  False if a limit is exceeded.

@@ -162,5 +162,55 @@ int main() {
         std::snprintf(buf, sizeof(buf), "matrix-free layout d=%d (%lld columns)", d, (long long)cols);
         report(buf, bad + (cols != rank ? 1.0 : 0.0), 0.0);
     }
+    // U chunk descriptors: for every stored column (k, s, h) the chunk's two words give the radial
+    // factor of (k, s) and the slot of harmonic h, and every padding column decodes to the zero
+    // factor (index nF) or to a padding slot; FP32 (4 columns per chunk) and FP64 (2)
+    for (int d = 3; d <= 6; ++d)
+        for (int vw : {4, 2}) {
+            const int L = 11;
+            FactorChoice fc;
+            fc.sk.assign(L + 1, 0);
+            for (int k = 0; k <= L; ++k) fc.sk[k] = (k % 5 == 4) ? 0 : 1 + (k * 7 + d) % 4;
+            fc.m[0] = fc.m[1] = 2;
+            fc.Wk.assign(L + 1, std::vector<double>());
+            for (int k = 0; k <= L; ++k) fc.Wk[k].assign((size_t)2 * fc.sk[k], 0.25);
+            int64_t rank = 0;
+            for (int k = 0; k <= L; ++k) rank += harmonic_count(k, d) * fc.sk[k];
+            fc.S.assign(rank, 1.0);
+            DeviceTables tb;
+            std::string err;
+            if (!make_tables(fc, d, L, vw, tb, err)) { report("chunk tables built", 1.0, 0.0); continue; }
+            auto decode = [&](int64_t c, uint32_t& F, uint32_t& slot) {
+                const int64_t q = c / vw;
+                const int u = (int)(c % vw);
+                const uint32_t w0 = tb.qdesc[2 * q], w1 = tb.qdesc[2 * q + 1];
+                const uint32_t e = (w0 >> 18) & 3u;
+                if (e == 0 || (uint32_t)u < e) { F = w0 >> 20; slot = (w0 & 0x3FFFFu) + u; }
+                else { F = w1 >> 20; slot = (w1 & 0xFFFFFu) + u - e; }
+            };
+            double bad = 0.0;
+            std::vector<char> stored(tb.ldU, 0);
+            for (int k = 0; k <= L; ++k)
+                for (int s = 0; s < fc.sk[k]; ++s)
+                    for (int h = 0; h < harmonic_count(k, d); ++h) {
+                        const int64_t c = tb.cbase[k] + (int64_t)s * tb.ktab[kTabStride * k + 5] + h;
+                        stored[c] = 1;
+                        uint32_t F, slot;
+                        decode(c, F, slot);
+                        bad += (F != (uint32_t)(tb.fbase[k] + s)) + (slot != (uint32_t)tb.gslot[tb.hbase[k] + h]);
+                    }
+            for (int64_t c = 0; c < tb.ldU; ++c) {
+                if (stored[c]) continue;
+                uint32_t F, slot;
+                decode(c, F, slot);
+                bad += !(F == (uint32_t)tb.nF || (slot < tb.ychain.size() && tb.ychain[slot] < 0));
+            }
+            int64_t pad = 0;
+            for (char x : stored) pad += !x;
+            char buf[96];
+            std::snprintf(buf, sizeof(buf), "U chunk descriptors d=%d vw=%d (%lld columns, %lld padding)", d, vw,
+                          (long long)rank, (long long)pad);
+            report(buf, bad + ((int64_t)tb.colmap.size() != rank ? 1.0 : 0.0), 0.0);
+        }
     return fails ? 1 : 0;
 }
