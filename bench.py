@@ -17,6 +17,10 @@ K~ V, D2H of Y).  The roofline object describes the dominant kernel of the step.
 FP64-bulk form of the same step is timed beside it (detail.fp64).
 
 Other workloads (--workload):
+  ball3_gauss     the plain FP64 method: n = 2,000 points uniform in the unit ball (d = 3), Gaussian
+                  l = 0.5, tol 1e-6, one N(0,1) vector; step = hdf_build + K~ v with FP64 bulk,
+                  the FP32-bulk form beside it; both checked against the dense kernel matrix; L2
+                  is flushed before each step.
   cube4_gauss     the differentiation row: n = 500,000 points in [-1,1]^4, Gaussian l = 0.8,
                   tol 1e-6, FP32; step = hdf_build + hdf_matvec_adjoint (gradient of w^T K~ v
                   with respect to the points and l); the dominant kernel is the adjoint kernel.
@@ -67,8 +71,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # 200,000-point case of the default workload (dram__bytes_read.sum + dram__bytes_write.sum over
 # n * ldU); the roofline's traffic is this figure scaled to the timed launch.  Set an entry to
 # None when its kernel changes, until it is captured again.
-TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.1663, "k_tc_utv": 4.1500, "k_tc_uw": 4.0655}
+TRAFFIC_PER_U_ELEMENT = {"k_uwriter": None, "k_tc_utv": None, "k_tc_uw": None}
 METRICS = {
+    "ball3_gauss": "factor-build points/s (build + K~v step) of the plain FP64 method, FP32 bulk beside it, vs the dense kernel matrix",
     "mixture3_matern": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
     "normal5_cauchy": "factor-build points/s (build + 16-column K~V of a matrix-free factor: U not stored), FP32 bulk",
     "cube4_gauss": "adjoint step points/s (build + gradient of w^T K~ v w.r.t. points and l), FP32 bulk",
@@ -216,7 +221,7 @@ def blas_threads():
     return None
 
 
-SINGLE_THREAD_WORKLOADS = ("mixture3_matern", "normal5_cauchy", "cube4_gauss", "batch512_gauss")
+SINGLE_THREAD_WORKLOADS = ("ball3_gauss", "mixture3_matern", "normal5_cauchy", "cube4_gauss", "batch512_gauss")
 SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
@@ -533,6 +538,149 @@ def _timed(args, ws, rank, dev, stream, one_step):
     clocks = sampler.stop() if sampler else None
     ms_total = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     return ms_total, recs, launches, clocks
+
+
+def _timed_flushed(args, ws, rank, dev, stream, one_step):
+    """As _timed, for inputs smaller than L2: before each step L2 is flushed by a 256 MiB write
+    outside the step's events, each step is timed by its own event pair, and the total is their
+    sum (max over ranks)."""
+    import torch
+    from paper_2202_03655_gb300 import hdf
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        one_step(False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    l0 = hdf.launch_count()
+    recs, pairs = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        recs.append(one_step(True))
+        e1.record(stream)
+        pairs.append((e0, e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = hdf.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    ms_total = max_over_ranks(sum(a.elapsed_time(b) for a, b in pairs), ws, dev)
+    return ms_total, recs, launches, clocks
+
+
+def bench_plain(args):
+    """The plain FP64 method on the small configuration (ball3_gauss: 2,000 points uniform in the
+    unit ball, Gaussian l = 0.5, tol 1e-6): a step is hdf_build + K~ v (one column) with FP64 bulk;
+    the FP32-bulk form of the same step is timed beside it, and both results are checked against
+    the dense 2,000 x 2,000 kernel matrix."""
+    import numpy as np
+    import torch
+    from paper_2202_03655_gb300 import hdf, workloads as W
+    ws, rank, dev = _setup(args)
+    w = workload_params(args)
+    n, d = w["n"], w["d"]
+    x_np = W.points(args.workload, n=n)
+    v_np = W.rng(w["idx"] + 100).standard_normal(n)
+    x = torch.from_numpy(x_np).to(dev)
+    vs = {"fp64": torch.from_numpy(v_np).to(dev), "fp32": torch.from_numpy(v_np).float().to(dev)}
+    ys = {k: torch.empty_like(v) for k, v in vs.items()}
+    stream = torch.cuda.current_stream(dev)
+
+    def stepper(prec):
+        def one(keep):
+            f = hdf.build(x, w["kernel"], w["ell"], w["tol"], precision=prec, p_max=args.p_max, stream=stream)
+            f.matvec_ptr(vs[prec].data_ptr(), n, 1, ys[prec].data_ptr(), n, stream=stream)
+            rec = None
+            if keep:
+                torch.cuda.current_stream(dev).synchronize()
+                rec = (f.info, f.matvec_timings())
+            f.free()
+            return rec
+        return one
+
+    ms_total, recs, launches, clocks = _timed_flushed(args, ws, rank, dev, stream, stepper("fp64"))
+    ms32, recs32, _, _ = _timed_flushed(args, ws, rank, dev, stream, stepper("fp32"))
+    value = whole_job_rate(n, ws, args.steps, ms_total)
+    # accuracy against the dense kernel matrix (outside the timed regions)
+    z = torch.cdist(x, x) / w["ell"]
+    Kv = torch.exp(-0.5 * z * z) @ vs["fp64"]
+    del z
+    err = {k: float(torch.linalg.norm(ys[k].double() - Kv) / torch.linalg.norm(Kv)) for k in ys}
+    info, info32 = recs[-1][0], recs32[-1][0]
+    r, ldu = info.rank, info.ldu
+    nF = sum(info.s_k[k] for k in range(info.L + 1))
+    mv = np.mean([q[1] for q in recs], axis=0)
+    uw_ms = float(np.mean([q[0].t_ms[5] for q in recs]))
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    kernels = {"k_uwriter": (uw_ms, n * (r * 8 + d * 8 + nF * 8)),
+               "k_utv_tile": (float(mv[0]), n * r * 8 + n * 8),
+               "k_uw_tile": (float(mv[2]), n * r * 8 + n * 8)}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_dom, b_dom = kernels[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": b_dom / (t_dom / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_source": peak_src + " copy bandwidth (burst)", "traffic": None,
+            "algorithmic_bytes": b_dom, "ms_per_launch": t_dom,
+            "note": "2,000 points: every launch is latency-bound; the fraction is reported, not a target"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end from pinned host buffers: H2D of x and v, FP64 build + K~ v, D2H of y
+    xh, vh = torch.from_numpy(x_np).pin_memory(), torch.from_numpy(v_np).pin_memory()
+    yh = torch.empty_like(vh).pin_memory()
+    xd = torch.empty_like(x)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        vs["fp64"].copy_(vh, non_blocking=True)
+        f = hdf.build(xd, w["kernel"], w["ell"], w["tol"], precision="fp64", p_max=args.p_max, stream=stream)
+        f.matvec_ptr(vs["fp64"].data_ptr(), n, 1, ys["fp64"].data_ptr(), n, stream=stream)
+        yh.copy_(ys["fp64"], non_blocking=True)
+        f.free()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = b0.elapsed_time(b1) / k2
+    e2e = {"value": ws * n / (e2e_ms / 1e3), "unit": "points/s", "h2d_bytes_per_step": n * d * 8 + n * 8,
+           "d2h_bytes_per_step": n * 8, "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        V = np.random.default_rng(1).standard_normal((n, 1))
+        cpu_oracle_step(x_np, w, V, args.p_max)
+        ts = cpu_oracle_step(x_np, w, V, args.p_max)
+        cpu = cpu_baseline_line(n / ts, f"all {n} points, one full step (build + K~v), FP64 numpy", args,
+                                args.workload)
+    if rank == 0:
+        line = {"metric": METRICS[args.workload], "value": value, "unit": "points/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "n": n, "d": d, "kernel": w["kernel"], "lengthscale": w["ell"],
+                           "tol": w["tol"], "ncols": 1, "p_max": args.p_max, "p": info.p, "rank": r, "ldu": ldu,
+                           "parallelism": f"replicas{ws}", "l2": "L2 flushed (256 MiB write) before each step"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+                "detail": {"rel_err_vs_dense": err["fp64"], "err_bound": info.err_bound,
+                           "build_ms": float(np.mean([q[0].t_ms[7] for q in recs])),
+                           "build_phase_ms": [float(t) for t in info.t_ms],
+                           "kernel_ms": {k: v[0] for k, v in kernels.items()},
+                           "fp32": {"ms_per_step": ms32 / args.steps, "points_per_s": whole_job_rate(n, ws, args.steps, ms32),
+                                    "rank": info32.rank, "rel_err_vs_dense": err["fp32"],
+                                    "build_ms": float(np.mean([q[0].t_ms[7] for q in recs32]))}}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
 
 
 def _cpu_baseline(args, w):
@@ -1394,6 +1542,8 @@ def main():
         return oracle_once(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ball3_gauss":
+        return bench_plain(args)
     if args.workload == "cube4_gauss":
         return bench_adjoint(args)
     if args.workload == "normal5_cauchy":
@@ -1483,7 +1633,8 @@ def main():
     r, ldu = info.rank, info.ldu
     nF = sum(info.s_k[k] for k in range(info.L + 1))
     # algorithmic bytes count the true rank r; U is stored with zero padding columns up to ldu
-    # (each (k, s) block of harmonics padded to 16 bytes), which the kernels also move
+    # (rows padded to whole sectors, blocks narrower than 16 bytes widened), which the kernels
+    # also move
     uw_bytes = n * r * 4 + n * d * 8 + n * nF * 4
     mv = np.array(mv_ms).mean(axis=0)            # utv, reduce, uw (first 64-column group)
     utv_bytes = n * r * 4 + n * c * 4

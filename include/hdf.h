@@ -241,6 +241,11 @@ hdf_status hdf_batch_info(const hdf_batch* b, int set, hdf_info* info);
  * the radial-factor phase and the U phases of every size class, index 4 is 0). */
 hdf_status hdf_batch_timings(const hdf_batch* b, double* t_ms);
 
+/* *flag = 1 if a kernel of hdf_batch_matvec on this batch gave up a bounded wait since the last
+ * call (the outputs of that product are then invalid), else 0; clears the flag.  Synchronises
+ * the device. */
+hdf_status hdf_batch_device_errors(const hdf_batch* b, int* flag);
+
 /* Copy set s's U (n_s x rank_s, packed row-major, bulk type) and S (FP64) to the host. */
 hdf_status hdf_batch_export(const hdf_batch* b, int set, void* U_host, double* S_host);
 

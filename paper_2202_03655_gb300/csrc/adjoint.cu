@@ -332,25 +332,30 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
             const int16_t* ch = P.chains + (int64_t)gi * P.cstride;
             const int tmu = ch[levels];
             T pvv[kMaxD], pzz[kMaxD], pqq[kMaxD];
-            T prod = trig[P.L + tmu];
 #pragma unroll
             for (int j = 0; j < levels; ++j) {
                 pvv[j] = tv[j * P.tri + ch[j]];
                 pzz[j] = tz[j * P.tri + ch[j]];
                 pqq[j] = tq[j * P.tri + ch[j]];
-                prod *= pvv[j];
             }
+            // suffix products suf[j] = prod_{j2 > j} P_j2, so that the product of all level
+            // factors but one is (trig * prefix) * suffix: O(levels) per harmonic
+            T suf[kMaxD];
+            if (levels > 0) suf[levels - 1] = (T)1;
+#pragma unroll
+            for (int j = levels - 2; j >= 0; --j) suf[j] = suf[j + 1] * pvv[j + 1];
+            const T pl = (levels > 0) ? pvv[0] * suf[0] : (T)1;      // all level factors
+            const T tr = trig[P.L + tmu];
+            const T prod = tr * pl;
             // Y x_hat term
 #pragma unroll
-    #pragma unroll
-        for (int m = 0; m < DD; ++m) g[m] += al * prod * xt[m];
+            for (int m = 0; m < DD; ++m) g[m] += al * prod * xt[m];
             // grad H: level terms
+            T pre = tr;                                  // trig * prod_{j2 < j} P_j2
 #pragma unroll
             for (int j = 0; j < levels; ++j) {
-                T other = trig[P.L + tmu];
-#pragma unroll
-                for (int j2 = 0; j2 < levels; ++j2)
-                    if (j2 != j) other *= pvv[j2];
+                const T other = pre * suf[j];
+                pre *= pvv[j];
                 const int D = DD - 1 - j;
                 const T cz = be * other * pzz[j], cq = be * other * pqq[j] * (T)2;
                 g[D] += cz;
@@ -359,9 +364,6 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams<T> P) {
                     if (m <= D) g[m] += cq * xt[m];
             }
             // grad H: trigonometric factor
-            T pl = (T)1;
-#pragma unroll
-            for (int j = 0; j < levels; ++j) pl *= pvv[j];
             g[0] += be * pl * trx[P.L + tmu];
             g[1] += be * pl * try_[P.L + tmu];
         }

@@ -18,6 +18,7 @@
 // choice in a JSON cache ($HDF_AUTOTUNE_CACHE, default $HOME/.cache/hdf_gb300_autotune.json):
 // tiles per item and CTAs per SM of the radial phase, warps per CTA (8, 16, 32) and CTAs per SM
 // of each U class, and CTAs per SM of the products.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -408,17 +409,12 @@ __global__ void __launch_bounds__(256) k_batch_uw(const MvSet* __restrict__ sets
 // instructions rather than by HBM.  U^T V: lane = TA consecutive columns of U (one 8- or 16-byte
 // load per row), the warps of a CTA stride over the rows of a chunk, V rows are staged in shared
 // memory and read as broadcasts; the eight warps' partial sums are added in a fixed order.
-// U W: a warp owns R rows and every column of them (lane = 4 columns per 128-column pass), W
-// is staged in 512-column blocks, and each row's sums are reduced across the warp by shuffles.
+// U W: k_batch_uw_b below (lane = row, U through bulk copies, W rows as broadcasts).
 template <int CT> struct SkinnyShape {
     static constexpr int TA = CT <= 8 ? 4 : 2;      // U^T V: columns per lane
     static constexpr int AB = 32 * TA;              // U^T V: columns per item
     static constexpr int VR = CT <= 4 ? 512 : (CT == 8 ? 384 : 128);   // U^T V: V rows staged per pass
                                                                         // (static shared memory < 48 KB)
-    static constexpr int R = CT <= 8 ? 4 : 2;       // U W: rows per warp and group
-    static constexpr int G = 4;                     // U W: row groups per warp and item
-    static constexpr int RB = 8 * R * G;            // U W: rows per item
-    static constexpr int WB = 512;                  // U W: W columns staged per pass
 };
 
 template <int N> struct FVec;
@@ -523,84 +519,13 @@ __global__ void __launch_bounds__(256) k_batch_utv_s(const MvSet* __restrict__ s
     }
 }
 
-template <int CT>
-__global__ void __launch_bounds__(256) k_batch_uw_s(const MvSet* __restrict__ sets, const MvItem* __restrict__ items,
-                                                    int nitems, int* counter, float* __restrict__ Y, int64_t ldy,
-                                                    int c) {
-    // W rows (CT floats, zero-padded) are read straight from L1/L2: a lane's four columns are
-    // 4 CT consecutive floats, shared by its R rows; no barrier in the loop.  Each warp takes G
-    // groups of R rows per item; a group's R x CT sums are reduced across the warp through
-    // shared memory (lane o adds output o over the 32 lanes).
-    using SS = SkinnyShape<CT>;
-    constexpr int R = SS::R, G = SS::G, RB = SS::RB, NO = R * CT;     // NO <= 32
-    __shared__ __align__(16) float red[8][32][NO + 1];        // odd row stride: conflict-free
-    __shared__ int s_item;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= nitems) break;
-        const MvItem w = items[it];
-        const MvSet& S = sets[w.set];
-        const float* U = reinterpret_cast<const float*>(S.U);
-        const float* W = reinterpret_cast<const float*>(S.W);
-        for (int gq = 0; gq < G; ++gq) {
-            const int64_t row0 = w.blk * RB + ((int64_t)gq * 8 + warp) * R;
-            if (row0 >= S.n) break;
-            float acc[R][CT];
-#pragma unroll
-            for (int t = 0; t < R; ++t)
-#pragma unroll
-                for (int j = 0; j < CT; ++j) acc[t][j] = 0.f;
-#pragma unroll 2
-            for (int64_t a = 4 * lane; a < S.r; a += 128) {        // S.r is a multiple of 4
-                float u[R][4];
-#pragma unroll
-                for (int t = 0; t < R; ++t) {
-                    const int64_t i = row0 + t;
-                    if (i < S.n) {
-                        FVec<4>::ld(U + i * S.ldU + a, u[t]);
-                    } else {
-                        u[t][0] = u[t][1] = u[t][2] = u[t][3] = 0.f;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float wv[CT];
-                    ld_row<CT>(W + (a + q) * CT, wv);
-#pragma unroll
-                    for (int t = 0; t < R; ++t)
-#pragma unroll
-                        for (int j = 0; j < CT; ++j) acc[t][j] += u[t][q] * wv[j];
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < R; ++t)
-#pragma unroll
-                for (int j = 0; j < CT; ++j) red[warp][lane][t * CT + j] = acc[t][j];
-            __syncwarp();
-            if (lane < NO) {
-                float v = 0.f;
-#pragma unroll 8
-                for (int l2 = 0; l2 < 32; ++l2) v += red[warp][l2][lane];
-                const int t = lane / CT, j = lane % CT;
-                const int64_t i = row0 + t;
-                if (i < S.n && j < c) Y[S.off + i + (int64_t)j * ldy] = v;
-            }
-            __syncwarp();
-        }
-    }
-}
-
 // ------------------------------------------------ pipelined U^T V (c <= 8)
 // The loads of k_batch_utv_s land in registers, which caps the bytes a SM keeps in flight
 // well below what HBM latency needs.  This variant streams U through a per-warp ring of
 // shared-memory stages filled by cp.async (16 bytes per lane, zero fill outside the set),
 // three tiles ahead of the arithmetic, so that registers hold only sums.  (The same ring for
-// U W measured slower than k_batch_uw_s: its shared memory leaves L1 too small to keep the
-// set's W resident, and every W read then waits on L2.)
+// U W, with lane = 4 columns, measured slower than register loads: each lane reads its own W
+// rows, and the ring's shared memory leaves L1 too small to keep the set's W resident.)
 constexpr int kPipeStages = 4;      // tiles in flight per warp
 constexpr int kPipeRows = 4;        // rows per tile
 constexpr int kPipeCols = 128;      // columns per tile (4 per lane)
@@ -764,6 +689,182 @@ void tune_store(const std::map<std::string, int>& m) {
     out << "}\n";
 }
 
+// ------------------------------------------------ U W with tensor copies (c <= 16)
+// Lane = row of the item's 32-row tile (acc[CT] in registers), so that every lane reads the same
+// W row (a shared-memory broadcast) instead of private ones.  The tile's U rows and the matching
+// rows of W stream through a per-warp ring of shared-memory stages, kBwStages - 1 stages ahead of
+// the arithmetic: per stage one TMA tensor copy brings the 32 x 32 block of U (the set's tensor
+// map; rows past the set and columns past its width arrive as zeros; 128-byte swizzle, so that
+// the 16-byte loads of eight consecutive rows hit distinct banks) and one bulk copy the 32 x CT
+// block of W, both completing on the stage's mbarrier.  Items (set, 32-row tile) are taken per
+// warp from a global counter, and the copies of the next items start while the current one is
+// computed.  Every wait is bounded; a warp that gives up records the error, waits (bounded) for
+// its copies in flight and leaves.
+constexpr int kBwCols = 32;                     // columns of U per stage (one 128-byte swizzle row)
+constexpr int kBwStages = 3;
+constexpr int kBwWarps = 4;
+constexpr long long kBwWait = 4000000000ll;     // about 2 s at 2 GHz
+// bytes of one stage: the U block (32 rows of 128 bytes, 1024-byte aligned for the swizzle),
+// then the W block, padded so that the next stage stays 1024-byte aligned
+template <int CT> constexpr int bw_stage_bytes() { return 4096 + ((128 * CT + 1023) / 1024) * 1024; }
+template <int CT> constexpr size_t bw_smem() { return 1024 + (size_t)kBwWarps * kBwStages * bw_stage_bytes<CT>(); }
+
+__device__ __forceinline__ uint32_t b_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool b_mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool b_mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = b_smem_u32(bar);
+    if (b_mbar_try(a, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (b_mbar_try(a, parity)) return true;
+        if (clock64() - t0 > kBwWait) return false;
+    }
+}
+
+// One item of k_batch_uw_b: a 32-row tile of one set, with what its copies and its output need.
+struct BwItem {
+    const float* W;         // the set's W (r x CT)
+    int64_t yoff;           // output row of the tile's first row (set offset + 32 blk)
+    int row0;               // first row of the tile within the set
+    int set;
+    int r;                  // the set's padded width (a multiple of 4)
+    int nrows;              // rows of the tile inside the set (1 .. 32)
+};
+
+template <int CT>
+__global__ void __launch_bounds__(32 * kBwWarps) k_batch_uw_b(const BwItem* __restrict__ items, int nitems,
+                                                              int* counter, const CUtensorMap* __restrict__ maps,
+                                                              float* __restrict__ Y, int64_t ldy, int c, int* err) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t full[kBwWarps][kBwStages];
+    constexpr int SB = bw_stage_bytes<CT>();
+    constexpr int NQ = 8;                     // claimed items not yet finished: at most kBwStages + 1
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // 1024-byte alignment by an offset from the shared-memory pointer itself, so that the
+    // compiler still sees shared-memory loads (a round trip through an integer would leave
+    // generic ones)
+    unsigned char* base = smraw + ((1024u - (b_smem_u32(smraw) & 1023u)) & 1023u);
+    unsigned char* ring = base + (size_t)warp * kBwStages * SB;
+    uint64_t* bar = full[warp];
+    if (lane < kBwStages) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_smem_u32(&bar[lane])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // The copies run ahead of the arithmetic across item boundaries: the issue cursor (stage ti
+    // of ni of the current issue item) takes the item claimed one ahead (its record already
+    // loaded) when its item is exhausted, and claims the next; lane (k mod NQ) keeps the width,
+    // output offset and row count of the k-th item for the arithmetic, which follows in order.
+    auto claim = [&]() -> int {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(counter, 1);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    uint32_t issued = 0, used = 0;            // stages issued and consumed by this warp (ring order)
+    uint32_t q_head = 0, q_tail = 0;          // items: finished, handed to the issue cursor
+    int q_r = 0, q_nrows = 0;
+    int64_t q_yoff = 0;
+    int ti = 0, ni = 0;
+    BwItem cur{};                             // the issue cursor's item
+    int nxt_idx = claim();                    // claimed one ahead, record loaded ahead of use
+    BwItem nxt{};
+    if (nxt_idx < nitems) nxt = items[nxt_idx];
+    bool ok = true;
+    auto advance_issue = [&]() {
+        if (ti >= ni) {                       // the issue item is exhausted (or there is none yet)
+            if (nxt_idx >= nitems) return;
+            cur = nxt;
+            ti = 0;
+            ni = (cur.r + kBwCols - 1) / kBwCols;
+            if (lane == (int)(q_tail % NQ)) { q_r = cur.r; q_nrows = cur.nrows; q_yoff = cur.yoff; }
+            ++q_tail;
+            nxt_idx = claim();
+            if (nxt_idx < nitems) nxt = items[nxt_idx];
+        }
+        const uint32_t slot = issued % kBwStages;
+        const int a0 = ti * kBwCols;
+        const uint32_t wbytes = (uint32_t)(min(kBwCols, cur.r - a0) * CT * 4);   // r: a multiple of 4
+        unsigned char* st = ring + (size_t)slot * SB;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // earlier reads of the slot
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t b = b_smem_u32(&bar[slot]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(4096u + wbytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(b_smem_u32(st)),
+                "l"((uint64_t)(maps + cur.set)), "r"(a0), "r"(cur.row0), "r"(b)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    b_smem_u32(st + 4096)),
+                "l"(cur.W + (int64_t)a0 * CT), "r"(wbytes), "r"(b)
+                : "memory");
+        }
+        ++issued;
+        ++ti;
+    };
+    for (int k = 0; k < kBwStages - 1; ++k) advance_issue();
+    while (ok && q_head < q_tail) {
+        const int src = (int)(q_head % NQ);
+        const int r = __shfl_sync(0xffffffffu, q_r, src);
+        const int nrows = __shfl_sync(0xffffffffu, q_nrows, src);
+        const int64_t yoff = __shfl_sync(0xffffffffu, q_yoff, src);
+        const int nst = (r + kBwCols - 1) / kBwCols;
+        float acc[CT];
+#pragma unroll
+        for (int j = 0; j < CT; ++j) acc[j] = 0.f;
+        for (int t = 0; t < nst; ++t) {
+            advance_issue();                  // keeps kBwStages - 1 stages ahead, across items
+            const uint32_t slot = used % kBwStages;
+            if (!__all_sync(0xffffffffu, b_mbar_wait(&bar[slot], (used / kBwStages) & 1))) { ok = false; break; }
+            ++used;
+            const unsigned char* su = ring + (size_t)slot * SB + lane * 128;     // this lane's row
+            const float* sw = reinterpret_cast<const float*>(ring + (size_t)slot * SB + 4096);
+            const int na = min(kBwCols, r - t * kBwCols);
+            auto cols4 = [&](int jj) {                // columns 4 jj .. 4 jj + 3 (16-byte chunk jj)
+                const float4 u = *reinterpret_cast<const float4*>(su + ((jj ^ (lane & 7)) << 4));
+                const float uq[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float wv[CT];
+                    ld_row<CT>(sw + (4 * jj + q) * CT, wv);
+#pragma unroll
+                    for (int j = 0; j < CT; ++j) acc[j] = fmaf(uq[q], wv[j], acc[j]);
+                }
+            };
+            if (na == kBwCols) {
+#pragma unroll 4
+                for (int jj = 0; jj < kBwCols / 4; ++jj) cols4(jj);
+            } else {
+                for (int jj = 0; jj < na / 4; ++jj) cols4(jj);
+            }
+            __syncwarp();                     // every lane is done with the slot before it is refilled
+        }
+        if (!ok) break;
+        if (lane < nrows) {
+#pragma unroll
+            for (int j = 0; j < CT; ++j)
+                if (j < c) Y[yoff + lane + (int64_t)j * ldy] = acc[j];
+        }
+        ++q_head;
+    }
+    if (!ok) {
+        // copies still in flight land before the warp leaves (bounded)
+        for (; used < issued; ++used) b_mbar_wait(&bar[used % kBwStages], (used / kBwStages) & 1);
+        if (lane == 0) atomicExch(err, 1);
+    }
+}
+
 int ct_for(int c) { return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : c <= 8 ? 8 : c <= 16 ? 16 : c <= 32 ? 32 : 64; }
 
 }  // namespace
@@ -781,6 +882,9 @@ struct hdf_batch {
     DevBuf U, S, arena, dsets;
     // matvec state
     DevBuf mvsets, mvitems_utv, mvitems_red, mvitems_uw, mvpart, mvW, counters;
+    DevBuf derr;                                    // set by a matvec kernel that gave up a bounded wait
+    DevBuf umaps;                                   // per set: TMA tensor map of U (32 x 32 boxes, FP32 batches)
+    DevBuf bwitems;                                 // items of the FP32 U W kernel (32-row tiles)
     int mv_c = 0, n_utv = 0, n_red = 0, n_uw = 0;
     cudaGraphExec_t mv_exec = nullptr;
     const void* mv_V = nullptr;
@@ -1356,7 +1460,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
         if (skinny) {                     // the streaming kernels' columns / rows per item
             AB = (ct <= 8) ? kPipeCols : SkinnyShape<16>::AB;
-            RB = (ct <= 8) ? SkinnyShape<8>::RB : SkinnyShape<16>::RB;
+            RB = 32;                      // k_batch_uw_b: one 32-row tile per item
         }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
@@ -1384,11 +1488,41 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             ms[s].part = b->mvpart.as<double>() + poff[s];
             ms[s].W = b->mvW.as<T>() + woff[s];
         }
+        if (skinny) {
+            // the U W kernel's tensor maps: set s's U as ldU x n FP32, 32 x 32 boxes, 128-byte swizzle
+            std::vector<CUtensorMap> maps(ns);
+            for (int s = 0; s < ns; ++s) {
+                const int64_t n = std::max<int64_t>(1, b->info[s].n), ld = std::max<int64_t>(4, b->info[s].ldu);
+                if (!encode_map_f32(&maps[s], b->U.as<T>() + b->uoff[s], (uint64_t)ld, (uint64_t)n,
+                                    (uint64_t)ld * sizeof(T), 32, 32, true))
+                    return fail(HDF_ECUDA, "hdf_batch_matvec: cannot encode a tensor map");
+            }
+            HDF_CUDA(b->umaps.alloc(sizeof(CUtensorMap) * ns));
+            HDF_CUDA(cudaMemcpyAsync(b->umaps.p, maps.data(), sizeof(CUtensorMap) * ns, cudaMemcpyHostToDevice, st));
+            std::vector<BwItem> bw(iw.size());
+            for (size_t k = 0; k < iw.size(); ++k) {
+                const MvItem& m = iw[k];
+                const int64_t row0 = m.blk * 32;
+                bw[k].W = reinterpret_cast<const float*>(b->mvW.as<T>() + woff[m.set]);
+                bw[k].yoff = b->off[m.set] + row0;
+                bw[k].row0 = (int)row0;
+                bw[k].set = m.set;
+                bw[k].r = (int)ms[m.set].r;
+                bw[k].nrows = (int)std::min<int64_t>(32, ms[m.set].n - row0);
+            }
+            HDF_CUDA(b->bwitems.alloc(sizeof(BwItem) * std::max<size_t>(1, bw.size())));
+            if (!bw.empty())
+                HDF_CUDA(cudaMemcpyAsync(b->bwitems.p, bw.data(), sizeof(BwItem) * bw.size(), cudaMemcpyHostToDevice, st));
+        }
         HDF_CUDA(b->mvsets.alloc_on(sizeof(MvSet) * ns, st));
         HDF_CUDA(b->mvitems_utv.alloc_on(sizeof(MvItem) * std::max<size_t>(1, iu.size()), st));
         HDF_CUDA(b->mvitems_red.alloc_on(sizeof(MvItem) * std::max<size_t>(1, ir.size()), st));
         HDF_CUDA(b->mvitems_uw.alloc_on(sizeof(MvItem) * std::max<size_t>(1, iw.size()), st));
         HDF_CUDA(b->counters.alloc_on(sizeof(int) * 2, st));
+        if (!b->derr.p) {
+            HDF_CUDA(b->derr.alloc(sizeof(int)));
+            HDF_CUDA(cudaMemsetAsync(b->derr.p, 0, sizeof(int), st));
+        }
         HDF_CUDA(cudaMemcpyAsync(b->mvsets.p, ms.data(), sizeof(MvSet) * ns, cudaMemcpyHostToDevice, st));
         if (!iu.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_utv.p, iu.data(), sizeof(MvItem) * iu.size(), cudaMemcpyHostToDevice, st));
         if (!ir.empty()) HDF_CUDA(cudaMemcpyAsync(b->mvitems_red.p, ir.data(), sizeof(MvItem) * ir.size(), cudaMemcpyHostToDevice, st));
@@ -1415,13 +1549,19 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         HDF_CUDA(cudaFuncSetAttribute(k_batch_utv_p<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
                                       (int)utv_pipe_smem<CT>()));                                                 \
         HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_p<CT>, 256, utv_pipe_smem<CT>())); \
-        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<CT>, 256, 0));                \
+        HDF_CUDA(cudaFuncSetAttribute(k_batch_uw_b<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                      (int)bw_smem<CT>()));                                                       \
+        HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_b<CT>, 32 * kBwWarps,          \
+                                                               bw_smem<CT>()));                                   \
         break;
                 HDF_B_OCC(1) HDF_B_OCC(2) HDF_B_OCC(4) HDF_B_OCC(8)
 #undef HDF_B_OCC
                 case 16:
                     HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, k_batch_utv_s<16>, 256, 0));
-                    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_s<16>, 256, 0));
+                    HDF_CUDA(cudaFuncSetAttribute(k_batch_uw_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)bw_smem<16>()));
+                    HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_uw_b<16>, 32 * kBwWarps,
+                                                                           bw_smem<16>()));
                     break;
             }
         }
@@ -1438,14 +1578,15 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
                 S, b->mvitems_utv.as<MvItem>(), b->n_utv, cnt, reinterpret_cast<const float*>(V), ldv, c);        \
         if (b->n_red) k_batch_reduce<T><<<b->n_red, 256, 0, b->cap>>>(S, b->mvitems_red.as<MvItem>(), c);          \
         if (b->n_uw)                                                                                              \
-            UW<<<nsm * std::max(occ_w, 1), 256, SW, b->cap>>>(S, b->mvitems_uw.as<MvItem>(), b->n_uw, cnt + 1,     \
-                                                            reinterpret_cast<float*>(Y), ldy, c);                 \
+            UW<<<nsm * std::max(occ_w, 1), 32 * kBwWarps, SW, b->cap>>>(                                          \
+                b->bwitems.as<BwItem>(), b->n_uw, cnt + 1, b->umaps.as<CUtensorMap>(),                            \
+                reinterpret_cast<float*>(Y), ldy, c, b->derr.as<int>());                                          \
         break;
-                HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_s<1>, utv_pipe_smem<1>(), 0)
-                HDF_B_SK(2, k_batch_utv_p<2>, k_batch_uw_s<2>, utv_pipe_smem<2>(), 0)
-                HDF_B_SK(4, k_batch_utv_p<4>, k_batch_uw_s<4>, utv_pipe_smem<4>(), 0)
-                HDF_B_SK(8, k_batch_utv_p<8>, k_batch_uw_s<8>, utv_pipe_smem<8>(), 0)
-                HDF_B_SK(16, k_batch_utv_s<16>, k_batch_uw_s<16>, 0, 0)
+                HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_b<1>, utv_pipe_smem<1>(), bw_smem<1>())
+                HDF_B_SK(2, k_batch_utv_p<2>, k_batch_uw_b<2>, utv_pipe_smem<2>(), bw_smem<2>())
+                HDF_B_SK(4, k_batch_utv_p<4>, k_batch_uw_b<4>, utv_pipe_smem<4>(), bw_smem<4>())
+                HDF_B_SK(8, k_batch_utv_p<8>, k_batch_uw_b<8>, utv_pipe_smem<8>(), bw_smem<8>())
+                HDF_B_SK(16, k_batch_utv_s<16>, k_batch_uw_b<16>, 0, bw_smem<16>())
 #undef HDF_B_SK
             }
         } else
@@ -1474,6 +1615,18 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
 }
 
 extern "C" {
+
+hdf_status hdf_batch_device_errors(const hdf_batch* b, int* flag) {
+    if (!b || !flag) return fail(HDF_EINVAL, "hdf_batch_device_errors: null argument");
+    *flag = 0;
+    if (!b->derr.p) return HDF_OK;
+    HDF_CUDA(cudaDeviceSynchronize());
+    int fl = 0;
+    HDF_CUDA(cudaMemcpy(&fl, b->derr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fl) HDF_CUDA(cudaMemset(b->derr.p, 0, sizeof(int)));
+    *flag = fl ? 1 : 0;
+    return HDF_OK;
+}
 
 hdf_status hdf_build_batched(int nsets, const int64_t* offsets, const double* x_dev, int d, hdf_kernel kernel,
                              const double* lengthscales, double tol, hdf_precision prec, const hdf_options* opt,

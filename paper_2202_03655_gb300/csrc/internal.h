@@ -12,6 +12,8 @@
 
 struct DevBuf;
 
+struct CUtensorMap_st;
+
 namespace hdf {
 
 // Sets the thread-local message returned by hdf_last_error and returns s.
@@ -21,6 +23,11 @@ extern std::atomic<long long> g_launches;
 
 // Tensor-core GEMMs of the FP32 matvec (tc_gemm.cu).  tc_bn: padded N (16, 32, 64) or 0.
 int tc_bn(int c);
+// 2-D FP32 tensor map for TMA: `inner` contiguous elements by `outer` rows of stride_bytes, box
+// {box_inner, box_outer}, zero fill out of bounds, 128-byte swizzle if asked; false when the
+// driver entry point is missing or refuses the arguments.
+bool encode_map_f32(CUtensorMap_st* map, const void* ptr, uint64_t inner, uint64_t outer, uint64_t stride_bytes,
+                    uint32_t box_inner, uint32_t box_outer, bool swizzle128);
 size_t tc_work_floats(int64_t n, int64_t r, int c);
 // Rows per chunk (a multiple of 32) and the number of chunks of the tensor-core U^T V split;
 // tc_utv writes exactly that many partial slices.

@@ -222,8 +222,10 @@ struct Smem {
     int64_t* items;
     uint32_t* slot;
     __device__ explicit Smem(unsigned char* raw) {
-        unsigned char* base =
-            reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+        // 1024-byte alignment by an offset from the shared-memory pointer itself, so that the
+        // compiler still sees shared-memory accesses (a round trip through an integer would
+        // leave generic ones)
+        unsigned char* base = raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u);
         U = base;
         B = U + S_U * UBYTES;
         ufull = reinterpret_cast<uint64_t*>(B + SB * BBYTES);
@@ -694,7 +696,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < BN; ++j) acc[j] = 0.f;
             const int nk = ksteps(item);
-            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = promote<BN>(sm, tmem, it, q, lane, acc);
+            for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = promote_lean<BN>(sm, tmem, it, q, lane, acc);
             if (!ok) break;
             const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
             const int64_t a = mb * BM + 32 * q + lane;
@@ -1217,6 +1219,11 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
 }
 
 }  // namespace tc
+
+bool encode_map_f32(CUtensorMap_st* map, const void* ptr, uint64_t inner, uint64_t outer, uint64_t stride_bytes,
+                    uint32_t box_inner, uint32_t box_outer, bool swizzle128) {
+    return tc::make_map(map, ptr, inner, outer, stride_bytes, box_inner, box_outer, swizzle128);
+}
 
 // Column count padded for the tensor-core path (16, 32 or 64); 0 if not eligible.
 int tc_bn(int c) { return c <= 16 ? 16 : c <= 32 ? 32 : c <= 64 ? 64 : 0; }

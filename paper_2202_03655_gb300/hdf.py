@@ -65,6 +65,7 @@ SIGNATURES = {
     "hdf_batch_matvec": (_c_int, [_vp, _vp, _c_i64, _c_int, _vp, _c_i64, _vp]),
     "hdf_batch_info": (_c_int, [_vp, _c_int, ctypes.POINTER(HdfInfo)]),
     "hdf_batch_timings": (_c_int, [_vp, _pdbl]),
+    "hdf_batch_device_errors": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "hdf_batch_export": (_c_int, [_vp, _c_int, _vp, _pdbl]),
     "hdf_batch_free": (None, [_vp]),
     "hdf_kmeans": (_c_int, [_vp, _c_i64, _c_int, _c_int, ctypes.POINTER(_c_i64), _c_int, _vp, _vp,
@@ -423,6 +424,12 @@ class Batch:
         out = np.zeros(NPHASE)
         _check(lib().hdf_batch_timings(self._h, _dptr(out)))
         return out
+
+    def device_errors(self):
+        """1 if a kernel of the batch's matvec gave up a bounded wait since the last call, else 0."""
+        fl = _c_int(0)
+        _check(lib().hdf_batch_device_errors(self._h, ctypes.byref(fl)))
+        return fl.value
 
     def matvec_ptr(self, V_ptr, ldv, ncols, Y_ptr, ldy, stream=None):
         _check(lib().hdf_batch_matvec(self._h, _vp(V_ptr), int(ldv), int(ncols), _vp(Y_ptr), int(ldy),

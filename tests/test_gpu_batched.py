@@ -64,7 +64,8 @@ def test_batch512_full_size_sampled():
 
 @pytest.mark.parametrize("c", [1, 2, 5, 8, 13, 16, 20])
 def test_batch_matvec_column_counts(c):
-    """FP32 batched K~V for every column-tile width (the streaming kernels for c <= 16, the
+    """FP32 batched K~V for every column-tile width (the streaming kernels for c <= 16, U W with
+    bulk copies of 32-row tiles and ragged last tiles of 3, 900 - 896 and 131 - 128 rows; the
     register-tiled ones above) against hdf_build + hdf_matvec on the same sets."""
     import torch
     from paper_2202_03655_gb300 import hdf
@@ -76,6 +77,7 @@ def test_batch_matvec_column_counts(c):
     Y = b.matvec(to_dev(V, torch.float32)).double().cpu().numpy().reshape(off[-1], c)
     Y2 = b.matvec(to_dev(V, torch.float32)).double().cpu().numpy().reshape(off[-1], c)
     assert np.array_equal(Y, Y2)                                   # deterministic replay
+    assert b.device_errors() == 0                                  # no bounded wait ran out
     for s in range(len(sizes)):
         xs, Vs = x[off[s]:off[s + 1]], V[off[s]:off[s + 1]]
         f1 = hdf.build(to_dev(xs), "gaussian", ells[s], tol, precision="fp32")
