@@ -1186,7 +1186,13 @@ static hdf_status build_device(hdf_factor* f, const double* x, int64_t n, int d,
         P.per_warp = (int)(pick.pw / sizeof(T));
         P.tab_bytes = (int)pick.tabs;
         const size_t sm = dev::align16((size_t)warps * pick.pw + sizeof(T) * 2 * (size_t)levels * ht.tri) + pick.tabs;
-        auto kern = pre ? dev::k_uwriter<T, true> : dev::k_uwriter<T, false>;
+        const bool stg = pick.staged;
+        auto kern = pre ? (stg ? dev::k_uwriter<T, true, false, true> : dev::k_uwriter<T, true, false, false>)
+                        : (stg ? dev::k_uwriter<T, false, false, true> : dev::k_uwriter<T, false, false, false>);
+        // FP32 factors, harmonics precomputed, tables staged, nF <= 32 kPfF: the next point's
+        // radial factors and coordinate are prefetched into registers
+        if constexpr (sizeof(T) == 4)
+            if (pre && stg && nF <= 32 * dev::kPfF) kern = dev::k_uwriter<T, true, true, true>;
         HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         int occ = 0;
         HDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, sm));

@@ -680,34 +680,53 @@ __host__ __device__ inline int uwriter_per_warp(int levels, int tri, int L, int 
 template <typename T>
 __device__ __forceinline__ void point_harmonic_tables(const double* __restrict__ x, int d, const Center& cen,
                                                       double inv2R, int L, int tri, const T* cA, const T* cB,
-                                                      T* tbl, T* trig, int64_t i, int lane) {
+                                                      T* tbl, T* trig, int64_t i, int lane, bool have_x = false,
+                                                      double x_lane = 0.0) {
     const int levels = d - 2;
     // FP32 factors: lane j forms coordinate j once and the warp shares it by shuffles (FP64
     // issues at a small fraction of the FP32 rate here).
+    // xh is indexed with compile-time indices only (loops over kMaxD with the dimension as a
+    // predicate), so that it stays in registers
     T xh[kMaxD];
     T s = (T)0;
     if constexpr (sizeof(T) == 4) {
         double cj = cen.c[0];                    // this lane's centre coordinate (register selects)
 #pragma unroll
         for (int j = 1; j < kMaxD; ++j) cj = (lane == j) ? cen.c[j] : cj;
-        const double xd = (lane < d) ? (x[i * d + lane] - cj) * inv2R : 0.0;   // one FP64 sub, mul
+        // one FP64 sub, mul (x_lane: this lane's coordinate, loaded ahead by the caller)
+        const double xd = (lane < d) ? ((have_x ? x_lane : x[i * d + lane]) - cj) * inv2R : 0.0;
         const float xf = (float)xd;
-        for (int j = 0; j < d; ++j) { xh[j] = __shfl_sync(0xffffffffu, xf, j); s += xh[j] * xh[j]; }
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j) {
+            const float v = __shfl_sync(0xffffffffu, xf, j);      // zero for j >= d
+            xh[j] = v;
+            s += v * v;
+        }
     } else {
-        for (int j = 0; j < d; ++j) { xh[j] = (T)((x[i * d + j] - cen.c[j]) * inv2R); s += xh[j] * xh[j]; }
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j) {
+            xh[j] = (j < d) ? (T)((x[i * d + j] - cen.c[j]) * inv2R) : (T)0;
+            s += xh[j] * xh[j];
+        }
     }
     if (s > (T)0) {
         const T inv = (T)1 / sqrt(s);
-        for (int j = 0; j < d; ++j) xh[j] *= inv;
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j) xh[j] *= inv;
     } else {
-        for (int j = 0; j < d; ++j) xh[j] = (j == 0) ? (T)1 : (T)0;
+#pragma unroll
+        for (int j = 0; j < kMaxD; ++j) xh[j] = (j == 0) ? (T)1 : (T)0;
     }
     // level tables: lanes over mu'
     for (int j = 0; j < levels; ++j) {
         const int D = d - 1 - j;
-        T q = (T)0;
-        for (int m = 0; m <= D; ++m) q += xh[m] * xh[m];
-        const T z = (T)xh[D], qq = (T)q;
+        T q = (T)0, z = (T)0;
+#pragma unroll
+        for (int m = 0; m < kMaxD; ++m) {
+            if (m <= D) q += xh[m] * xh[m];
+            if (m == D) z = xh[m];
+        }
+        const T qq = q;
         const T* A = cA + j * tri;
         const T* B = cB + j * tri;
         T* tb = tbl + j * tri;
@@ -753,9 +772,40 @@ __device__ __forceinline__ void point_harmonic_tables(const double* __restrict__
 // are multiplied out from the level tables as it is written.  A VW-wide chunk of the row meets
 // one or two (k, s) blocks; its two descriptor words give each block's radial factor and first
 // harmonic slot.
+// The radial-factor slots of a warp's shared area (nF + 1, the last one zero).
+template <typename T>
+__device__ __forceinline__ T* uwriter_fs(const UWParams& P, bool pre, T* base) {
+    return base + (pre ? P.nYp : 0) + (P.d - 2) * P.tri + 2 * P.L + 1;
+}
+
+// Radial factors and coordinate of one point loaded into registers one point ahead of use (FP32
+// factors with nF <= 32 kPfF): lane l holds F[i, l + 32 k] and x[i, l] (l < d), so that their
+// global-memory latency passes while the previous row is written.
+constexpr int kPfF = 16;
+template <typename T> struct PointPre { T f[kPfF]; double x; };
+template <typename T>
+__device__ __forceinline__ void point_prefetch(const UWParams& P, int64_t i, int lane, PointPre<T>& pp) {
+    const T* Fg = reinterpret_cast<const T*>(P.F) + i * P.ldF;
+#pragma unroll
+    for (int k = 0; k < kPfF; ++k) {
+        const int f = lane + 32 * k;
+        pp.f[k] = (f < P.nF) ? Fg[f] : (T)0;
+    }
+    pp.x = (lane < P.d) ? P.x[i * P.d + lane] : 0.0;
+}
+template <typename T>
+__device__ __forceinline__ void point_stage_f(const UWParams& P, const PointPre<T>& pp, T* Fs, int lane) {
+#pragma unroll
+    for (int k = 0; k < kPfF; ++k) {
+        const int f = lane + 32 * k;
+        if (f < P.nF) Fs[f] = pp.f[k];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X, bool pre, int64_t i, const T* cA,
-                                              const T* cB, T* base, int lane) {
+                                              const T* cB, T* base, int lane, bool staged = false,
+                                              double x_lane = 0.0) {
     const int levels = P.d - 2;
     T* Ys = base;                                // nYp (pre only)
     T* tbl = base + (pre ? P.nYp : 0);           // levels * tri
@@ -765,10 +815,12 @@ __device__ __forceinline__ void uwriter_point(const UWParams& P, const UWTabs& X
     T* Ug = reinterpret_cast<T*>(P.U);
     typedef typename Vec2<T>::type VT;
     constexpr int VW = Vec2<T>::w;
-    point_harmonic_tables<T>(P.x, P.d, P.c, P.inv2R, P.L, P.tri, cA, cB, tbl, trig, i, lane);
-    // this point's radial factors
-    for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
-    if (lane == 0) Fs[P.nF] = (T)0;
+    point_harmonic_tables<T>(P.x, P.d, P.c, P.inv2R, P.L, P.tri, cA, cB, tbl, trig, i, lane, staged, x_lane);
+    // this point's radial factors (staged: already in Fs, written by the caller)
+    if (!staged) {
+        for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
+        if (lane == 0) Fs[P.nF] = (T)0;
+    }
     __syncwarp();
     if (pre) {
         // padding slots were zeroed once per warp and are never written
@@ -853,7 +905,7 @@ __device__ __forceinline__ void uwriter_zero_slots(const UWParams& P, bool pre, 
 
 // Shared memory of the U writer: [nwarps x per_warp][coefA][coefB] (elements of T).
 // Shared memory: [nwarps x per_warp elements][cA][cB][staged index tables (tab_bytes)].
-template <typename T, bool PRE>
+template <typename T, bool PRE, bool PF, bool STAGED>
 __global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int levels = P.d - 2;
@@ -866,12 +918,15 @@ __global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
     UWTabs X{P.qdesc, P.chains, P.gslot, P.ychain};
-    if (P.tab_bytes) {
+    if constexpr (STAGED) {
+        // staged in shared memory (STAGED is a compile-time choice, so that the table reads
+        // compile to shared-memory loads)
         unsigned char* tp = reinterpret_cast<unsigned char*>(smem_raw) +
                             align16(sizeof(T) * ((size_t)nwarps * P.per_warp + 2 * (size_t)levels * P.tri));
         const int64_t nq = P.ldU / Vec2<T>::w;
         uint32_t* q = reinterpret_cast<uint32_t*>(tp);
         for (int64_t k = threadIdx.x; k < 2 * nq; k += blockDim.x) q[k] = P.qdesc[k];
+        X.qdesc = q;
         tp += align16(sizeof(uint32_t) * 2 * nq);
         int16_t* ch = reinterpret_cast<int16_t*>(tp);
         for (int64_t k = threadIdx.x; k < (int64_t)P.nH * P.cstride; k += blockDim.x) ch[k] = P.chains[k];
@@ -879,7 +934,7 @@ __global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
         int32_t* gs = reinterpret_cast<int32_t*>(tp);
         for (int k = threadIdx.x; k < P.nH; k += blockDim.x) gs[k] = P.gslot[k];
         tp += align16(sizeof(int32_t) * (size_t)P.nH);
-        X.qdesc = q; X.chains = ch; X.gslot = gs;
+        X.chains = ch; X.gslot = gs;
         if (!PRE) {
             int32_t* yc = reinterpret_cast<int32_t*>(tp);
             for (int k = threadIdx.x; k < P.nYp; k += blockDim.x) yc[k] = P.ychain[k];
@@ -889,7 +944,21 @@ __global__ void __launch_bounds__(1024) k_uwriter(UWParams P) {
     __syncthreads();
     uwriter_zero_slots<T>(P, PRE, base, lane);
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
-    for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, X, PRE, i, cA, cB, base, lane);
+    if constexpr (PF) {
+        // PF: the next point's radial factors and coordinate travel in registers during this row
+        T* Fs = uwriter_fs<T>(P, PRE, base);
+        if (lane == 0) Fs[P.nF] = (T)0;
+        PointPre<T> pp;
+        if (gw < P.n) point_prefetch<T>(P, gw, lane, pp);
+        for (int64_t i = gw; i < P.n; i += nw) {
+            point_stage_f<T>(P, pp, Fs, lane);
+            const double xl = pp.x;
+            if (i + nw < P.n) point_prefetch<T>(P, i + nw, lane, pp);
+            uwriter_point<T>(P, X, PRE, i, cA, cB, base, lane, true, xl);
+        }
+    } else {
+        for (int64_t i = gw; i < P.n; i += nw) uwriter_point<T>(P, X, PRE, i, cA, cB, base, lane);
+    }
 }
 
 // --------------------------------------------------------------------- A7: matvec
