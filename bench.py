@@ -67,11 +67,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# DRAM bytes (read + write) per stored U element, from one ncu capture of each kernel on the
-# 200,000-point case of the default workload (dram__bytes_read.sum + dram__bytes_write.sum over
-# n * ldU); the roofline's traffic is this figure scaled to the timed launch.  Set an entry to
-# None when its kernel changes, until it is captured again.
-TRAFFIC_PER_U_ELEMENT = {"k_uwriter": None, "k_tc_utv": None, "k_tc_uw": None}
+# DRAM bytes (read + write) per stored U element, from one ncu capture of each kernel at the
+# benchmark size (n = 1,000,000; dram__bytes_read.sum + dram__bytes_write.sum over n * ldU); the
+# roofline's traffic is this figure times n * ldU of the timed launch.  Set an entry to None
+# when its kernel changes, until it is captured again.
+TRAFFIC_PER_U_ELEMENT = {"k_uwriter": 4.171, "k_tc_utv": 4.276, "k_tc_uw": 4.069}
 METRICS = {
     "ball3_gauss": "factor-build points/s (build + K~v step) of the plain FP64 method, FP32 bulk beside it, vs the dense kernel matrix",
     "mixture3_matern": "factor-build points/s (build + K~V step) at stated rel. error, FP32 bulk vs FP64",
@@ -1663,7 +1663,7 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     tpe = TRAFFIC_PER_U_ELEMENT.get(dom)
     roof["traffic"] = (tpe * n * ldu) if tpe else None
-    roof["traffic_source"] = "ncu dram bytes per U element at n = 200,000, scaled by n * ldU" if tpe else None
+    roof["traffic_source"] = "ncu dram bytes per U element at n = 1,000,000, times n * ldU" if tpe else None
     roof["algorithmic_bytes"] = b_dom
     roof["ms_per_launch"] = t_dom
     kv_bytes = 2 * n * r * 4 + n * c * 8

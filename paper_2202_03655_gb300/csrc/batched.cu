@@ -253,10 +253,10 @@ struct BuildSet {
     int pre;
 };
 
-// Shared memory of one double-float radial tile (basis pairs, rho, Q) in the batched build.
+// Shared memory of the double-float radial tiles (two buffers of basis pairs and rho, then Q) in
+// the batched build.
 inline size_t batch_df_tile_smem(int L, int m0, int m1) {
-    return dev::align16(sizeof(float2) * dev::kFTile * (L + 1) + sizeof(float) * dev::kFTile) +
-           sizeof(float) * (size_t)(m0 + m1) * dev::kFTile;
+    return 2 * dev::radialF_df_basis_bytes(L) + sizeof(float) * (size_t)(m0 + m1) * dev::kFTile;
 }
 
 // A5 for every set in two persistent phases, each with its own register and shared-memory budget:
@@ -283,22 +283,39 @@ __global__ void __launch_bounds__(256, 2) k_batch_radial(const BuildSet* __restr
             const int64_t tq = t0 + (int64_t)q * dev::kFTile;
             if (tq >= S.rf.n) break;
             if constexpr (sizeof(T) == 4) {
-                if (S.rf.QC != nullptr) {
-                    const int LP1 = S.rf.L + 1;
-                    float2* Ts = reinterpret_cast<float2*>(smem_raw);
-                    float* rh = reinterpret_cast<float*>(Ts + dev::kFTile * LP1);
-                    float* Qs = reinterpret_cast<float*>(
-                        smem_raw + dev::align16(sizeof(float2) * dev::kFTile * LP1 + sizeof(float) * dev::kFTile));
-                    if (threadIdx.x < dev::kFTile) dev::radialF_df_basis(S.rf, tq, threadIdx.x, Ts, rh);
+                // FP32 sets always carry the double-float tables (QC): warp 0 forms the basis of
+                // the item's next tile while warps 1.. form this tile's Q (S.rf.kopt outputs per
+                // thread), then all warps form F
+                const int LP1 = S.rf.L + 1;
+                const size_t bb = dev::radialF_df_basis_bytes(S.rf.L);
+                unsigned char* b0 = smem_raw + (q & 1) * bb;          // this tile's basis
+                unsigned char* b1 = smem_raw + ((q & 1) ^ 1) * bb;    // the next tile's
+                float2* Tc = reinterpret_cast<float2*>(b0);
+                float* rc = reinterpret_cast<float*>(Tc + dev::kFTile * LP1);
+                float2* Tn = reinterpret_cast<float2*>(b1);
+                float* rn = reinterpret_cast<float*>(Tn + dev::kFTile * LP1);
+                float* Qs = reinterpret_cast<float*>(smem_raw + 2 * bb);
+                if (q == 0) {
+                    if (threadIdx.x < dev::kFTile) dev::radialF_df_basis(S.rf, tq, threadIdx.x, Tc, rc);
                     __syncthreads();
-                    dev::radialF_df_q<8>(S.rf, Ts, rh, S.rf.QC, Qs, threadIdx.x, blockDim.x);
-                    __syncthreads();
-                    dev::radialF_df_f(S.rf, tq, Qs, reinterpret_cast<const float*>(S.rf.Wt), threadIdx.x, blockDim.x);
-                    __syncthreads();
-                    continue;
                 }
+                if (threadIdx.x < 32) {
+                    const int64_t tn = tq + dev::kFTile;
+                    if (q + 1 < tiles_per_item && tn < S.rf.n && threadIdx.x < dev::kFTile)
+                        dev::radialF_df_basis(S.rf, tn, threadIdx.x, Tn, rn);
+                } else {
+                    const int tid = threadIdx.x - 32, nth = blockDim.x - 32;
+                    if (S.rf.kopt == 2)
+                        dev::radialF_df_q<2>(S.rf, Tc, rc, S.rf.QC, Qs, tid, nth);
+                    else
+                        dev::radialF_df_q<4>(S.rf, Tc, rc, S.rf.QC, Qs, tid, nth);
+                }
+                __syncthreads();
+                dev::radialF_df_f(S.rf, tq, Qs, reinterpret_cast<const float*>(S.rf.Wt), threadIdx.x, blockDim.x);
+                __syncthreads();
+            } else {
+                dev::radialF_tile<T>(S.rf, tq, smem_raw);
             }
-            dev::radialF_tile<T>(S.rf, tq, smem_raw);
         }
     }
 }
@@ -729,18 +746,17 @@ __device__ __forceinline__ bool b_mbar_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
-// One item of k_batch_uw_b: a 32-row tile of one set, with what its copies and its output need.
-struct BwItem {
+// A set of k_batch_uw_b: its 32-row tiles are items tile0 .. tile0 + ceil(n / 32) - 1.
+struct BwSet {
     const float* W;         // the set's W (r x CT)
-    int64_t yoff;           // output row of the tile's first row (set offset + 32 blk)
-    int row0;               // first row of the tile within the set
-    int set;
-    int r;                  // the set's padded width (a multiple of 4)
-    int nrows;              // rows of the tile inside the set (1 .. 32)
+    int64_t off;            // the set's first output row
+    int64_t tile0;          // its first item
+    int n;                  // rows
+    int r;                  // padded width (a multiple of 4)
 };
 
 template <int CT>
-__global__ void __launch_bounds__(32 * kBwWarps) k_batch_uw_b(const BwItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(32 * kBwWarps) k_batch_uw_b(const BwSet* __restrict__ bsets, int nsets, int nitems,
                                                               int* counter, const CUtensorMap* __restrict__ maps,
                                                               float* __restrict__ Y, int64_t ldy, int c, int* err) {
     extern __shared__ unsigned char smraw[];
@@ -772,11 +788,25 @@ __global__ void __launch_bounds__(32 * kBwWarps) k_batch_uw_b(const BwItem* __re
     uint32_t q_head = 0, q_tail = 0;          // items: finished, handed to the issue cursor
     int q_r = 0, q_nrows = 0;
     int64_t q_yoff = 0;
+    // an item's set (binary search over the sets' first items), first row and row count
+    struct Item { const float* W; int64_t yoff; int row0, set, r, nrows; };
+    auto item_of = [&](int v) {
+        int lo = 0, hi = nsets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bsets[mid].tile0 <= v) lo = mid; else hi = mid - 1;
+        }
+        const BwSet& S = bsets[lo];
+        Item t;
+        t.row0 = (int)((v - S.tile0) * 32);
+        t.W = S.W; t.yoff = S.off + t.row0; t.set = lo; t.r = S.r; t.nrows = min(32, S.n - t.row0);
+        return t;
+    };
     int ti = 0, ni = 0;
-    BwItem cur{};                             // the issue cursor's item
-    int nxt_idx = claim();                    // claimed one ahead, record loaded ahead of use
-    BwItem nxt{};
-    if (nxt_idx < nitems) nxt = items[nxt_idx];
+    Item cur{};                               // the issue cursor's item
+    int nxt_idx = claim();                    // claimed one ahead, located ahead of use
+    Item nxt{};
+    if (nxt_idx < nitems) nxt = item_of(nxt_idx);
     bool ok = true;
     auto advance_issue = [&]() {
         if (ti >= ni) {                       // the issue item is exhausted (or there is none yet)
@@ -787,7 +817,7 @@ __global__ void __launch_bounds__(32 * kBwWarps) k_batch_uw_b(const BwItem* __re
             if (lane == (int)(q_tail % NQ)) { q_r = cur.r; q_nrows = cur.nrows; q_yoff = cur.yoff; }
             ++q_tail;
             nxt_idx = claim();
-            if (nxt_idx < nitems) nxt = items[nxt_idx];
+            if (nxt_idx < nitems) nxt = item_of(nxt_idx);
         }
         const uint32_t slot = issued % kBwStages;
         const int a0 = ti * kBwCols;
@@ -884,8 +914,8 @@ struct hdf_batch {
     DevBuf mvsets, mvitems_utv, mvitems_red, mvitems_uw, mvpart, mvW, counters;
     DevBuf derr;                                    // set by a matvec kernel that gave up a bounded wait
     DevBuf umaps;                                   // per set: TMA tensor map of U (32 x 32 boxes, FP32 batches)
-    DevBuf bwitems;                                 // items of the FP32 U W kernel (32-row tiles)
-    int mv_c = 0, n_utv = 0, n_red = 0, n_uw = 0;
+    DevBuf bwsets;                                  // sets of the FP32 U W kernel (items: 32-row tiles)
+    int mv_c = 0, n_utv = 0, n_red = 0, n_uw = 0, n_bw = 0;
     cudaGraphExec_t mv_exec = nullptr;
     const void* mv_V = nullptr;
     void* mv_Y = nullptr;
@@ -1225,6 +1255,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (sizeof(T) == 4 && offs[s].mtp > 0) {
             R.QC = reinterpret_cast<const float2*>(A + offs[s].qc);
             R.mtp = offs[s].mtp;
+            R.kopt = std::min(4, dev::radialF_df_kopt(fc.m[0] + fc.m[1], 256 / 32 - 1));   // 2 or 4
         }
         R.F = dF.as<T>() + foff[s]; R.ldF = tb.nF;
         dev::UWParams& P = bs[s].uw;
@@ -1346,12 +1377,12 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     HDF_CUDA(cudaEventCreate(&e1));
     struct EvG { cudaEvent_t a, b; ~EvG() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{e0, e1};
     for (int ph = 0; ph <= nclass; ++ph) {
-        // candidates: radial tiles per item {1, 2, 4}; U warps per CTA {8, 16, 32} within the
+        // candidates: radial tiles per item {1, 2, 4, 8}; U warps per CTA {8, 16, 32} within the
         // class's shared memory; CTAs per SM from 1 to the occupancy limit
         std::vector<int> as;
         int64_t work = 0;
         if (ph == 0) {
-            as = {1, 2, 4};
+            as = {1, 2, 4, 8};
             for (int s = 0; s < ns; ++s) work += geo[s].n;
         } else {
             const UClass& u = ucls[ph - 1];
@@ -1363,7 +1394,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         while ((int64_t(1) << (bucket + 1)) <= std::max<int64_t>(1, work / 1024)) ++bucket;
         char key[160];
         if (ph == 0)
-            std::snprintf(key, sizeof(key), "batch_radial_v1:sm%d:d%d:%s:smem%zu:work2^%d", nsm, d,
+            std::snprintf(key, sizeof(key), "batch_radial_v2:sm%d:d%d:%s:smem%zu:work2^%d", nsm, d,
                           sizeof(T) == 4 ? "fp32" : "fp64", smem_rf / 4096, bucket);
         else
             std::snprintf(key, sizeof(key), "batch_urows_v1:sm%d:d%d:%s:pw%zu:fixed%zu:work2^%d", nsm, d,
@@ -1460,7 +1491,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         int AB = (ct == 1) ? 256 : 128, RB = (ct == 1) ? 256 : 128;
         if (skinny) {                     // the streaming kernels' columns / rows per item
             AB = (ct <= 8) ? kPipeCols : SkinnyShape<16>::AB;
-            RB = 32;                      // k_batch_uw_b: one 32-row tile per item
+            RB = 32;                      // k_batch_uw_b: one 32-row tile per item (from the set table)
         }
         int64_t ptot = 0, wtot = 0;
         std::vector<int64_t> poff(ns), woff(ns);
@@ -1478,7 +1509,8 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             for (int q = 0; q < ms[s].nchunk; ++q)
                 for (int64_t bl = 0; bl < (r + AB - 1) / AB; ++bl) iu.push_back({s, q, bl});
             for (int64_t bl = 0; bl < (r + 255) / 256; ++bl) ir.push_back({s, 0, bl});
-            for (int64_t bl = 0; bl < (n + RB - 1) / RB; ++bl) iw.push_back({s, 0, bl});
+            if (!skinny)                  // the FP32 U W kernel locates its tiles from the set table
+                for (int64_t bl = 0; bl < (n + RB - 1) / RB; ++bl) iw.push_back({s, 0, bl});
         }
         HDF_CUDA(b->mvpart.alloc_on(sizeof(double) * std::max<int64_t>(1, ptot), st));
         HDF_CUDA(b->mvW.alloc_on(sizeof(T) * std::max<int64_t>(1, wtot), st));
@@ -1499,20 +1531,20 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
             }
             HDF_CUDA(b->umaps.alloc(sizeof(CUtensorMap) * ns));
             HDF_CUDA(cudaMemcpyAsync(b->umaps.p, maps.data(), sizeof(CUtensorMap) * ns, cudaMemcpyHostToDevice, st));
-            std::vector<BwItem> bw(iw.size());
-            for (size_t k = 0; k < iw.size(); ++k) {
-                const MvItem& m = iw[k];
-                const int64_t row0 = m.blk * 32;
-                bw[k].W = reinterpret_cast<const float*>(b->mvW.as<T>() + woff[m.set]);
-                bw[k].yoff = b->off[m.set] + row0;
-                bw[k].row0 = (int)row0;
-                bw[k].set = m.set;
-                bw[k].r = (int)ms[m.set].r;
-                bw[k].nrows = (int)std::min<int64_t>(32, ms[m.set].n - row0);
+            std::vector<BwSet> bw(ns);
+            int64_t tiles = 0;
+            for (int s = 0; s < ns; ++s) {
+                bw[s].W = reinterpret_cast<const float*>(b->mvW.as<T>() + woff[s]);
+                bw[s].off = b->off[s];
+                bw[s].tile0 = tiles;
+                bw[s].n = (int)ms[s].n;
+                bw[s].r = (int)ms[s].r;
+                if (ms[s].r > 0) tiles += (ms[s].n + 31) / 32;      // rank-0 sets: no items
             }
-            HDF_CUDA(b->bwitems.alloc(sizeof(BwItem) * std::max<size_t>(1, bw.size())));
-            if (!bw.empty())
-                HDF_CUDA(cudaMemcpyAsync(b->bwitems.p, bw.data(), sizeof(BwItem) * bw.size(), cudaMemcpyHostToDevice, st));
+            b->n_bw = (int)tiles;
+            HDF_CUDA(b->bwsets.alloc(sizeof(BwSet) * ns));
+            HDF_CUDA(cudaMemcpyAsync(b->bwsets.p, bw.data(), sizeof(BwSet) * ns, cudaMemcpyHostToDevice, st));
+            HDF_CUDA(cudaStreamSynchronize(st));      // the host table is released on return
         }
         HDF_CUDA(b->mvsets.alloc_on(sizeof(MvSet) * ns, st));
         HDF_CUDA(b->mvitems_utv.alloc_on(sizeof(MvItem) * std::max<size_t>(1, iu.size()), st));
@@ -1530,7 +1562,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         HDF_CUDA(cudaStreamSynchronize(st));
         b->n_utv = (int)iu.size();
         b->n_red = (int)ir.size();
-        b->n_uw = (int)iw.size();
+        b->n_uw = skinny ? b->n_bw : (int)iw.size();
         b->mv_c = c;
     }
     if (!b->mv_exec || b->mv_V != (const void*)V || b->mv_Y != (void*)Y || b->mv_ldv != ldv || b->mv_ldy != ldy) {
@@ -1579,7 +1611,7 @@ static hdf_status batch_matvec_t(hdf_batch* b, const T* V, int64_t ldv, int c, T
         if (b->n_red) k_batch_reduce<T><<<b->n_red, 256, 0, b->cap>>>(S, b->mvitems_red.as<MvItem>(), c);          \
         if (b->n_uw)                                                                                              \
             UW<<<nsm * std::max(occ_w, 1), 32 * kBwWarps, SW, b->cap>>>(                                          \
-                b->bwitems.as<BwItem>(), b->n_uw, cnt + 1, b->umaps.as<CUtensorMap>(),                            \
+                b->bwsets.as<BwSet>(), ns, b->n_uw, cnt + 1, b->umaps.as<CUtensorMap>(),                          \
                 reinterpret_cast<float*>(Y), ldy, c, b->derr.as<int>());                                          \
         break;
                 HDF_B_SK(1, k_batch_utv_p<1>, k_batch_uw_b<1>, utv_pipe_smem<1>(), bw_smem<1>())

@@ -269,6 +269,7 @@ struct RFParams {
     const double* Qm0; int nb0, m0;
     const double* Qm1; int nb1, m1;
     const float2* QC; int mtp;   // FP32 factors: [Qm0 | Qm1] as (hi, lo) float pairs, (L+1) x mtp
+    int kopt;                    // FP32 factors in the batched build: outputs per thread of the Q part
     int stage_wt;                // FP32 factors: copy Wt into shared memory
     const void* Wt; const uint8_t* colpar; int nF;
     void* F; int64_t ldF;
