@@ -290,84 +290,257 @@ __global__ void k_block_gemv(const double* __restrict__ inv, const int64_t* __re
     if (lane == 0) z[row] = s;
 }
 
-// In-place inverse of a symmetric positive definite matrix (row-major n x n, both triangles
-// read from the lower one) by a blocked right-looking Cholesky A = L L^T (64-column panels:
-// the panel's rows below the diagonal block and the trailing update A22 -= L21 L21^T, in
-// register blocks against the transposed panel, run on the worker pool when par), then L^-1
-// one column at a time (forward substitution, stored transposed so that every inner loop is a
-// contiguous dot product) and A^-1 = L^-T L^-1 in register blocks.  False if A is not positive
-// definite to working precision.
-bool spd_inverse(int64_t n, double* A, bool par) {
-    const int64_t NB = 64, RB = 16;
-    auto run = [&](int64_t cnt, const std::function<void(int64_t)>& fn) {
-        if (par && cnt > 1) parallel_for((int)cnt, [&](int t) { fn(t); });
-        else for (int64_t t = 0; t < cnt; ++t) fn(t);
-    };
-    auto dot = [](const double* a, const double* b, int64_t len) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int64_t q = 0;
-        for (; q + 4 <= len; q += 4) { s0 += a[q] * b[q]; s1 += a[q + 1] * b[q + 1]; s2 += a[q + 2] * b[q + 2]; s3 += a[q + 3] * b[q + 3]; }
-        for (; q < len; ++q) s0 += a[q] * b[q];
-        return (s0 + s1) + (s2 + s3);
-    };
-    bool ok = true;
-    std::vector<double> Pt;                                    // transposed panel, NB x (n - ke)
-    for (int64_t kb = 0; kb < n && ok; kb += NB) {
-        const int64_t ke = std::min(n, kb + NB);
-        for (int64_t k = kb; k < ke; ++k) {                    // diagonal block
-            double* Ak = A + k * n;
-            const double s = Ak[k] - dot(Ak + kb, Ak + kb, k - kb);
-            if (!(s > 0.0)) { ok = false; break; }
-            Ak[k] = std::sqrt(s);
-            for (int64_t i = k + 1; i < ke; ++i) {
-                double* Ai = A + i * n;
-                Ai[k] = (Ai[k] - dot(Ai + kb, Ak + kb, k - kb)) / Ak[k];
-            }
-        }
-        if (!ok || ke == n) break;
-        const int64_t nt = n - ke, nrb = (nt + RB - 1) / RB, w = ke - kb;
-        run(nrb, [&](int64_t b) {                                // panel rows below the block
-            for (int64_t i = ke + b * RB; i < std::min(n, ke + (b + 1) * RB); ++i) {
-                double* Ai = A + i * n;
-                for (int64_t k = kb; k < ke; ++k) {
-                    const double* Ak = A + k * n;
-                    Ai[k] = (Ai[k] - dot(Ai + kb, Ak + kb, k - kb)) / Ak[k];
-                }
-            }
-        });
-        Pt.assign((size_t)w * nt, 0.0);
-        for (int64_t i = 0; i < nt; ++i)
-            for (int64_t q = 0; q < w; ++q) Pt[(size_t)q * nt + i] = A[(ke + i) * n + kb + q];
-        run(nrb, [&](int64_t b) {                                // A22 -= L21 L21^T (lower blocks)
-            const int64_t i0 = ke + b * RB, i1 = std::min(n, i0 + RB);
-            gemm_minus(i1 - i0, i1 - ke, w, A + i0 * n + kb, n, Pt.data(), nt, A + i0 * n + ke, n);
-        });
+// --------------------------------------- block preconditioner: batched SPD inverse (FP64)
+// A_c = lambda I + K_{C_c C_c} of every cluster c (packed row-major n_c x n_c at ioff[c]) is
+// inverted on the device in 64 x 64 tiles, all clusters side by side (blockIdx.y = cluster):
+//   Cholesky A = L L^T, right-looking, per panel j: the diagonal tile is factored in shared
+//   memory and its inverse D_j = L_jj^-1 kept; L_ij = A_ij D_j^T for the tiles below; the
+//   trailing lower tiles A_ik -= L_ij L_kj^T;
+//   W = L^-1 by tile rows: W_ii = D_i, W_ij = -D_i sum_{j <= k < i} L_ik W_kj;
+//   A^-1 = W^T W, both triangles written.
+// A non-positive pivot sets *bad (the host reports HDF_ESINGULAR).
+constexpr int kST = 64;                 // tile edge
+constexpr int kSP = kST + 1;            // shared row stride (doubles)
+
+struct SpdArgs {
+    double* A;                          // packed blocks (overwritten by L in the lower tiles)
+    double* W;                          // packed blocks: L^-1 (lower tiles), then A^-1 is written to A
+    double* D;                          // per cluster: nb_c diagonal-tile inverses, 64 x 64 each
+    const int64_t* offs;                // cluster c: rows offs[c] .. offs[c + 1]
+    const int64_t* ioff;                // packed offsets of the blocks
+    const int64_t* doff;                // offsets of the diagonal-tile inverses
+    int* bad;
+};
+
+__device__ __forceinline__ int64_t spd_n(const SpdArgs& P, int c) { return P.offs[c + 1] - P.offs[c]; }
+
+// tile (bi, bj) of the n x n row-major M -> s (kST x kSP), zeros outside the matrix
+__device__ __forceinline__ void spd_load(const double* M, int64_t n, int bi, int bj, double* s) {
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) {
+        const int r = e / kST, q = e % kST;
+        const int64_t gr = (int64_t)bi * kST + r, gc = (int64_t)bj * kST + q;
+        s[r * kSP + q] = (gr < n && gc < n) ? M[gr * n + gc] : 0.0;
     }
-    if (!ok) return false;
-    // T = (L^-1)^T: row c of T is column c of L^-1 (entries c..n-1); Li = L^-1 row-major
-    std::vector<double> T((size_t)n * n, 0.0), Li((size_t)n * n, 0.0);
-    run((n + RB - 1) / RB, [&](int64_t b) {
-        for (int64_t c = b * RB; c < std::min(n, (b + 1) * RB); ++c) {
-            double* x = T.data() + c * n;
-            x[c] = 1.0 / A[c * n + c];
-            for (int64_t i = c + 1; i < n; ++i) x[i] = -dot(A + i * n + c, x + c, i - c) / A[i * n + i];
+}
+__device__ __forceinline__ void spd_store(double* M, int64_t n, int bi, int bj, const double* s, bool transpose) {
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) {
+        const int r = e / kST, q = e % kST;
+        const int64_t gr = (int64_t)bi * kST + r, gc = (int64_t)bj * kST + q;
+        if (gr < n && gc < n) {
+            if (transpose) M[gc * n + gr] = s[r * kSP + q];
+            else M[gr * n + gc] = s[r * kSP + q];
         }
-    });
-    for (int64_t c = 0; c < n; ++c)
-        for (int64_t i = c; i < n; ++i) Li[i * n + c] = T[c * n + i];
-    // A^-1 = T Li for the lower blocks: rows [i0, i1), columns [0, i1), sums over q >= i0 (T[i][q]
-    // is zero below q = i); the negated product is accumulated into a zeroed block
-    run((n + RB - 1) / RB, [&](int64_t b) {
-        const int64_t i0 = b * RB, i1 = std::min(n, i0 + RB);
-        for (int64_t i = i0; i < i1; ++i)
-            for (int64_t j = 0; j < i1; ++j) A[i * n + j] = 0.0;
-        gemm_minus(i1 - i0, i1, n - i0, T.data() + i0 * n + i0, n, Li.data() + i0 * n, n, A + i0 * n, n);
-        for (int64_t i = i0; i < i1; ++i)
-            for (int64_t j = 0; j < i1; ++j) A[i * n + j] = -A[i * n + j];
-    });
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = i + 1; j < n; ++j) A[i * n + j] = A[j * n + i];
-    return true;
+    }
+}
+// acc (4 x 4 per thread, 256 threads: rows 4 ty.., columns 4 tx..) += X Y^T or X Y (tiles in shared)
+template <bool YT>
+__device__ __forceinline__ void spd_mma(const double* X, const double* Y, double acc[4][4]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int m = 0; m < kST; ++m) {
+        double xv[4], yv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[i] = X[(4 * ty + i) * kSP + m];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yv[j] = YT ? Y[(4 * tx + j) * kSP + m] : Y[m * kSP + 4 * tx + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
+    }
+}
+
+// Panel j, step 1: factor the diagonal tile in shared memory, write L_jj to A, D_j = L_jj^-1.
+__global__ void __launch_bounds__(256) k_spd_potrf(SpdArgs P, int j) {
+    extern __shared__ double sh[];
+    const int c = blockIdx.y;
+    const int64_t n = spd_n(P, c);
+    if ((int64_t)j * kST >= n) return;
+    const int t = (int)min((int64_t)kST, n - (int64_t)j * kST);
+    double* A = P.A + P.ioff[c];
+    double* S = sh;                       // the tile
+    double* X = sh + kST * kSP;           // its inverse
+    spd_load(A, n, j, j, S);
+    __syncthreads();
+    for (int k = 0; k < t; ++k) {
+        if (threadIdx.x == 0) {
+            const double piv = S[k * kSP + k];
+            if (!(piv > 0.0)) { atomicExch(P.bad, 1); S[k * kSP + k] = 1.0; }
+            else S[k * kSP + k] = sqrt(piv);
+        }
+        __syncthreads();
+        const double dk = S[k * kSP + k];
+        for (int r = k + 1 + threadIdx.x; r < t; r += blockDim.x) S[r * kSP + k] /= dk;
+        __syncthreads();
+        // trailing lower triangle: S[r][q] -= S[r][k] S[q][k], k < q <= r < t
+        const int m = t - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = k + 1 + e / m, q = k + 1 + e % m;
+            if (q <= r) S[r * kSP + q] -= S[r * kSP + k] * S[q * kSP + k];
+        }
+        __syncthreads();
+    }
+    // zero the strict upper triangle and the padding, so that the tile is exactly L_jj
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) {
+        const int r = e / kST, q = e % kST;
+        if (q > r || r >= t) S[r * kSP + q] = (r == q && r >= t) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // X = L^-1, column q by thread q: X[r][q] = (delta_rq - sum_{q <= m < r} L[r][m] X[m][q]) / L[r][r]
+    if (threadIdx.x < kST) {
+        const int q = threadIdx.x;
+        for (int r = 0; r < kST; ++r) {
+            if (r < q) { X[r * kSP + q] = 0.0; continue; }
+            double v = (r == q) ? 1.0 : 0.0;
+            for (int m = q; m < r; ++m) v -= S[r * kSP + m] * X[m * kSP + q];
+            X[r * kSP + q] = v / S[r * kSP + r];
+        }
+    }
+    __syncthreads();
+    spd_store(A, n, j, j, S, false);
+    double* D = P.D + P.doff[c] + (int64_t)j * kST * kST;
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) D[e] = X[(e / kST) * kSP + e % kST];
+}
+
+// Panel j, step 2: L_ij = A_ij D_j^T for the tiles below the diagonal (blockIdx.x = i - j - 1).
+__global__ void __launch_bounds__(256) k_spd_trsm(SpdArgs P, int j) {
+    extern __shared__ double sh[];
+    const int c = blockIdx.y;
+    const int64_t n = spd_n(P, c);
+    const int i = j + 1 + blockIdx.x;
+    if ((int64_t)i * kST >= n) return;
+    double* A = P.A + P.ioff[c];
+    const double* D = P.D + P.doff[c] + (int64_t)j * kST * kST;
+    double* Xs = sh;
+    double* Ds = sh + kST * kSP;
+    spd_load(A, n, i, j, Xs);
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) Ds[(e / kST) * kSP + e % kST] = D[e];
+    __syncthreads();
+    double acc[4][4] = {};
+    spd_mma<true>(Xs, Ds, acc);
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) Xs[(4 * ty + a) * kSP + 4 * tx + b2] = acc[a][b2];
+    __syncthreads();
+    spd_store(A, n, i, j, Xs, false);
+}
+
+// Panel j, step 3: A_ik -= L_ij L_kj^T for j < k <= i (blockIdx.x enumerates the pairs).
+__global__ void __launch_bounds__(256) k_spd_update(SpdArgs P, int j) {
+    extern __shared__ double sh[];
+    const int c = blockIdx.y;
+    const int64_t n = spd_n(P, c);
+    // pair index -> (i, k) with 0 <= kk <= ii, i = j + 1 + ii, k = j + 1 + kk
+    const int e = blockIdx.x;
+    int ii = (int)((sqrt(8.0 * e + 1.0) - 1.0) / 2.0);
+    while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+    while (ii * (ii + 1) / 2 > e) --ii;
+    const int kk = e - ii * (ii + 1) / 2;
+    const int i = j + 1 + ii, k = j + 1 + kk;
+    if ((int64_t)i * kST >= n) return;
+    double* A = P.A + P.ioff[c];
+    double* Li = sh;
+    double* Lk = sh + kST * kSP;
+    double* Cs = sh + 2 * kST * kSP;
+    spd_load(A, n, i, j, Li);
+    spd_load(A, n, k, j, Lk);
+    spd_load(A, n, i, k, Cs);
+    __syncthreads();
+    double acc[4][4] = {};
+    spd_mma<true>(Li, Lk, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) Cs[(4 * ty + a) * kSP + 4 * tx + b2] -= acc[a][b2];
+    __syncthreads();
+    spd_store(A, n, i, k, Cs, false);
+}
+
+// W = L^-1, tile row i (blockIdx.x = j <= i): W_ii = D_i, W_ij = -D_i sum_{j <= k < i} L_ik W_kj.
+__global__ void __launch_bounds__(256) k_spd_winv(SpdArgs P, int i) {
+    extern __shared__ double sh[];
+    const int c = blockIdx.y;
+    const int64_t n = spd_n(P, c);
+    const int j = blockIdx.x;
+    if ((int64_t)i * kST >= n || j > i) return;
+    const double* A = P.A + P.ioff[c];
+    double* W = P.W + P.ioff[c];
+    const double* D = P.D + P.doff[c] + (int64_t)i * kST * kST;
+    double* X = sh;
+    double* Y = sh + kST * kSP;
+    double* Z = sh + 2 * kST * kSP;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (j == i) {
+        for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) Z[(e / kST) * kSP + e % kST] = D[e];
+        __syncthreads();
+        spd_store(W, n, i, i, Z, false);
+        return;
+    }
+    double acc[4][4] = {};
+    for (int k = j; k < i; ++k) {           // S = sum_k L_ik W_kj
+        spd_load(A, n, i, k, X);
+        spd_load(W, n, k, j, Y);
+        __syncthreads();
+        spd_mma<false>(X, Y, acc);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) Y[(4 * ty + a) * kSP + 4 * tx + b2] = acc[a][b2];
+    for (int e = threadIdx.x; e < kST * kST; e += blockDim.x) X[(e / kST) * kSP + e % kST] = D[e];
+    __syncthreads();
+    double out[4][4] = {};
+    spd_mma<false>(X, Y, out);              // D_i S
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) Z[(4 * ty + a) * kSP + 4 * tx + b2] = -out[a][b2];
+    __syncthreads();
+    spd_store(W, n, i, j, Z, false);
+}
+
+// A^-1 = W^T W: tile (i, j), j <= i (blockIdx.x enumerates the pairs) = sum_{k >= i} W_ki^T W_kj,
+// written to (i, j) and, transposed, to (j, i).
+__global__ void __launch_bounds__(256) k_spd_wtw(SpdArgs P) {
+    extern __shared__ double sh[];
+    const int c = blockIdx.y;
+    const int64_t n = spd_n(P, c);
+    const int nb = (int)((n + kST - 1) / kST);
+    const int e = blockIdx.x;
+    int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) / 2.0);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    const int j = e - i * (i + 1) / 2;
+    if (i >= nb) return;
+    const double* W = P.W + P.ioff[c];
+    double* A = P.A + P.ioff[c];
+    double* X = sh;
+    double* Y = sh + kST * kSP;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int k = i; k < nb; ++k) {
+        // X = W_ki^T (transposed on load), Y = W_kj
+        for (int q = threadIdx.x; q < kST * kST; q += blockDim.x) {
+            const int r = q / kST, s2 = q % kST;
+            const int64_t gr = (int64_t)k * kST + r, gc = (int64_t)i * kST + s2;
+            X[s2 * kSP + r] = (gr < n && gc < n) ? W[gr * n + gc] : 0.0;
+        }
+        spd_load(W, n, k, j, Y);
+        __syncthreads();
+        spd_mma<false>(X, Y, acc);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) X[(4 * ty + a) * kSP + 4 * tx + b2] = acc[a][b2];
+    __syncthreads();
+    spd_store(A, n, i, j, X, false);
+    if (i != j) spd_store(A, n, i, j, X, true);
 }
 
 }  // namespace
@@ -582,7 +755,7 @@ hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* label
     if (s != HDF_OK && s != HDF_ETOL_UNREACHABLE) return bail(s);
     const hdf_status build_status = s;
     K->t_build = wall_ms() - t0;
-    // block preconditioner: exact blocks on the device, inverted on the host (Cholesky, FP64)
+    // block preconditioner: exact blocks, inverted on the device (Cholesky, FP64)
     const double t1 = wall_ms();
     K->ioff.assign(K->nclus + 1, 0);
     for (int c = 0; c < K->nclus; ++c) {
@@ -603,25 +776,54 @@ hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* label
                                             K->nclus, kernel, lengthscale, lambda, K->inv.as<double>());
         KRR_CUDA(cudaGetLastError());
     }
-    std::vector<double> hinv(K->ioff.back());
-    KRR_CUDA(cudaMemcpyAsync(hinv.data(), K->inv.p, sizeof(double) * hinv.size(), cudaMemcpyDeviceToHost, st));
-    KRR_CUDA(cudaStreamSynchronize(st));
-    // clusters of 256 points or more one at a time with the work of each spread over the pool
-    // (largest first), the smaller ones side by side
-    std::vector<char> ok(K->nclus, 1);
-    std::vector<int> big, small;
-    for (int c = 0; c < K->nclus; ++c) (K->offs[c + 1] - K->offs[c] >= 256 ? big : small).push_back(c);
-    std::sort(big.begin(), big.end(), [&](int a, int b) {
-        return K->offs[a + 1] - K->offs[a] > K->offs[b + 1] - K->offs[b];
-    });
-    for (int c : big) ok[c] = spd_inverse(K->offs[c + 1] - K->offs[c], hinv.data() + K->ioff[c], true) ? 1 : 0;
-    parallel_for((int)small.size(), [&](int t) {
-        const int c = small[t];
-        ok[c] = spd_inverse(K->offs[c + 1] - K->offs[c], hinv.data() + K->ioff[c], false) ? 1 : 0;
-    });
-    for (int c = 0; c < K->nclus; ++c)
-        if (!ok[c]) return bail(fail(HDF_ESINGULAR, "hdf_krr_build: a block lambda I + K_cc is not positive definite"));
-    KRR_CUDA(cudaMemcpyAsync(K->inv.p, hinv.data(), sizeof(double) * hinv.size(), cudaMemcpyHostToDevice, st));
+    {
+        // invert every block on the device (batched tiles; see k_spd_potrf and its siblings)
+        int nbmax = 0;
+        std::vector<int64_t> doff(K->nclus + 1, 0);
+        for (int c = 0; c < K->nclus; ++c) {
+            const int nb = (int)((K->offs[c + 1] - K->offs[c] + kST - 1) / kST);
+            nbmax = std::max(nbmax, nb);
+            doff[c + 1] = doff[c] + (int64_t)nb * kST * kST;
+        }
+        DevBuf W, D, ddoff, bad;
+        KRR_CUDA(W.alloc_on(sizeof(double) * std::max<int64_t>(1, K->ioff.back()), st));
+        KRR_CUDA(D.alloc_on(sizeof(double) * std::max<int64_t>(1, doff.back()), st));
+        KRR_CUDA(ddoff.alloc_on(sizeof(int64_t) * doff.size(), st));
+        KRR_CUDA(bad.alloc_on(sizeof(int), st));
+        KRR_CUDA(cudaMemcpyAsync(ddoff.p, doff.data(), sizeof(int64_t) * doff.size(), cudaMemcpyHostToDevice, st));
+        KRR_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+        SpdArgs P{K->inv.as<double>(), W.as<double>(), D.as<double>(), K->doffs.as<int64_t>(),
+                  K->dioff.as<int64_t>(), ddoff.as<int64_t>(), bad.as<int>()};
+        const int tile = (int)(sizeof(double) * kST * kSP);
+        KRR_CUDA(cudaFuncSetAttribute(k_spd_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * tile));
+        KRR_CUDA(cudaFuncSetAttribute(k_spd_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * tile));
+        KRR_CUDA(cudaFuncSetAttribute(k_spd_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * tile));
+        KRR_CUDA(cudaFuncSetAttribute(k_spd_winv, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * tile));
+        KRR_CUDA(cudaFuncSetAttribute(k_spd_wtw, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * tile));
+        const unsigned ncl = (unsigned)K->nclus;
+        for (int j = 0; j < nbmax; ++j) {
+            HDF_COUNT_LAUNCH();
+            k_spd_potrf<<<dim3(1, ncl), 256, 2 * tile, st>>>(P, j);
+            const int nt = nbmax - j - 1;
+            if (nt > 0) {
+                HDF_COUNT_LAUNCH();
+                k_spd_trsm<<<dim3((unsigned)nt, ncl), 256, 2 * tile, st>>>(P, j);
+                HDF_COUNT_LAUNCH();
+                k_spd_update<<<dim3((unsigned)(nt * (nt + 1) / 2), ncl), 256, 3 * tile, st>>>(P, j);
+            }
+        }
+        for (int i = 0; i < nbmax; ++i) {
+            HDF_COUNT_LAUNCH();
+            k_spd_winv<<<dim3((unsigned)(i + 1), ncl), 256, 3 * tile, st>>>(P, i);
+        }
+        HDF_COUNT_LAUNCH();
+        k_spd_wtw<<<dim3((unsigned)(nbmax * (nbmax + 1) / 2), ncl), 256, 2 * tile, st>>>(P);
+        KRR_CUDA(cudaGetLastError());
+        int hbad = 0;
+        KRR_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KRR_CUDA(cudaStreamSynchronize(st));
+        if (hbad) return bail(fail(HDF_ESINGULAR, "hdf_krr_build: a block lambda I + K_cc is not positive definite"));
+    }
     // work space
     K->split = direct_split(n, n, &K->S);
     KRR_CUDA(K->part.alloc(sizeof(double) * (size_t)K->S * n));
@@ -631,7 +833,7 @@ hdf_status hdf_krr_build(const double* x_dev, int64_t n, int d, const int* label
         KRR_CUDA(K->vb.alloc(sizeof(float) * n));
         KRR_CUDA(K->yb.alloc(sizeof(float) * n));
     }
-    KRR_CUDA(cudaStreamSynchronize(st));       // hinv is a local buffer
+    KRR_CUDA(cudaStreamSynchronize(st));
     K->t_precond = wall_ms() - t1;
 #undef KRR_CUDA
     *out = K;
