@@ -803,9 +803,18 @@ bool make_tables(const FactorChoice& fc, int d, int L, int vw, DeviceTables& t, 
     const std::vector<int>& sk = fc.sk;
     t.L_used = 0;
     for (int k = 0; k <= L; ++k) if (sk[k] > 0) t.L_used = k;
+    // radial-factor columns: the blocks of even k first, then those of odd k, so that the
+    // consecutive columns a warp forms share one parity (one radial basis, one loop length);
+    // fbase[L + 1] holds the total nF
     t.fbase.assign(L + 2, 0);
-    for (int k = 0; k <= L; ++k) t.fbase[k + 1] = t.fbase[k] + sk[k];
-    t.nF = t.fbase[L + 1];
+    int fpos = 0;
+    for (int par = 0; par < 2; ++par)
+        for (int k = par; k <= L; k += 2) {
+            t.fbase[k] = fpos;
+            fpos += sk[k];
+        }
+    t.fbase[L + 1] = fpos;
+    t.nF = fpos;
     t.mmax = std::max(fc.m[0], fc.m[1]);
     t.Wt.assign((size_t)std::max(1, t.mmax) * std::max(1, t.nF), 0.0);
     t.colpar.assign(std::max(1, t.nF), 0);
