@@ -610,7 +610,7 @@ constexpr int64_t kMaxSolveRank = 32768;      // the solve's r x r core and its 
 // and for FP64 factors the CUDA-core tile kernels run.  One GroupWork serves every group of up
 // to cmax columns of one call; its buffers come from the stream-ordered pool.
 struct GroupWork {
-    bool tc = false;
+    bool tc = false;         // tensor cores: the partial sums in `part` are FP32
     int nchunk = 0, tch = 0;
     int64_t chunk = 0, tchunk = 0;
     DevBuf part;             // partial sums: nchunk (or tch) x cmax x r, FP64
@@ -648,12 +648,28 @@ static hdf_status group_utv(const hdf_factor* fin, int64_t r, const T* V, int64_
             *np = g.tch;
             return tc_utv(reinterpret_cast<const float*>(fin->U.p), fin->info.ldu, nin, r,
                           reinterpret_cast<const float*>(V), ldv, cg, g.tchunk, g.part.as<double>(),
-                          g.twork.as<float>(), fin->dev_err.as<int>(), st);
+                          g.twork.as<float>(), fin->dev_err.as<int>(), st, true);
         }
     }
     *np = g.nchunk;
     launch_utv<T>(ct_for(cg), fin->U.as<T>(), fin->info.ldu, nin, r, V, ldv, cg, g.nchunk, g.chunk,
                   g.part.as<double>(), st);
+    HDF_CUDA(cudaGetLastError());
+    return HDF_OK;
+}
+
+// W (or Wd) = S .* (sum of the np partial slices of g) for cg columns: FP32 partials from the
+// tensor cores, FP64 from the CUDA-core kernels.
+template <typename T>
+static hdf_status group_reduce(const GroupWork& g, int np, int64_t r, int cg, const T* S, T* W, double* Wd,
+                               cudaStream_t st) {
+    HDF_COUNT_LAUNCH();
+    if (g.tc)
+        dev::k_reduce_scale<T, float><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(
+            reinterpret_cast<const float*>(g.part.p), np, r, cg, S, W, Wd);
+    else
+        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg, S, W,
+                                                                               Wd);
     HDF_CUDA(cudaGetLastError());
     return HDF_OK;
 }
@@ -741,10 +757,7 @@ static hdf_status matvec_t(const hdf_factor* f, const hdf_factor* fin, const T* 
         int np = 0;
         if (hdf_status e = group_utv<T>(fin, r, V + j0 * ldv, ldv, cg, g, &np, st); e != HDF_OK) return e;
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[1], st));
-        HDF_COUNT_LAUNCH();
-        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg,
-                                                                               S_scale, W.as<T>(), nullptr);
-        HDF_CUDA(cudaGetLastError());
+        if (hdf_status e = group_reduce<T>(g, np, r, cg, S_scale, W.as<T>(), nullptr, st); e != HDF_OK) return e;
         if (rec && j0 == 0) HDF_CUDA(cudaEventRecord(fm->mv_ev[2], st));
         if (hdf_status e = group_uw<T>(f, r, W.as<T>(), cg, alpha, B ? B + j0 * ldb : nullptr, ldb, beta,
                                        Y + j0 * ldy, ldy, g, st);
@@ -776,10 +789,7 @@ hdf_status utv_reduce(const hdf_factor* f, const T* V, int64_t ldv, int c, const
     if (hdf_status e = group_setup(f, f, r, c, g, st); e != HDF_OK) return e;
     int np = 0;
     if (hdf_status e = group_utv<T>(f, r, V, ldv, c, g, &np, st); e != HDF_OK) return e;
-    HDF_COUNT_LAUNCH();
-    dev::k_reduce_scale<T><<<grid_for(r * c, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, c, S_scale,
-                                                                          W, Wd);
-    HDF_CUDA(cudaGetLastError());
+    if (hdf_status e = group_reduce<T>(g, np, r, c, S_scale, W, Wd, st); e != HDF_OK) return e;
     return HDF_OK;      // the partial sums return to the pool in stream order
 }
 template hdf_status utv_reduce<float>(const hdf_factor*, const float*, int64_t, int, const float*, float*, double*,
@@ -858,10 +868,9 @@ static hdf_status woodbury_apply(hdf_factor* f, double lambda, const T* Bin, int
         const int cg = std::min(kMaxGroup, ncols - j0);
         int np = 0;
         if (hdf_status e = group_utv<T>(f, r, Bin + j0 * ldb, ldb, cg, g, &np, st); e != HDF_OK) return e;
-        HDF_COUNT_LAUNCH();
-        dev::k_reduce_scale<T><<<grid_for(r * cg, 256, 1 << 30), 256, 0, st>>>(g.part.as<double>(), np, r, cg,
-                                                                               nullptr, nullptr, Wd.as<double>());
-        HDF_CUDA(cudaGetLastError());
+        if (hdf_status e = group_reduce<T>(g, np, r, cg, (const T*)nullptr, (T*)nullptr, Wd.as<double>(), st);
+            e != HDF_OK)
+            return e;
         if (hdf_status e = lu_solve_device(r, f->core_lu.as<double>(), f->core_perm.as<int>(), Wd.as<double>(),
                                            Zd.as<double>(), cg, st);
             e != HDF_OK)

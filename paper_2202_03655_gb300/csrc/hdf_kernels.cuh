@@ -1060,15 +1060,15 @@ __global__ void __launch_bounds__(256) k_utv_tile(const T* __restrict__ U, int64
 }
 
 // W[a * c + j] = scale_a * sum_chunk part[(chunk * c + j) * r + a]; scale = S[a] or 1.
-template <typename T>
-__global__ void k_reduce_scale(const double* __restrict__ part, int nchunk, int64_t r, int c,
+template <typename T, typename P = double>
+__global__ void k_reduce_scale(const P* __restrict__ part, int nchunk, int64_t r, int c,
                                const T* __restrict__ S, T* __restrict__ W, double* __restrict__ Wd) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= r * c) return;
     const int64_t a = idx / c;
     const int j = (int)(idx % c);
     double s = 0.0;
-    for (int b = 0; b < nchunk; ++b) s += part[((int64_t)b * c + j) * r + a];
+    for (int b = 0; b < nchunk; ++b) s += (double)part[((int64_t)b * c + j) * r + a];
     if (S) s *= (double)S[a];
     if (W) W[idx] = (T)s;
     if (Wd) Wd[idx] = s;

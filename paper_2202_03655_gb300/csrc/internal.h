@@ -32,8 +32,10 @@ size_t tc_work_floats(int64_t n, int64_t r, int c);
 // Rows per chunk (a multiple of 32) and the number of chunks of the tensor-core U^T V split;
 // tc_utv writes exactly that many partial slices.
 void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk);
+// part32: the partial sums are written as FP32 into the same buffer (each is an FP32 register
+// sum, so nothing is lost); else FP64.
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
-                  double* part, float* work, int* err, cudaStream_t st);
+                  double* part, float* work, int* err, cudaStream_t st, bool part32 = false);
 hdf_status tc_gram(const float* U, int64_t ldU, int64_t n, int64_t r, double* G, int* err, cudaStream_t st);
 // Matrix-free products on the tensor cores (tc_gemm.cu) over the device views of a matrix-free
 // factor: the U^T V tiles (m, j0, n0) and the U W phases (m, n0, K steps, B row) for c columns

@@ -591,6 +591,7 @@ struct UtvArgs {
     int mblocks;        // ceil(r / 128)
     int c;
     double* part;       // part[(chunk * c + j) * r + a]
+    float* part32;      // the same partial sums in FP32 (each is an FP32 register sum) when not null
     int* err;
     int* next;          // work-item counter, zero at launch
 };
@@ -701,9 +702,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t mb = item % p.mblocks, ch = item / p.mblocks;
             const int64_t a = mb * BM + 32 * q + lane;
             if (a < p.r) {
+                if (p.part32) {
 #pragma unroll
-                for (int j = 0; j < BN; ++j)
-                    if (j < p.c) p.part[((int64_t)ch * p.c + j) * p.r + a] = (double)acc[j];
+                    for (int j = 0; j < BN; ++j)
+                        if (j < p.c) p.part32[((int64_t)ch * p.c + j) * p.r + a] = acc[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < BN; ++j)
+                        if (j < p.c) p.part[((int64_t)ch * p.c + j) * p.r + a] = (double)acc[j];
+                }
             }
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
@@ -1190,7 +1197,7 @@ static hdf_status uw_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const
 
 template <int BN>
 static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c,
-                         int64_t chunk, double* part, float* work, int* err, cudaStream_t st) {
+                         int64_t chunk, double* part, float* work, int* err, cudaStream_t st, bool part32 = false) {
     const int64_t ldo = ((n + 3) / 4) * 4;
     float* vhi = work;
     float* vlo = work + (size_t)c * ldo;
@@ -1207,7 +1214,8 @@ static hdf_status utv_bn(const float* U, int64_t ldU, int64_t n, int64_t r, cons
     const int nch = (int)((n + chunk - 1) / chunk);
     int* next = reinterpret_cast<int*>(vlo + (size_t)c * ldo);      // one int past the split V
     HDF_CUDA(cudaMemsetAsync(next, 0, sizeof(int), st));
-    UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, err, next};
+    UtvArgs a{r, n, chunk, nch, (int)((r + BM - 1) / BM), c, part, part32 ? reinterpret_cast<float*>(part) : nullptr,
+              err, next};
     const size_t sm = Smem<BN>::bytes();
     HDF_CUDA(cudaFuncSetAttribute(k_tc_utv<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t nitems = (int64_t)a.mblocks * nch;
@@ -1252,11 +1260,11 @@ void tc_utv_split(int64_t n, int64_t r, int64_t* chunk, int* nchunk) {
 }
 
 hdf_status tc_utv(const float* U, int64_t ldU, int64_t n, int64_t r, const float* V, int64_t ldv, int c, int64_t chunk,
-                  double* part, float* work, int* err, cudaStream_t st) {
+                  double* part, float* work, int* err, cudaStream_t st, bool part32) {
     switch (tc_bn(c)) {
-        case 16: return tc::utv_bn<16>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
-        case 32: return tc::utv_bn<32>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
-        case 64: return tc::utv_bn<64>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st);
+        case 16: return tc::utv_bn<16>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st, part32);
+        case 32: return tc::utv_bn<32>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st, part32);
+        case 64: return tc::utv_bn<64>(U, ldU, n, r, V, ldv, c, chunk, part, work, err, st, part32);
     }
     return fail(HDF_EINVAL, "tc_utv: column count");
 }
