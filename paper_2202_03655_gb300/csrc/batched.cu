@@ -253,10 +253,10 @@ struct BuildSet {
     int pre;
 };
 
-// Shared memory of the double-float radial tiles (two buffers of basis pairs and rho, then Q) in
-// the batched build.
-inline size_t batch_df_tile_smem(int L, int m0, int m1) {
-    return 2 * dev::radialF_df_basis_bytes(L) + sizeof(float) * (size_t)(m0 + m1) * dev::kFTile;
+// Shared memory of the double-float radial phase of the batched build for `tiles` tiles per
+// item: one buffer of basis pairs and rho per tile, then Q.
+inline size_t batch_df_tile_smem(int L, int mt, int tiles) {
+    return (size_t)tiles * dev::radialF_df_basis_bytes(L) + sizeof(float) * (size_t)mt * dev::kFTile;
 }
 
 // A5 for every set in two persistent phases, each with its own register and shared-memory budget:
@@ -279,41 +279,37 @@ __global__ void __launch_bounds__(256, 2) k_batch_radial(const BuildSet* __restr
         const int2 w = items[it];
         const BuildSet& S = sets[w.x];
         const int64_t t0 = (int64_t)w.y * tiles_per_item * dev::kFTile;
-        for (int q = 0; q < tiles_per_item; ++q) {
-            const int64_t tq = t0 + (int64_t)q * dev::kFTile;
-            if (tq >= S.rf.n) break;
-            if constexpr (sizeof(T) == 4) {
-                // FP32 sets always carry the double-float tables (QC): warp 0 forms the basis of
-                // the item's next tile while warps 1.. form this tile's Q (S.rf.kopt outputs per
-                // thread), then all warps form F
-                const int LP1 = S.rf.L + 1;
-                const size_t bb = dev::radialF_df_basis_bytes(S.rf.L);
-                unsigned char* b0 = smem_raw + (q & 1) * bb;          // this tile's basis
-                unsigned char* b1 = smem_raw + ((q & 1) ^ 1) * bb;    // the next tile's
-                float2* Tc = reinterpret_cast<float2*>(b0);
-                float* rc = reinterpret_cast<float*>(Tc + dev::kFTile * LP1);
-                float2* Tn = reinterpret_cast<float2*>(b1);
-                float* rn = reinterpret_cast<float*>(Tn + dev::kFTile * LP1);
-                float* Qs = reinterpret_cast<float*>(smem_raw + 2 * bb);
-                if (q == 0) {
-                    if (threadIdx.x < dev::kFTile) dev::radialF_df_basis(S.rf, tq, threadIdx.x, Tc, rc);
-                    __syncthreads();
-                }
-                if (threadIdx.x < 32) {
-                    const int64_t tn = tq + dev::kFTile;
-                    if (q + 1 < tiles_per_item && tn < S.rf.n && threadIdx.x < dev::kFTile)
-                        dev::radialF_df_basis(S.rf, tn, threadIdx.x, Tn, rn);
-                } else {
-                    const int tid = threadIdx.x - 32, nth = blockDim.x - 32;
-                    if (S.rf.kopt == 2)
-                        dev::radialF_df_q<2>(S.rf, Tc, rc, S.rf.QC, Qs, tid, nth);
-                    else
-                        dev::radialF_df_q<4>(S.rf, Tc, rc, S.rf.QC, Qs, tid, nth);
-                }
+        if constexpr (sizeof(T) == 4) {
+            // FP32 sets always carry the double-float tables (QC).  First the basis values of all
+            // the item's tiles at once (thread = point), then per tile Q (S.rf.kopt outputs per
+            // thread) and F by all warps.
+            const int LP1 = S.rf.L + 1;
+            const size_t bb = dev::radialF_df_basis_bytes(S.rf.L);
+            const int ntile = (int)min((int64_t)tiles_per_item, (S.rf.n - t0 + dev::kFTile - 1) / dev::kFTile);
+            for (int pt = threadIdx.x; pt < ntile * dev::kFTile; pt += blockDim.x) {
+                const int q = pt / dev::kFTile;
+                float2* Tq = reinterpret_cast<float2*>(smem_raw + q * bb);
+                dev::radialF_df_basis(S.rf, t0 + (int64_t)q * dev::kFTile, pt % dev::kFTile, Tq,
+                                      reinterpret_cast<float*>(Tq + dev::kFTile * LP1));
+            }
+            __syncthreads();
+            float* Qs = reinterpret_cast<float*>(smem_raw + tiles_per_item * bb);
+            for (int q = 0; q < ntile; ++q) {
+                const float2* Tq = reinterpret_cast<const float2*>(smem_raw + q * bb);
+                const float* rq = reinterpret_cast<const float*>(Tq + dev::kFTile * LP1);
+                if (S.rf.kopt == 2)
+                    dev::radialF_df_q<2>(S.rf, Tq, rq, S.rf.QC, Qs, threadIdx.x, blockDim.x);
+                else
+                    dev::radialF_df_q<4>(S.rf, Tq, rq, S.rf.QC, Qs, threadIdx.x, blockDim.x);
                 __syncthreads();
-                dev::radialF_df_f(S.rf, tq, Qs, reinterpret_cast<const float*>(S.rf.Wt), threadIdx.x, blockDim.x);
+                dev::radialF_df_f(S.rf, t0 + (int64_t)q * dev::kFTile, Qs, reinterpret_cast<const float*>(S.rf.Wt),
+                                  threadIdx.x, blockDim.x);
                 __syncthreads();
-            } else {
+            }
+        } else {
+            for (int q = 0; q < tiles_per_item; ++q) {
+                const int64_t tq = t0 + (int64_t)q * dev::kFTile;
+                if (tq >= S.rf.n) break;
                 dev::radialF_tile<T>(S.rf, tq, smem_raw);
             }
         }
@@ -1238,7 +1234,8 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     // set descriptors, shared-memory needs per phase and per set
     const size_t budget = 200 * 1024;
     std::vector<BuildSet> bs(ns);
-    size_t smem_rf = 0;
+    size_t smem_rf = 0;                               // radial phase: one tile per item
+    int rf_L = 0, rf_mt = 0;                          // largest degree and basis count of the sets
     std::vector<size_t> pw_bytes(ns, 0), fixed_bytes(ns, 0);
     unsigned char* A = b->arena.as<unsigned char>();
     for (int s = 0; s < ns; ++s) {
@@ -1255,7 +1252,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         if (sizeof(T) == 4 && offs[s].mtp > 0) {
             R.QC = reinterpret_cast<const float2*>(A + offs[s].qc);
             R.mtp = offs[s].mtp;
-            R.kopt = std::min(4, dev::radialF_df_kopt(fc.m[0] + fc.m[1], 256 / 32 - 1));   // 2 or 4
+            R.kopt = std::min(4, dev::radialF_df_kopt(fc.m[0] + fc.m[1], 256 / 32));   // 2 or 4
         }
         R.F = dF.as<T>() + foff[s]; R.ldF = tb.nF;
         dev::UWParams& P = bs[s].uw;
@@ -1276,9 +1273,11 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         bs[s].pre = pre ? 1 : 0;
         P.per_warp = pre ? pw_pre : pw_fly;
         pw_bytes[s] = sizeof(T) * (size_t)P.per_warp;
-        const size_t need_rf = (sizeof(T) == 4) ? batch_df_tile_smem(geo[s].L, fc.m[0], fc.m[1])
+        const size_t need_rf = (sizeof(T) == 4) ? batch_df_tile_smem(geo[s].L, fc.m[0] + fc.m[1], 1)
                                                 : dev::radialF_smem(geo[s].L, fc.m[0], fc.m[1], sizeof(T));
         smem_rf = std::max(smem_rf, need_rf);
+        rf_L = std::max(rf_L, geo[s].L);
+        rf_mt = std::max(rf_mt, fc.m[0] + fc.m[1]);
         if (fixed_bytes[s] + 8 * pw_bytes[s] > budget || need_rf > budget)
             return fail(HDF_ETOOBIG, "hdf_build_batched: per-set tables exceed shared memory");
     }
@@ -1327,14 +1326,19 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     struct Shape { int a, per_sm; };                  // (tiles or warps, CTAs per SM)
     struct Plan { DevBuf items; int nitems = 0; int a = 0, per_sm = 1, pts = 0; size_t smem = 0; };
     std::vector<Plan> plans(1 + nclass);
-    HDF_CUDA(cudaFuncSetAttribute(k_batch_radial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rf));
+    // FP32 radial phase: shared memory for `a` tiles per item (a basis buffer per tile)
+    auto smem_rf_of = [&](int a) -> size_t {
+        return (sizeof(T) == 4) ? std::max(smem_rf, batch_df_tile_smem(rf_L, rf_mt, a)) : smem_rf;
+    };
+    HDF_CUDA(cudaFuncSetAttribute(k_batch_radial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::min(budget, smem_rf_of(8))));
     HDF_CUDA(cudaFuncSetAttribute(k_batch_urows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget));
     auto set_plan = [&](int ph, int a) -> hdf_status {
         Plan& P = plans[ph];
         std::vector<int2> it;
         if (ph == 0) {
             it = radial_items(a);
-            P.smem = smem_rf;
+            P.smem = smem_rf_of(a);
             P.pts = a;
         } else {
             const UClass& u = ucls[ph - 1];
@@ -1382,7 +1386,8 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         std::vector<int> as;
         int64_t work = 0;
         if (ph == 0) {
-            as = {1, 2, 4, 8};
+            for (int a : {1, 2, 4, 8})
+                if (smem_rf_of(a) <= budget) as.push_back(a);
             for (int s = 0; s < ns; ++s) work += geo[s].n;
         } else {
             const UClass& u = ucls[ph - 1];
@@ -1394,7 +1399,7 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
         while ((int64_t(1) << (bucket + 1)) <= std::max<int64_t>(1, work / 1024)) ++bucket;
         char key[160];
         if (ph == 0)
-            std::snprintf(key, sizeof(key), "batch_radial_v2:sm%d:d%d:%s:smem%zu:work2^%d", nsm, d,
+            std::snprintf(key, sizeof(key), "batch_radial_v3:sm%d:d%d:%s:smem%zu:work2^%d", nsm, d,
                           sizeof(T) == 4 ? "fp32" : "fp64", smem_rf / 4096, bucket);
         else
             std::snprintf(key, sizeof(key), "batch_urows_v1:sm%d:d%d:%s:pw%zu:fixed%zu:work2^%d", nsm, d,
