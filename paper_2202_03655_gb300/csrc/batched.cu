@@ -1011,8 +1011,16 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     parallel_for(ns, [&](int s) {
         plan_degree(b->kernel, ells[s], Rs[s], mu2[s], geo[s].n, tol, eta, p_max, d, false, dps[s], false);
     });
+    // per-set host work in order of decreasing degree (the cost grows like p^5), so that the
+    // largest sets do not start last on the worker pool
+    std::vector<int> by_cost(ns);
+    for (int s = 0; s < ns; ++s) by_cost[s] = s;
+    std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return dps[a].p > dps[b].p; });
     auto cores_all = [&]() {
-        parallel_for(ns, [&](int s) { radial_cores(dps[s].a.data(), dps[s].p, d, dps[s].cores, false); });
+        parallel_for(ns, [&](int t) {
+            const int s = by_cost[t];
+            radial_cores(dps[s].a.data(), dps[s].p, d, dps[s].cores, false);
+        });
     };
     for (int s = 0; s < ns; ++s) geo[s].L = dps[s].L;
     b->t_ms[1] = now_ms_b() - t0;
@@ -1106,7 +1114,8 @@ static hdf_status batch_build_t(hdf_batch* b, const double* x, const std::vector
     std::vector<DeviceTables> tbs(ns);
     std::vector<std::string> errs(ns);
     std::vector<char> ok(ns, 1);
-    parallel_for(ns, [&](int s) {
+    parallel_for(ns, [&](int t) {
+        const int s = by_cost[t];
         plan_factor(grams[s], geo[s].L, d, dps[s].cores, dps[s].drop_budget, false, fcs[s]);
         ok[s] = make_tables(fcs[s], d, geo[s].L, vw, tbs[s], errs[s]) ? 1 : 0;
     });
