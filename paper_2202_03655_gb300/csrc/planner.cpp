@@ -369,31 +369,36 @@ void radial_cores(const double* a, int p, int d, std::vector<std::vector<double>
             u[j] = std::cos(kPi * (j + 0.5) / nb);
             rho[j] = std::sqrt((u[j] + 1.0) / 8.0);
         }
-        std::vector<double> Vv(nb * nb), rpow(nb), uqv(Nq), b1v(Nq), b2v(Nq);
+        std::vector<double> Vv(nb * nb), rpow(nb);
+        for (int i = 0; i < nb; ++i) rpow[i] = std::pow(rho[i], (double)(k - (k & 1)));   // (ab)^k' = a^k' b^k'
+        // Clenshaw at the Nq nodes of every pair (i, j <= i) of row i side by side: one long loop
+        // of independent recurrences (element e = j Nq + q), then the per-pair quadrature sums
+        std::vector<double> uqv((size_t)nb * Nq), b1v((size_t)nb * Nq), b2v((size_t)nb * Nq);
         double* uq = uqv.data();
         double* b1 = b1v.data();
         double* b2 = b2v.data();
-        for (int i = 0; i < nb; ++i) rpow[i] = std::pow(rho[i], (double)(k - (k & 1)));   // (ab)^k' = a^k' b^k'
         for (int i = 0; i < nb; ++i) {
+            const int ne = (i + 1) * Nq;
             for (int j = 0; j <= i; ++j) {
                 const double ab = rho[i] * rho[j];
                 const double s0 = rho[i] * rho[i] + rho[j] * rho[j];
-                // Clenshaw at all Nq nodes together (independent recurrences side by side)
-                for (int q = 0; q < Nq; ++q) {
-                    uq[q] = 2.0 * (s0 - 2.0 * ab * tq[q]) - 1.0;
-                    b1[q] = 0.0;
-                    b2[q] = 0.0;
+                for (int q = 0; q < Nq; ++q) uq[j * Nq + q] = 2.0 * (s0 - 2.0 * ab * tq[q]) - 1.0;
+            }
+            for (int e = 0; e < ne; ++e) { b1[e] = 0.0; b2[e] = 0.0; }
+            for (int m = (int)Fk.size() - 1; m >= 1; --m) {
+                const double cm = Fk[m];
+                for (int e = 0; e < ne; ++e) {
+                    const double b0 = 2.0 * uq[e] * b1[e] - b2[e] + cm;
+                    b2[e] = b1[e];
+                    b1[e] = b0;
                 }
-                for (int m = (int)Fk.size() - 1; m >= 1; --m) {
-                    const double cm = Fk[m];
-                    for (int q = 0; q < Nq; ++q) {
-                        const double b0 = 2.0 * uq[q] * b1[q] - b2[q] + cm;
-                        b2[q] = b1[q];
-                        b1[q] = b0;
-                    }
-                }
+            }
+            for (int j = 0; j <= i; ++j) {
                 double integ = 0.0;
-                for (int q = 0; q < Nq; ++q) integ += wq[q] * (uq[q] * b1[q] - b2[q] + Fk[0]);
+                for (int q = 0; q < Nq; ++q) {
+                    const int e = j * Nq + q;
+                    integ += wq[q] * (uq[e] * b1[e] - b2[e] + Fk[0]);
+                }
                 const double v = pref * rpow[i] * rpow[j] * integ;
                 Vv[i * nb + j] = Vv[j * nb + i] = v;
             }
