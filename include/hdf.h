@@ -350,6 +350,15 @@ hdf_status hdf_device_errors(const hdf_factor* f, int* flag);
  * later launch on the current device until changed; synchronous. */
 hdf_status hdf_set_wait_limit(long long cycles, long long* previous);
 
+/* Self-check of the operand rounding of the tensor-core products (3xTF32, FP32 bulk): each FP32
+ * operand x is split into hi = x rounded to TF32 (10 mantissa bits, nearest, ties away from
+ * zero) and lo = x - hi; the library forms hi with integer operations on the bit pattern.  Runs
+ * one kernel over all 2^32 bit patterns and compares that rounding with the device's own
+ * conversion instruction on every finite value; mismatches[0] receives the count below 2^127 in
+ * magnitude, mismatches[1] the count in the top binade (where rounding up overflows).  Both
+ * are 0 on a correct build.  Synchronous; needs a device. */
+hdf_status hdf_check_tf32_rounding(unsigned long long* mismatches);
+
 /* Host-side fault injection: the device allocation `after` allocations from now (0 = the next
  * one) made by the library reports out-of-memory without allocating, once; a negative value
  * cancels a pending injection.  The call that meets it returns HDF_ENOMEM with its output

@@ -205,6 +205,11 @@ hdf_status hdf_set_wait_limit(long long cycles, long long* previous) {
     return hdf::set_wait_limit(cycles, previous);
 }
 
+hdf_status hdf_check_tf32_rounding(unsigned long long* mismatches) {
+    if (!mismatches) return fail(HDF_EINVAL, "hdf_check_tf32_rounding: null argument");
+    return hdf::tf32_check(mismatches);
+}
+
 void hdf_debug_fail_alloc(long long after) {
     hdf::g_alloc_fail_at.store(after >= 0 ? after : -1);
 }

@@ -57,6 +57,9 @@ hdf_status tc_mf_uw(const MfTcView& v, const int4* phases, int nphase, int kpad,
                     int64_t ldy, int* err, cudaStream_t st);
 // Work-wait limit (clock cycles) of the tensor-core kernels on the current device.
 hdf_status set_wait_limit(long long cycles, long long* previous);
+// Mismatches of the tensor-core operand rounding (tf32_hi) against cvt.rna.tf32.f32 over all
+// finite FP32 values: bad2[0] below 2^127 in magnitude, bad2[1] in the top binade.
+hdf_status tf32_check(unsigned long long* bad2);
 // HDF_ETIMEOUT (and the flag cleared) if a kernel on f gave up a bounded wait since the last
 // check; synchronises the device.
 hdf_status take_device_error(const hdf_factor* f);

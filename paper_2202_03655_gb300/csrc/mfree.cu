@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
             zr[t] = v;
         }
         T* ar = reinterpret_cast<T*>(P.A0F) + i * (int64_t)P.ldA;
-        for (int q = lane; q < P.ldA; q += 32) ar[q] = (q < P.nA) ? tbl[a0off[q]] * Fs[afcol[q]] : (T)0;
+        for (int q = lane; q < P.ldA; q += 32) {
+            const int32_t o = q < P.nA ? a0off[q] : -1;      // -1: a padding column
+            ar[q] = o >= 0 ? tbl[o] * Fs[afcol[q]] : (T)0;
+        }
         __syncwarp();
     }
 }

@@ -1001,6 +1001,14 @@ bool make_free_tables(const FactorChoice& fc, int d, int L, const DeviceTables& 
             }
         }
         ft.acnt[m] = (int)ft.a0off.size() - ft.aoff[m];
+        // every block starts on a 16-byte boundary of an A0F row, so the (up to four) columns
+        // one product tile takes from a point are one aligned vector load; padding columns are
+        // zero (a0off = -1) and belong to no (k, s)
+        while (ft.a0off.size() % 4 != 0) {
+            ft.a0off.push_back(-1);
+            ft.afcol.push_back(0);
+            ft.wcol.push_back(-1);
+        }
     }
     ft.aoff[Lu + 1] = (int)ft.a0off.size();
     ft.nA = ft.aoff[Lu + 1];

@@ -156,9 +156,10 @@ struct FreeTables {
     int nZ = 0, ldZ = 0;                     // Z columns (blocks padded to 8) and row stride
     int nA = 0, ldA = 0;                     // A0F columns and row stride (a multiple of 4)
     std::vector<int> zoff, zcnt;             // per m <= L_used: first Z column, |H_m^(d-1)|
-    std::vector<int> aoff, acnt;             // per m: first A0F column, number of (k, s) with k >= m
+    std::vector<int> aoff, acnt;             // per m: first A0F column (a multiple of 4), number of (k, s)
+                                             // with k >= m (the block is padded to a multiple of 4)
     std::vector<int16_t> zchain;             // nZ x chain_stride(d): level-1..d-3 offsets, trig index
-    std::vector<int32_t> a0off;              // nA: level-0 table offset of P_0(m, k - m)
+    std::vector<int32_t> a0off;              // nA: level-0 table offset of P_0(m, k - m); -1: padding (zero)
     std::vector<int32_t> afcol;              // nA: F column fbase[k] + s
     std::vector<int64_t> wcol;               // nA: padded U column of (k, s, h = first tail of m)
 };

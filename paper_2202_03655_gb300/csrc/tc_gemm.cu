@@ -196,16 +196,34 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// The TF32 value nearest to x, ties away from zero, on the integer pipe: adding half a unit of
+// the 13 dropped mantissa bits to the bit pattern and clearing them rounds the magnitude to
+// nearest with ties away from zero (a carry into the exponent is the correct rounding up).  Equal
+// to the conversion instruction cvt.rna.tf32.f32 for every finite x (hdf_check_tf32_rounding
+// compares the two over all 2^32 bit patterns), at two integer operations instead of one
+// conversion, which the operand converters and generators issue once per element.
 __device__ __forceinline__ float tf32_hi(float x) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    return __uint_as_float(h);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 __device__ __forceinline__ void split_tf32(float x, uint32_t& h, uint32_t& l) {
     const float hf = tf32_hi(x);
     h = __float_as_uint(hf);
     l = __float_as_uint(x - hf);
 }
+
+// Asynchronous global -> shared copies (per thread; bytes beyond src_bytes are zero-filled), one
+// commit group per pipeline step, and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory carve-up common to both kernels: S_U raw U tiles (32 KB, 1024-aligned), SB
 // stacked B tiles (per 32-K half: BN hi rows then BN lo rows of 128 bytes, K-major SW128),
@@ -723,7 +741,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // by TMA exactly like the U tiles of k_tc_utv / k_tc_uw; only the small second operand changes.
 //   k_tc_mf_utv: W[(k,s,m,j), c] = sum_i Z[i, zoff_m + j] (A0F[i, aoff_m + q] V[i, c]).
 //     M = 128 rows j of the tails of degree m, N = BN columns n = (q, c), K = points.  The B
-//     tiles A0F (.) V are formed in shared memory by four generator warps (10..13), in the
+//     tiles A0F (.) V are formed in shared memory by two generator warps (10, 11), in the
 //     K-major 128-byte-swizzle layout the TMA would write, TF32 hi / lo stacked.
 //   k_tc_mf_uw: Y[i, c] = sum over phases (m, n0) of sum_q A0F[i, aoff_m + q] Q[i, (q, c)],
 //     Q = Z[:, zoff_m + j] W_m[j, (q, c)]: M = 128 points, N = BN columns, K = the tails of m.
@@ -752,6 +770,9 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
     using SM = Smem<BN>;
     static_assert(BN % CP == 0, "column groups must not straddle a tile");
     constexpr int SB = SM::SB;
+    // with CP = 16 the last U stage holds the generators' staging ring and Z takes the others
+    constexpr bool STG = CP == 16;
+    constexpr int SU = STG ? S_U - 1 : S_U;
     extern __shared__ unsigned char raw_[];
     SM sm(raw_);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -779,79 +800,208 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 int64_t nxt = nitems;
                 for (int kt = 0; kt < nk; ++kt, ++it) {
                     if (kt == claim_at) nxt = (int64_t)gridDim.x + atomicAdd(p.next, 1);
-                    const uint32_t s = it % S_U;
-                    if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
+                    const uint32_t s = it % SU;
+                    if (!mbar_wait(&sm.uempty[s], ((it / SU) & 1) ^ 1)) { ok = false; break; }
                     mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
                     tma_load_2d(sm.U + s * SM::UBYTES, &mZ, zx, (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
                 }
                 item = nxt;
             }
-            if (!producer_drain(sm.ufull, S_U, it)) ok = false;
+            if (!producer_drain(sm.ufull, SU, it)) ok = false;
             if (!ok) atomicExch(p.err, 1);
         }
     } else if (warp >= 10) {
-        // B generators: thread t (t < 64) = point kk of the step; per step it loads the point's
-        // BN / CP values of A0F and its CP values of V once and forms the BN products
-        static_assert(NGEN * 32 == BK, "one generator thread per point of a step");
-        const int kk = (warp - 10) * 32 + lane;
-        const int h = kk >> 5, jc = (kk & 31) >> 2, e = kk & 3;
-        constexpr int NQ = BN / CP;
-        uint32_t it = 0;
-        for (uint32_t k = 0; ok; ++k) {
-            const int64_t item = take_item<BN>(sm, k, true);
-            if (item < 0) { ok = false; break; }
-            if (item >= nitems) break;
-            const int4 tl = p.tiles[item % p.ntiles];
-            const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
-            const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
-            const int nk = ksteps(item);
-            // the point's values for step kt; with CP <= 32 the next step's are loaded while this
-            // step's products are formed (the loads' latency is the generators' main stall)
-            constexpr bool PF = CP <= 32;
-            float av[NQ], vv[CP], an[NQ], vn[CP];
-            auto load = [&](int kt2, float* a_, float* v_) {
-                const int64_t i = i0 + (int64_t)kt2 * BK + kk;
-                const bool pv = kt2 < nk && i < i1;
+        // B generators: warp 10 forms points 0..31 of a step, warp 11 points 32..63 (the two
+        // 32-K halves of the stage).  A thread owns four consecutive points 4 pg .. 4 pg + 3 (one
+        // 16-byte chunk of a K-major row; pg = 8 (warp - 10) + lane mod 8) and the 16 rows
+        // n = g CP + rs CP / 4 + u of the stage (rs = lane / 8, g < BN / CP, u < CP / 4).  Per step
+        // it takes the BN / CP values of A0F of each point (one aligned 16-byte piece: A0F blocks
+        // start on 16-byte boundaries and q0 is a multiple of BN / CP) and four values of V per
+        // column, and writes each row's hi and lo chunk with one 16-byte store.  With CP = 16 the
+        // values come through a cp.async ring DS - 1 steps ahead, otherwise as register loads one
+        // step ahead.
+        static_assert(NGEN * 32 == BK && BN == 64, "two generator warps, 8 chunks x 4 row sets each");
+        constexpr int NQ = BN / CP, NU = CP / 4;
+        const int pg = (warp - 10) * 8 + (lane & 7), rs = lane >> 3;
+        const int h = warp - 10, jc = lane & 7;
+        const bool vec = ((reinterpret_cast<uintptr_t>(p.V) | (uintptr_t)p.ldv * 4u) & 15u) == 0;
+        if constexpr (STG) {
+            // values of DS steps staged by cp.async, DS - 1 steps ahead (A0F rows come mostly from
+            // DRAM, far beyond one step's time): slot = [8 chunks][64 threads][16 bytes], chunk e < 4
+            // the A0F values q0 .. q0 + 3 of point 4 pg + e, chunk 4 + u the four points of V column
+            // 4 rs + u.  A thread reads back only what it copied, so its own wait_group suffices.
+            constexpr int DS = 4;
+            static_assert(NQ == 4 && NU == 4 && DS * 8 * 64 * 16 <= SM::UBYTES, "the ring fits one U stage");
+            float* stg = reinterpret_cast<float*>(sm.U + (S_U - 1) * SM::UBYTES);
+            const int t = (warp - 10) * 32 + lane;
+            uint32_t it = 0;
+            for (uint32_t k = 0; ok; ++k) {
+                const int64_t item = take_item<BN>(sm, k, true);
+                if (item < 0) { ok = false; break; }
+                if (item >= nitems) break;
+                const int4 tl = p.tiles[item % p.ntiles];
+                const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
+                const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
+                const int nk = ksteps(item);
+                const uint32_t abytes = 4u * (uint32_t)max(0, min(NQ, nq - q0));
+                // the copies of step kt2 (zero-filled outside the item; an empty group past its end)
+                auto issue = [&](int kt2) {
+                    if (kt2 < nk) {
+                        float* slot = stg + (kt2 % DS) * (8 * 64 * 4);
+                        const int64_t i4 = i0 + (int64_t)kt2 * BK + 4 * pg;
 #pragma unroll
-                for (int g = 0; g < NQ; ++g) a_[g] = (pv && q0 + g < nq) ? __ldg(p.A0F + i * p.ldA + ao + q0 + g) : 0.f;
+                        for (int e = 0; e < 4; ++e) {
+                            const bool pe = i4 + e < i1;
+                            const float* src = p.A0F + (pe ? i4 + e : i0) * p.ldA + ao + q0;
+                            cp_async16(slot + (e * 64 + t) * 4, src, pe ? abytes : 0u);
+                        }
+                        const int cnt = (int)max((int64_t)0, min((int64_t)4, i1 - i4));
 #pragma unroll
-                for (int cc = 0; cc < CP; ++cc) v_[cc] = (pv && cc < p.c) ? __ldg(p.V + i + (int64_t)cc * p.ldv) : 0.f;
-            };
-            if (PF) load(0, av, vv);
-            for (int kt = 0; kt < nk; ++kt, ++it) {
-                const uint32_t sb = it % SB;
-                if (PF) {
-                    load(kt + 1, an, vn);
-                } else {
-                    load(kt, av, vv);
-                }
-                bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
-                free_ = __all_sync(0xffffffffu, free_);
-                if (!free_) { ok = false; break; }
-                unsigned char* col = sm.B + sb * SM::BBYTES + h * SM::BHALF + e * 4;
+                        for (int u = 0; u < NU; ++u) {
+                            const int cc = rs * NU + u;
+                            const int nv = cc < p.c ? cnt : 0;
+                            float* dst = slot + ((4 + u) * 64 + t) * 4;
+                            const float* vp = nv > 0 ? p.V + i4 + (int64_t)cc * p.ldv : p.V;
+                            if (vec) {
+                                cp_async16(dst, vp, 4u * (uint32_t)nv);
+                            } else {
 #pragma unroll
-                for (int g = 0; g < NQ; ++g)
-#pragma unroll
-                    for (int cc = 0; cc < CP; ++cc) {
-                        const int nrow = g * CP + cc;
-                        uint32_t hi, lo;
-                        split_tf32(av[g] * vv[cc], hi, lo);
-                        const uint32_t off = (uint32_t)nrow * 128u + ((uint32_t)(jc ^ (nrow & 7)) << 4);
-                        *reinterpret_cast<uint32_t*>(col + off) = hi;
-                        *reinterpret_cast<uint32_t*>(col + BN * 128 + off) = lo;
+                                for (int e = 0; e < 4; ++e) cp_async4(dst + e, e < nv ? vp + e : p.V, e < nv ? 4u : 0u);
+                            }
+                        }
                     }
-                // the tensor core reads the stage through the async proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.bfull[sb]);
-                if (PF) {
+                    cp_commit();
+                };
 #pragma unroll
-                    for (int g = 0; g < NQ; ++g) av[g] = an[g];
+                for (int kt2 = 0; kt2 < DS - 1; ++kt2) issue(kt2);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const uint32_t sb = it % SB;
+                    issue(kt + DS - 1);
+                    cp_wait<DS - 1>();
+                    const float* slot = stg + (kt % DS) * (8 * 64 * 4);
+                    float av[NQ][4], vv[NU][4];
 #pragma unroll
-                    for (int cc = 0; cc < CP; ++cc) vv[cc] = vn[cc];
+                    for (int e = 0; e < 4; ++e) {
+                        const float4 w = *reinterpret_cast<const float4*>(slot + (e * 64 + t) * 4);
+                        av[0][e] = w.x; av[1][e] = w.y; av[2][e] = w.z; av[3][e] = w.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < NU; ++u) {
+                        const float4 w = *reinterpret_cast<const float4*>(slot + ((4 + u) * 64 + t) * 4);
+                        vv[u][0] = w.x; vv[u][1] = w.y; vv[u][2] = w.z; vv[u][3] = w.w;
+                    }
+                    bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
+                    free_ = __all_sync(0xffffffffu, free_);
+                    if (!free_) { ok = false; break; }
+                    unsigned char* stage = sm.B + sb * SM::BBYTES + h * SM::BHALF;
+#pragma unroll
+                    for (int g = 0; g < NQ; ++g)
+#pragma unroll
+                        for (int u = 0; u < NU; ++u) {
+                            const int nrow = g * CP + rs * NU + u;
+                            uint32_t hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) split_tf32(av[g][e] * vv[u][e], hi[e], lo[e]);
+                            const uint32_t off = (uint32_t)nrow * 128u + ((uint32_t)(jc ^ (nrow & 7)) << 4);
+                            *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<uint4*>(stage + BN * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                    // the tensor core reads the stage through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.bfull[sb]);
                 }
+                cp_wait<0>();      // no copy of this thread is in flight past its item
+                if (!ok) break;
             }
-            if (!ok) break;
+        } else {
+            uint32_t it = 0;
+            for (uint32_t k = 0; ok; ++k) {
+                const int64_t item = take_item<BN>(sm, k, true);
+                if (item < 0) { ok = false; break; }
+                if (item >= nitems) break;
+                const int4 tl = p.tiles[item % p.ntiles];
+                const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
+                const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
+                const int nk = ksteps(item);
+                // the thread's values for step kt; with CP <= 32 the next step's are loaded while this
+                // step's products are formed
+                constexpr bool PF = CP <= 32;
+                float av[NQ][4], vv[NU][4], an[NQ][4], vn[NU][4];
+                auto load = [&](int kt2, float (&a_)[NQ][4], float (&v_)[NU][4]) {
+                    const int64_t i4 = i0 + (int64_t)kt2 * BK + 4 * pg;
+                    const bool on = kt2 < nk;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const bool pe = on && i4 + e < i1;
+                        const float* ap = p.A0F + (i4 + e) * p.ldA + ao + q0;
+                        float w[NQ];
+                        if constexpr (NQ == 4) {
+                            const float4 t = pe ? __ldg(reinterpret_cast<const float4*>(ap)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+                        } else if constexpr (NQ == 2) {
+                            const float2 t = pe ? __ldg(reinterpret_cast<const float2*>(ap)) : make_float2(0.f, 0.f);
+                            w[0] = t.x; w[1] = t.y;
+                        } else {
+                            w[0] = pe ? __ldg(ap) : 0.f;
+                        }
+#pragma unroll
+                        for (int g = 0; g < NQ; ++g) a_[g][e] = q0 + g < nq ? w[g] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < NU; ++u) {
+                        const int cc = rs * NU + u;
+                        const float* vp = p.V + i4 + (int64_t)cc * p.ldv;
+                        if (on && cc < p.c && vec && i4 + 3 < i1) {
+                            const float4 w = __ldg(reinterpret_cast<const float4*>(vp));
+                            v_[u][0] = w.x; v_[u][1] = w.y; v_[u][2] = w.z; v_[u][3] = w.w;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) v_[u][e] = (on && cc < p.c && i4 + e < i1) ? __ldg(vp + e) : 0.f;
+                        }
+                    }
+                };
+                if (PF) load(0, av, vv);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const uint32_t sb = it % SB;
+                    if (PF) {
+                        load(kt + 1, an, vn);
+                    } else {
+                        load(kt, av, vv);
+                    }
+                    bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
+                    free_ = __all_sync(0xffffffffu, free_);
+                    if (!free_) { ok = false; break; }
+                    unsigned char* stage = sm.B + sb * SM::BBYTES + h * SM::BHALF;
+#pragma unroll
+                    for (int g = 0; g < NQ; ++g)
+#pragma unroll
+                        for (int u = 0; u < NU; ++u) {
+                            const int nrow = g * CP + rs * NU + u;
+                            uint32_t hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) split_tf32(av[g][e] * vv[u][e], hi[e], lo[e]);
+                            const uint32_t off = (uint32_t)nrow * 128u + ((uint32_t)(jc ^ (nrow & 7)) << 4);
+                            *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<uint4*>(stage + BN * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                    // the tensor core reads the stage through the async proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.bfull[sb]);
+                    if (PF) {
+#pragma unroll
+                        for (int g = 0; g < NQ; ++g)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) av[g][e] = an[g][e];
+#pragma unroll
+                        for (int u = 0; u < NU; ++u)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) vv[u][e] = vn[u][e];
+                    }
+                }
+                if (!ok) break;
+            }
         }
         if (!ok && lane == 0) atomicExch(p.err, 1);
     } else if (warp == 1) {
@@ -874,12 +1024,15 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
             if (item >= nitems) break;
             const int nk = ksteps(item);
             for (int kt = 0; kt < nk; ++kt, ++it) {
-                if (!convert_wait<BN>(sm, it)) { ok = false; break; }
-                const float* R = reinterpret_cast<const float*>(sm.U + (it % S_U) * SM::UBYTES) + mrow;
+                if (!mbar_wait(&sm.ufull[it % SU], (it / SU) & 1)) { ok = false; break; }
+                if (it >= (uint32_t)NA && !wait_done<BN>(sm, it - NA)) { ok = false; break; }
+                tc_fence_after();
+                const float* R = reinterpret_cast<const float*>(sm.U + (it % SU) * SM::UBYTES) + mrow;
                 float x[64];
 #pragma unroll
                 for (int k2 = 0; k2 < BK; ++k2) x[k2] = R[k2 * BM];
-                convert_release<BN>(sm, it, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.uempty[it % SU]);
                 convert_publish<BN>(sm, tmem, it, q, lane, x);
             }
         }
@@ -1301,6 +1454,40 @@ hdf_status set_wait_limit(long long cycles, long long* previous) {
     const long long v = cycles > 0 ? cycles : tc::kDefaultWaitCycles;
     HDF_CUDA(cudaMemcpyToSymbol(tc::d_wait_cycles, &v, sizeof(v)));
     if (previous) *previous = prev;
+    return HDF_OK;
+}
+
+namespace tc {
+// Every FP32 bit pattern with a finite value: tf32_hi against the conversion instruction.
+// bad[0] counts mismatches below 2^127 in magnitude, bad[1] those in the top binade (where
+// rounding up overflows).
+__global__ void k_tf32_check(unsigned long long* bad) {
+    unsigned long long low = 0, top = 0;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < (1ull << 32); u += step) {
+        const uint32_t b = (uint32_t)u;
+        const uint32_t e = b & 0x7F800000u;
+        if (e == 0x7F800000u) continue;
+        const float x = __uint_as_float(b);
+        uint32_t ref;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ref) : "f"(x));
+        if (__float_as_uint(tf32_hi(x)) != ref) {
+            if (e == 0x7F000000u) ++top; else ++low;
+        }
+    }
+    if (low) atomicAdd(&bad[0], low);
+    if (top) atomicAdd(&bad[1], top);
+}
+}  // namespace tc
+
+hdf_status tf32_check(unsigned long long* bad2) {
+    DevBuf b;
+    HDF_CUDA(b.alloc(2 * sizeof(unsigned long long)));
+    HDF_CUDA(cudaMemset(b.p, 0, 2 * sizeof(unsigned long long)));
+    HDF_COUNT_LAUNCH();
+    tc::k_tf32_check<<<tc::num_sms() * 4, 256>>>(b.as<unsigned long long>());
+    HDF_CUDA(cudaGetLastError());
+    HDF_CUDA(cudaMemcpy(bad2, b.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return HDF_OK;
 }
 

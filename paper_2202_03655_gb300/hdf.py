@@ -80,6 +80,7 @@ SIGNATURES = {
     "hdf_krr_free": (None, [_vp]),
     "hdf_set_wait_limit": (_c_int, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "hdf_debug_fail_alloc": (None, [ctypes.c_longlong]),
+    "hdf_check_tf32_rounding": (_c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "hdf_status_string": (ctypes.c_char_p, [_c_int]),
     "hdf_last_error": (ctypes.c_char_p, []),
     "hdf_launch_count": (ctypes.c_longlong, []),
@@ -161,6 +162,14 @@ def set_wait_limit(cycles):
     prev = ctypes.c_longlong()
     _check(lib().hdf_set_wait_limit(int(cycles), ctypes.byref(prev)))
     return prev.value
+
+
+def check_tf32_rounding():
+    """Mismatches of the library's TF32 operand rounding against the device's conversion
+    instruction over all finite FP32 values: (below 2^127 in magnitude, top binade)."""
+    out = (ctypes.c_ulonglong * 2)()
+    _check(lib().hdf_check_tf32_rounding(out))
+    return int(out[0]), int(out[1])
 
 
 def debug_fail_alloc(after):

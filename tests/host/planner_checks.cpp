@@ -158,6 +158,13 @@ int main() {
             }
             bad += (h != hk);
         }
+        // A0F blocks start on 16-byte boundaries; their padding columns are marked zero
+        for (int m = 0; m <= tb.L_used; ++m) {
+            bad += (ft.aoff[m] % 4 != 0);
+            bad += (ft.aoff[m + 1] - ft.aoff[m] != (ft.acnt[m] + 3) / 4 * 4);
+            for (int t = ft.aoff[m] + ft.acnt[m]; t < ft.aoff[m + 1]; ++t) bad += (ft.a0off[t] != -1);
+        }
+        bad += (ft.ldA % 4 != 0 || ft.ldA < ft.nA);
         char buf[96];
         std::snprintf(buf, sizeof(buf), "matrix-free layout d=%d (%lld columns)", d, (long long)cols);
         report(buf, bad + (cols != rank ? 1.0 : 0.0), 0.0);

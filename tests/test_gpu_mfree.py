@@ -80,6 +80,30 @@ def test_matrix_free_column_counts(c):
         assert rel(Yc[:, j], Ys[:, j]) <= 2e-5, j
 
 
+def test_matrix_free_padded_leading_dimension_ragged_n():
+    """A point count that is not a multiple of 4 with V's leading dimension padded to one (rows of
+    16-byte multiples), so the B generators of U^T V take their vector loads up to the last full
+    group of four points and element loads after it.  The padding holds NaN: a read past the
+    last point would reach the result."""
+    import torch
+    from paper_2202_03655_gb300 import hdf
+    n, c, ld = 1533, 16, 1536
+    x = W.points("normal5_cauchy", n=n)
+    fs, fm = _pair(x, "cauchy", 2.0, 1e-3, "fp32")
+    V = np.random.default_rng(77).standard_normal((n, c))
+    Vp = torch.full((c, ld), float("nan"), dtype=torch.float32, device="cuda")
+    Vp[:, :n] = torch.from_numpy(V.T.astype(np.float32)).cuda()
+    Y = torch.zeros((c, ld), dtype=torch.float32, device="cuda")
+    fm.matvec_ptr(Vp.data_ptr(), ld, c, Y.data_ptr(), ld)
+    torch.cuda.synchronize()
+    assert fm.device_errors() == 0
+    Ym = Y[:, :n].t().double().cpu().numpy()
+    Ys = fs.matvec(to_dev(V, torch.float32)).double().cpu().numpy()
+    assert np.isfinite(Ym).all()
+    for j in range(c):
+        assert rel(Ym[:, j], Ys[:, j]) <= 2e-5, j
+
+
 @pytest.fixture(scope="module")
 def oracle_normal5():
     x = W.points("normal5_cauchy", n=3000)

@@ -84,3 +84,11 @@ def test_tensor_core_gram_solve(case):
     res = lambda X: rel(lam * X + U @ (S[:, None] * (U.T @ X)), Bd)
     assert res(X_tc) <= 2 * res(X_cc) + 1e-6
     assert res(X_tc) <= 1e-2
+
+
+def test_tf32_operand_rounding_matches_conversion_instruction():
+    """The 3xTF32 split rounds each FP32 operand to TF32 (nearest, ties away from zero) with
+    integer operations on its bit pattern; over all 2^32 bit patterns it must equal the device's
+    cvt.rna.tf32.f32 on every finite value, including the top binade where rounding overflows."""
+    from paper_2202_03655_gb300 import hdf
+    assert hdf.check_tf32_rounding() == (0, 0)
