@@ -742,7 +742,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //   k_tc_mf_utv: W[(k,s,m,j), c] = sum_i Z[i, zoff_m + j] (A0F[i, aoff_m + q] V[i, c]).
 //     M = 128 rows j of the tails of degree m, N = BN columns n = (q, c), K = points.  The B
 //     tiles A0F (.) V are formed in shared memory by two generator warps (10, 11), in the
-//     K-major 128-byte-swizzle layout the TMA would write, TF32 hi / lo stacked.
+//     K-major 128-byte-swizzle layout the TMA would write, TF32 hi / lo stacked.  For the small
+//     degrees (few tails j, many pairs q) a tile takes the transposed roles: M = 128 pairs q (the
+//     A0F block of m by TMA), N = BN columns n = (j, c), B = Z (.) V.
 //   k_tc_mf_uw: Y[i, c] = sum over phases (m, n0) of sum_q A0F[i, aoff_m + q] Q[i, (q, c)],
 //     Q = Z[:, zoff_m + j] W_m[j, (q, c)]: M = 128 points, N = BN columns, K = the tails of m.
 //     The B tiles come by TMA from W gathered per phase (k_prep_mf_w); the promotion warps
@@ -754,19 +756,23 @@ constexpr int NCONS_MF = NGEN + 9;      // item consumers: generators, MMA, 4 co
 struct MfUtvTcArgs {
     int64_t n, chunk;                   // points, points per K chunk (a multiple of 64)
     int nchunk, ntiles;
-    const int4* tiles;                  // (m, j0, n0, -): rows j0.. of the tails of m, columns n0..
+    const int4* tiles;                  // (m, y0, n0, flag), see k_tc_mf_utv
     const float* A0F; int ldA;
+    const float* Z; int ldZ;
     const float* V; int64_t ldv; int c;
     const int* zoff; const int* zcnt; const int* aoff; const int* acnt; const int64_t* wcol;
     double* part; int64_t r;            // part[(chunk * c + cc) * r + a]
     int* err; int* next;
 };
 
-// CP: c padded to 16, 32 or 64 (a divisor of BN); column n of the product is (q, cc) =
-// (n / CP, n mod CP), zero for cc >= c.
+// CP: c padded to 16, 32 or 64 (a divisor of BN).  Tile (m, y0, n0, flag): with flag 0 rows
+// y0.. are the tails j of degree m (A = Z columns zoff_m + j, map mZ) and column n is
+// (q, cc) = (n / CP, n mod CP) (B = A0F (.) V); with flag 1 rows y0.. are the pairs q of m
+// (A = A0F columns aoff_m + q, map mA) and column n is (j, cc) (B = Z (.) V).  Columns with
+// cc >= c are zero.
 template <int BN, int CP>
 __global__ void __launch_bounds__(NTHREADS_MF, 1)
-    k_tc_mf_utv(const __grid_constant__ CUtensorMap mZ, MfUtvTcArgs p) {
+    k_tc_mf_utv(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mA, MfUtvTcArgs p) {
     using SM = Smem<BN>;
     static_assert(BN % CP == 0, "column groups must not straddle a tile");
     constexpr int SB = SM::SB;
@@ -794,7 +800,8 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 if (item >= nitems) break;
                 const int4 tl = p.tiles[item % p.ntiles];
                 const int64_t i0 = (item / p.ntiles) * p.chunk;
-                const int zx = p.zoff[tl.x] + tl.y;
+                const CUtensorMap* map = tl.w ? &mA : &mZ;
+                const int zx = (tl.w ? p.aoff[tl.x] : p.zoff[tl.x]) + tl.y;
                 const int nk = ksteps(item);
                 const int claim_at = nk > 8 ? nk - 8 : 0;
                 int64_t nxt = nitems;
@@ -803,7 +810,7 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                     const uint32_t s = it % SU;
                     if (!mbar_wait(&sm.uempty[s], ((it / SU) & 1) ^ 1)) { ok = false; break; }
                     mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
-                    tma_load_2d(sm.U + s * SM::UBYTES, &mZ, zx, (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
+                    tma_load_2d(sm.U + s * SM::UBYTES, map, zx, (int)(i0 + (int64_t)kt * BK), &sm.ufull[s]);
                 }
                 item = nxt;
             }
@@ -840,7 +847,12 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 if (item < 0) { ok = false; break; }
                 if (item >= nitems) break;
                 const int4 tl = p.tiles[item % p.ntiles];
-                const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
+                // the generated operand's factor: A0F columns aoff_m + q (flag 0) or Z columns
+                // zoff_m + j (flag 1), from column q0 of the block of nq
+                const int m = tl.x, q0 = tl.z / CP;
+                const float* gsrc = tl.w ? p.Z : p.A0F;
+                const int64_t gld = tl.w ? (int64_t)p.ldZ : (int64_t)p.ldA;
+                const int ao = tl.w ? p.zoff[m] : p.aoff[m], nq = tl.w ? p.zcnt[m] : p.acnt[m];
                 const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
                 const int nk = ksteps(item);
                 const uint32_t abytes = 4u * (uint32_t)max(0, min(NQ, nq - q0));
@@ -852,7 +864,7 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const bool pe = i4 + e < i1;
-                            const float* src = p.A0F + (pe ? i4 + e : i0) * p.ldA + ao + q0;
+                            const float* src = gsrc + (pe ? i4 + e : i0) * gld + ao + q0;
                             cp_async16(slot + (e * 64 + t) * 4, src, pe ? abytes : 0u);
                         }
                         const int cnt = (int)max((int64_t)0, min((int64_t)4, i1 - i4));
@@ -921,7 +933,12 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 if (item < 0) { ok = false; break; }
                 if (item >= nitems) break;
                 const int4 tl = p.tiles[item % p.ntiles];
-                const int m = tl.x, q0 = tl.z / CP, ao = p.aoff[m], nq = p.acnt[m];
+                // the generated operand's factor: A0F columns aoff_m + q (flag 0) or Z columns
+                // zoff_m + j (flag 1), from column q0 of the block of nq
+                const int m = tl.x, q0 = tl.z / CP;
+                const float* gsrc = tl.w ? p.Z : p.A0F;
+                const int64_t gld = tl.w ? (int64_t)p.ldZ : (int64_t)p.ldA;
+                const int ao = tl.w ? p.zoff[m] : p.aoff[m], nq = tl.w ? p.zcnt[m] : p.acnt[m];
                 const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
                 const int nk = ksteps(item);
                 // the thread's values for step kt; with CP <= 32 the next step's are loaded while this
@@ -934,7 +951,7 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const bool pe = on && i4 + e < i1;
-                        const float* ap = p.A0F + (i4 + e) * p.ldA + ao + q0;
+                        const float* ap = gsrc + (i4 + e) * gld + ao + q0;
                         float w[NQ];
                         if constexpr (NQ == 4) {
                             const float4 t = pe ? __ldg(reinterpret_cast<const float4*>(ap)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1051,14 +1068,16 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
             for (int kt = 0; kt < nk && ok; ++kt, ++it) ok = promote_lean<BN>(sm, tmem, it, q, lane, acc);
             if (!ok) break;
             const int4 tl = p.tiles[item % p.ntiles];
-            const int m = tl.x, ao = p.aoff[m], nq = p.acnt[m], q0 = tl.z / CP;
+            const int m = tl.x, ao = p.aoff[m], nq = p.acnt[m], zq = p.zcnt[m], g0 = tl.z / CP;
             const int64_t ch = item / p.ntiles;
-            const int jr = tl.y + 32 * q + lane;             // row of the tails of m
-            if (jr < p.zcnt[m]) {
+            // this thread's row: a tail j (flag 0) or a pair q (flag 1); column group g: the pair
+            // q0 + g or the tail j0 + g; U column of (q, j): wcol[aoff_m + q] + j
+            const int row = tl.y + 32 * q + lane;
+            if (row < (tl.w ? nq : zq)) {
 #pragma unroll
                 for (int g = 0; g < BN / CP; ++g) {
-                    if (q0 + g >= nq) continue;
-                    const int64_t a = p.wcol[ao + q0 + g] + jr;
+                    if (g0 + g >= (tl.w ? zq : nq)) continue;
+                    const int64_t a = tl.w ? p.wcol[ao + row] + g0 + g : p.wcol[ao + g0 + g] + row;
 #pragma unroll
                     for (int cc = 0; cc < CP; ++cc)
                         if (cc < p.c) p.part[(ch * p.c + cc) * p.r + a] = (double)acc[g * CP + cc];
@@ -1501,10 +1520,20 @@ void tc_mf_lists(const std::vector<int>& zcnt, const std::vector<int>& acnt, int
     const int cp = tc_mf_cp(c);
     int kmax = tc::BK;
     for (size_t m = 0; m < zcnt.size(); ++m) {
-        const int J = zcnt[m], Np = acnt[m] * cp;
+        const int J = zcnt[m], Np = acnt[m] * cp, Nt = J * cp;
         if (J == 0 || acnt[m] == 0) continue;
-        for (int j0 = 0; j0 < J; j0 += tc::BM)
-            for (int n0 = 0; n0 < Np; n0 += 64) tiles.push_back(make_int4((int)m, j0, n0, 0));
+        // U^T V tiles of degree m in the orientation with fewer tiles: rows = tails j, columns
+        // (q, cc) (flag 0), or rows = the (k, s) pairs q of A0F, columns (j, cc) (flag 1; few
+        // tails and many pairs, the small degrees)
+        const int64_t n_rows_j = (int64_t)((J + tc::BM - 1) / tc::BM) * ((Np + 63) / 64);
+        const int64_t n_rows_q = (int64_t)((acnt[m] + tc::BM - 1) / tc::BM) * ((Nt + 63) / 64);
+        if (n_rows_q < n_rows_j) {
+            for (int q0 = 0; q0 < acnt[m]; q0 += tc::BM)
+                for (int n0 = 0; n0 < Nt; n0 += 64) tiles.push_back(make_int4((int)m, q0, n0, 1));
+        } else {
+            for (int j0 = 0; j0 < J; j0 += tc::BM)
+                for (int n0 = 0; n0 < Np; n0 += 64) tiles.push_back(make_int4((int)m, j0, n0, 0));
+        }
         const int nk = (J + tc::BK - 1) / tc::BK;
         kmax = std::max(kmax, nk * tc::BK);
         for (int n0 = 0; n0 < Np; n0 += 64)
@@ -1531,13 +1560,14 @@ hdf_status tc_mf_utv(const MfTcView& v, const int4* tiles, int ntiles, const flo
     *nchunk = nch;
     HDF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nch * c * v.r, st));
     if (ntiles == 0) return HDF_OK;
-    CUtensorMap mZ;
-    if (!tc::make_map(&mZ, v.Z, (uint64_t)v.ldZ, (uint64_t)v.n, (uint64_t)v.ldZ * 4, tc::BM, tc::BK, false))
+    CUtensorMap mZ, mA;
+    if (!tc::make_map(&mZ, v.Z, (uint64_t)v.ldZ, (uint64_t)v.n, (uint64_t)v.ldZ * 4, tc::BM, tc::BK, false) ||
+        !tc::make_map(&mA, v.A0F, (uint64_t)v.ldA, (uint64_t)v.n, (uint64_t)v.ldA * 4, tc::BM, tc::BK, false))
         return fail(HDF_ECUDA, "matrix-free product: cannot encode a tensor map");
     DevBuf next;
     HDF_CUDA(next.alloc_on(sizeof(int), st));
     HDF_CUDA(cudaMemsetAsync(next.p, 0, sizeof(int), st));
-    tc::MfUtvTcArgs a{v.n, chunk, nch, ntiles, tiles, v.A0F, v.ldA, V, ldv, c,
+    tc::MfUtvTcArgs a{v.n, chunk, nch, ntiles, tiles, v.A0F, v.ldA, v.Z, v.ldZ, V, ldv, c,
                       v.zoff, v.zcnt, v.aoff, v.acnt, v.wcol, part, v.r, err, next.as<int>()};
     const size_t sm = tc::Smem<64>::bytes();
     const int64_t nitems = (int64_t)ntiles * nch;
@@ -1545,7 +1575,7 @@ hdf_status tc_mf_utv(const MfTcView& v, const int4* tiles, int ntiles, const flo
     auto kern = c <= 16 ? tc::k_tc_mf_utv<64, 16> : c <= 32 ? tc::k_tc_mf_utv<64, 32> : tc::k_tc_mf_utv<64, 64>;
     HDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HDF_COUNT_LAUNCH();
-    kern<<<grid, tc::NTHREADS_MF, sm, st>>>(mZ, a);
+    kern<<<grid, tc::NTHREADS_MF, sm, st>>>(mZ, mA, a);
     HDF_CUDA(cudaGetLastError());
     return HDF_OK;
 }
