@@ -1089,16 +1089,20 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
     cta_teardown<BN>(tmem, warp);
 }
 
+// m: the tail degree, plus kMfFlip when the phase takes the transposed roles (K = the pairs q of
+// m, columns n = (j, c), A = the A0F block of m, the accumulator contracted with Z).
+constexpr int kMfFlip = 1 << 16;
 struct MfPhase {
-    int m, n0, nk, y0;                  // tail degree, first column (q, c), K steps, row of its B tiles
+    int m, n0, nk, y0;                  // tail degree (| kMfFlip), first column, K steps, row of its B tiles
 };
 
 struct MfUwTcArgs {
     int64_t n;                          // points
     int nphase;
     const MfPhase* phases;
-    const int* zoff; const int* aoff; const int* acnt;
+    const int* zoff; const int* aoff; const int* acnt; const int* zcnt;
     const float* A0F; int ldA;
+    const float* Z; int ldZ;
     int c;
     float* Y; int64_t ldy;
     int* err;
@@ -1106,11 +1110,11 @@ struct MfUwTcArgs {
 
 // Y for 128-point tiles (persistent over tiles), phases in order; CP = c padded to 16, 32 or
 // 64 (a divisor of BN), so the column (q, cc) of accumulator entry j is q = (n0 + j) / CP,
-// cc = j mod CP.
+// cc = j mod CP (for a transposed phase the column (j, cc) with the tail j = (n0 + j) / CP).
 template <int BN, int CP>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_mf_uw(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mW,
-               const __grid_constant__ CUtensorMap mWlo, MfUwTcArgs p) {
+    k_tc_mf_uw(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mA,
+               const __grid_constant__ CUtensorMap mW, const __grid_constant__ CUtensorMap mWlo, MfUwTcArgs p) {
     using SM = Smem<BN>;
     static_assert(BN % CP == 0, "column groups must not straddle a tile");
     extern __shared__ unsigned char raw[];
@@ -1126,14 +1130,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 for (int ph = 0; ph < p.nphase && ok; ++ph) {
                     const MfPhase P = p.phases[ph];
-                    const int z0 = p.zoff[P.m];
+                    const bool fl = (P.m & kMfFlip) != 0;
+                    const int m = P.m & (kMfFlip - 1);
+                    const CUtensorMap* map = fl ? &mA : &mZ;
+                    const int z0 = fl ? p.aoff[m] : p.zoff[m];
                     for (int kt = 0; kt < P.nk; ++kt, ++it) {
                         const uint32_t s = it % S_U;
                         if (!mbar_wait(&sm.uempty[s], ((it / S_U) & 1) ^ 1)) { ok = false; break; }
                         mbar_expect_tx(&sm.ufull[s], SM::UBYTES);
                         unsigned char* dst = sm.U + s * SM::UBYTES;
-                        tma_load_2d(dst, &mZ, z0 + kt * BK, (int)(tile * BM), &sm.ufull[s]);
-                        tma_load_2d(dst + SM::UBYTES / 2, &mZ, z0 + kt * BK + KH, (int)(tile * BM), &sm.ufull[s]);
+                        tma_load_2d(dst, map, z0 + kt * BK, (int)(tile * BM), &sm.ufull[s]);
+                        tma_load_2d(dst + SM::UBYTES / 2, map, z0 + kt * BK + KH, (int)(tile * BM), &sm.ufull[s]);
                     }
                 }
             }
@@ -1199,10 +1206,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int j = 0; j < BN; ++j) acc[j] = 0.f;
                 for (int kt = 0; kt < P.nk && ok; ++kt, ++it) ok = promote_lean<BN>(sm, tmem, it, q, lane, acc);
                 if (!ok) break;
-                const int ao = p.aoff[P.m], nq = p.acnt[P.m], q0 = P.n0 / CP;
+                // contraction of the phase with its other factor: A0F (q = q0 + g) or, transposed, Z
+                // (j = q0 + g)
+                const bool fl = (P.m & kMfFlip) != 0;
+                const int m = P.m & (kMfFlip - 1), q0 = P.n0 / CP;
+                const float* fsrc = fl ? p.Z : p.A0F;
+                const int64_t fld = fl ? (int64_t)p.ldZ : (int64_t)p.ldA;
+                const int ao = fl ? p.zoff[m] : p.aoff[m], nq = fl ? p.zcnt[m] : p.acnt[m];
 #pragma unroll
                 for (int g = 0; g < BN / CP; ++g) {
-                    const float f = (rv && q0 + g < nq) ? __ldg(p.A0F + row * p.ldA + ao + q0 + g) : 0.f;
+                    const float f = (rv && q0 + g < nq) ? __ldg(fsrc + row * fld + ao + q0 + g) : 0.f;
 #pragma unroll
                     for (int j = 0; j < CP; ++j) y[j] += f * acc[g * CP + j];
                 }
@@ -1221,7 +1234,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // B operand of k_tc_mf_uw: for phase p (rows y0 .. y0 + BN of hi / lo) and K index kk (a tail j),
 // hi + lo = W[(wcol[aoff_m + q] + kk) c + cc] with (q, cc) = ((n0 + row) / CP, (n0 + row) mod CP),
-// zero where q >= acnt_m, cc >= c or kk >= zcnt_m.  Row-major [nphase BN][kpad].
+// zero where q >= acnt_m, cc >= c or kk >= zcnt_m; for a transposed phase K runs over the pairs
+// (kk = q) and the row is (j, cc): W[(wcol[aoff_m + kk] + j) c + cc].  Row-major [nphase BN][kpad].
 __global__ void k_prep_mf_w(const float* __restrict__ W, int c, int cp, const MfPhase* __restrict__ phases, int nphase,
                             int bn, int64_t kpad, const int* __restrict__ zcnt, const int* __restrict__ aoff,
                             const int* __restrict__ acnt, const int64_t* __restrict__ wcol, float* __restrict__ hi,
@@ -1230,9 +1244,14 @@ __global__ void k_prep_mf_w(const float* __restrict__ W, int c, int cp, const Mf
     if (idx >= (int64_t)nphase * bn * kpad) return;
     const int64_t rowg = idx / kpad, kk = idx % kpad;
     const MfPhase P = phases[rowg / bn];
+    const int m = P.m & (kMfFlip - 1);
     const int nidx = P.n0 + (int)(rowg % bn), q = nidx / cp, cc = nidx % cp;
     float v = 0.f;
-    if (q < acnt[P.m] && cc < c && kk < zcnt[P.m]) v = W[(wcol[aoff[P.m] + q] + kk) * c + cc];
+    if ((P.m & kMfFlip) != 0) {
+        if (q < zcnt[m] && cc < c && kk < acnt[m]) v = W[(wcol[aoff[m] + kk] + q) * c + cc];
+    } else {
+        if (q < acnt[m] && cc < c && kk < zcnt[m]) v = W[(wcol[aoff[m] + q] + kk) * c + cc];
+    }
     const float h = tf32_hi(v);
     hi[idx] = h;
     lo[idx] = v - h;
@@ -1534,10 +1553,19 @@ void tc_mf_lists(const std::vector<int>& zcnt, const std::vector<int>& acnt, int
             for (int j0 = 0; j0 < J; j0 += tc::BM)
                 for (int n0 = 0; n0 < Np; n0 += 64) tiles.push_back(make_int4((int)m, j0, n0, 0));
         }
-        const int nk = (J + tc::BK - 1) / tc::BK;
-        kmax = std::max(kmax, nk * tc::BK);
-        for (int n0 = 0; n0 < Np; n0 += 64)
-            phases.push_back(make_int4((int)m, n0, nk, (int)phases.size() * 64));
+        // U W phases of degree m in the orientation with fewer K steps: K = the tails, columns
+        // (q, cc), or (flagged) K = the pairs q, columns (j, cc)
+        const int nk = (J + tc::BK - 1) / tc::BK, nkq = (acnt[m] + tc::BK - 1) / tc::BK;
+        const int64_t steps_j = (int64_t)((Np + 63) / 64) * nk, steps_q = (int64_t)((Nt + 63) / 64) * nkq;
+        if (steps_q < steps_j) {
+            kmax = std::max(kmax, nkq * tc::BK);
+            for (int n0 = 0; n0 < Nt; n0 += 64)
+                phases.push_back(make_int4((int)m | tc::kMfFlip, n0, nkq, (int)phases.size() * 64));
+        } else {
+            kmax = std::max(kmax, nk * tc::BK);
+            for (int n0 = 0; n0 < Np; n0 += 64)
+                phases.push_back(make_int4((int)m, n0, nk, (int)phases.size() * 64));
+        }
     }
     *kpad = kmax;
 }
@@ -1583,18 +1611,19 @@ hdf_status tc_mf_utv(const MfTcView& v, const int4* tiles, int ntiles, const flo
 template <int CP>
 static hdf_status mf_uw_cp(const MfTcView& v, const tc::MfPhase* phases, int nphase, int kpad, const float* hi,
                            const float* lo, int c, float* Y, int64_t ldy, int* err, cudaStream_t st) {
-    CUtensorMap mZ, mW, mWl;
+    CUtensorMap mZ, mA, mW, mWl;
     if (!tc::make_map(&mZ, v.Z, (uint64_t)v.ldZ, (uint64_t)v.n, (uint64_t)v.ldZ * 4, tc::KH, tc::BM, true) ||
+        !tc::make_map(&mA, v.A0F, (uint64_t)v.ldA, (uint64_t)v.n, (uint64_t)v.ldA * 4, tc::KH, tc::BM, true) ||
         !tc::make_map(&mW, hi, (uint64_t)kpad, (uint64_t)nphase * 64, (uint64_t)kpad * 4, tc::KH, 64, true) ||
         !tc::make_map(&mWl, lo, (uint64_t)kpad, (uint64_t)nphase * 64, (uint64_t)kpad * 4, tc::KH, 64, true))
         return fail(HDF_ECUDA, "matrix-free product: cannot encode a tensor map");
-    tc::MfUwTcArgs a{v.n, nphase, phases, v.zoff, v.aoff, v.acnt, v.A0F, v.ldA, c, Y, ldy, err};
+    tc::MfUwTcArgs a{v.n, nphase, phases, v.zoff, v.aoff, v.acnt, v.zcnt, v.A0F, v.ldA, v.Z, v.ldZ, c, Y, ldy, err};
     const size_t sm = tc::Smem<64>::bytes();
     HDF_CUDA(cudaFuncSetAttribute(tc::k_tc_mf_uw<64, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t ntiles = (v.n + tc::BM - 1) / tc::BM;
     const int grid = (int)std::min<int64_t>(ntiles, tc::num_sms());
     HDF_COUNT_LAUNCH();
-    tc::k_tc_mf_uw<64, CP><<<grid, tc::NTHREADS, sm, st>>>(mZ, mW, mWl, a);
+    tc::k_tc_mf_uw<64, CP><<<grid, tc::NTHREADS, sm, st>>>(mZ, mA, mW, mWl, a);
     HDF_CUDA(cudaGetLastError());
     return HDF_OK;
 }
