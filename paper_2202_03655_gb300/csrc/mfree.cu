@@ -35,28 +35,47 @@ struct ZWParams {
     const double* x; int64_t n; int d; Center c; double inv2R;
     int L, tri;                      // highest kept degree, (L+1)(L+2)/2
     const int16_t* zchain; int cstride; int ldZ;
-    const int32_t* a0off; const int32_t* afcol; int nA; int ldA;
+    const int32_t* zpair; const int32_t* gmap; int ng;   // product form (d = 4, 5), else zpair = null
+    const int32_t* a0off; const int32_t* afcol; int nA; int ldA;   // a0off / afcol: ldA entries
     const void* F; int64_t ldF; int nF;
     void* Z; void* A0F;
     const void* coefA; const void* coefB;
     int per_warp;                    // shared elements per warp
-    int stage;                       // 1: zchain, a0off and afcol are copied to shared memory per CTA
+    int stage;                       // 1: the index tables are copied to shared memory per CTA
 };
 
-// Bytes of the index tables k_zwriter stages in shared memory (each part 16-byte aligned).
-__host__ __device__ inline size_t zwriter_tab_bytes(int ldZ, int cstride, int ldA) {
-    return align16(sizeof(int16_t) * (size_t)ldZ * cstride) + 2 * align16(sizeof(int32_t) * (size_t)ldA);
+// Bytes of the index tables k_zwriter stages in shared memory (each part 16-byte aligned): the
+// product-form pairs and G recipe (d = 4, 5) or the chains, then a0off and afcol.
+__host__ __device__ inline size_t zwriter_tab_bytes(bool pairs, int ldZ, int cstride, int ng, int ldA) {
+    const size_t z = pairs ? align16(sizeof(int32_t) * (size_t)ldZ) + align16(sizeof(int32_t) * (size_t)(ng > 0 ? ng : 1))
+                           : align16(sizeof(int16_t) * (size_t)ldZ * cstride);
+    return z + 2 * align16(sizeof(int32_t) * (size_t)ldA);
 }
 
-// Per warp shared: level tables (levels x tri), trig (2L+1), the point's F row (nF).
-__host__ __device__ inline int zwriter_per_warp(int levels, int tri, int L, int nF) {
-    return (levels * tri + 2 * L + 1 + nF + 3) & ~3;
+// Per warp shared: level tables (levels x tri), trig (2L+1) and a zero slot, the point's F row
+// (nF), and with d = 5 the point's G (ng + 1).
+__host__ __device__ inline int zwriter_per_warp(int levels, int tri, int L, int nF, int gsz) {
+    return (levels * tri + 2 * L + 2 + nF + gsz + 3) & ~3;
 }
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void store(float* p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void store(double* p, double a, double b, double c, double d) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+    }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int levels = P.d - 2;
+    const bool pairs = P.zpair != nullptr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * P.per_warp;
     T* cA = reinterpret_cast<T*>(smem_raw) + (size_t)nwarps * P.per_warp;
@@ -66,47 +85,88 @@ __global__ void __launch_bounds__(1024) k_zwriter(ZWParams P) {
         cB[idx] = reinterpret_cast<const T*>(P.coefB)[idx];
     }
     const int16_t* zchain = P.zchain;
+    const int32_t* zpair = P.zpair;
+    const int32_t* gmap = P.gmap;
     const int32_t* a0off = P.a0off;
     const int32_t* afcol = P.afcol;
     if (P.stage) {
         unsigned char* tp = reinterpret_cast<unsigned char*>(cB + levels * P.tri);
         tp = reinterpret_cast<unsigned char*>(align16(reinterpret_cast<size_t>(tp)));
-        int16_t* zc = reinterpret_cast<int16_t*>(tp);
-        for (int64_t k = threadIdx.x; k < (int64_t)P.ldZ * P.cstride; k += blockDim.x) zc[k] = P.zchain[k];
-        tp += align16(sizeof(int16_t) * (size_t)P.ldZ * P.cstride);
+        if (pairs) {
+            int32_t* zp = reinterpret_cast<int32_t*>(tp);
+            for (int k = threadIdx.x; k < P.ldZ; k += blockDim.x) zp[k] = P.zpair[k];
+            tp += align16(sizeof(int32_t) * (size_t)P.ldZ);
+            int32_t* gm = reinterpret_cast<int32_t*>(tp);
+            if (P.gmap)
+                for (int k = threadIdx.x; k < P.ng; k += blockDim.x) gm[k] = P.gmap[k];
+            tp += align16(sizeof(int32_t) * (size_t)(P.ng > 0 ? P.ng : 1));
+            zpair = zp;
+            if (P.gmap) gmap = gm;
+        } else {
+            int16_t* zc = reinterpret_cast<int16_t*>(tp);
+            for (int64_t k = threadIdx.x; k < (int64_t)P.ldZ * P.cstride; k += blockDim.x) zc[k] = P.zchain[k];
+            tp += align16(sizeof(int16_t) * (size_t)P.ldZ * P.cstride);
+            zchain = zc;
+        }
         int32_t* ao = reinterpret_cast<int32_t*>(tp);
         int32_t* af = ao + align16(sizeof(int32_t) * (size_t)P.ldA) / sizeof(int32_t);
-        for (int k = threadIdx.x; k < P.nA; k += blockDim.x) { ao[k] = P.a0off[k]; af[k] = P.afcol[k]; }
-        zchain = zc;
+        for (int k = threadIdx.x; k < P.ldA; k += blockDim.x) { ao[k] = P.a0off[k]; af[k] = P.afcol[k]; }
         a0off = ao;
         afcol = af;
     }
     __syncthreads();
     T* tbl = base;
     T* trig = tbl + levels * P.tri;
-    T* Fs = trig + 2 * P.L + 1;
+    T* Fs = trig + 2 * P.L + 2;
+    // G of the product form: the trigonometric factors themselves (d = 4), else its own array;
+    // its slot ng is zero (the padding columns)
+    T* G = P.gmap ? Fs + P.nF : trig;
+    if (pairs && lane == 0) G[P.ng] = (T)0;
     const T* Fg = reinterpret_cast<const T*>(P.F);
     const int tl = levels - 1;           // position of the trig index in a tail chain
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw = (int64_t)gridDim.x * nwarps;
     for (int64_t i = gw; i < P.n; i += nw) {
         point_harmonic_tables<T>(P.x, P.d, P.c, P.inv2R, P.L, P.tri, cA, cB, tbl, trig, i, lane);
         for (int f = lane; f < P.nF; f += 32) Fs[f] = Fg[i * P.ldF + f];
-        __syncwarp();
         T* zr = reinterpret_cast<T*>(P.Z) + i * (int64_t)P.ldZ;
-        for (int t = lane; t < P.ldZ; t += 32) {
-            const int16_t* ch = zchain + (int64_t)t * P.cstride;
-            const int tr = ch[tl];
-            T v = (T)0;
-            if (tr != 0x7fff) {                  // 0x7fff marks a padding column
-                v = trig[P.L + tr];
-                for (int l = 1; l < levels; ++l) v *= tbl[l * P.tri + ch[l - 1]];
+        if (pairs) {
+            // Z[i, t] = P_1[ia] G[ib] (P_1: the level-1 table), four consecutive columns per lane
+            // (ldZ is a multiple of 8)
+            if (P.gmap) {
+                __syncwarp();
+                for (int g = lane; g < P.ng; g += 32) {
+                    const int32_t gm = gmap[g];
+                    G[g] = tbl[2 * P.tri + (gm >> 16)] * trig[gm & 0xFFFF];   // level 2 x trig
+                }
             }
-            zr[t] = v;
+            __syncwarp();
+            const T* t1 = tbl + P.tri;
+            for (int t4 = lane; 4 * t4 < P.ldZ; t4 += 32) {
+                const int4 pr = *reinterpret_cast<const int4*>(zpair + 4 * t4);
+                Vec4<T>::store(zr + 4 * t4, t1[pr.x >> 16] * G[pr.x & 0xFFFF], t1[pr.y >> 16] * G[pr.y & 0xFFFF],
+                               t1[pr.z >> 16] * G[pr.z & 0xFFFF], t1[pr.w >> 16] * G[pr.w & 0xFFFF]);
+            }
+        } else {
+            __syncwarp();
+            for (int t = lane; t < P.ldZ; t += 32) {
+                const int16_t* ch = zchain + (int64_t)t * P.cstride;
+                const int tr = ch[tl];
+                T v = (T)0;
+                if (tr != 0x7fff) {                  // 0x7fff marks a padding column
+                    v = trig[P.L + tr];
+                    for (int l = 1; l < levels; ++l) v *= tbl[l * P.tri + ch[l - 1]];
+                }
+                zr[t] = v;
+            }
         }
+        // A0F[i, q] = P_0 entry times the radial factor, four columns per lane (ldA is a multiple
+        // of 4); a0off = -1 marks a padding column
         T* ar = reinterpret_cast<T*>(P.A0F) + i * (int64_t)P.ldA;
-        for (int q = lane; q < P.ldA; q += 32) {
-            const int32_t o = q < P.nA ? a0off[q] : -1;      // -1: a padding column
-            ar[q] = o >= 0 ? tbl[o] * Fs[afcol[q]] : (T)0;
+        for (int q4 = lane; 4 * q4 < P.ldA; q4 += 32) {
+            const int4 o = *reinterpret_cast<const int4*>(a0off + 4 * q4);
+            const int4 fc = *reinterpret_cast<const int4*>(afcol + 4 * q4);
+            Vec4<T>::store(ar + 4 * q4, o.x >= 0 ? tbl[o.x] * Fs[fc.x] : (T)0, o.y >= 0 ? tbl[o.y] * Fs[fc.y] : (T)0,
+                           o.z >= 0 ? tbl[o.z] * Fs[fc.z] : (T)0, o.w >= 0 ? tbl[o.w] * Fs[fc.w] : (T)0);
         }
         __syncwarp();
     }
@@ -399,21 +459,33 @@ hdf_status mf_write(hdf_factor* f, const double* x, int64_t n, int d, const dev:
                                     " bytes)");
     }
     const int Lp = ft.L_used + 1;
-    DevBuf dchain, da0, daf;
+    DevBuf dchain, da0, daf, dpair, dgmap;
+    // the writer reads a0off / afcol four at a time over the whole row stride: padded to ldA
+    std::vector<int32_t> a0p(ft.ldA, -1), afp(ft.ldA, 0);
+    std::copy(ft.a0off.begin(), ft.a0off.end(), a0p.begin());
+    std::copy(ft.afcol.begin(), ft.afcol.end(), afp.begin());
+    const bool pairs = !ft.zpair.empty();
     HDF_CUDA(dchain.alloc_on(sizeof(int16_t) * ft.zchain.size(), st));
-    HDF_CUDA(da0.alloc_on(sizeof(int32_t) * std::max(1, ft.nA), st));
-    HDF_CUDA(daf.alloc_on(sizeof(int32_t) * std::max(1, ft.nA), st));
+    HDF_CUDA(da0.alloc_on(sizeof(int32_t) * ft.ldA, st));
+    HDF_CUDA(daf.alloc_on(sizeof(int32_t) * ft.ldA, st));
+    if (pairs) {
+        HDF_CUDA(dpair.alloc_on(sizeof(int32_t) * ft.zpair.size(), st));
+        HDF_CUDA(cudaMemcpyAsync(dpair.p, ft.zpair.data(), sizeof(int32_t) * ft.zpair.size(), cudaMemcpyHostToDevice, st));
+        if (!ft.gmap.empty()) {
+            HDF_CUDA(dgmap.alloc_on(sizeof(int32_t) * ft.gmap.size(), st));
+            HDF_CUDA(cudaMemcpyAsync(dgmap.p, ft.gmap.data(), sizeof(int32_t) * ft.gmap.size(), cudaMemcpyHostToDevice, st));
+        }
+    }
+    HDF_CUDA(cudaMemcpyAsync(da0.p, a0p.data(), sizeof(int32_t) * ft.ldA, cudaMemcpyHostToDevice, st));
+    HDF_CUDA(cudaMemcpyAsync(daf.p, afp.data(), sizeof(int32_t) * ft.ldA, cudaMemcpyHostToDevice, st));
     HDF_CUDA(mf.dzoff.alloc(sizeof(int) * (Lp + 1)));
     HDF_CUDA(mf.dzcnt.alloc(sizeof(int) * Lp));
     HDF_CUDA(mf.daoff.alloc(sizeof(int) * (Lp + 1)));
     HDF_CUDA(mf.dacnt.alloc(sizeof(int) * Lp));
     HDF_CUDA(mf.dwcol.alloc(sizeof(int64_t) * std::max(1, ft.nA)));
     HDF_CUDA(cudaMemcpyAsync(dchain.p, ft.zchain.data(), sizeof(int16_t) * ft.zchain.size(), cudaMemcpyHostToDevice, st));
-    if (ft.nA > 0) {
-        HDF_CUDA(cudaMemcpyAsync(da0.p, ft.a0off.data(), sizeof(int32_t) * ft.nA, cudaMemcpyHostToDevice, st));
-        HDF_CUDA(cudaMemcpyAsync(daf.p, ft.afcol.data(), sizeof(int32_t) * ft.nA, cudaMemcpyHostToDevice, st));
+    if (ft.nA > 0)
         HDF_CUDA(cudaMemcpyAsync(mf.dwcol.p, ft.wcol.data(), sizeof(int64_t) * ft.nA, cudaMemcpyHostToDevice, st));
-    }
     HDF_CUDA(cudaMemcpyAsync(mf.dzoff.p, ft.zoff.data(), sizeof(int) * (Lp + 1), cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(mf.dzcnt.p, ft.zcnt.data(), sizeof(int) * Lp, cudaMemcpyHostToDevice, st));
     HDF_CUDA(cudaMemcpyAsync(mf.daoff.p, ft.aoff.data(), sizeof(int) * (Lp + 1), cudaMemcpyHostToDevice, st));
@@ -423,15 +495,18 @@ hdf_status mf_write(hdf_factor* f, const double* x, int64_t n, int d, const dev:
     P.x = x; P.n = n; P.d = d; P.c = cen; P.inv2R = inv2R;
     P.L = ft.L_used; P.tri = tb.tri;
     P.zchain = dchain.as<int16_t>(); P.cstride = chain_stride(d); P.ldZ = ft.ldZ;
+    P.zpair = pairs ? dpair.as<int32_t>() : nullptr;
+    P.gmap = ft.gmap.empty() ? nullptr : dgmap.as<int32_t>();
+    P.ng = ft.ng;
     P.a0off = da0.as<int32_t>(); P.afcol = daf.as<int32_t>(); P.nA = ft.nA; P.ldA = ft.ldA;
     P.F = F; P.ldF = ldF; P.nF = tb.nF;
     P.Z = mf.Z.p; P.A0F = mf.A0F.p;
     P.coefA = coefA; P.coefB = coefB;
     const int levels = d - 2;
-    P.per_warp = dev::zwriter_per_warp(levels, tb.tri, ft.L_used, tb.nF);
+    P.per_warp = dev::zwriter_per_warp(levels, tb.tri, ft.L_used, tb.nF, ft.gmap.empty() ? 0 : ft.ng + 1);
     const size_t coef = sizeof(T) * 2 * (size_t)levels * tb.tri;
     const size_t budget = 200 * 1024;
-    const size_t tabs = dev::zwriter_tab_bytes(ft.ldZ, chain_stride(d), ft.ldA) + 16;
+    const size_t tabs = dev::zwriter_tab_bytes(pairs, ft.ldZ, chain_stride(d), ft.ng, ft.ldA) + 16;
     // stage the index tables only when 16 warps still fit beside them (fewer warps measured slower)
     P.stage = (coef + tabs + 16 * sizeof(T) * (size_t)P.per_warp <= budget) ? 1 : 0;
     const size_t fixed = coef + (P.stage ? tabs : 0);

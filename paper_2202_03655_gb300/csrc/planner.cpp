@@ -983,6 +983,32 @@ bool make_free_tables(const FactorChoice& fc, int d, int L, const DeviceTables& 
         err = "matrix-free tail enumeration disagrees with the harmonic counts";
         return false;
     }
+    ft.zpair.clear();
+    ft.gmap.clear();
+    ft.ng = 0;
+    if (d == 4 || d == 5) {
+        ft.ng = (d == 4) ? 2 * Lu + 1 : (Lu + 1) * (Lu + 1);
+        ft.zpair.assign(ft.ldZ, ft.ng);                      // padding: level-1 entry 0 times the zero slot
+        for (int t = 0; t < ft.nZ; ++t) {
+            const int16_t* ch = &ft.zchain[(size_t)t * stride];
+            const int tr = ch[levels - 1];
+            if (tr == 0x7fff) continue;
+            int g = Lu + tr;
+            if (d == 5) {
+                const int a = std::abs(tr), mu2 = a + (ch[1] - tri_index(Lu, a, 0));
+                g = mu2 * mu2 + mu2 + tr;
+            }
+            ft.zpair[t] = ((int32_t)ch[0] << 16) | g;
+        }
+        if (d == 5) {
+            ft.gmap.assign(ft.ng, 0);
+            for (int mu2 = 0; mu2 <= Lu; ++mu2)
+                for (int mu3 = -mu2; mu3 <= mu2; ++mu3) {
+                    const int a = std::abs(mu3);
+                    ft.gmap[mu2 * mu2 + mu2 + mu3] = (tri_index(Lu, a, mu2 - a) << 16) | (Lu + mu3);
+                }
+        }
+    }
     // hoff[m]: offset of the tails of degree m inside H_k (the same for every k >= m)
     std::vector<int64_t> hoff(Lu + 2, 0);
     for (int m = 0; m <= Lu; ++m) hoff[m + 1] = hoff[m] + ft.zcnt[m];

@@ -162,6 +162,13 @@ struct FreeTables {
     std::vector<int32_t> a0off;              // nA: level-0 table offset of P_0(m, k - m); -1: padding (zero)
     std::vector<int32_t> afcol;              // nA: F column fbase[k] + s
     std::vector<int64_t> wcol;               // nA: padded U column of (k, s, h = first tail of m)
+    // d = 4, 5: the product form of the tails, Z[i, t] = P_1[zpair_t >> 16] G[zpair_t & 0xFFFF] with
+    // P_1 the level-1 table and G per point the product of the deeper factors: d = 4: G = the
+    // trigonometric factors (slot L + mu_2); d = 5: G[mu_2^2 + mu_2 + mu_3] = P_2(mu_2 -> |mu_3|)
+    // trig(mu_3), gmap = (level-2 offset << 16) | trig slot.  G[ng] = 0 serves the padding columns.
+    // Empty for d >= 6.
+    std::vector<int32_t> zpair, gmap;
+    int ng = 0;
 };
 // From the tables of make_tables (its cbase, dimp, fbase); false (with err) if d < 4.
 bool make_free_tables(const FactorChoice& fc, int d, int L, const DeviceTables& tb, FreeTables& out,

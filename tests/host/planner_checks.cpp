@@ -165,6 +165,22 @@ int main() {
             for (int t = ft.aoff[m] + ft.acnt[m]; t < ft.aoff[m + 1]; ++t) bad += (ft.a0off[t] != -1);
         }
         bad += (ft.ldA % 4 != 0 || ft.ldA < ft.nA);
+        // product form (d = 4, 5): each column's packed level-1 offset and G slot name the same
+        // factors as its chain; padding columns name the zero slot
+        if (d == 4 || d == 5) {
+            bad += ((int)ft.zpair.size() != ft.ldZ);
+            const int Lu = tb.L_used;
+            for (int t = 0; t < ft.ldZ && (int)ft.zpair.size() == ft.ldZ; ++t) {
+                const int ia = ft.zpair[t] >> 16, ib = ft.zpair[t] & 0xFFFF;
+                const int16_t* ch = t < ft.nZ ? &ft.zchain[(size_t)t * stride] : nullptr;
+                if (!ch || ch[levels - 1] == 0x7fff) { bad += (ib != ft.ng); continue; }
+                bad += (ia != ch[0]);
+                if (d == 4) bad += (ib != Lu + ch[1]);
+                else bad += (ib >= ft.ng || ft.gmap[ib] != (((int32_t)ch[1] << 16) | (Lu + ch[2])));
+            }
+        } else {
+            bad += !ft.zpair.empty();
+        }
         char buf[96];
         std::snprintf(buf, sizeof(buf), "matrix-free layout d=%d (%lld columns)", d, (long long)cols);
         report(buf, bad + (cols != rank ? 1.0 : 0.0), 0.0);
