@@ -834,11 +834,12 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
         const bool vec = ((reinterpret_cast<uintptr_t>(p.V) | (uintptr_t)p.ldv * 4u) & 15u) == 0;
         if constexpr (STG) {
             // values of DS steps staged by cp.async, DS - 1 steps ahead (A0F rows come mostly from
-            // DRAM, far beyond one step's time): slot = [8 chunks][64 threads][16 bytes], chunk e < 4
-            // the A0F values q0 .. q0 + 3 of point 4 pg + e, chunk 4 + u the four points of V column
-            // 4 rs + u.  A thread reads back only what it copied, so its own wait_group suffices.
-            constexpr int DS = 4;
-            static_assert(NQ == 4 && NU == 4 && DS * 8 * 64 * 16 <= SM::UBYTES, "the ring fits one U stage");
+            // DRAM, far beyond one step's time).  Slot: the 4 x 16 chunks of the generated factor
+            // (chunk [e][pg]: the 16 bytes of point 4 pg + e, copied by the lane with rs = e and
+            // read by the four lanes of pg after the warp's barrier), then the 4 x 64 chunks of V
+            // (chunk [u][t]: the four points of column 4 rs + u, copied and read by thread t).
+            constexpr int DS = 4, SLOT = (4 * 16 + 4 * 64) * 4;     // floats per slot
+            static_assert(NQ == 4 && NU == 4 && DS * SLOT * 4 <= (int)SM::UBYTES, "the ring fits one U stage");
             float* stg = reinterpret_cast<float*>(sm.U + (S_U - 1) * SM::UBYTES);
             const int t = (warp - 10) * 32 + lane;
             uint32_t it = 0;
@@ -856,23 +857,24 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                 const int64_t i0 = (item / p.ntiles) * p.chunk, i1 = min(p.n, i0 + p.chunk);
                 const int nk = ksteps(item);
                 const uint32_t abytes = 4u * (uint32_t)max(0, min(NQ, nq - q0));
+                // per-item bases, advanced by one step of BK points per copy
+                const int64_t ib = i0 + 4 * pg;
+                const float* g_first = gsrc + ao + q0;                       // row 0: a valid address
+                const float* a_base = g_first + (ib + rs) * gld;
+                const int64_t a_step = (int64_t)BK * gld;
                 // the copies of step kt2 (zero-filled outside the item; an empty group past its end)
                 auto issue = [&](int kt2) {
                     if (kt2 < nk) {
-                        float* slot = stg + (kt2 % DS) * (8 * 64 * 4);
-                        const int64_t i4 = i0 + (int64_t)kt2 * BK + 4 * pg;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const bool pe = i4 + e < i1;
-                            const float* src = gsrc + (pe ? i4 + e : i0) * gld + ao + q0;
-                            cp_async16(slot + (e * 64 + t) * 4, src, pe ? abytes : 0u);
-                        }
+                        float* slot = stg + (kt2 % DS) * SLOT;
+                        const int64_t i4 = ib + (int64_t)kt2 * BK;
+                        const bool pe = i4 + rs < i1;
+                        cp_async16(slot + (rs * 16 + pg) * 4, pe ? a_base + kt2 * a_step : g_first, pe ? abytes : 0u);
                         const int cnt = (int)max((int64_t)0, min((int64_t)4, i1 - i4));
 #pragma unroll
                         for (int u = 0; u < NU; ++u) {
                             const int cc = rs * NU + u;
                             const int nv = cc < p.c ? cnt : 0;
-                            float* dst = slot + ((4 + u) * 64 + t) * 4;
+                            float* dst = slot + 4 * 16 * 4 + (u * 64 + t) * 4;
                             const float* vp = nv > 0 ? p.V + i4 + (int64_t)cc * p.ldv : p.V;
                             if (vec) {
                                 cp_async16(dst, vp, 4u * (uint32_t)nv);
@@ -890,16 +892,17 @@ __global__ void __launch_bounds__(NTHREADS_MF, 1)
                     const uint32_t sb = it % SB;
                     issue(kt + DS - 1);
                     cp_wait<DS - 1>();
-                    const float* slot = stg + (kt % DS) * (8 * 64 * 4);
+                    __syncwarp();            // the factor chunks of the other lanes of this warp
+                    const float* slot = stg + (kt % DS) * SLOT;
                     float av[NQ][4], vv[NU][4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float4 w = *reinterpret_cast<const float4*>(slot + (e * 64 + t) * 4);
+                        const float4 w = *reinterpret_cast<const float4*>(slot + (e * 16 + pg) * 4);
                         av[0][e] = w.x; av[1][e] = w.y; av[2][e] = w.z; av[3][e] = w.w;
                     }
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
-                        const float4 w = *reinterpret_cast<const float4*>(slot + ((4 + u) * 64 + t) * 4);
+                        const float4 w = *reinterpret_cast<const float4*>(slot + 4 * 16 * 4 + (u * 64 + t) * 4);
                         vv[u][0] = w.x; vv[u][1] = w.y; vv[u][2] = w.z; vv[u][3] = w.w;
                     }
                     bool free_ = (it < (uint32_t)SB) || wait_done<BN>(sm, it - SB);
