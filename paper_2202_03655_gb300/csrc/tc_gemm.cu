@@ -1216,9 +1216,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const float* fsrc = fl ? p.Z : p.A0F;
                 const int64_t fld = fl ? (int64_t)p.ldZ : (int64_t)p.ldA;
                 const int ao = fl ? p.zoff[m] : p.aoff[m], nq = fl ? p.zcnt[m] : p.acnt[m];
+                // the BN / CP values of the point in one aligned load (blocks start on 16-byte
+                // boundaries, q0 is a multiple of BN / CP), masked past the block
+                constexpr int NG = BN / CP;
+                float fv[NG];
+                const float* fp = fsrc + row * fld + ao + q0;
+                if constexpr (NG == 4) {
+                    const float4 t = rv ? __ldg(reinterpret_cast<const float4*>(fp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    fv[0] = t.x; fv[1] = t.y; fv[2] = t.z; fv[3] = t.w;
+                } else if constexpr (NG == 2) {
+                    const float2 t = rv ? __ldg(reinterpret_cast<const float2*>(fp)) : make_float2(0.f, 0.f);
+                    fv[0] = t.x; fv[1] = t.y;
+                } else {
+                    fv[0] = rv ? __ldg(fp) : 0.f;
+                }
 #pragma unroll
-                for (int g = 0; g < BN / CP; ++g) {
-                    const float f = (rv && q0 + g < nq) ? __ldg(fsrc + row * fld + ao + q0 + g) : 0.f;
+                for (int g = 0; g < NG; ++g) {
+                    const float f = q0 + g < nq ? fv[g] : 0.f;
 #pragma unroll
                     for (int j = 0; j < CP; ++j) y[j] += f * acc[g * CP + j];
                 }
