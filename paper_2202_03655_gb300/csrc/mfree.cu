@@ -507,10 +507,12 @@ hdf_status mf_write(hdf_factor* f, const double* x, int64_t n, int d, const dev:
     const size_t coef = sizeof(T) * 2 * (size_t)levels * tb.tri;
     const size_t budget = 200 * 1024;
     const size_t tabs = dev::zwriter_tab_bytes(pairs, ft.ldZ, chain_stride(d), ft.ng, ft.ldA) + 16;
-    // stage the index tables only when 16 warps still fit beside them (fewer warps measured slower)
+    // stage the index tables only when 16 warps still fit beside them (fewer warps measured
+    // slower); then as many warps as the budget holds, up to 32 (24 at d = 5, p = 64: 7% faster
+    // than 16)
     P.stage = (coef + tabs + 16 * sizeof(T) * (size_t)P.per_warp <= budget) ? 1 : 0;
     const size_t fixed = coef + (P.stage ? tabs : 0);
-    const int warps = (int)std::min<size_t>(16, (budget - std::min(budget, fixed)) / (sizeof(T) * P.per_warp));
+    const int warps = (int)std::min<size_t>(32, (budget - std::min(budget, fixed)) / (sizeof(T) * P.per_warp));
     if (fixed + sizeof(T) * P.per_warp > budget || warps < 1)
         return fail(HDF_ETOOBIG, "hdf_build: matrix-free harmonic tables exceed shared memory");
     const size_t sm = fixed + sizeof(T) * (size_t)warps * P.per_warp;
